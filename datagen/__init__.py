@@ -1,0 +1,274 @@
+"""Seeded synthetic inputs for the unbinned-NLL path.
+
+This module only draws events and writes down the five workload models as plain
+data.  It holds none of the likelihood arithmetic: no normalisation integral, no
+log-likelihood, no gradient.  Both the FP64 oracle and the CUDA path take their
+inputs from here and from nowhere else.
+
+Random numbers come from numpy's Philox4x32-10 counter-based generator (Salmon
+et al., SC'11).  A large sample is drawn in fixed chunks of ``CHUNK`` events,
+chunk ``c`` of seed ``s`` from ``Philox(SeedSequence([s, c]))``, so the data do
+not depend on how the work is split.
+
+The paper's own workloads (Fig. 1: "datasets of 100 000 to 300 000 events for
+various likelihood models") are not available; these five models stand in for
+them.  Sampling methods (the paper's Sec. 3 "Generating Samples" contrasts
+accept/reject with dedicated generators; both are used here):
+  Gaussian      normal draws, truncated to the range by rejection
+  Exponential   inverse CDF of the truncated exponential
+  Chebychev     accept/reject against the bound 1 + sum |c_j|
+  Crystal Ball  accept/reject of uniform proposals (peak height 1)
+  ARGUS (p=1/2) tau ~ Gamma(3/2, rate -c) = (Exp(1) + Z^2/2)/(-c), truncated
+                to the range by rejection, m = m0 sqrt(1 - tau)
+FP32 columns hold the FP32 rounding of each draw; a draw whose FP32 value
+leaves the observable range is rejected and redrawn.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+CHUNK = 1 << 20
+SEEDS = {"c1": 12875001, "c2": 12875002, "c3": 12875003, "c4": 12875004,
+         "c5": 12875005}
+
+
+def rng(seed: int, chunk: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, chunk])))
+
+
+# ----------------------------------------------------------------- samplers
+
+def _fill(r, n, draw, dtype, lo, hi):
+    """Collect n draws from ``draw(r, k)`` that lie in [lo, hi] after rounding
+    to ``dtype``."""
+    out = np.empty(n, dtype)
+    got = 0
+    while got < n:
+        need = n - got
+        x = draw(r, int(need * 1.25) + 64).astype(dtype)
+        x = x[(x >= lo) & (x <= hi)]
+        k = min(len(x), need)
+        out[got:got + k] = x[:k]
+        got += k
+    return out
+
+
+def gauss(r, n, mu, sigma, lo, hi, dtype=np.float64):
+    return _fill(r, n, lambda r, k: r.normal(mu, sigma, k), dtype, lo, hi)
+
+
+def expo(r, n, lam, lo, hi, dtype=np.float64):
+    L = hi - lo
+    if lam == 0.0:
+        return _fill(r, n, lambda r, k: lo + L * r.random(k), dtype, lo, hi)
+    span = math.expm1(lam * L)
+    return _fill(r, n, lambda r, k: lo + np.log1p(r.random(k) * span) / lam, dtype, lo, hi)
+
+
+def cheb(r, n, coefs, lo, hi, dtype=np.float64):
+    bound = 1.0 + float(np.sum(np.abs(coefs)))
+
+    def draw(r, k):
+        x = lo + (hi - lo) * r.random(k)
+        u = (2.0 * x - lo - hi) / (hi - lo)
+        t_prev, t_cur, shape = np.ones_like(u), u, np.ones_like(u)
+        for j, c in enumerate(coefs, start=1):
+            if j > 1:
+                t_prev, t_cur = t_cur, 2.0 * u * t_cur - t_prev
+            shape = shape + c * t_cur
+        return x[r.random(k) * bound < shape]
+    return _fill(r, n, draw, dtype, lo, hi)
+
+
+def crystal_ball(r, n, m0, sigma, alpha, nexp, lo, hi, dtype=np.float64):
+    a = abs(alpha)
+    sgn = 1.0 if alpha >= 0 else -1.0
+    big_a = (nexp / a) ** nexp * math.exp(-0.5 * a * a)
+    big_b = nexp / a - a
+
+    def draw(r, k):
+        x = lo + (hi - lo) * r.random(k)
+        t = sgn * (x - m0) / sigma
+        in_core = t > -a
+        core = np.exp(-0.5 * t * t)
+        tail = big_a * np.power(np.where(in_core, big_b + a, big_b - t), -nexp)
+        shape = np.where(in_core, core, tail)
+        return x[r.random(k) < shape]
+    return _fill(r, n, draw, dtype, lo, hi)
+
+
+def argus_half(r, n, m0, c, lo, hi, dtype=np.float64):
+    """ARGUS with p = 1/2 through its Gamma(3/2) form in tau."""
+    k_rate = -c
+    if not k_rate > 0:
+        raise ValueError("argus_half needs c < 0")
+    tau_max = 1.0 - (lo / m0) ** 2
+
+    def draw(r, k):
+        tau = (r.standard_exponential(k) + 0.5 * r.standard_normal(k) ** 2) / k_rate
+        tau = tau[(tau > 0.0) & (tau <= tau_max)]
+        m = m0 * np.sqrt(1.0 - tau)
+        return m[m < m0]
+    out = _fill(r, n, draw, dtype, lo, hi)
+    if np.any(out.astype(np.float64) >= m0):  # the open support, after rounding
+        raise AssertionError("ARGUS draw at or above the endpoint")
+    return out
+
+
+# ----------------------------------------------------------------- workloads
+# Each workload returns {"spec", "cols" [n_obs, n], "dtype", "params",
+# "fixed", "name"}.  spec["params"] holds the evaluation point.
+
+def _gauss_spec(mu, sigma, lo, hi):
+    return {"obs": [(lo, hi)], "params": [mu, sigma], "fixed": [False, False],
+            "nodes": [{"type": "gauss", "obs": 0, "params": [0, 1]}], "root": 0}
+
+
+def c1(n=10_000, seed=SEEDS["c1"]):
+    """Single Gaussian on [-10, 10]; events from N(0.3, 1.2); NLL at (0.25, 1.1)."""
+    x = _chunked(n, seed, lambda r, k: gauss(r, k, 0.3, 1.2, -10.0, 10.0))
+    return {"name": "gauss_1e4_f64", "spec": _gauss_spec(0.25, 1.1, -10.0, 10.0),
+            "cols": x.reshape(1, -1), "dtype": "f64"}
+
+
+def gauss_exp_spec(mu=5.0, sigma=0.5, lam=-0.3, frac=0.2, lo=0.0, hi=10.0):
+    return {"obs": [(lo, hi)], "params": [mu, sigma, lam, frac],
+            "fixed": [False] * 4,
+            "nodes": [{"type": "gauss", "obs": 0, "params": [0, 1]},
+                      {"type": "exp", "obs": 0, "params": [2]},
+                      {"type": "add_frac", "children": [0, 1], "params": [3]}],
+            "root": 2}
+
+
+def c2(n=1_000_000, seed=SEEDS["c2"]):
+    """Gauss(5, 0.5) + Exp(-0.3) on [0, 10], fraction 0.2 on the Gaussian."""
+    def draw(r, k):
+        sig = r.random(k) < 0.2
+        ns = int(sig.sum())
+        out = np.empty(k)
+        out[sig] = gauss(r, ns, 5.0, 0.5, 0.0, 10.0)
+        out[~sig] = expo(r, k - ns, -0.3, 0.0, 10.0)
+        return out
+    x = _chunked(n, seed, draw)
+    return {"name": "gauss_exp_frac_1e6_f64", "spec": gauss_exp_spec(),
+            "cols": x.reshape(1, -1), "dtype": "f64"}
+
+
+CHEB4 = (0.2, -0.1, 0.05, 0.02)
+
+
+def prod3_spec(nu, extended=True):
+    nodes = [{"type": "gauss", "obs": 0, "params": [0, 1]},
+             {"type": "exp", "obs": 1, "params": [2]},
+             {"type": "cheb", "obs": 2, "params": [3, 4, 5, 6]},
+             {"type": "prod", "children": [0, 1, 2]}]
+    params = [0.0, 1.5, -0.5, *CHEB4]
+    if extended:
+        nodes.append({"type": "add_ext", "children": [3], "params": [7]})
+        params.append(float(nu))
+    return {"obs": [(-8.0, 8.0), (0.0, 10.0), (-1.0, 1.0)], "params": params,
+            "fixed": [False] * len(params), "nodes": nodes, "root": len(nodes) - 1}
+
+
+def c3(n=10_000_000, seed=SEEDS["c3"], extended=True):
+    """Gauss(x;0,1.5) x Exp(y;-0.5) x Cheb4(z) with FP32 columns; extended by a
+    yield nu (evaluated at nu = n) so that the model has 8 parameters."""
+    def draw(r, k):
+        return np.stack([gauss(r, k, 0.0, 1.5, -8.0, 8.0, np.float32),
+                         expo(r, k, -0.5, 0.0, 10.0, np.float32),
+                         cheb(r, k, CHEB4, -1.0, 1.0, np.float32)])
+    cols = _chunked(n, seed, draw, ncols=3, dtype=np.float32)
+    return {"name": "prod3_1e7_f32", "spec": prod3_spec(n, extended), "cols": cols,
+            "dtype": "f32"}
+
+
+def gauss_exp_ext_spec(mu=5.0, sigma=0.5, lam=-0.3, nu_s=1000.0, nu_b=1000.0):
+    return {"obs": [(0.0, 10.0)], "params": [mu, sigma, lam, nu_s, nu_b],
+            "fixed": [False] * 5,
+            "nodes": [{"type": "gauss", "obs": 0, "params": [0, 1]},
+                      {"type": "exp", "obs": 0, "params": [2]},
+                      {"type": "add_ext", "children": [0, 1], "params": [3, 4]}],
+            "root": 2}
+
+
+def c4(toys=4096, seed=SEEDS["c4"], nu_s_range=(500.0, 5e4), nu_b_range=(1e3, 1e5)):
+    """Toy study: per toy nu_s, nu_b log-uniform, counts Poisson, events from
+    Gauss(5, 0.5) + Exp(-0.3) on [0, 10], shuffled within the toy, FP64,
+    concatenated by toy.  Start point (per toy): generating shape with mu+0.05,
+    yields = the observed counts."""
+    r = rng(seed, 0)
+    ls, lb = np.log(nu_s_range), np.log(nu_b_range)
+    nu_s = np.exp(r.uniform(ls[0], ls[1], toys))
+    nu_b = np.exp(r.uniform(lb[0], lb[1], toys))
+    n_s = r.poisson(nu_s)
+    n_b = r.poisson(nu_b)
+    counts = n_s + n_b
+    offsets = np.zeros(toys + 1, np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    x = np.empty(int(offsets[-1]))
+    for t in range(toys):
+        rt = rng(seed, 1 + t)
+        ev = np.concatenate([gauss(rt, int(n_s[t]), 5.0, 0.5, 0.0, 10.0),
+                             expo(rt, int(n_b[t]), -0.3, 0.0, 10.0)])
+        rt.shuffle(ev)
+        x[offsets[t]:offsets[t + 1]] = ev
+    start = np.empty((toys, 5))
+    start[:, 0] = 5.05
+    start[:, 1] = 0.5
+    start[:, 2] = -0.3
+    start[:, 3] = n_s
+    start[:, 4] = n_b
+    return {"name": f"toys{toys}_gauss_exp_ext_f64", "spec": gauss_exp_ext_spec(),
+            "cols": x.reshape(1, -1), "dtype": "f64", "offsets": offsets,
+            "params_matrix": start, "nu_true": np.stack([nu_s, nu_b], 1)}
+
+
+def cb_argus_spec(nu_s=1e6, nu_b=1e8):
+    # params: 0 m0_cb, 1 sigma, 2 alpha, 3 n, 4 m0_argus, 5 c, 6 p, 7 nu_s, 8 nu_b
+    return {"obs": [(5.20, 5.29)],
+            "params": [5.279, 0.003, 1.5, 3.0, 5.29, -20.0, 0.5, float(nu_s), float(nu_b)],
+            "fixed": [False, False, False, False, True, False, True, False, False],
+            "nodes": [{"type": "cb", "obs": 0, "params": [0, 1, 2, 3]},
+                      {"type": "argus", "obs": 0, "params": [4, 5, 6]},
+                      {"type": "add_ext", "children": [0, 1], "params": [7, 8]}],
+            "root": 2}
+
+
+def c5(n_sig=1_000_000, n_bkg=100_000_000, seed=SEEDS["c5"]):
+    """Crystal Ball (5.279, 0.003, 1.5, 3) + ARGUS (5.29, -20, 1/2) on
+    [5.20, 5.29], FP32 column, exactly n_sig + n_bkg events in a uniformly
+    random order (per-chunk hypergeometric split, then a shuffle)."""
+    n = n_sig + n_bkg
+    nchunks = (n + CHUNK - 1) // CHUNK
+    r0 = rng(seed, 0)
+    left = np.array([n_sig, n_bkg], np.int64)
+    out = np.empty(n, np.float32)
+    for c in range(nchunks):
+        k = min(CHUNK, n - c * CHUNK)
+        split = r0.multivariate_hypergeometric(left, k) if left.sum() > k else left.copy()
+        left -= split
+        r = rng(seed, 1 + c)
+        ev = np.concatenate([
+            crystal_ball(r, int(split[0]), 5.279, 0.003, 1.5, 3.0, 5.20, 5.29, np.float32),
+            argus_half(r, int(split[1]), 5.29, -20.0, 5.20, 5.29, np.float32)])
+        r.shuffle(ev)
+        out[c * CHUNK:c * CHUNK + k] = ev
+    return {"name": "cb_argus_ext_1.01e8_f32", "spec": cb_argus_spec(n_sig, n_bkg),
+            "cols": out.reshape(1, -1), "dtype": "f32"}
+
+
+def _chunked(n, seed, draw, ncols=1, dtype=np.float64):
+    out = np.empty((ncols, n), dtype) if ncols > 1 else np.empty(n, dtype)
+    for c in range((n + CHUNK - 1) // CHUNK):
+        k = min(CHUNK, n - c * CHUNK)
+        block = draw(rng(seed, c), k)
+        if ncols > 1:
+            out[:, c * CHUNK:c * CHUNK + k] = block
+        else:
+            out[c * CHUNK:c * CHUNK + k] = block
+    return out
+
+
+WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5}

@@ -1,0 +1,681 @@
+/*
+ * rf_oracle.c -- FP64 CPU oracle for the unbinned NLL of a PDF graph.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
+ * bench's CPU-baseline leg, never by the product path.  Shares no code with the
+ * CUDA library.
+ *
+ * What it computes (Hageboeck, "A Faster, More Intuitive RooFit"):
+ *  - Sec. 5.1: the likelihood of each dataset entry is the probability of the
+ *    top node of a computation graph whose leaves hold the entry's observables;
+ *    the NLL is minus the sum of their logs.  The walk below evaluates every
+ *    node for every entry, as the classic single-value evaluation does.
+ *  - Sec. 5.1 (constant branches): parameter-only values -- here the leaf
+ *    normalisation integrals and their derivatives -- are computed once.
+ *  - Sec. 3 ("Analytic Integrals"): each PDF is divided by its integral over
+ *    the observable range, taken analytically.
+ *  - Sec. 3 ("Checking parameters"): parameters outside a PDF's definition
+ *    range, or an entry with non-positive / non-finite probability, give
+ *    NLL = +inf instead of a silent NaN.
+ * The paper prints no PDF formula; the leaf definitions are the standard ones:
+ *  Gaussian   f = exp(-(x-mu)^2 / (2 sigma^2))
+ *  Exponential f = exp(lambda x)
+ *  Chebychev  f = 1 + sum_{j>=1} c_j T_j(x'),  x' = (2x-lo-hi)/(hi-lo)
+ *             (implicit T_0 coefficient 1; order = number of coefficients)
+ *  CrystalBall t = s (x-m0)/sigma with s = sign(alpha), A = |alpha|:
+ *             f = exp(-t^2/2) for t > -A, else
+ *             f = exp(-A^2/2) * D^-n, D = 1 - (A/n)(A+t)   (== A'(B-t)^-n)
+ *  ARGUS      f = x tau^p exp(c tau), tau = 1-(x/m0)^2 for x < m0, else 0
+ *  Add (fractions)  P = sum_{k<K-1} f_k P_k + (1 - sum f_k) P_{K-1}
+ *  Add (extended)   P = sum_k nu_k P_k,  NLL += sum_k nu_k  (no log n! term)
+ *  Prod             P = prod_k P_k   (children on disjoint observables)
+ * Gradient: forward mode; each node returns P and dP/dtheta for all theta.
+ * Sums: Neumaier compensated, in event order, per fixed chunk of events;
+ * chunk results are merged in chunk order, so nthreads does not change them.
+ *
+ * Pins (tests/test_oracle_*.py): every normalised leaf integrates to one by
+ * high-precision quadrature; normalisation derivatives against finite
+ * differences of the quadrature-pinned integrals; the Gaussian NLL against its
+ * closed form from sufficient statistics; ML mu and sigma against the sample
+ * mean and 1/n standard deviation; Add/Prod against hand-expanded formulas;
+ * Crystal Ball value and slope continuity at t=-A; the gradient against
+ * Richardson-extrapolated central differences; the extended-ML invariant
+ * sum nu = n; Adam against its published update written out by hand.
+ */
+#include "rf_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define SQRT2 1.41421356237309504880
+#define SQRT_PI_2 1.25331413731550025121 /* sqrt(pi/2) */
+#define SQRT_PI 1.77245385090551602730
+
+/* ------------------------------------------------------------------ */
+/* small helpers                                                       */
+/* ------------------------------------------------------------------ */
+
+/* erf(z2) - erf(z1) for z1 <= z2, taken from erfc when both arguments are on
+ * the same side of zero so that tails do not cancel. */
+static double erf_diff(double z1, double z2) {
+  if (z1 >= 0.0) return erfc(z1) - erfc(z2);
+  if (z2 <= 0.0) return erfc(-z2) - erfc(-z1);
+  return erf(z2) - erf(z1);
+}
+
+/* E1(y) = (e^y - 1)/y, 1 at y = 0 */
+static double e1(double y) { return y == 0.0 ? 1.0 : expm1(y) / y; }
+
+/* dE1/dy = (e^y (y-1) + 1)/y^2; Taylor series sum_{k>=1} k y^(k-1)/(k+1)!
+ * near 0, where the closed form cancels. */
+static double e1_prime(double y) {
+  if (fabs(y) < 1.0) {
+    double s = 0.0, ypow = 1.0, fact = 2.0; /* (k+1)! for k = 1 */
+    for (int k = 1; k <= 30; ++k) {
+      s += k * ypow / fact;
+      ypow *= y;
+      fact *= (double)(k + 2);
+    }
+    return s;
+  }
+  return (exp(y) * (y - 1.0) + 1.0) / (y * y);
+}
+
+/* Neumaier compensated accumulator */
+typedef struct {
+  double s, c;
+} nsum;
+static void nsum_add(nsum* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x))
+    a->c += (a->s - t) + x;
+  else
+    a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double nsum_val(const nsum* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------ */
+/* leaves: unnormalised value f and d log f / d theta_j                */
+/* ------------------------------------------------------------------ */
+
+/* Returns f(x) (may be 0, or negative for a Chebychev polynomial) and fills
+ * dlogf[j] = d log f / d theta_j where f > 0. */
+static int leaf_value(int type, const double* th, int nth, double lo, double hi,
+                      double x, double* f_out, double* dlogf) {
+  for (int j = 0; j < nth; ++j) dlogf[j] = 0.0;
+  switch (type) {
+    case ORC_GAUSS: {
+      if (nth != 2) return ORC_EINVAL;
+      double mu = th[0], sigma = th[1];
+      double d = (x - mu) / sigma;
+      *f_out = exp(-0.5 * d * d);
+      dlogf[0] = (x - mu) / (sigma * sigma);
+      dlogf[1] = (x - mu) * (x - mu) / (sigma * sigma * sigma);
+      return ORC_OK;
+    }
+    case ORC_EXP: {
+      if (nth != 1) return ORC_EINVAL;
+      *f_out = exp(th[0] * x);
+      dlogf[0] = x;
+      return ORC_OK;
+    }
+    case ORC_CHEB: {
+      if (nth < 1 || nth > ORC_MAXNP) return ORC_EINVAL;
+      double xp = (2.0 * x - lo - hi) / (hi - lo);
+      double T[ORC_MAXNP + 1];
+      T[0] = 1.0;
+      T[1] = xp;
+      for (int j = 2; j <= nth; ++j) T[j] = 2.0 * xp * T[j - 1] - T[j - 2];
+      double f = 1.0;
+      for (int j = 1; j <= nth; ++j) f += th[j - 1] * T[j];
+      *f_out = f;
+      for (int j = 1; j <= nth; ++j) dlogf[j - 1] = T[j] / f;
+      return ORC_OK;
+    }
+    case ORC_CB: {
+      if (nth != 4) return ORC_EINVAL;
+      double m0 = th[0], sigma = th[1], alpha = th[2], n = th[3];
+      double s = alpha >= 0.0 ? 1.0 : -1.0;
+      double A = fabs(alpha);
+      double t = s * (x - m0) / sigma;
+      double du_dt, du_dA = 0.0, du_dn = 0.0, u;
+      if (t > -A) {
+        u = -0.5 * t * t;
+        du_dt = -t;
+      } else {
+        double D = 1.0 - (A / n) * (A + t);
+        u = -0.5 * A * A - n * log(D);
+        du_dt = A / D;
+        du_dA = -A + (2.0 * A + t) / D;
+        du_dn = -log(D) + 1.0 - 1.0 / D;
+      }
+      *f_out = exp(u);
+      dlogf[0] = du_dt * (-s / sigma);
+      dlogf[1] = du_dt * (-t / sigma);
+      dlogf[2] = s * du_dA;
+      dlogf[3] = du_dn;
+      return ORC_OK;
+    }
+    case ORC_ARGUS: {
+      if (nth != 3) return ORC_EINVAL;
+      double m0 = th[0], c = th[1], p = th[2];
+      if (x >= m0) {
+        *f_out = 0.0;
+        return ORC_OK;
+      }
+      double r = x / m0;
+      double tau = 1.0 - r * r;
+      *f_out = x * pow(tau, p) * exp(c * tau);
+      dlogf[0] = (p / tau + c) * 2.0 * x * x / (m0 * m0 * m0);
+      dlogf[1] = tau;
+      dlogf[2] = log(tau);
+      return ORC_OK;
+    }
+    default:
+      return ORC_EINVAL;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* leaves: normalisation integrals and their derivatives               */
+/* ------------------------------------------------------------------ */
+
+/* G(q, tau, c) = int_0^tau s^q e^{c s} ds for q = 1/2 or 3/2.
+ * Closed form through the lower incomplete gamma function when c < 0 and
+ * k tau >= 1/2 (k = -c):
+ *   gamma(3/2, y) = (sqrt(pi)/2) erf(sqrt y) - sqrt(y) e^-y
+ *   gamma(5/2, y) = (3/2) gamma(3/2, y) - y^(3/2) e^-y
+ *   G = k^-(q+1) gamma(q+1, k tau);
+ * otherwise the power series tau^(q+1) sum_j (c tau)^j / (j! (j+q+1)). */
+static double argus_G(double q, double tau, double c) {
+  if (tau <= 0.0) return 0.0;
+  double y = c * tau;
+  if (c < 0.0 && -y >= 0.5) {
+    double k = -c, ky = -y;
+    double g32 = 0.5 * SQRT_PI * erf(sqrt(ky)) - sqrt(ky) * exp(-ky);
+    if (q == 0.5) return pow(k, -1.5) * g32;
+    double g52 = 1.5 * g32 - pow(ky, 1.5) * exp(-ky);
+    return pow(k, -2.5) * g52;
+  }
+  double sum = 0.0, term = 1.0; /* y^j / j! */
+  for (int j = 0; j < 2000; ++j) {
+    double add = term / (j + q + 1.0);
+    sum += add;
+    if (j > fabs(y) && fabs(add) < 1e-18 * fabs(sum)) break;
+    term *= y / (j + 1.0);
+  }
+  return pow(tau, q + 1.0) * sum;
+}
+
+static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
+                     double* I_out, double* dI) {
+  for (int j = 0; j < nth; ++j) dI[j] = 0.0;
+  if (!(hi > lo)) return ORC_EINVAL;
+  switch (type) {
+    case ORC_GAUSS: {
+      if (nth != 2) return ORC_EINVAL;
+      double mu = th[0], sigma = th[1];
+      if (!(sigma > 0.0)) return ORC_EDOMAIN;
+      double ua = (lo - mu) / sigma, ub = (hi - mu) / sigma;
+      double I = sigma * SQRT_PI_2 * erf_diff(ua / SQRT2, ub / SQRT2);
+      double fa = exp(-0.5 * ua * ua), fb = exp(-0.5 * ub * ub);
+      *I_out = I;
+      dI[0] = fa - fb;                       /* int (x-mu)/sigma^2 f dx  */
+      dI[1] = ua * fa - ub * fb + I / sigma; /* int (x-mu)^2/sigma^3 f dx */
+      return ORC_OK;
+    }
+    case ORC_EXP: {
+      if (nth != 1) return ORC_EINVAL;
+      double lam = th[0], L = hi - lo, s = lam * L;
+      double I = exp(lam * lo) * L * e1(s);
+      /* d I / d lambda = int x e^{lambda x} dx = I * <x>,
+       * <x> = lo + L * (1/(1 - e^-s) - 1/s), series near s = 0 */
+      double mfrac;
+      if (fabs(s) < 1e-3)
+        mfrac = 0.5 + s / 12.0 - s * s * s / 720.0 + s * s * s * s * s / 30240.0;
+      else
+        mfrac = 1.0 / (-expm1(-s)) - 1.0 / s;
+      *I_out = I;
+      dI[0] = I * (lo + L * mfrac);
+      return ORC_OK;
+    }
+    case ORC_CHEB: {
+      if (nth < 1 || nth > ORC_MAXNP) return ORC_EINVAL;
+      /* int_{-1}^{1} T_j = (1 + (-1)^j)/(1 - j^2) for j != 1, 0 for j = 1 */
+      double half = 0.5 * (hi - lo);
+      double J = 2.0;
+      for (int j = 1; j <= nth; ++j) {
+        double tj = (j == 1) ? 0.0 : (1.0 + ((j % 2) ? -1.0 : 1.0)) / (1.0 - (double)j * j);
+        J += th[j - 1] * tj;
+        dI[j - 1] = half * tj;
+      }
+      *I_out = half * J;
+      if (!(*I_out > 0.0)) return ORC_EDOMAIN;
+      return ORC_OK;
+    }
+    case ORC_CB: {
+      if (nth != 4) return ORC_EINVAL;
+      double m0 = th[0], sigma = th[1], alpha = th[2], n = th[3];
+      if (!(sigma > 0.0) || !(n > 0.0) || alpha == 0.0) return ORC_EDOMAIN;
+      double s = alpha >= 0.0 ? 1.0 : -1.0, A = fabs(alpha);
+      double tlo, thi;
+      if (s > 0) {
+        tlo = (lo - m0) / sigma;
+        thi = (hi - m0) / sigma;
+      } else {
+        tlo = -(hi - m0) / sigma;
+        thi = -(lo - m0) / sigma;
+      }
+      /* Gaussian core over [max(tlo,-A), thi] */
+      double core = 0.0;
+      if (thi > -A) {
+        double c1 = tlo > -A ? tlo : -A;
+        core = SQRT_PI_2 * erf_diff(c1 / SQRT2, thi / SQRT2);
+      }
+      /* power-law tail over [tlo, min(thi,-A)], in the variable D:
+       * dt = -(n/A) dD, so tail = (n/A) e^{-A^2/2} int_{D2}^{D1} D^-n dD.
+       * With eps = 1-n, L = log D, Delta = L1 - L2:
+       *   Phi  = int D^{eps-1} dD       = e^{eps L2} Delta E1(eps Delta)
+       *   Phi' = int D^{eps-1} log D dD = L2 Phi + e^{eps L2} Delta^2 E1'(eps Delta)
+       *   Psi  = int D^{-n-1} dD        = (D2^-n - D1^-n)/n
+       * and, at fixed t-limits (the integrand is continuous at t=-A, so the
+       * moving split point contributes nothing),
+       *   d tail/dA = (n/A) e^{-A^2/2} (A + n/A) (Psi - Phi)
+       *   d tail/dn = (n/A) e^{-A^2/2} (Phi - Phi' - Psi). */
+      double tail = 0.0, dT_dA = 0.0, dT_dn = 0.0;
+      if (tlo < -A) {
+        double t1 = tlo, t2 = thi < -A ? thi : -A;
+        double D1 = 1.0 - (A / n) * (A + t1), D2 = 1.0 - (A / n) * (A + t2);
+        double L1 = log(D1), L2 = log(D2), Dl = L1 - L2, eps = 1.0 - n;
+        double ez = exp(eps * L2);
+        double Phi = ez * Dl * e1(eps * Dl);
+        double dPhi = L2 * Phi + ez * Dl * Dl * e1_prime(eps * Dl);
+        double Psi = (pow(D2, -n) - pow(D1, -n)) / n;
+        double pref = (n / A) * exp(-0.5 * A * A);
+        tail = pref * Phi;
+        dT_dA = pref * (A + n / A) * (Psi - Phi);
+        dT_dn = pref * (Phi - dPhi - Psi);
+      }
+      double J = core + tail;
+      /* integrand g(t) at the two ends of the range */
+      double g_lo, g_hi;
+      {
+        double t = tlo;
+        g_lo = (t > -A) ? exp(-0.5 * t * t)
+                        : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + t), -n);
+        t = thi;
+        g_hi = (t > -A) ? exp(-0.5 * t * t)
+                        : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + t), -n);
+      }
+      *I_out = sigma * J;
+      dI[0] = -s * (g_hi - g_lo);
+      dI[1] = J + (tlo * g_lo - thi * g_hi);
+      dI[2] = s * sigma * dT_dA;
+      dI[3] = sigma * dT_dn;
+      return ORC_OK;
+    }
+    case ORC_ARGUS: {
+      if (nth != 3) return ORC_EINVAL;
+      double m0 = th[0], c = th[1], p = th[2];
+      if (p != 0.5) return ORC_EUNSUPPORTED;
+      if (!(m0 > lo) || lo < 0.0) return ORC_EDOMAIN;
+      double bp = hi < m0 ? hi : m0;
+      double ra = lo / m0, rb = bp / m0;
+      double ta = 1.0 - ra * ra, tb = 1.0 - rb * rb;
+      /* m dm = -(m0^2/2) d tau */
+      double h = 0.5 * m0 * m0;
+      double I = h * (argus_G(0.5, ta, c) - argus_G(0.5, tb, c));
+      *I_out = I;
+      dI[1] = h * (argus_G(1.5, ta, c) - argus_G(1.5, tb, c));
+      double ea = (1.0 - ta) * pow(ta, p) * exp(c * ta);
+      double eb = tb > 0.0 ? (1.0 - tb) * pow(tb, p) * exp(c * tb) : 0.0;
+      dI[0] = m0 * (ea - eb) + 2.0 * I / m0;
+      dI[2] = NAN; /* d/dp of the incomplete gamma: not provided */
+      return ORC_OK;
+    }
+    default:
+      return ORC_EINVAL;
+  }
+}
+
+int orc_leaf_logf(int type, const double* theta, int ntheta, double lo,
+                  double hi, double x, double* logf, double* dlogf) {
+  double f;
+  int rc = leaf_value(type, theta, ntheta, lo, hi, x, &f, dlogf);
+  if (rc) return rc;
+  *logf = f > 0.0 ? log(f) : (f == 0.0 ? -INFINITY : NAN);
+  return ORC_OK;
+}
+
+int orc_leaf_norm(int type, const double* theta, int ntheta, double lo,
+                  double hi, double* I, double* dI) {
+  return leaf_norm(type, theta, ntheta, lo, hi, I, dI);
+}
+
+/* ------------------------------------------------------------------ */
+/* graph walk                                                          */
+/* ------------------------------------------------------------------ */
+
+static int is_leaf(int t) { return t >= ORC_GAUSS && t <= ORC_ARGUS; }
+
+typedef struct {
+  double I[ORC_MAXNODE];
+  double dlogI[ORC_MAXNODE][ORC_MAXNP];
+} leaf_cache;
+
+/* bit mask of the observables a subtree depends on; -1 on a malformed graph */
+static int64_t obs_mask(const orc_model* m, int i, int depth) {
+  if (i < 0 || i >= m->n_nodes || depth > m->n_nodes) return -1;
+  int t = m->type[i];
+  if (is_leaf(t)) {
+    int o = m->obs[i];
+    if (o < 0 || o >= m->n_obs || o >= 62) return -1;
+    return (int64_t)1 << o;
+  }
+  int64_t acc = 0;
+  for (int k = 0; k < m->nchild[i]; ++k) {
+    int64_t c = obs_mask(m, m->child[i * ORC_MAXCH + k], depth + 1);
+    if (c < 0) return -1;
+    if (t == ORC_PROD && (acc & c)) return -2; /* shared observable */
+    acc |= c;
+  }
+  return acc;
+}
+
+static int validate(const orc_model* m) {
+  if (!m || m->n_nodes <= 0 || m->n_nodes > ORC_MAXNODE) return ORC_EINVAL;
+  if (m->root < 0 || m->root >= m->n_nodes) return ORC_EINVAL;
+  if (m->n_par < 0 || m->n_par > ORC_MAXPAR) return ORC_EINVAL;
+  for (int i = 0; i < m->n_nodes; ++i) {
+    int t = m->type[i];
+    if (t < ORC_GAUSS || t > ORC_PROD) return ORC_EINVAL;
+    if (m->npar[i] < 0 || m->npar[i] > ORC_MAXNP) return ORC_EINVAL;
+    for (int j = 0; j < m->npar[i]; ++j) {
+      int p = m->par[i * ORC_MAXNP + j];
+      if (p < 0 || p >= m->n_par) return ORC_EINVAL;
+    }
+    if (!is_leaf(t)) {
+      int K = m->nchild[i];
+      if (K < 1 || K > ORC_MAXCH) return ORC_EINVAL;
+      if (t == ORC_ADD_FRAC && (K < 2 || m->npar[i] != K - 1)) return ORC_EINVAL;
+      if (t == ORC_ADD_EXT && m->npar[i] != K) return ORC_EINVAL;
+      if (t == ORC_ADD_EXT && i != m->root) return ORC_EUNSUPPORTED;
+      if (t == ORC_PROD && m->npar[i] != 0) return ORC_EINVAL;
+    }
+  }
+  int64_t mask = obs_mask(m, m->root, 0);
+  if (mask == -2) return ORC_EUNSUPPORTED;
+  if (mask < 0) return ORC_EINVAL;
+  for (int o = 0; o < m->n_obs; ++o)
+    if (!(m->obs_hi[o] > m->obs_lo[o])) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+static int fill_cache(const orc_model* m, const double* params, leaf_cache* lc) {
+  int rc_any = ORC_OK;
+  for (int i = 0; i < m->n_nodes; ++i) {
+    if (!is_leaf(m->type[i])) continue;
+    double th[ORC_MAXNP], dI[ORC_MAXNP];
+    int np = m->npar[i];
+    for (int j = 0; j < np; ++j) th[j] = params[m->par[i * ORC_MAXNP + j]];
+    int o = m->obs[i];
+    double I;
+    int rc = leaf_norm(m->type[i], th, np, m->obs_lo[o], m->obs_hi[o], &I, dI);
+    if (rc == ORC_EINVAL || rc == ORC_EUNSUPPORTED) return rc;
+    if (rc == ORC_EDOMAIN || !(I > 0.0) || !isfinite(I)) rc_any = ORC_EDOMAIN;
+    lc->I[i] = I;
+    for (int j = 0; j < np; ++j) lc->dlogI[i][j] = dI[j] / I;
+  }
+  return rc_any;
+}
+
+/* value v and derivative dv[n_par] (may be NULL) of node i at one event */
+static void eval_node(const orc_model* m, int i, const double* params,
+                      const double* xrow, const leaf_cache* lc, double* v,
+                      double* dv) {
+  int P = m->n_par;
+  int t = m->type[i];
+  if (dv)
+    for (int p = 0; p < P; ++p) dv[p] = 0.0;
+  if (is_leaf(t)) {
+    double th[ORC_MAXNP] = {0}, dlogf[ORC_MAXNP], f;
+    int np = m->npar[i], o = m->obs[i];
+    for (int j = 0; j < np; ++j) th[j] = params[m->par[i * ORC_MAXNP + j]];
+    leaf_value(t, th, np, m->obs_lo[o], m->obs_hi[o], xrow[o], &f, dlogf);
+    double val = f / lc->I[i];
+    *v = val;
+    if (dv && f != 0.0)
+      for (int j = 0; j < np; ++j)
+        dv[m->par[i * ORC_MAXNP + j]] += val * (dlogf[j] - lc->dlogI[i][j]);
+    return;
+  }
+  int K = m->nchild[i];
+  double cv[ORC_MAXCH];
+  double cdv[ORC_MAXCH][ORC_MAXPAR];
+  for (int k = 0; k < K; ++k)
+    eval_node(m, m->child[i * ORC_MAXCH + k], params, xrow, lc, &cv[k],
+              dv ? cdv[k] : NULL);
+  if (t == ORC_PROD) {
+    double prod = 1.0;
+    for (int k = 0; k < K; ++k) prod *= cv[k];
+    *v = prod;
+    if (dv)
+      for (int k = 0; k < K; ++k) {
+        double others = 1.0;
+        for (int j = 0; j < K; ++j)
+          if (j != k) others *= cv[j];
+        for (int p = 0; p < P; ++p) dv[p] += others * cdv[k][p];
+      }
+    return;
+  }
+  /* Add: coefficients */
+  double coef[ORC_MAXCH];
+  if (t == ORC_ADD_FRAC) {
+    double rest = 1.0;
+    for (int k = 0; k < K - 1; ++k) {
+      coef[k] = params[m->par[i * ORC_MAXNP + k]];
+      rest -= coef[k];
+    }
+    coef[K - 1] = rest;
+  } else {
+    for (int k = 0; k < K; ++k) coef[k] = params[m->par[i * ORC_MAXNP + k]];
+  }
+  double sum = 0.0;
+  for (int k = 0; k < K; ++k) sum += coef[k] * cv[k];
+  *v = sum;
+  if (dv) {
+    for (int k = 0; k < K; ++k)
+      for (int p = 0; p < P; ++p) dv[p] += coef[k] * cdv[k][p];
+    if (t == ORC_ADD_FRAC) {
+      for (int k = 0; k < K - 1; ++k)
+        dv[m->par[i * ORC_MAXNP + k]] += cv[k] - cv[K - 1];
+    } else {
+      for (int k = 0; k < K; ++k) dv[m->par[i * ORC_MAXNP + k]] += cv[k];
+    }
+  }
+}
+
+/* parameter checks of the composite nodes (fractions in [0,1], yields >= 0) */
+static int check_coefs(const orc_model* m, const double* params) {
+  for (int i = 0; i < m->n_nodes; ++i) {
+    int t = m->type[i];
+    if (t == ORC_ADD_FRAC) {
+      double rest = 1.0;
+      for (int k = 0; k < m->nchild[i] - 1; ++k) {
+        double f = params[m->par[i * ORC_MAXNP + k]];
+        if (!(f >= 0.0 && f <= 1.0)) return ORC_EDOMAIN;
+        rest -= f;
+      }
+      if (rest < -1e-15) return ORC_EDOMAIN;
+    } else if (t == ORC_ADD_EXT) {
+      for (int k = 0; k < m->nchild[i]; ++k)
+        if (!(params[m->par[i * ORC_MAXNP + k]] >= 0.0)) return ORC_EDOMAIN;
+    }
+  }
+  return ORC_OK;
+}
+
+#define ORC_CHUNK 4096
+
+int orc_nll(const orc_model* m, const double* params, const double* cols,
+            int64_t col_stride, int64_t n, int nthreads, double* nll,
+            double* grad) {
+  return orc_nll_scaled(m, params, cols, col_stride, n, nthreads, nll, grad,
+                        NULL);
+}
+
+int orc_nll_scaled(const orc_model* m, const double* params, const double* cols,
+                   int64_t col_stride, int64_t n, int nthreads, double* nll,
+                   double* grad, double* gscale) {
+  int rc = validate(m);
+  if (rc) return rc;
+  if (n < 0 || !params || !nll || (n > 0 && !cols)) return ORC_EINVAL;
+  int P = m->n_par;
+  leaf_cache lc;
+  int drc = fill_cache(m, params, &lc);
+  if (drc == ORC_EINVAL || drc == ORC_EUNSUPPORTED) return drc;
+  if (drc == ORC_OK) drc = check_coefs(m, params);
+  if (drc != ORC_OK) {
+    *nll = INFINITY;
+    if (grad)
+      for (int p = 0; p < P; ++p) grad[p] = NAN;
+    return ORC_EDOMAIN;
+  }
+  int64_t nchunks = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+  int want_scale = gscale != NULL && grad != NULL;
+  int W = 1 + P + (want_scale ? P : 0);
+  double* part = (double*)calloc((size_t)(nchunks > 0 ? nchunks : 1) * W, sizeof(double));
+  int* bad = (int*)calloc((size_t)(nchunks > 0 ? nchunks : 1), sizeof(int));
+  if (!part || !bad) {
+    free(part);
+    free(bad);
+    return ORC_EINVAL;
+  }
+  int want_grad = grad != NULL;
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    nsum acc[1 + 2 * ORC_MAXPAR];
+    memset(acc, 0, sizeof(acc));
+    double xrow[64];
+    double dv[ORC_MAXPAR];
+    int64_t i0 = ch * ORC_CHUNK, i1 = i0 + ORC_CHUNK < n ? i0 + ORC_CHUNK : n;
+    for (int64_t i = i0; i < i1; ++i) {
+      for (int o = 0; o < m->n_obs; ++o) xrow[o] = cols[o * col_stride + i];
+      double v;
+      eval_node(m, m->root, params, xrow, &lc, &v, want_grad ? dv : NULL);
+      if (!(v > 0.0) || !isfinite(v)) {
+        bad[ch] = 1;
+        continue;
+      }
+      nsum_add(&acc[0], -log(v));
+      if (want_grad)
+        for (int p = 0; p < P; ++p) nsum_add(&acc[1 + p], -dv[p] / v);
+      if (want_scale)
+        for (int p = 0; p < P; ++p) nsum_add(&acc[1 + P + p], fabs(dv[p] / v));
+    }
+    for (int w = 0; w < W; ++w) part[ch * W + w] = nsum_val(&acc[w]);
+  }
+  nsum tot[1 + 2 * ORC_MAXPAR];
+  memset(tot, 0, sizeof(tot));
+  int any_bad = 0;
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    any_bad |= bad[ch];
+    for (int w = 0; w < W; ++w) nsum_add(&tot[w], part[ch * W + w]);
+  }
+  free(part);
+  free(bad);
+  /* extended term: + sum_k nu_k, d/dnu_k = 1 */
+  if (m->type[m->root] == ORC_ADD_EXT) {
+    int r = m->root;
+    for (int k = 0; k < m->nchild[r]; ++k) {
+      int p = m->par[r * ORC_MAXNP + k];
+      nsum_add(&tot[0], params[p]);
+      nsum_add(&tot[1 + p], 1.0);
+      if (want_scale) nsum_add(&tot[1 + P + p], 1.0);
+    }
+  }
+  if (any_bad) {
+    *nll = INFINITY;
+    if (grad)
+      for (int p = 0; p < P; ++p) grad[p] = NAN;
+    return ORC_EDOMAIN;
+  }
+  *nll = nsum_val(&tot[0]);
+  if (grad)
+    for (int p = 0; p < P; ++p) grad[p] = nsum_val(&tot[1 + p]);
+  if (want_scale)
+    for (int p = 0; p < P; ++p) gscale[p] = nsum_val(&tot[1 + P + p]);
+  return ORC_OK;
+}
+
+int orc_logp(const orc_model* m, const double* params, const double* cols,
+             int64_t col_stride, int64_t n, double* logp) {
+  int rc = validate(m);
+  if (rc) return rc;
+  leaf_cache lc;
+  int drc = fill_cache(m, params, &lc);
+  if (drc == ORC_EINVAL || drc == ORC_EUNSUPPORTED) return drc;
+  double xrow[64];
+  for (int64_t i = 0; i < n; ++i) {
+    for (int o = 0; o < m->n_obs; ++o) xrow[o] = cols[o * col_stride + i];
+    double v;
+    eval_node(m, m->root, params, xrow, &lc, &v, NULL);
+    logp[i] = v > 0.0 ? log(v) : (v == 0.0 ? -INFINITY : NAN);
+  }
+  return drc;
+}
+
+int orc_nll_batched(const orc_model* m, const double* cols, int64_t col_stride,
+                    const int64_t* offsets, int32_t toys,
+                    const double* params_matrix, int nthreads, double* out) {
+  int rc = validate(m);
+  if (rc) return rc;
+  if (toys < 0 || (toys > 0 && (!offsets || !params_matrix || !out)))
+    return ORC_EINVAL;
+  for (int32_t t = 0; t < toys; ++t)
+    if (offsets[t + 1] < offsets[t]) return ORC_EINVAL;
+  int P = m->n_par;
+  int worst = ORC_OK;
+  /* toys are independent: one toy per thread, each summed in event order */
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int32_t t = 0; t < toys; ++t) {
+    int64_t b = offsets[t], e = offsets[t + 1];
+    int r = orc_nll(m, params_matrix + (int64_t)t * P, cols + b, col_stride,
+                    e - b, 1, out + (int64_t)t * (1 + P),
+                    out + (int64_t)t * (1 + P) + 1);
+    if (r) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      if (r > worst) worst = r;
+    }
+  }
+  return worst;
+}
+
+void orc_adam_step(int n_par, double* theta, const double* grad,
+                   const double* scale, const uint8_t* free_mask, double* m1,
+                   double* m2, int t, double lr, double beta1, double beta2,
+                   double eps) {
+  for (int j = 0; j < n_par; ++j) {
+    if (!free_mask[j]) continue;
+    double g = grad[j] * scale[j]; /* gradient in units of scale */
+    m1[j] = beta1 * m1[j] + (1.0 - beta1) * g;
+    m2[j] = beta2 * m2[j] + (1.0 - beta2) * g * g;
+    double mh = m1[j] / (1.0 - pow(beta1, t));
+    double vh = m2[j] / (1.0 - pow(beta2, t));
+    theta[j] -= scale[j] * lr * mh / (sqrt(vh) + eps);
+  }
+}
