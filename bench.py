@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark: fused unbinned NLL + adjoint gradient on one GB300 (or N, as
+independent weak-scaling replicas launched by torchrun).
+
+A step is one pass of the hot path over one batch: the FP64 prologue
+(normalisation integrals, coefficients), the per-event log-density and adjoint
+of every event, the compensated reduction and the FP64 epilogue -- one fused
+kernel launch through the C-ABI (rf_nll).
+
+Default workload: the B-factory-shaped mass fit -- Crystal Ball (5.279, 0.003,
+1.5, 3) + ARGUS (5.29, -20, 1/2), extended yields 1e6 + 1e8, 1.01e8 events in
+one FP32 column, 7 free parameters; FP32 per-event arithmetic with FP64
+normalisation, reduction and gradient accumulation.  The event column (404 MB)
+is larger than L2 (129 MB), so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the reference this build is checked against) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NLL+grad events/s on 1 GB300 (fused vs plain FP64), % roofline; toy NLLs/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    d = dict(FALLBACK_PEAKS)
+    d["source"] = "fallback"
+    return d
+
+
+def make_workload(name):
+    import datagen
+    if name == "c5":
+        return datagen.c5()
+    if name == "c3":
+        return datagen.c3()
+    if name == "c2":
+        return datagen.c2()
+    if name == "c1":
+        return datagen.c1()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.tmp.close()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def cpu_oracle_rate(w, sample_events, nthreads=0):
+    """Oracle events/s (NLL + analytic gradient, FP64) on the first
+    `sample_events` events of the workload, all allowed host cores."""
+    import numpy as np
+
+    import oracle
+    cols = np.ascontiguousarray(w["cols"][:, :sample_events].astype(np.float64))
+    p = w["spec"]["params"]
+    oracle.nll(w["spec"], p, cols[:, :1000], nthreads=nthreads)  # load / warm
+    t0 = time.perf_counter()
+    v, g, rc = oracle.nll(w["spec"], p, cols, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if nthreads <= 0 else nthreads
+    return cols.shape[1] / dt, cores, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload)
+    n = w["cols"].shape[1]
+    sample = min(n, args.cpu_sample)
+    rates = []
+    cores = 0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, min(sample, 100_000))
+    for _ in range(args.steps):
+        r, cores, _ = cpu_oracle_rate(w, sample)
+        rates.append(r)
+    value = statistics.median(rates)
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "events/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sample / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "events": n, "sample_events": sample},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"first {sample} of {n} events per step, FP64 NLL + "
+                                       "analytic gradient, OpenMP over fixed chunks"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c5")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_2003_12875_gb300 as rf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pk = peaks()
+
+    # ---------------------------------------------------------------- data
+    w = make_workload(args.workload)
+    spec = w["spec"]
+    n = w["cols"].shape[1]
+    col_bytes = 4 if w["dtype"] == "f32" else 8
+    host = torch.from_numpy(np.ascontiguousarray(w["cols"]))
+    ev = host.cuda()
+    params = torch.tensor(spec["params"], dtype=torch.float64, device="cuda")
+    G = rf.Graph(spec, w["dtype"], args.precision)
+    out = torch.empty(1 + len(spec["params"]), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    tuned_ms = None
+    if not args.no_tune:
+        tuned_ms = G.tune(ev, params)
+    for _ in range(args.warmup):
+        G.nll(ev, params, out=out)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+
+    # ---------------------------------------------------------- timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        G.nll(ev, params, out=out)
+        ends[i].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    per_launch = statistics.mean(launch_ms)
+    launches_per_step = G.last_launches()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step * 1e-3)
+    nll_value = float(out[0].item())
+
+    # -------------------------------------------------------------- e2e
+    pinned = host.pin_memory()
+    hp = torch.tensor(spec["params"], dtype=torch.float64)
+    G.nll_host(pinned, hp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_nll, _ = G.nll_host(pinned, hp)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e = {"value": world * n / e2e_s, "unit": "events/s",
+           "h2d_bytes_per_step": int(host.numel() * col_bytes + 8 * len(spec["params"])),
+           "d2h_bytes_per_step": int(8 * (1 + len(spec["params"]))),
+           "ms_per_step": e2e_s * 1e3}
+
+    # ----------------------------------------------------------- roofline
+    bytes_per_launch = n * w["cols"].shape[0] * col_bytes
+    achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_source": pk["source"], "kernel": "fused_nll_kernel",
+                "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch}
+
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "events": n, "columns": w["cols"].shape[0],
+                       "column_dtype": w["dtype"], "eval": args.precision,
+                       "free_params": sum(1 for f in (spec.get("fixed") or []) if not f)
+                       or len(spec["params"]),
+                       "l2": f"inputs larger than L2 ({bytes_per_launch / 1e6:.0f} MB > 129 MB), "
+                             "no flush",
+                       "launch": G.get_launch(), "tuned_ms": tuned_ms,
+                       "parallelism": f"{world} independent replica(s)"},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "clocks": clk, "e2e": e2e, "nll": nll_value}
+
+    # ------------------------------------------------------------ extras
+    if rank == 0 and world == 1 and not args.no_extras:
+        ex = {}
+        # fused FP64-eval on the same workload
+        G64 = rf.Graph(spec, w["dtype"], "fp64")
+        o64 = torch.empty_like(out)
+        G64.nll(ev, params, out=o64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            G64.nll(ev, params, out=o64)
+        b.record()
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 3
+        ex["fused_fp64_eval"] = {"events_per_s": n / (t64 * 1e-3), "ms": t64,
+                                 "nll": float(o64[0].item())}
+        # plain FP64 node-by-node baseline, gradient by central differences
+        v, g = G.nll_plain(ev, params)
+        torch.cuda.synchronize()
+        a.record()
+        v, g = G.nll_plain(ev, params)
+        b.record()
+        torch.cuda.synchronize()
+        tp = a.elapsed_time(b)
+        ex["plain_fp64"] = {"events_per_s": n / (tp * 1e-3), "ms": tp,
+                            "launches": G.last_launches(), "nll": float(v.item()),
+                            "fused_speedup": tp / ms_per_step}
+        a.record()
+        v, _ = G.nll_plain(ev, params, grad=False)
+        b.record()
+        torch.cuda.synchronize()
+        ex["plain_fp64_nll_only_ms"] = a.elapsed_time(b)
+        ex["microbench_ops_per_s"] = rf.microbench()
+        line["extras"] = ex
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, cores, dt = cpu_oracle_rate(w, min(n, args.cpu_sample))
+        line["cpu_baseline"] = {"value": r, "unit": "events/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {min(n, args.cpu_sample)} of {n} events, "
+                                          f"FP64 NLL + analytic gradient ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * rf.h -- C-ABI of librfgpu: the unbinned negative log-likelihood (NLL) of a
+ * PDF computation graph and its gradient, evaluated on one GB300 GPU.
+ *
+ * What is computed (Hageboeck, "A Faster, More Intuitive RooFit", Sec. 5.1):
+ * for every dataset entry the probability of the top node of a graph whose
+ * leaves are PDFs of the entry's observables, normalised by their analytic
+ * integrals over the observable ranges (Sec. 3, "Analytic Integrals");
+ * NLL = -sum_i log P(x_i).  The graph is compiled once (parameter-only
+ * branches -- normalisations, coefficients -- are hoisted out of the event
+ * loop, as the paper's constant branches are computed once, Sec. 5.1), and one
+ * fused kernel streams the event columns and produces the NLL and its
+ * gradient in the same pass.  The batch interface of Sec. 5.2 (contiguous
+ * arrays in, node-owned contiguous arrays out) is kept as the plain FP64
+ * node-by-node baseline, rf_nll_plain.
+ *
+ * Leaves (parameter order in rf_node_desc.params):
+ *   RF_GAUSS  (mu, sigma)            exp(-(x-mu)^2/(2 sigma^2))
+ *   RF_EXP    (lambda)               exp(lambda x)
+ *   RF_CHEB   (c_1..c_m), m <= 4     1 + sum_j c_j T_j(x'), x' = (2x-lo-hi)/(hi-lo)
+ *   RF_CB     (m0, sigma, alpha, n)  Crystal Ball; alpha > 0: tail below m0
+ *   RF_ARGUS  (m0, c, p), p = 1/2    x sqrt(1-(x/m0)^2) exp(c (1-(x/m0)^2)), x < m0
+ * Composites:
+ *   RF_ADD_FRAC (K children, K-1 fractions)  P = sum_{k<K-1} f_k P_k + (1-sum f) P_{K-1}
+ *   RF_ADD_EXT  (K children, K yields; root) P = sum nu_k P_k, NLL += sum nu_k
+ *   RF_PROD     (children on disjoint observables) P = prod P_k
+ * The GPU compiler accepts graphs whose root is a leaf, a PROD of leaves, or
+ * an ADD (fractions or extended) whose children are leaves or PRODs of leaves;
+ * at most 4 leaves and 4 components.  Other shapes return RF_EUNSUPPORTED.
+ *
+ * Memory: every pointer argument marked "dev" is caller-owned device memory
+ * (e.g. a torch tensor).  Event columns are structure-of-arrays: observable j
+ * of event i is at events[j*n_events + i], FP32 or FP64 as the descriptor says.
+ * The graph owns its workspace (block partials, tickets, tile tables), sized
+ * at compile / bind time; rf_nll and rf_nll_batched allocate nothing and never
+ * synchronise the host, so they may be captured in a CUDA graph.
+ *
+ * Concurrency: calls are asynchronous and ordered on the given stream.  One
+ * rf_graph must not be used on two streams at the same time.
+ *
+ * Errors: structural problems (bad descriptor, NULL, negative sizes, a
+ * misaligned column base) return an error code before any launch, and
+ * rf_last_error() describes them (thread-local).  Parameter-domain problems
+ * (sigma <= 0, a fraction outside [0,1], a negative yield, ARGUS m0 below the
+ * range) and events with a non-positive or non-finite probability do not
+ * trap: they set the NLL to +inf, the gradient to NaN, and a status bit read
+ * by rf_graph_status (Sec. 3, "Checking parameters").
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rf_stream; /* == cudaStream_t; NULL = legacy default */
+
+typedef enum {
+  RF_OK = 0,
+  RF_EINVAL = 1,       /* malformed descriptor or argument */
+  RF_EUNSUPPORTED = 2, /* valid graph the GPU compiler does not handle */
+  RF_EALIGN = 3,       /* column base not aligned to its element size */
+  RF_ECUDA = 4,        /* a CUDA call failed (message in rf_last_error) */
+  RF_ENOMEM = 5        /* device allocation failed at compile/bind time */
+} rf_status;
+
+enum {
+  RF_GAUSS = 1,
+  RF_EXP = 2,
+  RF_CHEB = 3,
+  RF_CB = 4,
+  RF_ARGUS = 5,
+  RF_ADD_FRAC = 6,
+  RF_ADD_EXT = 7,
+  RF_PROD = 8
+};
+
+enum { RF_F32 = 0, RF_F64 = 1 };           /* column dtype              */
+enum { RF_EVAL_FP32 = 0, RF_EVAL_FP64 = 1 }; /* per-event arithmetic      */
+
+/* status bits (rf_graph_status) */
+enum {
+  RF_STATUS_PARAM_DOMAIN = 1u, /* a parameter outside its definition range */
+  RF_STATUS_NONFINITE = 2u     /* an event with P <= 0 or a non-finite log P */
+};
+
+#define RF_MAX_CHILDREN 8
+#define RF_MAX_NODE_PARAMS 8
+#define RF_MAX_NODES 32
+#define RF_MAX_PARAMS 64
+
+typedef struct {
+  int32_t type;     /* RF_GAUSS .. RF_PROD                                   */
+  int32_t obs;      /* leaves: observable (column) index; composites: -1     */
+  int32_t n_children;
+  int32_t children[RF_MAX_CHILDREN]; /* node indices                        */
+  int32_t n_params;
+  int32_t params[RF_MAX_NODE_PARAMS]; /* indices into the parameter vector  */
+} rf_node_desc;
+
+typedef struct {
+  int32_t n_nodes;
+  const rf_node_desc* nodes;
+  int32_t root;
+  int32_t n_obs;
+  const double* obs_lo; /* [n_obs] observable ranges, host */
+  const double* obs_hi;
+  int32_t n_params;
+  const uint8_t* param_fixed; /* [n_params] or NULL: 1 = no gradient wanted   */
+  int32_t column_dtype;       /* RF_F32 / RF_F64                              */
+  int32_t eval_precision;     /* RF_EVAL_FP32: per-event math in FP32, with
+                                 normalisation, reduction and gradient sums in
+                                 FP64; RF_EVAL_FP64: all FP64                 */
+} rf_graph_desc;
+
+typedef struct rf_graph rf_graph;
+
+/* Check a descriptor on the host only (no GPU needed).  Returns RF_OK,
+ * RF_EINVAL or RF_EUNSUPPORTED; the reason is in rf_last_error(). */
+rf_status rf_graph_validate(const rf_graph_desc* desc);
+
+/* Validate, canonicalise (sum of products of leaves), assign accumulator
+ * slots, and allocate the graph's device workspace on the current device.
+ * Host-synchronous.  *out is owned by the caller: rf_graph_destroy it. */
+rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out);
+rf_status rf_graph_destroy(rf_graph* g);
+
+/* NLL and gradient of one dataset (Sec. 5.1 problem statement).
+ *   events  dev, SoA columns, n_events >= 0 (0 gives the extended term only)
+ *   params  dev [n_params] FP64
+ *   nll     dev [1] FP64
+ *   grad    dev [n_params] FP64 or NULL; entries of fixed params are 0
+ * One fused kernel launch on `stream`; no allocation, no host sync. */
+rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events,
+                 const double* params, double* nll, double* grad,
+                 rf_stream stream);
+
+/* As rf_nll with HOST buffers: copies events and params to the graph's device
+ * staging area, evaluates, copies nll / grad back, and synchronises the stream.
+ * The staging area grows (cudaMalloc) when n_events exceeds its size, so this
+ * entry point is not capturable.  host_grad may be NULL. */
+rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
+                      const double* host_params, double* host_nll,
+                      double* host_grad, rf_stream stream);
+
+/* Per-event log P(x_i) in FP64 (dev [n_events]); same arithmetic as rf_nll. */
+rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events,
+                  const double* params, double* logp, rf_stream stream);
+
+/* Toy studies (RooStats-style, Sec. 1): many datasets of uneven size that
+ * share one graph.  rf_graph_bind_events records the concatenated event
+ * columns (dev; column j at events + j*n_events); toy t owns events
+ * [offsets[t], offsets[t+1]).  Sizes the tile workspace for up to max_toys. */
+rf_status rf_graph_bind_events(rf_graph* g, const void* events,
+                               int64_t n_events, int32_t max_toys);
+
+/*   offsets        dev int64 [toys+1], non-decreasing, offsets[toys] <= n_events
+ *   params_matrix  dev FP64 [toys * n_params], row t = toy t's parameters
+ *   out            dev FP64 [toys * (1 + n_params)], row t = (NLL_t, grad_t)
+ * A tile plan, a per-toy FP64 prologue, and one persistent kernel over tiles
+ * that never straddle a toy; the last tile of each toy reduces that toy in
+ * fixed order.  No allocation, no host sync: capturable. */
+rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
+                         const double* params_matrix, double* out,
+                         rf_stream stream);
+
+/* A gradient fit of every toy: `iters` Adam steps (Kingma & Ba 2015) on
+ * parameters in units of scale[j] (dev FP64 [n_params]), learning rate lr,
+ * beta = (0.9, 0.999), eps = 1e-8; fixed parameters do not move.  The
+ * per-iteration work (prologue + tile kernel with the Adam step fused into
+ * each toy's final reduction) is captured once into a CUDA graph and
+ * replayed `iters` times.  params_matrix (dev) is updated in place; out
+ * (dev [toys*(1+n_params)]) holds the NLL and gradient of the last
+ * evaluation (at the parameters before the last step).  Host-synchronous. */
+rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
+                      double* params_matrix, const double* scale, int32_t iters,
+                      double lr, double* out, rf_stream stream);
+
+/* Baseline: the batch interface of Sec. 5.2 on the GPU, in FP64 -- one kernel
+ * per graph node, each writing an n-length node-owned FP64 array, then a log
+ * kernel and a reduction kernel.  The gradient (if grad != NULL) is taken by
+ * central finite differences (2 evaluations per free parameter, step
+ * 1e-6 * max(|theta|, 1e-3)).  Needs n_events * (n_nodes + 1) * 8 bytes of
+ * workspace, allocated on first use (not capturable). */
+rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events,
+                       const double* params, double* nll, double* grad,
+                       rf_stream stream);
+
+/* Launch configuration of the fused kernel: threads per block (64, 128 or
+ * 256), events per thread per iteration (FP32 eval: 4 or 8; FP64 eval: 2 or
+ * 4) and resident blocks per SM used to size the grid (1..8). */
+typedef struct {
+  int32_t block;
+  int32_t ept;
+  int32_t blocks_per_sm;
+  int32_t tile; /* batched mode: events per tile (multiple of block*ept) */
+} rf_launch;
+
+rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg);
+rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg);
+
+/* Autotune: times every launch configuration on the given data with CUDA
+ * events and keeps the fastest (host-synchronous).  best_ms may be NULL. */
+rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events,
+                        const double* params, rf_stream stream,
+                        double* best_ms);
+
+/* Synchronises the device, returns the OR of RF_STATUS_* bits raised since
+ * the last call, and clears them. */
+rf_status rf_graph_status(rf_graph* g, uint32_t* flags);
+
+/* Kernels the last rf_nll / rf_nll_batched call launched (for accounting). */
+int32_t rf_graph_last_launches(const rf_graph* g);
+
+/* Thread-local description of the last error ("" if none). */
+const char* rf_last_error(void);
+
+/* Throughput of single operations on this GPU, in operations per second,
+ * measured by dedicated kernels (used for the compute roofline):
+ * out[0] FP32 FMA, out[1] expf, out[2] logf, out[3] FP32 reciprocal (IEEE),
+ * out[4] FP64 FMA, out[5] exp (FP64), out[6] log (FP64), out[7] erf (FP64).
+ * Host-synchronous; allocates a small scratch buffer. */
+rf_status rf_microbench(double* out8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RF_H */

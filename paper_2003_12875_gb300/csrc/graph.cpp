@@ -1,0 +1,674 @@
+// graph.cpp -- host side of librfgpu: descriptor validation, the graph
+// compiler (canonical sum-of-products program, accumulator slots, hoisted
+// parameter-only work), workspace ownership, autotuning and every C-ABI entry
+// point of include/rf.h.
+//
+// Paper correspondence: the compiled program is the computation graph of
+// Sec. 5.1 with its parameter-only branches (normalisations, coefficients)
+// evaluated once per call instead of once per entry; rf_nll is the fused
+// replacement of the per-entry walk; rf_nll_plain keeps the node-per-call
+// batch interface of Sec. 5.2 as the baseline; the range checks follow
+// Sec. 3 ("Checking parameters").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rf.h"
+#include "rf_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+rf_status fail(rf_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+rf_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return RF_ECUDA;
+}
+
+bool is_leaf(int t) { return t >= RF_GAUSS && t <= RF_ARGUS; }
+
+int leaf_nparams_ok(int t, int np) {
+  switch (t) {
+    case RF_GAUSS: return np == 2;
+    case RF_EXP: return np == 1;
+    case RF_CHEB: return np >= 1 && np <= RF_LEAF_MAXP;
+    case RF_CB: return np == 4;
+    case RF_ARGUS: return np == 3;
+  }
+  return 0;
+}
+
+// Structural validation shared by rf_graph_validate and rf_graph_compile.
+rf_status validate_desc(const rf_graph_desc* d) {
+  if (!d) return fail(RF_EINVAL, "descriptor is NULL");
+  if (d->n_nodes <= 0 || d->n_nodes > RF_MAX_NODES || !d->nodes)
+    return fail(RF_EINVAL, "n_nodes must be in 1..32 and nodes non-NULL");
+  if (d->root < 0 || d->root >= d->n_nodes) return fail(RF_EINVAL, "root out of range");
+  if (d->n_obs <= 0 || d->n_obs > 62 || !d->obs_lo || !d->obs_hi)
+    return fail(RF_EINVAL, "n_obs must be in 1..62 with ranges given");
+  if (d->n_params < 0 || d->n_params > RF_MAX_PARAMS)
+    return fail(RF_EINVAL, "n_params must be in 0..64");
+  if (d->column_dtype != RF_F32 && d->column_dtype != RF_F64)
+    return fail(RF_EINVAL, "column_dtype must be RF_F32 or RF_F64");
+  if (d->eval_precision != RF_EVAL_FP32 && d->eval_precision != RF_EVAL_FP64)
+    return fail(RF_EINVAL, "eval_precision must be RF_EVAL_FP32 or RF_EVAL_FP64");
+  for (int o = 0; o < d->n_obs; ++o)
+    if (!(d->obs_hi[o] > d->obs_lo[o]) || !std::isfinite(d->obs_lo[o]) ||
+        !std::isfinite(d->obs_hi[o]))
+      return fail(RF_EINVAL, "observable " + std::to_string(o) + " has an empty or non-finite range");
+  for (int i = 0; i < d->n_nodes; ++i) {
+    const rf_node_desc& n = d->nodes[i];
+    if (n.type < RF_GAUSS || n.type > RF_PROD)
+      return fail(RF_EINVAL, "node " + std::to_string(i) + ": unknown type");
+    if (n.n_params < 0 || n.n_params > RF_MAX_NODE_PARAMS)
+      return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_params");
+    for (int j = 0; j < n.n_params; ++j)
+      if (n.params[j] < 0 || n.params[j] >= d->n_params)
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": parameter index out of range");
+    if (is_leaf(n.type)) {
+      if (n.obs < 0 || n.obs >= d->n_obs)
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": observable index out of range");
+      if (n.type == RF_CHEB && n.n_params > RF_LEAF_MAXP)
+        return fail(RF_EUNSUPPORTED, "Chebychev order above 4 is not supported on the GPU");
+      if (!leaf_nparams_ok(n.type, n.n_params))
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": wrong parameter count for its type");
+    } else {
+      if (n.n_children < 1 || n.n_children > RF_MAX_CHILDREN)
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_children");
+      for (int k = 0; k < n.n_children; ++k)
+        if (n.children[k] < 0 || n.children[k] >= d->n_nodes || n.children[k] == i)
+          return fail(RF_EINVAL, "node " + std::to_string(i) + ": child index out of range");
+      if (n.type == RF_ADD_FRAC && (n.n_children < 2 || n.n_params != n.n_children - 1))
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": ADD_FRAC needs K>=2 children and K-1 fractions");
+      if (n.type == RF_ADD_EXT && n.n_params != n.n_children)
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": ADD_EXT needs one yield per child");
+      if (n.type == RF_ADD_EXT && i != d->root)
+        return fail(RF_EUNSUPPORTED, "ADD_EXT is only supported at the root");
+      if (n.type == RF_PROD && n.n_params != 0)
+        return fail(RF_EINVAL, "node " + std::to_string(i) + ": PROD takes no parameters");
+    }
+  }
+  return RF_OK;
+}
+
+struct Canon {
+  RfProgram prog;
+};
+
+// Map the descriptor onto the sum-of-products program.
+rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
+  std::memset(P, 0, sizeof(*P));
+  const rf_node_desc& root = d->nodes[d->root];
+  std::vector<std::vector<int>> comps;  // leaf node ids per component
+  auto leaves_of = [&](int id, std::vector<int>* out) -> rf_status {
+    const rf_node_desc& n = d->nodes[id];
+    if (is_leaf(n.type)) {
+      out->push_back(id);
+      return RF_OK;
+    }
+    if (n.type == RF_PROD) {
+      for (int k = 0; k < n.n_children; ++k) {
+        const rf_node_desc& c = d->nodes[n.children[k]];
+        if (!is_leaf(c.type))
+          return fail(RF_EUNSUPPORTED, "a PROD child must be a leaf on the GPU path");
+        out->push_back(n.children[k]);
+      }
+      return RF_OK;
+    }
+    return fail(RF_EUNSUPPORTED, "an ADD child must be a leaf or a PROD of leaves");
+  };
+  int kind = RF_KIND_PROD;
+  if (is_leaf(root.type) || root.type == RF_PROD) {
+    comps.emplace_back();
+    rf_status s = leaves_of(d->root, &comps.back());
+    if (s) return s;
+  } else {
+    kind = root.type == RF_ADD_FRAC ? RF_KIND_FRAC : RF_KIND_EXT;
+    for (int k = 0; k < root.n_children; ++k) {
+      comps.emplace_back();
+      rf_status s = leaves_of(root.children[k], &comps.back());
+      if (s) return s;
+    }
+    for (int j = 0; j < root.n_params; ++j) P->coef_par[j] = root.params[j];
+  }
+  int nl = 0;
+  for (auto& c : comps) nl += (int)c.size();
+  if ((int)comps.size() > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 4 components");
+  if (nl > RF_MAXL) return fail(RF_EUNSUPPORTED, "more than 4 leaves");
+  P->n_leaves = nl;
+  P->n_comp = (int)comps.size();
+  P->kind = kind;
+  P->n_par = d->n_params;
+  auto fixed = [&](int p) { return d->param_fixed && d->param_fixed[p]; };
+  for (int p = 0; p < d->n_params; ++p)
+    if (fixed(p)) {
+      if (p < 64) P->fixed_lo |= 1ull << p;
+      else P->fixed_hi |= 1ull << (p - 64);
+    }
+  if (kind != RF_KIND_PROD) {
+    int ncoef = kind == RF_KIND_FRAC ? P->n_comp - 1 : P->n_comp;
+    for (int c = 0; c < ncoef; ++c)
+      if (!fixed(P->coef_par[c])) P->coef_free |= 1 << c;
+  }
+  int n_cols = 0;
+  int k = 0;
+  for (int c = 0; c < P->n_comp; ++c) {
+    uint64_t comp_obs = 0;
+    for (int id : comps[c]) {
+      const rf_node_desc& n = d->nodes[id];
+      if (comps[c].size() > 1) {
+        if (comp_obs & (1ull << n.obs))
+          return fail(RF_EUNSUPPORTED, "PROD children must use disjoint observables");
+        comp_obs |= 1ull << n.obs;
+      }
+      RfLeafProg& L = P->leaf[k++];
+      L.type = n.type;  // RF_GAUSS..RF_ARGUS == RFL_GAUSS..RFL_ARGUS
+      L.comp = c;
+      L.npar = n.n_params;
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) L.par[j] = j < n.n_params ? n.params[j] : 0;
+      L.lo = d->obs_lo[n.obs];
+      L.hi = d->obs_hi[n.obs];
+      int slot = -1;
+      for (int s = 0; s < n_cols; ++s)
+        if (P->col_obs[s] == n.obs) slot = s;
+      if (slot < 0) {
+        slot = n_cols;
+        P->col_obs[n_cols++] = n.obs;
+      }
+      L.col = slot;
+      int gm = 0;
+      for (int j = 0; j < n.n_params; ++j)
+        if (!fixed(n.params[j])) gm |= 1 << j;
+      if (n.type == RF_ARGUS) {
+        if (!fixed(n.params[2]))
+          return fail(RF_EUNSUPPORTED, "ARGUS p must be a fixed parameter (its integral's d/dp is not provided)");
+        gm &= 3;
+      }
+      L.gmask = gm;
+    }
+  }
+  P->n_cols = n_cols;
+  return RF_OK;
+}
+
+bool ept_ok(int eval, int coldt, int ept) {
+  if (eval == RF_EVAL_FP32) return ept == 4 || ept == 8;
+  if (coldt == RF_F64) return ept == 2 || ept == 4;
+  return ept == 4;
+}
+
+}  // namespace
+
+struct rf_graph {
+  RfProgram prog;
+  int eval = 0, coldt = 0, n_obs = 0;
+  int device = 0, num_sms = 0;
+  RfLaunchCfg cfg{256, 4, 2, 8192};
+  RfWork work{};
+  int64_t max_rows_single = 0;
+  // batched
+  const void* bound_events = nullptr;
+  int64_t bound_n = 0;
+  int32_t max_toys = 0;
+  int64_t max_tile_rows = 0;
+  // host staging
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // plain workspace
+  double* plain_buf = nullptr;
+  size_t plain_bytes = 0;
+  double* plain_partials = nullptr;
+  unsigned int* plain_counter = nullptr;
+  cudaStream_t fit_stream = nullptr;
+  int last_launches = 0;
+};
+
+static void free_work(rf_graph* g) {
+  cudaFree(g->work.partials);
+  cudaFree(g->work.counter);
+  cudaFree(g->work.tile_start);
+  cudaFree(g->work.toy_counter);
+  cudaFree(g->work.toy_consts);
+  cudaFree(g->work.adam_m1);
+  cudaFree(g->work.adam_m2);
+  cudaFree(g->stage);
+  cudaFree(g->plain_buf);
+  cudaFree(g->plain_partials);
+  if (g->fit_stream) cudaStreamDestroy(g->fit_stream);
+}
+
+extern "C" {
+
+const char* rf_last_error(void) { return g_err.c_str(); }
+
+rf_status rf_graph_validate(const rf_graph_desc* desc) {
+  g_err.clear();
+  rf_status s = validate_desc(desc);
+  if (s) return s;
+  RfProgram P;
+  return canonicalise(desc, &P);
+}
+
+rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
+  g_err.clear();
+  if (!out) return fail(RF_EINVAL, "out is NULL");
+  *out = nullptr;
+  rf_status s = validate_desc(desc);
+  if (s) return s;
+  rf_graph* g = new rf_graph();
+  s = canonicalise(desc, &g->prog);
+  if (s) {
+    delete g;
+    return s;
+  }
+  g->eval = desc->eval_precision;
+  g->coldt = desc->column_dtype;
+  g->n_obs = desc->n_obs;
+  if (g->eval == RF_EVAL_FP64) g->cfg.ept = (g->coldt == RF_F64) ? 2 : 4;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "rf_graph_compile: device query");
+  }
+  g->max_rows_single = (int64_t)g->num_sms * 8;
+  e = cudaMalloc(&g->work.partials, sizeof(double) * RF_NACC_MAX * g->max_rows_single);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.counter, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(g->work.counter, 0, 4 * sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    free_work(g);
+    delete g;
+    return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
+  }
+  g->work.status = g->work.counter + 1;
+  g->work.next_tile = g->work.counter + 2;
+  *out = g;
+  return RF_OK;
+}
+
+rf_status rf_graph_destroy(rf_graph* g) {
+  if (!g) return RF_OK;
+  free_work(g);
+  delete g;
+  return RF_OK;
+}
+
+static rf_status check_events(const rf_graph* g, const void* events, int64_t n) {
+  if (n < 0) return fail(RF_EINVAL, "n_events < 0");
+  if (n > 0 && !events) return fail(RF_EINVAL, "events is NULL");
+  size_t sz = g->coldt == RF_F64 ? 8 : 4;
+  if (reinterpret_cast<uintptr_t>(events) % sz)
+    return fail(RF_EALIGN, "event columns are not aligned to their element size");
+  return RF_OK;
+}
+
+static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, int64_t n,
+                          const double* params, double* nll, double* grad, cudaStream_t st) {
+  const RfProgram& P = g->prog;
+  if (g->eval == RF_EVAL_FP32)
+    return g->coldt == RF_F32
+               ? rf_fused_f32_c32(P, cfg, g->num_sms, ev, n, params, g->work, nll, grad, st)
+               : rf_fused_f32_c64(P, cfg, g->num_sms, ev, n, params, g->work, nll, grad, st);
+  return g->coldt == RF_F32
+             ? rf_fused_f64_c32(P, cfg, g->num_sms, ev, n, params, g->work, nll, grad, st)
+             : rf_fused_f64_c64(P, cfg, g->num_sms, ev, n, params, g->work, nll, grad, st);
+}
+
+rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events, const double* params,
+                 double* nll, double* grad, rf_stream stream) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  rf_status s = check_events(g, events, n_events);
+  if (s) return s;
+  if (!params && g->prog.n_par > 0) return fail(RF_EINVAL, "params is NULL");
+  if (!nll) return fail(RF_EINVAL, "nll is NULL");
+  int e = fused_dispatch(g, g->cfg, events, n_events, params, nll, grad,
+                         reinterpret_cast<cudaStream_t>(stream));
+  g->last_launches = 1;
+  if (e) return cuda_fail((cudaError_t)e, "rf_nll launch");
+  return RF_OK;
+}
+
+rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
+                      const double* host_params, double* host_nll, double* host_grad,
+                      rf_stream stream) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (n_events < 0 || (n_events > 0 && !host_events) || !host_nll ||
+      (!host_params && g->prog.n_par > 0))
+    return fail(RF_EINVAL, "NULL or negative argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t sz = g->coldt == RF_F64 ? 8 : 4;
+  const size_t ev_bytes = (size_t)g->n_obs * (size_t)n_events * sz;
+  const size_t ev_pad = (ev_bytes + 255) & ~(size_t)255;
+  const size_t need = ev_pad + sizeof(double) * (2 * RF_MAXPAR + 2);
+  if (need > g->stage_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host sync");
+    cudaFree(g->stage);
+    g->stage = nullptr;
+    g->stage_bytes = 0;
+    e = cudaMalloc(&g->stage, need);
+    if (e != cudaSuccess) return fail(RF_ENOMEM, "rf_nll_host: staging allocation failed");
+    g->stage_bytes = need;
+  }
+  char* base = static_cast<char*>(g->stage);
+  double* dp = reinterpret_cast<double*>(base + ev_pad);
+  double* dout = dp + RF_MAXPAR;
+  const int np = g->prog.n_par;
+  cudaError_t e = cudaSuccess;
+  if (ev_bytes) e = cudaMemcpyAsync(base, host_events, ev_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && np)
+    e = cudaMemcpyAsync(dp, host_params, sizeof(double) * np, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host H2D");
+  int le = fused_dispatch(g, g->cfg, base, n_events, dp, dout, host_grad ? dout + 1 : nullptr, st);
+  g->last_launches = 1;
+  if (le) return cuda_fail((cudaError_t)le, "rf_nll_host launch");
+  e = cudaMemcpyAsync(host_nll, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && host_grad && np)
+    e = cudaMemcpyAsync(host_grad, dout + 1, sizeof(double) * np, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host D2H");
+  return RF_OK;
+}
+
+rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events, const double* params,
+                  double* logp, rf_stream stream) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  rf_status s = check_events(g, events, n_events);
+  if (s) return s;
+  if ((!params && g->prog.n_par > 0) || (!logp && n_events > 0))
+    return fail(RF_EINVAL, "params or logp is NULL");
+  if (n_events == 0) return RF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const RfProgram& P = g->prog;
+  int e;
+  if (g->eval == RF_EVAL_FP32)
+    e = g->coldt == RF_F32 ? rf_logp_f32_c32(P, events, n_events, params, logp, st)
+                           : rf_logp_f32_c64(P, events, n_events, params, logp, st);
+  else
+    e = g->coldt == RF_F32 ? rf_logp_f64_c32(P, events, n_events, params, logp, st)
+                           : rf_logp_f64_c64(P, events, n_events, params, logp, st);
+  g->last_launches = 1;
+  if (e) return cuda_fail((cudaError_t)e, "rf_logp launch");
+  return RF_OK;
+}
+
+rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events,
+                               int32_t max_toys) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  rf_status s = check_events(g, events, n_events);
+  if (s) return s;
+  if (max_toys < 1) return fail(RF_EINVAL, "max_toys must be >= 1");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "rf_graph_bind_events sync");
+  cudaFree(g->work.tile_start);
+  cudaFree(g->work.toy_counter);
+  cudaFree(g->work.toy_consts);
+  cudaFree(g->work.adam_m1);
+  cudaFree(g->work.adam_m2);
+  g->work.tile_start = nullptr;
+  g->work.toy_counter = nullptr;
+  g->work.toy_consts = nullptr;
+  g->work.adam_m1 = g->work.adam_m2 = nullptr;
+  g->work.adam_t = nullptr;
+  // tiles hold at least 1024 events, so rows <= toys + n/1024 + 1
+  int64_t rows = (int64_t)max_toys + n_events / 1024 + 1;
+  int64_t have_rows = g->max_rows_single;
+  if (rows > have_rows) {
+    cudaFree(g->work.partials);
+    g->work.partials = nullptr;
+    e = cudaMalloc(&g->work.partials, sizeof(double) * RF_NACC_MAX * rows);
+    if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: partials allocation failed");
+    g->max_rows_single = rows;
+  }
+  const size_t np = (size_t)std::max(g->prog.n_par, 1);
+  e = cudaMalloc(&g->work.tile_start, sizeof(int64_t) * ((size_t)max_toys + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_counter, sizeof(unsigned int) * (size_t)max_toys + 8);
+  if (e == cudaSuccess) e = cudaMemset(g->work.toy_counter, 0, sizeof(unsigned int) * (size_t)max_toys + 8);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m1, sizeof(double) * np * (size_t)max_toys);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
+  if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
+  g->work.adam_t = reinterpret_cast<int32_t*>(g->work.toy_counter + max_toys);
+  g->bound_events = events;
+  g->bound_n = n_events;
+  g->max_toys = max_toys;
+  g->max_tile_rows = rows;
+  return RF_OK;
+}
+
+static rf_status batched_checks(rf_graph* g, const int64_t* offsets, int32_t toys,
+                                const double* pm, const double* out) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (!g->work.tile_start) return fail(RF_EINVAL, "rf_graph_bind_events was not called");
+  if (toys < 1 || toys > g->max_toys) return fail(RF_EINVAL, "toys must be in 1..max_toys");
+  if (!offsets || !pm || !out) return fail(RF_EINVAL, "NULL argument");
+  if (g->cfg.tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
+  return RF_OK;
+}
+
+rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
+                         const double* params_matrix, double* out, rf_stream stream) {
+  rf_status s = batched_checks(g, offsets, toys, params_matrix, out);
+  if (s) return s;
+  int n = 0;
+  int e = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
+                            g->bound_n, offsets, toys, const_cast<double*>(params_matrix), out,
+                            g->work, nullptr, 0.0, true, g->max_tile_rows, stream, &n);
+  g->last_launches = n;
+  if (e) return cuda_fail((cudaError_t)e, "rf_nll_batched launch");
+  return RF_OK;
+}
+
+rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
+                      double* params_matrix, const double* scale, int32_t iters, double lr,
+                      double* out, rf_stream stream) {
+  rf_status s = batched_checks(g, offsets, toys, params_matrix, out);
+  if (s) return s;
+  if (!scale || iters < 0) return fail(RF_EINVAL, "scale is NULL or iters < 0");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!g->fit_stream) e = cudaStreamCreateWithFlags(&g->fit_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys stream");
+  cudaStream_t fs = g->fit_stream;
+  cudaEvent_t ev;
+  e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, ev, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys order");
+  const size_t np = (size_t)std::max(g->prog.n_par, 1);
+  e = cudaMemsetAsync(g->work.adam_m1, 0, sizeof(double) * np * toys, fs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_m2, 0, sizeof(double) * np * toys, fs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_t, 0, sizeof(int32_t), fs);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys reset");
+  int le = rf_toys_plan(offsets, toys, g->cfg.tile, g->work, fs);
+  if (le) return cuda_fail((cudaError_t)le, "rf_fit_toys plan");
+  int launches = 1;
+  if (iters > 0) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(fs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys capture");
+    int n = 0;
+    le = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
+                           g->bound_n, offsets, toys, params_matrix, out, g->work, scale, lr,
+                           false, g->max_tile_rows, fs, &n);
+    e = cudaStreamEndCapture(fs, &graph);
+    if (le) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail((cudaError_t)le, "rf_fit_toys captured launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys end capture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(e, "rf_fit_toys instantiate");
+    }
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, fs);
+    launches += n * iters;
+    cudaError_t e2 = cudaStreamSynchronize(fs);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys replay");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "rf_fit_toys sync");
+  }
+  e = cudaEventRecord(ev, fs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(fs);
+  cudaEventDestroy(ev);
+  g->last_launches = launches;
+  if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys finish");
+  return RF_OK;
+}
+
+rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events, const double* params,
+                       double* nll, double* grad, rf_stream stream) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  rf_status s = check_events(g, events, n_events);
+  if (s) return s;
+  if ((!params && g->prog.n_par > 0) || !nll) return fail(RF_EINVAL, "NULL argument");
+  size_t need = rf_plain_bytes(g->prog, n_events);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (need > g->plain_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rf_nll_plain sync");
+    cudaFree(g->plain_buf);
+    g->plain_buf = nullptr;
+    g->plain_bytes = 0;
+    e = cudaMalloc(&g->plain_buf, need);
+    if (e != cudaSuccess) return fail(RF_ENOMEM, "rf_nll_plain: node buffers allocation failed");
+    g->plain_bytes = need;
+  }
+  if (!g->plain_partials) {
+    cudaError_t e = cudaMalloc(&g->plain_partials, sizeof(double) * RF_NACC_MAX * 4096 + 64);
+    if (e != cudaSuccess) return fail(RF_ENOMEM, "rf_nll_plain: partials allocation failed");
+    g->plain_counter = reinterpret_cast<unsigned int*>(g->plain_partials + RF_NACC_MAX * 4096);
+    e = cudaMemset(g->plain_counter, 0, 64);
+    if (e != cudaSuccess) return cuda_fail(e, "rf_nll_plain memset");
+  }
+  int n = 0;
+  int e = rf_launch_plain(g->prog, g->coldt, events, n_events, params, g->plain_buf, nll, grad,
+                          g->plain_partials, g->plain_counter, st, &n);
+  g->last_launches = n;
+  if (e) return cuda_fail((cudaError_t)e, "rf_nll_plain launch");
+  return RF_OK;
+}
+
+rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg) {
+  if (!g || !cfg) return fail(RF_EINVAL, "NULL argument");
+  cfg->block = g->cfg.block;
+  cfg->ept = g->cfg.ept;
+  cfg->blocks_per_sm = g->cfg.blocks_per_sm;
+  cfg->tile = g->cfg.tile;
+  return RF_OK;
+}
+
+rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
+  if (!g || !cfg) return fail(RF_EINVAL, "NULL argument");
+  if (cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
+    return fail(RF_EINVAL, "block must be 64, 128 or 256");
+  if (!ept_ok(g->eval, g->coldt, cfg->ept))
+    return fail(RF_EINVAL, "events per thread not available for this precision / dtype");
+  if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
+    return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
+  if (cfg->tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
+  g->cfg.block = cfg->block;
+  g->cfg.ept = cfg->ept;
+  g->cfg.blocks_per_sm = cfg->blocks_per_sm;
+  g->cfg.tile = cfg->tile;
+  return RF_OK;
+}
+
+rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const double* params,
+                        rf_stream stream, double* best_ms) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  rf_status s = check_events(g, events, n_events);
+  if (s) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* dout = nullptr;
+  cudaError_t e = cudaMalloc(&dout, sizeof(double) * (1 + RF_MAXPAR));
+  if (e != cudaSuccess) return fail(RF_ENOMEM, "tune scratch");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int blocks[3] = {64, 128, 256};
+  const int bpss[6] = {1, 2, 3, 4, 6, 8};
+  int epts[2];
+  if (g->eval == RF_EVAL_FP32) {
+    epts[0] = 4;
+    epts[1] = 8;
+  } else if (g->coldt == RF_F64) {
+    epts[0] = 2;
+    epts[1] = 4;
+  } else {
+    epts[0] = epts[1] = 4;
+  }
+  RfLaunchCfg best = g->cfg;
+  float best_t = 1e30f;
+  for (int bi = 0; bi < 3; ++bi)
+    for (int ei = 0; ei < 2; ++ei) {
+      if (ei == 1 && epts[1] == epts[0]) continue;
+      for (int pi = 0; pi < 6; ++pi) {
+        RfLaunchCfg c = g->cfg;
+        c.block = blocks[bi];
+        c.ept = epts[ei];
+        c.blocks_per_sm = bpss[pi];
+        float tsum = 0.f;
+        for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
+          cudaEventRecord(a, st);
+          int le = fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
+          cudaEventRecord(b, st);
+          if (le) e = (cudaError_t)le;
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          if (rep >= 2) tsum += ms;  // first two are warm-up
+        }
+        if (e != cudaSuccess) break;
+        if (tsum < best_t) {
+          best_t = tsum;
+          best = c;
+        }
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "rf_graph_tune");
+  g->cfg.block = best.block;
+  g->cfg.ept = best.ept;
+  g->cfg.blocks_per_sm = best.blocks_per_sm;
+  if (best_ms) *best_ms = best_t / 5.0;
+  return RF_OK;
+}
+
+rf_status rf_graph_status(rf_graph* g, uint32_t* flags) {
+  if (!g || !flags) return fail(RF_EINVAL, "NULL argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, g->work.status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(g->work.status, 0, sizeof(v));
+  if (e != cudaSuccess) return cuda_fail(e, "rf_graph_status");
+  *flags = v;
+  return RF_OK;
+}
+
+int32_t rf_graph_last_launches(const rf_graph* g) { return g ? g->last_launches : 0; }
+
+rf_status rf_microbench(double* out8) {
+  if (!out8) return fail(RF_EINVAL, "out8 is NULL");
+  int e = rf_run_microbench(out8);
+  if (e) return cuda_fail((cudaError_t)e, "rf_microbench");
+  return RF_OK;
+}
+
+}  // extern "C"

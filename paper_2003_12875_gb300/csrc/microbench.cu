@@ -1,0 +1,76 @@
+// microbench.cu -- throughput of single operations on this GPU, for the
+// compute side of the roofline.  Each thread runs 8 independent dependency
+// chains of one operation; the result feeds a store that never fires, so the
+// work cannot be removed.  Ops/s = threads * 8 * iterations / kernel time.
+#include <cuda_runtime.h>
+
+#include "rf_internal.h"
+
+namespace {
+
+template <int OP>
+struct Op;
+template <> struct Op<0> { typedef float T; static __device__ __forceinline__ float f(float a) { return fmaf(a, 0.9999f, 0.0001f); } };
+template <> struct Op<1> { typedef float T; static __device__ __forceinline__ float f(float a) { return expf(-a); } };
+template <> struct Op<2> { typedef float T; static __device__ __forceinline__ float f(float a) { return logf(a + 2.0f); } };
+template <> struct Op<3> { typedef float T; static __device__ __forceinline__ float f(float a) { return __frcp_rn(a + 1.0f); } };
+template <> struct Op<4> { typedef double T; static __device__ __forceinline__ double f(double a) { return fma(a, 0.9999, 0.0001); } };
+template <> struct Op<5> { typedef double T; static __device__ __forceinline__ double f(double a) { return exp(-a); } };
+template <> struct Op<6> { typedef double T; static __device__ __forceinline__ double f(double a) { return log(a + 2.0); } };
+template <> struct Op<7> { typedef double T; static __device__ __forceinline__ double f(double a) { return erf(a) + 0.25; } };
+
+template <int OP>
+__global__ void __launch_bounds__(256) mb_kernel(typename Op<OP>::T* sink, int iters) {
+  typedef typename Op<OP>::T T;
+  T a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (T)(0.1 + 0.01 * j + 1e-6 * threadIdx.x);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = Op<OP>::f(a[j]);
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == (T)-12345.0) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int OP>
+double run(int sms, void* sink, int iters) {
+  const int block = 256, grid = sms * 8;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  typedef typename Op<OP>::T T;
+  mb_kernel<OP><<<grid, block>>>(static_cast<T*>(sink), iters / 10);  // warm-up
+  cudaEventRecord(a);
+  mb_kernel<OP><<<grid, block>>>(static_cast<T*>(sink), iters);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return (double)grid * block * 8.0 * iters / (ms * 1e-3);
+}
+
+}  // namespace
+
+int rf_run_microbench(double* out) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, (size_t)sms * 8 * 256 * sizeof(double));
+  if (e != cudaSuccess) return (int)e;
+  out[0] = run<0>(sms, sink, 4096);
+  out[1] = run<1>(sms, sink, 1024);
+  out[2] = run<2>(sms, sink, 1024);
+  out[3] = run<3>(sms, sink, 1024);
+  out[4] = run<4>(sms, sink, 256);
+  out[5] = run<5>(sms, sink, 32);
+  out[6] = run<6>(sms, sink, 32);
+  out[7] = run<7>(sms, sink, 32);
+  e = cudaGetLastError();
+  cudaFree(sink);
+  return (int)e;
+}

@@ -1,0 +1,746 @@
+// rf_device.cuh -- device building blocks of the fused NLL + adjoint kernels.
+//
+//  * FP64 normalisation integrals I_k and d log I_k / d theta (the parameter-
+//    only "constant branches" of Sec. 5.1, hoisted out of the event loop),
+//  * per-event leaf log-densities and their parameter derivatives in the
+//    evaluation precision (FP32 or FP64), branch-free where the paper's
+//    Sec. 5.3 replaces branches by selects,
+//  * compensated per-thread accumulation, a fixed-order FP64 block/grid
+//    reduction (deterministic for a fixed launch configuration),
+//  * the FP64 epilogue that turns the accumulated sums into the NLL and
+//    its gradient, including the normalisation-integral derivatives.
+//
+// Leaf definitions (the paper prints none; standard forms):
+//  Gaussian    f = exp(-(x-mu)^2/(2 sigma^2))
+//  Exponential f = exp(lambda x)
+//  Chebychev   f = 1 + sum_j c_j T_j(x'), x' = (2x - lo - hi)/(hi - lo)
+//  CrystalBall t = s (x-m0)/sigma, s = sign(alpha), A = |alpha|:
+//              f = exp(-t^2/2) (t > -A), else exp(-A^2/2) D^-n,
+//              D = 1 - (A/n)(A + t)
+//  ARGUS       f = x tau^(1/2) exp(c tau), tau = 1 - (x/m0)^2 (x < m0)
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "rf_internal.h"
+
+namespace rf {
+
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kSqrtHalfPi = 1.25331413731550025121;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+// ------------------------------------------------------------------ FP64 math
+__device__ inline double erf_diff(double z1, double z2) {  // erf(z2)-erf(z1)
+  if (z1 >= 0.0) return erfc(z1) - erfc(z2);
+  if (z2 <= 0.0) return erfc(-z2) - erfc(-z1);
+  return erf(z2) - erf(z1);
+}
+
+// (e^y - 1)/y and its derivative; the derivative's closed form cancels near
+// 0, where its Taylor series sum_{k>=1} k y^(k-1)/(k+1)! is used instead.
+__device__ inline double expm1_over(double y) {
+  return y == 0.0 ? 1.0 : expm1(y) / y;
+}
+__device__ inline double expm1_over_d(double y) {
+  if (fabs(y) < 1.0) {
+    double acc = 0.0, yp = 1.0, fact = 2.0;
+    for (int k = 1; k <= 30; ++k) {
+      acc += k * yp / fact;
+      yp *= y;
+      fact *= (double)(k + 2);
+    }
+    return acc;
+  }
+  return (exp(y) * (y - 1.0) + 1.0) / (y * y);
+}
+
+// int_0^tau s^q e^{c s} ds, q in {1/2, 3/2}: incomplete-gamma closed form for
+// c < 0 and -c tau >= 1/2, power series otherwise.
+__device__ inline double argus_int(double q, double tau, double c) {
+  if (tau <= 0.0) return 0.0;
+  double y = c * tau;
+  if (c < 0.0 && -y >= 0.5) {
+    double k = -c, ky = -y, sky = sqrt(ky), eky = exp(-ky);
+    double g32 = 0.5 * kSqrtPi * erf(sky) - sky * eky;  // gamma(3/2, ky)
+    if (q == 0.5) return g32 / (k * sqrt(k));
+    double g52 = 1.5 * g32 - ky * sky * eky;            // gamma(5/2, ky)
+    return g52 / (k * k * sqrt(k));
+  }
+  double sum = 0.0, term = 1.0;
+  for (int j = 0; j < 2000; ++j) {
+    double add = term / (j + q + 1.0);
+    sum += add;
+    if (j > fabs(y) && fabs(add) < 1e-18 * fabs(sum)) break;
+    term *= y / (j + 1.0);
+  }
+  return pow(tau, q + 1.0) * sum;
+}
+
+// log(I) - off and d(log I - off)/d theta_j for one leaf (FP64).  `off` is
+// the constant the per-event code leaves out of u = log f - off (Exponential:
+// lambda * lo, so that u = lambda (x - lo) stays small).  Returns false when
+// the parameters are outside the leaf's definition range.
+__device__ inline bool leaf_lognorm(int type, const double* th, double lo,
+                                    double hi, double* lnI, double* dln) {
+  for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = 0.0;
+  switch (type) {
+    case RFL_GAUSS: {
+      double mu = th[0], sg = th[1];
+      if (!(sg > 0.0)) return false;
+      double za = (lo - mu) / sg, zb = (hi - mu) / sg;
+      double I = sg * kSqrtHalfPi * erf_diff(za / kSqrt2, zb / kSqrt2);
+      double pa = exp(-0.5 * za * za), pb = exp(-0.5 * zb * zb);
+      *lnI = log(I);
+      dln[0] = (pa - pb) / I;
+      dln[1] = 1.0 / sg + (za * pa - zb * pb) / I;
+      return I > 0.0 && isfinite(I);
+    }
+    case RFL_EXP: {
+      // I = e^{lambda lo} L E1(lambda L); off = lambda lo.
+      double lam = th[0], L = hi - lo, s = lam * L;
+      *lnI = log(L * expm1_over(s));
+      // d log I / d lambda - lo = <x> - lo = L (1/(1-e^-s) - 1/s)
+      double m = (fabs(s) < 1e-3)
+                     ? 0.5 + s / 12.0 - s * s * s / 720.0 + s * s * s * s * s / 30240.0
+                     : 1.0 / (-expm1(-s)) - 1.0 / s;
+      dln[0] = L * m;
+      return isfinite(*lnI);
+    }
+    case RFL_CHEB: {
+      // int_{-1}^1 T_j = (1 + (-1)^j)/(1 - j^2), 0 for j = 1
+      double half = 0.5 * (hi - lo), J = 2.0, dJ[RF_LEAF_MAXP];
+      for (int j = 1; j <= RF_LEAF_MAXP; ++j) {
+        double tj = (j & 1) ? 0.0 : 2.0 / (1.0 - (double)(j * j));
+        J += th[j - 1] * tj;
+        dJ[j - 1] = tj;
+      }
+      if (!(J > 0.0)) return false;
+      *lnI = log(half * J);
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = dJ[j] / J;
+      return true;
+    }
+    case RFL_CB: {
+      double m0 = th[0], sg = th[1], al = th[2], n = th[3];
+      if (!(sg > 0.0) || !(n > 0.0) || al == 0.0) return false;
+      double s = al > 0.0 ? 1.0 : -1.0, A = fabs(al);
+      double tlo = (s > 0.0) ? (lo - m0) / sg : (m0 - hi) / sg;
+      double thi = (s > 0.0) ? (hi - m0) / sg : (m0 - lo) / sg;
+      double core = 0.0;
+      if (thi > -A) core = kSqrtHalfPi * erf_diff(fmax(tlo, -A) / kSqrt2, thi / kSqrt2);
+      double tail = 0.0, dA = 0.0, dn = 0.0;
+      if (tlo < -A) {
+        // substitute D = 1 - (A/n)(A+t): tail = (n/A) e^{-A^2/2} int D^-n dD
+        double D1 = 1.0 - (A / n) * (A + tlo);
+        double D2 = 1.0 - (A / n) * (A + fmin(thi, -A));
+        double L1 = log(D1), L2 = log(D2), dL = L1 - L2, eps = 1.0 - n;
+        double ez = exp(eps * L2);
+        double Phi = ez * dL * expm1_over(eps * dL);                  // int D^-n
+        double PhiL = L2 * Phi + ez * dL * dL * expm1_over_d(eps * dL); // int D^-n log D
+        double Psi = (pow(D2, -n) - pow(D1, -n)) / n;                  // int D^-n-1
+        double pre = (n / A) * exp(-0.5 * A * A);
+        tail = pre * Phi;
+        dA = pre * (A + n / A) * (Psi - Phi);
+        dn = pre * (Phi - PhiL - Psi);
+      }
+      double J = core + tail;
+      double glo = (tlo > -A) ? exp(-0.5 * tlo * tlo)
+                              : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + tlo), -n);
+      double ghi = (thi > -A) ? exp(-0.5 * thi * thi)
+                              : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + thi), -n);
+      double I = sg * J;
+      *lnI = log(I);
+      dln[0] = -s * (ghi - glo) / I;
+      dln[1] = (J + tlo * glo - thi * ghi) / I;
+      dln[2] = s * dA / J;
+      dln[3] = dn / J;
+      return I > 0.0 && isfinite(I);
+    }
+    case RFL_ARGUS: {
+      double m0 = th[0], c = th[1], p = th[2];
+      if (p != 0.5 || !(m0 > lo) || lo < 0.0) return false;
+      double b = fmin(hi, m0);
+      double ta = 1.0 - (lo / m0) * (lo / m0), tb = 1.0 - (b / m0) * (b / m0);
+      double h = 0.5 * m0 * m0;
+      double I = h * (argus_int(0.5, ta, c) - argus_int(0.5, tb, c));
+      double dIc = h * (argus_int(1.5, ta, c) - argus_int(1.5, tb, c));
+      double ea = (1.0 - ta) * sqrt(ta) * exp(c * ta);
+      double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * exp(c * tb) : 0.0;
+      double dIm = m0 * (ea - eb) + 2.0 * I / m0;
+      *lnI = log(I);
+      dln[0] = dIm / I;
+      dln[1] = dIc / I;
+      return I > 0.0 && isfinite(I);
+    }
+  }
+  return false;
+}
+
+// --------------------------------------------------------- prologue (FP64)
+template <typename Real>
+__device__ inline void split_hi_lo(double v, Real& hi, Real& lo) {
+  hi = (Real)v;
+  lo = (Real)(v - (double)hi);
+}
+
+// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k] and lnI_out.
+template <typename Real>
+__device__ inline bool leaf_consts(const RfProgram& P, const double* params,
+                                   RfConsts<Real>& K, int k, double* lnI_out) {
+  const RfLeafProg& L = P.leaf[k];
+  double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
+  double dln[RF_LEAF_MAXP];
+  bool ok = leaf_lognorm(L.type, th, L.lo, L.hi, lnI_out, dln);
+  K.lnI[k] = *lnI_out;
+  Real* pc = K.pc[k];
+  for (int j = 0; j < RF_PC; ++j) pc[j] = Real(0);
+  for (int j = 0; j < RF_LEAF_MAXP; ++j) {
+    K.dlogI[k][j] = dln[j];
+    K.dtheta[k][j] = 0.0;
+  }
+  switch (L.type) {
+    case RFL_GAUSS: {
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (Real)(1.0 / th[1]);
+      K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
+      break;
+    }
+    case RFL_EXP: {
+      pc[0] = (Real)th[0];
+      split_hi_lo(L.lo, pc[1], pc[2]);
+      K.dtheta[k][0] = (double)pc[0] - th[0];
+      break;
+    }
+    case RFL_CHEB: {
+      // x' = (x - mid) * (2/(hi-lo))
+      pc[0] = (Real)(2.0 / (L.hi - L.lo));
+      pc[1] = (Real)(-(L.hi + L.lo) / (L.hi - L.lo));
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) {
+        pc[2 + j] = (Real)th[j];
+        K.dtheta[k][j] = (double)pc[2 + j] - th[j];
+      }
+      break;
+    }
+    case RFL_CB: {
+      double s = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (Real)(1.0 / th[1]);
+      pc[3] = (Real)s;
+      pc[4] = (Real)A;
+      pc[5] = (Real)(A / n);
+      pc[6] = (Real)n;
+      pc[7] = (Real)(-0.5 * A * A);
+      K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
+      break;
+    }
+    case RFL_ARGUS: {
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (Real)(1.0 / (th[0] * th[0]));
+      pc[3] = (Real)th[1];
+      pc[4] = (Real)(2.0 / th[0]);
+      K.dtheta[k][1] = (double)pc[3] - th[1];
+      break;
+    }
+  }
+  return ok;
+}
+
+// Combination constants (one thread), after every leaf's lnI is known.
+template <typename Real>
+__device__ inline void comb_consts(const RfProgram& P, const double* params,
+                                   RfConsts<Real>& K, const double* lnI,
+                                   bool leaves_ok) {
+  bool bad = !leaves_ok;
+  const int C = P.n_comp;
+  double coef[RF_MAXC], base[RF_MAXC];
+  for (int c = 0; c < RF_MAXC; ++c) {
+    coef[c] = 0.0;
+    base[c] = 0.0;
+  }
+  K.ext_sum = 0.0;
+  if (P.kind == RF_KIND_PROD) {
+    coef[0] = 1.0;
+  } else if (P.kind == RF_KIND_FRAC) {
+    double rest = 1.0;
+    for (int c = 0; c < C - 1; ++c) {
+      double f = params[P.coef_par[c]];
+      if (!(f >= 0.0 && f <= 1.0)) bad = true;
+      coef[c] = f;
+      rest -= f;
+    }
+    if (rest < 0.0) {
+      if (rest < -1e-15) bad = true;
+      rest = 0.0;
+    }
+    coef[C - 1] = rest;
+  } else {
+    for (int c = 0; c < C; ++c) {
+      double v = params[P.coef_par[c]];
+      if (!(v >= 0.0) || !isfinite(v)) bad = true;
+      coef[c] = v;
+      K.ext_sum += v;
+    }
+  }
+  for (int k = 0; k < P.n_leaves; ++k) base[P.leaf[k].comp] -= lnI[k];
+  double beta[RF_MAXC];
+  double ref = -CUDART_INF;
+  int zero = 0;
+  for (int c = 0; c < C; ++c) {
+    if (coef[c] > 0.0) {
+      beta[c] = log(coef[c]) + base[c];
+      ref = fmax(ref, beta[c]);
+    } else {
+      beta[c] = -CUDART_INF;
+      zero |= 1 << c;
+    }
+  }
+  if (!(ref > -CUDART_INF) || !isfinite(ref)) {
+    bad = true;
+    ref = 0.0;
+  }
+  K.beta_ref = ref;
+  K.zero_mask = zero;
+  for (int c = 0; c < RF_MAXC; ++c) {
+    K.coef[c] = coef[c];
+    if (c < C && !((zero >> c) & 1)) {
+      double d = beta[c] - ref;
+      K.delta[c] = (Real)d;
+      K.delta_lo[c] = d - (double)K.delta[c];
+    } else {
+      K.delta[c] = (Real)(-CUDART_INF);
+      K.delta_lo[c] = 0.0;
+    }
+    K.delta_nc[c] = (Real)(c < C ? base[c] - ref : 0.0);
+  }
+  K.bad = bad ? 1 : 0;
+}
+
+// All constants by one thread (batched prologue: one thread per toy).
+template <typename Real>
+__device__ inline void build_consts_serial(const RfProgram& P,
+                                           const double* params,
+                                           RfConsts<Real>& K) {
+  double lnI[RF_MAXL];
+  bool ok = true;
+  for (int k = 0; k < P.n_leaves; ++k) ok &= leaf_consts(P, params, K, k, &lnI[k]);
+  comb_consts(P, params, K, lnI, ok);
+}
+
+// ------------------------------------------------------------ event math
+template <typename Real>
+struct Fn;
+template <>
+struct Fn<float> {
+  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  static __device__ __forceinline__ float exp(float x) { return expf(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float ninf() { return -CUDART_INF_F; }
+};
+template <>
+struct Fn<double> {
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double ninf() { return -CUDART_INF; }
+};
+
+// u = log f(x) - off and g_j = d u / d theta_j for one event.  `gm` selects
+// the derivatives that are needed (uniform across the grid).
+template <typename Real>
+__device__ __forceinline__ void eval_leaf(int type, int gm, Real x,
+                                          const Real* __restrict__ pc, Real& u,
+                                          Real (&g)[RF_LEAF_MAXP]) {
+  typedef Fn<Real> F;
+  const Real one = Real(1), half = Real(0.5);
+  switch (type) {
+    case RFL_GAUSS: {
+      Real d = ((x - pc[0]) - pc[1]) * pc[2];
+      u = -half * d * d;
+      g[0] = d * pc[2];
+      g[1] = d * d * pc[2];
+      g[2] = g[3] = Real(0);
+      break;
+    }
+    case RFL_EXP: {
+      Real d = (x - pc[1]) - pc[2];
+      u = pc[0] * d;
+      g[0] = d;
+      g[1] = g[2] = g[3] = Real(0);
+      break;
+    }
+    case RFL_CHEB: {
+      Real xp = x * pc[0] + pc[1];
+      Real t1 = xp, t2 = Real(2) * xp * t1 - one;
+      Real t3 = Real(2) * xp * t2 - t1, t4 = Real(2) * xp * t3 - t2;
+      Real f = one + pc[2] * t1 + pc[3] * t2 + pc[4] * t3 + pc[5] * t4;
+      u = F::log(f);
+      Real r = F::rcp(f);
+      g[0] = t1 * r;
+      g[1] = t2 * r;
+      g[2] = t3 * r;
+      g[3] = t4 * r;
+      break;
+    }
+    case RFL_CB: {
+      // both pieces are evaluated and one is selected (no divergence)
+      Real t = pc[3] * (((x - pc[0]) - pc[1]) * pc[2]);
+      Real A = pc[4];
+      bool tail = t <= -A;
+      Real D = one + pc[5] * (-A - t);
+      Real Lg = F::log(D);
+      Real rD = F::rcp(D);
+      u = tail ? pc[7] - pc[6] * Lg : -half * t * t;
+      Real dudt = tail ? A * rD : -t;
+      g[0] = -dudt * pc[3] * pc[2];
+      g[1] = -dudt * t * pc[2];
+      g[2] = tail ? pc[3] * ((Real(2) * A + t) * rD - A) : Real(0);
+      g[3] = tail ? (one - rD) - Lg : Real(0);
+      break;
+    }
+    case RFL_ARGUS: {
+      Real dm = (pc[0] - x) + pc[1];
+      Real sm = (pc[0] + x) + pc[1];
+      Real tau = dm * sm * pc[2];
+      bool ok = tau > Real(0);
+      Real arg = x * x * tau;
+      u = ok ? half * F::log(arg) + pc[3] * tau : F::ninf();
+      g[1] = ok ? tau : Real(0);
+      if (gm & 1) {
+        Real r = F::rcp(tau);
+        g[0] = ok ? (half * r + pc[3]) * (one - tau) * pc[4] : Real(0);
+      } else {
+        g[0] = Real(0);
+      }
+      g[2] = g[3] = Real(0);
+      break;
+    }
+    default:
+      u = Real(0);
+      g[0] = g[1] = g[2] = g[3] = Real(0);
+  }
+}
+
+// Per-event constants copied from shared memory into registers.
+template <typename Real, int NL>
+struct EvalConsts {
+  Real pc[NL][RF_PC];
+  Real delta[NL];
+  Real delta_nc[NL];
+  int zero_mask;
+  __device__ __forceinline__ void load(const RfConsts<Real>& K) {
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+#pragma unroll
+      for (int j = 0; j < RF_PC; ++j) pc[k][j] = K.pc[k][j];
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      delta[c] = K.delta[c];
+      delta_nc[c] = K.delta_nc[c];
+    }
+    zero_mask = K.zero_mask;
+  }
+};
+
+// One event: leaves -> components -> log-sum-exp -> adjoint weights, added
+// into the iteration partials q (NACC = RF_NACC(NL)).
+template <typename Real, int NL>
+__device__ __forceinline__ void event_accumulate(const RfProgram& P,
+                                                 const EvalConsts<Real, NL>& K,
+                                                 const Real (&xc)[NL],
+                                                 Real (&q)[RF_NACC(NL)]) {
+  typedef Fn<Real> F;
+  Real u[NL], g[NL][RF_LEAF_MAXP];
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int col = P.leaf[k].col;
+    Real x = xc[0];
+#pragma unroll
+    for (int c = 1; c < NL; ++c)
+      if (col == c) x = xc[c];
+    eval_leaf<Real>(P.leaf[k].type, P.leaf[k].gmask, x, K.pc[k], u[k], g[k]);
+  }
+  Real v[NL], w[NL];
+#pragma unroll
+  for (int c = 0; c < NL; ++c) {
+    v[c] = K.delta[c];
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+      if (P.leaf[k].comp == c) v[c] += u[k];
+    w[c] = Real(0);
+  }
+  Real ell;
+  const int C = P.n_comp;
+  if (C == 1) {
+    ell = v[0];
+    w[0] = Real(1);
+  } else if (NL >= 2 && C == 2) {
+    Real dv = v[1] - v[0];
+    Real e = F::exp(-fabs(dv));
+    Real s = Real(1) + e;
+    Real rs = F::rcp(s);
+    ell = fmax(v[0], v[1]) + F::log(s);
+    Real wb = rs, ws = e * rs;
+    w[0] = dv > Real(0) ? ws : wb;
+    w[1] = dv > Real(0) ? wb : ws;
+  } else {
+    Real m = v[0];
+#pragma unroll
+    for (int c = 1; c < NL; ++c)
+      if (c < C) m = fmax(m, v[c]);
+    Real s = Real(0);
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      w[c] = (c < C) ? F::exp(v[c] - m) : Real(0);
+      s += w[c];
+    }
+    ell = m + F::log(s);
+    Real rs = F::rcp(s);
+#pragma unroll
+    for (int c = 0; c < NL; ++c) w[c] *= rs;
+  }
+  q[0] += ell;
+  if (K.zero_mask == 0) {
+#pragma unroll
+    for (int c = 0; c < NL; ++c) q[1 + c] += w[c];
+  } else {
+    // a component with coefficient exactly 0: accumulate P_c/P instead
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      if ((K.zero_mask >> c) & 1) {
+        Real vc = K.delta_nc[c];
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+          if (P.leaf[k].comp == c) vc += u[k];
+        q[1 + c] += F::exp(vc - ell);
+      } else {
+        q[1 + c] += w[c];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int comp = P.leaf[k].comp;
+    Real wk = w[0];
+#pragma unroll
+    for (int c = 1; c < NL; ++c)
+      if (comp == c) wk = w[c];
+    const int gm = P.leaf[k].gmask;
+#pragma unroll
+    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+      if ((gm >> j) & 1) q[1 + NL + k * RF_LEAF_MAXP + j] += wk * g[k][j];
+  }
+}
+
+// ---------------------------------------------------------- event loading
+template <typename Col>
+struct Vec;
+template <>
+struct Vec<float> {
+  static constexpr int W = 4;
+  typedef float4 T;
+};
+template <>
+struct Vec<double> {
+  static constexpr int W = 2;
+  typedef double2 T;
+};
+
+template <typename Real, typename Col, int NL, int EPT>
+__device__ __forceinline__ void load_full(const RfProgram& P,
+                                          const Col* __restrict__ ev,
+                                          int64_t stride, int64_t i0, bool vec,
+                                          Real (&x)[NL][EPT]) {
+  constexpr int W = Vec<Col>::W;
+  static_assert(EPT % W == 0, "EPT must be a multiple of the vector width");
+#pragma unroll
+  for (int c = 0; c < NL; ++c) {
+    if (c < P.n_cols) {
+      const Col* col = ev + (int64_t)P.col_obs[c] * stride + i0;
+      if (vec) {
+        const typename Vec<Col>::T* vp = reinterpret_cast<const typename Vec<Col>::T*>(col);
+#pragma unroll
+        for (int v = 0; v < EPT / W; ++v) {
+          typename Vec<Col>::T t = __ldg(vp + v);
+          const Col* tc = reinterpret_cast<const Col*>(&t);
+#pragma unroll
+          for (int e = 0; e < W; ++e) x[c][v * W + e] = (Real)tc[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) x[c][e] = (Real)__ldg(col + e);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) x[c][e] = Real(0);
+    }
+  }
+}
+
+// Kahan-compensated running sums (value = s - c)
+template <typename Real, int N>
+struct Acc {
+  Real s[N], c[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = c[i] = Real(0);
+  }
+  __device__ __forceinline__ void add(const Real (&q)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      Real y = q[i] - c[i];
+      Real t = s[i] + y;
+      c[i] = (t - s[i]) - y;
+      s[i] = t;
+    }
+  }
+};
+
+// Full iteration: EPT consecutive events starting at i0 (all valid).
+template <typename Real, typename Col, int NL, int EPT>
+__device__ __forceinline__ void iterate_full(const RfProgram& P,
+                                             const EvalConsts<Real, NL>& K,
+                                             const Col* __restrict__ ev,
+                                             int64_t stride, int64_t i0,
+                                             bool vec,
+                                             Acc<Real, RF_NACC(NL)>& acc) {
+  Real x[NL][EPT];
+  load_full<Real, Col, NL, EPT>(P, ev, stride, i0, vec, x);
+  Real q[RF_NACC(NL)];
+#pragma unroll
+  for (int i = 0; i < RF_NACC(NL); ++i) q[i] = Real(0);
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    Real xc[NL];
+#pragma unroll
+    for (int c = 0; c < NL; ++c) xc[c] = x[c][e];
+    event_accumulate<Real, NL>(P, K, xc, q);
+  }
+  acc.add(q);
+}
+
+// Events [i0, i1) with scalar loads, one at a time (heads and tails).
+template <typename Real, typename Col, int NL>
+__device__ inline void iterate_scalar(const RfProgram& P,
+                                      const EvalConsts<Real, NL>& K,
+                                      const Col* __restrict__ ev,
+                                      int64_t stride, int64_t i0, int64_t i1,
+                                      Acc<Real, RF_NACC(NL)>& acc) {
+  for (int64_t i = i0; i < i1; ++i) {
+    Real xc[NL];
+#pragma unroll
+    for (int c = 0; c < NL; ++c)
+      xc[c] = (c < P.n_cols) ? (Real)ev[(int64_t)P.col_obs[c] * stride + i] : Real(0);
+    Real q[RF_NACC(NL)];
+#pragma unroll
+    for (int j = 0; j < RF_NACC(NL); ++j) q[j] = Real(0);
+    event_accumulate<Real, NL>(P, K, xc, q);
+    acc.add(q);
+  }
+}
+
+// --------------------------------------------------------------- reduction
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum N per-thread values over the block in a fixed order; result in
+// out[0..N) (shared), valid after the trailing barrier.  red: [32*N] shared.
+template <int N>
+__device__ inline void block_sum(const double (&val)[N], double* red,
+                                 double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double v = warp_sum(val[i]);
+    if (lane == 0) red[wid * N + i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Sum rows [r0, r1) of partials[row * RF_NACC_MAX + i] for i < N, in a fixed
+// order for a given block size; result in out[0..N) (shared).
+template <int N>
+__device__ inline void rows_sum(const double* partials, int64_t r0, int64_t r1,
+                                double* red, double* out) {
+  double v[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = 0.0;
+  double cmp[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) cmp[i] = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {  // Neumaier
+      double x = __ldcg(partials + r * RF_NACC_MAX + i);
+      double t = v[i] + x;
+      cmp[i] += (fabs(v[i]) >= fabs(x)) ? (v[i] - t) + x : (x - t) + v[i];
+      v[i] = t;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] += cmp[i];
+  block_sum<N>(v, red, out);
+}
+
+// ---------------------------------------------------------------- epilogue
+// T: FP64 totals of the accumulators, n: events.  Writes NLL and gradient.
+template <typename Real, int NL>
+__device__ inline void epilogue(const RfProgram& P, const RfConsts<Real>& K,
+                                const double* T, int64_t n, double* nll,
+                                double* grad, unsigned int* status) {
+  const int C = P.n_comp;
+  double L = T[0];
+  for (int c = 0; c < C; ++c)
+    if (!((K.zero_mask >> c) & 1)) L += T[1 + c] * K.delta_lo[c];
+  for (int k = 0; k < P.n_leaves; ++k)
+    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+      if ((P.leaf[k].gmask >> j) & 1)
+        L -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.dtheta[k][j];
+  double v = -((double)n * K.beta_ref + L) + K.ext_sum;
+  bool bad = K.bad || !isfinite(v);
+  if (grad) {
+    for (int p = 0; p < P.n_par; ++p) grad[p] = 0.0;
+    for (int k = 0; k < P.n_leaves; ++k) {
+      const RfLeafProg& lf = P.leaf[k];
+      double S = ((K.zero_mask >> lf.comp) & 1) ? 0.0 : T[1 + lf.comp];
+      for (int j = 0; j < RF_LEAF_MAXP; ++j)
+        if ((lf.gmask >> j) & 1)
+          grad[lf.par[j]] -= T[1 + NL + k * RF_LEAF_MAXP + j] - S * K.dlogI[k][j];
+    }
+    double R[RF_MAXC];
+    for (int c = 0; c < C; ++c)
+      R[c] = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
+    if (P.kind == RF_KIND_FRAC) {
+      for (int c = 0; c < C - 1; ++c)
+        if ((P.coef_free >> c) & 1) grad[P.coef_par[c]] -= R[c] - R[C - 1];
+    } else if (P.kind == RF_KIND_EXT) {
+      for (int c = 0; c < C; ++c)
+        if ((P.coef_free >> c) & 1) grad[P.coef_par[c]] += 1.0 - R[c];
+    }
+    for (int p = 0; p < P.n_par; ++p) {
+      bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
+      if (fx) grad[p] = 0.0;
+      if (bad) grad[p] = CUDART_NAN;
+    }
+  }
+  if (bad) {
+    v = CUDART_INF;
+    if (status)
+      atomicOr(status, K.bad ? (unsigned)RF_STATUS_PARAM_DOMAIN_BIT
+                             : (unsigned)RF_STATUS_NONFINITE_BIT);
+  }
+  *nll = v;
+}
+
+}  // namespace rf

@@ -1,0 +1,122 @@
+// rf_internal.h -- compiled-graph layout shared by the host graph compiler and
+// the CUDA kernels of librfgpu.  Not part of the public C-ABI (include/rf.h).
+//
+// A graph is compiled into a "sum of products" program: P(x) = sum_c coef_c *
+// prod_{k in c} f_k(x_obs(k)) / I_k, with at most RF_MAXL leaves and RF_MAXC
+// components (the root is a leaf, a Prod of leaves, or an Add whose children
+// are leaves or Prods of leaves).  Per event the kernels work in log space:
+//   u_k   = log f_k(x) - off_k                (unnormalised leaf log-density)
+//   v_c   = delta_c + sum_{k in c} u_k,  delta_c = beta_c - beta_ref
+//   beta_c = log coef_c + sum_{k in c} (off_k - log I_k)     (FP64, hoisted)
+//   ell   = log sum_c exp(v_c),  log P = beta_ref + ell
+// so the NLL is -(n beta_ref + sum_i ell_i) (+ sum of yields if extended).
+#pragma once
+#include <stdint.h>
+
+#define RF_MAXL 4        // leaves per compiled graph
+#define RF_MAXC 4        // components (Add children)
+#define RF_LEAF_MAXP 4   // parameters per leaf
+#define RF_PC 8          // per-leaf evaluation constants
+#define RF_MAXPAR 64
+// per-thread accumulators: ell, one per component, one per (leaf, leaf param)
+#define RF_NACC(NL) (1 + (NL) + (NL) * RF_LEAF_MAXP)
+#define RF_NACC_MAX RF_NACC(RF_MAXL)
+
+enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
+// device status bits (same values as RF_STATUS_* in include/rf.h)
+#define RF_STATUS_PARAM_DOMAIN_BIT 1u
+#define RF_STATUS_NONFINITE_BIT 2u
+enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5 };
+
+struct RfLeafProg {
+  int32_t type;      // RFL_*
+  int32_t col;       // index among the loaded columns (0..n_cols-1)
+  int32_t comp;      // component index
+  int32_t npar;      // parameters of this leaf
+  int32_t par[RF_LEAF_MAXP];  // global parameter slots
+  int32_t gmask;     // bit j: gradient of leaf param j is wanted
+  int32_t pad_;
+  double lo, hi;     // observable range
+};
+
+struct RfProgram {
+  int32_t n_leaves;  // 1..RF_MAXL
+  int32_t n_comp;    // 1..RF_MAXC
+  int32_t kind;      // RF_KIND_*
+  int32_t n_par;     // parameters in the vector
+  int32_t n_cols;    // distinct observables read
+  int32_t col_obs[RF_MAXL];  // column slot -> observable index in the SoA
+  int32_t coef_par[RF_MAXC]; // FRAC: K-1 fraction slots; EXT: K yield slots
+  int32_t coef_free;         // bit c: gradient of coefficient c wanted
+  uint64_t fixed_lo, fixed_hi;  // bit p: parameter p is fixed (grad = 0)
+  RfLeafProg leaf[RF_MAXL];
+};
+
+// Per-call constants, computed in FP64 from the parameter vector (prologue).
+template <typename Real>
+struct RfConsts {
+  Real pc[RF_MAXL][RF_PC];     // per-leaf evaluation constants
+  Real delta[RF_MAXC];         // delta_c rounded to Real (-inf: coef_c == 0)
+  Real delta_nc[RF_MAXC];      // delta_c - log coef_c (used when coef_c == 0)
+  double beta_ref;
+  double lnI[RF_MAXL];         // log I_k - off_k
+  double delta_lo[RF_MAXC];    // delta_c - (double)delta[c]
+  double dlogI[RF_MAXL][RF_LEAF_MAXP];   // d(log I_k - off_k)/d theta_kj
+  double dtheta[RF_MAXL][RF_LEAF_MAXP];  // theta used per event - theta
+  double coef[RF_MAXC];
+  double ext_sum;              // sum of yields (extended) else 0
+  int32_t zero_mask;           // bit c: coef_c == 0
+  int32_t bad;                 // parameter outside its definition range
+};
+
+// Device workspace owned by an rf_graph.
+struct RfWork {
+  double* partials;        // [max_blocks_or_tiles * RF_NACC_MAX]
+  unsigned int* counter;   // [1] block ticket (single dataset)
+  unsigned int* status;    // [1] RF_STATUS_* bits
+  // batched mode
+  int64_t* tile_start;     // [max_toys + 1]
+  unsigned int* toy_counter;  // [max_toys]
+  unsigned int* next_tile; // [1]
+  void* toy_consts;        // [max_toys] RfConsts<Real>
+  double* adam_m1;         // [max_toys * n_par]
+  double* adam_m2;
+  int32_t* adam_t;         // [1] step counter
+};
+
+struct RfLaunchCfg {
+  int block;
+  int ept;
+  int blocks_per_sm;
+  int tile;
+};
+
+// ---- launchers (defined in the .cu files) -------------------------------
+// All return a cudaError_t value (0 = success).  `stream` is a cudaStream_t.
+typedef struct CUstream_st* rf_cuda_stream;
+#define RF_DECL_FUSED(R, C)                                                      \
+  int rf_fused_##R##_##C(const RfProgram&, const RfLaunchCfg&, int, const void*, \
+                         int64_t, const double*, RfWork, double*, double*,       \
+                         rf_cuda_stream);                                         \
+  int rf_logp_##R##_##C(const RfProgram&, const void*, int64_t, const double*,   \
+                        double*, rf_cuda_stream);
+RF_DECL_FUSED(f32, c32)
+RF_DECL_FUSED(f32, c64)
+RF_DECL_FUSED(f64, c32)
+RF_DECL_FUSED(f64, c64)
+
+int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, RfWork W,
+                 void* stream);
+int rf_launch_batched(const RfProgram& P, int eval, int coldt,
+                      const RfLaunchCfg& cfg, int num_sms, const void* events,
+                      int64_t n_events, const int64_t* offsets, int32_t toys,
+                      double* pm, double* out, RfWork W,
+                      const double* adam_scale, double adam_lr, bool plan,
+                      int64_t max_rows, void* stream, int* launches);
+int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
+                    int64_t n, const double* params, double* node_buf,
+                    double* nll, double* grad, double* partials,
+                    unsigned int* counter, void* stream, int* launches);
+size_t rf_plain_bytes(const RfProgram& prog, int64_t n);
+int rf_run_microbench(double* out8);
+size_t rf_consts_size(int eval);

@@ -1,0 +1,111 @@
+"""Host-side tests of the C-ABI (no GPU): the library builds and loads, exports
+every function include/rf.h declares, and the graph compiler's validation
+accepts the five workload models and rejects malformed or unsupported graphs
+with the documented codes."""
+import copy
+import os
+import re
+
+import pytest
+
+import datagen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rf():
+    import paper_2003_12875_gb300 as rf
+    rf.load()
+    return rf
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "rf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(rf):
+    lib = rf.load()
+    names = header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(rf.SYMBOLS)
+
+
+def test_library_is_built_for_sm103a():
+    import paper_2003_12875_gb300.build as b
+    assert "arch=compute_103a,code=sm_103a" in b.ARCH
+
+
+@pytest.mark.parametrize("make", [datagen.c1, lambda: datagen.c2(n=10),
+                                  lambda: datagen.c3(n=10), lambda: datagen.c5(5, 50)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_workload_models_validate(rf, make, prec):
+    w = make()
+    assert rf.validate(w["spec"], w["dtype"], prec) == 0
+
+
+def test_toy_model_validates(rf):
+    assert rf.validate(datagen.gauss_exp_ext_spec(), "f64", "fp64") == 0
+
+
+def _bad(spec, **node_changes):
+    s = copy.deepcopy(spec)
+    for idx, ch in node_changes.items():
+        s["nodes"][int(idx[1:])].update(ch)
+    return s
+
+
+EINVAL, EUNSUPPORTED = 1, 2
+
+
+def test_validation_errors(rf):
+    base = datagen.gauss_exp_spec()
+    assert rf.validate(_bad(base, n0={"params": [0, 9]})) == EINVAL        # index out of range
+    assert rf.validate(_bad(base, n0={"params": [0]})) == EINVAL           # wrong count
+    assert rf.validate(_bad(base, n0={"obs": 3})) == EINVAL                # observable
+    assert rf.validate(_bad(base, n2={"params": []})) == EINVAL            # fraction missing
+    s = copy.deepcopy(base)
+    s["root"] = 7
+    assert rf.validate(s) == EINVAL
+    s = copy.deepcopy(base)
+    s["obs"] = [(1.0, 1.0)]
+    assert rf.validate(s) == EINVAL                                       # empty range
+    s = copy.deepcopy(base)
+    s["nodes"][0]["type"] = "nope" if False else "gauss"
+    assert rf.validate(s) == 0
+
+
+def test_unsupported_shapes(rf):
+    # Prod of two leaves on the same observable
+    s = {"obs": [(0.0, 1.0)], "params": [0.5, 1.0, -1.0],
+         "nodes": [{"type": "gauss", "obs": 0, "params": [0, 1]},
+                   {"type": "exp", "obs": 0, "params": [2]},
+                   {"type": "prod", "children": [0, 1]}], "root": 2}
+    assert rf.validate(s) == EUNSUPPORTED
+    # extended Add below the root
+    s = copy.deepcopy(datagen.gauss_exp_ext_spec())
+    s["nodes"].append({"type": "prod", "children": [2]})
+    s["root"] = 3
+    assert rf.validate(s) == EUNSUPPORTED
+    # five leaves
+    nodes = [{"type": "gauss", "obs": 0, "params": [0, 1]} for _ in range(5)]
+    nodes.append({"type": "add_frac", "children": [0, 1, 2, 3, 4], "params": [2, 2, 2, 2]})
+    s = {"obs": [(0.0, 1.0)], "params": [0.5, 1.0, 0.1], "nodes": nodes, "root": 5}
+    assert rf.validate(s) == EUNSUPPORTED
+    # Chebychev of order 5
+    s = {"obs": [(-1.0, 1.0)], "params": [0.1] * 5,
+         "nodes": [{"type": "cheb", "obs": 0, "params": [0, 1, 2, 3, 4]}], "root": 0}
+    assert rf.validate(s) == EUNSUPPORTED
+    # ARGUS with a free p
+    s = copy.deepcopy(datagen.cb_argus_spec())
+    s["fixed"][6] = False
+    assert rf.validate(s, "f32", "fp32") == EUNSUPPORTED
+    # Add of an Add
+    s = copy.deepcopy(datagen.gauss_exp_spec())
+    s["nodes"].append({"type": "add_frac", "children": [2, 0], "params": [3]})
+    s["root"] = 3
+    assert rf.validate(s) == EUNSUPPORTED

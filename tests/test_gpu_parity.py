@@ -1,0 +1,331 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
+same seeded inputs.  Sizes span several blocks and a ragged tail; the shape
+sweep covers empty, tiny and unaligned inputs; tolerances are in _common.py."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+from _common import TOL, free_mask, grad_l1, logp_err, rel_nll
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def rf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2003_12875_gb300 as rf
+    rf.load()
+    return rf
+
+
+def to_dev(w):
+    dt = torch.float32 if w["dtype"] == "f32" else torch.float64
+    return torch.from_numpy(np.ascontiguousarray(w["cols"])).to(DEV, dt)
+
+
+def params_dev(p):
+    return torch.tensor(np.asarray(p, np.float64), device=DEV)
+
+
+SMALL = {
+    "c1": lambda: datagen.c1(),
+    "c2": lambda: datagen.c2(n=200_003),
+    "c3": lambda: datagen.c3(n=100_003),
+    "c3_noext": lambda: datagen.c3(n=50_001, extended=False),
+    "c5": lambda: datagen.c5(3_000, 300_000),
+}
+OFF_MIN = {  # gradient checks away from the minimum
+    "c1": [0.25, 1.1],
+    "c2": [5.05, 0.52, -0.28, 0.21],
+    "c3": [0.05, 1.55, -0.48, 0.21, -0.09, 0.055, 0.025, 100_500.0],
+    "c3_noext": [0.05, 1.55, -0.48, 0.21, -0.09, 0.055, 0.025],
+    "c5": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.5, 3_050.0, 299_000.0],
+}
+_cache = {}
+
+
+def workload(name):
+    if name not in _cache:
+        w = SMALL[name]()
+        p = OFF_MIN[name]
+        v, g, sc, rc = oracle.nll_scaled(w["spec"], p, w["cols"].astype(np.float64))
+        assert rc == 0
+        _cache[name] = (w, p, v, g, sc)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_nll_and_gradient_match_oracle(rf, name, prec):
+    w, p, v, g, sc = workload(name)
+    G = rf.Graph(w["spec"], w["dtype"], prec)
+    nll, grad = G.nll(to_dev(w), params_dev(p))
+    torch.cuda.synchronize()
+    nll = float(nll.item())
+    grad = grad.cpu().numpy()
+    assert rel_nll(nll, v) <= TOL[prec]["nll"], (nll, v, rel_nll(nll, v))
+    err = grad_l1(grad, g, sc, free_mask(w["spec"]))
+    assert err.max() <= TOL[prec]["grad"], (err, grad, g)
+    fixed = [not f for f in free_mask(w["spec"])]
+    assert all(grad[k] == 0.0 for k in range(len(grad)) if fixed[k])
+    assert G.status() == 0
+    assert G.last_launches() == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5"])
+def test_per_event_log_probability(rf, name, prec):
+    w, p, *_ = workload(name)
+    sub = {**w, "cols": w["cols"][:, :20_011]}
+    want, rc = oracle.logp(w["spec"], p, sub["cols"].astype(np.float64))
+    G = rf.Graph(w["spec"], w["dtype"], prec)
+    got = G.logp(to_dev(sub), params_dev(p)).cpu().numpy()
+    err = logp_err(got, want)
+    assert err.max() <= TOL[prec]["logp"], (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [0, 1, 3, 4, 5, 7, 8, 9, 31, 32, 33, 1023, 1024, 1025, 100_007])
+def test_shape_sweep(rf, n, prec):
+    w = datagen.c2(n=n) if n > 0 else {**datagen.c2(n=1), "cols": np.zeros((1, 0))}
+    p = OFF_MIN["c2"]
+    v, g, sc, rc = oracle.nll_scaled(w["spec"], p, w["cols"])
+    G = rf.Graph(w["spec"], "f64", prec)
+    nll, grad = G.nll(to_dev(w), params_dev(p))
+    nll = float(nll.item())
+    if n == 0:
+        assert nll == 0.0 and np.all(grad.cpu().numpy() == 0.0)
+        return
+    assert rel_nll(nll, v) <= TOL[prec]["nll"]
+    assert grad_l1(grad.cpu().numpy(), g, sc, [True] * 4).max() <= TOL[prec]["grad"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,shift", [(4001, 0), (4000, 1), (4003, 3), (4004, 2), (2, 1)])
+def test_unaligned_columns(rf, n, shift, prec):
+    """Column bases off the 16-byte grid (a sliced buffer) and column phases
+    that differ between observables (n not a multiple of 4)."""
+    w = datagen.c3(n=n)
+    p = OFF_MIN["c3"][:7] + [float(n)]
+    v, g, sc, rc = oracle.nll_scaled(w["spec"], p, w["cols"].astype(np.float64))
+    flat = torch.zeros(3 * n + shift, dtype=torch.float32, device=DEV)
+    flat[shift:] = torch.from_numpy(w["cols"].reshape(-1)).to(DEV)
+    ev = flat[shift:].view(3, n)
+    G = rf.Graph(w["spec"], "f32", prec)
+    nll, grad = G.nll(ev, params_dev(p))
+    assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"]
+    assert grad_l1(grad.cpu().numpy(), g, sc, [True] * 8).max() <= TOL[prec]["grad"]
+
+
+def test_every_launch_configuration(rf):
+    w, p, v, g, sc = workload("c5")
+    ev = to_dev(w)
+    pd = params_dev(p)
+    for prec, epts in (("fp32", (4, 8)), ("fp64", (4,))):
+        G = rf.Graph(w["spec"], "f32", prec)
+        for block in (64, 128, 256):
+            for ept in epts:
+                for bps in (1, 2, 3, 4, 6, 8):
+                    G.set_launch(block=block, ept=ept, blocks_per_sm=bps)
+                    nll, grad = G.nll(ev, pd)
+                    assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"], (block, ept, bps)
+                    err = grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"]))
+                    assert err.max() <= TOL[prec]["grad"], (block, ept, bps, err)
+
+
+def test_tuner_picks_a_valid_configuration(rf):
+    w, p, v, *_ = workload("c2")
+    G = rf.Graph(w["spec"], "f64", "fp32")
+    ms = G.tune(to_dev(w), params_dev(p))
+    assert ms > 0
+    cfg = G.get_launch()
+    assert cfg["block"] in (64, 128, 256) and cfg["ept"] in (4, 8)
+    nll, _ = G.nll(to_dev(w), params_dev(p))
+    assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_run_to_run_bitwise_determinism(rf, prec):
+    w, p, *_ = workload("c5")
+    G = rf.Graph(w["spec"], "f32", prec)
+    ev, pd = to_dev(w), params_dev(p)
+    a = torch.cat(G.nll(ev, pd)).cpu()
+    for _ in range(3):
+        b = torch.cat(G.nll(ev, pd)).cpu()
+        assert torch.equal(a, b)
+
+
+def test_gradient_against_finite_differences(rf):
+    """GPU adjoint vs Richardson differences of the GPU FP64 NLL (<= 1e-4)."""
+    w, p, v, g, sc = workload("c2")
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    ev = to_dev(w)
+    _, grad = G.nll(ev, params_dev(p))
+    grad = grad.cpu().numpy()
+    G32 = rf.Graph(w["spec"], "f64", "fp32")
+    _, grad32 = G32.nll(ev, params_dev(p))
+    grad32 = grad32.cpu().numpy()
+    for j in range(4):
+        h = 1e-4 * max(abs(p[j]), 1e-2)
+
+        def f(x):
+            q = list(p)
+            q[j] = x
+            return float(G.nll(ev, params_dev(q), grad=False)[0].item())
+        d1 = (f(p[j] + h) - f(p[j] - h)) / (2 * h)
+        d2 = (f(p[j] + h / 2) - f(p[j] - h / 2)) / h
+        fd = (4 * d2 - d1) / 3
+        assert abs(grad[j] - fd) <= 1e-4 * sc[j]
+        assert abs(grad32[j] - fd) <= 1e-4 * sc[j]
+
+
+def test_parameter_domain_errors(rf):
+    w, p, *_ = workload("c2")
+    G = rf.Graph(w["spec"], "f64", "fp32")
+    ev = to_dev(w)
+    for bad in ([5.0, -0.5, -0.3, 0.2], [5.0, 0.5, -0.3, 1.5], [5.0, 0.0, -0.3, 0.2]):
+        nll, grad = G.nll(ev, params_dev(bad))
+        assert math.isinf(float(nll.item())) and float(nll.item()) > 0
+        assert torch.isnan(grad).all()
+    st = G.status()
+    assert st & 1
+    assert G.status() == 0          # cleared on read
+    # an event where the Chebychev polynomial is negative: non-finite log P
+    cheb = {"obs": [(-1.0, 1.0)], "params": [1.5], "fixed": [False],
+            "nodes": [{"type": "cheb", "obs": 0, "params": [0]}], "root": 0}
+    G2 = rf.Graph(cheb, "f64", "fp64")
+    nll, _ = G2.nll(torch.tensor([[-0.9, 0.5]], dtype=torch.float64, device=DEV),
+                    params_dev([1.5]))
+    assert math.isinf(float(nll.item()))
+    assert G2.status() & 2
+
+
+def test_zero_fraction_edge(rf):
+    """f = 0 and f = 1: a component with coefficient exactly 0."""
+    w, p, *_ = workload("c2")
+    for f in (0.0, 1.0):
+        q = [5.0, 0.5, -0.3, f]
+        v, g, sc, rc = oracle.nll_scaled(w["spec"], q, w["cols"])
+        for prec in ("fp64", "fp32"):
+            G = rf.Graph(w["spec"], "f64", prec)
+            nll, grad = G.nll(to_dev(w), params_dev(q))
+            assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"]
+            err = grad_l1(grad.cpu().numpy(), g, sc, [True] * 4)
+            assert err.max() <= TOL[prec]["grad"], (f, prec, err)
+
+
+def test_autograd_function(rf):
+    w, p, v, g, sc = workload("c2")
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    pt = params_dev(p).requires_grad_(True)
+    out = rf.RFNll.apply(pt, to_dev(w), G)
+    (2.0 * out).backward()
+    assert rel_nll(float(out.item()), v) <= 1e-12
+    err = grad_l1(pt.grad.cpu().numpy() / 2.0, g, sc, [True] * 4)
+    assert err.max() <= 1e-10
+
+
+def test_host_buffers_entry_point(rf):
+    w, p, v, g, sc = workload("c3")
+    G = rf.Graph(w["spec"], "f32", "fp32")
+    ev = torch.from_numpy(np.ascontiguousarray(w["cols"])).pin_memory()
+    nll, grad = G.nll_host(ev, torch.tensor(p, dtype=torch.float64))
+    d_nll, d_grad = G.nll(to_dev(w), params_dev(p))
+    assert nll == float(d_nll.item())
+    assert torch.equal(grad, d_grad.cpu())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plain_node_by_node_baseline(rf, prec):
+    w, p, v, g, sc = workload("c5")
+    G = rf.Graph(w["spec"], "f32", prec)
+    nll, grad = G.nll_plain(to_dev(w), params_dev(p))
+    assert rel_nll(float(nll.item()), v) <= 1e-12        # always FP64
+    err = grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"]))
+    assert err.max() <= 1e-4                              # central differences
+    assert G.last_launches() > 10
+
+
+def small_toys(t=64):
+    return datagen.c4(toys=t, nu_s_range=(20.0, 2000.0), nu_b_range=(50.0, 5000.0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("tile", [1024, 4096])
+def test_batched_toys_match_oracle_and_single(rf, prec, tile):
+    w = small_toys()
+    pm = w["params_matrix"].copy()
+    pm[:, 0] += 0.02
+    want, rc = oracle.nll_batched(w["spec"], w["cols"], w["offsets"], pm)
+    G = rf.Graph(w["spec"], "f64", prec)
+    ev = to_dev(w)
+    G.set_launch(tile=tile)
+    G.bind_events(ev, 64)
+    off = torch.from_numpy(w["offsets"]).to(DEV)
+    pmd = torch.from_numpy(pm).to(DEV)
+    got = G.nll_batched(off, pmd).cpu().numpy()
+    assert G.last_launches() == 3
+    for t in range(64):
+        b, e = w["offsets"][t], w["offsets"][t + 1]
+        _, gref, sc, _ = oracle.nll_scaled(w["spec"], pm[t], w["cols"][:, b:e])
+        assert rel_nll(got[t, 0], want[t, 0]) <= TOL[prec]["nll"], t
+        assert grad_l1(got[t, 1:], gref, sc, [True] * 5).max() <= TOL[prec]["grad"], t
+        single = G.nll(ev[:, b:e].contiguous(), pmd[t].contiguous())
+        assert rel_nll(float(single[0].item()), got[t, 0]) <= TOL[prec]["nll"]
+
+
+def test_batched_empty_and_tiny_toys(rf):
+    w = small_toys(8)
+    off = w["offsets"].copy()
+    # toy 2 empty, toy 5 one event
+    counts = np.diff(off)
+    counts[2] = 0
+    counts[5] = 1
+    new_off = np.zeros(9, np.int64)
+    np.cumsum(counts, out=new_off[1:])
+    pm = w["params_matrix"]
+    want, _ = oracle.nll_batched(w["spec"], w["cols"], new_off, pm)
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    G.bind_events(to_dev(w), 8)
+    got = G.nll_batched(torch.from_numpy(new_off).to(DEV),
+                        torch.from_numpy(pm).to(DEV)).cpu().numpy()
+    np.testing.assert_allclose(got[:, 0], want[:, 0], rtol=1e-12)
+    assert got[2, 0] == pm[2, 3] + pm[2, 4]          # extended term only
+
+
+def test_fit_toys_follows_oracle_adam(rf):
+    """50 Adam steps per toy, CUDA-graph replayed, against the oracle replaying
+    the same updates from its own gradients (16 toys, FP64 evaluation)."""
+    w = small_toys(16)
+    pm0 = w["params_matrix"].copy()
+    scale = np.array([0.5, 0.5, 0.3, 100.0, 100.0])
+    iters, lr = 50, 1e-2
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    G.bind_events(to_dev(w), 16)
+    pmd = torch.from_numpy(pm0.copy()).to(DEV)
+    G.fit_toys(torch.from_numpy(w["offsets"]).to(DEV), pmd,
+               torch.from_numpy(scale).to(DEV), iters, lr)
+    got = pmd.cpu().numpy()
+    for t in range(16):
+        b, e = w["offsets"][t], w["offsets"][t + 1]
+        th = pm0[t].copy()
+        m1, m2 = np.zeros(5), np.zeros(5)
+        for it in range(1, iters + 1):
+            _, gr, _ = oracle.nll(w["spec"], th, w["cols"][:, b:e])
+            oracle.adam_step(th, gr, scale, [1] * 5, m1, m2, it, lr)
+        np.testing.assert_allclose(got[t], th, rtol=0, atol=1e-7 * scale.max())
+    # the fit moved the parameters toward the generating point
+    assert np.mean(np.abs(got[:, 0] - 5.0)) < np.mean(np.abs(pm0[:, 0] - 5.0))
+
+
+def test_microbench_reports_positive_rates(rf):
+    r = rf.microbench()
+    assert all(v > 0 for v in r.values())
+    assert r["fp32_fma"] > r["fp64_fma"]
