@@ -167,9 +167,11 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
                          const double* params_matrix, double* out,
                          rf_stream stream);
 
-/* A gradient fit of every toy: `iters` Adam steps (Kingma & Ba 2015) on
- * parameters in units of scale[j] (dev FP64 [n_params]), learning rate lr,
- * beta = (0.9, 0.999), eps = 1e-8; fixed parameters do not move.  The
+/* A gradient fit of every toy: `iters` Adam steps (Kingma & Ba 2015) on the
+ * parameters of toy t in units of scale[t*n_params + j] (dev FP64
+ * [toys * n_params]; e.g. each toy's starting |theta|), learning rate lr,
+ * beta = (0.9, 0.999), eps = 1e-8; fixed parameters do not move, and a toy
+ * whose NLL is not finite keeps its parameters for that step.  The
  * per-iteration work (prologue + tile kernel with the Adam step fused into
  * each toy's final reduction) is captured once into a CUDA graph and
  * replayed `iters` times.  params_matrix (dev) is updated in place; out

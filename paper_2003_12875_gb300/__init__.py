@@ -261,8 +261,11 @@ class Graph:
     def fit_toys(self, offsets: torch.Tensor, params_matrix: torch.Tensor,
                  scale: torch.Tensor, iters: int, lr: float) -> torch.Tensor:
         """Adam on every toy, `iters` CUDA-graph replays; params_matrix is
-        updated in place; returns the (NLL, grad) rows of the last evaluation."""
+        updated in place; scale is [toys, n_params] (units of each toy's
+        parameters); returns the (NLL, grad) rows of the last evaluation."""
         toys = offsets.numel() - 1
+        if scale.shape != (toys, self.n_par) or scale.dtype != torch.float64:
+            raise ValueError("scale must be float64 [toys, n_params]")
         out = torch.empty(toys, 1 + self.n_par, dtype=torch.float64, device=offsets.device)
         _check(load().rf_fit_toys(self._h, _ptr(offsets), toys, _ptr(params_matrix),
                                   _ptr(scale), int(iters), float(lr), _ptr(out), _stream()))

@@ -142,11 +142,12 @@ __global__ void __launch_bounds__(256)
           for (int p = 0; p < P.n_par; ++p) {
             bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
             if (fx) continue;
-            double gsc = row[1 + p] * adam_scale[p];
+            const double sc = adam_scale[toy * (int64_t)P.n_par + p];
+            double gsc = row[1 + p] * sc;
             m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
             m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
             double mh = m1[p] / c1, vh = m2[p] / c2;
-            th[p] -= adam_scale[p] * adam_lr * mh / (sqrt(vh) + eps);
+            th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
           }
         }
       }
