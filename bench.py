@@ -161,6 +161,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--generic", action="store_true",
+                    help="run the precompiled generic kernels instead of the per-graph ones")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="events for the CPU oracle baseline (0: the whole workload)")
@@ -192,6 +194,8 @@ def main():
     ev = host.cuda()
     params = torch.tensor(spec["params"], dtype=torch.float64, device="cuda")
     G = rf.Graph(spec, w["dtype"], args.precision)
+    if args.generic:
+        G.set_jit(False)
     out = torch.empty(1 + len(spec["params"]), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -274,6 +278,8 @@ def main():
                        "l2": f"inputs larger than L2 ({bytes_per_launch / 1e6:.0f} MB > 129 MB), "
                              "no flush",
                        "launch": G.get_launch(), "tuned_ms": tuned_ms,
+                       "kernel": "specialised (NVRTC)" if G.uses_jit() else "generic",
+                       "regs_per_thread": G.kernel_regs(),
                        "parallelism": f"{world} independent replica(s)"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "nll": nll_value}

@@ -210,6 +210,23 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events,
                         const double* params, rf_stream stream,
                         double* best_ms);
 
+/* Kernel specialisation.  rf_graph_compile also emits, for its graph, a
+ * model in which the leaf types, columns, component sums and gradient masks
+ * are compile-time constants, and compiles the fused, toy and log P kernels
+ * for it with NVRTC (sm_103a), caching the module for the process; without
+ * it (RF_JIT=0 in the environment, or NVRTC unavailable) the precompiled
+ * generic kernels run the same device code with run-time dispatch.
+ * rf_graph_set_jit(g, 0/1) switches between them (1 compiles if needed and
+ * returns RF_ECUDA with the compiler log in rf_last_error on failure);
+ * rf_graph_uses_jit tells which is in use; rf_graph_kernel_regs gives the
+ * registers per thread of the specialised fused kernel (0 if generic). */
+rf_status rf_graph_set_jit(rf_graph* g, int32_t enable);
+/* Compile the specialised kernels of a descriptor with NVRTC without loading
+ * them (no GPU needed): RF_OK, or RF_ECUDA with the compiler log. */
+rf_status rf_jit_check(const rf_graph_desc* desc);
+int32_t rf_graph_uses_jit(const rf_graph* g);
+int32_t rf_graph_kernel_regs(const rf_graph* g);
+
 /* Synchronises the device, returns the OR of RF_STATUS_* bits raised since
  * the last call, and clears them. */
 rf_status rf_graph_status(rf_graph* g, uint32_t* flags);
@@ -219,6 +236,11 @@ int32_t rf_graph_last_launches(const rf_graph* g);
 
 /* Thread-local description of the last error ("" if none). */
 const char* rf_last_error(void);
+
+/* Diagnostics: y_fast[i] = the library's FP32 natural log of x[i] (used for
+ * per-event log-densities), y_ref[i] = CUDA logf(x[i]); dev arrays [n]. */
+rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
+                       rf_stream stream);
 
 /* Throughput of single operations on this GPU, in operations per second,
  * measured by dedicated kernels (used for the compute roofline):

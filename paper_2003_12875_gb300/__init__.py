@@ -68,7 +68,8 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_nll_host", "rf_logp", "rf_graph_bind_events", "rf_nll_batched",
            "rf_fit_toys", "rf_nll_plain", "rf_graph_get_launch", "rf_graph_set_launch",
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
-           "rf_microbench"]
+           "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
+           "rf_jit_check", "rf_check_log"]
 
 
 def lib_path() -> str:
@@ -107,8 +108,16 @@ def load(build_if_missing: bool = True):
         L.rf_graph_last_launches.restype = i32
         L.rf_last_error.restype = C.c_char_p
         L.rf_microbench.argtypes = [dp]
+        L.rf_graph_set_jit.argtypes = [vp, i32]
+        L.rf_graph_uses_jit.argtypes = [vp]
+        L.rf_graph_uses_jit.restype = i32
+        L.rf_graph_kernel_regs.argtypes = [vp]
+        L.rf_graph_kernel_regs.restype = i32
+        L.rf_jit_check.argtypes = [C.POINTER(_Desc)]
+        L.rf_check_log.argtypes = [vp, vp, vp, i64, vp]
         for name in SYMBOLS:
-            if name not in ("rf_last_error", "rf_graph_last_launches"):
+            if name not in ("rf_last_error", "rf_graph_last_launches", "rf_graph_uses_jit",
+                            "rf_graph_kernel_regs"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -158,6 +167,20 @@ def validate(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64"
     """Host-only check of a spec; returns the rf_status code (0 = OK)."""
     d, keep = make_desc(spec, column_dtype, eval_precision)
     return load().rf_graph_validate(C.byref(d))
+
+
+def jit_check(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64") -> int:
+    """NVRTC-compile the graph's specialised kernels without a GPU; 0 = OK."""
+    d, keep = make_desc(spec, column_dtype, eval_precision)
+    return load().rf_jit_check(C.byref(d))
+
+
+def check_log(x: torch.Tensor):
+    """(library FP32 log, CUDA logf) of a CUDA float32 tensor."""
+    x = x.contiguous()
+    yf, yr = torch.empty_like(x), torch.empty_like(x)
+    _check(load().rf_check_log(_ptr(x), _ptr(yf), _ptr(yr), x.numel(), _stream()))
+    return yf, yr
 
 
 class Graph:
@@ -305,6 +328,15 @@ class Graph:
 
     def last_launches(self) -> int:
         return int(load().rf_graph_last_launches(self._h))
+
+    def set_jit(self, enable: bool):
+        _check(load().rf_graph_set_jit(self._h, 1 if enable else 0))
+
+    def uses_jit(self) -> bool:
+        return bool(load().rf_graph_uses_jit(self._h))
+
+    def kernel_regs(self) -> int:
+        return int(load().rf_graph_kernel_regs(self._h))
 
 
 class RFNll(torch.autograd.Function):

@@ -51,13 +51,38 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 
+PRELUDE_HEADERS = ["rf_internal.h", "rf_device.cuh", "rf_kernels.cuh"]
+
+
+def write_prelude() -> str:
+    """Embed the device headers (the text NVRTC compiles per graph, jit.cpp)
+    as one C++ raw string."""
+    parts = []
+    for h in PRELUDE_HEADERS:
+        with open(os.path.join(CSRC, h)) as f:
+            for line in f:
+                t = line.strip()
+                if t == "#pragma once" or (t.startswith('#include "') and t.endswith('"')):
+                    continue
+                parts.append(line)
+    body = "".join(parts)
+    assert ")RFJIT\"" not in body
+    out = os.path.join(BUILD, "rf_jit_prelude.inc")
+    text = 'static const char kRfJitPrelude[] = R"RFJIT(\n' + body + '\n)RFJIT";\n'
+    if not os.path.exists(out) or open(out).read() != text:
+        with open(out, "w") as f:
+            f.write(text)
+    return out
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_prelude()
     nvcc = _nvcc()
     common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC,
-              "-I", os.path.join(HERE, "..", "include")]
+              "-I", BUILD, "-I", os.path.join(HERE, "..", "include")]
     objs, cmds = [], []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -82,7 +107,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = _cuda_lib_dir(nvcc)
     link = [nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs,
-            "-L", libdir, "-Xlinker", f"-rpath,{libdir}"]
+            "-L", libdir, "-lnvrtc", "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

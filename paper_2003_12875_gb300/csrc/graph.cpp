@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -231,7 +232,35 @@ struct rf_graph {
   unsigned int* plain_counter = nullptr;
   cudaStream_t fit_stream = nullptr;
   int last_launches = 0;
+  // per-graph specialised kernels (NVRTC), by events per thread (index 0 or
+  // 1 of the precision's two options); compiled on first need
+  bool jit = false;
+  cudaKernel_t jk_fused[2] = {nullptr, nullptr};
+  cudaKernel_t jk_toys[2] = {nullptr, nullptr};
+  cudaKernel_t jk_logp = nullptr;
+  int jk_regs[2] = {0, 0};
 };
+
+// index of an events-per-thread option within its precision's pair
+static int ept_index(int eval, int coldt, int ept) {
+  if (eval == RF_EVAL_FP32) return ept == 8 ? 1 : 0;
+  if (coldt == RF_F64) return ept == 4 ? 1 : 0;
+  return 0;
+}
+
+static cudaKernel_t jit_fused(rf_graph* g, int ept, std::string* err) {
+  int i = ept_index(g->eval, g->coldt, ept);
+  if (!g->jk_fused[i])
+    g->jk_fused[i] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_FUSED, ept, &g->jk_regs[i], err);
+  return g->jk_fused[i];
+}
+
+static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
+  int i = ept_index(g->eval, g->coldt, ept);
+  if (!g->jk_toys[i])
+    g->jk_toys[i] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_TOYS, ept, nullptr, err);
+  return g->jk_toys[i];
+}
 
 static void free_work(rf_graph* g) {
   cudaFree(g->work.partials);
@@ -292,7 +321,57 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   }
   g->work.status = g->work.counter + 1;
   g->work.next_tile = g->work.counter + 2;
+  // Specialise the fused kernel for this graph unless RF_JIT=0.  If that is
+  // not possible the graph keeps the precompiled generic kernels (same device
+  // code, run-time dispatch); rf_graph_uses_jit reports which one runs.
+  const char* env = getenv("RF_JIT");
+  if (!(env && env[0] == '0')) {
+    g->jit = true;
+    std::string err;
+    if (!jit_fused(g, g->cfg.ept, &err)) {
+      g->jit = false;
+      g_err = "JIT unavailable, generic kernels in use: " + err;
+    }
+  }
   *out = g;
+  return RF_OK;
+}
+
+rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (!enable) {
+    g->jit = false;
+    return RF_OK;
+  }
+  bool was = g->jit;
+  g->jit = true;
+  std::string err;
+  if (!jit_fused(g, g->cfg.ept, &err)) {
+    g->jit = was;
+    return fail(RF_ECUDA, "JIT compile/load failed: " + err);
+  }
+  return RF_OK;
+}
+
+int32_t rf_graph_uses_jit(const rf_graph* g) { return g && g->jit ? 1 : 0; }
+
+int32_t rf_graph_kernel_regs(const rf_graph* g) {
+  if (!g || !g->jit) return 0;
+  return g->jk_regs[ept_index(g->eval, g->coldt, g->cfg.ept)];
+}
+
+rf_status rf_jit_check(const rf_graph_desc* desc) {
+  g_err.clear();
+  rf_status s = validate_desc(desc);
+  if (s) return s;
+  RfProgram P;
+  s = canonicalise(desc, &P);
+  if (s) return s;
+  std::string err;
+  const int ept = desc->eval_precision == RF_EVAL_FP32 ? 4 : (desc->column_dtype == RF_F64 ? 2 : 4);
+  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_LOGP})
+    if (!rf_jit_compile_only(P, desc->eval_precision, desc->column_dtype, kind, ept, &err))
+      return fail(RF_ECUDA, err);
   return RF_OK;
 }
 
@@ -315,6 +394,12 @@ static rf_status check_events(const rf_graph* g, const void* events, int64_t n) 
 static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, int64_t n,
                           const double* params, double* nll, double* grad, cudaStream_t st) {
   const RfProgram& P = g->prog;
+  if (g->jit) {
+    cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)];
+    if (!k) return (int)cudaErrorInvalidValue;  // compiled by compile/set_launch/tune
+    return rf_jit_launch_fused(k, P, g->coldt, cfg, g->num_sms, ev, n, params, g->work, nll,
+                               grad, st);
+  }
   if (g->eval == RF_EVAL_FP32)
     return g->coldt == RF_F32
                ? rf_fused_f32_c32(P, cfg, g->num_sms, ev, n, params, g->work, nll, grad, st)
@@ -391,7 +476,14 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events, const doubl
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const RfProgram& P = g->prog;
   int e;
-  if (g->eval == RF_EVAL_FP32)
+  if (g->jit && !g->jk_logp) {
+    std::string err;  // first call compiles the kernel (host-synchronous)
+    g->jk_logp = rf_jit_kernel(P, g->eval, g->coldt, RF_JIT_LOGP, 0, nullptr, &err);
+    if (!g->jk_logp) return fail(RF_ECUDA, "JIT log P kernel: " + err);
+  }
+  if (g->jit)
+    e = rf_jit_launch_logp(g->jk_logp, P, events, n_events, params, logp, st);
+  else if (g->eval == RF_EVAL_FP32)
     e = g->coldt == RF_F32 ? rf_logp_f32_c32(P, events, n_events, params, logp, st)
                            : rf_logp_f32_c64(P, events, n_events, params, logp, st);
   else
@@ -439,6 +531,10 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
   if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
   g->work.adam_t = reinterpret_cast<int32_t*>(g->work.toy_counter + max_toys);
+  if (g->jit) {
+    std::string err;
+    if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
+  }
   g->bound_events = events;
   g->bound_n = n_events;
   g->max_toys = max_toys;
@@ -453,6 +549,10 @@ static rf_status batched_checks(rf_graph* g, const int64_t* offsets, int32_t toy
   if (toys < 1 || toys > g->max_toys) return fail(RF_EINVAL, "toys must be in 1..max_toys");
   if (!offsets || !pm || !out) return fail(RF_EINVAL, "NULL argument");
   if (g->cfg.tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
+  if (g->jit && !g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)]) {
+    std::string err;
+    if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
+  }
   return RF_OK;
 }
 
@@ -463,7 +563,9 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
   int n = 0;
   int e = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
                             g->bound_n, offsets, toys, const_cast<double*>(params_matrix), out,
-                            g->work, nullptr, 0.0, true, g->max_tile_rows, stream, &n);
+                            g->work, nullptr, 0.0, true, g->max_tile_rows,
+                            g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
+                            stream, &n);
   g->last_launches = n;
   if (e) return cuda_fail((cudaError_t)e, "rf_nll_batched launch");
   return RF_OK;
@@ -501,7 +603,9 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
     int n = 0;
     le = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
                            g->bound_n, offsets, toys, params_matrix, out, g->work, scale, lr,
-                           false, g->max_tile_rows, fs, &n);
+                           false, g->max_tile_rows,
+                           g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
+                           fs, &n);
     e = cudaStreamEndCapture(fs, &graph);
     if (le) {
       if (graph) cudaGraphDestroy(graph);
@@ -581,6 +685,12 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
   if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
     return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
   if (cfg->tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
+  if (g->jit) {
+    std::string err;
+    if (!jit_fused(g, cfg->ept, &err)) return fail(RF_ECUDA, "JIT fused kernel: " + err);
+    if (g->bound_events && !jit_toys(g, cfg->ept, &err))
+      return fail(RF_ECUDA, "JIT toy kernel: " + err);
+  }
   g->cfg.block = cfg->block;
   g->cfg.ept = cfg->ept;
   g->cfg.blocks_per_sm = cfg->blocks_per_sm;
@@ -611,6 +721,14 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
     epts[1] = 4;
   } else {
     epts[0] = epts[1] = 4;
+  }
+  if (g->jit) {
+    std::string err;
+    for (int ei = 0; ei < 2; ++ei)
+      if (!jit_fused(g, epts[ei], &err)) {
+        cudaFree(dout);
+        return fail(RF_ECUDA, "JIT fused kernel: " + err);
+      }
   }
   RfLaunchCfg best = g->cfg;
   float best_t = 1e30f;
@@ -663,6 +781,14 @@ rf_status rf_graph_status(rf_graph* g, uint32_t* flags) {
 }
 
 int32_t rf_graph_last_launches(const rf_graph* g) { return g ? g->last_launches : 0; }
+
+rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
+                       rf_stream stream) {
+  if (n < 0 || (n > 0 && (!x || !y_fast || !y_ref))) return fail(RF_EINVAL, "bad argument");
+  int e = rf_run_check_log(x, y_fast, y_ref, n, reinterpret_cast<cudaStream_t>(stream));
+  if (e) return cuda_fail((cudaError_t)e, "rf_check_log");
+  return RF_OK;
+}
 
 rf_status rf_microbench(double* out8) {
   if (!out8) return fail(RF_EINVAL, "out8 is NULL");

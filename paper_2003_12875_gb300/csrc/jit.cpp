@@ -1,0 +1,283 @@
+// jit.cpp -- per-graph specialisation of the fused kernels.
+//
+// rf_graph_compile turns the graph into a small Model struct in which the leaf
+// types, the column each leaf reads, the component sums and the gradient
+// masks are compile-time constants, appends it to the library's own device
+// headers (rf_internal.h, rf_device.cuh, rf_kernels.cuh, embedded at build
+// time), and compiles the fused, toy-tile and log P kernels for sm_103a with
+// NVRTC.  The per-event code then has no run-time dispatch and computes only
+// the derivatives that are needed.  Compiled modules are cached for the
+// process by their source text and device.  The paper's own just-in-time path
+// (Sec. 4: formula PDFs compiled by cling) motivates the form; here the
+// compiler specialises the built-in PDFs of one graph.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "rf_internal.h"
+#include "rf_jit_prelude.inc"  // kRfJitPrelude: the device headers as text
+
+namespace {
+
+std::mutex g_mu;
+std::map<std::string, cudaKernel_t> g_cache;      // (device | source) -> kernel
+std::vector<cudaLibrary_t> g_libs;                // kept loaded for the process
+
+const char* leaf_fn(int type) {
+  switch (type) {
+    case RFL_GAUSS: return "leaf_gauss";
+    case RFL_EXP: return "leaf_exp";
+    case RFL_CHEB: return "leaf_cheb";
+    case RFL_CB: return "leaf_cb";
+    case RFL_ARGUS: return "leaf_argus";
+  }
+  return nullptr;
+}
+
+// FNV-1a, for the on-disk cache file name
+uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::string cache_dir() {
+  if (const char* d = getenv("RF_JIT_CACHE_DIR")) return d;
+  const char* tmp = getenv("TMPDIR");
+  return std::string(tmp ? tmp : "/tmp") + "/rfgpu-jit";
+}
+
+}  // namespace
+
+std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept) {
+  const int NL = P.n_leaves, NC = P.n_comp;
+  unsigned long long amask = 1ull;  // ell
+  for (int c = 0; c < NC; ++c) amask |= 1ull << (1 + c);
+  for (int k = 0; k < NL; ++k)
+    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+      if ((P.leaf[k].gmask >> j) & 1) amask |= 1ull << (1 + NL + k * RF_LEAF_MAXP + j);
+  std::ostringstream o;
+  o << kRfJitPrelude << "\n// ---- model emitted for this graph\n";
+  o << "struct RfModel {\n  static constexpr int NL_ = " << NL << ";\n"
+    << "  static constexpr int NCOL = " << P.n_cols << ";\n"
+    << "  static constexpr unsigned long long AMASK = " << amask << "ull;\n"
+    << "  template <typename Real>\n  static __device__ __forceinline__ void event(const RfProgram& P, "
+       "const rf::EvalConsts<Real, NL_>& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
+  for (int k = 0; k < NL; ++k) {
+    const RfLeafProg& L = P.leaf[k];
+    o << "    Real u" << k << ", g" << k << "[4];\n    rf::" << leaf_fn(L.type) << "<Real, "
+      << L.gmask << ">(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k << ");\n";
+  }
+  o << "    Real v[" << NC << "], w[" << NC << "];\n";
+  std::vector<std::string> usum(NC);
+  for (int c = 0; c < NC; ++c) {
+    std::string s;
+    for (int k = 0; k < NL; ++k)
+      if (P.leaf[k].comp == c) s += " + u" + std::to_string(k);
+    usum[c] = s;
+    o << "    v[" << c << "] = K.delta[" << c << "]" << s << ";\n";
+  }
+  o << "    const Real ell = rf::lse<Real, " << NC << ">(v, w);\n    q[0] += ell;\n";
+  if (NC == 1) {
+    o << "    q[1] += Real(1);\n";
+  } else {
+    for (int c = 0; c < NC; ++c)
+      o << "    q[" << 1 + c << "] += rf::comp_weight<Real>(K.zero_mask, " << c << ", K.delta_nc["
+        << c << "]" << usum[c] << ", ell, w[" << c << "]);\n";
+  }
+  for (int k = 0; k < NL; ++k)
+    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+      if ((P.leaf[k].gmask >> j) & 1)
+        o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += w[" << P.leaf[k].comp << "] * g" << k
+          << "[" << j << "];\n";
+  o << "  }\n};\n";
+  const char* R = eval ? "double" : "float";
+  const char* C = coldt ? "double" : "float";
+  if (kind == RF_JIT_FUSED) {
+    o << "extern \"C\" __global__ void __launch_bounds__(256) rf_fused_jit(const RfProgram P, const "
+      << C << "* __restrict__ ev, int64_t n, int64_t head, int vec, const double* __restrict__ "
+              "params, RfWork W, double* nll, double* grad) {\n  rf::fused_body<RfModel, "
+      << R << ", " << C << ", " << ept << ">(P, ev, n, head, vec, params, W, nll, grad);\n}\n";
+  } else if (kind == RF_JIT_TOYS) {
+    o << "extern \"C\" __global__ void __launch_bounds__(256) rf_toys_jit(const RfProgram P, const "
+      << C << "* __restrict__ ev, int64_t stride, int vec, const int64_t* __restrict__ offsets, "
+              "int32_t toys, int64_t tile_ev, double* pm, double* out, RfWork W, "
+              "const double* __restrict__ adam_scale, double adam_lr, int64_t max_rows) {\n"
+              "  rf::toy_tile_body<RfModel, "
+      << R << ", " << C << ", " << ept
+      << ">(P, ev, stride, vec, offsets, toys, tile_ev, pm, out, W, adam_scale, adam_lr, "
+         "max_rows);\n}\n";
+  } else {
+    o << "extern \"C\" __global__ void __launch_bounds__(256) rf_logp_jit(const RfProgram P, const "
+      << C << "* __restrict__ ev, int64_t n, const double* __restrict__ params, double* logp) {\n"
+              "  rf::logp_body<RfModel, "
+      << R << ", " << C << ">(P, ev, n, params, logp);\n}\n";
+  }
+  return o.str();
+}
+
+// NVRTC: source -> cubin for sm_103a (no device needed).
+static bool compile_cubin(const std::string& src, std::vector<char>* cubin, std::string* err) {
+  if (const char* dump = getenv("RF_JIT_DUMP")) {  // write the emitted source for inspection
+    if (FILE* f = fopen(dump, "w")) {
+      fputs(src.c_str(), f);
+      fclose(f);
+    }
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "rf_graph.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-DRF_JIT=1"};
+  nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  size_t log_size = 0;
+  nvrtcGetProgramLogSize(prog, &log_size);
+  std::string log(log_size, '\0');
+  if (log_size) nvrtcGetProgramLog(prog, &log[0]);
+  if (getenv("RF_JIT_VERBOSE")) fprintf(stderr, "[rf jit] %s\n", log.c_str());
+  if (r != NVRTC_SUCCESS) {
+    *err = std::string("NVRTC: ") + nvrtcGetErrorString(r) + "\n" + log;
+    nvrtcDestroyProgram(&prog);
+    return false;
+  }
+  size_t cubin_size = 0;
+  nvrtcGetCUBINSize(prog, &cubin_size);
+  cubin->resize(cubin_size);
+  nvrtcGetCUBIN(prog, cubin->data());
+  nvrtcDestroyProgram(&prog);
+  return true;
+}
+
+bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                         std::string* err) {
+  std::vector<char> cubin;
+  return compile_cubin(rf_jit_source(P, eval, coldt, kind, ept), &cubin, err);
+}
+
+// The kernel of the given kind specialised for P: from the process cache, else
+// from the on-disk cache, else compiled with NVRTC (and written to disk).
+// Host-synchronous; returns nullptr and fills *err on failure.
+cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                           int* regs, std::string* err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    *err = "no current device";
+    return nullptr;
+  }
+  std::string src = rf_jit_source(P, eval, coldt, kind, ept);
+  std::string key = std::to_string(dev) + "|" + src;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(key);
+  cudaKernel_t k = nullptr;
+  if (it != g_cache.end()) {
+    k = it->second;
+  } else {
+    char name[64];
+    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v2"));
+    const std::string dir = cache_dir(), path = dir + name;
+    std::vector<char> cubin;
+    if (FILE* f = fopen(path.c_str(), "rb")) {
+      fseek(f, 0, SEEK_END);
+      long sz = ftell(f);
+      fseek(f, 0, SEEK_SET);
+      if (sz > 0) {
+        cubin.resize((size_t)sz);
+        if (fread(cubin.data(), 1, (size_t)sz, f) != (size_t)sz) cubin.clear();
+      }
+      fclose(f);
+    }
+    if (cubin.empty()) {
+      if (!compile_cubin(src, &cubin, err)) return nullptr;
+      mkdir(dir.c_str(), 0700);
+      std::string tmp = path + "." + std::to_string(getpid());
+      if (FILE* f = fopen(tmp.c_str(), "wb")) {
+        bool ok = fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+        fclose(f);
+        if (ok) rename(tmp.c_str(), path.c_str());
+        else remove(tmp.c_str());
+      }
+    }
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+      *err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    const char* kname = kind == RF_JIT_FUSED ? "rf_fused_jit"
+                        : kind == RF_JIT_TOYS ? "rf_toys_jit" : "rf_logp_jit";
+    e = cudaLibraryGetKernel(&k, lib, kname);
+    if (e != cudaSuccess) {
+      *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+      cudaLibraryUnload(lib);
+      return nullptr;
+    }
+    g_libs.push_back(lib);
+    g_cache[key] = k;
+  }
+  if (regs) {
+    cudaFuncAttributes a;
+    *regs = cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k)) == cudaSuccess ? a.numRegs : 0;
+  }
+  return k;
+}
+
+int rf_jit_launch_fused(cudaKernel_t k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
+                        int num_sms, const void* events, int64_t n, const double* params,
+                        RfWork W, double* nll, double* grad, cudaStream_t st) {
+  int vec = 0;
+  int64_t head = 0;
+  rf_vec_plan(P, events, n, coldt ? 8 : 4, &vec, &head);
+  int64_t chunks = n / cfg.ept;
+  int64_t want = (chunks + cfg.block - 1) / cfg.block;
+  int64_t cap = (int64_t)num_sms * cfg.blocks_per_sm;
+  int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+  RfProgram Pc = P;
+  const void* ev = events;
+  void* args[] = {&Pc, &ev, &n, &head, &vec, &params, &W, &nll, &grad};
+  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(cfg.block),
+                               args, 0, st);
+}
+
+int rf_jit_launch_toys(cudaKernel_t k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
+                       int num_sms, const void* events, int64_t n_events,
+                       const int64_t* offsets, int32_t toys, double* pm, double* out,
+                       RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
+                       cudaStream_t st) {
+  int vec = 0;
+  int64_t head = 0;
+  rf_vec_plan(P, events, n_events, coldt ? 8 : 4, &vec, &head);
+  int grid = num_sms * cfg.blocks_per_sm;
+  RfProgram Pc = P;
+  const void* ev = events;
+  int64_t stride = n_events, tile = cfg.tile;
+  void* args[] = {&Pc, &ev, &stride, &vec, &offsets, &toys, &tile, &pm, &out, &W,
+                  &adam_scale, &adam_lr, &max_rows};
+  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(cfg.block),
+                               args, 0, st);
+}
+
+int rf_jit_launch_logp(cudaKernel_t k, const RfProgram& P, const void* events, int64_t n,
+                       const double* params, double* logp, cudaStream_t st) {
+  int64_t g = (n + 255) / 256;
+  int grid = (int)(g < 1 ? 1 : (g > 65535 * 8 ? 65535 * 8 : g));
+  RfProgram Pc = P;
+  const void* ev = events;
+  void* args[] = {&Pc, &ev, &n, &params, &logp};
+  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(256), args, 0,
+                               st);
+}

@@ -76,7 +76,8 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
                       int num_sms, const void* events, int64_t n_events,
                       const int64_t* offsets, int32_t toys, double* pm, double* out,
                       RfWork W, const double* adam_scale, double adam_lr, bool plan,
-                      int64_t max_rows, void* stream, int* launches) {
+                      int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
+                      int* launches) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int n = 0, rc;
   if (plan) {
@@ -96,7 +97,10 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   ++n;
   rc = (int)cudaGetLastError();
   if (rc) return rc;
-  if (eval == 0 && coldt == 0)
+  if (jit_toys)
+    rc = rf_jit_launch_toys(jit_toys, P, coldt, cfg, num_sms, events, n_events, offsets, toys, pm,
+                            out, W, adam_scale, adam_lr, max_rows, st);
+  else if (eval == 0 && coldt == 0)
     rc = rf_toys_f32_c32(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);
   else if (eval == 0)
     rc = rf_toys_f32_c64(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);

@@ -4,7 +4,7 @@
 // work cannot be removed.  Ops/s = threads * 8 * iterations / kernel time.
 #include <cuda_runtime.h>
 
-#include "rf_internal.h"
+#include "rf_device.cuh"
 
 namespace {
 
@@ -73,4 +73,22 @@ int rf_run_microbench(double* out) {
   e = cudaGetLastError();
   cudaFree(sink);
   return (int)e;
+}
+
+// The library's FP32 logarithm next to CUDA's logf on the same inputs (for the
+// accuracy test of the former).
+__global__ void check_log_kernel(const float* x, float* yf, float* yr, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    yf[i] = rf::log_fast(x[i]);
+    yr[i] = logf(x[i]);
+  }
+}
+
+int rf_run_check_log(const float* x, float* y_fast, float* y_ref, int64_t n, cudaStream_t st) {
+  if (n == 0) return 0;
+  int64_t g = (n + 255) / 256;
+  int grid = (int)(g > 4096 ? 4096 : g);
+  check_log_kernel<<<grid, 256, 0, st>>>(x, y_fast, y_ref, n);
+  return (int)cudaGetLastError();
 }

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256)
     rows_sum<1>(partials, 0, gridDim.x, red, tot);
     if (threadIdx.x == 0) {
       double v = tot[0] + K->ext_sum;
-      *res = (K->bad || !isfinite(v)) ? CUDART_INF : v;
+      *res = (K->bad || !isfinite(v)) ? kInf() : v;
       *counter = 0u;
     }
   }

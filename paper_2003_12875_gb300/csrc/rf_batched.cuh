@@ -13,7 +13,7 @@
 //                  toy's parameter row.
 // Results do not depend on which block ran which tile.
 #pragma once
-#include "rf_device.cuh"
+#include "rf_kernels.cuh"
 
 namespace rf {
 
@@ -21,16 +21,7 @@ template <typename Real>
 __global__ void toy_prep_kernel(const RfProgram P, const double* __restrict__ pm,
                                 int32_t toys, RfConsts<Real>* consts,
                                 unsigned int* next_tile, int32_t* adam_t) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    *next_tile = 0u;
-    if (adam_t) *adam_t += 1;
-  }
-  if (t < toys) {
-    RfConsts<Real> K;
-    build_consts_serial(P, pm + (int64_t)t * P.n_par, K);
-    consts[t] = K;
-  }
+  toy_prep_body<Real>(P, pm, toys, consts, next_tile, adam_t);
 }
 
 template <typename Real, typename Col, int NL, int EPT>
@@ -40,120 +31,8 @@ __global__ void __launch_bounds__(256)
                     int64_t tile_ev, double* pm, double* out, RfWork W,
                     const double* __restrict__ adam_scale, double adam_lr,
                     int64_t max_rows) {
-  constexpr int NA = RF_NACC(NL);
-  __shared__ RfConsts<Real> K;
-  __shared__ double red[32 * NA];
-  __shared__ double tot[NA];
-  __shared__ int64_t s_tile, s_toy, s_b, s_e, s_total;
-  __shared__ int s_last;
-  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
-  static_assert(sizeof(RfConsts<Real>) % sizeof(double) == 0, "RfConsts size");
-
-  if (threadIdx.x == 0) s_total = __ldcg(W.tile_start + toys);
-  __syncthreads();
-  const int64_t total = s_total < max_rows ? s_total : max_rows;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      int64_t tl = (int64_t)atomicAdd(W.next_tile, 1u);
-      s_tile = tl;
-      if (tl < total) {
-        int lo = 0, hi = toys - 1;  // last toy with tile_start <= tl
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (__ldcg(W.tile_start + mid) <= tl) lo = mid;
-          else hi = mid - 1;
-        }
-        int64_t j = tl - __ldcg(W.tile_start + lo);
-        // clamp to the bound columns: a bad offset table reads nothing outside
-        int64_t ob = offsets[lo], oe = offsets[lo + 1];
-        ob = ob < 0 ? 0 : (ob > stride ? stride : ob);
-        oe = oe < ob ? ob : (oe > stride ? stride : oe);
-        int64_t b = ob + j * tile_ev;
-        int64_t e = b + tile_ev < oe ? b + tile_ev : oe;
-        s_toy = lo;
-        s_b = b < oe ? b : oe;
-        s_e = e;
-      }
-    }
-    __syncthreads();
-    const int64_t tl = s_tile;
-    if (tl >= total) break;
-    const int64_t toy = s_toy, b = s_b, e = s_e;
-    {
-      const double* src = reinterpret_cast<const double*>(consts + toy);
-      double* dst = reinterpret_cast<double*>(&K);
-      for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = __ldcg(src + w);
-    }
-    __syncthreads();
-
-    Acc<Real, NA> acc;
-    acc.zero();
-    if (!K.bad && e > b) {
-      EvalConsts<Real, NL> E;
-      E.load(K);
-      int64_t h = 0;
-      if (vec) {
-        uintptr_t a = reinterpret_cast<uintptr_t>(ev + (int64_t)P.col_obs[0] * stride + b);
-        h = (int64_t)(((16u - (a & 15u)) & 15u) / sizeof(Col));
-        if (h > e - b) h = e - b;
-      }
-      const int64_t nfull = (e - b - h) / EPT;
-      for (int64_t ch = threadIdx.x; ch < nfull; ch += blockDim.x)
-        iterate_full<Real, Col, NL, EPT>(P, E, ev, stride, b + h + ch * EPT, vec != 0, acc);
-      if (threadIdx.x == blockDim.x - 1) {
-        iterate_scalar<Real, Col, NL>(P, E, ev, stride, b, b + h, acc);
-        iterate_scalar<Real, Col, NL>(P, E, ev, stride, b + h + nfull * EPT, e, acc);
-      }
-    }
-    double val[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) val[i] = (double)acc.s[i] - (double)acc.c[i];
-    block_sum<NA>(val, red, tot);
-    if (threadIdx.x < NA) W.partials[tl * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t r0 = __ldcg(W.tile_start + toy), r1 = __ldcg(W.tile_start + toy + 1);
-      unsigned need = (unsigned)(r1 - r0);
-      s_last = (atomicAdd(W.toy_counter + toy, 1u) == need - 1u) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      int64_t r0 = __ldcg(W.tile_start + toy), r1 = __ldcg(W.tile_start + toy + 1);
-      rows_sum<NA>(W.partials, r0, r1, red, tot);
-      if (threadIdx.x == 0) {
-        int64_t ob = offsets[toy], oe = offsets[toy + 1];
-        ob = ob < 0 ? 0 : (ob > stride ? stride : ob);
-        oe = oe < ob ? ob : (oe > stride ? stride : oe);
-        int64_t nt = oe - ob;
-        double* row = out + toy * (int64_t)(1 + P.n_par);
-        epilogue<Real, NL>(P, K, tot, nt, row, row + 1, W.status);
-        W.toy_counter[toy] = 0u;
-        if (adam_scale && isfinite(row[0])) {
-          // Adam (Kingma & Ba 2015) in units of scale: u = theta / scale
-          const int step = *W.adam_t;
-          const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
-          const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-          double* th = pm + toy * (int64_t)P.n_par;
-          double* m1 = W.adam_m1 + toy * (int64_t)P.n_par;
-          double* m2 = W.adam_m2 + toy * (int64_t)P.n_par;
-          for (int p = 0; p < P.n_par; ++p) {
-            bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
-            if (fx) continue;
-            const double sc = adam_scale[toy * (int64_t)P.n_par + p];
-            double gsc = row[1 + p] * sc;
-            m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
-            m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
-            double mh = m1[p] / c1, vh = m2[p] / c2;
-            th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
+  toy_tile_body<GenericModel<NL>, Real, Col, EPT>(P, ev, stride, vec, offsets, toys, tile_ev,
+                                                  pm, out, W, adam_scale, adam_lr, max_rows);
 }
 
 template <typename Real, typename Col, int NL, int EPT>

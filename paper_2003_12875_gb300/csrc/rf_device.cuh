@@ -19,13 +19,15 @@
 //              D = 1 - (A/n)(A + t)
 //  ARGUS       f = x tau^(1/2) exp(c tau), tau = 1 - (x/m0)^2 (x < m0)
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
-#include <math_constants.h>
-#include <stdint.h>
-
+#endif
 #include "rf_internal.h"
 
 namespace rf {
+
+__device__ __forceinline__ double kInf() { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ double kNaN() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kSqrtHalfPi = 1.25331413731550025121;
@@ -82,7 +84,7 @@ __device__ inline double argus_int(double q, double tau, double c) {
 // the constant the per-event code leaves out of u = log f - off (Exponential:
 // lambda * lo, so that u = lambda (x - lo) stays small).  Returns false when
 // the parameters are outside the leaf's definition range.
-__device__ inline bool leaf_lognorm(int type, const double* th, double lo,
+static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, double lo,
                                     double hi, double* lnI, double* dln) {
   for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = 0.0;
   switch (type) {
@@ -186,7 +188,7 @@ __device__ inline void split_hi_lo(double v, Real& hi, Real& lo) {
 
 // Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k] and lnI_out.
 template <typename Real>
-__device__ inline bool leaf_consts(const RfProgram& P, const double* params,
+__device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, int k, double* lnI_out) {
   const RfLeafProg& L = P.leaf[k];
   double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
@@ -226,13 +228,13 @@ __device__ inline bool leaf_consts(const RfProgram& P, const double* params,
     case RFL_CB: {
       double s = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
       split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(1.0 / th[1]);
+      pc[2] = (Real)(s / th[1]);  // t = (x - m0) * s/sigma
       pc[3] = (Real)s;
       pc[4] = (Real)A;
       pc[5] = (Real)(A / n);
       pc[6] = (Real)n;
       pc[7] = (Real)(-0.5 * A * A);
-      K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
+      K.dtheta[k][1] = 1.0 / fabs((double)pc[2]) - th[1];
       break;
     }
     case RFL_ARGUS: {
@@ -249,7 +251,7 @@ __device__ inline bool leaf_consts(const RfProgram& P, const double* params,
 
 // Combination constants (one thread), after every leaf's lnI is known.
 template <typename Real>
-__device__ inline void comb_consts(const RfProgram& P, const double* params,
+__device__ __noinline__ void comb_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, const double* lnI,
                                    bool leaves_ok) {
   bool bad = !leaves_ok;
@@ -285,18 +287,18 @@ __device__ inline void comb_consts(const RfProgram& P, const double* params,
   }
   for (int k = 0; k < P.n_leaves; ++k) base[P.leaf[k].comp] -= lnI[k];
   double beta[RF_MAXC];
-  double ref = -CUDART_INF;
+  double ref = -kInf();
   int zero = 0;
   for (int c = 0; c < C; ++c) {
     if (coef[c] > 0.0) {
       beta[c] = log(coef[c]) + base[c];
       ref = fmax(ref, beta[c]);
     } else {
-      beta[c] = -CUDART_INF;
+      beta[c] = -kInf();
       zero |= 1 << c;
     }
   }
-  if (!(ref > -CUDART_INF) || !isfinite(ref)) {
+  if (!(ref > -kInf()) || !isfinite(ref)) {
     bad = true;
     ref = 0.0;
   }
@@ -309,7 +311,7 @@ __device__ inline void comb_consts(const RfProgram& P, const double* params,
       K.delta[c] = (Real)d;
       K.delta_lo[c] = d - (double)K.delta[c];
     } else {
-      K.delta[c] = (Real)(-CUDART_INF);
+      K.delta[c] = (Real)(-kInf());
       K.delta_lo[c] = 0.0;
     }
     K.delta_nc[c] = (Real)(c < C ? base[c] - ref : 0.0);
@@ -329,97 +331,196 @@ __device__ inline void build_consts_serial(const RfProgram& P,
 }
 
 // ------------------------------------------------------------ event math
+// FP32 natural logarithm for x > 0 (normal, finite): x = 2^e m with
+// m in [1/sqrt2, sqrt2), log m = 2 atanh(s), s = (m-1)/(m+1), |s| <= 0.1716,
+// by the series 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) (the classical
+// argument-reduction + atanh expansion, e.g. Abramowitz & Stegun 4.1.27);
+// the first omitted term is < 1e-9 relative.  s uses the approximate
+// hardware reciprocal (max 1 ulp), so the result is within a few ulp of the
+// correctly rounded log.  Zero, negative, subnormal, infinite and NaN
+// arguments go to logf.  Tested against logf in the GPU tests.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float log_fast(float x) {
+  if (!(x >= 1.17549435e-38f && x <= 3.40282347e+38f)) return logf(x);
+  const int ix = __float_as_int(x);
+  const int e = (ix - 0x3f3504f3) >> 23;  // m = x / 2^e in [0.70710677, 1.4142135)
+  const float m = __int_as_float(ix - (e << 23));
+  const float s = (m - 1.0f) * rcp_approx(m + 1.0f);
+  const float z = s * s;
+  float p = fmaf(z, 0.11111111f, 0.14285715f);
+  p = fmaf(z, p, 0.2f);
+  p = fmaf(z, p, 0.33333334f);
+  p = fmaf(z, p, 1.0f);
+  const float lm = 2.0f * s * p;
+  const float fe = (float)e;
+  return fmaf(fe, 0.693145752f, fmaf(fe, 1.42860677e-06f, lm));  // ln2 = hi + lo
+}
+
 template <typename Real>
 struct Fn;
 template <>
 struct Fn<float> {
-  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  static __device__ __forceinline__ float log(float x) { return log_fast(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float ninf() { return -CUDART_INF_F; }
+  static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  static __device__ __forceinline__ float ninf() { return -__int_as_float(0x7f800000); }
 };
 template <>
 struct Fn<double> {
   static __device__ __forceinline__ double log(double x) { return ::log(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-  static __device__ __forceinline__ double ninf() { return -CUDART_INF; }
+  static __device__ __forceinline__ double ninf() { return -kInf(); }
 };
 
-// u = log f(x) - off and g_j = d u / d theta_j for one event.  `gm` selects
-// the derivatives that are needed (uniform across the grid).
+// Typed leaves: u = log f(x) - off and g_j = d u / d theta_j.  GM is the
+// compile-time mask of the derivatives that are needed; the others are 0.
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_gauss(Real x, const Real* __restrict__ pc, Real& u,
+                                           Real (&g)[RF_LEAF_MAXP]) {
+  Real d = ((x - pc[0]) - pc[1]) * pc[2];
+  u = Real(-0.5) * d * d;
+  g[0] = (GM & 1) ? d * pc[2] : Real(0);
+  g[1] = (GM & 2) ? d * d * pc[2] : Real(0);
+  g[2] = g[3] = Real(0);
+}
+
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_exp(Real x, const Real* __restrict__ pc, Real& u,
+                                         Real (&g)[RF_LEAF_MAXP]) {
+  Real d = (x - pc[1]) - pc[2];
+  u = pc[0] * d;
+  g[0] = (GM & 1) ? d : Real(0);
+  g[1] = g[2] = g[3] = Real(0);
+}
+
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_cheb(Real x, const Real* __restrict__ pc, Real& u,
+                                          Real (&g)[RF_LEAF_MAXP]) {
+  typedef Fn<Real> F;
+  Real xp = x * pc[0] + pc[1];
+  Real t1 = xp, t2 = Real(2) * xp * t1 - Real(1);
+  Real t3 = Real(2) * xp * t2 - t1, t4 = Real(2) * xp * t3 - t2;
+  Real f = Real(1) + pc[2] * t1 + pc[3] * t2 + pc[4] * t3 + pc[5] * t4;
+  u = F::log(f);
+  if (GM) {
+    Real r = F::rcp(f);
+    g[0] = (GM & 1) ? t1 * r : Real(0);
+    g[1] = (GM & 2) ? t2 * r : Real(0);
+    g[2] = (GM & 4) ? t3 * r : Real(0);
+    g[3] = (GM & 8) ? t4 * r : Real(0);
+  } else {
+    g[0] = g[1] = g[2] = g[3] = Real(0);
+  }
+}
+
+// Crystal Ball: both pieces are evaluated and one is selected (no divergence).
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Real& u,
+                                        Real (&g)[RF_LEAF_MAXP]) {
+  typedef Fn<Real> F;
+  const Real A = pc[4];
+  Real t = ((x - pc[0]) - pc[1]) * pc[2];  // s (x - m0) / sigma
+  bool tail = t <= -A;
+  Real D = Real(1) - pc[5] * (A + t);
+  Real Lg = F::log(D);
+  u = tail ? pc[7] - pc[6] * Lg : Real(-0.5) * t * t;
+  if (GM) {
+    Real rD = F::rcp(D);
+    Real dudt = tail ? A * rD : -t;
+    g[0] = (GM & 1) ? -dudt * pc[2] : Real(0);
+    g[1] = (GM & 2) ? -dudt * t * (pc[3] * pc[2]) : Real(0);
+    g[2] = (GM & 4) ? (tail ? pc[3] * ((Real(2) * A + t) * rD - A) : Real(0)) : Real(0);
+    g[3] = (GM & 8) ? (tail ? (Real(1) - rD) - Lg : Real(0)) : Real(0);
+  } else {
+    g[0] = g[1] = g[2] = g[3] = Real(0);
+  }
+}
+
+// ARGUS, p = 1/2: u = (1/2) log(x^2 tau) + c tau; -inf at and above m0.
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, Real& u,
+                                           Real (&g)[RF_LEAF_MAXP]) {
+  typedef Fn<Real> F;
+  Real dm = (pc[0] - x) + pc[1];
+  Real sm = (pc[0] + x) + pc[1];
+  Real tau = dm * sm * pc[2];
+  bool ok = tau > Real(0);
+  u = ok ? Real(0.5) * F::log(x * x * tau) + pc[3] * tau : F::ninf();
+  g[1] = (GM & 2) ? (ok ? tau : Real(0)) : Real(0);
+  if (GM & 1) {
+    Real r = F::rcp(tau);
+    g[0] = ok ? (Real(0.5) * r + pc[3]) * (Real(1) - tau) * pc[4] : Real(0);
+  } else {
+    g[0] = Real(0);
+  }
+  g[2] = g[3] = Real(0);
+}
+
+// Runtime dispatch (the generic, precompiled model): all derivatives are
+// computed; the accumulation step keeps the ones in the leaf's gmask.
 template <typename Real>
 __device__ __forceinline__ void eval_leaf(int type, int gm, Real x,
                                           const Real* __restrict__ pc, Real& u,
                                           Real (&g)[RF_LEAF_MAXP]) {
-  typedef Fn<Real> F;
-  const Real one = Real(1), half = Real(0.5);
   switch (type) {
-    case RFL_GAUSS: {
-      Real d = ((x - pc[0]) - pc[1]) * pc[2];
-      u = -half * d * d;
-      g[0] = d * pc[2];
-      g[1] = d * d * pc[2];
-      g[2] = g[3] = Real(0);
+    case RFL_GAUSS: leaf_gauss<Real, 3>(x, pc, u, g); break;
+    case RFL_EXP: leaf_exp<Real, 1>(x, pc, u, g); break;
+    case RFL_CHEB: leaf_cheb<Real, 15>(x, pc, u, g); break;
+    case RFL_CB: leaf_cb<Real, 15>(x, pc, u, g); break;
+    case RFL_ARGUS:
+      if (gm & 1) leaf_argus<Real, 3>(x, pc, u, g);
+      else leaf_argus<Real, 2>(x, pc, u, g);
       break;
-    }
-    case RFL_EXP: {
-      Real d = (x - pc[1]) - pc[2];
-      u = pc[0] * d;
-      g[0] = d;
-      g[1] = g[2] = g[3] = Real(0);
-      break;
-    }
-    case RFL_CHEB: {
-      Real xp = x * pc[0] + pc[1];
-      Real t1 = xp, t2 = Real(2) * xp * t1 - one;
-      Real t3 = Real(2) * xp * t2 - t1, t4 = Real(2) * xp * t3 - t2;
-      Real f = one + pc[2] * t1 + pc[3] * t2 + pc[4] * t3 + pc[5] * t4;
-      u = F::log(f);
-      Real r = F::rcp(f);
-      g[0] = t1 * r;
-      g[1] = t2 * r;
-      g[2] = t3 * r;
-      g[3] = t4 * r;
-      break;
-    }
-    case RFL_CB: {
-      // both pieces are evaluated and one is selected (no divergence)
-      Real t = pc[3] * (((x - pc[0]) - pc[1]) * pc[2]);
-      Real A = pc[4];
-      bool tail = t <= -A;
-      Real D = one + pc[5] * (-A - t);
-      Real Lg = F::log(D);
-      Real rD = F::rcp(D);
-      u = tail ? pc[7] - pc[6] * Lg : -half * t * t;
-      Real dudt = tail ? A * rD : -t;
-      g[0] = -dudt * pc[3] * pc[2];
-      g[1] = -dudt * t * pc[2];
-      g[2] = tail ? pc[3] * ((Real(2) * A + t) * rD - A) : Real(0);
-      g[3] = tail ? (one - rD) - Lg : Real(0);
-      break;
-    }
-    case RFL_ARGUS: {
-      Real dm = (pc[0] - x) + pc[1];
-      Real sm = (pc[0] + x) + pc[1];
-      Real tau = dm * sm * pc[2];
-      bool ok = tau > Real(0);
-      Real arg = x * x * tau;
-      u = ok ? half * F::log(arg) + pc[3] * tau : F::ninf();
-      g[1] = ok ? tau : Real(0);
-      if (gm & 1) {
-        Real r = F::rcp(tau);
-        g[0] = ok ? (half * r + pc[3]) * (one - tau) * pc[4] : Real(0);
-      } else {
-        g[0] = Real(0);
-      }
-      g[2] = g[3] = Real(0);
-      break;
-    }
     default:
       u = Real(0);
       g[0] = g[1] = g[2] = g[3] = Real(0);
   }
+}
+
+// log sum_c exp(v_c) with a max shift, and the weights w_c = exp(v_c - ell).
+template <typename Real, int NC>
+__device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
+  typedef Fn<Real> F;
+  if constexpr (NC == 1) {
+    w[0] = Real(1);
+    return v[0];
+  } else if constexpr (NC == 2) {
+    Real dv = v[1] - v[0];
+    Real e = F::exp(-fabs(dv));
+    Real s = Real(1) + e;
+    Real rs = F::rcp(s);
+    Real wb = rs, ws = e * rs;
+    w[0] = dv > Real(0) ? ws : wb;
+    w[1] = dv > Real(0) ? wb : ws;
+    return fmax(v[0], v[1]) + F::log(s);
+  } else {
+    Real m = v[0];
+#pragma unroll
+    for (int c = 1; c < NC; ++c) m = fmax(m, v[c]);
+    Real s = Real(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      w[c] = F::exp(v[c] - m);
+      s += w[c];
+    }
+    Real rs = F::rcp(s);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) w[c] *= rs;
+    return m + F::log(s);
+  }
+}
+
+// What component c contributes to its accumulator: w_c, or P_c/P when its
+// coefficient is exactly 0 (vnc = delta_nc_c + sum of the component's u).
+template <typename Real>
+__device__ __forceinline__ Real comp_weight(int zero_mask, int c, Real vnc, Real ell, Real wc) {
+  if ((zero_mask >> c) & 1) return Fn<Real>::exp(vnc - ell);
+  return wc;
 }
 
 // Per-event constants copied from shared memory into registers.
@@ -442,203 +543,6 @@ struct EvalConsts {
     zero_mask = K.zero_mask;
   }
 };
-
-// One event: leaves -> components -> log-sum-exp -> adjoint weights, added
-// into the iteration partials q (NACC = RF_NACC(NL)).
-template <typename Real, int NL>
-__device__ __forceinline__ void event_accumulate(const RfProgram& P,
-                                                 const EvalConsts<Real, NL>& K,
-                                                 const Real (&xc)[NL],
-                                                 Real (&q)[RF_NACC(NL)]) {
-  typedef Fn<Real> F;
-  Real u[NL], g[NL][RF_LEAF_MAXP];
-#pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int col = P.leaf[k].col;
-    Real x = xc[0];
-#pragma unroll
-    for (int c = 1; c < NL; ++c)
-      if (col == c) x = xc[c];
-    eval_leaf<Real>(P.leaf[k].type, P.leaf[k].gmask, x, K.pc[k], u[k], g[k]);
-  }
-  Real v[NL], w[NL];
-#pragma unroll
-  for (int c = 0; c < NL; ++c) {
-    v[c] = K.delta[c];
-#pragma unroll
-    for (int k = 0; k < NL; ++k)
-      if (P.leaf[k].comp == c) v[c] += u[k];
-    w[c] = Real(0);
-  }
-  Real ell;
-  const int C = P.n_comp;
-  if (C == 1) {
-    ell = v[0];
-    w[0] = Real(1);
-  } else if (NL >= 2 && C == 2) {
-    Real dv = v[1] - v[0];
-    Real e = F::exp(-fabs(dv));
-    Real s = Real(1) + e;
-    Real rs = F::rcp(s);
-    ell = fmax(v[0], v[1]) + F::log(s);
-    Real wb = rs, ws = e * rs;
-    w[0] = dv > Real(0) ? ws : wb;
-    w[1] = dv > Real(0) ? wb : ws;
-  } else {
-    Real m = v[0];
-#pragma unroll
-    for (int c = 1; c < NL; ++c)
-      if (c < C) m = fmax(m, v[c]);
-    Real s = Real(0);
-#pragma unroll
-    for (int c = 0; c < NL; ++c) {
-      w[c] = (c < C) ? F::exp(v[c] - m) : Real(0);
-      s += w[c];
-    }
-    ell = m + F::log(s);
-    Real rs = F::rcp(s);
-#pragma unroll
-    for (int c = 0; c < NL; ++c) w[c] *= rs;
-  }
-  q[0] += ell;
-  if (K.zero_mask == 0) {
-#pragma unroll
-    for (int c = 0; c < NL; ++c) q[1 + c] += w[c];
-  } else {
-    // a component with coefficient exactly 0: accumulate P_c/P instead
-#pragma unroll
-    for (int c = 0; c < NL; ++c) {
-      if ((K.zero_mask >> c) & 1) {
-        Real vc = K.delta_nc[c];
-#pragma unroll
-        for (int k = 0; k < NL; ++k)
-          if (P.leaf[k].comp == c) vc += u[k];
-        q[1 + c] += F::exp(vc - ell);
-      } else {
-        q[1 + c] += w[c];
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    const int comp = P.leaf[k].comp;
-    Real wk = w[0];
-#pragma unroll
-    for (int c = 1; c < NL; ++c)
-      if (comp == c) wk = w[c];
-    const int gm = P.leaf[k].gmask;
-#pragma unroll
-    for (int j = 0; j < RF_LEAF_MAXP; ++j)
-      if ((gm >> j) & 1) q[1 + NL + k * RF_LEAF_MAXP + j] += wk * g[k][j];
-  }
-}
-
-// ---------------------------------------------------------- event loading
-template <typename Col>
-struct Vec;
-template <>
-struct Vec<float> {
-  static constexpr int W = 4;
-  typedef float4 T;
-};
-template <>
-struct Vec<double> {
-  static constexpr int W = 2;
-  typedef double2 T;
-};
-
-template <typename Real, typename Col, int NL, int EPT>
-__device__ __forceinline__ void load_full(const RfProgram& P,
-                                          const Col* __restrict__ ev,
-                                          int64_t stride, int64_t i0, bool vec,
-                                          Real (&x)[NL][EPT]) {
-  constexpr int W = Vec<Col>::W;
-  static_assert(EPT % W == 0, "EPT must be a multiple of the vector width");
-#pragma unroll
-  for (int c = 0; c < NL; ++c) {
-    if (c < P.n_cols) {
-      const Col* col = ev + (int64_t)P.col_obs[c] * stride + i0;
-      if (vec) {
-        const typename Vec<Col>::T* vp = reinterpret_cast<const typename Vec<Col>::T*>(col);
-#pragma unroll
-        for (int v = 0; v < EPT / W; ++v) {
-          typename Vec<Col>::T t = __ldg(vp + v);
-          const Col* tc = reinterpret_cast<const Col*>(&t);
-#pragma unroll
-          for (int e = 0; e < W; ++e) x[c][v * W + e] = (Real)tc[e];
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) x[c][e] = (Real)__ldg(col + e);
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) x[c][e] = Real(0);
-    }
-  }
-}
-
-// Kahan-compensated running sums (value = s - c)
-template <typename Real, int N>
-struct Acc {
-  Real s[N], c[N];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = c[i] = Real(0);
-  }
-  __device__ __forceinline__ void add(const Real (&q)[N]) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      Real y = q[i] - c[i];
-      Real t = s[i] + y;
-      c[i] = (t - s[i]) - y;
-      s[i] = t;
-    }
-  }
-};
-
-// Full iteration: EPT consecutive events starting at i0 (all valid).
-template <typename Real, typename Col, int NL, int EPT>
-__device__ __forceinline__ void iterate_full(const RfProgram& P,
-                                             const EvalConsts<Real, NL>& K,
-                                             const Col* __restrict__ ev,
-                                             int64_t stride, int64_t i0,
-                                             bool vec,
-                                             Acc<Real, RF_NACC(NL)>& acc) {
-  Real x[NL][EPT];
-  load_full<Real, Col, NL, EPT>(P, ev, stride, i0, vec, x);
-  Real q[RF_NACC(NL)];
-#pragma unroll
-  for (int i = 0; i < RF_NACC(NL); ++i) q[i] = Real(0);
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    Real xc[NL];
-#pragma unroll
-    for (int c = 0; c < NL; ++c) xc[c] = x[c][e];
-    event_accumulate<Real, NL>(P, K, xc, q);
-  }
-  acc.add(q);
-}
-
-// Events [i0, i1) with scalar loads, one at a time (heads and tails).
-template <typename Real, typename Col, int NL>
-__device__ inline void iterate_scalar(const RfProgram& P,
-                                      const EvalConsts<Real, NL>& K,
-                                      const Col* __restrict__ ev,
-                                      int64_t stride, int64_t i0, int64_t i1,
-                                      Acc<Real, RF_NACC(NL)>& acc) {
-  for (int64_t i = i0; i < i1; ++i) {
-    Real xc[NL];
-#pragma unroll
-    for (int c = 0; c < NL; ++c)
-      xc[c] = (c < P.n_cols) ? (Real)ev[(int64_t)P.col_obs[c] * stride + i] : Real(0);
-    Real q[RF_NACC(NL)];
-#pragma unroll
-    for (int j = 0; j < RF_NACC(NL); ++j) q[j] = Real(0);
-    event_accumulate<Real, NL>(P, K, xc, q);
-    acc.add(q);
-  }
-}
 
 // --------------------------------------------------------------- reduction
 __device__ __forceinline__ double warp_sum(double v) {
@@ -696,7 +600,7 @@ __device__ inline void rows_sum(const double* partials, int64_t r0, int64_t r1,
 // ---------------------------------------------------------------- epilogue
 // T: FP64 totals of the accumulators, n: events.  Writes NLL and gradient.
 template <typename Real, int NL>
-__device__ inline void epilogue(const RfProgram& P, const RfConsts<Real>& K,
+__device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& K,
                                 const double* T, int64_t n, double* nll,
                                 double* grad, unsigned int* status) {
   const int C = P.n_comp;
@@ -731,11 +635,11 @@ __device__ inline void epilogue(const RfProgram& P, const RfConsts<Real>& K,
     for (int p = 0; p < P.n_par; ++p) {
       bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
       if (fx) grad[p] = 0.0;
-      if (bad) grad[p] = CUDART_NAN;
+      if (bad) grad[p] = kNaN();
     }
   }
   if (bad) {
-    v = CUDART_INF;
+    v = kInf();
     if (status)
       atomicOr(status, K.bad ? (unsigned)RF_STATUS_PARAM_DOMAIN_BIT
                              : (unsigned)RF_STATUS_NONFINITE_BIT);

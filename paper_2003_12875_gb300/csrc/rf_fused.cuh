@@ -1,106 +1,28 @@
-// rf_fused.cuh -- the fused single-dataset kernel: FP64 prologue (leaf
+// rf_fused.cuh -- the precompiled (generic-model) single-dataset kernels and
+// their host-side launch helpers.  The fused kernel: FP64 prologue (leaf
 // normalisations and coefficients, once per block), a grid-stride loop over
 // the events with 128-bit coalesced loads of the SoA columns, the per-event
 // log-density and adjoint in registers, compensated per-thread sums, and a
 // deterministic FP64 reduction finished by the last block to arrive, which
 // writes the NLL and its gradient.  One launch per call; no host sync.
 #pragma once
-#include "rf_device.cuh"
+#include "rf_kernels.cuh"
 
 namespace rf {
-
-// Prologue run by every block: leaf k by lane 0 of warp k (their FP64 work
-// proceeds in parallel), then the combination by thread 0.
-template <typename Real>
-__device__ inline void block_prologue(const RfProgram& P, const double* params,
-                                      RfConsts<Real>& K, double* lnI, int* ok) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int k = wid; k < P.n_leaves; k += nw)
-    if (lane == 0) ok[k] = leaf_consts(P, params, K, k, &lnI[k]) ? 1 : 0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool all = true;
-    for (int k = 0; k < P.n_leaves; ++k) all &= ok[k] != 0;
-    comb_consts(P, params, K, lnI, all);
-  }
-  __syncthreads();
-}
 
 template <typename Real, typename Col, int NL, int EPT>
 __global__ void __launch_bounds__(256)
     fused_nll_kernel(const RfProgram P, const Col* __restrict__ ev, int64_t n,
                      int64_t head, int vec, const double* __restrict__ params,
                      RfWork W, double* nll, double* grad) {
-  constexpr int NA = RF_NACC(NL);
-  __shared__ RfConsts<Real> K;
-  __shared__ double lnI[RF_MAXL];
-  __shared__ int ok[RF_MAXL];
-  __shared__ double red[32 * NA];
-  __shared__ double tot[NA];
-  __shared__ int s_last;
-
-  block_prologue(P, params, K, lnI, ok);
-
-  Acc<Real, NA> acc;
-  acc.zero();
-  if (!K.bad) {
-    EvalConsts<Real, NL> E;
-    E.load(K);
-    const int64_t h = head < n ? head : n;
-    const int64_t nfull = (n - h) / EPT;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nfull; ch += gsz)
-      iterate_full<Real, Col, NL, EPT>(P, E, ev, n, h + ch * EPT, vec != 0, acc);
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
-      iterate_scalar<Real, Col, NL>(P, E, ev, n, 0, h, acc);
-      iterate_scalar<Real, Col, NL>(P, E, ev, n, h + nfull * EPT, n, acc);
-    }
-  }
-
-  double val[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) val[i] = (double)acc.s[i] - (double)acc.c[i];
-  block_sum<NA>(val, red, tot);
-  if (threadIdx.x < NA) W.partials[(int64_t)blockIdx.x * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(W.counter, 1u) == gridDim.x - 1) ? 1 : 0;
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    rows_sum<NA>(W.partials, 0, gridDim.x, red, tot);
-    if (threadIdx.x == 0) {
-      epilogue<Real, NL>(P, K, tot, n, nll, grad, W.status);
-      *W.counter = 0u;
-    }
-  }
+  fused_body<GenericModel<NL>, Real, Col, EPT>(P, ev, n, head, vec, params, W, nll, grad);
 }
 
-// Per-event log P(x_i) = beta_ref + ell_i (FP64 output), one event per thread.
 template <typename Real, typename Col, int NL>
 __global__ void __launch_bounds__(256)
     logp_kernel(const RfProgram P, const Col* __restrict__ ev, int64_t n,
                 const double* __restrict__ params, double* logp) {
-  constexpr int NA = RF_NACC(NL);
-  __shared__ RfConsts<Real> K;
-  __shared__ double lnI[RF_MAXL];
-  __shared__ int ok[RF_MAXL];
-  block_prologue(P, params, K, lnI, ok);
-  EvalConsts<Real, NL> E;
-  E.load(K);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    Real xc[NL];
-#pragma unroll
-    for (int c = 0; c < NL; ++c)
-      xc[c] = (c < P.n_cols) ? (Real)ev[(int64_t)P.col_obs[c] * n + i] : Real(0);
-    Real q[NA];
-#pragma unroll
-    for (int j = 0; j < NA; ++j) q[j] = Real(0);
-    event_accumulate<Real, NL>(P, E, xc, q);
-    logp[i] = K.bad ? CUDART_NAN : K.beta_ref + (double)q[0];
-  }
+  logp_body<GenericModel<NL>, Real, Col>(P, ev, n, params, logp);
 }
 
 // Vector path if every column read shares one 16-byte phase; head = events

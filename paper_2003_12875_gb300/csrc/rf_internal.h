@@ -11,7 +11,16 @@
 //   ell   = log sum_c exp(v_c),  log P = beta_ref + ell
 // so the NLL is -(n beta_ref + sum_i ell_i) (+ sum of yields if extended).
 #pragma once
+#ifdef __CUDACC_RTC__
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef unsigned long long uintptr_t;
+#else
+#include <stddef.h>
 #include <stdint.h>
+#endif
 
 #define RF_MAXL 4        // leaves per compiled graph
 #define RF_MAXC 4        // components (Add children)
@@ -91,6 +100,7 @@ struct RfLaunchCfg {
   int tile;
 };
 
+#ifndef __CUDACC_RTC__
 // ---- launchers (defined in the .cu files) -------------------------------
 // All return a cudaError_t value (0 = success).  `stream` is a cudaStream_t.
 typedef struct CUstream_st* rf_cuda_stream;
@@ -112,11 +122,40 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       int64_t n_events, const int64_t* offsets, int32_t toys,
                       double* pm, double* out, RfWork W,
                       const double* adam_scale, double adam_lr, bool plan,
-                      int64_t max_rows, void* stream, int* launches);
+                      int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
+                      int* launches);
 int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
                     int64_t n, const double* params, double* node_buf,
                     double* nll, double* grad, double* partials,
                     unsigned int* counter, void* stream, int* launches);
 size_t rf_plain_bytes(const RfProgram& prog, int64_t n);
 int rf_run_microbench(double* out8);
+int rf_run_check_log(const float* x, float* y_fast, float* y_ref, int64_t n, rf_cuda_stream st);
 size_t rf_consts_size(int eval);
+
+// vector-load plan shared by the generic and specialised launchers
+// (rf_launch.cpp): vec = every column read starts at the same 16-byte phase;
+// head = events before the first aligned one.
+void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int elem_bytes,
+                 int* vec, int64_t* head);
+
+// per-graph specialised kernels (jit.cpp)
+#include <string>
+enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2 };
+typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
+std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept);
+bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                         std::string* err);
+rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                             int* regs, std::string* err);
+int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
+                        int num_sms, const void* events, int64_t n, const double* params,
+                        RfWork W, double* nll, double* grad, rf_cuda_stream st);
+int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
+                       int num_sms, const void* events, int64_t n_events,
+                       const int64_t* offsets, int32_t toys, double* pm, double* out,
+                       RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
+                       rf_cuda_stream st);
+int rf_jit_launch_logp(rf_cuda_kernel k, const RfProgram& P, const void* events, int64_t n,
+                       const double* params, double* logp, rf_cuda_stream st);
+#endif  // __CUDACC_RTC__

@@ -109,3 +109,14 @@ def test_unsupported_shapes(rf):
     s["nodes"].append({"type": "add_frac", "children": [2, 0], "params": [3]})
     s["root"] = 3
     assert rf.validate(s) == EUNSUPPORTED
+
+
+@pytest.mark.parametrize("make,dt,prec", [(lambda: datagen.c5(5, 50), "f32", "fp32"),
+                                          (lambda: datagen.c3(n=10), "f32", "fp32"),
+                                          (lambda: datagen.c2(n=10), "f64", "fp64")])
+def test_specialised_kernels_compile_without_gpu(rf, make, dt, prec):
+    """rf_graph_compile's per-graph kernels (fused, toy tile, log P) compile
+    with NVRTC for sm_103a; no device is needed for this step."""
+    w = make()
+    rc = rf.jit_check(w["spec"], dt, prec)
+    assert rc == 0, rf.load().rf_last_error().decode()[:2000]
