@@ -106,23 +106,26 @@ struct Canon {
   RfProgram prog;
 };
 
-// Map the descriptor onto the sum-of-products program.
+// Map the descriptor onto the sum-of-products program (fixed-size arrays
+// only: no heap allocation on the success path).
 rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
   std::memset(P, 0, sizeof(*P));
   const rf_node_desc& root = d->nodes[d->root];
-  std::vector<std::vector<int>> comps;  // leaf node ids per component
-  auto leaves_of = [&](int id, std::vector<int>* out) -> rf_status {
+  int comp_leaf[RF_MAX_CHILDREN][RF_MAX_CHILDREN];  // leaf node ids per component
+  int comp_n[RF_MAX_CHILDREN] = {0};
+  int n_comps = 0;
+  auto leaves_of = [&](int id, int c) -> rf_status {
     const rf_node_desc& n = d->nodes[id];
     if (is_leaf(n.type)) {
-      out->push_back(id);
+      comp_leaf[c][comp_n[c]++] = id;
       return RF_OK;
     }
     if (n.type == RF_PROD) {
       for (int k = 0; k < n.n_children; ++k) {
-        const rf_node_desc& c = d->nodes[n.children[k]];
-        if (!is_leaf(c.type))
+        const rf_node_desc& ch = d->nodes[n.children[k]];
+        if (!is_leaf(ch.type))
           return fail(RF_EUNSUPPORTED, "a PROD child must be a leaf on the GPU path");
-        out->push_back(n.children[k]);
+        comp_leaf[c][comp_n[c]++] = n.children[k];
       }
       return RF_OK;
     }
@@ -130,24 +133,23 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
   };
   int kind = RF_KIND_PROD;
   if (is_leaf(root.type) || root.type == RF_PROD) {
-    comps.emplace_back();
-    rf_status s = leaves_of(d->root, &comps.back());
+    rf_status s = leaves_of(d->root, n_comps++);
     if (s) return s;
   } else {
     kind = root.type == RF_ADD_FRAC ? RF_KIND_FRAC : RF_KIND_EXT;
     for (int k = 0; k < root.n_children; ++k) {
-      comps.emplace_back();
-      rf_status s = leaves_of(root.children[k], &comps.back());
+      rf_status s = leaves_of(root.children[k], n_comps++);
       if (s) return s;
     }
-    for (int j = 0; j < root.n_params; ++j) P->coef_par[j] = root.params[j];
+    if (n_comps <= RF_MAXC)
+      for (int j = 0; j < root.n_params; ++j) P->coef_par[j] = root.params[j];
   }
   int nl = 0;
-  for (auto& c : comps) nl += (int)c.size();
-  if ((int)comps.size() > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 4 components");
+  for (int c = 0; c < n_comps; ++c) nl += comp_n[c];
+  if (n_comps > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 4 components");
   if (nl > RF_MAXL) return fail(RF_EUNSUPPORTED, "more than 4 leaves");
   P->n_leaves = nl;
-  P->n_comp = (int)comps.size();
+  P->n_comp = n_comps;
   P->kind = kind;
   P->n_par = d->n_params;
   auto fixed = [&](int p) { return d->param_fixed && d->param_fixed[p]; };
@@ -165,9 +167,9 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
   int k = 0;
   for (int c = 0; c < P->n_comp; ++c) {
     uint64_t comp_obs = 0;
-    for (int id : comps[c]) {
-      const rf_node_desc& n = d->nodes[id];
-      if (comps[c].size() > 1) {
+    for (int li = 0; li < comp_n[c]; ++li) {
+      const rf_node_desc& n = d->nodes[comp_leaf[c][li]];
+      if (comp_n[c] > 1) {
         if (comp_obs & (1ull << n.obs))
           return fail(RF_EUNSUPPORTED, "PROD children must use disjoint observables");
         comp_obs |= 1ull << n.obs;
