@@ -210,6 +210,30 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events,
                         const double* params, rf_stream stream,
                         double* best_ms);
 
+/* NLL and gradient for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Some callers cannot call cudaMalloc at all --
+ * code in a host callback or driver hook, a real-time loop whose allocator
+ * is frozen after start-up, a host whose device memory pool belongs to
+ * another framework -- so they cannot build an rf_graph, whose compile step
+ * allocates its workspace.  This entry point takes the descriptor directly
+ * and runs the precompiled generic fused kernel with its scratch (per-block
+ * partial sums, block ticket, status word) in a file-scope static device
+ * array of the library: about 172 KB, enough for the partial sums of
+ * blocks <= 1024 (0 = twice the SM count, capped at 1024; larger values
+ * return RF_EINVAL).  Every GPU that loads the library holds that array until
+ * the process exits.  It allocates nothing: no cudaMalloc/cudaFree and no
+ * allocating library routine.  Its first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents: the ticket and status words
+ * are cleared on `stream` at the start of each call, and calls that overlap
+ * on the GPU race on the array.  Arguments, layout and results as rf_nll
+ * (events, params, nll, grad are caller-owned device memory); domain errors
+ * give NLL = +inf and a NaN gradient (the status word is not reported). */
+rf_status rf_nll_noalloc(const rf_graph_desc* desc, const void* events,
+                         int64_t n_events, const double* params, double* nll,
+                         double* grad, int32_t blocks, rf_stream stream);
+
 /* Kernel specialisation.  rf_graph_compile also emits, for its graph, a
  * model in which the leaf types, columns, component sums and gradient masks
  * are compile-time constants, and compiles the fused, toy and log P kernels

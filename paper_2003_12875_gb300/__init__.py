@@ -69,7 +69,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_fit_toys", "rf_nll_plain", "rf_graph_get_launch", "rf_graph_set_launch",
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
-           "rf_jit_check", "rf_check_log"]
+           "rf_jit_check", "rf_check_log", "rf_nll_noalloc"]
 
 
 def lib_path() -> str:
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         L.rf_graph_kernel_regs.restype = i32
         L.rf_jit_check.argtypes = [C.POINTER(_Desc)]
         L.rf_check_log.argtypes = [vp, vp, vp, i64, vp]
+        L.rf_nll_noalloc.argtypes = [C.POINTER(_Desc), vp, i64, vp, vp, vp, i32, vp]
         for name in SYMBOLS:
             if name not in ("rf_last_error", "rf_graph_last_launches", "rf_graph_uses_jit",
                             "rf_graph_kernel_regs"):
@@ -173,6 +174,18 @@ def jit_check(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64
     """NVRTC-compile the graph's specialised kernels without a GPU; 0 = OK."""
     d, keep = make_desc(spec, column_dtype, eval_precision)
     return load().rf_jit_check(C.byref(d))
+
+
+def nll_noalloc(spec: dict, events: torch.Tensor, params: torch.Tensor, out: torch.Tensor,
+                column_dtype: str = "f64", eval_precision: str = "fp64", blocks: int = 0):
+    """rf_nll_noalloc: NLL and gradient with no device allocation by the
+    library (its scratch is a static device array).  `out` is a caller-owned
+    CUDA float64 tensor [1 + n_params]: out[0] = NLL, out[1:] = gradient."""
+    d, keep = make_desc(spec, column_dtype, eval_precision)
+    n = events.shape[-1] if events.dim() == 2 else events.numel()
+    _check(load().rf_nll_noalloc(C.byref(d), _ptr(events), int(n), _ptr(params), _ptr(out),
+                                 C.c_void_p(out.data_ptr() + 8), int(blocks), _stream()))
+    return out
 
 
 def check_log(x: torch.Tensor):

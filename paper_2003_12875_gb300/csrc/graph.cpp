@@ -278,6 +278,16 @@ static void free_work(rf_graph* g) {
   if (g->fit_stream) cudaStreamDestroy(g->fit_stream);
 }
 
+// For other translation units of the library (noalloc.cu): validation plus
+// canonicalisation of a descriptor, and setting the thread's error message.
+rf_status rf_canonical_program(const rf_graph_desc* desc, RfProgram* P) {
+  rf_status s = validate_desc(desc);
+  if (s) return s;
+  return canonicalise(desc, P);
+}
+
+void rf_set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* rf_last_error(void) { return g_err.c_str(); }

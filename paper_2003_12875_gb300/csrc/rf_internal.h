@@ -30,6 +30,8 @@ typedef unsigned long long uintptr_t;
 // per-thread accumulators: ell, one per component, one per (leaf, leaf param)
 #define RF_NACC(NL) (1 + (NL) + (NL) * RF_LEAF_MAXP)
 #define RF_NACC_MAX RF_NACC(RF_MAXL)
+// blocks whose partial sums fit the static scratch of rf_nll_noalloc
+#define RF_NOALLOC_MAX_BLOCKS 1024
 
 enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 // device status bits (same values as RF_STATUS_* in include/rf.h)
