@@ -121,6 +121,110 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
     return cols.shape[1] / dt, cores, dt
 
 
+# FP32-pipe instructions per event of the fused kernel's formulation, by piece
+# (derived op by op from the formulas; the table is in DESIGN.md, "Roofline").
+# leaf type -> (base, extra per wanted derivative by leaf-parameter index,
+#               shared extra when any derivative is wanted)
+LEAF_INSTR = {
+    "gauss": (5, {0: 1, 1: 2}, 0),
+    "exp": (3, {0: 0}, 0),
+    "cheb": (34, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
+    "cb": (30, {0: 1, 1: 2, 2: 4, 3: 3}, 3),
+    "argus": (35, {0: 5, 1: 1}, 0),
+}
+
+
+def algorithmic_instr_per_event(spec: dict, ept: int) -> float:
+    nodes = spec["nodes"]
+    fixed = spec.get("fixed") or [False] * len(spec["params"])
+    leaves = [nd for nd in nodes if nd["type"] in LEAF_INSTR]
+    root = nodes[spec.get("root", len(nodes) - 1)]
+    nc = len(root["children"]) if root["type"] in ("add_frac", "add_ext") else 1
+    total, free = 0.0, 0
+    for lf in leaves:
+        base, per, shared = LEAF_INSTR[lf["type"]]
+        wanted = [j for j, p in enumerate(lf["params"]) if not fixed[p] and j in per]
+        total += base + (shared if wanted else 0) + sum(per[j] for j in wanted)
+        free += len(wanted)
+    total += len(leaves)                      # component sums delta_c + sum u_k
+    if nc == 2:
+        total += 34                           # two-term log-sum-exp and weights
+    elif nc > 2:
+        total += 12 * nc + 25
+    total += 1 + (nc if nc > 1 else 1) + free + (2 if nc > 1 else 0)   # adjoint sums
+    total += 4.0 * (1 + nc + free) / ept      # compensated per-iteration sums
+    total += 1                                # loads and loop
+    return total
+
+
+def profiled_traffic(kernel_hash: str):
+    """DRAM bytes per launch from a committed ncu summary taken on exactly this
+    kernel (matched by its source hash), else None."""
+    import glob
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and line.strip().split("=")[0].strip() in (
+                        "kernel_hash", "dram_bytes_per_launch"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_hash") == kernel_hash and "dram_bytes_per_launch" in kv:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The slowest rank's value (every rank gets it); x itself on one rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(events_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job events/s: every rank (an independent replica on its own GPU)
+    processes events_per_rank per step; the step time is the slowest rank's."""
+    return world * events_per_rank / (ms_per_step * 1e-3)
+
+
+def toy_study(rf, torch, toys=4096, iters=50):
+    """Toy NLLs/s: 4096 extended Gauss+Exp toys (about 1.3e8 FP64 events), one
+    batched evaluation and a 50-iteration Adam fit replayed from a CUDA graph,
+    FP32 and FP64 per-event arithmetic."""
+    import numpy as np
+
+    import datagen
+    w = datagen.c4(toys=toys)
+    ev = torch.from_numpy(w["cols"]).cuda()
+    off = torch.from_numpy(w["offsets"]).cuda()
+    res = {"toys": toys, "events": int(w["offsets"][-1]), "iters": iters}
+    for prec in ("fp32", "fp64"):
+        G = rf.Graph(w["spec"], "f64", prec)
+        G.bind_events(ev, toys)
+        pm = torch.from_numpy(w["params_matrix"]).cuda()
+        G.nll_batched(off, pm)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            G.nll_batched(off, pm)
+        b.record()
+        torch.cuda.synchronize()
+        t_eval = a.elapsed_time(b) / 5
+        scale = torch.from_numpy(np.maximum(np.abs(w["params_matrix"]), 1.0)).cuda()
+        t0 = time.perf_counter()
+        G.fit_toys(off, pm, scale, iters, 1e-2)
+        t_fit = (time.perf_counter() - t0) * 1e3
+        res[prec] = {"eval_ms": t_eval, "toy_nll_per_s": toys / (t_eval * 1e-3),
+                     "events_per_s": res["events"] / (t_eval * 1e-3),
+                     "fit_ms": t_fit, "fit_toy_iters_per_s": toys * iters / (t_fit * 1e-3),
+                     "launches_per_fit": G.last_launches(), "kernel": G.uses_jit()}
+    return res
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -237,12 +341,9 @@ def main():
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     per_launch = statistics.mean(launch_ms)
     launches_per_step = G.last_launches()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step * 1e-3)
+    value = job_throughput(n, world, ms_per_step)
     nll_value = float(out[0].item())
 
     # -------------------------------------------------------------- e2e
@@ -260,12 +361,32 @@ def main():
            "ms_per_step": e2e_s * 1e3}
 
     # ----------------------------------------------------------- roofline
+    # The fused FP32-eval kernel is bound by instruction issue (transcendentals
+    # and selects per event), not by HBM: report it against the FP32 issue
+    # peak of the chip (SMs x 128 lanes x max SM clock), with the HBM figure
+    # beside it.  per_launch spans the whole call (prologue + fused kernel).
     bytes_per_launch = n * w["cols"].shape[0] * col_bytes
-    achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "peak_source": pk["source"], "kernel": "fused_nll_kernel",
-                "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch}
+    hbm_achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    launch_cfg = G.get_launch()
+    traffic = profiled_traffic(G.kernel_hash()) if G.uses_jit() else None
+    hbm = {"achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": hbm_achieved / pk["hbm_gbs"], "peak_source": pk["source"],
+           "bytes_per_launch": bytes_per_launch}
+    if args.precision == "fp32":
+        instr = algorithmic_instr_per_event(spec, launch_cfg["ept"])
+        peak = sms * 128 * sm_mhz * 1e6
+        achieved = instr * n / (per_launch * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                    "unit": "G FP32-lane instr/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": "rf_fused_jit (+ prologue)",
+                    "algorithmic_instr_per_event": instr,
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                    "launch_ms": per_launch, "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", **hbm, "traffic": traffic, "kernel": "rf_fused_jit",
+                    "launch_ms": per_launch}
 
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -318,6 +439,7 @@ def main():
         torch.cuda.synchronize()
         ex["plain_fp64_nll_only_ms"] = a.elapsed_time(b)
         ex["microbench_ops_per_s"] = rf.microbench()
+        ex["toys"] = toy_study(rf, torch)
         line["extras"] = ex
 
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -249,6 +249,10 @@ rf_status rf_graph_set_jit(rf_graph* g, int32_t enable);
  * them (no GPU needed): RF_OK, or RF_ECUDA with the compiler log. */
 rf_status rf_jit_check(const rf_graph_desc* desc);
 int32_t rf_graph_uses_jit(const rf_graph* g);
+/* FNV-1a hash of the specialised fused kernel's source for the current
+ * launch configuration (0 for the generic kernels): identifies the exact
+ * kernel a profile was taken on. */
+uint64_t rf_graph_kernel_hash(const rf_graph* g);
 int32_t rf_graph_kernel_regs(const rf_graph* g);
 
 /* Synchronises the device, returns the OR of RF_STATUS_* bits raised since
@@ -269,9 +273,11 @@ rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
 /* Throughput of single operations on this GPU, in operations per second,
  * measured by dedicated kernels (used for the compute roofline):
  * out[0] FP32 FMA, out[1] expf, out[2] logf, out[3] FP32 reciprocal (IEEE),
- * out[4] FP64 FMA, out[5] exp (FP64), out[6] log (FP64), out[7] erf (FP64).
+ * out[4] FP64 FMA, out[5] exp (FP64), out[6] log (FP64), out[7] erf (FP64),
+ * out[8] the library's FP32 log, out[9] its FP32 exp(-x) (x >= 0),
+ * out[10] the approximate FP32 reciprocal.  out has 11 entries.
  * Host-synchronous; allocates a small scratch buffer. */
-rf_status rf_microbench(double* out8);
+rf_status rf_microbench(double* out);
 
 #ifdef __cplusplus
 }

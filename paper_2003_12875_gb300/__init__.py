@@ -69,7 +69,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_fit_toys", "rf_nll_plain", "rf_graph_get_launch", "rf_graph_set_launch",
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
-           "rf_jit_check", "rf_check_log", "rf_nll_noalloc"]
+           "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash"]
 
 
 def lib_path() -> str:
@@ -116,9 +116,11 @@ def load(build_if_missing: bool = True):
         L.rf_jit_check.argtypes = [C.POINTER(_Desc)]
         L.rf_check_log.argtypes = [vp, vp, vp, i64, vp]
         L.rf_nll_noalloc.argtypes = [C.POINTER(_Desc), vp, i64, vp, vp, vp, i32, vp]
+        L.rf_graph_kernel_hash.argtypes = [vp]
+        L.rf_graph_kernel_hash.restype = C.c_uint64
         for name in SYMBOLS:
             if name not in ("rf_last_error", "rf_graph_last_launches", "rf_graph_uses_jit",
-                            "rf_graph_kernel_regs"):
+                            "rf_graph_kernel_regs", "rf_graph_kernel_hash"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -351,6 +353,9 @@ class Graph:
     def kernel_regs(self) -> int:
         return int(load().rf_graph_kernel_regs(self._h))
 
+    def kernel_hash(self) -> str:
+        return f"{int(load().rf_graph_kernel_hash(self._h)):016x}"
+
 
 class RFNll(torch.autograd.Function):
     """NLL as a differentiable function of the parameter tensor: the forward
@@ -371,7 +376,8 @@ class RFNll(torch.autograd.Function):
 
 def microbench() -> dict:
     """Measured per-operation throughput (operations/s) on the current GPU."""
-    out = (C.c_double * 8)()
+    out = (C.c_double * 11)()
     _check(load().rf_microbench(out))
-    keys = ["fp32_fma", "expf", "logf", "rcp_f32", "fp64_fma", "exp_f64", "log_f64", "erf_f64"]
+    keys = ["fp32_fma", "expf", "logf", "rcp_f32", "fp64_fma", "exp_f64", "log_f64", "erf_f64",
+            "log_fast_f32", "exp_neg_f32", "rcp_approx_f32"]
     return dict(zip(keys, list(out)))

@@ -233,6 +233,7 @@ struct rf_graph {
   double* plain_partials = nullptr;
   unsigned int* plain_counter = nullptr;
   cudaStream_t fit_stream = nullptr;
+  void* pro_buf = nullptr;
   int last_launches = 0;
   // per-graph specialised kernels (NVRTC), by events per thread (index 0 or
   // 1 of the precision's two options); compiled on first need
@@ -276,6 +277,7 @@ static void free_work(rf_graph* g) {
   cudaFree(g->plain_buf);
   cudaFree(g->plain_partials);
   if (g->fit_stream) cudaStreamDestroy(g->fit_stream);
+  cudaFree(g->pro_buf);
 }
 
 // For other translation units of the library (noalloc.cu): validation plus
@@ -333,6 +335,18 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   }
   g->work.status = g->work.counter + 1;
   g->work.next_tile = g->work.counter + 2;
+  g->work.pro_ticket = g->work.counter + 3;
+  // constants of the separate prologue kernel
+  e = cudaMalloc(&g->pro_buf, rf_consts_size(g->eval) + sizeof(double) * RF_MAXL +
+                                  sizeof(int) * RF_MAXL + 64);
+  if (e != cudaSuccess) {
+    free_work(g);
+    delete g;
+    return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
+  }
+  g->work.consts = g->pro_buf;
+  g->work.pro_lnI = reinterpret_cast<double*>(static_cast<char*>(g->pro_buf) + rf_consts_size(g->eval));
+  g->work.pro_ok = reinterpret_cast<int*>(g->work.pro_lnI + RF_MAXL);
   // Specialise the fused kernel for this graph unless RF_JIT=0.  If that is
   // not possible the graph keeps the precompiled generic kernels (same device
   // code, run-time dispatch); rf_graph_uses_jit reports which one runs.
@@ -366,6 +380,11 @@ rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
 }
 
 int32_t rf_graph_uses_jit(const rf_graph* g) { return g && g->jit ? 1 : 0; }
+
+uint64_t rf_graph_kernel_hash(const rf_graph* g) {
+  if (!g || !g->jit) return 0;
+  return rf_jit_hash(g->prog, g->eval, g->coldt, RF_JIT_FUSED, g->cfg.ept);
+}
 
 int32_t rf_graph_kernel_regs(const rf_graph* g) {
   if (!g || !g->jit) return 0;
@@ -403,9 +422,13 @@ static rf_status check_events(const rf_graph* g, const void* events, int64_t n) 
   return RF_OK;
 }
 
+// One call = the FP64 prologue kernel, then the fused kernel as its
+// programmatic dependent (it launches at once and waits for the constants).
 static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, int64_t n,
                           const double* params, double* nll, double* grad, cudaStream_t st) {
   const RfProgram& P = g->prog;
+  int pe = rf_launch_prologue(P, g->eval, params, g->work, st);
+  if (pe) return pe;
   if (g->jit) {
     cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)];
     if (!k) return (int)cudaErrorInvalidValue;  // compiled by compile/set_launch/tune
@@ -430,7 +453,7 @@ rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events, const double
   if (!nll) return fail(RF_EINVAL, "nll is NULL");
   int e = fused_dispatch(g, g->cfg, events, n_events, params, nll, grad,
                          reinterpret_cast<cudaStream_t>(stream));
-  g->last_launches = 1;
+  g->last_launches = 2;
   if (e) return cuda_fail((cudaError_t)e, "rf_nll launch");
   return RF_OK;
 }
@@ -467,7 +490,7 @@ rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
     e = cudaMemcpyAsync(dp, host_params, sizeof(double) * np, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host H2D");
   int le = fused_dispatch(g, g->cfg, base, n_events, dp, dout, host_grad ? dout + 1 : nullptr, st);
-  g->last_launches = 1;
+  g->last_launches = 2;
   if (le) return cuda_fail((cudaError_t)le, "rf_nll_host launch");
   e = cudaMemcpyAsync(host_nll, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && host_grad && np)
@@ -802,9 +825,9 @@ rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
   return RF_OK;
 }
 
-rf_status rf_microbench(double* out8) {
-  if (!out8) return fail(RF_EINVAL, "out8 is NULL");
-  int e = rf_run_microbench(out8);
+rf_status rf_microbench(double* out) {
+  if (!out) return fail(RF_EINVAL, "out is NULL");
+  int e = rf_run_microbench(out);
   if (e) return cuda_fail((cudaError_t)e, "rf_microbench");
   return RF_OK;
 }

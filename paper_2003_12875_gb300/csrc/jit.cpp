@@ -95,9 +95,14 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   if (NC == 1) {
     o << "    q[1] += Real(1);\n";
   } else {
+    // common case first: no coefficient is exactly zero (one uniform branch)
+    o << "    if (K.zero_mask == 0) {\n";
+    for (int c = 0; c < NC; ++c) o << "      q[" << 1 + c << "] += w[" << c << "];\n";
+    o << "    } else {\n";
     for (int c = 0; c < NC; ++c)
-      o << "    q[" << 1 + c << "] += rf::comp_weight<Real>(K.zero_mask, " << c << ", K.delta_nc["
-        << c << "]" << usum[c] << ", ell, w[" << c << "]);\n";
+      o << "      q[" << 1 + c << "] += rf::comp_weight<Real>(K.zero_mask, " << c
+        << ", K.delta_nc[" << c << "]" << usum[c] << ", ell, w[" << c << "]);\n";
+    o << "    }\n";
   }
   for (int k = 0; k < NL; ++k)
     for (int j = 0; j < RF_LEAF_MAXP; ++j)
@@ -107,8 +112,13 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   o << "  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
+  // RF_JIT_MINBLOCKS=k asks the compiler to fit k blocks of 256 threads per SM
+  // (fewer registers per thread, more warps to hide latency)
+  std::string lb = "__launch_bounds__(256)";
+  if (const char* mb = getenv("RF_JIT_MINBLOCKS"))
+    if (atoi(mb) > 0) lb = "__launch_bounds__(256, " + std::to_string(atoi(mb)) + ")";
   if (kind == RF_JIT_FUSED) {
-    o << "extern \"C\" __global__ void __launch_bounds__(256) rf_fused_jit(const RfProgram P, const "
+    o << "extern \"C\" __global__ void " << lb << " rf_fused_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t n, int64_t head, int vec, const double* __restrict__ "
               "params, RfWork W, double* nll, double* grad) {\n  rf::fused_body<RfModel, "
       << R << ", " << C << ", " << ept << ">(P, ev, n, head, vec, params, W, nll, grad);\n}\n";
@@ -133,7 +143,8 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
 // NVRTC: source -> cubin for sm_103a (no device needed).
 static bool compile_cubin(const std::string& src, std::vector<char>* cubin, std::string* err) {
   if (const char* dump = getenv("RF_JIT_DUMP")) {  // write the emitted source for inspection
-    if (FILE* f = fopen(dump, "w")) {
+    std::string path = std::string(dump) + "." + std::to_string(fnv1a(src) & 0xffff) + ".cu";
+    if (FILE* f = fopen(path.c_str(), "w")) {
       fputs(src.c_str(), f);
       fclose(f);
     }
@@ -163,6 +174,10 @@ static bool compile_cubin(const std::string& src, std::vector<char>* cubin, std:
   return true;
 }
 
+uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept) {
+  return fnv1a(rf_jit_source(P, eval, coldt, kind, ept));
+}
+
 bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
                          std::string* err) {
   std::vector<char> cubin;
@@ -188,7 +203,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
     k = it->second;
   } else {
     char name[64];
-    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v2"));
+    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v6"));
     const std::string dir = cache_dir(), path = dir + name;
     std::vector<char> cubin;
     if (FILE* f = fopen(path.c_str(), "rb")) {
@@ -249,8 +264,18 @@ int rf_jit_launch_fused(cudaKernel_t k, const RfProgram& P, int coldt, const RfL
   RfProgram Pc = P;
   const void* ev = events;
   void* args[] = {&Pc, &ev, &n, &head, &vec, &params, &W, &nll, &grad};
-  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(cfg.block),
-                               args, 0, st);
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(cfg.block);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  if (W.consts) {  // dependent of the prologue kernel launched just before
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+  }
+  return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void*>(k), args);
 }
 
 int rf_jit_launch_toys(cudaKernel_t k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,

@@ -18,6 +18,10 @@ template <> struct Op<4> { typedef double T; static __device__ __forceinline__ d
 template <> struct Op<5> { typedef double T; static __device__ __forceinline__ double f(double a) { return exp(-a); } };
 template <> struct Op<6> { typedef double T; static __device__ __forceinline__ double f(double a) { return log(a + 2.0); } };
 template <> struct Op<7> { typedef double T; static __device__ __forceinline__ double f(double a) { return erf(a) + 0.25; } };
+// the library's own FP32 per-event functions
+template <> struct Op<8> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::log_fast(a + 2.0f); } };
+template <> struct Op<9> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::exp_neg_approx(-a); } };
+template <> struct Op<10> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::rcp_approx(a + 1.0f); } };
 
 template <int OP>
 __global__ void __launch_bounds__(256) mb_kernel(typename Op<OP>::T* sink, int iters) {
@@ -70,6 +74,9 @@ int rf_run_microbench(double* out) {
   out[5] = run<5>(sms, sink, 32);
   out[6] = run<6>(sms, sink, 32);
   out[7] = run<7>(sms, sink, 32);
+  out[8] = run<8>(sms, sink, 1024);
+  out[9] = run<9>(sms, sink, 1024);
+  out[10] = run<10>(sms, sink, 1024);
   e = cudaGetLastError();
   cudaFree(sink);
   return (int)e;

@@ -34,16 +34,26 @@ constexpr double kSqrtHalfPi = 1.25331413731550025121;
 constexpr double kSqrtPi = 1.77245385090551602730;
 
 // ------------------------------------------------------------------ FP64 math
-__device__ inline double erf_diff(double z1, double z2) {  // erf(z2)-erf(z1)
-  if (z1 >= 0.0) return erfc(z1) - erfc(z2);
-  if (z2 <= 0.0) return erfc(-z2) - erfc(-z1);
-  return erf(z2) - erf(z1);
+// One out-of-line copy of each FP64 function the prologue calls: the prologue
+// runs once per call on a few threads, so code size (instruction-cache misses
+// on cold code) matters more than call overhead.
+static __device__ __noinline__ double d_exp(double x) { return exp(x); }
+static __device__ __noinline__ double d_log(double x) { return log(x); }
+static __device__ __noinline__ double d_erf(double x) { return erf(x); }
+static __device__ __noinline__ double d_erfc(double x) { return erfc(x); }
+static __device__ __noinline__ double d_expm1(double x) { return expm1(x); }
+static __device__ __noinline__ double d_pow(double x, double y) { return pow(x, y); }
+
+__device__ inline double erf_diff(double z1, double z2) {  // d_erf(z2)-d_erf(z1)
+  if (z1 >= 0.0) return d_erfc(z1) - d_erfc(z2);
+  if (z2 <= 0.0) return d_erfc(-z2) - d_erfc(-z1);
+  return d_erf(z2) - d_erf(z1);
 }
 
 // (e^y - 1)/y and its derivative; the derivative's closed form cancels near
 // 0, where its Taylor series sum_{k>=1} k y^(k-1)/(k+1)! is used instead.
 __device__ inline double expm1_over(double y) {
-  return y == 0.0 ? 1.0 : expm1(y) / y;
+  return y == 0.0 ? 1.0 : d_expm1(y) / y;
 }
 __device__ inline double expm1_over_d(double y) {
   if (fabs(y) < 1.0) {
@@ -55,7 +65,7 @@ __device__ inline double expm1_over_d(double y) {
     }
     return acc;
   }
-  return (exp(y) * (y - 1.0) + 1.0) / (y * y);
+  return (d_exp(y) * (y - 1.0) + 1.0) / (y * y);
 }
 
 // int_0^tau s^q e^{c s} ds, q in {1/2, 3/2}: incomplete-gamma closed form for
@@ -64,8 +74,8 @@ __device__ inline double argus_int(double q, double tau, double c) {
   if (tau <= 0.0) return 0.0;
   double y = c * tau;
   if (c < 0.0 && -y >= 0.5) {
-    double k = -c, ky = -y, sky = sqrt(ky), eky = exp(-ky);
-    double g32 = 0.5 * kSqrtPi * erf(sky) - sky * eky;  // gamma(3/2, ky)
+    double k = -c, ky = -y, sky = sqrt(ky), eky = d_exp(-ky);
+    double g32 = 0.5 * kSqrtPi * d_erf(sky) - sky * eky;  // gamma(3/2, ky)
     if (q == 0.5) return g32 / (k * sqrt(k));
     double g52 = 1.5 * g32 - ky * sky * eky;            // gamma(5/2, ky)
     return g52 / (k * k * sqrt(k));
@@ -77,10 +87,10 @@ __device__ inline double argus_int(double q, double tau, double c) {
     if (j > fabs(y) && fabs(add) < 1e-18 * fabs(sum)) break;
     term *= y / (j + 1.0);
   }
-  return pow(tau, q + 1.0) * sum;
+  return d_pow(tau, q + 1.0) * sum;
 }
 
-// log(I) - off and d(log I - off)/d theta_j for one leaf (FP64).  `off` is
+// d_log(I) - off and d(log I - off)/d theta_j for one leaf (FP64).  `off` is
 // the constant the per-event code leaves out of u = log f - off (Exponential:
 // lambda * lo, so that u = lambda (x - lo) stays small).  Returns false when
 // the parameters are outside the leaf's definition range.
@@ -93,8 +103,8 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
       if (!(sg > 0.0)) return false;
       double za = (lo - mu) / sg, zb = (hi - mu) / sg;
       double I = sg * kSqrtHalfPi * erf_diff(za / kSqrt2, zb / kSqrt2);
-      double pa = exp(-0.5 * za * za), pb = exp(-0.5 * zb * zb);
-      *lnI = log(I);
+      double pa = d_exp(-0.5 * za * za), pb = d_exp(-0.5 * zb * zb);
+      *lnI = d_log(I);
       dln[0] = (pa - pb) / I;
       dln[1] = 1.0 / sg + (za * pa - zb * pb) / I;
       return I > 0.0 && isfinite(I);
@@ -102,11 +112,11 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
     case RFL_EXP: {
       // I = e^{lambda lo} L E1(lambda L); off = lambda lo.
       double lam = th[0], L = hi - lo, s = lam * L;
-      *lnI = log(L * expm1_over(s));
+      *lnI = d_log(L * expm1_over(s));
       // d log I / d lambda - lo = <x> - lo = L (1/(1-e^-s) - 1/s)
       double m = (fabs(s) < 1e-3)
                      ? 0.5 + s / 12.0 - s * s * s / 720.0 + s * s * s * s * s / 30240.0
-                     : 1.0 / (-expm1(-s)) - 1.0 / s;
+                     : 1.0 / (-d_expm1(-s)) - 1.0 / s;
       dln[0] = L * m;
       return isfinite(*lnI);
     }
@@ -119,7 +129,7 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
         dJ[j - 1] = tj;
       }
       if (!(J > 0.0)) return false;
-      *lnI = log(half * J);
+      *lnI = d_log(half * J);
       for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = dJ[j] / J;
       return true;
     }
@@ -132,27 +142,34 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
       double core = 0.0;
       if (thi > -A) core = kSqrtHalfPi * erf_diff(fmax(tlo, -A) / kSqrt2, thi / kSqrt2);
       double tail = 0.0, dA = 0.0, dn = 0.0;
+      const double eA = d_exp(-0.5 * A * A);
+      // integrand g(t) at the two range ends; in the tail g = e^{-A^2/2} D^-n
+      // = e^{-A^2/2 - n log D}, which reuses the logs the tail integral needs
+      double glo = 0.0, ghi = 0.0;
       if (tlo < -A) {
         // substitute D = 1 - (A/n)(A+t): tail = (n/A) e^{-A^2/2} int D^-n dD
         double D1 = 1.0 - (A / n) * (A + tlo);
-        double D2 = 1.0 - (A / n) * (A + fmin(thi, -A));
-        double L1 = log(D1), L2 = log(D2), dL = L1 - L2, eps = 1.0 - n;
-        double ez = exp(eps * L2);
-        double Phi = ez * dL * expm1_over(eps * dL);                  // int D^-n
-        double PhiL = L2 * Phi + ez * dL * dL * expm1_over_d(eps * dL); // int D^-n log D
-        double Psi = (pow(D2, -n) - pow(D1, -n)) / n;                  // int D^-n-1
-        double pre = (n / A) * exp(-0.5 * A * A);
+        double t2 = fmin(thi, -A);
+        double D2 = 1.0 - (A / n) * (A + t2);
+        double L1 = d_log(D1), L2 = (t2 == -A) ? 0.0 : d_log(D2), dL = L1 - L2, eps = 1.0 - n;
+        double ez = (L2 == 0.0) ? 1.0 : d_exp(eps * L2);
+        double Phi = ez * dL * expm1_over(eps * dL);                    // int D^-n
+        double PhiL = L2 * Phi + ez * dL * dL * expm1_over_d(eps * dL);  // int D^-n log D
+        double p1 = d_exp(-n * L1), p2 = (L2 == 0.0) ? 1.0 : d_exp(-n * L2);
+        double Psi = (p2 - p1) / n;                                      // int D^-n-1
+        double pre = (n / A) * eA;
         tail = pre * Phi;
         dA = pre * (A + n / A) * (Psi - Phi);
         dn = pre * (Phi - PhiL - Psi);
+        glo = eA * p1;
+        if (thi <= -A) ghi = eA * p2;
+      } else {
+        glo = d_exp(-0.5 * tlo * tlo);
       }
+      if (thi > -A) ghi = d_exp(-0.5 * thi * thi);
       double J = core + tail;
-      double glo = (tlo > -A) ? exp(-0.5 * tlo * tlo)
-                              : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + tlo), -n);
-      double ghi = (thi > -A) ? exp(-0.5 * thi * thi)
-                              : exp(-0.5 * A * A) * pow(1.0 - (A / n) * (A + thi), -n);
       double I = sg * J;
-      *lnI = log(I);
+      *lnI = d_log(I);
       dln[0] = -s * (ghi - glo) / I;
       dln[1] = (J + tlo * glo - thi * ghi) / I;
       dln[2] = s * dA / J;
@@ -167,10 +184,10 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
       double h = 0.5 * m0 * m0;
       double I = h * (argus_int(0.5, ta, c) - argus_int(0.5, tb, c));
       double dIc = h * (argus_int(1.5, ta, c) - argus_int(1.5, tb, c));
-      double ea = (1.0 - ta) * sqrt(ta) * exp(c * ta);
-      double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * exp(c * tb) : 0.0;
+      double ea = (1.0 - ta) * sqrt(ta) * d_exp(c * ta);
+      double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * d_exp(c * tb) : 0.0;
       double dIm = m0 * (ea - eb) + 2.0 * I / m0;
-      *lnI = log(I);
+      *lnI = d_log(I);
       dln[0] = dIm / I;
       dln[1] = dIc / I;
       return I > 0.0 && isfinite(I);
@@ -291,7 +308,7 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
   int zero = 0;
   for (int c = 0; c < C; ++c) {
     if (coef[c] > 0.0) {
-      beta[c] = log(coef[c]) + base[c];
+      beta[c] = d_log(coef[c]) + base[c];
       ref = fmax(ref, beta[c]);
     } else {
       beta[c] = -kInf();
@@ -344,8 +361,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float log_fast(float x) {
-  if (!(x >= 1.17549435e-38f && x <= 3.40282347e+38f)) return logf(x);
+// Core of the fast log for x > 0 normal and finite (no argument checks).
+// The exponent becomes a float through the 1.5*2^23 trick (one integer add
+// and one float subtract) instead of an int-to-float conversion.
+__device__ __forceinline__ float log_pos(float x) {
   const int ix = __float_as_int(x);
   const int e = (ix - 0x3f3504f3) >> 23;  // m = x / 2^e in [0.70710677, 1.4142135)
   const float m = __int_as_float(ix - (e << 23));
@@ -356,8 +375,21 @@ __device__ __forceinline__ float log_fast(float x) {
   p = fmaf(z, p, 0.33333334f);
   p = fmaf(z, p, 1.0f);
   const float lm = 2.0f * s * p;
-  const float fe = (float)e;
+  const float fe = __int_as_float(0x4b400000 + e) - 12582912.0f;  // (float)e, |e| < 2^22
   return fmaf(fe, 0.693145752f, fmaf(fe, 1.42860677e-06f, lm));  // ln2 = hi + lo
+}
+__device__ __forceinline__ float log_fast(float x) {
+  if (!(x >= 1.17549435e-38f && x <= 3.40282347e+38f)) return logf(x);
+  return log_pos(x);
+}
+// exp(x) for x <= 0 through the hardware base-2 exponential (max relative
+// error 2^-22 by the PTX specification) of x * log2(e); used for the mixture
+// weight exp(-|v1 - v0|) in (0, 1], whose absolute error then stays below
+// 4e-8 for every argument.
+__device__ __forceinline__ float exp_neg_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.44269504f));
+  return r;
 }
 
 template <typename Real>
@@ -365,6 +397,9 @@ struct Fn;
 template <>
 struct Fn<float> {
   static __device__ __forceinline__ float log(float x) { return log_fast(x); }
+  // x known positive and finite wherever its result is used
+  static __device__ __forceinline__ float logp(float x) { return log_pos(x); }
+  static __device__ __forceinline__ float exp_neg(float x) { return exp_neg_approx(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
   static __device__ __forceinline__ float ninf() { return -__int_as_float(0x7f800000); }
@@ -372,6 +407,8 @@ struct Fn<float> {
 template <>
 struct Fn<double> {
   static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double logp(double x) { return ::log(x); }
+  static __device__ __forceinline__ double exp_neg(double x) { return ::exp(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double ninf() { return -kInf(); }
@@ -427,7 +464,7 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   Real t = ((x - pc[0]) - pc[1]) * pc[2];  // s (x - m0) / sigma
   bool tail = t <= -A;
   Real D = Real(1) - pc[5] * (A + t);
-  Real Lg = F::log(D);
+  Real Lg = F::logp(D);  // used only in the tail, where D >= 1
   u = tail ? pc[7] - pc[6] * Lg : Real(-0.5) * t * t;
   if (GM) {
     Real rD = F::rcp(D);
@@ -491,13 +528,13 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
     return v[0];
   } else if constexpr (NC == 2) {
     Real dv = v[1] - v[0];
-    Real e = F::exp(-fabs(dv));
+    Real e = F::exp_neg(-fabs(dv));
     Real s = Real(1) + e;
     Real rs = F::rcp(s);
     Real wb = rs, ws = e * rs;
     w[0] = dv > Real(0) ? ws : wb;
     w[1] = dv > Real(0) ? wb : ws;
-    return fmax(v[0], v[1]) + F::log(s);
+    return fmax(v[0], v[1]) + F::log(s);  // s in [1, 2], or NaN from NaN inputs
   } else {
     Real m = v[0];
 #pragma unroll

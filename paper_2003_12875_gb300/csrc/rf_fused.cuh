@@ -65,9 +65,20 @@ inline int launch_fused_nl(const RfProgram& P, const RfLaunchCfg& cfg, int num_s
   vec_plan<Col>(P, events, n, &vec, &head);
   int64_t chunks = n / EPT;
   int grid = grid_for(chunks, cfg.block, num_sms, cfg.blocks_per_sm);
-  fused_nll_kernel<Real, Col, NL, EPT><<<grid, cfg.block, 0, st>>>(
-      P, static_cast<const Col*>(events), n, head, vec, params, W, nll, grad);
-  return (int)cudaGetLastError();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(cfg.block);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  if (W.consts) {  // dependent of the prologue kernel launched just before
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+  }
+  const Col* ev = static_cast<const Col*>(events);
+  return (int)cudaLaunchKernelEx(&lc, fused_nll_kernel<Real, Col, NL, EPT>, P, ev, n, head, vec,
+                                 params, W, nll, grad);
 }
 
 template <typename Real, typename Col, int EPT>

@@ -93,6 +93,12 @@ struct RfWork {
   double* adam_m1;         // [max_toys * n_par]
   double* adam_m2;
   int32_t* adam_t;         // [1] step counter
+  // single dataset: constants from the separate prologue kernel (NULL: each
+  // block computes them itself)
+  void* consts;            // [1] RfConsts<Real>
+  double* pro_lnI;         // [RF_MAXL]
+  int* pro_ok;             // [RF_MAXL]
+  unsigned int* pro_ticket;  // [1]
 };
 
 struct RfLaunchCfg {
@@ -117,6 +123,12 @@ RF_DECL_FUSED(f32, c64)
 RF_DECL_FUSED(f64, c32)
 RF_DECL_FUSED(f64, c64)
 
+// FP64 prologue kernel for the single-dataset path: one block per leaf, the
+// last block combines; writes W.consts and lets the dependent (fused) kernel
+// launch at once (programmatic dependent launch).
+int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
+                       rf_cuda_stream st);
+
 int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, RfWork W,
                  void* stream);
 int rf_launch_batched(const RfProgram& P, int eval, int coldt,
@@ -131,7 +143,7 @@ int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
                     double* nll, double* grad, double* partials,
                     unsigned int* counter, void* stream, int* launches);
 size_t rf_plain_bytes(const RfProgram& prog, int64_t n);
-int rf_run_microbench(double* out8);
+int rf_run_microbench(double* out);
 int rf_run_check_log(const float* x, float* y_fast, float* y_ref, int64_t n, rf_cuda_stream st);
 size_t rf_consts_size(int eval);
 
@@ -146,6 +158,7 @@ void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int ele
 enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2 };
 typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
 std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept);
+uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept);
 bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
                          std::string* err);
 rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,

@@ -177,15 +177,13 @@ struct Acc {
   }
 };
 
-template <class M, typename Real, typename Col, int EPT>
-__device__ __forceinline__ void iterate_full(const RfProgram& P,
+// EPT events already in registers -> the iteration's partial sums -> acc.
+template <class M, typename Real, int EPT>
+__device__ __forceinline__ void compute_full(const RfProgram& P,
                                              const EvalConsts<Real, M::NL_>& K,
-                                             const Col* __restrict__ ev, int64_t stride,
-                                             int64_t i0, bool vec,
+                                             const Real (&x)[M::NL_][EPT],
                                              Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
   constexpr int NL = M::NL_;
-  Real x[NL][EPT];
-  load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, i0, vec, x);
   Real q[RF_NACC(NL)];
 #pragma unroll
   for (int i = 0; i < RF_NACC(NL); ++i) q[i] = Real(0);
@@ -197,6 +195,36 @@ __device__ __forceinline__ void iterate_full(const RfProgram& P,
     M::template event<Real>(P, K, xc, q);
   }
   acc.add(q);
+}
+
+// Chunks first, first+step, ... < nfull of EPT events each (chunk c starts at
+// event base + c*EPT).  The next chunk's 128-bit loads are issued before the
+// current chunk is computed (register double buffering), so the memory
+// latency overlaps the arithmetic.
+template <class M, typename Real, typename Col, int EPT>
+__device__ __forceinline__ void stream_chunks(const RfProgram& P,
+                                              const EvalConsts<Real, M::NL_>& K,
+                                              const Col* __restrict__ ev, int64_t stride,
+                                              int64_t base, int64_t first, int64_t step,
+                                              int64_t nfull, bool vec,
+                                              Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
+  constexpr int NL = M::NL_;
+  if (first >= nfull) return;
+  Real xa[NL][EPT];
+  load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + first * EPT, vec, xa);
+  for (int64_t ch = first;;) {
+    const int64_t nx = ch + step;
+    const bool more = nx < nfull;
+    Real xb[NL][EPT];
+    if (more) load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nx * EPT, vec, xb);
+    compute_full<M, Real, EPT>(P, K, xa, acc);
+    if (!more) break;
+#pragma unroll
+    for (int c = 0; c < NL; ++c)
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) xa[c][e] = xb[c][e];
+    ch = nx;
+  }
 }
 
 template <class M, typename Real, typename Col>
@@ -251,7 +279,18 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   __shared__ double tot[NA];
   __shared__ int s_last;
 
-  block_prologue(P, params, K, lnI, ok);
+  if (W.consts) {
+    // constants from the prologue kernel, which this launch may overlap:
+    // wait for it (a no-op when this grid was not launched as its dependent)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
+    const double* src = static_cast<const double*>(W.consts);
+    double* dst = reinterpret_cast<double*>(&K);
+    for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = __ldcg(src + w);
+    __syncthreads();
+  } else {
+    block_prologue(P, params, K, lnI, ok);
+  }
 
   Acc<Real, NA, M::AMASK> acc;
   acc.zero();
@@ -261,8 +300,8 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     const int64_t h = head < n ? head : n;
     const int64_t nfull = (n - h) / EPT;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nfull; ch += gsz)
-      iterate_full<M, Real, Col, EPT>(P, E, ev, n, h + ch * EPT, vec != 0, acc);
+    stream_chunks<M, Real, Col, EPT>(P, E, ev, n, h, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                     gsz, nfull, vec != 0, acc);
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
       iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
       iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
@@ -312,6 +351,34 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
     for (int j = 0; j < NA; ++j) q[j] = Real(0);
     M::template event<Real>(P, E, xc, q);
     logp[i] = K.bad ? kNaN() : K.beta_ref + (double)q[0];
+  }
+}
+
+// The single-dataset prologue as its own grid: block k computes leaf k (the
+// FP64 work of different leaves runs on different SMs), the last block to
+// finish combines.  It lets the dependent fused grid launch immediately.
+template <typename Real>
+__device__ __forceinline__ void prologue_body(const RfProgram& P, const double* __restrict__ params,
+                                              RfWork& W) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  RfConsts<Real>* K = static_cast<RfConsts<Real>*>(W.consts);
+  const int k = blockIdx.x;
+  if (threadIdx.x != 0 || k >= P.n_leaves) return;
+  double lnI = 0.0;
+  const bool ok = leaf_consts(P, params, *K, k, &lnI);
+  W.pro_lnI[k] = lnI;
+  W.pro_ok[k] = ok ? 1 : 0;
+  __threadfence();
+  if (atomicAdd(W.pro_ticket, 1u) == (unsigned)P.n_leaves - 1u) {
+    __threadfence();
+    double l[RF_MAXL];
+    bool all = true;
+    for (int j = 0; j < P.n_leaves; ++j) {
+      l[j] = __ldcg(W.pro_lnI + j);
+      all &= __ldcg(W.pro_ok + j) != 0;
+    }
+    comb_consts(P, params, *K, l, all);
+    *W.pro_ticket = 0u;
   }
 }
 
@@ -405,8 +472,8 @@ __device__ __forceinline__ void toy_tile_body(const RfProgram& P, const Col* __r
         if (h > e - b) h = e - b;
       }
       const int64_t nfull = (e - b - h) / EPT;
-      for (int64_t ch = threadIdx.x; ch < nfull; ch += blockDim.x)
-        iterate_full<M, Real, Col, EPT>(P, E, ev, stride, b + h + ch * EPT, vec != 0, acc);
+      stream_chunks<M, Real, Col, EPT>(P, E, ev, stride, b + h, threadIdx.x, blockDim.x, nfull,
+                                       vec != 0, acc);
       if (threadIdx.x == blockDim.x - 1) {
         iterate_scalar<M, Real, Col>(P, E, ev, stride, b, b + h, acc);
         iterate_scalar<M, Real, Col>(P, E, ev, stride, b + h + nfull * EPT, e, acc);
