@@ -128,13 +128,15 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
 LEAF_INSTR = {
     "gauss": (5, {0: 1, 1: 2}, 0),
     "exp": (3, {0: 0}, 0),
-    "cheb": (34, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
-    "cb": (30, {0: 1, 1: 2, 2: 4, 3: 3}, 3),
-    "argus": (35, {0: 5, 1: 1}, 0),
+    "cheb": (13, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
+    "cb": (12, {0: 1, 1: 2, 2: 4, 3: 3}, 3),
+    "argus": (14, {0: 5, 1: 1}, 0),
 }
+LOG_INSTR = 2          # hardware log2 and a multiply by ln 2
+F64_TO_F32_INSTR = 9   # integer-pipe rounding of an FP64 column value
 
 
-def algorithmic_instr_per_event(spec: dict, ept: int) -> float:
+def algorithmic_instr_per_event(spec: dict, ept: int, f64_columns: bool = False) -> float:
     nodes = spec["nodes"]
     fixed = spec.get("fixed") or [False] * len(spec["params"])
     leaves = [nd for nd in nodes if nd["type"] in LEAF_INSTR]
@@ -148,12 +150,14 @@ def algorithmic_instr_per_event(spec: dict, ept: int) -> float:
         free += len(wanted)
     total += len(leaves)                      # component sums delta_c + sum u_k
     if nc == 2:
-        total += 34                           # two-term log-sum-exp and weights
+        total += 13                           # two-term log-sum-exp and weights
     elif nc > 2:
         total += 12 * nc + 25
     total += 1 + (nc if nc > 1 else 1) + free + (2 if nc > 1 else 0)   # adjoint sums
     total += 4.0 * (1 + nc + free) / ept      # compensated per-iteration sums
     total += 1                                # loads and loop
+    if f64_columns:
+        total += F64_TO_F32_INSTR * len(spec["obs"])
     return total
 
 
@@ -225,6 +229,43 @@ def toy_study(rf, torch, toys=4096, iters=50):
     return res
 
 
+def toy_bench(args, rf, torch, rank, world, pk):
+    """--workload c4: a step is one batched NLL + gradient of all 4096 toys."""
+    import numpy as np
+
+    import datagen
+    w = datagen.c4()
+    ev = torch.from_numpy(w["cols"]).cuda()
+    off = torch.from_numpy(w["offsets"]).cuda()
+    pm = torch.from_numpy(w["params_matrix"]).cuda()
+    toys = len(w["offsets"]) - 1
+    n = int(w["offsets"][-1])
+    G = rf.Graph(w["spec"], "f64", args.precision)
+    G.bind_events(ev, toys)
+    out = G.nll_batched(off, pm)
+    for _ in range(args.warmup):
+        G.nll_batched(off, pm, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        G.nll_batched(off, pm, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    line = {"metric": METRIC, "value": job_throughput(n, world, ms), "unit": "events/s",
+            "toy_nll_per_s": world * toys / (ms * 1e-3), "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "toys": toys, "events": n,
+                       "launch": G.get_launch(), "kernel": G.uses_jit()},
+            "gpu_launches": G.last_launches() * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -265,6 +306,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ept", type=int, default=0,
+                    help="events per thread of the fused kernel (0: default / tuned)")
     ap.add_argument("--generic", action="store_true",
                     help="run the precompiled generic kernels instead of the per-graph ones")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -289,6 +332,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     pk = peaks()
 
+    if args.workload == "c4":
+        return toy_bench(args, rf, torch, rank, world, pk)
+
     # ---------------------------------------------------------------- data
     w = make_workload(args.workload)
     spec = w["spec"]
@@ -304,6 +350,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     tuned_ms = None
+    if args.ept:
+        G.set_launch(ept=args.ept)
     if not args.no_tune:
         tuned_ms = G.tune(ev, params)
     for _ in range(args.warmup):
@@ -358,7 +406,10 @@ def main():
     e2e = {"value": world * n / e2e_s, "unit": "events/s",
            "h2d_bytes_per_step": int(host.numel() * col_bytes + 8 * len(spec["params"])),
            "d2h_bytes_per_step": int(8 * (1 + len(spec["params"]))),
-           "ms_per_step": e2e_s * 1e3}
+           "ms_per_step": e2e_s * 1e3,
+           "path": "rf_nll_host on pinned host memory ("
+                   + ("staged copy" if os.environ.get("RF_HOST_DIRECT") == "0"
+                      else "read in place by the kernel over the host link") + ")"}
 
     # ----------------------------------------------------------- roofline
     # The fused FP32-eval kernel is bound by instruction issue (transcendentals
@@ -375,7 +426,7 @@ def main():
            "frac": hbm_achieved / pk["hbm_gbs"], "peak_source": pk["source"],
            "bytes_per_launch": bytes_per_launch}
     if args.precision == "fp32":
-        instr = algorithmic_instr_per_event(spec, launch_cfg["ept"])
+        instr = algorithmic_instr_per_event(spec, launch_cfg["ept"], w["dtype"] == "f64")
         peak = sms * 128 * sm_mhz * 1e6
         achieved = instr * n / (per_launch * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
@@ -401,6 +452,7 @@ def main():
                        "launch": G.get_launch(), "tuned_ms": tuned_ms,
                        "kernel": "specialised (NVRTC)" if G.uses_jit() else "generic",
                        "regs_per_thread": G.kernel_regs(),
+                       "kernel_hash": G.kernel_hash(),
                        "parallelism": f"{world} independent replica(s)"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "nll": nll_value}

@@ -138,10 +138,15 @@ rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events,
                  const double* params, double* nll, double* grad,
                  rf_stream stream);
 
-/* As rf_nll with HOST buffers: copies events and params to the graph's device
- * staging area, evaluates, copies nll / grad back, and synchronises the stream.
- * The staging area grows (cudaMalloc) when n_events exceeds its size, so this
- * entry point is not capturable.  host_grad may be NULL. */
+/* As rf_nll with HOST buffers: evaluates, copies nll / grad back, and
+ * synchronises the stream.  Page-locked host memory that the device can
+ * address (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch tensor) is
+ * read by the fused kernel in place -- on a Grace-Blackwell node over
+ * NVLink-C2C, each byte crossing the link once; other host memory is first
+ * copied into the graph's device staging area (RF_HOST_DIRECT=0 in the
+ * environment forces the copy).  The staging area grows (cudaMalloc) when
+ * n_events exceeds its size, so this entry point is not capturable.
+ * host_grad may be NULL. */
 rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
                       const double* host_params, double* host_nll,
                       double* host_grad, rf_stream stream);
@@ -198,7 +203,7 @@ typedef struct {
   int32_t block;
   int32_t ept;
   int32_t blocks_per_sm;
-  int32_t tile; /* batched mode: events per tile (multiple of block*ept) */
+  int32_t tile; /* batched mode: events per tile, >= 1024 (default 32768) */
 } rf_launch;
 
 rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg);
@@ -269,13 +274,19 @@ const char* rf_last_error(void);
  * per-event log-densities), y_ref[i] = CUDA logf(x[i]); dev arrays [n]. */
 rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
                        rf_stream stream);
+/* Diagnostics: y_fast[i] = the library's integer-pipe FP64 -> FP32 rounding
+ * of x[i] (used when FP64 columns are evaluated in FP32), y_ref[i] = the
+ * hardware conversion (__double2float_rn); dev arrays [n]. */
+rf_status rf_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n,
+                       rf_stream stream);
 
 /* Throughput of single operations on this GPU, in operations per second,
  * measured by dedicated kernels (used for the compute roofline):
  * out[0] FP32 FMA, out[1] expf, out[2] logf, out[3] FP32 reciprocal (IEEE),
  * out[4] FP64 FMA, out[5] exp (FP64), out[6] log (FP64), out[7] erf (FP64),
  * out[8] the library's FP32 log, out[9] its FP32 exp(-x) (x >= 0),
- * out[10] the approximate FP32 reciprocal.  out has 11 entries.
+ * out[10] the approximate FP32 reciprocal, out[11] FP32 FMAs/s issued as
+ * packed FP32x2 FMA instructions.  out has 12 entries.
  * Host-synchronous; allocates a small scratch buffer. */
 rf_status rf_microbench(double* out);
 

@@ -69,7 +69,8 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_fit_toys", "rf_nll_plain", "rf_graph_get_launch", "rf_graph_set_launch",
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
-           "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash"]
+           "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
+           "rf_check_d2f"]
 
 
 def lib_path() -> str:
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = True):
         L.rf_jit_check.argtypes = [C.POINTER(_Desc)]
         L.rf_check_log.argtypes = [vp, vp, vp, i64, vp]
         L.rf_nll_noalloc.argtypes = [C.POINTER(_Desc), vp, i64, vp, vp, vp, i32, vp]
+        L.rf_check_d2f.argtypes = [vp, vp, vp, i64, vp]
         L.rf_graph_kernel_hash.argtypes = [vp]
         L.rf_graph_kernel_hash.restype = C.c_uint64
         for name in SYMBOLS:
@@ -188,6 +190,15 @@ def nll_noalloc(spec: dict, events: torch.Tensor, params: torch.Tensor, out: tor
     _check(load().rf_nll_noalloc(C.byref(d), _ptr(events), int(n), _ptr(params), _ptr(out),
                                  C.c_void_p(out.data_ptr() + 8), int(blocks), _stream()))
     return out
+
+
+def check_d2f(x: torch.Tensor):
+    """(library FP64->FP32 rounding, hardware rounding) of a CUDA float64 tensor."""
+    x = x.contiguous()
+    yf = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    yr = torch.empty_like(yf)
+    _check(load().rf_check_d2f(_ptr(x), _ptr(yf), _ptr(yr), x.numel(), _stream()))
+    return yf, yr
 
 
 def check_log(x: torch.Tensor):
@@ -376,8 +387,8 @@ class RFNll(torch.autograd.Function):
 
 def microbench() -> dict:
     """Measured per-operation throughput (operations/s) on the current GPU."""
-    out = (C.c_double * 11)()
+    out = (C.c_double * 12)()
     _check(load().rf_microbench(out))
     keys = ["fp32_fma", "expf", "logf", "rcp_f32", "fp64_fma", "exp_f64", "log_f64", "erf_f64",
-            "log_fast_f32", "exp_neg_f32", "rcp_approx_f32"]
+            "log_fast_f32", "exp_neg_f32", "rcp_approx_f32", "fp32_fma_packed_x2"]
     return dict(zip(keys, list(out)))

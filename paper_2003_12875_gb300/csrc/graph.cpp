@@ -216,7 +216,7 @@ struct rf_graph {
   RfProgram prog;
   int eval = 0, coldt = 0, n_obs = 0;
   int device = 0, num_sms = 0;
-  RfLaunchCfg cfg{256, 4, 2, 8192};
+  RfLaunchCfg cfg{256, 4, 2, 32768};
   RfWork work{};
   int64_t max_rows_single = 0;
   // batched
@@ -269,6 +269,8 @@ static void free_work(rf_graph* g) {
   cudaFree(g->work.partials);
   cudaFree(g->work.counter);
   cudaFree(g->work.tile_start);
+  cudaFree(g->work.tile_toy);
+  cudaFree(g->work.tile_be);
   cudaFree(g->work.toy_counter);
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
@@ -484,12 +486,26 @@ rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
   double* dp = reinterpret_cast<double*>(base + ev_pad);
   double* dout = dp + RF_MAXPAR;
   const int np = g->prog.n_par;
+  // Page-locked host memory the device can address is read by the fused
+  // kernel in place (on a Grace-Blackwell node over NVLink-C2C: the link
+  // carries each byte once and no staging copy is made); other host memory
+  // is staged with one copy.  RF_HOST_DIRECT=0 always stages.
+  const void* ev_dev = base;
+  if (ev_bytes && !(getenv("RF_HOST_DIRECT") && getenv("RF_HOST_DIRECT")[0] == '0')) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, host_events) == cudaSuccess &&
+        pa.type == cudaMemoryTypeHost && pa.devicePointer)
+      ev_dev = pa.devicePointer;
+    else
+      cudaGetLastError();  // not registered with CUDA: stage it
+  }
   cudaError_t e = cudaSuccess;
-  if (ev_bytes) e = cudaMemcpyAsync(base, host_events, ev_bytes, cudaMemcpyHostToDevice, st);
+  if (ev_bytes && ev_dev == base)
+    e = cudaMemcpyAsync(base, host_events, ev_bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && np)
     e = cudaMemcpyAsync(dp, host_params, sizeof(double) * np, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host H2D");
-  int le = fused_dispatch(g, g->cfg, base, n_events, dp, dout, host_grad ? dout + 1 : nullptr, st);
+  int le = fused_dispatch(g, g->cfg, ev_dev, n_events, dp, dout, host_grad ? dout + 1 : nullptr, st);
   g->last_launches = 2;
   if (le) return cuda_fail((cudaError_t)le, "rf_nll_host launch");
   e = cudaMemcpyAsync(host_nll, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -538,11 +554,15 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "rf_graph_bind_events sync");
   cudaFree(g->work.tile_start);
+  cudaFree(g->work.tile_toy);
+  cudaFree(g->work.tile_be);
   cudaFree(g->work.toy_counter);
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
   g->work.tile_start = nullptr;
+  g->work.tile_toy = nullptr;
+  g->work.tile_be = nullptr;
   g->work.toy_counter = nullptr;
   g->work.toy_consts = nullptr;
   g->work.adam_m1 = g->work.adam_m2 = nullptr;
@@ -559,6 +579,8 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   }
   const size_t np = (size_t)std::max(g->prog.n_par, 1);
   e = cudaMalloc(&g->work.tile_start, sizeof(int64_t) * ((size_t)max_toys + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.tile_toy, sizeof(int32_t) * (size_t)rows);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.tile_be, 2 * sizeof(int64_t) * (size_t)rows);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_counter, sizeof(unsigned int) * (size_t)max_toys + 8);
   if (e == cudaSuccess) e = cudaMemset(g->work.toy_counter, 0, sizeof(unsigned int) * (size_t)max_toys + 8);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
@@ -627,7 +649,7 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
   if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_m2, 0, sizeof(double) * np * toys, fs);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_t, 0, sizeof(int32_t), fs);
   if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys reset");
-  int le = rf_toys_plan(offsets, toys, g->cfg.tile, g->work, fs);
+  int le = rf_toys_plan(offsets, toys, g->cfg.tile, g->max_tile_rows, g->bound_n, g->work, fs);
   if (le) return cuda_fail((cudaError_t)le, "rf_fit_toys plan");
   int launches = 1;
   if (iters > 0) {
@@ -816,6 +838,14 @@ rf_status rf_graph_status(rf_graph* g, uint32_t* flags) {
 }
 
 int32_t rf_graph_last_launches(const rf_graph* g) { return g ? g->last_launches : 0; }
+
+rf_status rf_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n,
+                       rf_stream stream) {
+  if (n < 0 || (n > 0 && (!x || !y_fast || !y_ref))) return fail(RF_EINVAL, "bad argument");
+  int e = rf_run_check_d2f(x, y_fast, y_ref, n, reinterpret_cast<cudaStream_t>(stream));
+  if (e) return cuda_fail((cudaError_t)e, "rf_check_d2f");
+  return RF_OK;
+}
 
 rf_status rf_check_log(const float* x, float* y_fast, float* y_ref, int64_t n,
                        rf_stream stream) {

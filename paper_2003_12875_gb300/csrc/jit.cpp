@@ -71,6 +71,7 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
     for (int j = 0; j < RF_LEAF_MAXP; ++j)
       if ((P.leaf[k].gmask >> j) & 1) amask |= 1ull << (1 + NL + k * RF_LEAF_MAXP + j);
   std::ostringstream o;
+  if (getenv("RF_EVENTS_KEEP_L2")) o << "#define RF_EVENTS_KEEP_L2 1\n";  // experiment switch
   o << kRfJitPrelude << "\n// ---- model emitted for this graph\n";
   o << "struct RfModel {\n  static constexpr int NL_ = " << NL << ";\n"
     << "  static constexpr int NCOL = " << P.n_cols << ";\n"
@@ -115,6 +116,7 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   // RF_JIT_MINBLOCKS=k asks the compiler to fit k blocks of 256 threads per SM
   // (fewer registers per thread, more warps to hide latency)
   std::string lb = "__launch_bounds__(256)";
+
   if (const char* mb = getenv("RF_JIT_MINBLOCKS"))
     if (atoi(mb) > 0) lb = "__launch_bounds__(256, " + std::to_string(atoi(mb)) + ")";
   if (kind == RF_JIT_FUSED) {
@@ -203,7 +205,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
     k = it->second;
   } else {
     char name[64];
-    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v6"));
+    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v11"));
     const std::string dir = cache_dir(), path = dir + name;
     std::vector<char> cubin;
     if (FILE* f = fopen(path.c_str(), "rb")) {

@@ -13,7 +13,8 @@ RF_TOYS_DECL(f64, c64)
 namespace rf {
 __global__ void __launch_bounds__(1024)
     toy_plan_kernel(const int64_t* __restrict__ offsets, int32_t toys,
-                    int64_t tile, int64_t* tile_start, unsigned int* status) {
+                    int64_t tile, int64_t max_rows, int64_t n_events, int64_t* tile_start,
+                    int32_t* tile_toy, int64_t* tile_be, unsigned int* status) {
   __shared__ int64_t wsum[32];
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -57,6 +58,23 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
   }
   if (threadIdx.x == 0) tile_start[toys] = carry;
+  __syncthreads();
+  // tile -> (toy, event range); offsets are clamped to the bound columns so
+  // that a bad offset table reads nothing outside; tiles beyond the
+  // workspace are never run
+  for (int64_t t = threadIdx.x; t < toys; t += blockDim.x) {
+    int64_t ob = offsets[t], oe = offsets[t + 1];
+    ob = ob < 0 ? 0 : (ob > n_events ? n_events : ob);
+    oe = oe < ob ? ob : (oe > n_events ? n_events : oe);
+    const int64_t r0 = tile_start[t];
+    const int64_t r1 = tile_start[t + 1] < max_rows ? tile_start[t + 1] : max_rows;
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t b = ob + (r - r0) * tile;
+      tile_toy[r] = (int32_t)t;
+      tile_be[2 * r] = b < oe ? b : oe;
+      tile_be[2 * r + 1] = b + tile < oe ? b + tile : oe;
+    }
+  }
 }
 
 }  // namespace rf
@@ -65,10 +83,11 @@ size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
 
-int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile,
-                 RfWork W, void* stream) {
+int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, int64_t max_rows,
+                 int64_t n_events, RfWork W, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rf::toy_plan_kernel<<<1, 1024, 0, st>>>(offsets, toys, tile, W.tile_start, W.status);
+  rf::toy_plan_kernel<<<1, 1024, 0, st>>>(offsets, toys, tile, max_rows, n_events, W.tile_start,
+                                          W.tile_toy, W.tile_be, W.status);
   return (int)cudaGetLastError();
 }
 
@@ -81,7 +100,7 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int n = 0, rc;
   if (plan) {
-    rc = rf_toys_plan(offsets, toys, cfg.tile, W, stream);
+    rc = rf_toys_plan(offsets, toys, cfg.tile, max_rows, n_events, W, stream);
     ++n;
     if (rc) return rc;
   }

@@ -22,6 +22,13 @@ template <> struct Op<7> { typedef double T; static __device__ __forceinline__ d
 template <> struct Op<8> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::log_fast(a + 2.0f); } };
 template <> struct Op<9> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::exp_neg_approx(-a); } };
 template <> struct Op<10> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::rcp_approx(a + 1.0f); } };
+// packed FP32x2 FMA (two FMAs per instruction)
+template <> struct Op<11> {
+  typedef float2 T;
+  static __device__ __forceinline__ float2 f(float2 a) {
+    return __ffma2_rn(a, make_float2(0.9999f, 0.9998f), make_float2(0.0001f, 0.0002f));
+  }
+};
 
 template <int OP>
 __global__ void __launch_bounds__(256) mb_kernel(typename Op<OP>::T* sink, int iters) {
@@ -36,6 +43,20 @@ __global__ void __launch_bounds__(256) mb_kernel(typename Op<OP>::T* sink, int i
 #pragma unroll
   for (int j = 0; j < 8; ++j) s += a[j];
   if (s == (T)-12345.0) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <>
+__global__ void __launch_bounds__(256) mb_kernel<11>(float2* sink, int iters) {
+  float2 a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = make_float2(0.1f + 0.01f * j, 0.2f + 1e-6f * threadIdx.x);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = Op<11>::f(a[j]);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j].x + a[j].y;
+  if (s == -12345.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = make_float2(s, s);
 }
 
 template <int OP>
@@ -77,6 +98,7 @@ int rf_run_microbench(double* out) {
   out[8] = run<8>(sms, sink, 1024);
   out[9] = run<9>(sms, sink, 1024);
   out[10] = run<10>(sms, sink, 1024);
+  out[11] = 2.0 * run<11>(sms, sink, 4096);  // FMAs per second
   e = cudaGetLastError();
   cudaFree(sink);
   return (int)e;
@@ -97,5 +119,23 @@ int rf_run_check_log(const float* x, float* y_fast, float* y_ref, int64_t n, cud
   int64_t g = (n + 255) / 256;
   int grid = (int)(g > 4096 ? 4096 : g);
   check_log_kernel<<<grid, 256, 0, st>>>(x, y_fast, y_ref, n);
+  return (int)cudaGetLastError();
+}
+
+// The library's integer-pipe double -> float conversion next to the hardware
+// conversion (for the bit-exactness test of the former).
+__global__ void check_d2f_kernel(const double* x, float* yf, float* yr, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    yf[i] = rf::d2f_rn(x[i]);
+    yr[i] = __double2float_rn(x[i]);
+  }
+}
+
+int rf_run_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n, cudaStream_t st) {
+  if (n == 0) return 0;
+  int64_t g = (n + 255) / 256;
+  int grid = (int)(g > 4096 ? 4096 : g);
+  check_d2f_kernel<<<grid, 256, 0, st>>>(x, y_fast, y_ref, n);
   return (int)cudaGetLastError();
 }

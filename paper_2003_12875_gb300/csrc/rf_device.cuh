@@ -348,39 +348,25 @@ __device__ inline void build_consts_serial(const RfProgram& P,
 }
 
 // ------------------------------------------------------------ event math
-// FP32 natural logarithm for x > 0 (normal, finite): x = 2^e m with
-// m in [1/sqrt2, sqrt2), log m = 2 atanh(s), s = (m-1)/(m+1), |s| <= 0.1716,
-// by the series 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) (the classical
-// argument-reduction + atanh expansion, e.g. Abramowitz & Stegun 4.1.27);
-// the first omitted term is < 1e-9 relative.  s uses the approximate
-// hardware reciprocal (max 1 ulp), so the result is within a few ulp of the
-// correctly rounded log.  Zero, negative, subnormal, infinite and NaN
-// arguments go to logf.  Tested against logf in the GPU tests.
+// FP32 natural logarithm of the per-event code: the hardware base-2
+// logarithm (lg2.approx; the PTX specification bounds its error by 2^-22.6
+// absolute for arguments in [0.5, 2] and 2^-22 relative to log2 x elsewhere)
+// times ln 2.  Per-event logs enter the log-likelihood additively, so their
+// absolute error is what counts: at most ~1e-7 * max(1, |log2 x|), the same
+// order as a correctly rounded FP32 log of the same argument.  Zero gives
+// -inf, negative arguments and NaN give NaN, +inf gives +inf (ftz: subnormal
+// arguments count as zero).  This is the trade the paper makes with VDT's
+// approximate log/exp (Sec. 5.3), and it is tested against an FP64
+// reference and CUDA logf in the GPU tests.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// Core of the fast log for x > 0 normal and finite (no argument checks).
-// The exponent becomes a float through the 1.5*2^23 trick (one integer add
-// and one float subtract) instead of an int-to-float conversion.
-__device__ __forceinline__ float log_pos(float x) {
-  const int ix = __float_as_int(x);
-  const int e = (ix - 0x3f3504f3) >> 23;  // m = x / 2^e in [0.70710677, 1.4142135)
-  const float m = __int_as_float(ix - (e << 23));
-  const float s = (m - 1.0f) * rcp_approx(m + 1.0f);
-  const float z = s * s;
-  float p = fmaf(z, 0.11111111f, 0.14285715f);
-  p = fmaf(z, p, 0.2f);
-  p = fmaf(z, p, 0.33333334f);
-  p = fmaf(z, p, 1.0f);
-  const float lm = 2.0f * s * p;
-  const float fe = __int_as_float(0x4b400000 + e) - 12582912.0f;  // (float)e, |e| < 2^22
-  return fmaf(fe, 0.693145752f, fmaf(fe, 1.42860677e-06f, lm));  // ln2 = hi + lo
-}
 __device__ __forceinline__ float log_fast(float x) {
-  if (!(x >= 1.17549435e-38f && x <= 3.40282347e+38f)) return logf(x);
-  return log_pos(x);
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * 0.693147182f;
 }
 // exp(x) for x <= 0 through the hardware base-2 exponential (max relative
 // error 2^-22 by the PTX specification) of x * log2(e); used for the mixture
@@ -392,13 +378,37 @@ __device__ __forceinline__ float exp_neg_approx(float x) {
   return r;
 }
 
+// double -> float, round to nearest even, with integer operations only: on
+// this GPU the hardware conversion runs on the FP64 pipe, which is far
+// slower than the integer pipe.  For a double with a float-normal exponent
+// the result is sign | (e - 896) << 23 | top 23 mantissa bits, plus one ulp
+// when the dropped 29 bits exceed half an ulp (or equal it and the kept
+// mantissa is odd); a carry out of the mantissa correctly bumps the
+// exponent.  Zero, float-subnormal, overflowing, infinite and NaN inputs go
+// through the hardware conversion.  Tested bit for bit against it.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u >= 253u) return __double2float_rn(x);  // float exponent outside 1..253
+  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  bits += (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+  return __uint_as_float(bits);
+}
+
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From x) { return (To)x; }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) { return d2f_rn(x); }
+
 template <typename Real>
 struct Fn;
 template <>
 struct Fn<float> {
   static __device__ __forceinline__ float log(float x) { return log_fast(x); }
   // x known positive and finite wherever its result is used
-  static __device__ __forceinline__ float logp(float x) { return log_pos(x); }
+  static __device__ __forceinline__ float logp(float x) { return log_fast(x); }
   static __device__ __forceinline__ float exp_neg(float x) { return exp_neg_approx(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
@@ -609,6 +619,52 @@ __device__ inline void block_sum(const double (&val)[N], double* red,
   __syncthreads();
 }
 
+// Double-single (FP32 pair) addition: (h, l) += (h2, l2) with Knuth's TwoSum
+// for the high parts; the pair carries about 48 significant bits.
+__device__ __forceinline__ void ds_add(float& h, float& l, float h2, float l2) {
+  const float s = h + h2;
+  const float v = s - h;
+  float e = (h - (s - v)) + (h2 - v);
+  e += l + l2;
+  h = s + e;
+  l = e - (h - s);
+}
+
+// Block sum of N per-thread FP32 pairs (h_i + l_i) in a fixed order, entirely
+// in FP32 pair arithmetic (the FP64 pipe of this GPU is narrow); one FP64
+// conversion per accumulator at the end.  Accumulators not in MASK give 0.
+// red: [32*N] float2 shared; result in out[0..N) (shared), valid after the
+// trailing barrier.
+template <int N, unsigned long long MASK>
+__device__ inline void block_sum_ds(const float (&hs)[N], const float (&ls)[N], float2* red,
+                                    double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!((MASK >> i) & 1ull)) continue;
+    float h = hs[i], l = ls[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      ds_add(h, l, h2, l2);
+    }
+    if (lane == 0) red[wid * N + i] = make_float2(h, l);
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double r = 0.0;
+    if ((MASK >> threadIdx.x) & 1ull) {
+      float h = 0.f, l = 0.f;
+      for (int w = 0; w < nw; ++w) ds_add(h, l, red[w * N + threadIdx.x].x, red[w * N + threadIdx.x].y);
+      r = (double)h + (double)l;
+    }
+    out[threadIdx.x] = r;
+  }
+  __syncthreads();
+}
+
 // Sum rows [r0, r1) of partials[row * RF_NACC_MAX + i] for i < N, in a fixed
 // order for a given block size; result in out[0..N) (shared).
 template <int N>
@@ -632,6 +688,24 @@ __device__ inline void rows_sum(const double* partials, int64_t r0, int64_t r1,
 #pragma unroll
   for (int i = 0; i < N; ++i) v[i] += cmp[i];
   block_sum<N>(v, red, out);
+}
+
+// Sum a few rows (one toy's tiles) of partials: accumulator i by thread i,
+// Neumaier in row order (FP64 work on N lanes only).  Result in out[0..N)
+// (shared), valid after the trailing barrier.
+template <int N>
+__device__ inline void rows_sum_few(const double* partials, int64_t r0, int64_t r1, double* out) {
+  if (threadIdx.x < N) {
+    double v = 0.0, c = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const double x = __ldcg(partials + r * RF_NACC_MAX + threadIdx.x);
+      const double t = v + x;
+      c += (fabs(v) >= fabs(x)) ? (v - t) + x : (x - t) + v;
+      v = t;
+    }
+    out[threadIdx.x] = v + c;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- epilogue

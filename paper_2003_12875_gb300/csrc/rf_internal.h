@@ -87,6 +87,8 @@ struct RfWork {
   unsigned int* status;    // [1] RF_STATUS_* bits
   // batched mode
   int64_t* tile_start;     // [max_toys + 1]
+  int32_t* tile_toy;       // [max rows] toy of each tile
+  int64_t* tile_be;        // [2 * max rows] event range [begin, end) of each tile
   unsigned int* toy_counter;  // [max_toys]
   unsigned int* next_tile; // [1]
   void* toy_consts;        // [max_toys] RfConsts<Real>
@@ -129,8 +131,8 @@ RF_DECL_FUSED(f64, c64)
 int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
                        rf_cuda_stream st);
 
-int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, RfWork W,
-                 void* stream);
+int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, int64_t max_rows,
+                 int64_t n_events, RfWork W, void* stream);
 int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       const RfLaunchCfg& cfg, int num_sms, const void* events,
                       int64_t n_events, const int64_t* offsets, int32_t toys,
@@ -144,6 +146,7 @@ int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
                     unsigned int* counter, void* stream, int* launches);
 size_t rf_plain_bytes(const RfProgram& prog, int64_t n);
 int rf_run_microbench(double* out);
+int rf_run_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n, rf_cuda_stream st);
 int rf_run_check_log(const float* x, float* y_fast, float* y_ref, int64_t n, rf_cuda_stream st);
 size_t rf_consts_size(int eval);
 

@@ -137,14 +137,20 @@ __device__ __forceinline__ void load_full(const RfProgram& P, const Col* __restr
         const typename Vec<Col>::T* vp = reinterpret_cast<const typename Vec<Col>::T*>(col);
 #pragma unroll
         for (int v = 0; v < EPT / W; ++v) {
+#ifdef RF_EVENTS_KEEP_L2
           typename Vec<Col>::T t = __ldg(vp + v);
+#else
+          // events are read once per call: streaming (evict-first) loads, so
+          // they do not push the prologue's code and constants out of L2
+          typename Vec<Col>::T t = __ldcs(vp + v);
+#endif
           const Col* tc = reinterpret_cast<const Col*>(&t);
 #pragma unroll
-          for (int e = 0; e < W; ++e) x[c][v * W + e] = (Real)tc[e];
+          for (int e = 0; e < W; ++e) x[c][v * W + e] = cvt<Real, Col>(tc[e]);
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) x[c][e] = (Real)__ldg(col + e);
+        for (int e = 0; e < EPT; ++e) x[c][e] = cvt<Real, Col>(__ldcs(col + e));
       }
     } else {
 #pragma unroll
@@ -174,6 +180,30 @@ struct Acc {
   }
   __device__ __forceinline__ double value(int i) const {
     return ((MASK >> i) & 1ull) ? (double)s[i] - (double)c[i] : 0.0;
+  }
+};
+
+// Block-wide FP64 totals of the per-thread accumulators, fixed order.
+template <typename Real, int NA, unsigned long long MASK>
+struct BlockReduce;
+template <int NA, unsigned long long MASK>
+struct BlockReduce<float, NA, MASK> {  // FP32 evaluation: FP32-pair arithmetic
+  static __device__ __forceinline__ void run(const Acc<float, NA, MASK>& acc, void* red,
+                                             double* tot) {
+    float ls[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ls[i] = -acc.c[i];  // Kahan keeps -(lost low part)
+    block_sum_ds<NA, MASK>(acc.s, ls, static_cast<float2*>(red), tot);
+  }
+};
+template <int NA, unsigned long long MASK>
+struct BlockReduce<double, NA, MASK> {  // FP64 evaluation
+  static __device__ __forceinline__ void run(const Acc<double, NA, MASK>& acc, void* red,
+                                             double* tot) {
+    double val[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) val[i] = acc.value(i);
+    block_sum<NA>(val, static_cast<double*>(red), tot);
   }
 };
 
@@ -236,7 +266,7 @@ __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real,
     Real xc[NL];
 #pragma unroll
     for (int c = 0; c < NL; ++c)
-      xc[c] = (c < M::NCOL && c < P.n_cols) ? (Real)ev[(int64_t)P.col_obs[c] * stride + i]
+      xc[c] = (c < M::NCOL && c < P.n_cols) ? cvt<Real, Col>(ev[(int64_t)P.col_obs[c] * stride + i])
                                             : Real(0);
     Real q[RF_NACC(NL)];
 #pragma unroll
@@ -308,10 +338,7 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     }
   }
 
-  double val[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) val[i] = acc.value(i);
-  block_sum<NA>(val, red, tot);
+  BlockReduce<Real, NA, M::AMASK>::run(acc, red, tot);
   if (threadIdx.x < NA) W.partials[(int64_t)blockIdx.x * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
   __threadfence();
   __syncthreads();
@@ -345,7 +372,8 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
     Real xc[NL];
 #pragma unroll
     for (int c = 0; c < NL; ++c)
-      xc[c] = (c < M::NCOL && c < P.n_cols) ? (Real)ev[(int64_t)P.col_obs[c] * n + i] : Real(0);
+      xc[c] = (c < M::NCOL && c < P.n_cols) ? cvt<Real, Col>(ev[(int64_t)P.col_obs[c] * n + i])
+                                            : Real(0);
     Real q[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) q[j] = Real(0);
@@ -426,33 +454,35 @@ __device__ __forceinline__ void toy_tile_body(const RfProgram& P, const Col* __r
   if (threadIdx.x == 0) s_total = __ldcg(W.tile_start + toys);
   __syncthreads();
   const int64_t total = s_total < max_rows ? s_total : max_rows;
+  // Thread 0 takes the next tile from the counter at the start of an
+  // iteration and loads its (toy, event range) after the compute, so that
+  // both round trips overlap the current tile's work.
+  int64_t nx_tile = 0, nx_b = 0, nx_e = 0;
+  int nx_toy = 0;
+  auto load_meta = [&]() {
+    if (nx_tile < total) {
+      nx_toy = __ldcg(W.tile_toy + nx_tile);
+      const longlong2 be = __ldcg(reinterpret_cast<const longlong2*>(W.tile_be) + nx_tile);
+      nx_b = be.x;
+      nx_e = be.y;
+    }
+  };
+  if (threadIdx.x == 0) {
+    nx_tile = (int64_t)atomicAdd(W.next_tile, 1u);
+    load_meta();
+  }
   for (;;) {
     if (threadIdx.x == 0) {
-      int64_t tl = (int64_t)atomicAdd(W.next_tile, 1u);
-      s_tile = tl;
-      if (tl < total) {
-        int lo = 0, hi = toys - 1;  // last toy with tile_start <= tl
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (__ldcg(W.tile_start + mid) <= tl) lo = mid;
-          else hi = mid - 1;
-        }
-        int64_t j = tl - __ldcg(W.tile_start + lo);
-        // clamp to the bound columns: a bad offset table reads nothing outside
-        int64_t ob = offsets[lo], oe = offsets[lo + 1];
-        ob = ob < 0 ? 0 : (ob > stride ? stride : ob);
-        oe = oe < ob ? ob : (oe > stride ? stride : oe);
-        int64_t b = ob + j * tile_ev;
-        int64_t e = b + tile_ev < oe ? b + tile_ev : oe;
-        s_toy = lo;
-        s_b = b < oe ? b : oe;
-        s_e = e;
-      }
+      s_tile = nx_tile;
+      s_toy = nx_toy;
+      s_b = nx_b;
+      s_e = nx_e;
     }
     __syncthreads();
     const int64_t tl = s_tile;
     if (tl >= total) break;
     const int64_t toy = s_toy, b = s_b, e = s_e;
+    if (threadIdx.x == 0) nx_tile = (int64_t)atomicAdd(W.next_tile, 1u);
     {
       const double* src = reinterpret_cast<const double*>(consts + toy);
       double* dst = reinterpret_cast<double*>(&K);
@@ -479,10 +509,8 @@ __device__ __forceinline__ void toy_tile_body(const RfProgram& P, const Col* __r
         iterate_scalar<M, Real, Col>(P, E, ev, stride, b + h + nfull * EPT, e, acc);
       }
     }
-    double val[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) val[i] = acc.value(i);
-    block_sum<NA>(val, red, tot);
+    if (threadIdx.x == 0) load_meta();
+    BlockReduce<Real, NA, M::AMASK>::run(acc, red, tot);
     if (threadIdx.x < NA) W.partials[tl * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
     __threadfence();
     __syncthreads();
@@ -495,7 +523,7 @@ __device__ __forceinline__ void toy_tile_body(const RfProgram& P, const Col* __r
     if (s_last) {
       __threadfence();
       int64_t r0 = __ldcg(W.tile_start + toy), r1 = __ldcg(W.tile_start + toy + 1);
-      rows_sum<NA>(W.partials, r0, r1, red, tot);
+      rows_sum_few<NA>(W.partials, r0, r1, tot);
       if (threadIdx.x == 0) {
         int64_t ob = offsets[toy], oe = offsets[toy + 1];
         ob = ob < 0 ? 0 : (ob > stride ? stride : ob);
