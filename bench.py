@@ -46,6 +46,9 @@ def peaks():
     return d
 
 
+L2_BYTES = 129 << 20
+
+
 def make_workload(name):
     import datagen
     if name == "c5":
@@ -126,10 +129,10 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
 # leaf type -> (base, extra per wanted derivative by leaf-parameter index,
 #               shared extra when any derivative is wanted)
 LEAF_INSTR = {
-    "gauss": (5, {0: 1, 1: 2}, 0),
+    "gauss": (5, {0: 0, 1: 1}, 0),
     "exp": (3, {0: 0}, 0),
     "cheb": (13, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
-    "cb": (12, {0: 1, 1: 2, 2: 4, 3: 3}, 3),
+    "cb": (12, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
     "argus": (14, {0: 5, 1: 1}, 0),
 }
 LOG_INSTR = 2          # hardware log2 and a multiply by ln 2
@@ -226,6 +229,65 @@ def toy_study(rf, torch, toys=4096, iters=50):
                      "events_per_s": res["events"] / (t_eval * 1e-3),
                      "fit_ms": t_fit, "fit_toy_iters_per_s": toys * iters / (t_fit * 1e-3),
                      "launches_per_fit": G.last_launches(), "kernel": G.uses_jit()}
+    return res
+
+
+def small_configs(rf, torch):
+    """Per-call latency of the small workloads (C1 1e4, C2 1e6, C3 1e7 events):
+    a host loop of calls on one stream, and the same calls replayed from a
+    CUDA graph (GPU time only); C2 (8 MB, L2-resident) also with L2 flushed
+    before every call.  FP32 evaluation, plus FP64 evaluation for C1 and C2."""
+    import numpy as np
+
+    res = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for name, precs in (("c1", ("fp64", "fp32")), ("c2", ("fp64", "fp32")), ("c3", ("fp32",))):
+        w = make_workload(name)
+        ev = torch.from_numpy(np.ascontiguousarray(w["cols"])).cuda()
+        n = w["cols"].shape[1]
+        params = torch.tensor(w["spec"]["params"], dtype=torch.float64, device="cuda")
+        for prec in precs:
+            G = rf.Graph(w["spec"], w["dtype"], prec)
+            out = torch.empty(1 + len(w["spec"]["params"]), dtype=torch.float64, device="cuda")
+            for _ in range(20):
+                G.nll(ev, params, out=out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = 200
+            a.record()
+            for _ in range(k):
+                G.nll(ev, params, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            r = {"events": n, "stream_us": a.elapsed_time(b) * 1e3 / k}
+            try:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    for _ in range(20):
+                        G.nll(ev, params, out=out)
+                g.replay()
+                torch.cuda.synchronize()
+                a.record()
+                for _ in range(10):
+                    g.replay()
+                b.record()
+                torch.cuda.synchronize()
+                r["graph_us"] = a.elapsed_time(b) * 1e3 / 200
+            except Exception as exc:  # capture unsupported here: report why
+                r["graph_us"] = None
+                r["graph_error"] = str(exc)[:200]
+            if name == "c2":
+                ts = []
+                for _ in range(20):
+                    flush.zero_()
+                    a.record()
+                    G.nll(ev, params, out=out)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b) * 1e3)
+                r["cold_us_median"] = statistics.median(ts)
+            r["events_per_s_graph"] = n / (r["graph_us"] * 1e-6) if r.get("graph_us") else None
+            res[f"{name}_{prec}"] = r
     return res
 
 
@@ -372,11 +434,19 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
+    # inputs smaller than twice the L2 are flushed before every step (a
+    # 256 MB write outside the per-step events) and the step time is the sum
+    # of the per-step events
+    in_bytes = n * w["cols"].shape[0] * col_bytes
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda") \
+        if in_bytes < 2 * L2_BYTES else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_all0.record(stream)
     for i in range(args.steps):
+        if flush is not None:
+            flush.zero_()
         starts[i].record(stream)
         G.nll(ev, params, out=out)
         ends[i].record(stream)
@@ -385,8 +455,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(launch_ms) if flush is not None else t_all0.elapsed_time(t_all1)
     per_launch = statistics.mean(launch_ms)
     launches_per_step = G.last_launches()
     total_ms = max_over_ranks(total_ms, dist, "cuda")
@@ -447,8 +517,10 @@ def main():
                        "column_dtype": w["dtype"], "eval": args.precision,
                        "free_params": sum(1 for f in (spec.get("fixed") or []) if not f)
                        or len(spec["params"]),
-                       "l2": f"inputs larger than L2 ({bytes_per_launch / 1e6:.0f} MB > 129 MB), "
-                             "no flush",
+                       "l2": (f"inputs larger than L2 ({bytes_per_launch / 1e6:.0f} MB > 2 x 129 MB), "
+                              "no flush") if flush is None else
+                             (f"inputs {bytes_per_launch / 1e6:.1f} MB: L2 flushed (256 MB write) "
+                              "before every step, step time = sum of per-step events"),
                        "launch": G.get_launch(), "tuned_ms": tuned_ms,
                        "kernel": "specialised (NVRTC)" if G.uses_jit() else "generic",
                        "regs_per_thread": G.kernel_regs(),
@@ -491,6 +563,7 @@ def main():
         torch.cuda.synchronize()
         ex["plain_fp64_nll_only_ms"] = a.elapsed_time(b)
         ex["microbench_ops_per_s"] = rf.microbench()
+        ex["small_configs"] = small_configs(rf, torch)
         ex["toys"] = toy_study(rf, torch)
         line["extras"] = ex
 
@@ -501,6 +574,11 @@ def main():
                                 "sample": f"first {sample} of {n} events, one pass, "
                                           f"FP64 NLL + analytic gradient ({dt:.2f} s wall, "
                                           f"{cores} threads)"}
+        s1 = min(n, 10_000_000)
+        r1, _, dt1 = cpu_oracle_rate(w, s1, nthreads=1)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": r1, "unit": "events/s", "cores": 1,
+            "sample": f"first {s1} of {n} events, one pass ({dt1:.2f} s wall)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -31,7 +31,7 @@
  * Memory: every pointer argument marked "dev" is caller-owned device memory
  * (e.g. a torch tensor).  Event columns are structure-of-arrays: observable j
  * of event i is at events[j*n_events + i], FP32 or FP64 as the descriptor says.
- * The graph owns its workspace (block partials, tickets, tile tables), sized
+ * The graph owns its workspace (block and segment partials, tickets), sized
  * at compile / bind time; rf_nll and rf_nll_batched allocate nothing and never
  * synchronise the host, so they may be captured in a CUDA graph.
  *
@@ -84,7 +84,10 @@ enum { RF_EVAL_FP32 = 0, RF_EVAL_FP64 = 1 }; /* per-event arithmetic      */
 /* status bits (rf_graph_status) */
 enum {
   RF_STATUS_PARAM_DOMAIN = 1u, /* a parameter outside its definition range */
-  RF_STATUS_NONFINITE = 2u     /* an event with P <= 0 or a non-finite log P */
+  RF_STATUS_NONFINITE = 2u,    /* an event with P <= 0 or a non-finite log P */
+  RF_STATUS_TIMEOUT = 4u       /* a bounded wait inside a kernel gave up (an event
+                                  copy did not arrive); that call's results are
+                                  not valid */
 };
 
 #define RF_MAX_CHILDREN 8
@@ -158,16 +161,23 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events,
 /* Toy studies (RooStats-style, Sec. 1): many datasets of uneven size that
  * share one graph.  rf_graph_bind_events records the concatenated event
  * columns (dev; column j at events + j*n_events); toy t owns events
- * [offsets[t], offsets[t+1]).  Sizes the tile workspace for up to max_toys. */
+ * [offsets[t], offsets[t+1]).  Sizes the toy workspace for up to max_toys. */
 rf_status rf_graph_bind_events(rf_graph* g, const void* events,
                                int64_t n_events, int32_t max_toys);
 
 /*   offsets        dev int64 [toys+1], non-decreasing, offsets[toys] <= n_events
  *   params_matrix  dev FP64 [toys * n_params], row t = toy t's parameters
  *   out            dev FP64 [toys * (1 + n_params)], row t = (NLL_t, grad_t)
- * A tile plan, a per-toy FP64 prologue, and one persistent kernel over tiles
- * that never straddle a toy; the last tile of each toy reduces that toy in
- * fixed order.  No allocation, no host sync: capturable. */
+ * Three kernels: a per-toy FP64 prologue (one thread per toy); a segment
+ * kernel that splits all toys' events [offsets[0], offsets[toys]) evenly over
+ * its warps (one grid of SMs x blocks_per_sm blocks) and writes one FP64 row
+ * of partial sums per (warp, toy) pair that share events; and a finalize
+ * kernel, one warp per toy, that sums the toy's rows in a fixed order and
+ * writes (NLL, grad).  Results depend on the inputs and the launch shape
+ * only.  Offsets outside [0, n_events] are clamped and a decreasing pair
+ * raises RF_STATUS_NONFINITE (the affected toys' results are then
+ * meaningless, but nothing outside the bound columns is read).  No
+ * allocation, no host sync: capturable. */
 rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
                          const double* params_matrix, double* out,
                          rf_stream stream);
@@ -177,8 +187,8 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
  * [toys * n_params]; e.g. each toy's starting |theta|), learning rate lr,
  * beta = (0.9, 0.999), eps = 1e-8; fixed parameters do not move, and a toy
  * whose NLL is not finite keeps its parameters for that step.  The
- * per-iteration work (prologue + tile kernel with the Adam step fused into
- * each toy's final reduction) is captured once into a CUDA graph and
+ * per-iteration work (the three kernels of rf_nll_batched, the Adam step
+ * fused into the finalize kernel) is captured once into a CUDA graph and
  * replayed `iters` times.  params_matrix (dev) is updated in place; out
  * (dev [toys*(1+n_params)]) holds the NLL and gradient of the last
  * evaluation (at the parameters before the last step).  Host-synchronous. */
@@ -196,14 +206,14 @@ rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events,
                        const double* params, double* nll, double* grad,
                        rf_stream stream);
 
-/* Launch configuration of the fused kernel: threads per block (64, 128 or
- * 256), events per thread per iteration (FP32 eval: 4 or 8; FP64 eval: 2 or
- * 4) and resident blocks per SM used to size the grid (1..8). */
+/* Launch configuration of the fused and segment kernels: threads per block
+ * (64, 128 or 256), events per thread per iteration (FP32 eval: 4 or 8;
+ * FP64 eval: 2 or 4) and resident blocks per SM used to size the grid
+ * (1..8). */
 typedef struct {
   int32_t block;
   int32_t ept;
   int32_t blocks_per_sm;
-  int32_t tile; /* batched mode: events per tile, >= 1024 (default 32768) */
 } rf_launch;
 
 rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg);
@@ -286,7 +296,10 @@ rf_status rf_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n,
  * out[4] FP64 FMA, out[5] exp (FP64), out[6] log (FP64), out[7] erf (FP64),
  * out[8] the library's FP32 log, out[9] its FP32 exp(-x) (x >= 0),
  * out[10] the approximate FP32 reciprocal, out[11] FP32 FMAs/s issued as
- * packed FP32x2 FMA instructions.  out has 12 entries.
+ * packed FP32x2 FMA instructions; then latencies in ns per dependent
+ * operation within one warp: out[12] FP64 FMA with 1 active lane, out[13]
+ * FP64 FMA with 32 active lanes, out[14] exp (FP64) with 1 lane, out[15]
+ * exp (FP64) with 32 lanes.  out has 16 entries.
  * Host-synchronous; allocates a small scratch buffer. */
 rf_status rf_microbench(double* out);
 

@@ -58,8 +58,7 @@ class _Desc(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("block", C.c_int32), ("ept", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("tile", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("ept", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
 _lib = None
@@ -331,12 +330,12 @@ class Graph:
     def get_launch(self) -> dict:
         c = _Launch()
         _check(load().rf_graph_get_launch(self._h, C.byref(c)))
-        return {"block": c.block, "ept": c.ept, "blocks_per_sm": c.blocks_per_sm, "tile": c.tile}
+        return {"block": c.block, "ept": c.ept, "blocks_per_sm": c.blocks_per_sm}
 
-    def set_launch(self, block=None, ept=None, blocks_per_sm=None, tile=None):
+    def set_launch(self, block=None, ept=None, blocks_per_sm=None):
         cur = self.get_launch()
         c = _Launch(block or cur["block"], ept or cur["ept"],
-                    blocks_per_sm or cur["blocks_per_sm"], tile or cur["tile"])
+                    blocks_per_sm or cur["blocks_per_sm"])
         _check(load().rf_graph_set_launch(self._h, C.byref(c)))
 
     def tune(self, events: torch.Tensor, params: torch.Tensor) -> float:
@@ -386,9 +385,12 @@ class RFNll(torch.autograd.Function):
 
 
 def microbench() -> dict:
-    """Measured per-operation throughput (operations/s) on the current GPU."""
-    out = (C.c_double * 12)()
+    """Measured per-operation throughput (operations/s) on the current GPU,
+    and single-warp FP64 latencies (ns per dependent operation)."""
+    out = (C.c_double * 16)()
     _check(load().rf_microbench(out))
     keys = ["fp32_fma", "expf", "logf", "rcp_f32", "fp64_fma", "exp_f64", "log_f64", "erf_f64",
-            "log_fast_f32", "exp_neg_f32", "rcp_approx_f32", "fp32_fma_packed_x2"]
+            "log_fast_f32", "exp_neg_f32", "rcp_approx_f32", "fp32_fma_packed_x2",
+            "fp64_fma_latency_ns_1lane", "fp64_fma_latency_ns_32lanes",
+            "exp_f64_latency_ns_1lane", "exp_f64_latency_ns_32lanes"]
     return dict(zip(keys, list(out)))

@@ -216,14 +216,15 @@ struct rf_graph {
   RfProgram prog;
   int eval = 0, coldt = 0, n_obs = 0;
   int device = 0, num_sms = 0;
-  RfLaunchCfg cfg{256, 4, 2, 32768};
+  RfLaunchCfg cfg{256, 4, 2};
   RfWork work{};
   int64_t max_rows_single = 0;
   // batched
   const void* bound_events = nullptr;
+  bool bound = false;
   int64_t bound_n = 0;
   int32_t max_toys = 0;
-  int64_t max_tile_rows = 0;
+  int64_t max_toy_rows = 0;  // segment rows: launch warps + toys
   // host staging
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -260,18 +261,26 @@ static cudaKernel_t jit_fused(rf_graph* g, int ept, std::string* err) {
 
 static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
   int i = ept_index(g->eval, g->coldt, ept);
-  if (!g->jk_toys[i])
-    g->jk_toys[i] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_TOYS, ept, nullptr, err);
+  if (!g->jk_toys[i]) {
+    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_TOYS, ept, nullptr, err);
+    if (k) {  // its stage ring may use more than 48 KB of shared memory
+      int optin = 0;
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) {
+        *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return nullptr;
+      }
+    }
+    g->jk_toys[i] = k;
+  }
   return g->jk_toys[i];
 }
 
 static void free_work(rf_graph* g) {
   cudaFree(g->work.partials);
   cudaFree(g->work.counter);
-  cudaFree(g->work.tile_start);
-  cudaFree(g->work.tile_toy);
-  cudaFree(g->work.tile_be);
-  cudaFree(g->work.toy_counter);
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
@@ -336,7 +345,7 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
     return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
   }
   g->work.status = g->work.counter + 1;
-  g->work.next_tile = g->work.counter + 2;
+  g->work.adam_t = reinterpret_cast<int32_t*>(g->work.counter + 2);
   g->work.pro_ticket = g->work.counter + 3;
   // constants of the separate prologue kernel
   e = cudaMalloc(&g->pro_buf, rf_consts_size(g->eval) + sizeof(double) * RF_MAXL +
@@ -553,59 +562,49 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   if (max_toys < 1) return fail(RF_EINVAL, "max_toys must be >= 1");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "rf_graph_bind_events sync");
-  cudaFree(g->work.tile_start);
-  cudaFree(g->work.tile_toy);
-  cudaFree(g->work.tile_be);
-  cudaFree(g->work.toy_counter);
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
-  g->work.tile_start = nullptr;
-  g->work.tile_toy = nullptr;
-  g->work.tile_be = nullptr;
-  g->work.toy_counter = nullptr;
   g->work.toy_consts = nullptr;
   g->work.adam_m1 = g->work.adam_m2 = nullptr;
-  g->work.adam_t = nullptr;
-  // tiles hold at least 1024 events, so rows <= toys + n/1024 + 1
-  int64_t rows = (int64_t)max_toys + n_events / 1024 + 1;
-  int64_t have_rows = g->max_rows_single;
-  if (rows > have_rows) {
+  g->bound = false;
+  g->max_toys = 0;
+  // one row per (warp, toy) segment: at most (launch warps) + toys, and a
+  // launch has at most 8 blocks of 8 warps per SM
+  const int64_t rows = (int64_t)max_toys + (int64_t)g->num_sms * 64;
+  if (rows > g->max_rows_single) {
     cudaFree(g->work.partials);
     g->work.partials = nullptr;
     e = cudaMalloc(&g->work.partials, sizeof(double) * RF_NACC_MAX * rows);
-    if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: partials allocation failed");
+    if (e != cudaSuccess) {
+      g->max_rows_single = 0;
+      return fail(RF_ENOMEM, "bind: partials allocation failed");
+    }
     g->max_rows_single = rows;
   }
   const size_t np = (size_t)std::max(g->prog.n_par, 1);
-  e = cudaMalloc(&g->work.tile_start, sizeof(int64_t) * ((size_t)max_toys + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&g->work.tile_toy, sizeof(int32_t) * (size_t)rows);
-  if (e == cudaSuccess) e = cudaMalloc(&g->work.tile_be, 2 * sizeof(int64_t) * (size_t)rows);
-  if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_counter, sizeof(unsigned int) * (size_t)max_toys + 8);
-  if (e == cudaSuccess) e = cudaMemset(g->work.toy_counter, 0, sizeof(unsigned int) * (size_t)max_toys + 8);
-  if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
+  e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m1, sizeof(double) * np * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
   if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
-  g->work.adam_t = reinterpret_cast<int32_t*>(g->work.toy_counter + max_toys);
   if (g->jit) {
     std::string err;
     if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
   g->bound_events = events;
+  g->bound = true;
   g->bound_n = n_events;
   g->max_toys = max_toys;
-  g->max_tile_rows = rows;
+  g->max_toy_rows = rows;
   return RF_OK;
 }
 
 static rf_status batched_checks(rf_graph* g, const int64_t* offsets, int32_t toys,
                                 const double* pm, const double* out) {
   if (!g) return fail(RF_EINVAL, "graph is NULL");
-  if (!g->work.tile_start) return fail(RF_EINVAL, "rf_graph_bind_events was not called");
+  if (!g->bound) return fail(RF_EINVAL, "rf_graph_bind_events was not called");
   if (toys < 1 || toys > g->max_toys) return fail(RF_EINVAL, "toys must be in 1..max_toys");
   if (!offsets || !pm || !out) return fail(RF_EINVAL, "NULL argument");
-  if (g->cfg.tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
   if (g->jit && !g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)]) {
     std::string err;
     if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
@@ -620,7 +619,7 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
   int n = 0;
   int e = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
                             g->bound_n, offsets, toys, const_cast<double*>(params_matrix), out,
-                            g->work, nullptr, 0.0, true, g->max_tile_rows,
+                            g->work, nullptr, 0.0, g->max_toy_rows,
                             g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
                             stream, &n);
   g->last_launches = n;
@@ -649,9 +648,8 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
   if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_m2, 0, sizeof(double) * np * toys, fs);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->work.adam_t, 0, sizeof(int32_t), fs);
   if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys reset");
-  int le = rf_toys_plan(offsets, toys, g->cfg.tile, g->max_tile_rows, g->bound_n, g->work, fs);
-  if (le) return cuda_fail((cudaError_t)le, "rf_fit_toys plan");
-  int launches = 1;
+  int le = 0;
+  int launches = 0;
   if (iters > 0) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -660,7 +658,7 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
     int n = 0;
     le = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
                            g->bound_n, offsets, toys, params_matrix, out, g->work, scale, lr,
-                           false, g->max_tile_rows,
+                           g->max_toy_rows,
                            g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
                            fs, &n);
     e = cudaStreamEndCapture(fs, &graph);
@@ -729,7 +727,6 @@ rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg) {
   cfg->block = g->cfg.block;
   cfg->ept = g->cfg.ept;
   cfg->blocks_per_sm = g->cfg.blocks_per_sm;
-  cfg->tile = g->cfg.tile;
   return RF_OK;
 }
 
@@ -741,17 +738,15 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
     return fail(RF_EINVAL, "events per thread not available for this precision / dtype");
   if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
     return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
-  if (cfg->tile < 1024) return fail(RF_EINVAL, "tile must be >= 1024 events");
   if (g->jit) {
     std::string err;
     if (!jit_fused(g, cfg->ept, &err)) return fail(RF_ECUDA, "JIT fused kernel: " + err);
-    if (g->bound_events && !jit_toys(g, cfg->ept, &err))
+    if (g->bound && !jit_toys(g, cfg->ept, &err))
       return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
   g->cfg.block = cfg->block;
   g->cfg.ept = cfg->ept;
   g->cfg.blocks_per_sm = cfg->blocks_per_sm;
-  g->cfg.tile = cfg->tile;
   return RF_OK;
 }
 

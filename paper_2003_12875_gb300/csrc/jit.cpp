@@ -127,12 +127,8 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   } else if (kind == RF_JIT_TOYS) {
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_toys_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t stride, int vec, const int64_t* __restrict__ offsets, "
-              "int32_t toys, int64_t tile_ev, double* pm, double* out, RfWork W, "
-              "const double* __restrict__ adam_scale, double adam_lr, int64_t max_rows) {\n"
-              "  rf::toy_tile_body<RfModel, "
-      << R << ", " << C << ", " << ept
-      << ">(P, ev, stride, vec, offsets, toys, tile_ev, pm, out, W, adam_scale, adam_lr, "
-         "max_rows);\n}\n";
+              "int32_t toys, int stages, RfWork W) {\n  rf::toy_segment_body<RfModel, "
+      << R << ", " << C << ", " << ept << ">(P, ev, stride, vec, offsets, toys, stages, W);\n}\n";
   } else {
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_logp_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t n, const double* __restrict__ params, double* logp) {\n"
@@ -280,22 +276,24 @@ int rf_jit_launch_fused(cudaKernel_t k, const RfProgram& P, int coldt, const RfL
   return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void*>(k), args);
 }
 
-int rf_jit_launch_toys(cudaKernel_t k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
-                       int num_sms, const void* events, int64_t n_events,
-                       const int64_t* offsets, int32_t toys, double* pm, double* out,
-                       RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
-                       cudaStream_t st) {
-  int vec = 0;
-  int64_t head = 0;
-  rf_vec_plan(P, events, n_events, coldt ? 8 : 4, &vec, &head);
-  int grid = num_sms * cfg.blocks_per_sm;
+int rf_jit_launch_toys(cudaKernel_t k, const RfProgram& P, int grid, int block, int vec,
+                       int stages, size_t smem, const void* events, int64_t n_events,
+                       const int64_t* offsets, int32_t toys, RfWork W, cudaStream_t st) {
   RfProgram Pc = P;
   const void* ev = events;
-  int64_t stride = n_events, tile = cfg.tile;
-  void* args[] = {&Pc, &ev, &stride, &vec, &offsets, &toys, &tile, &pm, &out, &W,
-                  &adam_scale, &adam_lr, &max_rows};
-  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(cfg.block),
-                               args, 0, st);
+  int64_t stride = n_events;
+  void* args[] = {&Pc, &ev, &stride, &vec, &offsets, &toys, &stages, &W};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(block);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void*>(k), args);
 }
 
 int rf_jit_launch_logp(cudaKernel_t k, const RfProgram& P, const void* events, int64_t n,

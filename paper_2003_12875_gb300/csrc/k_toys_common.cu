@@ -1,133 +1,96 @@
-// Toy-study orchestration: tile plan, per-toy prologue, tile kernel.
+// Toy-study orchestration: prep kernel, segment kernel, finalize kernel.
+#include <algorithm>
+#include <cstdlib>
+
 #include "rf_batched.cuh"
 
-#define RF_TOYS_DECL(R, C)                                                          \
-  int rf_toys_##R##_##C(const RfProgram&, const RfLaunchCfg&, int, const void*,   \
-                        int64_t, const int64_t*, int32_t, double*, double*, RfWork, \
-                        const double*, double, int64_t, cudaStream_t);
+#define RF_TOYS_DECL(R, C)                                                              \
+  int rf_toys_##R##_##C(const RfProgram&, int, int, int, int, int, size_t, const void*, \
+                        int64_t, const int64_t*, int32_t, RfWork, cudaStream_t);
 RF_TOYS_DECL(f32, c32)
 RF_TOYS_DECL(f32, c64)
 RF_TOYS_DECL(f64, c32)
 RF_TOYS_DECL(f64, c64)
 
-namespace rf {
-__global__ void __launch_bounds__(1024)
-    toy_plan_kernel(const int64_t* __restrict__ offsets, int32_t toys,
-                    int64_t tile, int64_t max_rows, int64_t n_events, int64_t* tile_start,
-                    int32_t* tile_toy, int64_t* tile_be, unsigned int* status) {
-  __shared__ int64_t wsum[32];
-  __shared__ int64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t base = 0; base < toys; base += blockDim.x) {
-    int64_t t = base + threadIdx.x;
-    int64_t nt = 0;
-    if (t < toys) {
-      int64_t b = offsets[t], e = offsets[t + 1];
-      if (e < b) {
-        atomicOr(status, RF_STATUS_NONFINITE_BIT);
-        e = b;
-      }
-      nt = (e - b + tile - 1) / tile;
-      if (nt < 1) nt = 1;
-    }
-    // inclusive warp scan, then across warps
-    int64_t v = nt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int64_t y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    if (lane == 31) wsum[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-      int64_t w = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    int64_t incl = v + (wid > 0 ? wsum[wid - 1] : 0) + carry;
-    if (t < toys) tile_start[t] = incl - nt;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = incl;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) tile_start[toys] = carry;
-  __syncthreads();
-  // tile -> (toy, event range); offsets are clamped to the bound columns so
-  // that a bad offset table reads nothing outside; tiles beyond the
-  // workspace are never run
-  for (int64_t t = threadIdx.x; t < toys; t += blockDim.x) {
-    int64_t ob = offsets[t], oe = offsets[t + 1];
-    ob = ob < 0 ? 0 : (ob > n_events ? n_events : ob);
-    oe = oe < ob ? ob : (oe > n_events ? n_events : oe);
-    const int64_t r0 = tile_start[t];
-    const int64_t r1 = tile_start[t + 1] < max_rows ? tile_start[t + 1] : max_rows;
-    for (int64_t r = r0; r < r1; ++r) {
-      const int64_t b = ob + (r - r0) * tile;
-      tile_toy[r] = (int32_t)t;
-      tile_be[2 * r] = b < oe ? b : oe;
-      tile_be[2 * r + 1] = b + tile < oe ? b + tile : oe;
-    }
-  }
-}
-
-}  // namespace rf
-
 size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
 
-int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, int64_t max_rows,
-                 int64_t n_events, RfWork W, void* stream) {
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rf::toy_plan_kernel<<<1, 1024, 0, st>>>(offsets, toys, tile, max_rows, n_events, W.tile_start,
-                                          W.tile_toy, W.tile_be, W.status);
+namespace {
+
+template <typename Real>
+int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, int64_t stride,
+                    int64_t warps, double* pm, double* out, RfWork W,
+                    const double* adam_scale, double adam_lr, cudaStream_t st) {
+  const int fb = 256, fg = (toys + fb / 32 - 1) / (fb / 32);
+  switch (P.n_leaves) {
+    case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 3: rf::toy_finalize_kernel<Real, 3><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 4: rf::toy_finalize_kernel<Real, 4><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
   return (int)cudaGetLastError();
 }
+
+}  // namespace
 
 int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg& cfg,
                       int num_sms, const void* events, int64_t n_events,
                       const int64_t* offsets, int32_t toys, double* pm, double* out,
-                      RfWork W, const double* adam_scale, double adam_lr, bool plan,
-                      int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
-                      int* launches) {
+                      RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
+                      struct CUkern_st* jit_toys, void* stream, int* launches) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int n = 0, rc;
-  if (plan) {
-    rc = rf_toys_plan(offsets, toys, cfg.tile, max_rows, n_events, W, stream);
-    ++n;
-    if (rc) return rc;
-  }
-  const int pb = 32;  // few threads per block: the FP64 prologue spreads over SMs
+  if (launches) *launches = 0;
+  // segment rows: one per (warp, toy) pair that shares events, at most
+  // warps + toys of them
+  const int wpb = cfg.block / 32;
+  int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
+  const int64_t room = max_rows - toys;
+  if (wpb < 1 || room < wpb) return (int)cudaErrorInvalidValue;
+  if (grid * wpb > room) grid = room / wpb;
+  const int64_t warps = grid * wpb;
+  int vec = 0;
+  int64_t head = 0;
+  const size_t esz = coldt ? 8 : 4;
+  rf_vec_plan(P, events, n_events, (int)esz, &vec, &head);
+  // stage ring per warp: as many stages of 32*EPT events (all columns) as
+  // fit in about 96 KB per block, 2..8
+  const size_t stage_bytes = (size_t)std::max(P.n_cols, 1) * 32 * cfg.ept * esz;
+  int stages = (int)std::min<size_t>(8, std::max<size_t>(2, (96u << 10) / (wpb * stage_bytes)));
+  const size_t smem = (size_t)wpb * (8 * 8 + stages * stage_bytes);
+
+  int pb = 32;  // few threads per block: the FP64 work spreads over SMs
+  if (const char* v = getenv("RF_TOY_PREP_BLOCK")) pb = atoi(v) >= 1 && atoi(v) <= 256 ? atoi(v) : 32;
   const int pg = (toys + pb - 1) / pb > 0 ? (toys + pb - 1) / pb : 1;
   int32_t* at = adam_scale ? W.adam_t : nullptr;
   if (eval)
-    rf::toy_prep_kernel<double><<<pg, pb, 0, st>>>(
-        P, pm, toys, static_cast<RfConsts<double>*>(W.toy_consts), W.next_tile, at);
+    rf::toy_prep_kernel<double><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
+                                                   static_cast<RfConsts<double>*>(W.toy_consts),
+                                                   W.status, at);
   else
-    rf::toy_prep_kernel<float><<<pg, pb, 0, st>>>(
-        P, pm, toys, static_cast<RfConsts<float>*>(W.toy_consts), W.next_tile, at);
-  ++n;
-  rc = (int)cudaGetLastError();
+    rf::toy_prep_kernel<float><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
+                                                  static_cast<RfConsts<float>*>(W.toy_consts),
+                                                  W.status, at);
+  int rc = (int)cudaGetLastError();
   if (rc) return rc;
+  const int g = (int)grid;
   if (jit_toys)
-    rc = rf_jit_launch_toys(jit_toys, P, coldt, cfg, num_sms, events, n_events, offsets, toys, pm,
-                            out, W, adam_scale, adam_lr, max_rows, st);
+    rc = rf_jit_launch_toys(jit_toys, P, g, cfg.block, vec, stages, smem, events, n_events,
+                            offsets, toys, W, st);
   else if (eval == 0 && coldt == 0)
-    rc = rf_toys_f32_c32(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);
+    rc = rf_toys_f32_c32(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
   else if (eval == 0)
-    rc = rf_toys_f32_c64(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);
+    rc = rf_toys_f32_c64(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
   else if (coldt == 0)
-    rc = rf_toys_f64_c32(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);
+    rc = rf_toys_f64_c32(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
   else
-    rc = rf_toys_f64_c64(P, cfg, num_sms, events, n_events, offsets, toys, pm, out, W, adam_scale, adam_lr, max_rows, st);
-  ++n;
-  if (launches) *launches = n;
+    rc = rf_toys_f64_c64(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
+  if (rc) return rc;
+  rc = eval ? launch_finalize<double>(P, offsets, toys, n_events, warps, pm, out, W, adam_scale,
+                                      adam_lr, st)
+            : launch_finalize<float>(P, offsets, toys, n_events, warps, pm, out, W, adam_scale,
+                                     adam_lr, st);
+  if (launches) *launches = 3;
   return rc;
 }

@@ -1,14 +1,10 @@
-// Batched-toy tile kernels: float per-event arithmetic, double columns.
+// Batched-toy segment kernels (precompiled, generic model): float per-event arithmetic, double columns.
 #include "rf_batched.cuh"
 
-int rf_toys_f32_c64(const RfProgram& P, const RfLaunchCfg& cfg, int sms,
-                     const void* ev, int64_t n_events, const int64_t* offsets,
-                     int32_t toys, double* pm, double* out, RfWork W,
-                     const double* adam_scale, double adam_lr, int64_t max_rows,
-                     cudaStream_t st) {
-  if (cfg.ept == 8)
-    return rf::launch_toys_ept<float, double, 8>(P, cfg, sms, ev, n_events, offsets, toys, pm,
-                                                  out, W, adam_scale, adam_lr, max_rows, st);
-  return rf::launch_toys_ept<float, double, 4>(P, cfg, sms, ev, n_events, offsets, toys, pm,
-                                                out, W, adam_scale, adam_lr, max_rows, st);
+int rf_toys_f32_c64(const RfProgram& P, int ept, int grid, int block, int vec, int stages,
+                 size_t smem, const void* ev, int64_t n_events, const int64_t* offsets,
+                 int32_t toys, RfWork W, cudaStream_t st) {
+  if (ept == 8)
+    return rf::launch_toys_ept<float, double, 8>(P, grid, block, vec, stages, smem, ev, n_events, offsets, toys, W, st);
+  return rf::launch_toys_ept<float, double, 4>(P, grid, block, vec, stages, smem, ev, n_events, offsets, toys, W, st);
 }

@@ -59,6 +59,36 @@ __global__ void __launch_bounds__(256) mb_kernel<11>(float2* sink, int iters) {
   if (s == -12345.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = make_float2(s, s);
 }
 
+// Latency of one dependent chain per active lane in a single warp: the time
+// per operation with 1 and with 32 active lanes shows whether the FP64 pipe
+// serialises lanes (then 32 lanes cost more per step) or not.
+template <int OP>
+__global__ void lat_kernel(typename Op<OP>::T* sink, int iters, int lanes) {
+  typedef typename Op<OP>::T T;
+  if ((int)threadIdx.x >= lanes) return;
+  T a = (T)(0.1 + 1e-6 * threadIdx.x);
+  for (int it = 0; it < iters; ++it) a = Op<OP>::f(a);
+  if (a == (T)-12345.0) sink[threadIdx.x] = a;
+}
+
+template <int OP>
+double lat_ns(void* sink, int iters, int lanes) {
+  typedef typename Op<OP>::T T;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  lat_kernel<OP><<<1, 32>>>(static_cast<T*>(sink), iters / 10, lanes);  // warm-up
+  cudaEventRecord(a);
+  lat_kernel<OP><<<1, 32>>>(static_cast<T*>(sink), iters, lanes);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return (double)ms * 1e6 / iters;
+}
+
 template <int OP>
 double run(int sms, void* sink, int iters) {
   const int block = 256, grid = sms * 8;
@@ -99,6 +129,10 @@ int rf_run_microbench(double* out) {
   out[9] = run<9>(sms, sink, 1024);
   out[10] = run<10>(sms, sink, 1024);
   out[11] = 2.0 * run<11>(sms, sink, 4096);  // FMAs per second
+  out[12] = lat_ns<4>(sink, 200000, 1);
+  out[13] = lat_ns<4>(sink, 200000, 32);
+  out[14] = lat_ns<5>(sink, 20000, 1);
+  out[15] = lat_ns<5>(sink, 20000, 32);
   e = cudaGetLastError();
   cudaFree(sink);
   return (int)e;

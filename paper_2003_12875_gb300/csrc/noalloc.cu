@@ -111,7 +111,6 @@ extern "C" rf_status rf_nll_noalloc(const rf_graph_desc* desc, const void* event
   RfLaunchCfg cfg;
   cfg.block = 256;
   cfg.blocks_per_sm = 1;
-  cfg.tile = 8192;
   int le;
   if (desc->eval_precision == RF_EVAL_FP32) {
     cfg.ept = 4;

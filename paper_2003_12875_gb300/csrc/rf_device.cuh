@@ -50,44 +50,70 @@ __device__ inline double erf_diff(double z1, double z2) {  // d_erf(z2)-d_erf(z1
   return d_erf(z2) - d_erf(z1);
 }
 
-// (e^y - 1)/y and its derivative; the derivative's closed form cancels near
-// 0, where its Taylor series sum_{k>=1} k y^(k-1)/(k+1)! is used instead.
+// (e^y - 1)/y and its derivative d/dy = (e^y (y - 1) + 1) / y^2.  The
+// derivative's closed form cancels near 0, where the Taylor series
+// sum_{k>=1} k y^(k-1) / (k+1)! is summed by Horner's rule instead (22 terms:
+// the first omitted one is below 2^-60 of the sum for |y| < 1).  ey = e^y is
+// passed in by the caller, which needs it anyway.
 __device__ inline double expm1_over(double y) {
   return y == 0.0 ? 1.0 : d_expm1(y) / y;
 }
-__device__ inline double expm1_over_d(double y) {
-  if (fabs(y) < 1.0) {
-    double acc = 0.0, yp = 1.0, fact = 2.0;
-    for (int k = 1; k <= 30; ++k) {
-      acc += k * yp / fact;
-      yp *= y;
-      fact *= (double)(k + 2);
+struct ExpmSeries {
+  double c[23];
+  __host__ __device__ constexpr ExpmSeries() : c() {
+    double f = 1.0;
+    for (int k = 1; k <= 22; ++k) {
+      f *= (double)(k + 1);
+      c[k] = (double)k / f;
     }
+  }
+};
+__device__ inline double expm1_over_d(double y, double ey) {
+  if (fabs(y) < 1.0) {
+    constexpr ExpmSeries S;
+    double acc = S.c[22];
+#pragma unroll
+    for (int k = 21; k >= 1; --k) acc = fma(acc, y, S.c[k]);
     return acc;
   }
-  return (d_exp(y) * (y - 1.0) + 1.0) / (y * y);
+  return (ey * (y - 1.0) + 1.0) / (y * y);
 }
 
-// int_0^tau s^q e^{c s} ds, q in {1/2, 3/2}: incomplete-gamma closed form for
-// c < 0 and -c tau >= 1/2, power series otherwise.
-__device__ inline double argus_int(double q, double tau, double c) {
-  if (tau <= 0.0) return 0.0;
-  double y = c * tau;
-  if (c < 0.0 && -y >= 0.5) {
-    double k = -c, ky = -y, sky = sqrt(ky), eky = d_exp(-ky);
-    double g32 = 0.5 * kSqrtPi * d_erf(sky) - sky * eky;  // gamma(3/2, ky)
-    if (q == 0.5) return g32 / (k * sqrt(k));
-    double g52 = 1.5 * g32 - ky * sky * eky;            // gamma(5/2, ky)
-    return g52 / (k * k * sqrt(k));
+// J_q(tau) = int_0^tau s^q e^{c s} ds for q = 1/2 and q = 3/2, and e^{c tau}.
+// For c < 0 and -c tau >= 1/2 the incomplete-gamma closed forms share one erf
+// and one exp: with k = -c, u = k tau, gamma(3/2, u) = (sqrt(pi)/2) erf(sqrt u)
+// - sqrt(u) e^-u, gamma(5/2, u) = (3/2) gamma(3/2, u) - u^(3/2) e^-u, and
+// J_q = gamma(q + 1, u) / k^(q + 1).  Otherwise both power series
+// J_q = tau^(q+1) sum_j (c tau)^j / (j! (j + q + 1)) run in one loop.
+__device__ inline void argus_int2(double tau, double c, double* J12, double* J32,
+                                  double* ect) {
+  if (tau <= 0.0) {
+    *J12 = *J32 = 0.0;
+    *ect = 1.0;
+    return;
   }
-  double sum = 0.0, term = 1.0;
+  const double y = c * tau;
+  if (c < 0.0 && -y >= 0.5) {
+    const double k = -c, u = -y, su = sqrt(u), eu = d_exp(-u), sk = sqrt(k);
+    const double g32 = 0.5 * kSqrtPi * d_erf(su) - su * eu;
+    const double g52 = 1.5 * g32 - u * su * eu;
+    *J12 = g32 / (k * sk);
+    *J32 = g52 / (k * k * sk);
+    *ect = eu;
+    return;
+  }
+  double s12 = 0.0, s32 = 0.0, term = 1.0;
   for (int j = 0; j < 2000; ++j) {
-    double add = term / (j + q + 1.0);
-    sum += add;
-    if (j > fabs(y) && fabs(add) < 1e-18 * fabs(sum)) break;
+    const double a12 = term / (j + 1.5), a32 = term / (j + 2.5);
+    s12 += a12;
+    s32 += a32;
+    if (j > fabs(y) && fabs(a12) < 1e-18 * fabs(s12) && fabs(a32) < 1e-18 * fabs(s32)) break;
     term *= y / (j + 1.0);
   }
-  return d_pow(tau, q + 1.0) * sum;
+  const double st = tau * sqrt(tau);
+  *J12 = st * s12;
+  *J32 = st * tau * s32;
+  *ect = d_exp(y);
 }
 
 // d_log(I) - off and d(log I - off)/d theta_j for one leaf (FP64).  `off` is
@@ -152,10 +178,22 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
         double t2 = fmin(thi, -A);
         double D2 = 1.0 - (A / n) * (A + t2);
         double L1 = d_log(D1), L2 = (t2 == -A) ? 0.0 : d_log(D2), dL = L1 - L2, eps = 1.0 - n;
-        double ez = (L2 == 0.0) ? 1.0 : d_exp(eps * L2);
-        double Phi = ez * dL * expm1_over(eps * dL);                    // int D^-n
-        double PhiL = L2 * Phi + ez * dL * dL * expm1_over_d(eps * dL);  // int D^-n log D
-        double p1 = d_exp(-n * L1), p2 = (L2 == 0.0) ? 1.0 : d_exp(-n * L2);
+        double ez = (L2 == 0.0) ? 1.0 : d_exp(eps * L2);                // D2^(1-n)
+        // y = (1-n) log(D1/D2): e^y and e^y - 1 from one call (e^y - 1 is
+        // only formed by subtraction where it cannot cancel, |y| >= 1)
+        const double y = eps * dL;
+        double ey, em1;
+        if (fabs(y) >= 1.0) {
+          ey = d_exp(y);
+          em1 = ey - 1.0;
+        } else {
+          em1 = d_expm1(y);
+          ey = 1.0 + em1;
+        }
+        double Phi = ez * dL * (y == 0.0 ? 1.0 : em1 / y);               // int D^-n
+        double PhiL = L2 * Phi + ez * dL * dL * expm1_over_d(y, ey);     // int D^-n log D
+        // D^-n = D^(1-n) / D at both ends
+        double p1 = ez * ey / D1, p2 = (L2 == 0.0) ? 1.0 : ez / D2;
         double Psi = (p2 - p1) / n;                                      // int D^-n-1
         double pre = (n / A) * eA;
         tail = pre * Phi;
@@ -182,10 +220,13 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
       double b = fmin(hi, m0);
       double ta = 1.0 - (lo / m0) * (lo / m0), tb = 1.0 - (b / m0) * (b / m0);
       double h = 0.5 * m0 * m0;
-      double I = h * (argus_int(0.5, ta, c) - argus_int(0.5, tb, c));
-      double dIc = h * (argus_int(1.5, ta, c) - argus_int(1.5, tb, c));
-      double ea = (1.0 - ta) * sqrt(ta) * d_exp(c * ta);
-      double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * d_exp(c * tb) : 0.0;
+      double Ja, Ka, Ea, Jb, Kb, Eb;
+      argus_int2(ta, c, &Ja, &Ka, &Ea);
+      argus_int2(tb, c, &Jb, &Kb, &Eb);
+      double I = h * (Ja - Jb);
+      double dIc = h * (Ka - Kb);
+      double ea = (1.0 - ta) * sqrt(ta) * Ea;
+      double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * Eb : 0.0;
       double dIm = m0 * (ea - eb) + 2.0 * I / m0;
       *lnI = d_log(I);
       dln[0] = dIm / I;
@@ -218,12 +259,14 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
     K.dlogI[k][j] = dln[j];
     K.dtheta[k][j] = 0.0;
+    K.gmul[k][j] = 1.0;
   }
   switch (L.type) {
     case RFL_GAUSS: {
       split_hi_lo(th[0], pc[0], pc[1]);
       pc[2] = (Real)(1.0 / th[1]);
       K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
+      K.gmul[k][0] = K.gmul[k][1] = 1.0 / th[1];  // d u/d mu = d/sigma, d u/d sigma = d^2/sigma
       break;
     }
     case RFL_EXP: {
@@ -252,6 +295,9 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       pc[6] = (Real)n;
       pc[7] = (Real)(-0.5 * A * A);
       K.dtheta[k][1] = 1.0 / fabs((double)pc[2]) - th[1];
+      K.gmul[k][0] = -s / th[1];   // d u/d m0 = -(s/sigma) du/dt
+      K.gmul[k][1] = -1.0 / th[1]; // d u/d sigma = -(t/sigma) du/dt
+      K.gmul[k][2] = s;            // d u/d alpha = s d u/d|alpha|
       break;
     }
     case RFL_ARGUS: {
@@ -260,6 +306,7 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       pc[3] = (Real)th[1];
       pc[4] = (Real)(2.0 / th[0]);
       K.dtheta[k][1] = (double)pc[3] - th[1];
+      K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (1/(2 tau) + c)(1 - tau)
       break;
     }
   }
@@ -386,11 +433,14 @@ __device__ __forceinline__ float exp_neg_approx(float x) {
 // mantissa is odd); a carry out of the mantissa correctly bumps the
 // exponent.  Zero, float-subnormal, overflowing, infinite and NaN inputs go
 // through the hardware conversion.  Tested bit for bit against it.
+// The rare cases out of line, so that the compiler cannot turn the branch into
+// an FP64-pipe conversion executed for every value.
+static __device__ __noinline__ float d2f_hw(double x) { return __double2float_rn(x); }
 __device__ __forceinline__ float d2f_rn(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e - 897u >= 253u) return __double2float_rn(x);  // float exponent outside 1..253
+  if (e - 897u >= 253u) return d2f_hw(x);  // float exponent outside 1..253
   unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rem = lo & 0x1fffffffu;
   bits += (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ? 1u : 0u;
@@ -431,8 +481,8 @@ __device__ __forceinline__ void leaf_gauss(Real x, const Real* __restrict__ pc, 
                                            Real (&g)[RF_LEAF_MAXP]) {
   Real d = ((x - pc[0]) - pc[1]) * pc[2];
   u = Real(-0.5) * d * d;
-  g[0] = (GM & 1) ? d * pc[2] : Real(0);
-  g[1] = (GM & 2) ? d * d * pc[2] : Real(0);
+  g[0] = (GM & 1) ? d : Real(0);       // times 1/sigma (gmul)
+  g[1] = (GM & 2) ? d * d : Real(0);   // times 1/sigma (gmul)
   g[2] = g[3] = Real(0);
 }
 
@@ -479,9 +529,10 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   if (GM) {
     Real rD = F::rcp(D);
     Real dudt = tail ? A * rD : -t;
-    g[0] = (GM & 1) ? -dudt * pc[2] : Real(0);
-    g[1] = (GM & 2) ? -dudt * t * (pc[3] * pc[2]) : Real(0);
-    g[2] = (GM & 4) ? (tail ? pc[3] * ((Real(2) * A + t) * rD - A) : Real(0)) : Real(0);
+    // constant factors (-s/sigma, -1/sigma, s) are applied to the sums (gmul)
+    g[0] = (GM & 1) ? dudt : Real(0);
+    g[1] = (GM & 2) ? dudt * t : Real(0);
+    g[2] = (GM & 4) ? (tail ? (Real(2) * A + t) * rD - A : Real(0)) : Real(0);
     g[3] = (GM & 8) ? (tail ? (Real(1) - rD) - Lg : Real(0)) : Real(0);
   } else {
     g[0] = g[1] = g[2] = g[3] = Real(0);
@@ -501,7 +552,7 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
   g[1] = (GM & 2) ? (ok ? tau : Real(0)) : Real(0);
   if (GM & 1) {
     Real r = F::rcp(tau);
-    g[0] = ok ? (Real(0.5) * r + pc[3]) * (Real(1) - tau) * pc[4] : Real(0);
+    g[0] = ok ? (Real(0.5) * r + pc[3]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
   } else {
     g[0] = Real(0);
   }
@@ -690,24 +741,6 @@ __device__ inline void rows_sum(const double* partials, int64_t r0, int64_t r1,
   block_sum<N>(v, red, out);
 }
 
-// Sum a few rows (one toy's tiles) of partials: accumulator i by thread i,
-// Neumaier in row order (FP64 work on N lanes only).  Result in out[0..N)
-// (shared), valid after the trailing barrier.
-template <int N>
-__device__ inline void rows_sum_few(const double* partials, int64_t r0, int64_t r1, double* out) {
-  if (threadIdx.x < N) {
-    double v = 0.0, c = 0.0;
-    for (int64_t r = r0; r < r1; ++r) {
-      const double x = __ldcg(partials + r * RF_NACC_MAX + threadIdx.x);
-      const double t = v + x;
-      c += (fabs(v) >= fabs(x)) ? (v - t) + x : (x - t) + v;
-      v = t;
-    }
-    out[threadIdx.x] = v + c;
-  }
-  __syncthreads();
-}
-
 // ---------------------------------------------------------------- epilogue
 // T: FP64 totals of the accumulators, n: events.  Writes NLL and gradient.
 template <typename Real, int NL>
@@ -721,7 +754,7 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
   for (int k = 0; k < P.n_leaves; ++k)
     for (int j = 0; j < RF_LEAF_MAXP; ++j)
       if ((P.leaf[k].gmask >> j) & 1)
-        L -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.dtheta[k][j];
+        L -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] * K.dtheta[k][j];
   double v = -((double)n * K.beta_ref + L) + K.ext_sum;
   bool bad = K.bad || !isfinite(v);
   if (grad) {
@@ -731,7 +764,7 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
       double S = ((K.zero_mask >> lf.comp) & 1) ? 0.0 : T[1 + lf.comp];
       for (int j = 0; j < RF_LEAF_MAXP; ++j)
         if ((lf.gmask >> j) & 1)
-          grad[lf.par[j]] -= T[1 + NL + k * RF_LEAF_MAXP + j] - S * K.dlogI[k][j];
+          grad[lf.par[j]] -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] - S * K.dlogI[k][j];
     }
     double R[RF_MAXC];
     for (int c = 0; c < C; ++c)

@@ -37,6 +37,7 @@ enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 // device status bits (same values as RF_STATUS_* in include/rf.h)
 #define RF_STATUS_PARAM_DOMAIN_BIT 1u
 #define RF_STATUS_NONFINITE_BIT 2u
+#define RF_STATUS_TIMEOUT_BIT 4u
 enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5 };
 
 struct RfLeafProg {
@@ -74,6 +75,7 @@ struct RfConsts {
   double delta_lo[RF_MAXC];    // delta_c - (double)delta[c]
   double dlogI[RF_MAXL][RF_LEAF_MAXP];   // d(log I_k - off_k)/d theta_kj
   double dtheta[RF_MAXL][RF_LEAF_MAXP];  // theta used per event - theta
+  double gmul[RF_MAXL][RF_LEAF_MAXP];    // d u/d theta = gmul * (per-event factor)
   double coef[RF_MAXC];
   double ext_sum;              // sum of yields (extended) else 0
   int32_t zero_mask;           // bit c: coef_c == 0
@@ -82,15 +84,11 @@ struct RfConsts {
 
 // Device workspace owned by an rf_graph.
 struct RfWork {
-  double* partials;        // [max_blocks_or_tiles * RF_NACC_MAX]
+  double* partials;        // [rows * RF_NACC_MAX]: block partials (single
+                           // dataset) or segment partials (toys)
   unsigned int* counter;   // [1] block ticket (single dataset)
   unsigned int* status;    // [1] RF_STATUS_* bits
   // batched mode
-  int64_t* tile_start;     // [max_toys + 1]
-  int32_t* tile_toy;       // [max rows] toy of each tile
-  int64_t* tile_be;        // [2 * max rows] event range [begin, end) of each tile
-  unsigned int* toy_counter;  // [max_toys]
-  unsigned int* next_tile; // [1]
   void* toy_consts;        // [max_toys] RfConsts<Real>
   double* adam_m1;         // [max_toys * n_par]
   double* adam_m2;
@@ -107,7 +105,6 @@ struct RfLaunchCfg {
   int block;
   int ept;
   int blocks_per_sm;
-  int tile;
 };
 
 #ifndef __CUDACC_RTC__
@@ -131,13 +128,14 @@ RF_DECL_FUSED(f64, c64)
 int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
                        rf_cuda_stream st);
 
-int rf_toys_plan(const int64_t* offsets, int32_t toys, int64_t tile, int64_t max_rows,
-                 int64_t n_events, RfWork W, void* stream);
+// Toy studies: prep kernel (per-toy FP64 constants), segment kernel (events
+// split evenly over the launch's warps), finalize kernel (one warp per toy:
+// fixed-order sum of its segments, epilogue, optional Adam step).
 int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       const RfLaunchCfg& cfg, int num_sms, const void* events,
                       int64_t n_events, const int64_t* offsets, int32_t toys,
                       double* pm, double* out, RfWork W,
-                      const double* adam_scale, double adam_lr, bool plan,
+                      const double* adam_scale, double adam_lr,
                       int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
                       int* launches);
 int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
@@ -169,11 +167,11 @@ rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, 
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
                         RfWork W, double* nll, double* grad, rf_cuda_stream st);
-int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
-                       int num_sms, const void* events, int64_t n_events,
-                       const int64_t* offsets, int32_t toys, double* pm, double* out,
-                       RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
-                       rf_cuda_stream st);
+// segment kernel of a toy study, as a programmatic dependent of the prep
+// kernel launched just before it
+int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int grid, int block, int vec,
+                       int stages, size_t smem, const void* events, int64_t n_events,
+                       const int64_t* offsets, int32_t toys, RfWork W, rf_cuda_stream st);
 int rf_jit_launch_logp(rf_cuda_kernel k, const RfProgram& P, const void* events, int64_t n,
                        const double* params, double* logp, rf_cuda_stream st);
 #endif  // __CUDACC_RTC__

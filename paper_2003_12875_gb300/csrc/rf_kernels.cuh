@@ -260,9 +260,10 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
 template <class M, typename Real, typename Col>
 __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real, M::NL_>& K,
                                       const Col* __restrict__ ev, int64_t stride, int64_t i0,
-                                      int64_t i1, Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
+                                      int64_t i1, Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc,
+                                      int step = 1) {
   constexpr int NL = M::NL_;
-  for (int64_t i = i0; i < i1; ++i) {
+  for (int64_t i = i0; i < i1; i += step) {
     Real xc[NL];
 #pragma unroll
     for (int c = 0; c < NL; ++c)
@@ -411,149 +412,420 @@ __device__ __forceinline__ void prologue_body(const RfProgram& P, const double* 
 }
 
 // ------------------------------------------------------ toy studies
-// One thread per toy: the toy's FP64 normalisations and coefficients.
+// The toys' events [B, E) (B = offsets[0], E = offsets[toys], clamped to the
+// bound columns) are split into N contiguous ranges of (almost) equal size,
+// one per warp of the segment kernel: warp w takes [start(w), start(w+1)),
+// N = min(warps, E - B) so that no range is empty.  The part of toy t inside
+// warp w's range is segment (w, t); its partial sums go to row w + t of the
+// partials, which no other segment uses (w + t counts the warp starts and toy
+// starts before the segment).  Toy t's segments are therefore the rows w + t
+// for w = warp_of(offsets[t]) .. warp_of(offsets[t+1] - 1), summed in that
+// order by the finalize kernel.  Every warp reads one contiguous stretch of
+// the columns, and no warp waits on another.
+struct ToySplit {
+  int64_t B, E, N;
+  __device__ __forceinline__ int64_t start(int64_t w) const {
+    return B + (int64_t)(((unsigned long long)w * (unsigned long long)(E - B)) /
+                         (unsigned long long)N);
+  }
+  // the warp whose range holds event i (B <= i < E): the largest w with
+  // start(w) <= i, i.e. floor(((i - B + 1) N - 1) / (E - B))
+  __device__ __forceinline__ int64_t warp_of(int64_t i) const {
+    const unsigned long long r =
+        ((unsigned long long)(i - B + 1) * (unsigned long long)N - 1ull) /
+        (unsigned long long)(E - B);
+    return (int64_t)r < N ? (int64_t)r : N - 1;
+  }
+};
+
+// offsets[t] clamped to the bound columns [0, n]
+__device__ __forceinline__ int64_t toy_off(const int64_t* __restrict__ off, int64_t t, int64_t n) {
+  const int64_t v = off[t];
+  return v < 0 ? 0 : (v > n ? n : v);
+}
+
+__device__ __forceinline__ ToySplit toy_split(const int64_t* __restrict__ off, int32_t toys,
+                                              int64_t n, int64_t warps) {
+  ToySplit s;
+  s.B = toy_off(off, 0, n);
+  s.E = toy_off(off, toys, n);
+  if (s.E < s.B) s.E = s.B;
+  const int64_t len = s.E - s.B;
+  s.N = warps < len ? warps : len;
+  if (s.N < 1) s.N = 1;
+  return s;
+}
+
+// The largest t in [0, toys) with offsets[t] <= i (clamped offsets), by a
+// 32-way search: each round the 31 lanes probe 31 evenly spaced toys and a
+// ballot keeps the bracket between the last probe at or below i and the next
+// one.  Every lane returns the same t; the bracket shrinks every round, so at
+// most ceil(log32(toys)) + 1 rounds run (a non-monotone offset table gives
+// some t in [0, toys), never an index outside it).
+__device__ inline int32_t find_toy(const int64_t* __restrict__ off, int32_t toys, int64_t n,
+                                   int64_t i) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = toys;
+  for (int round = 0; round < 16 && hi - lo > 1; ++round) {
+    const int64_t span = hi - lo;
+    const int64_t p = lo + (span * (lane + 1)) / 32;
+    const bool le = lane < 31 && (p == lo || toy_off(off, p, n) <= i);
+    const int k = __popc(__ballot_sync(0xffffffffu, le));
+    const int64_t nlo = k > 0 ? lo + (span * k) / 32 : lo;
+    int64_t nhi = k < 31 ? lo + (span * (k + 1)) / 32 : hi;
+    if (nhi <= nlo) nhi = nlo + 1;
+    lo = nlo;
+    hi = nhi;
+  }
+  return (int32_t)lo;
+}
+
+// Warp-wide fixed-order totals of the per-lane accumulators (FP32 pairs for
+// FP32 evaluation, FP64 otherwise); lane 0 writes the FP64 row.
+template <typename Real, int NA, unsigned long long MASK>
+struct WarpRow;
+template <int NA, unsigned long long MASK>
+struct WarpRow<float, NA, MASK> {
+  static __device__ __forceinline__ void write(const Acc<float, NA, MASK>& acc, double* row) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      double r = 0.0;
+      if ((MASK >> i) & 1ull) {
+        float h = acc.s[i], l = -acc.c[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+          ds_add(h, l, h2, l2);
+        }
+        r = (double)h + (double)l;
+      }
+      if (lane == 0) row[i] = r;
+    }
+  }
+};
+template <int NA, unsigned long long MASK>
+struct WarpRow<double, NA, MASK> {
+  static __device__ __forceinline__ void write(const Acc<double, NA, MASK>& acc, double* row) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const double r = ((MASK >> i) & 1ull) ? warp_sum(acc.value(i)) : 0.0;
+      if (lane == 0) row[i] = r;
+    }
+  }
+};
+
+// One thread per toy: the toy's FP64 normalisations and coefficients, and a
+// check of its offsets.  Lets the segment kernel launch at once.
 template <typename Real>
 __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* __restrict__ pm,
-                                              int32_t toys, RfConsts<Real>* consts,
-                                              unsigned int* next_tile, int32_t* adam_t) {
+                                              const int64_t* __restrict__ offsets,
+                                              int32_t toys, int64_t n_events,
+                                              RfConsts<Real>* consts, unsigned int* status,
+                                              int32_t* adam_t) {
+  asm volatile("griddepcontrol.launch_dependents;");
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    *next_tile = 0u;
-    if (adam_t) *adam_t += 1;
-  }
+  if (t == 0 && adam_t) *adam_t += 1;
   if (t < toys) {
+    const int64_t b = offsets[t], e = offsets[t + 1];
+    if (b < 0 || e < b || e > n_events) atomicOr(status, RF_STATUS_NONFINITE_BIT);
     RfConsts<Real> K;
     build_consts_serial(P, pm + (int64_t)t * P.n_par, K);
     consts[t] = K;
   }
 }
 
-// Persistent blocks take tiles from an atomic counter; a tile holds events of
-// one toy only; the last tile of a toy to finish (per-toy ticket) sums that
-// toy's tile partials in tile order and writes (NLL, grad), optionally
-// followed by one Adam step on the toy's parameter row.  Results do not
-// depend on which block ran which tile.
-template <class M, typename Real, typename Col, int EPT>
-__device__ __forceinline__ void toy_tile_body(const RfProgram& P, const Col* __restrict__ ev,
-                                              int64_t stride, int vec,
-                                              const int64_t* __restrict__ offsets, int32_t toys,
-                                              int64_t tile_ev, double* pm, double* out,
-                                              RfWork& W, const double* __restrict__ adam_scale,
-                                              double adam_lr, int64_t max_rows) {
+// ------------------------------------------------ bulk-copy event streaming
+// Each warp streams its own contiguous event range through a ring of S
+// shared-memory stages.  Lane 0 fills a stage with one cp.async.bulk (TMA
+// bulk copy) per column, completing on the stage's mbarrier; the lanes wait
+// on the barrier's phase, evaluate the stage from shared memory, and lane 0
+// refills it with the chunk S ahead.  Up to S chunks are in flight per warp
+// without holding registers.  Every wait is bounded: a wait that gives up
+// raises RF_STATUS_TIMEOUT_BIT and the warp stops streaming.
+namespace bulk {
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void fence_bar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(b))
+      : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(smem_addr(b)), "r"(parity) : "memory");
+  return done != 0;
+}
+// bounded wait for the phase with the given parity (about a second at most)
+__device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (try_wait(b, parity)) return true;
+  return false;
+}
+constexpr int kMaxStages = 8;
+}  // namespace bulk
+
+// Per-warp state of a toy walk: the current toy, its event range and
+// constants, and the running sums of the current segment.
+template <class M, typename Real>
+struct ToyWalk {
+  static constexpr int NL = M::NL_;
+  static constexpr int NA = RF_NACC(NL);
+  const RfConsts<Real>* consts;
+  const int64_t* offsets;
+  int64_t stride, w;
+  int32_t toys, t;
+  int64_t te;       // end of toy t (clamped)
+  bool bad, any;    // constants outside their domain; segment has events
+  EvalConsts<Real, NL> E;
+  Acc<Real, NA, M::AMASK> acc;
+
+  __device__ __forceinline__ void open(int32_t tt) {
+    t = tt;
+    te = toy_off(offsets, (int64_t)t + 1, stride);
+    const RfConsts<Real>& K = consts[t];
+    bad = K.bad != 0;
+    if (!bad) E.load(K);
+    acc.zero();
+    any = false;
+  }
+  __device__ __forceinline__ void close(double* partials) {
+    if (any) WarpRow<Real, NA, M::AMASK>::write(acc, partials + (w + t) * RF_NACC_MAX);
+  }
+  // move to the toy that holds event p (the toys in between are empty)
+  __device__ __forceinline__ void seek(int64_t p, double* partials) {
+    while (te <= p && t + 1 < toys) {
+      close(partials);
+      open(t + 1);
+    }
+  }
+};
+
+// Evaluate events [p0, p1) of a chunk that starts at event c0 and holds
+// 32*EPT events, column c at buf[c * CE + j]; lane l takes j = l + 32 k.
+// FULL: the chunk lies inside [p0, p1) (no per-event test).
+template <class M, typename Real, typename Col, int EPT, bool FULL>
+__device__ __forceinline__ void eval_chunk(const RfProgram& P, ToyWalk<M, Real>& T,
+                                           const Col* buf, int64_t c0, int64_t p0, int64_t p1) {
   constexpr int NL = M::NL_;
   constexpr int NA = RF_NACC(NL);
-  __shared__ RfConsts<Real> K;
-  __shared__ double red[32 * NA];
-  __shared__ double tot[NA];
-  __shared__ int64_t s_tile, s_toy, s_b, s_e, s_total;
-  __shared__ int s_last;
-  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
-  static_assert(sizeof(RfConsts<Real>) % sizeof(double) == 0, "RfConsts size");
-
-  if (threadIdx.x == 0) s_total = __ldcg(W.tile_start + toys);
-  __syncthreads();
-  const int64_t total = s_total < max_rows ? s_total : max_rows;
-  // Thread 0 takes the next tile from the counter at the start of an
-  // iteration and loads its (toy, event range) after the compute, so that
-  // both round trips overlap the current tile's work.
-  int64_t nx_tile = 0, nx_b = 0, nx_e = 0;
-  int nx_toy = 0;
-  auto load_meta = [&]() {
-    if (nx_tile < total) {
-      nx_toy = __ldcg(W.tile_toy + nx_tile);
-      const longlong2 be = __ldcg(reinterpret_cast<const longlong2*>(W.tile_be) + nx_tile);
-      nx_b = be.x;
-      nx_e = be.y;
+  constexpr int CE = 32 * EPT;
+  const int lane = threadIdx.x & 31;
+  Real q[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) q[i] = Real(0);
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int j = lane + 32 * k;
+    const int64_t i = c0 + j;
+    if (FULL || (i >= p0 && i < p1)) {
+      Real xc[NL];
+#pragma unroll
+      for (int c = 0; c < NL; ++c)
+        xc[c] = (c < M::NCOL && c < P.n_cols) ? cvt<Real, Col>(buf[c * CE + j]) : Real(0);
+      M::template event<Real>(P, T.E, xc, q);
     }
-  };
-  if (threadIdx.x == 0) {
-    nx_tile = (int64_t)atomicAdd(W.next_tile, 1u);
-    load_meta();
   }
-  for (;;) {
-    if (threadIdx.x == 0) {
-      s_tile = nx_tile;
-      s_toy = nx_toy;
-      s_b = nx_b;
-      s_e = nx_e;
-    }
-    __syncthreads();
-    const int64_t tl = s_tile;
-    if (tl >= total) break;
-    const int64_t toy = s_toy, b = s_b, e = s_e;
-    if (threadIdx.x == 0) nx_tile = (int64_t)atomicAdd(W.next_tile, 1u);
-    {
-      const double* src = reinterpret_cast<const double*>(consts + toy);
-      double* dst = reinterpret_cast<double*>(&K);
-      for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = __ldcg(src + w);
-    }
-    __syncthreads();
+  T.acc.add(q);
+}
 
-    Acc<Real, NA, M::AMASK> acc;
-    acc.zero();
-    if (!K.bad && e > b) {
-      EvalConsts<Real, NL> E;
-      E.load(K);
-      int64_t h = 0;
-      if (vec) {
-        uintptr_t a = reinterpret_cast<uintptr_t>(ev + (int64_t)P.col_obs[0] * stride + b);
-        h = (int64_t)(((16u - (a & 15u)) & 15u) / sizeof(Col));
-        if (h > e - b) h = e - b;
-      }
-      const int64_t nfull = (e - b - h) / EPT;
-      stream_chunks<M, Real, Col, EPT>(P, E, ev, stride, b + h, threadIdx.x, blockDim.x, nfull,
-                                       vec != 0, acc);
-      if (threadIdx.x == blockDim.x - 1) {
-        iterate_scalar<M, Real, Col>(P, E, ev, stride, b, b + h, acc);
-        iterate_scalar<M, Real, Col>(P, E, ev, stride, b + h + nfull * EPT, e, acc);
+// Events [p0, p1) straight from the columns (ragged ends), lanes striding.
+template <class M, typename Real, typename Col>
+__device__ __forceinline__ void eval_global(const RfProgram& P, ToyWalk<M, Real>& T,
+                                            const Col* __restrict__ ev, int64_t stride,
+                                            int64_t p0, int64_t p1) {
+  iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p0 + (threadIdx.x & 31), p1, T.acc, 32);
+}
+
+// Walk [p0, p1) across toy boundaries; `run(a, b)` evaluates [a, b) with the
+// current toy's constants.
+template <class M, typename Real, class Run>
+__device__ __forceinline__ void walk(ToyWalk<M, Real>& T, double* partials, int64_t p0,
+                                     int64_t p1, Run run) {
+  while (p0 < p1) {
+    T.seek(p0, partials);
+    const int64_t q1 = p1 < T.te ? p1 : T.te;
+    if (q1 <= p0) break;  // only with a non-monotone offset table
+    if (!T.bad) run(p0, q1);
+    T.any = true;
+    p0 = q1;
+  }
+}
+
+// Segment kernel: warp w streams [start(w), start(w+1)) through its stage
+// ring (chunks of 32*EPT events from the first 16-byte-aligned event; the
+// ragged ends are read directly), switching toy constants at toy boundaries
+// and writing one FP64 row per toy it meets.  The bulk copies of the first
+// stages and the search for the first toy need only the offsets and the
+// events, so they are issued before the wait for the prep kernel.
+// Dynamic shared memory: warps * (kMaxStages barriers + S stages of
+// n_cols * 32*EPT columns values).
+template <class M, typename Real, typename Col, int EPT>
+__device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* __restrict__ ev,
+                                                 int64_t stride, int vec,
+                                                 const int64_t* __restrict__ offsets,
+                                                 int32_t toys, int stages, RfWork& W) {
+  constexpr int CE = 32 * EPT;
+  extern __shared__ __align__(128) unsigned char rf_dyn_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rf_dyn_smem) + wib * bulk::kMaxStages;
+  const size_t stage_elems = (size_t)P.n_cols * CE;
+  Col* ring = reinterpret_cast<Col*>(rf_dyn_smem + (size_t)wpb * bulk::kMaxStages * 8) +
+              (size_t)wib * stages * stage_elems;
+  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(Col));
+
+  const int64_t w = (int64_t)blockIdx.x * wpb + wib;
+  const ToySplit Sp = toy_split(offsets, toys, stride, (int64_t)gridDim.x * wpb);
+  const bool active = w < Sp.N && Sp.E > Sp.B;
+  int64_t wb = 0, we = 0, a0 = 0, nch = 0;
+  int32_t t0 = 0;
+  if (active) {
+    wb = Sp.start(w);
+    we = Sp.start(w + 1);
+    t0 = find_toy(offsets, toys, stride, wb);
+    a0 = we;
+    if (vec) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(ev + (int64_t)P.col_obs[0] * stride + wb);
+      a0 = wb + (int64_t)(((16u - (a & 15u)) & 15u) / sizeof(Col));
+      if (a0 > we) a0 = we;
+      nch = (we - a0) / CE;
+    }
+  }
+  auto issue = [&](int64_t c) {  // lane 0: chunk c into stage c % stages
+    const int s = (int)(c % stages);
+    Col* dst = ring + (size_t)s * stage_elems;
+    bulk::arrive_expect_tx(&bars[s], stage_bytes);
+    for (int col = 0; col < P.n_cols; ++col)
+      bulk::copy(dst + (size_t)col * CE, ev + (int64_t)P.col_obs[col] * stride + a0 + c * CE,
+                 (uint32_t)(CE * sizeof(Col)), &bars[s]);
+  };
+  if (lane == 0) {
+    for (int s = 0; s < stages; ++s) bulk::bar_init(&bars[s], 1);
+    bulk::fence_bar_init();
+    for (int64_t c = 0; c < nch && c < stages; ++c) issue(c);
+  }
+  __syncwarp();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!active) return;
+
+  ToyWalk<M, Real> T;
+  T.consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
+  T.offsets = offsets;
+  T.stride = stride;
+  T.w = w;
+  T.toys = toys;
+  T.open(t0);
+  auto from_global = [&](int64_t p, int64_t q) {
+    eval_global<M, Real, Col>(P, T, ev, stride, p, q);
+  };
+  walk(T, W.partials, wb, a0, from_global);
+  for (int64_t c = 0; c < nch; ++c) {
+    const int s = (int)(c % stages);
+    if (!bulk::wait(&bars[s], (uint32_t)((c / stages) & 1))) {
+      if (lane == 0) atomicOr(W.status, RF_STATUS_TIMEOUT_BIT);
+      // let the copies already issued land before the warp leaves
+      for (int64_t d = c + 1; d < nch && d < c + stages; ++d)
+        bulk::wait(&bars[d % stages], (uint32_t)((d / stages) & 1));
+      return;
+    }
+    const Col* buf = ring + (size_t)s * stage_elems;
+    const int64_t c0 = a0 + c * CE;
+    if (c0 >= T.te || c0 + CE > T.te) {  // a toy boundary inside (or at) the chunk
+      walk(T, W.partials, c0, c0 + CE, [&](int64_t p, int64_t q) {
+        eval_chunk<M, Real, Col, EPT, false>(P, T, buf, c0, p, q);
+      });
+    } else {
+      if (!T.bad) eval_chunk<M, Real, Col, EPT, true>(P, T, buf, c0, c0, c0 + CE);
+      T.any = true;
+    }
+    __syncwarp();
+    if (lane == 0 && c + stages < nch) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(c + stages);
+    }
+  }
+  walk(T, W.partials, a0 + nch * CE, we, from_global);
+  T.close(W.partials);
+}
+
+// Finalize kernel: one warp per toy.  Lane i sums accumulator i over the
+// toy's segment rows in row order (Neumaier, FP64); lane 0 then runs the
+// epilogue into out row t, and, for a fit, the lanes apply one Adam step
+// (Kingma & Ba 2015) to the toy's free parameters in units of its scale row.
+template <typename Real, int NL>
+__device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
+                                                  const int64_t* __restrict__ offsets,
+                                                  int32_t toys, int64_t stride, int64_t warps,
+                                                  double* pm, double* out, RfWork& W,
+                                                  const double* __restrict__ adam_scale,
+                                                  double adam_lr) {
+  constexpr int NA = RF_NACC(NL);
+  __shared__ double tot[32][RF_NACC_MAX];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+  if (t >= toys) return;
+  const ToySplit S = toy_split(offsets, toys, stride, warps);
+  int64_t ob = toy_off(offsets, t, stride), oe = toy_off(offsets, t + 1, stride);
+  ob = ob < S.B ? S.B : ob;
+  oe = oe > S.E ? S.E : oe;
+  if (oe < ob) oe = ob;
+  if (lane < NA) {
+    double v = 0.0, c = 0.0;
+    if (oe > ob) {
+      const int64_t r1 = S.warp_of(oe - 1) + t;
+      for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
+        const double x = __ldcg(W.partials + r * RF_NACC_MAX + lane);
+        const double s = v + x;
+        c += (fabs(v) >= fabs(x)) ? (v - s) + x : (x - s) + v;
+        v = s;
       }
     }
-    if (threadIdx.x == 0) load_meta();
-    BlockReduce<Real, NA, M::AMASK>::run(acc, red, tot);
-    if (threadIdx.x < NA) W.partials[tl * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t r0 = __ldcg(W.tile_start + toy), r1 = __ldcg(W.tile_start + toy + 1);
-      unsigned need = (unsigned)(r1 - r0);
-      s_last = (atomicAdd(W.toy_counter + toy, 1u) == need - 1u) ? 1 : 0;
+    tot[wid][lane] = v + c;
+  }
+  __syncwarp();
+  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
+  double* row = out + t * (int64_t)(1 + P.n_par);
+  if (lane == 0) epilogue<Real, NL>(P, consts[t], tot[wid], oe - ob, row, row + 1, W.status);
+  __syncwarp();
+  if (adam_scale && isfinite(row[0])) {
+    const int step = *W.adam_t;
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    double* th = pm + t * (int64_t)P.n_par;
+    double* m1 = W.adam_m1 + t * (int64_t)P.n_par;
+    double* m2 = W.adam_m2 + t * (int64_t)P.n_par;
+    for (int p = lane; p < P.n_par; p += 32) {
+      const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
+      if (fx) continue;
+      const double sc = adam_scale[t * (int64_t)P.n_par + p];
+      const double gsc = row[1 + p] * sc;
+      m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
+      m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
+      const double mh = m1[p] / c1, vh = m2[p] / c2;
+      th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
     }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      int64_t r0 = __ldcg(W.tile_start + toy), r1 = __ldcg(W.tile_start + toy + 1);
-      rows_sum_few<NA>(W.partials, r0, r1, tot);
-      if (threadIdx.x == 0) {
-        int64_t ob = offsets[toy], oe = offsets[toy + 1];
-        ob = ob < 0 ? 0 : (ob > stride ? stride : ob);
-        oe = oe < ob ? ob : (oe > stride ? stride : oe);
-        int64_t nt = oe - ob;
-        double* row = out + toy * (int64_t)(1 + P.n_par);
-        epilogue<Real, NL>(P, K, tot, nt, row, row + 1, W.status);
-        W.toy_counter[toy] = 0u;
-        if (adam_scale && isfinite(row[0])) {
-          // Adam (Kingma & Ba 2015) in units of the toy's scale row
-          const int step = *W.adam_t;
-          const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
-          const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-          double* th = pm + toy * (int64_t)P.n_par;
-          double* m1 = W.adam_m1 + toy * (int64_t)P.n_par;
-          double* m2 = W.adam_m2 + toy * (int64_t)P.n_par;
-          for (int p = 0; p < P.n_par; ++p) {
-            bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
-            if (fx) continue;
-            const double sc = adam_scale[toy * (int64_t)P.n_par + p];
-            double gsc = row[1 + p] * sc;
-            m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
-            m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
-            double mh = m1[p] / c1, vh = m2[p] / c2;
-            th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
-          }
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 

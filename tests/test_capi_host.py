@@ -115,7 +115,7 @@ def test_unsupported_shapes(rf):
                                           (lambda: datagen.c3(n=10), "f32", "fp32"),
                                           (lambda: datagen.c2(n=10), "f64", "fp64")])
 def test_specialised_kernels_compile_without_gpu(rf, make, dt, prec):
-    """rf_graph_compile's per-graph kernels (fused, toy tile, log P) compile
+    """rf_graph_compile's per-graph kernels (fused, toy segment, log P) compile
     with NVRTC for sm_103a; no device is needed for this step."""
     w = make()
     rc = rf.jit_check(w["spec"], dt, prec)
