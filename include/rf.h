@@ -161,7 +161,11 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events,
 /* Toy studies (RooStats-style, Sec. 1): many datasets of uneven size that
  * share one graph.  rf_graph_bind_events records the concatenated event
  * columns (dev; column j at events + j*n_events); toy t owns events
- * [offsets[t], offsets[t+1]).  Sizes the toy workspace for up to max_toys. */
+ * [offsets[t], offsets[t+1]).  Sizes the toy workspace for up to max_toys.
+ * A graph evaluated in FP32 over FP64 columns converts the columns to FP32
+ * here, once (round to nearest: the value every per-event conversion would
+ * give), and its toy calls read that copy (n_obs * n_events * 4 bytes, owned
+ * by the graph); bind again after changing the events.  Host-synchronous. */
 rf_status rf_graph_bind_events(rf_graph* g, const void* events,
                                int64_t n_events, int32_t max_toys);
 
@@ -206,10 +210,11 @@ rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events,
                        const double* params, double* nll, double* grad,
                        rf_stream stream);
 
-/* Launch configuration of the fused and segment kernels: threads per block
- * (64, 128 or 256), events per thread per iteration (FP32 eval: 4 or 8;
- * FP64 eval: 2 or 4) and resident blocks per SM used to size the grid
- * (1..8). */
+/* Launch configuration: threads per block (64, 128 or 256) and resident
+ * blocks per SM used to size the grid (1..8) of the fused and segment
+ * kernels, and events per thread per iteration of the fused kernel (FP32
+ * eval: 4 or 8; FP64 eval: 2 or 4; the toy segment kernel always takes the
+ * larger option). */
 typedef struct {
   int32_t block;
   int32_t ept;

@@ -222,6 +222,10 @@ struct rf_graph {
   // batched
   const void* bound_events = nullptr;
   bool bound = false;
+  // FP32 evaluation of FP64 columns: the toy columns rounded to FP32 once at
+  // bind time (what every per-event conversion would give)
+  float* bound32 = nullptr;
+  size_t bound32_elems = 0;
   int64_t bound_n = 0;
   int32_t max_toys = 0;
   int64_t max_toy_rows = 0;  // segment rows: launch warps + toys
@@ -259,10 +263,22 @@ static cudaKernel_t jit_fused(rf_graph* g, int ept, std::string* err) {
   return g->jk_fused[i];
 }
 
+// column type the toy kernels read: FP32-evaluated graphs read FP32 columns
+// (FP64 ones are converted at bind time)
+static int toy_coldt(const rf_graph* g) { return g->eval == RF_EVAL_FP32 ? RF_F32 : g->coldt; }
+// events per thread per chunk of the segment kernel: the larger option of the
+// precision (its per-chunk bookkeeping is spread over more events)
+static int toy_ept(const rf_graph* g) { return g->eval == RF_EVAL_FP32 ? 8 : 4; }
+static RfLaunchCfg toy_cfg(const rf_graph* g) {
+  RfLaunchCfg c = g->cfg;
+  c.ept = toy_ept(g);
+  return c;
+}
+
 static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
-  int i = ept_index(g->eval, g->coldt, ept);
+  int i = ept_index(g->eval, toy_coldt(g), ept);
   if (!g->jk_toys[i]) {
-    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_TOYS, ept, nullptr, err);
+    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g), RF_JIT_TOYS, ept, nullptr, err);
     if (k) {  // its stage ring may use more than 48 KB of shared memory
       int optin = 0;
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
@@ -284,6 +300,7 @@ static void free_work(rf_graph* g) {
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
+  cudaFree(g->bound32);
   cudaFree(g->stage);
   cudaFree(g->plain_buf);
   cudaFree(g->plain_partials);
@@ -411,9 +428,14 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
   if (s) return s;
   std::string err;
   const int ept = desc->eval_precision == RF_EVAL_FP32 ? 4 : (desc->column_dtype == RF_F64 ? 2 : 4);
-  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_LOGP})
-    if (!rf_jit_compile_only(P, desc->eval_precision, desc->column_dtype, kind, ept, &err))
+  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_LOGP}) {
+    // FP32-evaluated toy kernels read FP32 columns (converted at bind time)
+    const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
+    const int cd = (kind == RF_JIT_TOYS && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
+    const int ke = kind == RF_JIT_TOYS ? (fp32 ? 8 : 4) : ept;
+    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, &err))
       return fail(RF_ECUDA, err);
+  }
   return RF_OK;
 }
 
@@ -587,11 +609,28 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m1, sizeof(double) * np * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
   if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
+  const void* toy_events = events;
+  if (g->eval == RF_EVAL_FP32 && g->coldt == RF_F64) {
+    const size_t elems = (size_t)g->n_obs * (size_t)n_events;
+    if (elems > g->bound32_elems) {
+      cudaFree(g->bound32);
+      g->bound32 = nullptr;
+      g->bound32_elems = 0;
+      e = cudaMalloc(&g->bound32, sizeof(float) * std::max<size_t>(elems, 1));
+      if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: FP32 column allocation failed");
+      g->bound32_elems = elems;
+    }
+    int ce = rf_columns_to_f32(static_cast<const double*>(events), g->bound32, (int64_t)elems,
+                               nullptr);
+    if (ce == 0) ce = (int)cudaDeviceSynchronize();
+    if (ce) return cuda_fail((cudaError_t)ce, "bind: FP32 column conversion");
+    toy_events = g->bound32;
+  }
   if (g->jit) {
     std::string err;
-    if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
+    if (!jit_toys(g, toy_ept(g), &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
-  g->bound_events = events;
+  g->bound_events = toy_events;
   g->bound = true;
   g->bound_n = n_events;
   g->max_toys = max_toys;
@@ -605,9 +644,9 @@ static rf_status batched_checks(rf_graph* g, const int64_t* offsets, int32_t toy
   if (!g->bound) return fail(RF_EINVAL, "rf_graph_bind_events was not called");
   if (toys < 1 || toys > g->max_toys) return fail(RF_EINVAL, "toys must be in 1..max_toys");
   if (!offsets || !pm || !out) return fail(RF_EINVAL, "NULL argument");
-  if (g->jit && !g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)]) {
+  if (g->jit && !g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))]) {
     std::string err;
-    if (!jit_toys(g, g->cfg.ept, &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
+    if (!jit_toys(g, toy_ept(g), &err)) return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
   return RF_OK;
 }
@@ -617,10 +656,10 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
   rf_status s = batched_checks(g, offsets, toys, params_matrix, out);
   if (s) return s;
   int n = 0;
-  int e = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
+  int e = rf_launch_batched(g->prog, g->eval, toy_coldt(g), toy_cfg(g), g->num_sms, g->bound_events,
                             g->bound_n, offsets, toys, const_cast<double*>(params_matrix), out,
                             g->work, nullptr, 0.0, g->max_toy_rows,
-                            g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
+                            g->jit ? g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))] : nullptr,
                             stream, &n);
   g->last_launches = n;
   if (e) return cuda_fail((cudaError_t)e, "rf_nll_batched launch");
@@ -656,10 +695,10 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
     e = cudaStreamBeginCapture(fs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys capture");
     int n = 0;
-    le = rf_launch_batched(g->prog, g->eval, g->coldt, g->cfg, g->num_sms, g->bound_events,
+    le = rf_launch_batched(g->prog, g->eval, toy_coldt(g), toy_cfg(g), g->num_sms, g->bound_events,
                            g->bound_n, offsets, toys, params_matrix, out, g->work, scale, lr,
                            g->max_toy_rows,
-                           g->jit ? g->jk_toys[ept_index(g->eval, g->coldt, g->cfg.ept)] : nullptr,
+                           g->jit ? g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))] : nullptr,
                            fs, &n);
     e = cudaStreamEndCapture(fs, &graph);
     if (le) {
@@ -741,7 +780,7 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
   if (g->jit) {
     std::string err;
     if (!jit_fused(g, cfg->ept, &err)) return fail(RF_ECUDA, "JIT fused kernel: " + err);
-    if (g->bound && !jit_toys(g, cfg->ept, &err))
+    if (g->bound && !jit_toys(g, toy_ept(g), &err))
       return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
   g->cfg.block = cfg->block;

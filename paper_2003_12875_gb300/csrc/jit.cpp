@@ -113,9 +113,11 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   o << "  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
-  // RF_JIT_MINBLOCKS=k asks the compiler to fit k blocks of 256 threads per SM
-  // (fewer registers per thread, more warps to hide latency)
-  std::string lb = "__launch_bounds__(256)";
+  // The fused kernel is declared for 2 resident blocks of 256 threads per SM:
+  // without a minimum, ptxas budgets registers for 3 blocks and schedules the
+  // event loop with less overlap (measured slower on the Crystal Ball + ARGUS
+  // model).  RF_JIT_MINBLOCKS=k asks for k blocks instead.
+  std::string lb = "__launch_bounds__(256, 2)";
 
   if (const char* mb = getenv("RF_JIT_MINBLOCKS"))
     if (atoi(mb) > 0) lb = "__launch_bounds__(256, " + std::to_string(atoi(mb)) + ")";

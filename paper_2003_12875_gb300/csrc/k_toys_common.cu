@@ -12,6 +12,23 @@ RF_TOYS_DECL(f32, c64)
 RF_TOYS_DECL(f64, c32)
 RF_TOYS_DECL(f64, c64)
 
+namespace {
+__global__ void columns_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out,
+                                      int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(in[i]);
+}
+}  // namespace
+
+int rf_columns_to_f32(const double* in, float* out, int64_t n, void* stream) {
+  if (n <= 0) return 0;
+  int64_t g = (n + 255) / 256;
+  const int grid = (int)(g > 65536 ? 65536 : g);
+  columns_to_f32_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
+  return (int)cudaGetLastError();
+}
+
 size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
@@ -22,7 +39,7 @@ template <typename Real>
 int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, int64_t stride,
                     int64_t warps, double* pm, double* out, RfWork W,
                     const double* adam_scale, double adam_lr, cudaStream_t st) {
-  const int fb = 256, fg = (toys + fb / 32 - 1) / (fb / 32);
+  const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, one warp per block
   switch (P.n_leaves) {
     case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
@@ -45,20 +62,29 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   // segment rows: one per (warp, toy) pair that shares events, at most
   // warps + toys of them
   const int wpb = cfg.block / 32;
-  int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
-  const int64_t room = max_rows - toys;
-  if (wpb < 1 || room < wpb) return (int)cudaErrorInvalidValue;
-  if (grid * wpb > room) grid = room / wpb;
-  const int64_t warps = grid * wpb;
   int vec = 0;
   int64_t head = 0;
   const size_t esz = coldt ? 8 : 4;
   rf_vec_plan(P, events, n_events, (int)esz, &vec, &head);
   // stage ring per warp: as many stages of 32*EPT events (all columns) as
-  // fit in about 96 KB per block, 2..8
+  // fit in about 64 KB per block, 2..8
   const size_t stage_bytes = (size_t)std::max(P.n_cols, 1) * 32 * cfg.ept * esz;
-  int stages = (int)std::min<size_t>(8, std::max<size_t>(2, (96u << 10) / (wpb * stage_bytes)));
+  int stages = (int)std::min<size_t>(8, std::max<size_t>(2, (64u << 10) / (wpb * stage_bytes)));
   const size_t smem = (size_t)wpb * (8 * 8 + stages * stage_bytes);
+  // grid: the SMs times the blocks of this size that fit on one (registers,
+  // shared memory), at least the configured blocks per SM
+  int fit = 0;
+  if (jit_toys &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, reinterpret_cast<const void*>(jit_toys),
+                                                    cfg.block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    fit = 0;
+  }
+  int64_t grid = (int64_t)num_sms * std::max(cfg.blocks_per_sm, std::min(fit, 8));
+  const int64_t room = max_rows - toys;
+  if (wpb < 1 || room < wpb) return (int)cudaErrorInvalidValue;
+  if (grid * wpb > room) grid = room / wpb;
+  const int64_t warps = grid * wpb;
 
   int pb = 32;  // few threads per block: the FP64 work spreads over SMs
   if (const char* v = getenv("RF_TOY_PREP_BLOCK")) pb = atoi(v) >= 1 && atoi(v) <= 256 ? atoi(v) : 32;

@@ -433,14 +433,11 @@ __device__ __forceinline__ float exp_neg_approx(float x) {
 // mantissa is odd); a carry out of the mantissa correctly bumps the
 // exponent.  Zero, float-subnormal, overflowing, infinite and NaN inputs go
 // through the hardware conversion.  Tested bit for bit against it.
-// The rare cases out of line, so that the compiler cannot turn the branch into
-// an FP64-pipe conversion executed for every value.
-static __device__ __noinline__ float d2f_hw(double x) { return __double2float_rn(x); }
 __device__ __forceinline__ float d2f_rn(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e - 897u >= 253u) return d2f_hw(x);  // float exponent outside 1..253
+  if (e - 897u >= 253u) return __double2float_rn(x);  // float exponent outside 1..253
   unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rem = lo & 0x1fffffffu;
   bits += (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ? 1u : 0u;
@@ -716,6 +713,55 @@ __device__ inline void block_sum_ds(const float (&hs)[N], const float (&ls)[N], 
   __syncthreads();
 }
 
+// As block_sum_ds, but the block totals stay FP32 pairs: out[i] (shared).
+template <int N, unsigned long long MASK>
+__device__ inline void block_sum_ds2(const float (&hs)[N], const float (&ls)[N], float2* red,
+                                     float2* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (!((MASK >> i) & 1ull)) continue;
+    float h = hs[i], l = ls[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      ds_add(h, l, h2, l2);
+    }
+    if (lane == 0) red[wid * N + i] = make_float2(h, l);
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    float h = 0.f, l = 0.f;
+    if ((MASK >> threadIdx.x) & 1ull)
+      for (int w = 0; w < nw; ++w) ds_add(h, l, red[w * N + threadIdx.x].x, red[w * N + threadIdx.x].y);
+    out[threadIdx.x] = make_float2(h, l);
+  }
+  __syncthreads();
+}
+
+// Rows [r0, r1) of FP32-pair partials (pair i of row r in the 8-byte slot
+// partials[r * RF_NACC_MAX + i]) summed in FP32-pair arithmetic in a fixed
+// order for a given block size; FP64 totals in out[0..N) (shared).
+template <int N, unsigned long long MASK>
+__device__ inline void rows_sum_ds(const double* partials, int64_t r0, int64_t r1, float2* red,
+                                   double* out) {
+  float h[N], l[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) h[i] = l[i] = 0.f;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const float2* row = reinterpret_cast<const float2*>(partials + r * RF_NACC_MAX);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if ((MASK >> i) & 1ull) {
+        const float2 v = __ldcg(row + i);
+        ds_add(h[i], l[i], v.x, v.y);
+      }
+  }
+  block_sum_ds<N, MASK>(h, l, red, out);
+}
+
 // Sum rows [r0, r1) of partials[row * RF_NACC_MAX + i] for i < N, in a fixed
 // order for a given block size; result in out[0..N) (shared).
 template <int N>
@@ -789,6 +835,71 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
                              : (unsigned)RF_STATUS_NONFINITE_BIT);
   }
   *nll = v;
+}
+
+// The epilogue on one warp (all 32 lanes): the NLL's terms on separate lanes
+// summed by a shuffle tree, and gradient component p on lane p (the FP64 unit
+// takes one warp instruction at a time however many lanes are active, so the
+// parallel form is as cheap per instruction as the serial one and its chains
+// are short).  Same formulas as epilogue().
+template <typename Real, int NL>
+__device__ __forceinline__ void epilogue_warp(const RfProgram& P, const RfConsts<Real>& K,
+                                     const double* T, int64_t n, double* nll, double* grad,
+                                     unsigned int* status) {
+  const int lane = threadIdx.x & 31;
+  const int C = P.n_comp;
+  double term = 0.0;
+  if (lane == 0) {
+    term = T[0];
+  } else if (lane <= C) {
+    const int c = lane - 1;
+    if (!((K.zero_mask >> c) & 1)) term = T[1 + c] * K.delta_lo[c];
+  } else {
+    const int idx = lane - 1 - C, k = idx >> 2, j = idx & 3;
+    if (k < P.n_leaves && ((P.leaf[k].gmask >> j) & 1))
+      term = -(T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] * K.dtheta[k][j]);
+  }
+  const double L = warp_sum(term);
+  double v = -((double)n * K.beta_ref + L) + K.ext_sum;
+  const bool bad = K.bad || !isfinite(v);
+  if (grad) {
+    for (int p = lane; p < P.n_par; p += 32) {
+      double g = 0.0;
+      for (int k = 0; k < P.n_leaves; ++k) {
+        const RfLeafProg& lf = P.leaf[k];
+        for (int j = 0; j < RF_LEAF_MAXP; ++j)
+          if (((lf.gmask >> j) & 1) && lf.par[j] == p) {
+            const double S = ((K.zero_mask >> lf.comp) & 1) ? 0.0 : T[1 + lf.comp];
+            g -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] - S * K.dlogI[k][j];
+          }
+      }
+      for (int c = 0; c < C; ++c) {
+        if (!((P.coef_free >> c) & 1)) continue;
+        if (P.kind == RF_KIND_FRAC && c < C - 1 && P.coef_par[c] == p) {
+          const double Rc = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
+          const int l = C - 1;
+          const double Rl = ((K.zero_mask >> l) & 1) ? T[1 + l] : T[1 + l] / K.coef[l];
+          g -= Rc - Rl;
+        } else if (P.kind == RF_KIND_EXT && P.coef_par[c] == p) {
+          const double Rc = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
+          g += 1.0 - Rc;
+        }
+      }
+      const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
+      if (fx) g = 0.0;
+      if (bad) g = kNaN();
+      grad[p] = g;
+    }
+  }
+  if (lane == 0) {
+    if (bad) {
+      v = kInf();
+      if (status)
+        atomicOr(status, K.bad ? (unsigned)RF_STATUS_PARAM_DOMAIN_BIT
+                               : (unsigned)RF_STATUS_NONFINITE_BIT);
+    }
+    *nll = v;
+  }
 }
 
 }  // namespace rf

@@ -138,6 +138,9 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       const double* adam_scale, double adam_lr,
                       int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
                       int* launches);
+// FP64 -> FP32 (round to nearest) of n values, for the toy columns of an
+// FP32-evaluated graph (converted once at bind time)
+int rf_columns_to_f32(const double* in, float* out, int64_t n, void* stream);
 int rf_launch_plain(const RfProgram& prog, int coldt, const void* events,
                     int64_t n, const double* params, double* node_buf,
                     double* nll, double* grad, double* partials,

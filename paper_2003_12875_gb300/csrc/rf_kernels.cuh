@@ -183,27 +183,43 @@ struct Acc {
   }
 };
 
-// Block-wide FP64 totals of the per-thread accumulators, fixed order.
+// A block's row of partial sums and the last block's sum over all rows, in a
+// fixed order.  FP32 evaluation: FP32 pairs (TwoSum) from the thread sums to
+// the final total, one FP64 conversion per accumulator at the very end (the
+// FP64 pipe of this GPU is narrow); a pair sits in the row's 8-byte slot.
+// FP64 evaluation: FP64 throughout.  red: shared, 32 * NA doubles.
 template <typename Real, int NA, unsigned long long MASK>
-struct BlockReduce;
+struct BlockRow;
 template <int NA, unsigned long long MASK>
-struct BlockReduce<float, NA, MASK> {  // FP32 evaluation: FP32-pair arithmetic
-  static __device__ __forceinline__ void run(const Acc<float, NA, MASK>& acc, void* red,
-                                             double* tot) {
+struct BlockRow<float, NA, MASK> {
+  static __device__ __forceinline__ void write(const Acc<float, NA, MASK>& acc, double* red,
+                                               double* row) {
+    __shared__ float2 pr[NA];
     float ls[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) ls[i] = -acc.c[i];  // Kahan keeps -(lost low part)
-    block_sum_ds<NA, MASK>(acc.s, ls, static_cast<float2*>(red), tot);
+    block_sum_ds2<NA, MASK>(acc.s, ls, reinterpret_cast<float2*>(red), pr);
+    if (threadIdx.x < NA) reinterpret_cast<float2*>(row)[threadIdx.x] = pr[threadIdx.x];
+  }
+  static __device__ __forceinline__ void sum(const double* partials, int64_t rows, double* red,
+                                             double* tot) {
+    rows_sum_ds<NA, MASK>(partials, 0, rows, reinterpret_cast<float2*>(red), tot);
   }
 };
 template <int NA, unsigned long long MASK>
-struct BlockReduce<double, NA, MASK> {  // FP64 evaluation
-  static __device__ __forceinline__ void run(const Acc<double, NA, MASK>& acc, void* red,
-                                             double* tot) {
+struct BlockRow<double, NA, MASK> {
+  static __device__ __forceinline__ void write(const Acc<double, NA, MASK>& acc, double* red,
+                                               double* row) {
+    __shared__ double bt[NA];
     double val[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) val[i] = acc.value(i);
-    block_sum<NA>(val, static_cast<double*>(red), tot);
+    block_sum<NA>(val, red, bt);
+    if (threadIdx.x < NA) row[threadIdx.x] = bt[threadIdx.x];
+  }
+  static __device__ __forceinline__ void sum(const double* partials, int64_t rows, double* red,
+                                             double* tot) {
+    rows_sum<NA>(partials, 0, rows, red, tot);
   }
 };
 
@@ -339,19 +355,16 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     }
   }
 
-  BlockReduce<Real, NA, M::AMASK>::run(acc, red, tot);
-  if (threadIdx.x < NA) W.partials[(int64_t)blockIdx.x * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
+  BlockRow<Real, NA, M::AMASK>::write(acc, red, W.partials + (int64_t)blockIdx.x * RF_NACC_MAX);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(W.counter, 1u) == gridDim.x - 1) ? 1 : 0;
   __syncthreads();
   if (s_last) {
     __threadfence();
-    rows_sum<NA>(W.partials, 0, gridDim.x, red, tot);
-    if (threadIdx.x == 0) {
-      epilogue<Real, NL>(P, K, tot, n, nll, grad, W.status);
-      *W.counter = 0u;
-    }
+    BlockRow<Real, NA, M::AMASK>::sum(W.partials, gridDim.x, red, tot);
+    if (threadIdx.x < 32) epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
+    if (threadIdx.x == 0) *W.counter = 0u;
   }
 }
 
@@ -586,92 +599,90 @@ __device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity) {
 constexpr int kMaxStages = 8;
 }  // namespace bulk
 
-// Per-warp state of a toy walk: the current toy, its event range and
-// constants, and the running sums of the current segment.
-template <class M, typename Real>
-struct ToyWalk {
-  static constexpr int NL = M::NL_;
-  static constexpr int NA = RF_NACC(NL);
-  const RfConsts<Real>* consts;
-  const int64_t* offsets;
-  int64_t stride, w;
-  int32_t toys, t;
-  int64_t te;       // end of toy t (clamped)
-  bool bad, any;    // constants outside their domain; segment has events
-  EvalConsts<Real, NL> E;
-  Acc<Real, NA, M::AMASK> acc;
-
-  __device__ __forceinline__ void open(int32_t tt) {
-    t = tt;
-    te = toy_off(offsets, (int64_t)t + 1, stride);
-    const RfConsts<Real>& K = consts[t];
-    bad = K.bad != 0;
-    if (!bad) E.load(K);
-    acc.zero();
-    any = false;
-  }
-  __device__ __forceinline__ void close(double* partials) {
-    if (any) WarpRow<Real, NA, M::AMASK>::write(acc, partials + (w + t) * RF_NACC_MAX);
-  }
-  // move to the toy that holds event p (the toys in between are empty)
-  __device__ __forceinline__ void seek(int64_t p, double* partials) {
-    while (te <= p && t + 1 < toys) {
-      close(partials);
-      open(t + 1);
-    }
-  }
-};
-
 // Evaluate events [p0, p1) of a chunk that starts at event c0 and holds
-// 32*EPT events, column c at buf[c * CE + j]; lane l takes j = l + 32 k.
-// FULL: the chunk lies inside [p0, p1) (no per-event test).
+// CE = 32*EPT events, column c at buf[c * CE + j].  Lanes read 128-bit
+// vectors (conflict-free: a warp's loads cover contiguous 512 bytes): lane l
+// takes vectors l + 32 m, i.e. events V (l + 32 m) + r.  FULL: the chunk lies
+// inside [p0, p1) (no per-event test).
 template <class M, typename Real, typename Col, int EPT, bool FULL>
-__device__ __forceinline__ void eval_chunk(const RfProgram& P, ToyWalk<M, Real>& T,
+__device__ __forceinline__ void eval_chunk(const RfProgram& P, const EvalConsts<Real, M::NL_>& E,
+                                           Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc,
                                            const Col* buf, int64_t c0, int64_t p0, int64_t p1) {
   constexpr int NL = M::NL_;
   constexpr int NA = RF_NACC(NL);
   constexpr int CE = 32 * EPT;
+  constexpr int V = Vec<Col>::W;
+  static_assert(EPT % V == 0, "EPT must be a multiple of the vector width");
+  typedef typename Vec<Col>::T VT;
   const int lane = threadIdx.x & 31;
   Real q[NA];
 #pragma unroll
   for (int i = 0; i < NA; ++i) q[i] = Real(0);
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int j = lane + 32 * k;
-    const int64_t i = c0 + j;
-    if (FULL || (i >= p0 && i < p1)) {
-      Real xc[NL];
+  for (int m = 0; m < EPT / V; ++m) {
+    const int vi = lane + 32 * m;
+    Col xv[NL][V];
 #pragma unroll
-      for (int c = 0; c < NL; ++c)
-        xc[c] = (c < M::NCOL && c < P.n_cols) ? cvt<Real, Col>(buf[c * CE + j]) : Real(0);
-      M::template event<Real>(P, T.E, xc, q);
+    for (int c = 0; c < NL; ++c) {
+      if (c < M::NCOL && c < P.n_cols) {
+        const VT t = reinterpret_cast<const VT*>(buf + c * CE)[vi];
+        const Col* tc = reinterpret_cast<const Col*>(&t);
+#pragma unroll
+        for (int r = 0; r < V; ++r) xv[c][r] = tc[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < V; ++r) xv[c][r] = Col(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+      const int j = V * vi + r;
+      if (FULL || (c0 + j >= p0 && c0 + j < p1)) {
+        Real xc[NL];
+#pragma unroll
+        for (int c = 0; c < NL; ++c) xc[c] = cvt<Real, Col>(xv[c][r]);
+        M::template event<Real>(P, E, xc, q);
+      }
     }
   }
-  T.acc.add(q);
+  acc.add(q);
 }
 
-// Events [p0, p1) straight from the columns (ragged ends), lanes striding.
-template <class M, typename Real, typename Col>
-__device__ __forceinline__ void eval_global(const RfProgram& P, ToyWalk<M, Real>& T,
-                                            const Col* __restrict__ ev, int64_t stride,
-                                            int64_t p0, int64_t p1) {
-  iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p0 + (threadIdx.x & 31), p1, T.acc, 32);
-}
-
-// Walk [p0, p1) across toy boundaries; `run(a, b)` evaluates [a, b) with the
-// current toy's constants.
-template <class M, typename Real, class Run>
-__device__ __forceinline__ void walk(ToyWalk<M, Real>& T, double* partials, int64_t p0,
-                                     int64_t p1, Run run) {
-  while (p0 < p1) {
-    T.seek(p0, partials);
-    const int64_t q1 = p1 < T.te ? p1 : T.te;
-    if (q1 <= p0) break;  // only with a non-monotone offset table
-    if (!T.bad) run(p0, q1);
-    T.any = true;
-    p0 = q1;
+// The toy a warp is in: its event range [tb, te), constants, running sums.
+// seek() moves to the toy holding event p, writing the finished toy's row
+// (when it had events) and skipping empty toys; false only when p lies past
+// the last toy (a non-monotone offset table).
+template <class M, typename Real>
+struct ToyState {
+  static constexpr int NL = M::NL_;
+  static constexpr int NA = RF_NACC(NL);
+  int32_t t;
+  int64_t tb, te;
+  bool bad, any;
+  EvalConsts<Real, NL> E;
+  Acc<Real, NA, M::AMASK> acc;
+  __device__ __forceinline__ void open(const RfConsts<Real>* consts, const int64_t* offsets,
+                                       int64_t stride, int32_t tt) {
+    t = tt;
+    tb = toy_off(offsets, t, stride);
+    te = toy_off(offsets, (int64_t)t + 1, stride);
+    bad = consts[t].bad != 0;
+    if (!bad) E.load(consts[t]);
+    acc.zero();
+    any = false;
   }
-}
+  __device__ __forceinline__ void close(double* rows) {
+    if (any) WarpRow<Real, NA, M::AMASK>::write(acc, rows + (int64_t)t * RF_NACC_MAX);
+  }
+  __device__ __forceinline__ bool seek(const RfConsts<Real>* consts, const int64_t* offsets,
+                                       int64_t stride, int32_t toys, int64_t p, double* rows) {
+    while (te <= p && t + 1 < toys) {
+      close(rows);
+      open(consts, offsets, stride, t + 1);
+    }
+    return te > p;
+  }
+};
 
 // Segment kernel: warp w streams [start(w), start(w+1)) through its stage
 // ring (chunks of 32*EPT events from the first 16-byte-aligned event; the
@@ -680,18 +691,20 @@ __device__ __forceinline__ void walk(ToyWalk<M, Real>& T, double* partials, int6
 // stages and the search for the first toy need only the offsets and the
 // events, so they are issued before the wait for the prep kernel.
 // Dynamic shared memory: warps * (kMaxStages barriers + S stages of
-// n_cols * 32*EPT columns values).
+// n_cols * 32*EPT column values).
 template <class M, typename Real, typename Col, int EPT>
 __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* __restrict__ ev,
                                                  int64_t stride, int vec,
                                                  const int64_t* __restrict__ offsets,
                                                  int32_t toys, int stages, RfWork& W) {
+  constexpr int NL = M::NL_;
+  constexpr int NA = RF_NACC(NL);
   constexpr int CE = 32 * EPT;
   extern __shared__ __align__(128) unsigned char rf_dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   uint64_t* bars = reinterpret_cast<uint64_t*>(rf_dyn_smem) + wib * bulk::kMaxStages;
-  const size_t stage_elems = (size_t)P.n_cols * CE;
+  const int stage_elems = P.n_cols * CE;
   Col* ring = reinterpret_cast<Col*>(rf_dyn_smem + (size_t)wpb * bulk::kMaxStages * 8) +
               (size_t)wib * stages * stage_elems;
   const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(Col));
@@ -700,11 +713,11 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
   const ToySplit Sp = toy_split(offsets, toys, stride, (int64_t)gridDim.x * wpb);
   const bool active = w < Sp.N && Sp.E > Sp.B;
   int64_t wb = 0, we = 0, a0 = 0, nch = 0;
-  int32_t t0 = 0;
+  int32_t t = 0;
   if (active) {
     wb = Sp.start(w);
     we = Sp.start(w + 1);
-    t0 = find_toy(offsets, toys, stride, wb);
+    t = find_toy(offsets, toys, stride, wb);
     a0 = we;
     if (vec) {
       const uintptr_t a = reinterpret_cast<uintptr_t>(ev + (int64_t)P.col_obs[0] * stride + wb);
@@ -713,67 +726,92 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
       nch = (we - a0) / CE;
     }
   }
-  auto issue = [&](int64_t c) {  // lane 0: chunk c into stage c % stages
-    const int s = (int)(c % stages);
-    Col* dst = ring + (size_t)s * stage_elems;
-    bulk::arrive_expect_tx(&bars[s], stage_bytes);
-    for (int col = 0; col < P.n_cols; ++col)
-      bulk::copy(dst + (size_t)col * CE, ev + (int64_t)P.col_obs[col] * stride + a0 + c * CE,
-                 (uint32_t)(CE * sizeof(Col)), &bars[s]);
-  };
   if (lane == 0) {
     for (int s = 0; s < stages; ++s) bulk::bar_init(&bars[s], 1);
     bulk::fence_bar_init();
-    for (int64_t c = 0; c < nch && c < stages; ++c) issue(c);
+    for (int64_t c = 0; c < nch && c < stages; ++c) {
+      Col* dst = ring + (size_t)c * stage_elems;
+      bulk::arrive_expect_tx(&bars[c], stage_bytes);
+      for (int col = 0; col < P.n_cols; ++col)
+        bulk::copy(dst + col * CE, ev + (int64_t)P.col_obs[col] * stride + a0 + c * CE,
+                   (uint32_t)(CE * sizeof(Col)), &bars[c]);
+    }
   }
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (!active) return;
 
-  ToyWalk<M, Real> T;
-  T.consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  T.offsets = offsets;
-  T.stride = stride;
-  T.w = w;
-  T.toys = toys;
-  T.open(t0);
-  auto from_global = [&](int64_t p, int64_t q) {
-    eval_global<M, Real, Col>(P, T, ev, stride, p, q);
-  };
-  walk(T, W.partials, wb, a0, from_global);
-  for (int64_t c = 0; c < nch; ++c) {
-    const int s = (int)(c % stages);
-    if (!bulk::wait(&bars[s], (uint32_t)((c / stages) & 1))) {
+  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
+  ToyState<M, Real> T;
+  T.open(consts, offsets, stride, t);
+  double* rows = W.partials + w * RF_NACC_MAX;  // row of (w, t) = rows + t * RF_NACC_MAX
+  // ragged head, straight from the columns
+  for (int64_t p = wb; p < a0;) {
+    if (!T.seek(consts, offsets, stride, toys, p, rows)) break;
+    const int64_t q = a0 < T.te ? a0 : T.te;
+    if (!T.bad) iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p + lane, q, T.acc, 32);
+    T.any = true;
+    p = q;
+  }
+  // aligned chunks through the stage ring; s and ph: stage and phase of chunk c
+  int s = 0;
+  uint32_t ph = 0;
+  int64_t c0 = a0;
+  for (int64_t c = 0; c < nch; ++c, c0 += CE) {
+    if (!bulk::wait(&bars[s], ph)) {
       if (lane == 0) atomicOr(W.status, RF_STATUS_TIMEOUT_BIT);
-      // let the copies already issued land before the warp leaves
-      for (int64_t d = c + 1; d < nch && d < c + stages; ++d)
-        bulk::wait(&bars[d % stages], (uint32_t)((d / stages) & 1));
+      int ds = s;  // let the copies already issued land before the warp leaves
+      uint32_t dph = ph;
+      for (int64_t d = c + 1; d < nch && d < c + stages; ++d) {
+        if (++ds == stages) { ds = 0; dph ^= 1u; }
+        bulk::wait(&bars[ds], dph);
+      }
       return;
     }
-    const Col* buf = ring + (size_t)s * stage_elems;
-    const int64_t c0 = a0 + c * CE;
-    if (c0 >= T.te || c0 + CE > T.te) {  // a toy boundary inside (or at) the chunk
-      walk(T, W.partials, c0, c0 + CE, [&](int64_t p, int64_t q) {
-        eval_chunk<M, Real, Col, EPT, false>(P, T, buf, c0, p, q);
-      });
-    } else {
-      if (!T.bad) eval_chunk<M, Real, Col, EPT, true>(P, T, buf, c0, c0, c0 + CE);
+    const Col* buf = ring + s * stage_elems;
+    if (c0 + CE <= T.te && c0 >= T.tb) {  // the whole chunk in the current toy
+      if (!T.bad) eval_chunk<M, Real, Col, EPT, true>(P, T.E, T.acc, buf, c0, c0, c0 + CE);
       T.any = true;
+    } else {
+      for (int64_t p = c0; p < c0 + CE;) {
+        if (!T.seek(consts, offsets, stride, toys, p, rows)) break;
+        const int64_t q = c0 + CE < T.te ? c0 + CE : T.te;
+        if (!T.bad) eval_chunk<M, Real, Col, EPT, false>(P, T.E, T.acc, buf, c0, p, q);
+        T.any = true;
+        p = q;
+      }
     }
     __syncwarp();
-    if (lane == 0 && c + stages < nch) {
+    if (lane == 0 && c + stages < nch) {  // refill the stage with the chunk `stages` ahead
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(c + stages);
+      bulk::arrive_expect_tx(&bars[s], stage_bytes);
+      const int64_t src = a0 + (c + stages) * CE;
+      for (int col = 0; col < P.n_cols; ++col)
+        bulk::copy(const_cast<Col*>(buf) + col * CE, ev + (int64_t)P.col_obs[col] * stride + src,
+                   (uint32_t)(CE * sizeof(Col)), &bars[s]);
+    }
+    if (++s == stages) {
+      s = 0;
+      ph ^= 1u;
     }
   }
-  walk(T, W.partials, a0 + nch * CE, we, from_global);
-  T.close(W.partials);
+  // ragged tail
+  for (int64_t p = a0 + nch * CE; p < we;) {
+    if (!T.seek(consts, offsets, stride, toys, p, rows)) break;
+    const int64_t q = we < T.te ? we : T.te;
+    if (!T.bad) iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p + lane, q, T.acc, 32);
+    T.any = true;
+    p = q;
+  }
+  T.close(rows);
 }
 
-// Finalize kernel: one warp per toy.  Lane i sums accumulator i over the
-// toy's segment rows in row order (Neumaier, FP64); lane 0 then runs the
-// epilogue into out row t, and, for a fit, the lanes apply one Adam step
-// (Kingma & Ba 2015) to the toy's free parameters in units of its scale row.
+// Finalize kernel: one thread per toy (the FP64 unit takes one warp
+// instruction at a time whatever the number of active lanes, so 32 toys per
+// warp cost what one does).  The thread sums the toy's segment rows in row
+// order, runs the FP64 epilogue into out row t and, for a fit, applies one
+// Adam step (Kingma & Ba 2015) to the toy's free parameters in units of its
+// scale row.
 template <typename Real, int NL>
 __device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
                                                   const int64_t* __restrict__ offsets,
@@ -782,33 +820,27 @@ __device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
                                                   const double* __restrict__ adam_scale,
                                                   double adam_lr) {
   constexpr int NA = RF_NACC(NL);
-  __shared__ double tot[32][RF_NACC_MAX];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= toys) return;
   const ToySplit S = toy_split(offsets, toys, stride, warps);
   int64_t ob = toy_off(offsets, t, stride), oe = toy_off(offsets, t + 1, stride);
   ob = ob < S.B ? S.B : ob;
   oe = oe > S.E ? S.E : oe;
   if (oe < ob) oe = ob;
-  if (lane < NA) {
-    double v = 0.0, c = 0.0;
-    if (oe > ob) {
-      const int64_t r1 = S.warp_of(oe - 1) + t;
-      for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
-        const double x = __ldcg(W.partials + r * RF_NACC_MAX + lane);
-        const double s = v + x;
-        c += (fabs(v) >= fabs(x)) ? (v - s) + x : (x - s) + v;
-        v = s;
-      }
+  double tot[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) tot[i] = 0.0;
+  if (oe > ob) {  // a toy meets a few warp ranges: plain FP64 sums of a few rows
+    const int64_t r1 = S.warp_of(oe - 1) + t;
+    for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
+      const double* row = W.partials + r * RF_NACC_MAX;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) tot[i] += __ldcg(row + i);
     }
-    tot[wid][lane] = v + c;
   }
-  __syncwarp();
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
   double* row = out + t * (int64_t)(1 + P.n_par);
-  if (lane == 0) epilogue<Real, NL>(P, consts[t], tot[wid], oe - ob, row, row + 1, W.status);
-  __syncwarp();
+  epilogue<Real, NL>(P, consts[t], tot, oe - ob, row, row + 1, W.status);
   if (adam_scale && isfinite(row[0])) {
     const int step = *W.adam_t;
     const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
@@ -816,7 +848,7 @@ __device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
     double* th = pm + t * (int64_t)P.n_par;
     double* m1 = W.adam_m1 + t * (int64_t)P.n_par;
     double* m2 = W.adam_m2 + t * (int64_t)P.n_par;
-    for (int p = lane; p < P.n_par; p += 32) {
+    for (int p = 0; p < P.n_par; ++p) {
       const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
       if (fx) continue;
       const double sc = adam_scale[t * (int64_t)P.n_par + p];
