@@ -136,7 +136,14 @@ rf_status rf_graph_destroy(rf_graph* g);
  *   params  dev [n_params] FP64
  *   nll     dev [1] FP64
  *   grad    dev [n_params] FP64 or NULL; entries of fixed params are 0
- * One fused kernel launch on `stream`; no allocation, no host sync. */
+ * Two launches on `stream`, no allocation, no host sync: an FP64 prologue
+ * (normalisations, coefficients) and the fused event kernel.  The prologue
+ * is a programmatic dependent of the kernel before it in the stream, so that
+ * back-to-back calls overlap a call's FP64 prologue with the previous call's
+ * event pass; it reads `params` while that kernel may still run, so params
+ * must not be written by the kernels of the call immediately before on the
+ * same stream (e.g. passing one call's gradient output as the next call's
+ * params).  Work of any other kind between the two calls orders as usual. */
 rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events,
                  const double* params, double* nll, double* grad,
                  rf_stream stream);

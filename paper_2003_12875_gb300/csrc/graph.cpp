@@ -363,18 +363,14 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   }
   g->work.status = g->work.counter + 1;
   g->work.adam_t = reinterpret_cast<int32_t*>(g->work.counter + 2);
-  g->work.pro_ticket = g->work.counter + 3;
   // constants of the separate prologue kernel
-  e = cudaMalloc(&g->pro_buf, rf_consts_size(g->eval) + sizeof(double) * RF_MAXL +
-                                  sizeof(int) * RF_MAXL + 64);
+  e = cudaMalloc(&g->pro_buf, rf_consts_size(g->eval));
   if (e != cudaSuccess) {
     free_work(g);
     delete g;
     return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
   }
   g->work.consts = g->pro_buf;
-  g->work.pro_lnI = reinterpret_cast<double*>(static_cast<char*>(g->pro_buf) + rf_consts_size(g->eval));
-  g->work.pro_ok = reinterpret_cast<int*>(g->work.pro_lnI + RF_MAXL);
   // Specialise the fused kernel for this graph unless RF_JIT=0.  If that is
   // not possible the graph keeps the precompiled generic kernels (same device
   // code, run-time dispatch); rf_graph_uses_jit reports which one runs.

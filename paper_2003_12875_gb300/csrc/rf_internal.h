@@ -96,9 +96,6 @@ struct RfWork {
   // single dataset: constants from the separate prologue kernel (NULL: each
   // block computes them itself)
   void* consts;            // [1] RfConsts<Real>
-  double* pro_lnI;         // [RF_MAXL]
-  int* pro_ok;             // [RF_MAXL]
-  unsigned int* pro_ticket;  // [1]
 };
 
 struct RfLaunchCfg {
@@ -122,9 +119,10 @@ RF_DECL_FUSED(f32, c64)
 RF_DECL_FUSED(f64, c32)
 RF_DECL_FUSED(f64, c64)
 
-// FP64 prologue kernel for the single-dataset path: one block per leaf, the
-// last block combines; writes W.consts and lets the dependent (fused) kernel
-// launch at once (programmatic dependent launch).
+// FP64 prologue kernel for the single-dataset path: one block, one warp per
+// leaf; writes W.consts.  Launched as a programmatic dependent of the previous
+// kernel in the stream and lets its own dependent (the fused kernel) launch at
+// once.
 int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
                        rf_cuda_stream st);
 

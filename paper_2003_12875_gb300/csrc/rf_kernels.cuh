@@ -335,6 +335,9 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     double* dst = reinterpret_cast<double*>(&K);
     for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = __ldcg(src + w);
     __syncthreads();
+    // the constants are in shared memory: the next call's prologue may start
+    // (it publishes new constants only after this grid has finished)
+    asm volatile("griddepcontrol.launch_dependents;");
   } else {
     block_prologue(P, params, K, lnI, ok);
   }
@@ -396,32 +399,26 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
   }
 }
 
-// The single-dataset prologue as its own grid: block k computes leaf k (the
-// FP64 work of different leaves runs on different SMs), the last block to
-// finish combines.  It lets the dependent fused grid launch immediately.
+// Single-dataset prologue: one block, warp k computes leaf k's normalisation
+// and constants (the leaves' FP64 chains run on different SM sub-partitions),
+// thread 0 combines, all in shared memory.  It lets its dependent (the fused
+// kernel) launch at once, and it is itself launched as a programmatic
+// dependent of the previous kernel in the stream: when that is the previous
+// call's fused kernel, this FP64 work overlaps it, and the wait before the
+// constants are published keeps that kernel's readers safe.
 template <typename Real>
 __device__ __forceinline__ void prologue_body(const RfProgram& P, const double* __restrict__ params,
                                               RfWork& W) {
   asm volatile("griddepcontrol.launch_dependents;");
-  RfConsts<Real>* K = static_cast<RfConsts<Real>*>(W.consts);
-  const int k = blockIdx.x;
-  if (threadIdx.x != 0 || k >= P.n_leaves) return;
-  double lnI = 0.0;
-  const bool ok = leaf_consts(P, params, *K, k, &lnI);
-  W.pro_lnI[k] = lnI;
-  W.pro_ok[k] = ok ? 1 : 0;
-  __threadfence();
-  if (atomicAdd(W.pro_ticket, 1u) == (unsigned)P.n_leaves - 1u) {
-    __threadfence();
-    double l[RF_MAXL];
-    bool all = true;
-    for (int j = 0; j < P.n_leaves; ++j) {
-      l[j] = __ldcg(W.pro_lnI + j);
-      all &= __ldcg(W.pro_ok + j) != 0;
-    }
-    comb_consts(P, params, *K, l, all);
-    *W.pro_ticket = 0u;
-  }
+  __shared__ RfConsts<Real> K;
+  __shared__ double lnI[RF_MAXL];
+  __shared__ int ok[RF_MAXL];
+  block_prologue(P, params, K, lnI, ok);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
+  const double* src = reinterpret_cast<const double*>(&K);
+  double* dst = static_cast<double*>(W.consts);
+  for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
 }
 
 // ------------------------------------------------------ toy studies

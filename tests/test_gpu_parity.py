@@ -170,6 +170,42 @@ def test_run_to_run_bitwise_determinism(rf, prec):
         assert torch.equal(a, b)
 
 
+def test_back_to_back_calls_with_changing_parameters(rf):
+    """Calls queued back to back on one stream (each prologue overlaps the
+    previous call's event pass): parameters rewritten between calls by a
+    device kernel and by a host copy, two graphs interleaved, outputs written
+    to separate buffers; every result equals the same call made alone."""
+    w, p, *_ = workload("c5")
+    G = rf.Graph(w["spec"], "f32", "fp32")
+    w2, p2, *_ = workload("c2")
+    G2 = rf.Graph(w2["spec"], "f64", "fp32")
+    ev, ev2 = to_dev(w), to_dev(w2)
+    pts = [np.array(p) * (1.0 + 1e-3 * k * np.array([0, 1, 1, 0, 0, 1, 0, 1, 1]))
+           for k in range(4)]
+    alone = []
+    for q in pts:
+        alone.append(torch.cat(G.nll(ev, params_dev(list(q)))).cpu())
+    alone2 = torch.cat(G2.nll(ev2, params_dev(p2))).cpu()
+    torch.cuda.synchronize()
+    pd = params_dev(list(pts[0]))
+    pd2 = params_dev(p2)
+    outs = [torch.empty(1 + len(p), dtype=torch.float64, device=DEV) for _ in pts]
+    out2 = torch.empty(1 + len(p2), dtype=torch.float64, device=DEV)
+    for k in range(len(pts)):
+        if k == 1:
+            pd.copy_(torch.from_numpy(pts[1]).to(DEV))          # device-side update
+        elif k == 2:
+            pd.copy_(torch.from_numpy(pts[2]), non_blocking=False)  # host copy
+        elif k == 3:
+            pd.mul_(0).add_(torch.from_numpy(pts[3]).to(DEV))   # two device kernels
+        G.nll(ev, pd, out=outs[k])
+        G2.nll(ev2, pd2, out=out2)
+    torch.cuda.synchronize()
+    for k in range(len(pts)):
+        assert torch.equal(outs[k].cpu(), alone[k]), k
+    assert torch.equal(out2.cpu(), alone2)
+
+
 def test_gradient_against_finite_differences(rf):
     """GPU adjoint vs Richardson differences of the GPU FP64 NLL (<= 1e-4)."""
     w, p, v, g, sc = workload("c2")
