@@ -308,21 +308,63 @@ def toy_bench(args, rf, torch, rank, world, pk):
     for _ in range(args.warmup):
         G.nll_batched(off, pm, out=out)
     torch.cuda.synchronize()
+    uuid = None
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        uuid = u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
     a.record()
     for _ in range(args.steps):
         G.nll_batched(off, pm, out=out)
     b.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(a.elapsed_time(b), dist, "cuda") / args.steps
+    # roofline of the step (prep + segment + finalize kernels): FP32 issue for
+    # FP32 evaluation (columns read as FP32, rounded once at bind), with the
+    # HBM figure beside it
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_mhz = float(pk.get("sm_max_mhz") or 2070.0)
+    col_bytes = 4 if args.precision == "fp32" else 8
+    hbm_gbs = n * col_bytes / (ms * 1e-3) / 1e9
+    hbm = {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": hbm_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
+           "bytes_per_launch": n * col_bytes}
+    if args.precision == "fp32":
+        instr = algorithmic_instr_per_event(w["spec"], 8, False)
+        peak = sms * 128 * sm_mhz * 1e6
+        achieved = instr * n / (ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                    "unit": "G FP32-lane instr/s", "frac": achieved / peak, "traffic": None,
+                    "kernel": "rf_toys_jit (+ prep, finalize)",
+                    "algorithmic_instr_per_event": instr,
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                    "launch_ms": ms, "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", **hbm, "traffic": None, "kernel": "rf_toys_jit",
+                    "launch_ms": ms}
     line = {"metric": METRIC, "value": job_throughput(n, world, ms), "unit": "events/s",
             "toy_nll_per_s": world * toys / (ms * 1e-3), "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": w["name"], "toys": toys, "events": n,
-                       "launch": G.get_launch(), "kernel": G.uses_jit()},
-            "gpu_launches": G.last_launches() * args.steps}
+                       "launch": G.get_launch(), "kernel": G.uses_jit(),
+                       "l2": f"inputs larger than L2 ({n * col_bytes / 1e6:.0f} MB > 2 x 129 MB), "
+                             "no flush"},
+            "clocks": clk,
+            "gpu_launches": G.last_launches() * args.steps, "roofline": roofline}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

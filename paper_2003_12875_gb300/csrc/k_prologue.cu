@@ -4,6 +4,28 @@
 #include "rf_kernels.cuh"
 
 namespace rf {
+// Single-dataset prologue: one block, warp k computes leaf k's normalisation
+// and constants (the leaves' FP64 chains run on different SM sub-partitions),
+// thread 0 combines, all in shared memory.  It lets its dependent (the fused
+// kernel) launch at once, and it is itself launched as a programmatic
+// dependent of the previous kernel in the stream: when that is the previous
+// call's fused kernel, this FP64 work overlaps it, and the wait before the
+// constants are published keeps that kernel's readers safe.
+template <typename Real>
+__device__ __forceinline__ void prologue_body(const RfProgram& P, const double* __restrict__ params,
+                                              RfWork& W) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  __shared__ RfConsts<Real> K;
+  __shared__ double lnI[RF_MAXL];
+  __shared__ int ok[RF_MAXL];
+  block_prologue(P, params, K, lnI, ok);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
+  const double* src = reinterpret_cast<const double*>(&K);
+  double* dst = static_cast<double*>(W.consts);
+  for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(32 * RF_MAXL) prologue_kernel(const RfProgram P,
                                                                 const double* __restrict__ params,

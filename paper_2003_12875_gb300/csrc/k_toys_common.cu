@@ -39,7 +39,7 @@ template <typename Real>
 int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, int64_t stride,
                     int64_t warps, double* pm, double* out, RfWork W,
                     const double* adam_scale, double adam_lr, cudaStream_t st) {
-  const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, one warp per block
+  const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, 32 toys per block
   switch (P.n_leaves) {
     case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
@@ -86,9 +86,9 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   if (grid * wpb > room) grid = room / wpb;
   const int64_t warps = grid * wpb;
 
-  int pb = 32;  // few threads per block: the FP64 work spreads over SMs
-  if (const char* v = getenv("RF_TOY_PREP_BLOCK")) pb = atoi(v) >= 1 && atoi(v) <= 256 ? atoi(v) : 32;
-  const int pg = (toys + pb - 1) / pb > 0 ? (toys + pb - 1) / pb : 1;
+  // prep: blocks of one warp per leaf and 32 toys
+  const int pb = 32 * std::max(P.n_leaves, 1);
+  const int pg = (toys + 31) / 32 > 0 ? (toys + 31) / 32 : 1;
   int32_t* at = adam_scale ? W.adam_t : nullptr;
   if (eval)
     rf::toy_prep_kernel<double><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,

@@ -66,7 +66,7 @@ struct RfProgram {
 
 // Per-call constants, computed in FP64 from the parameter vector (prologue).
 template <typename Real>
-struct RfConsts {
+struct alignas(16) RfConsts {  // 16-byte multiple: arrays of it are bulk-copied
   Real pc[RF_MAXL][RF_PC];     // per-leaf evaluation constants
   Real delta[RF_MAXC];         // delta_c rounded to Real (-inf: coef_c == 0)
   Real delta_nc[RF_MAXC];      // delta_c - log coef_c (used when coef_c == 0)

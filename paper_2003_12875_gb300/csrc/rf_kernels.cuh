@@ -399,28 +399,6 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
   }
 }
 
-// Single-dataset prologue: one block, warp k computes leaf k's normalisation
-// and constants (the leaves' FP64 chains run on different SM sub-partitions),
-// thread 0 combines, all in shared memory.  It lets its dependent (the fused
-// kernel) launch at once, and it is itself launched as a programmatic
-// dependent of the previous kernel in the stream: when that is the previous
-// call's fused kernel, this FP64 work overlaps it, and the wait before the
-// constants are published keeps that kernel's readers safe.
-template <typename Real>
-__device__ __forceinline__ void prologue_body(const RfProgram& P, const double* __restrict__ params,
-                                              RfWork& W) {
-  asm volatile("griddepcontrol.launch_dependents;");
-  __shared__ RfConsts<Real> K;
-  __shared__ double lnI[RF_MAXL];
-  __shared__ int ok[RF_MAXL];
-  block_prologue(P, params, K, lnI, ok);
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
-  const double* src = reinterpret_cast<const double*>(&K);
-  double* dst = static_cast<double*>(W.consts);
-  for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
-}
-
 // ------------------------------------------------------ toy studies
 // The toys' events [B, E) (B = offsets[0], E = offsets[toys], clamped to the
 // bound columns) are split into N contiguous ranges of (almost) equal size,
@@ -526,26 +504,6 @@ struct WarpRow<double, NA, MASK> {
     }
   }
 };
-
-// One thread per toy: the toy's FP64 normalisations and coefficients, and a
-// check of its offsets.  Lets the segment kernel launch at once.
-template <typename Real>
-__device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* __restrict__ pm,
-                                              const int64_t* __restrict__ offsets,
-                                              int32_t toys, int64_t n_events,
-                                              RfConsts<Real>* consts, unsigned int* status,
-                                              int32_t* adam_t) {
-  asm volatile("griddepcontrol.launch_dependents;");
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0 && adam_t) *adam_t += 1;
-  if (t < toys) {
-    const int64_t b = offsets[t], e = offsets[t + 1];
-    if (b < 0 || e < b || e > n_events) atomicOr(status, RF_STATUS_NONFINITE_BIT);
-    RfConsts<Real> K;
-    build_consts_serial(P, pm + (int64_t)t * P.n_par, K);
-    consts[t] = K;
-  }
-}
 
 // ------------------------------------------------ bulk-copy event streaming
 // Each warp streams its own contiguous event range through a ring of S
@@ -801,61 +759,6 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
     p = q;
   }
   T.close(rows);
-}
-
-// Finalize kernel: one thread per toy (the FP64 unit takes one warp
-// instruction at a time whatever the number of active lanes, so 32 toys per
-// warp cost what one does).  The thread sums the toy's segment rows in row
-// order, runs the FP64 epilogue into out row t and, for a fit, applies one
-// Adam step (Kingma & Ba 2015) to the toy's free parameters in units of its
-// scale row.
-template <typename Real, int NL>
-__device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
-                                                  const int64_t* __restrict__ offsets,
-                                                  int32_t toys, int64_t stride, int64_t warps,
-                                                  double* pm, double* out, RfWork& W,
-                                                  const double* __restrict__ adam_scale,
-                                                  double adam_lr) {
-  constexpr int NA = RF_NACC(NL);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= toys) return;
-  const ToySplit S = toy_split(offsets, toys, stride, warps);
-  int64_t ob = toy_off(offsets, t, stride), oe = toy_off(offsets, t + 1, stride);
-  ob = ob < S.B ? S.B : ob;
-  oe = oe > S.E ? S.E : oe;
-  if (oe < ob) oe = ob;
-  double tot[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) tot[i] = 0.0;
-  if (oe > ob) {  // a toy meets a few warp ranges: plain FP64 sums of a few rows
-    const int64_t r1 = S.warp_of(oe - 1) + t;
-    for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
-      const double* row = W.partials + r * RF_NACC_MAX;
-#pragma unroll
-      for (int i = 0; i < NA; ++i) tot[i] += __ldcg(row + i);
-    }
-  }
-  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  double* row = out + t * (int64_t)(1 + P.n_par);
-  epilogue<Real, NL>(P, consts[t], tot, oe - ob, row, row + 1, W.status);
-  if (adam_scale && isfinite(row[0])) {
-    const int step = *W.adam_t;
-    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
-    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-    double* th = pm + t * (int64_t)P.n_par;
-    double* m1 = W.adam_m1 + t * (int64_t)P.n_par;
-    double* m2 = W.adam_m2 + t * (int64_t)P.n_par;
-    for (int p = 0; p < P.n_par; ++p) {
-      const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
-      if (fx) continue;
-      const double sc = adam_scale[t * (int64_t)P.n_par + p];
-      const double gsc = row[1 + p] * sc;
-      m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
-      m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
-      const double mh = m1[p] / c1, vh = m2[p] / c2;
-      th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
-    }
-  }
 }
 
 }  // namespace rf
