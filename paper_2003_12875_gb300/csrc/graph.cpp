@@ -266,9 +266,15 @@ static cudaKernel_t jit_fused(rf_graph* g, int ept, std::string* err) {
 // column type the toy kernels read: FP32-evaluated graphs read FP32 columns
 // (FP64 ones are converted at bind time)
 static int toy_coldt(const rf_graph* g) { return g->eval == RF_EVAL_FP32 ? RF_F32 : g->coldt; }
-// events per thread per chunk of the segment kernel: the larger option of the
-// precision (its per-chunk bookkeeping is spread over more events)
-static int toy_ept(const rf_graph* g) { return g->eval == RF_EVAL_FP32 ? 8 : 4; }
+// events per lane per chunk of the segment kernel (its per-chunk bookkeeping
+// and compensated sums are spread over that many events)
+static int toy_ept(const rf_graph* g) {
+  if (const char* v = getenv("RF_TOY_EPT")) {  // tuning: 8 or 16 (FP32), 4 or 8 (FP64)
+    const int e = atoi(v);
+    if (g->eval == RF_EVAL_FP32 ? (e == 8 || e == 16) : (e == 4 || e == 8)) return e;
+  }
+  return 8;  // measured on C4: 8 beats 16 (registers, occupancy) in FP32 and 4 in FP64
+}
 static RfLaunchCfg toy_cfg(const rf_graph* g) {
   RfLaunchCfg c = g->cfg;
   c.ept = toy_ept(g);
@@ -428,7 +434,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     // FP32-evaluated toy kernels read FP32 columns (converted at bind time)
     const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
     const int cd = (kind == RF_JIT_TOYS && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
-    const int ke = kind == RF_JIT_TOYS ? (fp32 ? 8 : 4) : ept;
+    const int ke = kind == RF_JIT_TOYS ? 8 : ept;
     if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, &err))
       return fail(RF_ECUDA, err);
   }

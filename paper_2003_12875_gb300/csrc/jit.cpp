@@ -129,7 +129,8 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   } else if (kind == RF_JIT_TOYS) {
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_toys_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t stride, int vec, const int64_t* __restrict__ offsets, "
-              "int32_t toys, int stages, RfWork W) {\n  rf::toy_segment_body<RfModel, "
+              "int32_t toys, int stages, RfWork W) {\n  rf::"
+      << (rf_toy_stream_reg() ? "toy_segment_body_reg" : "toy_segment_body") << "<RfModel, "
       << R << ", " << C << ", " << ept << ">(P, ev, stride, vec, offsets, toys, stages, W);\n}\n";
   } else {
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_logp_jit(const RfProgram P, const "

@@ -29,6 +29,11 @@ int rf_columns_to_f32(const double* in, float* out, int64_t n, void* stream) {
   return (int)cudaGetLastError();
 }
 
+bool rf_toy_stream_reg() {
+  const char* v = getenv("RF_TOY_STREAM");
+  return v && v[0] == 'r';
+}
+
 size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
@@ -70,7 +75,8 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   // fit in about 64 KB per block, 2..8
   const size_t stage_bytes = (size_t)std::max(P.n_cols, 1) * 32 * cfg.ept * esz;
   int stages = (int)std::min<size_t>(8, std::max<size_t>(2, (64u << 10) / (wpb * stage_bytes)));
-  const size_t smem = (size_t)wpb * (8 * 8 + stages * stage_bytes);
+  size_t smem = (size_t)wpb * (8 * 8 + stages * stage_bytes);
+  if (jit_toys && rf_toy_stream_reg()) smem = 0;  // register-streaming form
   // grid: the SMs times the blocks of this size that fit on one (registers,
   // shared memory), at least the configured blocks per SM
   int fit = 0;

@@ -4,6 +4,9 @@
 int rf_toys_f64_c32(const RfProgram& P, int ept, int grid, int block, int vec, int stages,
                  size_t smem, const void* ev, int64_t n_events, const int64_t* offsets,
                  int32_t toys, RfWork W, cudaStream_t st) {
-  (void)ept;
-  return rf::launch_toys_ept<double, float, 4>(P, grid, block, vec, stages, smem, ev, n_events, offsets, toys, W, st);
+  if (ept == 8)
+    return rf::launch_toys_ept<double, float, 8>(P, grid, block, vec, stages, smem, ev, n_events, offsets, toys, W, st);
+  if (ept == 4)
+    return rf::launch_toys_ept<double, float, 4>(P, grid, block, vec, stages, smem, ev, n_events, offsets, toys, W, st);
+  return (int)cudaErrorInvalidValue;
 }

@@ -168,6 +168,9 @@ rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, 
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
                         RfWork W, double* nll, double* grad, rf_cuda_stream st);
+// toy segment kernel form: bulk-copy stage rings (default) or register
+// streaming (RF_TOY_STREAM=reg)
+bool rf_toy_stream_reg();
 // segment kernel of a toy study, as a programmatic dependent of the prep
 // kernel launched just before it
 int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int grid, int block, int vec,

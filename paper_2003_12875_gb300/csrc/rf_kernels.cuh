@@ -761,4 +761,55 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
   T.close(rows);
 }
 
+// Segment kernel, register-streaming form: the same warp ranges, toy walk
+// and rows, but each segment's aligned middle is read with 128-bit loads into
+// registers, the next chunk's loads issued before the current chunk is
+// evaluated (as in the fused kernel); lanes take chunks of EPT events in turn.
+// No shared memory.
+template <class M, typename Real, typename Col, int EPT>
+__device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
+                                                     const Col* __restrict__ ev, int64_t stride,
+                                                     int vec, const int64_t* __restrict__ offsets,
+                                                     int32_t toys, int stages, RfWork& W) {
+  (void)stages;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * wpb + wib;
+  const ToySplit Sp = toy_split(offsets, toys, stride, (int64_t)gridDim.x * wpb);
+  const bool active = w < Sp.N && Sp.E > Sp.B;
+  int64_t wb = 0, we = 0;
+  int32_t t = 0;
+  if (active) {
+    wb = Sp.start(w);
+    we = Sp.start(w + 1);
+    t = find_toy(offsets, toys, stride, wb);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!active) return;
+  const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
+  ToyState<M, Real> T;
+  T.open(consts, offsets, stride, t);
+  double* rows = W.partials + w * RF_NACC_MAX;
+  for (int64_t p = wb; p < we;) {
+    if (!T.seek(consts, offsets, stride, toys, p, rows)) break;
+    const int64_t q = we < T.te ? we : T.te;
+    if (!T.bad) {
+      int64_t h = 0;
+      if (vec) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(ev + (int64_t)P.col_obs[0] * stride + p);
+        h = (int64_t)(((16u - (a & 15u)) & 15u) / sizeof(Col));
+        if (h > q - p) h = q - p;
+      }
+      const int64_t nfull = (q - p - h) / EPT;
+      stream_chunks<M, Real, Col, EPT>(P, T.E, ev, stride, p + h, lane, 32, nfull, vec != 0,
+                                       T.acc);
+      iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p + lane, p + h, T.acc, 32);
+      iterate_scalar<M, Real, Col>(P, T.E, ev, stride, p + h + nfull * EPT + lane, q, T.acc, 32);
+    }
+    T.any = true;
+    p = q;
+  }
+  T.close(rows);
+}
+
 }  // namespace rf
