@@ -51,14 +51,15 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 
+# the device headers NVRTC compiles per graph (jit.cpp): every kernel gets the
+# first list; toy kernels also get the second
 PRELUDE_HEADERS = ["rf_internal.h", "rf_device.cuh", "rf_kernels.cuh"]
+TOY_PRELUDE_HEADERS = ["rf_toys.cuh"]
 
 
-def write_prelude() -> str:
-    """Embed the device headers (the text NVRTC compiles per graph, jit.cpp)
-    as one C++ raw string."""
+def _raw(name: str, headers: list[str]) -> str:
     parts = []
-    for h in PRELUDE_HEADERS:
+    for h in headers:
         with open(os.path.join(CSRC, h)) as f:
             for line in f:
                 t = line.strip()
@@ -67,8 +68,13 @@ def write_prelude() -> str:
                 parts.append(line)
     body = "".join(parts)
     assert ")RFJIT\"" not in body
+    return f'static const char {name}[] = R"RFJIT(\n' + body + '\n)RFJIT";\n'
+
+
+def write_prelude() -> str:
+    """Embed the device headers as C++ raw strings (rf_jit_prelude.inc)."""
     out = os.path.join(BUILD, "rf_jit_prelude.inc")
-    text = 'static const char kRfJitPrelude[] = R"RFJIT(\n' + body + '\n)RFJIT";\n'
+    text = _raw("kRfJitPrelude", PRELUDE_HEADERS) + _raw("kRfJitToysPrelude", TOY_PRELUDE_HEADERS)
     if not os.path.exists(out) or open(out).read() != text:
         with open(out, "w") as f:
             f.write(text)

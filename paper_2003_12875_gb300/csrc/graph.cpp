@@ -226,6 +226,9 @@ struct rf_graph {
   // bind time (what every per-event conversion would give)
   float* bound32 = nullptr;
   size_t bound32_elems = 0;
+  // toy segment kernel form, fixed at compile: register streaming, or
+  // bulk-copy stage rings when RF_TOY_STREAM=bulk
+  bool toy_bulk = false;
   int64_t bound_n = 0;
   int32_t max_toys = 0;
   int64_t max_toy_rows = 0;  // segment rows: launch warps + toys
@@ -284,8 +287,9 @@ static RfLaunchCfg toy_cfg(const rf_graph* g) {
 static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
   int i = ept_index(g->eval, toy_coldt(g), ept);
   if (!g->jk_toys[i]) {
-    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g), RF_JIT_TOYS, ept, nullptr, err);
-    if (k) {  // its stage ring may use more than 48 KB of shared memory
+    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g),
+                                   g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept, nullptr, err);
+    if (k && g->toy_bulk) {  // its stage ring may use more than 48 KB of shared memory
       int optin = 0;
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
       cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
@@ -351,6 +355,7 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   g->eval = desc->eval_precision;
   g->coldt = desc->column_dtype;
   g->n_obs = desc->n_obs;
+  if (const char* v = getenv("RF_TOY_STREAM")) g->toy_bulk = v[0] == 'b';
   if (g->eval == RF_EVAL_FP64) g->cfg.ept = (g->coldt == RF_F64) ? 2 : 4;
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
@@ -430,11 +435,12 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
   if (s) return s;
   std::string err;
   const int ept = desc->eval_precision == RF_EVAL_FP32 ? 4 : (desc->column_dtype == RF_F64 ? 2 : 4);
-  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_LOGP}) {
+  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_TOYS_BULK, RF_JIT_LOGP}) {
     // FP32-evaluated toy kernels read FP32 columns (converted at bind time)
     const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
-    const int cd = (kind == RF_JIT_TOYS && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
-    const int ke = kind == RF_JIT_TOYS ? 8 : ept;
+    const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
+    const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
+    const int ke = toy ? 8 : ept;
     if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, &err))
       return fail(RF_ECUDA, err);
   }
@@ -662,6 +668,7 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
                             g->bound_n, offsets, toys, const_cast<double*>(params_matrix), out,
                             g->work, nullptr, 0.0, g->max_toy_rows,
                             g->jit ? g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))] : nullptr,
+                            g->jit && g->toy_bulk,
                             stream, &n);
   g->last_launches = n;
   if (e) return cuda_fail((cudaError_t)e, "rf_nll_batched launch");
@@ -701,6 +708,7 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
                            g->bound_n, offsets, toys, params_matrix, out, g->work, scale, lr,
                            g->max_toy_rows,
                            g->jit ? g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))] : nullptr,
+                            g->jit && g->toy_bulk,
                            fs, &n);
     e = cudaStreamEndCapture(fs, &graph);
     if (le) {

@@ -26,7 +26,7 @@
 #include <vector>
 
 #include "rf_internal.h"
-#include "rf_jit_prelude.inc"  // kRfJitPrelude: the device headers as text
+#include "rf_jit_prelude.inc"  // kRfJitPrelude, kRfJitToysPrelude: device headers as text
 
 namespace {
 
@@ -126,11 +126,12 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
       << C << "* __restrict__ ev, int64_t n, int64_t head, int vec, const double* __restrict__ "
               "params, RfWork W, double* nll, double* grad) {\n  rf::fused_body<RfModel, "
       << R << ", " << C << ", " << ept << ">(P, ev, n, head, vec, params, W, nll, grad);\n}\n";
-  } else if (kind == RF_JIT_TOYS) {
+  } else if (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) {
+    o << kRfJitToysPrelude << "\n";
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_toys_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t stride, int vec, const int64_t* __restrict__ offsets, "
               "int32_t toys, int stages, RfWork W) {\n  rf::"
-      << (rf_toy_stream_reg() ? "toy_segment_body_reg" : "toy_segment_body") << "<RfModel, "
+      << (kind == RF_JIT_TOYS ? "toy_segment_body_reg" : "toy_segment_body") << "<RfModel, "
       << R << ", " << C << ", " << ept << ">(P, ev, stride, vec, offsets, toys, stages, W);\n}\n";
   } else {
     o << "extern \"C\" __global__ void __launch_bounds__(256) rf_logp_jit(const RfProgram P, const "
@@ -235,7 +236,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
       return nullptr;
     }
     const char* kname = kind == RF_JIT_FUSED ? "rf_fused_jit"
-                        : kind == RF_JIT_TOYS ? "rf_toys_jit" : "rf_logp_jit";
+                        : (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) ? "rf_toys_jit" : "rf_logp_jit";
     e = cudaLibraryGetKernel(&k, lib, kname);
     if (e != cudaSuccess) {
       *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);

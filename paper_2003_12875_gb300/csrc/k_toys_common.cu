@@ -29,11 +29,6 @@ int rf_columns_to_f32(const double* in, float* out, int64_t n, void* stream) {
   return (int)cudaGetLastError();
 }
 
-bool rf_toy_stream_reg() {
-  const char* v = getenv("RF_TOY_STREAM");
-  return v && v[0] == 'r';
-}
-
 size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
@@ -61,7 +56,7 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
                       int num_sms, const void* events, int64_t n_events,
                       const int64_t* offsets, int32_t toys, double* pm, double* out,
                       RfWork W, const double* adam_scale, double adam_lr, int64_t max_rows,
-                      struct CUkern_st* jit_toys, void* stream, int* launches) {
+                      struct CUkern_st* jit_toys, bool bulk, void* stream, int* launches) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (launches) *launches = 0;
   // segment rows: one per (warp, toy) pair that shares events, at most
@@ -71,12 +66,13 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   int64_t head = 0;
   const size_t esz = coldt ? 8 : 4;
   rf_vec_plan(P, events, n_events, (int)esz, &vec, &head);
-  // stage ring per warp: as many stages of 32*EPT events (all columns) as
-  // fit in about 64 KB per block, 2..8
+  // bulk-copy form: a stage ring per warp, as many stages of 32*EPT events
+  // (all columns) as fit in about 64 KB per block, 2..8; the register form
+  // uses no shared memory
   const size_t stage_bytes = (size_t)std::max(P.n_cols, 1) * 32 * cfg.ept * esz;
-  int stages = (int)std::min<size_t>(8, std::max<size_t>(2, (64u << 10) / (wpb * stage_bytes)));
-  size_t smem = (size_t)wpb * (8 * 8 + stages * stage_bytes);
-  if (jit_toys && rf_toy_stream_reg()) smem = 0;  // register-streaming form
+  const int stages =
+      (int)std::min<size_t>(8, std::max<size_t>(2, (64u << 10) / (wpb * stage_bytes)));
+  const size_t smem = bulk ? (size_t)wpb * (8 * 8 + stages * stage_bytes) : 0;
   // grid: the SMs times the blocks of this size that fit on one (registers,
   // shared memory), at least the configured blocks per SM
   int fit = 0;

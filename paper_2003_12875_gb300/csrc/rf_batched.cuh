@@ -10,7 +10,7 @@
 //                   epilogue (NLL, gradient), optionally one Adam step.
 // Results depend only on the inputs and the launch shape, not on timing.
 #pragma once
-#include "rf_kernels.cuh"
+#include "rf_toys.cuh"
 
 namespace rf {
 
@@ -136,7 +136,8 @@ template <typename Real, typename Col, int NL, int EPT>
 __global__ void __launch_bounds__(256)
     toy_segment_kernel(const RfProgram P, const Col* __restrict__ ev, int64_t stride, int vec,
                        const int64_t* __restrict__ offsets, int32_t toys, int stages, RfWork W) {
-  toy_segment_body<GenericModel<NL>, Real, Col, EPT>(P, ev, stride, vec, offsets, toys, stages, W);
+  toy_segment_body_reg<GenericModel<NL>, Real, Col, EPT>(P, ev, stride, vec, offsets, toys, stages,
+                                                         W);
 }
 
 template <typename Real, int NL>
@@ -151,19 +152,11 @@ template <typename Real, typename Col, int NL, int EPT>
 inline int launch_toys_nl(const RfProgram& P, int grid, int block, int vec, int stages,
                           size_t smem, const void* events, int64_t n_events,
                           const int64_t* offsets, int32_t toys, RfWork W, cudaStream_t st) {
-  auto kern = toy_segment_kernel<Real, Col, NL, EPT>;
-  static bool sized = false;  // opt in to more than 48 KB of dynamic shared memory once
-  if (!sized) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    sized = true;
-  }
+  auto kern = toy_segment_kernel<Real, Col, NL, EPT>;  // register form: no shared memory
+  (void)smem;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
   lc.blockDim = dim3(block);
-  lc.dynamicSmemBytes = smem;
   lc.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -134,7 +134,7 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       int64_t n_events, const int64_t* offsets, int32_t toys,
                       double* pm, double* out, RfWork W,
                       const double* adam_scale, double adam_lr,
-                      int64_t max_rows, struct CUkern_st* jit_toys, void* stream,
+                      int64_t max_rows, struct CUkern_st* jit_toys, bool bulk, void* stream,
                       int* launches);
 // FP64 -> FP32 (round to nearest) of n values, for the toy columns of an
 // FP32-evaluated graph (converted once at bind time)
@@ -157,7 +157,9 @@ void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int ele
 
 // per-graph specialised kernels (jit.cpp)
 #include <string>
-enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2 };
+// toy segment kernel: register streaming (RF_JIT_TOYS) or bulk-copy stage
+// rings (RF_JIT_TOYS_BULK)
+enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2, RF_JIT_TOYS_BULK = 3 };
 typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
 std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept);
 uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept);
@@ -168,9 +170,6 @@ rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, 
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
                         RfWork W, double* nll, double* grad, rf_cuda_stream st);
-// toy segment kernel form: bulk-copy stage rings (default) or register
-// streaming (RF_TOY_STREAM=reg)
-bool rf_toy_stream_reg();
 // segment kernel of a toy study, as a programmatic dependent of the prep
 // kernel launched just before it
 int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int grid, int block, int vec,

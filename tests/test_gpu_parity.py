@@ -336,6 +336,34 @@ def test_batched_toys_match_oracle_and_single(rf, prec, shape, jit):
         assert rel_nll(float(single[0].item()), got[t, 0]) <= TOL[prec]["nll"]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_toys_bulk_copy_form(rf, prec, monkeypatch):
+    """The segment kernel's bulk-copy form (per-warp shared-memory stage rings
+    filled by cp.async.bulk, RF_TOY_STREAM=bulk at graph compile) against the
+    oracle, with hundreds of tiny toys among large ones."""
+    monkeypatch.setenv("RF_TOY_STREAM", "bulk")
+    w = small_toys(256)
+    counts = np.diff(w["offsets"]).copy()
+    counts[5:205] = np.arange(200) % 7           # 200 toys of 0..6 events
+    off = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    pm = w["params_matrix"].copy()
+    pm[:, 0] += 0.01
+    want, rc = oracle.nll_batched(w["spec"], w["cols"], off, pm)
+    G = rf.Graph(w["spec"], "f64", prec)
+    G.bind_events(to_dev(w), len(counts))
+    got = G.nll_batched(torch.from_numpy(off).to(DEV), torch.from_numpy(pm).to(DEV)).cpu().numpy()
+    assert G.status() == 0
+    for t in range(len(counts)):
+        assert rel_nll(got[t, 0], want[t, 0]) <= TOL[prec]["nll"], t
+        if counts[t] >= 200 or prec == "fp64":
+            if counts[t] == 0:
+                continue
+            b, e = off[t], off[t + 1]
+            _, gref, sc, _ = oracle.nll_scaled(w["spec"], pm[t], w["cols"][:, b:e])
+            assert grad_l1(got[t, 1:], gref, sc, [True] * 5).max() <= TOL[prec]["grad"], t
+
+
 def test_batched_empty_and_tiny_toys(rf):
     w = small_toys(8)
     off = w["offsets"].copy()
