@@ -229,6 +229,25 @@ def toy_study(rf, torch, toys=4096, iters=50):
                      "events_per_s": res["events"] / (t_eval * 1e-3),
                      "fit_ms": t_fit, "fit_toy_iters_per_s": toys * iters / (t_fit * 1e-3),
                      "launches_per_fit": G.last_launches(), "kernel": G.uses_jit()}
+    # toy generation on the device: the same 4096 toys (per-component counts
+    # = the workload's signal / background split), FP64 columns
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    counts = torch.from_numpy(np.rint(w["params_matrix"][:, 3:5]).astype(np.int64)).cuda()
+    goff = torch.zeros(toys + 1, dtype=torch.int64, device="cuda")
+    goff[1:] = torch.cumsum(counts.sum(1), 0)
+    pmg = torch.from_numpy(w["params_matrix"]).cuda()
+    ng = int(goff[-1].item())
+    buf = torch.empty(1, ng, dtype=torch.float64, device="cuda")
+    G.generate_toys(pmg, counts, goff, seed=1, out=buf)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        G.generate_toys(pmg, counts, goff, seed=2, out=buf)
+    b.record()
+    torch.cuda.synchronize()
+    t_gen = a.elapsed_time(b) / 3
+    res["generation"] = {"events": ng, "ms": t_gen, "events_per_s": ng / (t_gen * 1e-3),
+                         "toys_per_s": toys / (t_gen * 1e-3)}
     return res
 
 

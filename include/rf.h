@@ -85,9 +85,12 @@ enum { RF_EVAL_FP32 = 0, RF_EVAL_FP64 = 1 }; /* per-event arithmetic      */
 enum {
   RF_STATUS_PARAM_DOMAIN = 1u, /* a parameter outside its definition range */
   RF_STATUS_NONFINITE = 2u,    /* an event with P <= 0 or a non-finite log P */
-  RF_STATUS_TIMEOUT = 4u       /* a bounded wait inside a kernel gave up (an event
+  RF_STATUS_TIMEOUT = 4u,      /* a bounded wait inside a kernel gave up (an event
                                   copy did not arrive); that call's results are
                                   not valid */
+  RF_STATUS_GEN_EXHAUSTED = 8u /* rf_generate_toys: a value took the maximum of
+                                  4096 accept-reject attempts (the last one is
+                                  stored) */
 };
 
 #define RF_MAX_CHILDREN 8
@@ -206,6 +209,31 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
 rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
                       double* params_matrix, const double* scale, int32_t iters,
                       double lr, double* out, rf_stream stream);
+
+/* Toy generation: the events of `toys` datasets drawn from the graph, on the
+ * device, in the layout rf_graph_bind_events / rf_nll_batched read.
+ *   params_matrix dev FP64 [toys * n_params]: each toy's generating parameters
+ *   comp_counts   dev int64 [toys * n_comp]: events of each component per toy
+ *                 (Poisson draws around the yields for an extended model, a
+ *                 multinomial split for fractions; drawn by the caller)
+ *   offsets       dev int64 [toys + 1]: toy t owns [offsets[t], offsets[t+1]),
+ *                 offsets[t+1] - offsets[t] = the sum of its counts
+ *   events        dev, column j (observable j) at events + j * n_events, of the
+ *                 graph's column type; n_events >= offsets[toys]
+ * Toy t's events are, in order, comp_counts[t*n_comp + c] events of component
+ * c; each observable comes from the component's leaf on it, drawn in FP64 by
+ * inverse CDF (Gaussian, Exponential, Crystal Ball) or accept-reject
+ * (Chebychev, ARGUS), from uniforms ((w >> 11) + 1/2) 2^-53 of the words w of
+ * Philox4x64-10 (Salmon et al. 2011) with key {seed, 0x52462D544F595321} and
+ * counter {event, observable, attempt, 0} -- the values do not depend on the
+ * launch.  A value is rounded to the column type and accepted only inside
+ * the observable's range (ARGUS: below m0).  Every component must cover every
+ * observable (RF_EUNSUPPORTED otherwise).  A toy whose counts do not fill its
+ * range gets NaN events there and RF_STATUS_NONFINITE.  Asynchronous. */
+rf_status rf_generate_toys(rf_graph* g, const double* params_matrix,
+                           const int64_t* comp_counts, const int64_t* offsets,
+                           int32_t toys, uint64_t seed, void* events,
+                           int64_t n_events, rf_stream stream);
 
 /* Baseline: the batch interface of Sec. 5.2 on the GPU, in FP64 -- one kernel
  * per graph node, each writing an n-length node-owned FP64 array, then a log

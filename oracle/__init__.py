@@ -85,6 +85,14 @@ def lib():
                                         C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double]
             L.orc_adam_step.restype = None
+            u64p = C.POINTER(C.c_uint64)
+            L.orc_philox4x64.argtypes = [u64p, u64p, u64p]
+            L.orc_philox4x64.restype = None
+            L.orc_erfcinv.argtypes = [C.c_double]
+            L.orc_erfcinv.restype = C.c_double
+            i64p = C.POINTER(C.c_int64)
+            L.orc_generate.argtypes = [C.POINTER(_Model), dp, C.c_int32, i64p, i64p, C.c_uint64,
+                                       C.c_int, dp, C.c_int64, i64p]
             _lib = L
     return _lib
 
@@ -207,3 +215,34 @@ def adam_step(theta, grad, scale, free_mask, m1, m2, t, lr, beta1=0.9, beta2=0.9
     lib().orc_adam_step(len(theta), _dp(theta), _dp(g), _dp(sc),
                         fm.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(m1), _dp(m2), t, lr,
                         beta1, beta2, eps)
+
+
+def philox4x64(counter, key):
+    """One Philox4x64-10 block (4 uint64) for a 4-word counter and 2-word key."""
+    c = (C.c_uint64 * 4)(*[int(x) for x in counter])
+    k = (C.c_uint64 * 2)(*[int(x) for x in key])
+    o = (C.c_uint64 * 4)()
+    lib().orc_philox4x64(c, k, o)
+    return [int(x) for x in o]
+
+
+def erfcinv(q: float) -> float:
+    return float(lib().orc_erfcinv(float(q)))
+
+
+def generate(spec: dict, params_matrix, comp_counts, offsets, seed: int, col_f32: bool,
+             n_events: int | None = None):
+    """Toy events drawn by the oracle's generator: (cols [n_obs, n_events] FP64,
+    values that exhausted their attempts, return code).  comp_counts [toys, K]."""
+    m = Model(spec)
+    pm = np.ascontiguousarray(np.asarray(params_matrix, np.float64))
+    cc = np.ascontiguousarray(np.asarray(comp_counts, np.int64))
+    off = np.ascontiguousarray(np.asarray(offsets, np.int64))
+    toys = len(off) - 1
+    n = int(off[-1]) if n_events is None else int(n_events)
+    cols = np.full((len(spec["obs"]), n), np.nan)
+    ex = C.c_int64(0)
+    rc = lib().orc_generate(C.byref(m.s), _dp(pm), toys, cc.ctypes.data_as(C.POINTER(C.c_int64)),
+                            off.ctypes.data_as(C.POINTER(C.c_int64)), C.c_uint64(seed),
+                            1 if col_f32 else 0, _dp(cols), n, C.byref(ex))
+    return cols, int(ex.value), rc

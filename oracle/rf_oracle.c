@@ -679,3 +679,243 @@ void orc_adam_step(int n_par, double* theta, const double* grad,
     theta[j] -= scale[j] * lr * mh / (sqrt(vh) + eps);
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* toy generation                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplications,
+ * the key bumped by the Weyl constants between rounds. */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(M0, c0, &hi0, &lo0);
+    mulhilo64(M1, c2, &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    if (r < 9) {
+      k0 += W0;
+      k1 += W1;
+    }
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* inverse of erfc on (0, 2): Newton's method on erfc from a rough start,
+ * to convergence in FP64 */
+double orc_erfcinv(double q) {
+  if (!(q > 0.0 && q < 2.0)) return q == 0.0 ? INFINITY : (q == 2.0 ? -INFINITY : NAN);
+  if (q >= 0.5 && q <= 1.5) {
+    /* erf(z) = 1 - q, exact here (Sterbenz): Newton on erf keeps the small
+     * root's relative accuracy */
+    double e = 1.0 - q, z = 0.8862269254527580 * e;
+    for (int it = 0; it < 100; ++it) {
+      double f = erf(z) - e;
+      double dz = f / (1.1283791670955126 * exp(-z * z));
+      dz = dz / (1.0 - z * dz);
+      z -= dz;
+      if (fabs(dz) <= 1e-17 * fabs(z) + 1e-300) break;
+    }
+    return z;
+  }
+  if (q > 1.0) return -orc_erfcinv(2.0 - q);
+  /* start: erfc(z) ~ exp(-z^2) / (z sqrt(pi)) for large z; z = 0.5 * (1-q) near 1 */
+  double z = q > 0.3 ? 0.8862269254527580 * (1.0 - q)
+                     : sqrt(-log(q)) - 0.25 * log(-log(q) * 3.141592653589793) / sqrt(-log(q));
+  for (int it = 0; it < 100; ++it) {
+    double f = erfc(z) - q;
+    double fp = -1.1283791670955126 * exp(-z * z); /* d erfc/dz = -2/sqrt(pi) e^{-z^2} */
+    double dz = f / fp;
+    /* Halley's correction: f'' / f' = -2 z */
+    dz = dz / (1.0 + z * dz);
+    z -= dz;
+    if (fabs(dz) <= 1e-17 * fabs(z) + 1e-300) break;
+  }
+  return z;
+}
+
+/* z with Phi(z) = Phi(za) + u (Phi(zb) - Phi(za)), Phi the standard normal
+ * CDF; the lower- or upper-tail form is used whichever is small */
+static double tn_inv(double u, double za, double zb) {
+  const double r2 = 1.4142135623730951;
+  double Pa = 0.5 * erfc(-za / r2), Pb = 0.5 * erfc(-zb / r2);
+  double P = Pa + u * (Pb - Pa);
+  if (P <= 0.5) return -r2 * orc_erfcinv(2.0 * P);
+  double Qa = 0.5 * erfc(za / r2), Qb = 0.5 * erfc(zb / r2);
+  double Q = Qb + (1.0 - u) * (Qa - Qb);
+  return r2 * orc_erfcinv(2.0 * Q);
+}
+
+/* One candidate value of a leaf from the four uniforms of one attempt;
+ * *accept = 0 asks for another attempt (accept-reject). */
+static double sample_leaf(int type, const double* th, int nth, double a, double b,
+                          const double* u, int* accept) {
+  *accept = 1;
+  switch (type) {
+    case ORC_GAUSS: {
+      double mu = th[0], sg = th[1];
+      return mu + sg * tn_inv(u[0], (a - mu) / sg, (b - mu) / sg);
+    }
+    case ORC_EXP: {
+      double lam = th[0], L = b - a;
+      if (lam == 0.0) return a + u[0] * L;
+      /* CDF expm1(lam (x - a)) / expm1(lam L), inverted from the end whose
+       * exponential does not overflow */
+      if (lam < 0.0) return a + log1p(u[0] * expm1(lam * L)) / lam;
+      /* 1 - F(x) = expm1(lam (x - b)) / expm1(-lam L) */
+      return b + log1p((1.0 - u[0]) * expm1(-lam * L)) / lam;
+    }
+    case ORC_CHEB: {
+      /* uniform proposal on [-1, 1]; f = 1 + sum c_j T_j <= 1 + sum |c_j| */
+      double xp = -1.0 + 2.0 * u[0], fmax = 1.0, f = 1.0, tm = 1.0, t = xp;
+      for (int j = 0; j < nth; ++j) {
+        fmax += fabs(th[j]);
+        f += th[j] * t;
+        double tn = 2.0 * xp * t - tm;
+        tm = t;
+        t = tn;
+      }
+      *accept = u[1] * fmax <= f;
+      return a + 0.5 * (xp + 1.0) * (b - a);
+    }
+    case ORC_CB: {
+      double m0 = th[0], sg = th[1], al = th[2], n = th[3];
+      double s = al > 0.0 ? 1.0 : -1.0, A = fabs(al);
+      double tlo = s > 0.0 ? (a - m0) / sg : (m0 - b) / sg;
+      double thi = s > 0.0 ? (b - m0) / sg : (m0 - a) / sg;
+      double tc = tlo > -A ? tlo : -A;
+      double core = thi > -A ? 1.2533141373155003 * erf_diff(tc / 1.4142135623730951,
+                                                              thi / 1.4142135623730951)
+                             : 0.0;
+      double tail = 0.0, pre = (n / A) * exp(-0.5 * A * A), D1 = 1.0, G1 = 0.0;
+      double t2 = thi < -A ? thi : -A;
+      if (tlo < -A) {
+        /* D = 1 - (A/n)(A + t); tail mass from tlo to t = pre (G(D(tlo)) - G(D(t))),
+         * G(D) = D^(1-n)/(1-n), log D at n = 1 */
+        D1 = 1.0 - (A / n) * (A + tlo);
+        double D2 = 1.0 - (A / n) * (A + t2);
+        G1 = n == 1.0 ? log(D1) : pow(D1, 1.0 - n) / (1.0 - n);
+        double G2 = n == 1.0 ? log(D2) : pow(D2, 1.0 - n) / (1.0 - n);
+        tail = pre * (G1 - G2);
+      }
+      double T = u[0] * (core + tail), t;
+      if (T < tail) {
+        double G = G1 - T / pre;
+        double Dt = n == 1.0 ? exp(G) : pow((1.0 - n) * G, 1.0 / (1.0 - n));
+        t = (n / A) * (1.0 - Dt) - A;
+      } else {
+        double v = core > 0.0 ? (T - tail) / core : 0.0;
+        t = tn_inv(v, tc, thi);
+      }
+      return s > 0.0 ? m0 + sg * t : m0 - sg * t;
+    }
+    case ORC_ARGUS: {
+      /* m dm ~ sqrt(tau) e^{c tau} d tau with tau = 1 - (m/m0)^2 */
+      double m0 = th[0], c = th[1];
+      double bb = b < m0 ? b : m0;
+      double ta = 1.0 - (a / m0) * (a / m0), tb = 1.0 - (bb / m0) * (bb / m0), tau;
+      if (c < 0.0) {
+        /* Gamma(3/2, rate -c) = (E + Z^2/2) / (-c): E exponential, Z normal
+         * (Box-Muller), truncated to [tb, ta] by rejection */
+        double E = -log(u[0]);
+        double Z = sqrt(-2.0 * log(u[1])) * cos(6.283185307179586 * u[2]);
+        tau = (E + 0.5 * Z * Z) / (-c);
+        *accept = tau >= tb && tau <= ta;
+      } else {
+        tau = tb + u[0] * (ta - tb);
+        double gmax = sqrt(ta) * exp(c * ta);
+        *accept = u[1] * gmax <= sqrt(tau) * exp(c * tau);
+      }
+      return m0 * sqrt(1.0 - tau);
+    }
+  }
+  *accept = 1;
+  return NAN;
+}
+
+/* leaves (node indices) of component node i: the leaf itself or a Prod's */
+static int comp_leaves(const orc_model* m, int i, int* out) {
+  if (is_leaf(m->type[i])) {
+    out[0] = i;
+    return 1;
+  }
+  if (m->type[i] != ORC_PROD) return -1;
+  int k = 0;
+  for (int j = 0; j < m->nchild[i]; ++j) {
+    int ch = m->child[i * ORC_MAXCH + j];
+    if (!is_leaf(m->type[ch])) return -1;
+    out[k++] = ch;
+  }
+  return k;
+}
+
+int orc_generate(const orc_model* m, const double* params_matrix, int32_t toys,
+                 const int64_t* comp_counts, const int64_t* offsets, uint64_t seed,
+                 int col_f32, double* cols, int64_t col_stride, int64_t* exhausted) {
+  int rc = validate(m);
+  if (rc) return rc;
+  int comps[ORC_MAXCH], nc = 0;
+  int rt = m->type[m->root];
+  if (rt == ORC_ADD_FRAC || rt == ORC_ADD_EXT) {
+    nc = m->nchild[m->root];
+    for (int c = 0; c < nc; ++c) comps[c] = m->child[m->root * ORC_MAXCH + c];
+  } else {
+    nc = 1;
+    comps[0] = m->root;
+  }
+  int lv[ORC_MAXCH][ORC_MAXCH], nlv[ORC_MAXCH];
+  for (int c = 0; c < nc; ++c) {
+    nlv[c] = comp_leaves(m, comps[c], lv[c]);
+    if (nlv[c] < 0) return ORC_EUNSUPPORTED;
+    int64_t cover = 0;
+    for (int k = 0; k < nlv[c]; ++k) cover |= (int64_t)1 << m->obs[lv[c][k]];
+    if (cover != ((int64_t)1 << m->n_obs) - 1) return ORC_EUNSUPPORTED;
+  }
+  const uint64_t key[2] = {seed, 0x52462D544F595321ULL};
+  *exhausted = 0;
+  for (int32_t t = 0; t < toys; ++t) {
+    const double* p = params_matrix + (int64_t)t * m->n_par;
+    int64_t i = offsets[t];
+    for (int c = 0; c < nc; ++c) {
+      for (int64_t e = 0; e < comp_counts[(int64_t)t * nc + c]; ++e, ++i) {
+        for (int k = 0; k < nlv[c]; ++k) {
+          int node = lv[c][k], o = m->obs[node];
+          double th[ORC_MAXNP];
+          for (int j = 0; j < m->npar[node]; ++j) th[j] = p[m->par[node * ORC_MAXNP + j]];
+          double lo = m->obs_lo[o], hi = m->obs_hi[o], x = NAN;
+          int ok = 0;
+          for (uint64_t r = 0; r < 4096 && !ok; ++r) {
+            uint64_t ctr[4] = {(uint64_t)i, (uint64_t)o, r, 0}, w[4];
+            double u[4];
+            orc_philox4x64(ctr, key, w);
+            for (int q = 0; q < 4; ++q) u[q] = ((double)(w[q] >> 11) + 0.5) * 0x1p-53;
+            x = sample_leaf(m->type[node], th, m->npar[node], lo, hi, u, &ok);
+            if (col_f32) x = (double)(float)x;
+            /* the stored value must lie in the range (ARGUS: below m0) */
+            if (ok && !(x >= lo && x <= hi)) ok = 0;
+            if (ok && m->type[node] == ORC_ARGUS && !(x < th[0])) ok = 0;
+          }
+          if (!ok) ++*exhausted;
+          cols[(int64_t)o * col_stride + i] = x;
+        }
+      }
+    }
+  }
+  return ORC_OK;
+}

@@ -112,6 +112,24 @@ void orc_adam_step(int n_par, double* theta, const double* grad,
                    double* m2, int t, double lr, double beta1, double beta2,
                    double eps);
 
+/* Toy generation.
+ * Philox4x64-10 block for counter ctr and key (Salmon et al., SC'11). */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+/* inverse complementary error function on (0, 2) */
+double orc_erfcinv(double q);
+/* Events of `toys` datasets: toy t's events [offsets[t], ...) are, in order,
+ * comp_counts[t*K + c] events of component c (K = root's children for an Add,
+ * else 1), each observable drawn from the component's leaf on it with the
+ * toy's parameter row: inverse CDF (Gaussian, Exponential, Crystal Ball) or
+ * accept-reject (Chebychev, ARGUS), uniforms ((w >> 11) + 0.5) 2^-53 from the
+ * 64-bit words w of Philox4x64-10 with key {seed, 0x52462D544F595321} and
+ * counter {event, observable, attempt, 0}; a value is stored rounded to the
+ * column type (col_f32) and accepted only inside the observable's range
+ * (ARGUS: below m0).  *exhausted counts values that took 4096 attempts. */
+int orc_generate(const orc_model* m, const double* params_matrix, int32_t toys,
+                 const int64_t* comp_counts, const int64_t* offsets, uint64_t seed,
+                 int col_f32, double* cols, int64_t col_stride, int64_t* exhausted);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,7 +69,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
            "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
-           "rf_check_d2f"]
+           "rf_check_d2f", "rf_generate_toys"]
 
 
 def lib_path() -> str:
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.rf_graph_bind_events.argtypes = [vp, vp, i64, i32]
         L.rf_nll_batched.argtypes = [vp, vp, i32, vp, vp, vp]
         L.rf_fit_toys.argtypes = [vp, vp, i32, vp, vp, i32, C.c_double, vp, vp]
+        L.rf_generate_toys.argtypes = [vp, vp, vp, vp, i32, C.c_uint64, vp, i64, vp]
         L.rf_nll_plain.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.rf_graph_get_launch.argtypes = [vp, C.POINTER(_Launch)]
         L.rf_graph_set_launch.argtypes = [vp, C.POINTER(_Launch)]
@@ -304,6 +305,30 @@ class Graph:
             out = torch.empty(toys, 1 + self.n_par, dtype=torch.float64, device=offsets.device)
         _check(load().rf_nll_batched(self._h, _ptr(offsets), toys, _ptr(params_matrix),
                                      _ptr(out), _stream()))
+        return out
+
+    def generate_toys(self, params_matrix: torch.Tensor, comp_counts: torch.Tensor,
+                      offsets: torch.Tensor, seed: int, n_events: int | None = None,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+        """Events of toys drawn on the device (rf_generate_toys): params_matrix
+        [toys, n_params] FP64, comp_counts [toys, n_comp] int64, offsets
+        [toys + 1] int64, all CUDA; returns (or fills) the [n_obs, n_events]
+        column tensor of the graph's column type."""
+        toys = offsets.numel() - 1
+        for t, dt in ((params_matrix, torch.float64), (comp_counts, torch.int64),
+                      (offsets, torch.int64)):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise TypeError("generate_toys takes contiguous CUDA tensors "
+                                "(FP64 params, int64 counts and offsets)")
+        if params_matrix.shape != (toys, self.n_par) or comp_counts.shape[0] != toys:
+            raise ValueError("params_matrix [toys, n_params], comp_counts [toys, n_comp]")
+        if n_events is None:
+            n_events = int(offsets[-1].item())
+        if out is None:
+            out = torch.empty(self.n_obs, n_events, dtype=self.dtype, device=offsets.device)
+        _check(load().rf_generate_toys(self._h, _ptr(params_matrix), _ptr(comp_counts),
+                                       _ptr(offsets), toys, C.c_uint64(seed), _ptr(out),
+                                       int(n_events), _stream()))
         return out
 
     def fit_toys(self, offsets: torch.Tensor, params_matrix: torch.Tensor,

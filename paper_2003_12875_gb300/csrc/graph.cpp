@@ -738,6 +738,32 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
   return RF_OK;
 }
 
+rf_status rf_generate_toys(rf_graph* g, const double* params_matrix, const int64_t* comp_counts,
+                           const int64_t* offsets, int32_t toys, uint64_t seed, void* events,
+                           int64_t n_events, rf_stream stream) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (toys < 1 || !params_matrix || !comp_counts || !offsets || n_events < 0 ||
+      (n_events > 0 && !events))
+    return fail(RF_EINVAL, "NULL or negative argument");
+  const RfProgram& P = g->prog;
+  // every component must draw every observable
+  if (P.n_cols != g->n_obs) return fail(RF_EUNSUPPORTED, "an observable no leaf reads");
+  for (int c = 0; c < P.n_comp; ++c) {
+    int mask = 0;
+    for (int k = 0; k < P.n_leaves; ++k)
+      if (P.leaf[k].comp == c) mask |= 1 << P.leaf[k].col;
+    if (mask != (1 << P.n_cols) - 1)
+      return fail(RF_EUNSUPPORTED, "a component does not cover every observable");
+  }
+  if (n_events == 0) return RF_OK;
+  int e = rf_launch_generate(P, g->coldt, params_matrix, comp_counts, offsets, toys,
+                             (unsigned long long)seed, events, n_events, g->work.status,
+                             g->num_sms, reinterpret_cast<cudaStream_t>(stream));
+  g->last_launches = 1;
+  if (e) return cuda_fail((cudaError_t)e, "rf_generate_toys launch");
+  return RF_OK;
+}
+
 rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events, const double* params,
                        double* nll, double* grad, rf_stream stream) {
   if (!g) return fail(RF_EINVAL, "graph is NULL");

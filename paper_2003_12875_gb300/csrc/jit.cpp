@@ -113,11 +113,13 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   o << "  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
-  // The fused kernel is declared for 2 resident blocks of 256 threads per SM:
-  // without a minimum, ptxas budgets registers for 3 blocks and schedules the
-  // event loop with less overlap (measured slower on the Crystal Ball + ARGUS
-  // model).  RF_JIT_MINBLOCKS=k asks for k blocks instead.
-  std::string lb = "__launch_bounds__(256, 2)";
+  // The fused kernel is declared for 3 resident blocks of 256 threads per SM
+  // (80 registers on the Crystal Ball + ARGUS model; measured 1.5% faster than
+  // 2 blocks at 93 registers, with the tuner picking the block shape).  Without
+  // a minimum, ptxas's budget depends on the rest of the kernel (an FP64 tail
+  // once pulled the event loop to 80 registers with spills).
+  // RF_JIT_MINBLOCKS=k asks for k blocks instead.
+  std::string lb = "__launch_bounds__(256, 3)";
 
   if (const char* mb = getenv("RF_JIT_MINBLOCKS"))
     if (atoi(mb) > 0) lb = "__launch_bounds__(256, " + std::to_string(atoi(mb)) + ")";

@@ -38,6 +38,7 @@ enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 #define RF_STATUS_PARAM_DOMAIN_BIT 1u
 #define RF_STATUS_NONFINITE_BIT 2u
 #define RF_STATUS_TIMEOUT_BIT 4u
+#define RF_STATUS_GEN_EXHAUSTED_BIT 8u
 enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5 };
 
 struct RfLeafProg {
@@ -136,6 +137,11 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt,
                       const double* adam_scale, double adam_lr,
                       int64_t max_rows, struct CUkern_st* jit_toys, bool bulk, void* stream,
                       int* launches);
+// toy generation (k_generate.cu)
+int rf_launch_generate(const RfProgram& P, int coldt, const double* params_matrix,
+                       const int64_t* comp_counts, const int64_t* offsets, int32_t toys,
+                       unsigned long long seed, void* events, int64_t n_events,
+                       unsigned int* status, int num_sms, rf_cuda_stream st);
 // FP64 -> FP32 (round to nearest) of n values, for the toy columns of an
 // FP32-evaluated graph (converted once at bind time)
 int rf_columns_to_f32(const double* in, float* out, int64_t n, void* stream);
