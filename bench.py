@@ -134,6 +134,7 @@ LEAF_INSTR = {
     "cheb": (13, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
     "cb": (12, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
     "argus": (14, {0: 5, 1: 1}, 0),
+    "johnson": (14, {0: 0, 1: 1, 2: 0, 3: 1}, 4),
 }
 LOG_INSTR = 2          # hardware log2 and a multiply by ln 2
 F64_TO_F32_INSTR = 9   # integer-pipe rounding of an FP64 column value

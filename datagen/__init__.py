@@ -31,7 +31,7 @@ import numpy as np
 
 CHUNK = 1 << 20
 SEEDS = {"c1": 12875001, "c2": 12875002, "c3": 12875003, "c4": 12875004,
-         "c5": 12875005}
+         "c5": 12875005, "johnson": 12875006}
 
 
 def rng(seed: int, chunk: int = 0) -> np.random.Generator:
@@ -115,6 +115,13 @@ def argus_half(r, n, m0, c, lo, hi, dtype=np.float64):
     if np.any(out.astype(np.float64) >= m0):  # the open support, after rounding
         raise AssertionError("ARGUS draw at or above the endpoint")
     return out
+
+
+def johnson_su(r, n, mu, lam, gamma, delta, lo, hi, dtype=np.float64):
+    """Johnson SU by its defining transform: gamma + delta asinh((x-mu)/lam)
+    is a standard normal, so x = mu + lam sinh((z - gamma)/delta)."""
+    return _fill(r, n, lambda r, k: mu + lam * np.sinh((r.standard_normal(k) - gamma) / delta),
+                 dtype, lo, hi)
 
 
 # ----------------------------------------------------------------- workloads
@@ -257,6 +264,28 @@ def c5(n_sig=1_000_000, n_bkg=100_000_000, seed=SEEDS["c5"]):
         out[c * CHUNK:c * CHUNK + k] = ev
     return {"name": "cb_argus_ext_1.01e8_f32", "spec": cb_argus_spec(n_sig, n_bkg),
             "cols": out.reshape(1, -1), "dtype": "f32"}
+
+
+def johnson_exp_spec(nu_s=2e4, nu_b=8e4):
+    # params: 0 mu, 1 lambda, 2 gamma, 3 delta, 4 exp slope, 5 nu_s, 6 nu_b
+    return {"obs": [(0.0, 10.0)],
+            "params": [4.0, 0.8, -0.5, 1.6, -0.2, float(nu_s), float(nu_b)],
+            "fixed": [False] * 7,
+            "nodes": [{"type": "johnson", "obs": 0, "params": [0, 1, 2, 3]},
+                      {"type": "exp", "obs": 0, "params": [4]},
+                      {"type": "add_ext", "children": [0, 1], "params": [5, 6]}],
+            "root": 2}
+
+
+def johnson_exp(n_sig=20_000, n_bkg=80_000, seed=SEEDS["johnson"]):
+    """Extended Johnson SU (4.0, 0.8, -0.5, 1.6) + Exp(-0.2) on [0, 10], FP32
+    column, the two blocks shuffled together."""
+    r = rng(seed, 0)
+    ev = np.concatenate([johnson_su(r, n_sig, 4.0, 0.8, -0.5, 1.6, 0.0, 10.0, np.float32),
+                         expo(r, n_bkg, -0.2, 0.0, 10.0, np.float32)])
+    r.shuffle(ev)
+    return {"name": "johnson_exp_ext_f32", "spec": johnson_exp_spec(n_sig, n_bkg),
+            "cols": ev.reshape(1, -1), "dtype": "f32"}
 
 
 def _chunked(n, seed, draw, ncols=1, dtype=np.float64):

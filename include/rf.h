@@ -20,6 +20,9 @@
  *   RF_CHEB   (c_1..c_m), m <= 4     1 + sum_j c_j T_j(x'), x' = (2x-lo-hi)/(hi-lo)
  *   RF_CB     (m0, sigma, alpha, n)  Crystal Ball; alpha > 0: tail below m0
  *   RF_ARGUS  (m0, c, p), p = 1/2    x sqrt(1-(x/m0)^2) exp(c (1-(x/m0)^2)), x < m0
+ *   RF_JOHNSON (mu, lambda, gamma, delta)  Johnson's SU (Sec. 3): with
+ *             z = (x-mu)/lambda, w = gamma + delta asinh z standard normal:
+ *             delta / (lambda sqrt(2 pi (1+z^2))) exp(-w^2/2)
  * Composites:
  *   RF_ADD_FRAC (K children, K-1 fractions)  P = sum_{k<K-1} f_k P_k + (1-sum f) P_{K-1}
  *   RF_ADD_EXT  (K children, K yields; root) P = sum nu_k P_k, NLL += sum nu_k
@@ -75,7 +78,8 @@ enum {
   RF_ARGUS = 5,
   RF_ADD_FRAC = 6,
   RF_ADD_EXT = 7,
-  RF_PROD = 8
+  RF_PROD = 8,
+  RF_JOHNSON = 9
 };
 
 enum { RF_F32 = 0, RF_F64 = 1 };           /* column dtype              */
@@ -99,7 +103,7 @@ enum {
 #define RF_MAX_PARAMS 64
 
 typedef struct {
-  int32_t type;     /* RF_GAUSS .. RF_PROD                                   */
+  int32_t type;     /* RF_GAUSS .. RF_JOHNSON                                */
   int32_t obs;      /* leaves: observable (column) index; composites: -1     */
   int32_t n_children;
   int32_t children[RF_MAX_CHILDREN]; /* node indices                        */
@@ -209,6 +213,14 @@ rf_status rf_nll_batched(rf_graph* g, const int64_t* offsets, int32_t toys,
 rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
                       double* params_matrix, const double* scale, int32_t iters,
                       double lr, double* out, rf_stream stream);
+
+/* Sharded evaluation (the multi-process mode of Sec. 5.2, footnote: a
+ * dataset's contiguous batches divided among processes).  Each process
+ * evaluates its shard with rf_nll; the NLLs and gradients of the shards add
+ * up to the whole dataset's once the extended term sum(nu) (and its +1 in
+ * d/d nu) is counted on exactly one shard.  w is that term's weight in this
+ * graph (default 1): 1 on one shard, 0 on the others.  Host only. */
+rf_status rf_graph_set_shard_weight(rf_graph* g, double w);
 
 /* Toy generation: the events of `toys` datasets drawn from the graph, on the
  * device, in the layout rf_graph_bind_events / rf_nll_batched read.

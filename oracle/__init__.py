@@ -30,7 +30,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
-TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5,
+TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5, "johnson": 9,
          "add_frac": 6, "add_ext": 7, "prod": 8}
 MAXCH, MAXNP, MAXPAR = 8, 8, 64
 OK, EINVAL, EUNSUPPORTED, EDOMAIN = 0, 1, 2, 3

@@ -177,6 +177,22 @@ static int leaf_value(int type, const double* th, int nth, double lo, double hi,
       dlogf[2] = log(tau);
       return ORC_OK;
     }
+    case ORC_JOHNSON: {
+      /* Johnson's SU (N. L. Johnson, Biometrika 36 (1949) 149): z = (x-mu)/lambda,
+       * w = gamma + delta asinh z standard normal;
+       * f = delta / (lambda sqrt(2 pi) sqrt(1 + z^2)) exp(-w^2 / 2) */
+      if (nth != 4) return ORC_EINVAL;
+      double mu = th[0], lam = th[1], gam = th[2], del = th[3];
+      double z = (x - mu) / lam, r = sqrt(1.0 + z * z), as = asinh(z);
+      double w = gam + del * as;
+      *f_out = del / (lam * 2.5066282746310002 * r) * exp(-0.5 * w * w);
+      double dz = -z / (r * r) - w * del / r; /* d log f / dz */
+      dlogf[0] = dz * (-1.0 / lam);
+      dlogf[1] = -1.0 / lam + dz * (-z / lam);
+      dlogf[2] = -w;
+      dlogf[3] = 1.0 / del - w * as;
+      return ORC_OK;
+    }
     default:
       return ORC_EINVAL;
   }
@@ -339,6 +355,26 @@ static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
       dI[2] = NAN; /* d/dp of the incomplete gamma: not provided */
       return ORC_OK;
     }
+    case ORC_JOHNSON: {
+      /* the density integrates to 1 on the real line: on [lo, hi] it is
+       * Phi(w(hi)) - Phi(w(lo)), w = gamma + delta asinh((x - mu)/lambda) */
+      if (nth != 4) return ORC_EINVAL;
+      double mu = th[0], lam = th[1], gam = th[2], del = th[3];
+      if (!(lam > 0.0) || !(del > 0.0)) return ORC_EDOMAIN;
+      double za = (lo - mu) / lam, zb = (hi - mu) / lam;
+      double asa = asinh(za), asb = asinh(zb);
+      double wa = gam + del * asa, wb = gam + del * asb;
+      *I_out = 0.5 * erf_diff(wa / SQRT2, wb / SQRT2);
+      double pa = exp(-0.5 * wa * wa) / 2.5066282746310002;
+      double pb = exp(-0.5 * wb * wb) / 2.5066282746310002;
+      double ra = sqrt(1.0 + za * za), rb = sqrt(1.0 + zb * zb);
+      /* dI/dtheta = phi(wb) dwb/dtheta - phi(wa) dwa/dtheta */
+      dI[0] = pb * (-del / (lam * rb)) - pa * (-del / (lam * ra));
+      dI[1] = pb * (-del * zb / (lam * rb)) - pa * (-del * za / (lam * ra));
+      dI[2] = pb - pa;
+      dI[3] = pb * asb - pa * asa;
+      return ORC_OK;
+    }
     default:
       return ORC_EINVAL;
   }
@@ -362,7 +398,7 @@ int orc_leaf_norm(int type, const double* theta, int ntheta, double lo,
 /* graph walk                                                          */
 /* ------------------------------------------------------------------ */
 
-static int is_leaf(int t) { return t >= ORC_GAUSS && t <= ORC_ARGUS; }
+static int is_leaf(int t) { return (t >= ORC_GAUSS && t <= ORC_ARGUS) || t == ORC_JOHNSON; }
 
 typedef struct {
   double I[ORC_MAXNODE];
@@ -394,7 +430,7 @@ static int validate(const orc_model* m) {
   if (m->n_par < 0 || m->n_par > ORC_MAXPAR) return ORC_EINVAL;
   for (int i = 0; i < m->n_nodes; ++i) {
     int t = m->type[i];
-    if (t < ORC_GAUSS || t > ORC_PROD) return ORC_EINVAL;
+    if (t < ORC_GAUSS || t > ORC_JOHNSON) return ORC_EINVAL;
     if (m->npar[i] < 0 || m->npar[i] > ORC_MAXNP) return ORC_EINVAL;
     for (int j = 0; j < m->npar[i]; ++j) {
       int p = m->par[i * ORC_MAXNP + j];
@@ -824,6 +860,13 @@ static double sample_leaf(int type, const double* th, int nth, double a, double 
         t = tn_inv(v, tc, thi);
       }
       return s > 0.0 ? m0 + sg * t : m0 - sg * t;
+    }
+    case ORC_JOHNSON: {
+      /* w = gamma + delta asinh z is standard normal on [w(a), w(b)] */
+      double mu = th[0], lam = th[1], gam = th[2], del = th[3];
+      double wa = gam + del * asinh((a - mu) / lam), wb = gam + del * asinh((b - mu) / lam);
+      double w = tn_inv(u[0], wa, wb);
+      return mu + lam * sinh((w - gam) / del);
     }
     case ORC_ARGUS: {
       /* m dm ~ sqrt(tau) e^{c tau} d tau with tau = 1 - (m/m0)^2 */

@@ -38,7 +38,8 @@ enum {
   ORC_ARGUS = 5,    /* params (m0, c, p); p must equal 0.5     */
   ORC_ADD_FRAC = 6, /* K children, K-1 fraction params         */
   ORC_ADD_EXT = 7,  /* K children, K yield params; root only   */
-  ORC_PROD = 8      /* K children on disjoint observables      */
+  ORC_PROD = 8,     /* K children on disjoint observables      */
+  ORC_JOHNSON = 9   /* params (mu, lambda, gamma, delta): Johnson's SU */
 };
 
 #define ORC_MAXCH 8   /* children per node   */

@@ -30,7 +30,7 @@ from . import build as _build
 __all__ = ["Graph", "RFNll", "RFError", "load", "microbench", "TYPES"]
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5,
-         "add_frac": 6, "add_ext": 7, "prod": 8}
+         "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9}
 _STATUS = {0: "RF_OK", 1: "RF_EINVAL", 2: "RF_EUNSUPPORTED", 3: "RF_EALIGN",
            4: "RF_ECUDA", 5: "RF_ENOMEM"}
 MAX_CHILDREN, MAX_NODE_PARAMS = 8, 8
@@ -69,7 +69,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
            "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
-           "rf_check_d2f", "rf_generate_toys"]
+           "rf_check_d2f", "rf_generate_toys", "rf_graph_set_shard_weight"]
 
 
 def lib_path() -> str:
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
         L.rf_nll_batched.argtypes = [vp, vp, i32, vp, vp, vp]
         L.rf_fit_toys.argtypes = [vp, vp, i32, vp, vp, i32, C.c_double, vp, vp]
         L.rf_generate_toys.argtypes = [vp, vp, vp, vp, i32, C.c_uint64, vp, i64, vp]
+        L.rf_graph_set_shard_weight.argtypes = [vp, C.c_double]
         L.rf_nll_plain.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.rf_graph_get_launch.argtypes = [vp, C.POINTER(_Launch)]
         L.rf_graph_set_launch.argtypes = [vp, C.POINTER(_Launch)]
@@ -307,6 +308,11 @@ class Graph:
                                      _ptr(out), _stream()))
         return out
 
+    def set_shard_weight(self, w: float):
+        """Weight of the extended term in this graph's NLL (1 on exactly one
+        shard of a dataset split over processes, 0 on the others)."""
+        _check(load().rf_graph_set_shard_weight(self._h, float(w)))
+
     def generate_toys(self, params_matrix: torch.Tensor, comp_counts: torch.Tensor,
                       offsets: torch.Tensor, seed: int, n_events: int | None = None,
                       out: torch.Tensor | None = None) -> torch.Tensor:
@@ -419,3 +425,23 @@ def microbench() -> dict:
             "fp64_fma_latency_ns_1lane", "fp64_fma_latency_ns_32lanes",
             "exp_f64_latency_ns_1lane", "exp_f64_latency_ns_32lanes"]
     return dict(zip(keys, list(out)))
+
+
+def shard_range(n_events: int, rank: int, world: int) -> tuple[int, int]:
+    """The contiguous event range [lo, hi) of rank `rank` of `world`."""
+    return rank * n_events // world, (rank + 1) * n_events // world
+
+
+def sharded_nll(graph: "Graph", shard_events: torch.Tensor, params: torch.Tensor,
+                rank: int, group=None) -> torch.Tensor:
+    """NLL and gradient of a dataset split over the processes of a
+    torch.distributed group: this rank evaluates its contiguous shard
+    (rf_nll; the extended term on rank 0 only) and one sum all-reduce adds the
+    ranks' (1 + n_params) values.  Returns [1 + n_params] (NLL, gradient) of
+    the whole dataset on every rank."""
+    import torch.distributed as dist
+    graph.set_shard_weight(1.0 if rank == 0 else 0.0)
+    out = torch.empty(1 + graph.n_par, dtype=torch.float64, device=shard_events.device)
+    graph.nll(shard_events, params, out=out)
+    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+    return out

@@ -36,7 +36,7 @@ rf_status cuda_fail(cudaError_t e, const char* where) {
   return RF_ECUDA;
 }
 
-bool is_leaf(int t) { return t >= RF_GAUSS && t <= RF_ARGUS; }
+bool is_leaf(int t) { return (t >= RF_GAUSS && t <= RF_ARGUS) || t == RF_JOHNSON; }
 
 int leaf_nparams_ok(int t, int np) {
   switch (t) {
@@ -45,6 +45,7 @@ int leaf_nparams_ok(int t, int np) {
     case RF_CHEB: return np >= 1 && np <= RF_LEAF_MAXP;
     case RF_CB: return np == 4;
     case RF_ARGUS: return np == 3;
+    case RF_JOHNSON: return np == 4;
   }
   return 0;
 }
@@ -69,7 +70,7 @@ rf_status validate_desc(const rf_graph_desc* d) {
       return fail(RF_EINVAL, "observable " + std::to_string(o) + " has an empty or non-finite range");
   for (int i = 0; i < d->n_nodes; ++i) {
     const rf_node_desc& n = d->nodes[i];
-    if (n.type < RF_GAUSS || n.type > RF_PROD)
+    if (n.type < RF_GAUSS || n.type > RF_JOHNSON)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": unknown type");
     if (n.n_params < 0 || n.n_params > RF_MAX_NODE_PARAMS)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_params");
@@ -110,6 +111,7 @@ struct Canon {
 // only: no heap allocation on the success path).
 rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
   std::memset(P, 0, sizeof(*P));
+  P->ext_weight = 1.0;
   const rf_node_desc& root = d->nodes[d->root];
   int comp_leaf[RF_MAX_CHILDREN][RF_MAX_CHILDREN];  // leaf node ids per component
   int comp_n[RF_MAX_CHILDREN] = {0};
@@ -175,7 +177,7 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
         comp_obs |= 1ull << n.obs;
       }
       RfLeafProg& L = P->leaf[k++];
-      L.type = n.type;  // RF_GAUSS..RF_ARGUS == RFL_GAUSS..RFL_ARGUS
+      L.type = n.type;  // RF_<leaf> == RFL_<leaf>
       L.comp = c;
       L.npar = n.n_params;
       for (int j = 0; j < RF_LEAF_MAXP; ++j) L.par[j] = j < n.n_params ? n.params[j] : 0;
@@ -735,6 +737,13 @@ rf_status rf_fit_toys(rf_graph* g, const int64_t* offsets, int32_t toys,
   cudaEventDestroy(ev);
   g->last_launches = launches;
   if (e != cudaSuccess) return cuda_fail(e, "rf_fit_toys finish");
+  return RF_OK;
+}
+
+rf_status rf_graph_set_shard_weight(rf_graph* g, double w) {
+  if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (!std::isfinite(w)) return fail(RF_EINVAL, "weight must be finite");
+  g->prog.ext_weight = w;
   return RF_OK;
 }
 

@@ -41,6 +41,7 @@ const char* leaf_fn(int type) {
     case RFL_CHEB: return "leaf_cheb";
     case RFL_CB: return "leaf_cb";
     case RFL_ARGUS: return "leaf_argus";
+    case RFL_JOHNSON: return "leaf_johnson";
   }
   return nullptr;
 }

@@ -137,6 +137,13 @@ __device__ double sample_leaf(int type, const double* th, int npar, double a, do
       }
       return s > 0.0 ? m0 + sg * t : m0 - sg * t;
     }
+    case RFL_JOHNSON: {
+      // w = gamma + delta asinh z is standard normal on [w(a), w(b)]
+      const double mu = th[0], lam = th[1], gam = th[2], del = th[3];
+      const double wa = gam + del * asinh((a - mu) / lam), wb = gam + del * asinh((b - mu) / lam);
+      const double w = tn_inv(u[0], wa, wb);
+      return mu + lam * sinh((w - gam) / del);
+    }
     case RFL_ARGUS: {
       // m dm ~ sqrt(tau) e^{c tau} d tau, tau = 1 - (m/m0)^2: for c < 0 a
       // Gamma(3/2, rate -c) variate (E + Z^2/2)/(-c), E exponential and Z

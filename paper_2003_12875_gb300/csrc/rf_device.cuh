@@ -214,6 +214,25 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
       dln[3] = dn / J;
       return I > 0.0 && isfinite(I);
     }
+    case RFL_JOHNSON: {
+      // u = -log(1 + z^2)/2 - w^2/2 per event (z = (x-mu)/lambda, w = gamma +
+      // delta asinh z): I = lambda sqrt(2 pi)/delta (Phi(w(hi)) - Phi(w(lo)))
+      double mu = th[0], lam = th[1], gam = th[2], del = th[3];
+      if (!(lam > 0.0) || !(del > 0.0)) return false;
+      double za = (lo - mu) / lam, zb = (hi - mu) / lam;
+      double asa = asinh(za), asb = asinh(zb);
+      double wa = gam + del * asa, wb = gam + del * asb;
+      double dP = 0.5 * erf_diff(wa / kSqrt2, wb / kSqrt2);
+      double pa = d_exp(-0.5 * wa * wa) * 0.3989422804014327;
+      double pb = d_exp(-0.5 * wb * wb) * 0.3989422804014327;
+      double ra = sqrt(1.0 + za * za), rb = sqrt(1.0 + zb * zb);
+      *lnI = d_log(lam * 2.5066282746310002 / del * dP);
+      dln[0] = (pb * (-del / (lam * rb)) - pa * (-del / (lam * ra))) / dP;
+      dln[1] = 1.0 / lam + (pb * (-del * zb / (lam * rb)) - pa * (-del * za / (lam * ra))) / dP;
+      dln[2] = (pb - pa) / dP;
+      dln[3] = -1.0 / del + (pb * asb - pa * asa) / dP;
+      return dP > 0.0 && isfinite(*lnI);
+    }
     case RFL_ARGUS: {
       double m0 = th[0], c = th[1], p = th[2];
       if (p != 0.5 || !(m0 > lo) || lo < 0.0) return false;
@@ -300,6 +319,18 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       K.gmul[k][2] = s;            // d u/d alpha = s d u/d|alpha|
       break;
     }
+    case RFL_JOHNSON: {
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (Real)(1.0 / th[1]);
+      pc[3] = (Real)th[2];
+      pc[4] = (Real)th[3];
+      K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
+      K.dtheta[k][2] = (double)pc[3] - th[2];
+      K.dtheta[k][3] = (double)pc[4] - th[3];
+      K.gmul[k][0] = K.gmul[k][1] = -1.0 / th[1];  // d u/d mu = -du/dz / lambda, etc.
+      K.gmul[k][2] = K.gmul[k][3] = -1.0;         // d u/d gamma = -w, d u/d delta = -w asinh z
+      break;
+    }
     case RFL_ARGUS: {
       split_hi_lo(th[0], pc[0], pc[1]);
       pc[2] = (Real)(1.0 / (th[0] * th[0]));
@@ -348,6 +379,7 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
       coef[c] = v;
       K.ext_sum += v;
     }
+    K.ext_sum *= P.ext_weight;
   }
   for (int k = 0; k < P.n_leaves; ++k) base[P.leaf[k].comp] -= lnI[k];
   double beta[RF_MAXC];
@@ -459,6 +491,7 @@ struct Fn<float> {
   static __device__ __forceinline__ float exp_neg(float x) { return exp_neg_approx(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float ninf() { return -__int_as_float(0x7f800000); }
 };
 template <>
@@ -468,6 +501,7 @@ struct Fn<double> {
   static __device__ __forceinline__ double exp_neg(double x) { return ::exp(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   static __device__ __forceinline__ double ninf() { return -kInf(); }
 };
 
@@ -556,6 +590,30 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
   g[2] = g[3] = Real(0);
 }
 
+// Johnson's SU: t = 1 + z^2, u = -(log t + w^2)/2 with w = gamma + delta asinh z
+// (asinh z = sign(z) log(|z| + sqrt t)); du/dz = -(z + w delta sqrt t)/t.
+// Constant factors (-1/lambda, -1) are applied to the sums (gmul).
+template <typename Real, int GM>
+__device__ __forceinline__ void leaf_johnson(Real x, const Real* __restrict__ pc, Real& u,
+                                             Real (&g)[RF_LEAF_MAXP]) {
+  typedef Fn<Real> F;
+  const Real z = ((x - pc[0]) - pc[1]) * pc[2];
+  const Real t = Real(1) + z * z;
+  const Real r = F::sqrt(t);
+  const Real as = copysign(F::logp(fabs(z) + r), z);
+  const Real w = pc[3] + pc[4] * as;
+  u = Real(-0.5) * (F::logp(t) + w * w);
+  if (GM & 3) {
+    const Real dudz = -(z + w * pc[4] * r) * F::rcp(t);
+    g[0] = (GM & 1) ? dudz : Real(0);
+    g[1] = (GM & 2) ? dudz * z : Real(0);
+  } else {
+    g[0] = g[1] = Real(0);
+  }
+  g[2] = (GM & 4) ? w : Real(0);
+  g[3] = (GM & 8) ? w * as : Real(0);
+}
+
 // Runtime dispatch (the generic, precompiled model): all derivatives are
 // computed; the accumulation step keeps the ones in the leaf's gmask.
 template <typename Real>
@@ -571,6 +629,7 @@ __device__ __forceinline__ void eval_leaf(int type, int gm, Real x,
       if (gm & 1) leaf_argus<Real, 3>(x, pc, u, g);
       else leaf_argus<Real, 2>(x, pc, u, g);
       break;
+    case RFL_JOHNSON: leaf_johnson<Real, 15>(x, pc, u, g); break;
     default:
       u = Real(0);
       g[0] = g[1] = g[2] = g[3] = Real(0);
@@ -820,7 +879,7 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
         if ((P.coef_free >> c) & 1) grad[P.coef_par[c]] -= R[c] - R[C - 1];
     } else if (P.kind == RF_KIND_EXT) {
       for (int c = 0; c < C; ++c)
-        if ((P.coef_free >> c) & 1) grad[P.coef_par[c]] += 1.0 - R[c];
+        if ((P.coef_free >> c) & 1) grad[P.coef_par[c]] += P.ext_weight - R[c];
     }
     for (int p = 0; p < P.n_par; ++p) {
       bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
@@ -882,7 +941,7 @@ __device__ __forceinline__ void epilogue_warp(const RfProgram& P, const RfConsts
           g -= Rc - Rl;
         } else if (P.kind == RF_KIND_EXT && P.coef_par[c] == p) {
           const double Rc = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
-          g += 1.0 - Rc;
+          g += P.ext_weight - Rc;
         }
       }
       const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);

@@ -39,7 +39,7 @@ enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 #define RF_STATUS_NONFINITE_BIT 2u
 #define RF_STATUS_TIMEOUT_BIT 4u
 #define RF_STATUS_GEN_EXHAUSTED_BIT 8u
-enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5 };
+enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5, RFL_JOHNSON = 9 };
 
 struct RfLeafProg {
   int32_t type;      // RFL_*
@@ -62,6 +62,8 @@ struct RfProgram {
   int32_t coef_par[RF_MAXC]; // FRAC: K-1 fraction slots; EXT: K yield slots
   int32_t coef_free;         // bit c: gradient of coefficient c wanted
   uint64_t fixed_lo, fixed_hi;  // bit p: parameter p is fixed (grad = 0)
+  double ext_weight;         // weight of the extended term sum(nu) and its
+                             // gradient (1; 0 on all shards but one)
   RfLeafProg leaf[RF_MAXL];
 };
 

@@ -43,6 +43,8 @@ CASES = [
     ("cb", [0.0, 1.0, -1.2, 1.0], -3.0, 12.0, None),
     ("argus", [5.29, -20.0, 0.5], 5.20, 5.29, [True, False, True]),
     ("argus", [5.29, 2.0, 0.5], 5.0, 5.29, [True, False, True]),
+    ("johnson", [0.5, 1.3, -0.4, 1.7], -2.0, 3.0, None),
+    ("johnson", [0.0, 1.0, 2.5, 0.9], 2.0, 40.0, None),
 ]
 
 

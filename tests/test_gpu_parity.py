@@ -40,6 +40,7 @@ SMALL = {
     "c3": lambda: datagen.c3(n=100_003),
     "c3_noext": lambda: datagen.c3(n=50_001, extended=False),
     "c5": lambda: datagen.c5(3_000, 300_000),
+    "johnson": lambda: datagen.johnson_exp(20_011, 80_000),
 }
 OFF_MIN = {  # gradient checks away from the minimum
     "c1": [0.25, 1.1],
@@ -47,6 +48,7 @@ OFF_MIN = {  # gradient checks away from the minimum
     "c3": [0.05, 1.55, -0.48, 0.21, -0.09, 0.055, 0.025, 100_500.0],
     "c3_noext": [0.05, 1.55, -0.48, 0.21, -0.09, 0.055, 0.025],
     "c5": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.5, 3_050.0, 299_000.0],
+    "johnson": [4.05, 0.78, -0.45, 1.62, -0.21, 19_800.0, 80_300.0],
 }
 _cache = {}
 
@@ -85,7 +87,7 @@ def test_nll_and_gradient_match_oracle(rf, name, prec, jit):
 
 @pytest.mark.parametrize("jit", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson"])
 def test_per_event_log_probability(rf, name, prec, jit):
     w, p, *_ = workload(name)
     sub = {**w, "cols": w["cols"][:, :20_011]}
@@ -204,6 +206,29 @@ def test_back_to_back_calls_with_changing_parameters(rf):
     for k in range(len(pts)):
         assert torch.equal(outs[k].cpu(), alone[k]), k
     assert torch.equal(out2.cpu(), alone2)
+
+
+@pytest.mark.parametrize("shards", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sharded_evaluation_adds_up(rf, shards, prec):
+    """A dataset split into contiguous shards (the multi-process mode): with
+    the extended term weighted 1 on one shard and 0 on the others, the
+    shards' NLLs and gradients add up to the whole dataset's."""
+    w = datagen.c4(toys=1, nu_s_range=(30_000, 30_001), nu_b_range=(90_000, 90_001))
+    spec = w["spec"]
+    p = [5.03, 0.51, -0.29, 29_500.0, 91_000.0]
+    ev = to_dev(w)
+    n = ev.shape[1]
+    whole = torch.cat(rf.Graph(spec, "f64", prec).nll(ev, params_dev(p))).cpu().numpy()
+    total = np.zeros_like(whole)
+    for r in range(shards):
+        lo, hi = rf.shard_range(n, r, shards)
+        G = rf.Graph(spec, "f64", prec)
+        G.set_shard_weight(1.0 if r == 0 else 0.0)
+        total += torch.cat(G.nll(ev[:, lo:hi].contiguous(), params_dev(p))).cpu().numpy()
+    assert rel_nll(total[0], whole[0]) <= TOL[prec]["nll"]
+    _, gref, sc, _ = oracle.nll_scaled(spec, p, w["cols"])
+    assert grad_l1(total[1:], whole[1:], sc, [True] * 5).max() <= TOL[prec]["grad"]
 
 
 def test_gradient_against_finite_differences(rf):

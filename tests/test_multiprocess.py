@@ -73,3 +73,70 @@ def test_two_rank_aggregation_and_event_partition():
     summed[5] -= 1.0
     assert abs(summed[0] - v) <= 1e-12 * abs(v)
     np.testing.assert_allclose(summed[1:], g, rtol=1e-10, atol=1e-8)
+
+
+class _FakeGraph:
+    """Stands in for a Graph on CPU: its 'NLL' is the shard's oracle NLL with
+    the extended term weighted as set (no GPU needed)."""
+
+    def __init__(self, spec, cols, p):
+        self.spec, self.cols, self.p = spec, cols, p
+        self.n_par = len(p)
+        self.w = None
+
+    def set_shard_weight(self, w):
+        self.w = w
+
+    def nll(self, ev, params, out):
+        import oracle
+        import torch
+        v, g, rc = oracle.nll(self.spec, self.p, self.cols)
+        ext = sum(self.p[3:5])
+        v = v - ext + self.w * ext                 # extended term weighted
+        g = np.array(g)
+        g[3:5] += self.w - 1.0
+        out.copy_(torch.tensor([v, *g], dtype=torch.float64))
+
+
+def _shard_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+
+    import datagen
+    import paper_2003_12875_gb300 as rf
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        w = datagen.c4(toys=1, nu_s_range=(800, 800.001), nu_b_range=(2000, 2000.001))
+        n = w["cols"].shape[1]
+        lo, hi = rf.shard_range(n, rank, world)
+        p = [5.02, 0.51, -0.29, 790.0, 2010.0]
+        G = _FakeGraph(w["spec"], w["cols"][:, lo:hi], p)
+        out = rf.sharded_nll(G, torch.empty(1, hi - lo), torch.tensor(p), rank)
+        q.put((rank, G.w, out.numpy().tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_nll_helper_reduces_over_ranks():
+    """paper_2003_12875_gb300.sharded_nll on three gloo ranks: the extended
+    term is weighted on rank 0 only and the all-reduced result is the whole
+    dataset's NLL and gradient (oracle shards stand in for the GPU)."""
+    import datagen
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 3, port, q)) for r in range(3)]
+    for pr in procs:
+        pr.start()
+    res = sorted(q.get(timeout=180) for _ in range(3))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    assert [r[1] for r in res] == [1.0, 0.0, 0.0]
+    w = datagen.c4(toys=1, nu_s_range=(800, 800.001), nu_b_range=(2000, 2000.001))
+    v, g, rc = oracle.nll(w["spec"], [5.02, 0.51, -0.29, 790.0, 2010.0], w["cols"])
+    for _, _, out in res:
+        assert abs(out[0] - v) <= 1e-11 * abs(v)
+        np.testing.assert_allclose(out[1:], g, rtol=1e-9, atol=1e-9)

@@ -53,6 +53,10 @@ def lib_logpdf(kind, th, lo, hi, x):
         assert p == 0.5
         d = st.argus(math.sqrt(-2 * c), loc=0.0, scale=m0)
         return d.logpdf(x) - np.log(d.cdf(min(hi, m0)) - d.cdf(lo))
+    if kind == "johnson":
+        mu, lam, gamma, delta = th
+        d = st.johnsonsu(gamma, delta, loc=mu, scale=lam)
+        return d.logpdf(x) - np.log(d.cdf(hi) - d.cdf(lo))
     raise KeyError(kind)
 
 
@@ -70,7 +74,7 @@ def oracle_lognorm(kind, th, lo, hi, x):
 def fd_step(kind, th, j, lo, hi, rel):
     """Difference step on the natural scale of parameter j: the width for a
     location parameter, the parameter itself otherwise."""
-    if kind in ("gauss", "cb") and j == 0:
+    if kind in ("gauss", "cb", "johnson") and j == 0:
         return rel * th[1]
     if kind == "argus" and j == 0:
         return rel * (hi - lo)
@@ -109,6 +113,10 @@ LEAF_CASES = [
     ("argus", [5.29, -1.0, 0.5], 5.0, 5.29),    # series branch
     ("argus", [1.0, -40.0, 0.5], 0.2, 0.9),     # range ends below m0
     ("argus", [1.0, -3.0, 0.5], 0.0, 1.5),      # range extends past m0
+    ("johnson", [0.5, 1.3, -0.4, 1.7], -2.0, 3.0),
+    ("johnson", [5.28, 0.004, 0.8, 1.1], 5.20, 5.29),   # heavy tails, skewed
+    ("johnson", [0.0, 1.0, 0.0, 3.0], -1.0, 8.0),       # near-Gaussian core
+    ("johnson", [0.0, 1.0, 2.5, 0.9], 2.0, 40.0),       # far upper tail only
 ]
 
 
