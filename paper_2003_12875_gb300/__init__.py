@@ -58,7 +58,8 @@ class _Desc(C.Structure):
 
 
 class _Launch(C.Structure):
-    _fields_ = [("block", C.c_int32), ("ept", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("ept", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("min_blocks", C.c_int32)]
 
 
 _lib = None
@@ -361,12 +362,13 @@ class Graph:
     def get_launch(self) -> dict:
         c = _Launch()
         _check(load().rf_graph_get_launch(self._h, C.byref(c)))
-        return {"block": c.block, "ept": c.ept, "blocks_per_sm": c.blocks_per_sm}
+        return {"block": c.block, "ept": c.ept, "blocks_per_sm": c.blocks_per_sm,
+                "min_blocks": c.min_blocks}
 
-    def set_launch(self, block=None, ept=None, blocks_per_sm=None):
+    def set_launch(self, block=None, ept=None, blocks_per_sm=None, min_blocks=None):
         cur = self.get_launch()
         c = _Launch(block or cur["block"], ept or cur["ept"],
-                    blocks_per_sm or cur["blocks_per_sm"])
+                    blocks_per_sm or cur["blocks_per_sm"], min_blocks or cur["min_blocks"])
         _check(load().rf_graph_set_launch(self._h, C.byref(c)))
 
     def tune(self, events: torch.Tensor, params: torch.Tensor) -> float:

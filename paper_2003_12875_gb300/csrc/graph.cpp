@@ -218,7 +218,7 @@ struct rf_graph {
   RfProgram prog;
   int eval = 0, coldt = 0, n_obs = 0;
   int device = 0, num_sms = 0;
-  RfLaunchCfg cfg{256, 4, 2};
+  RfLaunchCfg cfg{256, 4, 2, 3};
   RfWork work{};
   int64_t max_rows_single = 0;
   // batched
@@ -246,12 +246,13 @@ struct rf_graph {
   void* pro_buf = nullptr;
   int last_launches = 0;
   // per-graph specialised kernels (NVRTC), by events per thread (index 0 or
-  // 1 of the precision's two options); compiled on first need
+  // 1 of the precision's two options) and, for the fused kernel, register
+  // budget (min_blocks 2 or 3); compiled on first need
   bool jit = false;
-  cudaKernel_t jk_fused[2] = {nullptr, nullptr};
+  cudaKernel_t jk_fused[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaKernel_t jk_toys[2] = {nullptr, nullptr};
   cudaKernel_t jk_logp = nullptr;
-  int jk_regs[2] = {0, 0};
+  int jk_regs[2][2] = {{0, 0}, {0, 0}};
 };
 
 // index of an events-per-thread option within its precision's pair
@@ -261,11 +262,14 @@ static int ept_index(int eval, int coldt, int ept) {
   return 0;
 }
 
-static cudaKernel_t jit_fused(rf_graph* g, int ept, std::string* err) {
-  int i = ept_index(g->eval, g->coldt, ept);
-  if (!g->jk_fused[i])
-    g->jk_fused[i] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_FUSED, ept, &g->jk_regs[i], err);
-  return g->jk_fused[i];
+static bool min_blocks_ok(int mb) { return mb == 2 || mb == 3; }
+
+static cudaKernel_t jit_fused(rf_graph* g, int ept, int min_blocks, std::string* err) {
+  const int i = ept_index(g->eval, g->coldt, ept), m = min_blocks - 2;
+  if (!g->jk_fused[i][m])
+    g->jk_fused[i][m] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_FUSED, ept, min_blocks,
+                                      &g->jk_regs[i][m], err);
+  return g->jk_fused[i][m];
 }
 
 // column type the toy kernels read: FP32-evaluated graphs read FP32 columns
@@ -290,7 +294,8 @@ static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
   int i = ept_index(g->eval, toy_coldt(g), ept);
   if (!g->jk_toys[i]) {
     cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g),
-                                   g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept, nullptr, err);
+                                   g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept, 0, nullptr,
+                                   err);
     if (k && g->toy_bulk) {  // its stage ring may use more than 48 KB of shared memory
       int optin = 0;
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
@@ -358,7 +363,10 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   g->coldt = desc->column_dtype;
   g->n_obs = desc->n_obs;
   if (const char* v = getenv("RF_TOY_STREAM")) g->toy_bulk = v[0] == 'b';
-  if (g->eval == RF_EVAL_FP64) g->cfg.ept = (g->coldt == RF_F64) ? 2 : 4;
+  if (g->eval == RF_EVAL_FP64) {
+    g->cfg.ept = (g->coldt == RF_F64) ? 2 : 4;
+    g->cfg.min_blocks = 2;  // FP64 evaluation runs out of registers at 80
+  }
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
   if (e != cudaSuccess) {
@@ -391,7 +399,7 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   if (!(env && env[0] == '0')) {
     g->jit = true;
     std::string err;
-    if (!jit_fused(g, g->cfg.ept, &err)) {
+    if (!jit_fused(g, g->cfg.ept, g->cfg.min_blocks, &err)) {
       g->jit = false;
       g_err = "JIT unavailable, generic kernels in use: " + err;
     }
@@ -409,7 +417,7 @@ rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
   bool was = g->jit;
   g->jit = true;
   std::string err;
-  if (!jit_fused(g, g->cfg.ept, &err)) {
+  if (!jit_fused(g, g->cfg.ept, g->cfg.min_blocks, &err)) {
     g->jit = was;
     return fail(RF_ECUDA, "JIT compile/load failed: " + err);
   }
@@ -420,12 +428,12 @@ int32_t rf_graph_uses_jit(const rf_graph* g) { return g && g->jit ? 1 : 0; }
 
 uint64_t rf_graph_kernel_hash(const rf_graph* g) {
   if (!g || !g->jit) return 0;
-  return rf_jit_hash(g->prog, g->eval, g->coldt, RF_JIT_FUSED, g->cfg.ept);
+  return rf_jit_hash(g->prog, g->eval, g->coldt, RF_JIT_FUSED, g->cfg.ept, g->cfg.min_blocks);
 }
 
 int32_t rf_graph_kernel_regs(const rf_graph* g) {
   if (!g || !g->jit) return 0;
-  return g->jk_regs[ept_index(g->eval, g->coldt, g->cfg.ept)];
+  return g->jk_regs[ept_index(g->eval, g->coldt, g->cfg.ept)][g->cfg.min_blocks - 2];
 }
 
 rf_status rf_jit_check(const rf_graph_desc* desc) {
@@ -443,7 +451,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
     const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
     const int ke = toy ? 8 : ept;
-    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, &err))
+    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, 3, &err))
       return fail(RF_ECUDA, err);
   }
   return RF_OK;
@@ -473,7 +481,7 @@ static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, i
   int pe = rf_launch_prologue(P, g->eval, params, g->work, st);
   if (pe) return pe;
   if (g->jit) {
-    cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)];
+    cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)][cfg.min_blocks - 2];
     if (!k) return (int)cudaErrorInvalidValue;  // compiled by compile/set_launch/tune
     return rf_jit_launch_fused(k, P, g->coldt, cfg, g->num_sms, ev, n, params, g->work, nll,
                                grad, st);
@@ -570,7 +578,7 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events, const doubl
   int e;
   if (g->jit && !g->jk_logp) {
     std::string err;  // first call compiles the kernel (host-synchronous)
-    g->jk_logp = rf_jit_kernel(P, g->eval, g->coldt, RF_JIT_LOGP, 0, nullptr, &err);
+    g->jk_logp = rf_jit_kernel(P, g->eval, g->coldt, RF_JIT_LOGP, 0, 0, nullptr, &err);
     if (!g->jk_logp) return fail(RF_ECUDA, "JIT log P kernel: " + err);
   }
   if (g->jit)
@@ -811,6 +819,7 @@ rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg) {
   cfg->block = g->cfg.block;
   cfg->ept = g->cfg.ept;
   cfg->blocks_per_sm = g->cfg.blocks_per_sm;
+  cfg->min_blocks = g->cfg.min_blocks;
   return RF_OK;
 }
 
@@ -822,15 +831,18 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
     return fail(RF_EINVAL, "events per thread not available for this precision / dtype");
   if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
     return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
+  if (!min_blocks_ok(cfg->min_blocks)) return fail(RF_EINVAL, "min_blocks must be 2 or 3");
   if (g->jit) {
     std::string err;
-    if (!jit_fused(g, cfg->ept, &err)) return fail(RF_ECUDA, "JIT fused kernel: " + err);
+    if (!jit_fused(g, cfg->ept, cfg->min_blocks, &err))
+      return fail(RF_ECUDA, "JIT fused kernel: " + err);
     if (g->bound && !jit_toys(g, toy_ept(g), &err))
       return fail(RF_ECUDA, "JIT toy kernel: " + err);
   }
   g->cfg.block = cfg->block;
   g->cfg.ept = cfg->ept;
   g->cfg.blocks_per_sm = cfg->blocks_per_sm;
+  g->cfg.min_blocks = cfg->min_blocks;
   return RF_OK;
 }
 
@@ -858,24 +870,30 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   } else {
     epts[0] = epts[1] = 4;
   }
+  // register budgets: both for the specialised kernel, the generic kernels
+  // have one
+  const int n_mb = g->jit ? 2 : 1;
+  const int mbs[2] = {g->jit ? 2 : g->cfg.min_blocks, 3};
   if (g->jit) {
     std::string err;
     for (int ei = 0; ei < 2; ++ei)
-      if (!jit_fused(g, epts[ei], &err)) {
-        cudaFree(dout);
-        return fail(RF_ECUDA, "JIT fused kernel: " + err);
-      }
+      for (int mi = 0; mi < n_mb; ++mi)
+        if (!jit_fused(g, epts[ei], mbs[mi], &err)) {
+          cudaFree(dout);
+          return fail(RF_ECUDA, "JIT fused kernel: " + err);
+        }
   }
   RfLaunchCfg best = g->cfg;
   float best_t = 1e30f;
   for (int bi = 0; bi < 3; ++bi)
     for (int ei = 0; ei < 2; ++ei) {
       if (ei == 1 && epts[1] == epts[0]) continue;
-      for (int pi = 0; pi < 6; ++pi) {
+      for (int pi = 0; pi < 6 * n_mb; ++pi) {
         RfLaunchCfg c = g->cfg;
         c.block = blocks[bi];
         c.ept = epts[ei];
-        c.blocks_per_sm = bpss[pi];
+        c.blocks_per_sm = bpss[pi % 6];
+        c.min_blocks = mbs[pi / 6];
         float tsum = 0.f;
         for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
           cudaEventRecord(a, st);
@@ -901,6 +919,7 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   g->cfg.block = best.block;
   g->cfg.ept = best.ept;
   g->cfg.blocks_per_sm = best.blocks_per_sm;
+  g->cfg.min_blocks = best.min_blocks;
   if (best_ms) *best_ms = best_t / 5.0;
   return RF_OK;
 }

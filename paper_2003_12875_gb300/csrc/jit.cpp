@@ -64,7 +64,8 @@ std::string cache_dir() {
 
 }  // namespace
 
-std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept) {
+std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                          int min_blocks) {
   const int NL = P.n_leaves, NC = P.n_comp;
   unsigned long long amask = 1ull;  // ell
   for (int c = 0; c < NC; ++c) amask |= 1ull << (1 + c);
@@ -114,16 +115,15 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
   o << "  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
-  // The fused kernel is declared for 3 resident blocks of 256 threads per SM
-  // (80 registers on the Crystal Ball + ARGUS model; measured 1.5% faster than
-  // 2 blocks at 93 registers, with the tuner picking the block shape).  Without
-  // a minimum, ptxas's budget depends on the rest of the kernel (an FP64 tail
-  // once pulled the event loop to 80 registers with spills).
-  // RF_JIT_MINBLOCKS=k asks for k blocks instead.
-  std::string lb = "__launch_bounds__(256, 3)";
-
-  if (const char* mb = getenv("RF_JIT_MINBLOCKS"))
-    if (atoi(mb) > 0) lb = "__launch_bounds__(256, " + std::to_string(atoi(mb)) + ")";
+  // The fused kernel is declared for min_blocks resident blocks of 256
+  // threads per SM: a register budget of 80 (3 blocks) or 128 (2 blocks).
+  // The best budget depends on the graph (the FP32 Crystal Ball + ARGUS
+  // model runs 1.5% faster at 80 registers than at 93; the FP64 and the
+  // three-observable models lose at 80), so it is a tuned launch parameter.
+  // A fixed minimum also keeps ptxas's budget from depending on the rest of
+  // the kernel (an FP64 tail once pulled the event loop to 80 registers
+  // with spills).
+  const std::string lb = "__launch_bounds__(256, " + std::to_string(min_blocks) + ")";
   if (kind == RF_JIT_FUSED) {
     o << "extern \"C\" __global__ void " << lb << " rf_fused_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t n, int64_t head, int vec, const double* __restrict__ "
@@ -179,27 +179,27 @@ static bool compile_cubin(const std::string& src, std::vector<char>* cubin, std:
   return true;
 }
 
-uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept) {
-  return fnv1a(rf_jit_source(P, eval, coldt, kind, ept));
+uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept, int min_blocks) {
+  return fnv1a(rf_jit_source(P, eval, coldt, kind, ept, min_blocks));
 }
 
 bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                         std::string* err) {
+                         int min_blocks, std::string* err) {
   std::vector<char> cubin;
-  return compile_cubin(rf_jit_source(P, eval, coldt, kind, ept), &cubin, err);
+  return compile_cubin(rf_jit_source(P, eval, coldt, kind, ept, min_blocks), &cubin, err);
 }
 
 // The kernel of the given kind specialised for P: from the process cache, else
 // from the on-disk cache, else compiled with NVRTC (and written to disk).
 // Host-synchronous; returns nullptr and fills *err on failure.
 cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                           int* regs, std::string* err) {
+                           int min_blocks, int* regs, std::string* err) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     *err = "no current device";
     return nullptr;
   }
-  std::string src = rf_jit_source(P, eval, coldt, kind, ept);
+  std::string src = rf_jit_source(P, eval, coldt, kind, ept, min_blocks);
   std::string key = std::to_string(dev) + "|" + src;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(key);

@@ -111,6 +111,7 @@ extern "C" rf_status rf_nll_noalloc(const rf_graph_desc* desc, const void* event
   RfLaunchCfg cfg;
   cfg.block = 256;
   cfg.blocks_per_sm = 1;
+  cfg.min_blocks = 2;  // not used by the generic kernels
   int le;
   if (desc->eval_precision == RF_EVAL_FP32) {
     cfg.ept = 4;

@@ -105,6 +105,7 @@ struct RfLaunchCfg {
   int block;
   int ept;
   int blocks_per_sm;
+  int min_blocks;  // register budget of the specialised fused kernel (2 or 3)
 };
 
 #ifndef __CUDACC_RTC__
@@ -169,12 +170,15 @@ void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int ele
 // rings (RF_JIT_TOYS_BULK)
 enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2, RF_JIT_TOYS_BULK = 3 };
 typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
-std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept);
-uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept);
+// min_blocks: the fused kernel's launch bounds (blocks of 256 threads per SM);
+// the other kinds ignore it
+std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept,
+                          int min_blocks);
+uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept, int min_blocks);
 bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                         std::string* err);
+                         int min_blocks, std::string* err);
 rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                             int* regs, std::string* err);
+                             int min_blocks, int* regs, std::string* err);
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
                         RfWork W, double* nll, double* grad, rf_cuda_stream st);

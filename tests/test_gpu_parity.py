@@ -143,11 +143,23 @@ def test_every_launch_configuration(rf, jit):
         for block in (64, 128, 256):
             for ept in epts:
                 for bps in (1, 2, 3, 4, 6, 8):
-                    G.set_launch(block=block, ept=ept, blocks_per_sm=bps)
-                    nll, grad = G.nll(ev, pd)
-                    assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"], (block, ept, bps)
-                    err = grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"]))
-                    assert err.max() <= TOL[prec]["grad"], (block, ept, bps, err)
+                    for mb in ((2, 3) if jit else (2,)):
+                        G.set_launch(block=block, ept=ept, blocks_per_sm=bps, min_blocks=mb)
+                        nll, grad = G.nll(ev, pd)
+                        cfg = (block, ept, bps, mb)
+                        assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"], cfg
+                        err = grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"]))
+                        assert err.max() <= TOL[prec]["grad"], (cfg, err)
+
+
+def test_launch_defaults_and_invalid_register_budget(rf):
+    w, p, *_ = workload("c2")
+    assert rf.Graph(w["spec"], "f64", "fp32").get_launch()["min_blocks"] == 3
+    G = rf.Graph(w["spec"], "f64", "fp64")
+    assert G.get_launch()["min_blocks"] == 2
+    with pytest.raises(rf.RFError):
+        G.set_launch(min_blocks=4)
+    assert G.get_launch()["min_blocks"] == 2
 
 
 def test_tuner_picks_a_valid_configuration(rf):
@@ -157,6 +169,7 @@ def test_tuner_picks_a_valid_configuration(rf):
     assert ms > 0
     cfg = G.get_launch()
     assert cfg["block"] in (64, 128, 256) and cfg["ept"] in (4, 8)
+    assert cfg["min_blocks"] in (2, 3)
     nll, _ = G.nll(to_dev(w), params_dev(p))
     assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
 
