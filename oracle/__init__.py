@@ -14,7 +14,8 @@ A model is the plain-data ``spec`` dict used throughout the repository::
      "root": index}
 
 Leaf parameter order: gauss (mu, sigma); exp (lambda); cheb (c_1..c_m);
-cb (m0, sigma, alpha, n); argus (m0, c, p).
+cb (m0, sigma, alpha, n); argus (m0, c, p); johnson (mu, lambda, gamma,
+delta); expr (p0 .. p(m-1) of the node's "expr" formula in x).
 """
 from __future__ import annotations
 
@@ -31,7 +32,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5, "johnson": 9,
-         "add_frac": 6, "add_ext": 7, "prod": 8}
+         "expr": 10, "add_frac": 6, "add_ext": 7, "prod": 8}
 MAXCH, MAXNP, MAXPAR = 8, 8, 64
 OK, EINVAL, EUNSUPPORTED, EDOMAIN = 0, 1, 2, 3
 
@@ -61,7 +62,8 @@ class _Model(C.Structure):
                 ("type", C.c_void_p), ("obs", C.c_void_p),
                 ("nchild", C.c_void_p), ("child", C.c_void_p),
                 ("npar", C.c_void_p), ("par", C.c_void_p),
-                ("obs_lo", C.c_void_p), ("obs_hi", C.c_void_p)]
+                ("obs_lo", C.c_void_p), ("obs_hi", C.c_void_p),
+                ("expr", C.c_void_p)]
 
 
 def lib():
@@ -93,6 +95,10 @@ def lib():
             i64p = C.POINTER(C.c_int64)
             L.orc_generate.argtypes = [C.POINTER(_Model), dp, C.c_int32, i64p, i64p, C.c_uint64,
                                        C.c_int, dp, C.c_int64, i64p]
+            L.orc_expr_check.argtypes = [C.c_char_p, C.c_int]
+            L.orc_expr_logf.argtypes = [C.c_char_p, dp, C.c_int, C.c_double, dp, dp]
+            L.orc_expr_norm.argtypes = [C.c_char_p, dp, C.c_int, C.c_double, C.c_double, dp,
+                                        dp]
             _lib = L
     return _lib
 
@@ -123,6 +129,8 @@ class Model:
             ps = nd.get("params", [])
             self.npar[i] = len(ps)
             self.par[i * MAXNP:i * MAXNP + len(ps)] = ps
+        self.texts = [nd.get("expr", "").encode() for nd in nodes]
+        self.expr = (C.c_char_p * N)(*self.texts)
         rng = np.asarray(spec["obs"], np.float64).reshape(-1, 2)
         self.lo = np.ascontiguousarray(rng[:, 0])
         self.hi = np.ascontiguousarray(rng[:, 1])
@@ -131,7 +139,8 @@ class Model:
                         self.type.ctypes.data, self.obs.ctypes.data,
                         self.nchild.ctypes.data, self.child.ctypes.data,
                         self.npar.ctypes.data, self.par.ctypes.data,
-                        self.lo.ctypes.data, self.hi.ctypes.data)
+                        self.lo.ctypes.data, self.hi.ctypes.data,
+                        C.cast(self.expr, C.c_void_p).value)
 
 
 def _cols(cols) -> np.ndarray:
@@ -189,6 +198,30 @@ def leaf_norm(kind: str, theta, lo: float, hi: float):
     I = np.zeros(1)
     d = np.zeros(max(len(th), 1))
     rc = lib().orc_leaf_norm(TYPES[kind], _dp(th), len(th), lo, hi, _dp(I), _dp(d))
+    return float(I[0]), d[:len(th)], rc
+
+
+def expr_check(text: str, npar: int) -> int:
+    return lib().orc_expr_check(text.encode(), npar)
+
+
+def expr_logf(text: str, theta, x: float):
+    """(log f(x), d log f / dp_j, return code) of a formula leaf."""
+    th = np.ascontiguousarray(np.asarray(theta, np.float64))
+    lf = np.zeros(1)
+    d = np.zeros(max(len(th), 1))
+    rc = lib().orc_expr_logf(text.encode(), _dp(th) if len(th) else None, len(th), x,
+                             _dp(lf), _dp(d))
+    return float(lf[0]), d[:len(th)], rc
+
+
+def expr_norm(text: str, theta, lo: float, hi: float):
+    """(I, dI/dp_j, return code) of a formula leaf on [lo, hi]."""
+    th = np.ascontiguousarray(np.asarray(theta, np.float64))
+    I = np.zeros(1)
+    d = np.zeros(max(len(th), 1))
+    rc = lib().orc_expr_norm(text.encode(), _dp(th) if len(th) else None, len(th), lo, hi,
+                             _dp(I), _dp(d))
     return float(I[0]), d[:len(th)], rc
 
 

@@ -26,6 +26,9 @@
  *             f = exp(-t^2/2) for t > -A, else
  *             f = exp(-A^2/2) * D^-n, D = 1 - (A/n)(A+t)   (== A'(B-t)^-n)
  *  ARGUS      f = x tau^p exp(c tau), tau = 1-(x/m0)^2 for x < m0, else 0
+ *  Johnson SU f = delta/(lambda sqrt(2 pi (1+z^2))) exp(-(gamma+delta asinh z)^2/2)
+ *  Formula    f = the node's text in x and p0..p(m-1) (Sec. 4, formula PDFs),
+ *             normalised by adaptive Gauss-Legendre quadrature
  *  Add (fractions)  P = sum_{k<K-1} f_k P_k + (1 - sum f_k) P_{K-1}
  *  Add (extended)   P = sum_k nu_k P_k,  NLL += sum_k nu_k  (no log n! term)
  *  Prod             P = prod_k P_k   (children on disjoint observables)
@@ -41,6 +44,10 @@
  * Crystal Ball value and slope continuity at t=-A; the gradient against
  * Richardson-extrapolated central differences; the extended-ML invariant
  * sum nu = n; Adam against its published update written out by hand.
+ * Formula leaves: texts that spell out a built-in leaf reproduce it (value,
+ * derivatives, integral, whole-model NLL); values against Python's own
+ * evaluation of the text; integrals against mpmath quadrature and a
+ * Breit-Wigner's arctangent closed form.
  */
 #include "rf_oracle.h"
 
@@ -55,6 +62,7 @@
 #define SQRT2 1.41421356237309504880
 #define SQRT_PI_2 1.25331413731550025121 /* sqrt(pi/2) */
 #define SQRT_PI 1.77245385090551602730
+#define PI_VAL 3.14159265358979323846
 
 /* ------------------------------------------------------------------ */
 /* small helpers                                                       */
@@ -101,15 +109,486 @@ static void nsum_add(nsum* a, double x) {
 static double nsum_val(const nsum* a) { return a->s + a->c; }
 
 /* ------------------------------------------------------------------ */
+/* expression leaves (ORC_EXPR)                                        */
+/* ------------------------------------------------------------------ */
+/* Formula PDFs (Sec. 4: RooGenericPdf, a PDF written as a formula string and
+ * compiled just in time).  Here the text is parsed into a tree once per call
+ * and the tree is walked for every value, with forward-mode derivatives with
+ * respect to the leaf's parameters p0 .. p(m-1); the normalisation integral
+ * and its derivatives come from adaptive Gauss-Legendre quadrature.
+ * Grammar:
+ *   sum   := prod (('+' | '-') prod)*
+ *   prod  := unary (('*' | '/') unary)*
+ *   unary := ('-' | '+') unary | power
+ *   power := atom ('^' unary)?          (right-associative; -a^2 = -(a^2))
+ *   atom  := number | 'x' | 'p'digits | name '(' sum ')' | 'pow' '(' sum ',' sum ')'
+ *            | '(' sum ')'
+ *   number: digits ['.' digits] [('e'|'E') ['+'|'-'] digits], or '.' digits ...
+ *   name: exp log sqrt sin cos tanh sinh cosh asinh atan erf erfc abs
+ * a^b (and pow(a, b)) with b an integer literal is a repeated product, valid
+ * for any sign of a; any other b gives exp(b log a). */
+enum {
+  X_NUM, X_VAR, X_PAR, X_NEG, X_ADD, X_SUB, X_MUL, X_DIV, X_POWI, X_POW,
+  X_EXP, X_LOG, X_SQRT, X_SIN, X_COS, X_TANH, X_SINH, X_COSH, X_ASINH, X_ATAN,
+  X_ERF, X_ERFC, X_ABS
+};
+#define ORC_XMAX 256
+#define ORC_XLEN 4096
+typedef struct {
+  int op, a, b;
+  double c;
+} xnode;
+typedef struct {
+  xnode n[ORC_XMAX];
+  int len, root;
+} xprog;
+typedef struct {
+  const char* s;
+  int pos, npar, err, depth;
+  xprog* p;
+} xparser;
+
+static const struct {
+  const char* name;
+  int op;
+} xfuncs[] = {{"exp", X_EXP},     {"log", X_LOG},   {"sqrt", X_SQRT}, {"sin", X_SIN},
+              {"cos", X_COS},     {"tanh", X_TANH}, {"sinh", X_SINH}, {"cosh", X_COSH},
+              {"asinh", X_ASINH}, {"atan", X_ATAN}, {"erf", X_ERF},   {"erfc", X_ERFC},
+              {"abs", X_ABS}};
+
+static int xnew(xparser* q, int op, int a, int b, double c) {
+  if (q->p->len >= ORC_XMAX) {
+    q->err = 1;
+    return 0;
+  }
+  xnode* n = &q->p->n[q->p->len];
+  n->op = op;
+  n->a = a;
+  n->b = b;
+  n->c = c;
+  return q->p->len++;
+}
+static void xskip(xparser* q) {
+  while (q->s[q->pos] == ' ' || q->s[q->pos] == '\t' || q->s[q->pos] == '\n') q->pos++;
+}
+static int xisdigit(char c) { return c >= '0' && c <= '9'; }
+static int xisalpha(char c) { return (c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z') || c == '_'; }
+static int xsum(xparser* q);
+static int xunary(xparser* q);
+
+/* a^b: an integer literal exponent becomes X_POWI (exponent in c) */
+static int xpow_node(xparser* q, int base, int ex) {
+  const xnode* e = &q->p->n[ex];
+  if (e->op == X_NUM && e->c == floor(e->c) && fabs(e->c) <= 64.0)
+    return xnew(q, X_POWI, base, -1, e->c);
+  if (e->op == X_NEG && q->p->n[e->a].op == X_NUM) {
+    double v = -q->p->n[e->a].c;
+    if (v == floor(v) && fabs(v) <= 64.0) return xnew(q, X_POWI, base, -1, v);
+  }
+  return xnew(q, X_POW, base, ex, 0.0);
+}
+
+static int xatom(xparser* q) {
+  xskip(q);
+  const char* s = q->s;
+  char c = s[q->pos];
+  if (xisdigit(c) || (c == '.' && xisdigit(s[q->pos + 1]))) {
+    int b = q->pos;
+    while (xisdigit(s[q->pos])) q->pos++;
+    if (s[q->pos] == '.') {
+      q->pos++;
+      while (xisdigit(s[q->pos])) q->pos++;
+    }
+    if (s[q->pos] == 'e' || s[q->pos] == 'E') {
+      int save = q->pos++;
+      if (s[q->pos] == '+' || s[q->pos] == '-') q->pos++;
+      if (!xisdigit(s[q->pos])) {
+        q->pos = save;
+        q->err = 1;
+        return 0;
+      }
+      while (xisdigit(s[q->pos])) q->pos++;
+    }
+    char buf[64];
+    int len = q->pos - b;
+    if (len >= (int)sizeof(buf)) {
+      q->err = 1;
+      return 0;
+    }
+    memcpy(buf, s + b, (size_t)len);
+    buf[len] = 0;
+    return xnew(q, X_NUM, -1, -1, strtod(buf, NULL));
+  }
+  if (xisalpha(c)) {
+    int b = q->pos;
+    while (xisalpha(s[q->pos]) || xisdigit(s[q->pos])) q->pos++;
+    int len = q->pos - b;
+    if (len == 1 && c == 'x') return xnew(q, X_VAR, -1, -1, 0.0);
+    if (c == 'p' && len >= 2) {
+      int k = 0, allnum = 1;
+      for (int i = 1; i < len; ++i) {
+        if (!xisdigit(s[b + i])) allnum = 0;
+        else k = k * 10 + (s[b + i] - '0');
+        if (k > 1000) allnum = 0;
+      }
+      if (allnum) {
+        if (k >= q->npar) {
+          q->err = 1;
+          return 0;
+        }
+        return xnew(q, X_PAR, k, -1, 0.0);
+      }
+    }
+    int op = -1, is_pow = (len == 3 && strncmp(s + b, "pow", 3) == 0);
+    for (size_t i = 0; i < sizeof(xfuncs) / sizeof(xfuncs[0]); ++i)
+      if ((int)strlen(xfuncs[i].name) == len && strncmp(s + b, xfuncs[i].name, (size_t)len) == 0)
+        op = xfuncs[i].op;
+    if (op < 0 && !is_pow) {
+      q->err = 1;
+      return 0;
+    }
+    xskip(q);
+    if (s[q->pos] != '(') {
+      q->err = 1;
+      return 0;
+    }
+    q->pos++;
+    int a = xsum(q);
+    if (q->err) return 0;
+    xskip(q);
+    int r;
+    if (is_pow) {
+      if (s[q->pos] != ',') {
+        q->err = 1;
+        return 0;
+      }
+      q->pos++;
+      int e = xsum(q);
+      if (q->err) return 0;
+      xskip(q);
+      r = xpow_node(q, a, e);
+    } else {
+      r = xnew(q, op, a, -1, 0.0);
+    }
+    if (s[q->pos] != ')') {
+      q->err = 1;
+      return 0;
+    }
+    q->pos++;
+    return r;
+  }
+  if (c == '(') {
+    q->pos++;
+    int a = xsum(q);
+    if (q->err) return 0;
+    xskip(q);
+    if (s[q->pos] != ')') {
+      q->err = 1;
+      return 0;
+    }
+    q->pos++;
+    return a;
+  }
+  q->err = 1;
+  return 0;
+}
+
+static int xpower(xparser* q) {
+  int a = xatom(q);
+  if (q->err) return 0;
+  xskip(q);
+  if (q->s[q->pos] == '^') {
+    q->pos++;
+    int e = xunary(q);
+    if (q->err) return 0;
+    return xpow_node(q, a, e);
+  }
+  return a;
+}
+
+static int xunary(xparser* q) {
+  if (++q->depth > 200) {
+    q->err = 1;
+    return 0;
+  }
+  xskip(q);
+  int r;
+  if (q->s[q->pos] == '-') {
+    q->pos++;
+    int a = xunary(q);
+    r = q->err ? 0 : xnew(q, X_NEG, a, -1, 0.0);
+  } else if (q->s[q->pos] == '+') {
+    q->pos++;
+    r = xunary(q);
+  } else {
+    r = xpower(q);
+  }
+  q->depth--;
+  return r;
+}
+
+static int xprod(xparser* q) {
+  int a = xunary(q);
+  while (!q->err) {
+    xskip(q);
+    char c = q->s[q->pos];
+    if (c != '*' && c != '/') break;
+    q->pos++;
+    int b = xunary(q);
+    if (q->err) return 0;
+    a = xnew(q, c == '*' ? X_MUL : X_DIV, a, b, 0.0);
+  }
+  return a;
+}
+
+static int xsum(xparser* q) {
+  if (++q->depth > 200) {
+    q->err = 1;
+    return 0;
+  }
+  int a = xprod(q);
+  while (!q->err) {
+    xskip(q);
+    char c = q->s[q->pos];
+    if (c != '+' && c != '-') break;
+    q->pos++;
+    int b = xprod(q);
+    if (q->err) return 0;
+    a = xnew(q, c == '+' ? X_ADD : X_SUB, a, b, 0.0);
+  }
+  q->depth--;
+  return a;
+}
+
+/* Parses text with parameters p0 .. p(npar-1).  ORC_EINVAL on any error. */
+static int xparse(const char* text, int npar, xprog* p) {
+  if (!text || npar < 0 || npar > ORC_MAXNP || strlen(text) > ORC_XLEN) return ORC_EINVAL;
+  xparser q = {text, 0, npar, 0, 0, p};
+  p->len = 0;
+  p->root = xsum(&q);
+  xskip(&q);
+  if (q.err || text[q.pos] != 0) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+/* value v and dv[j] = dv/dp_j (j < m) of node i */
+static void xeval(const xprog* p, int i, double x, const double* th, int m, double* v,
+                  double* dv) {
+  const xnode* n = &p->n[i];
+  double a, da[ORC_MAXNP], b, db[ORC_MAXNP];
+  for (int j = 0; j < m; ++j) dv[j] = 0.0;
+  switch (n->op) {
+    case X_NUM:
+      *v = n->c;
+      return;
+    case X_VAR:
+      *v = x;
+      return;
+    case X_PAR:
+      *v = th[n->a];
+      dv[n->a] = 1.0;
+      return;
+    default:
+      break;
+  }
+  xeval(p, n->a, x, th, m, &a, da);
+  if (n->op >= X_ADD && n->op <= X_DIV) xeval(p, n->b, x, th, m, &b, db);
+  if (n->op == X_POW) xeval(p, n->b, x, th, m, &b, db);
+  double s = 0.0; /* dv = s * da (one-argument functions) */
+  switch (n->op) {
+    case X_NEG: *v = -a; s = -1.0; break;
+    case X_ADD:
+      *v = a + b;
+      for (int j = 0; j < m; ++j) dv[j] = da[j] + db[j];
+      return;
+    case X_SUB:
+      *v = a - b;
+      for (int j = 0; j < m; ++j) dv[j] = da[j] - db[j];
+      return;
+    case X_MUL:
+      *v = a * b;
+      for (int j = 0; j < m; ++j) dv[j] = da[j] * b + a * db[j];
+      return;
+    case X_DIV:
+      *v = a / b;
+      for (int j = 0; j < m; ++j) dv[j] = (da[j] - *v * db[j]) / b;
+      return;
+    case X_POWI: {
+      double k = n->c;
+      *v = pow(a, k);
+      s = k == 0.0 ? 0.0 : k * pow(a, k - 1.0);
+      break;
+    }
+    case X_POW: {
+      double la = log(a);
+      *v = exp(b * la);
+      for (int j = 0; j < m; ++j) dv[j] = *v * (db[j] * la + b * da[j] / a);
+      return;
+    }
+    case X_EXP: *v = exp(a); s = *v; break;
+    case X_LOG: *v = log(a); s = 1.0 / a; break;
+    case X_SQRT: *v = sqrt(a); s = 0.5 / *v; break;
+    case X_SIN: *v = sin(a); s = cos(a); break;
+    case X_COS: *v = cos(a); s = -sin(a); break;
+    case X_TANH: *v = tanh(a); s = 1.0 - *v * *v; break;
+    case X_SINH: *v = sinh(a); s = cosh(a); break;
+    case X_COSH: *v = cosh(a); s = sinh(a); break;
+    case X_ASINH: *v = asinh(a); s = 1.0 / sqrt(1.0 + a * a); break;
+    case X_ATAN: *v = atan(a); s = 1.0 / (1.0 + a * a); break;
+    case X_ERF: *v = erf(a); s = (2.0 / SQRT_PI) * exp(-a * a); break;
+    case X_ERFC: *v = erfc(a); s = -(2.0 / SQRT_PI) * exp(-a * a); break;
+    case X_ABS: *v = fabs(a); s = a < 0.0 ? -1.0 : 1.0; break;
+    default: *v = NAN; return;
+  }
+  for (int j = 0; j < m; ++j) dv[j] = s * da[j];
+}
+
+/* n-point Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on
+ * P_n(t) from the usual cosine first guesses, P_n and P_n' by the three-term
+ * recurrence (Golub & Welsch's alternative is not needed at n = 20). */
+#define ORC_GLN 20
+static void gl_rule(double* t, double* w) {
+  const int n = ORC_GLN;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(PI_VAL * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    t[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+typedef struct {
+  const xprog* p;
+  const double* th;
+  int m;
+  double t[ORC_GLN], w[ORC_GLN];
+  long budget;
+  int bad;
+} xquad;
+
+/* rule on [a, b]: out[0] = int f, out[1+j] = int df/dp_j; mag[] = int |.| */
+static void xrule(xquad* Q, double a, double b, double* out, double* mag) {
+  double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+  for (int c = 0; c <= Q->m; ++c) out[c] = mag[c] = 0.0;
+  for (int i = 0; i < ORC_GLN; ++i) {
+    double v, dv[ORC_MAXNP];
+    xeval(Q->p, Q->p->root, mid + half * Q->t[i], Q->th, Q->m, &v, dv);
+    if (!isfinite(v)) Q->bad = 1;
+    double wh = Q->w[i] * half;
+    out[0] += wh * v;
+    mag[0] += wh * fabs(v);
+    for (int j = 0; j < Q->m; ++j) {
+      out[1 + j] += wh * dv[j];
+      mag[1 + j] += wh * fabs(dv[j]);
+    }
+  }
+  Q->budget--;
+}
+
+/* adaptive bisection: accept the halves once they reproduce the whole to
+ * 1e-14 of the absolute integrand in every component */
+static void xadapt(xquad* Q, double a, double b, const double* whole, int depth, double* acc) {
+  double l[1 + ORC_MAXNP], lm[1 + ORC_MAXNP], r[1 + ORC_MAXNP], rm[1 + ORC_MAXNP];
+  double mid = 0.5 * (a + b);
+  xrule(Q, a, mid, l, lm);
+  xrule(Q, mid, b, r, rm);
+  int done = depth >= 50 || Q->budget <= 0 || Q->bad;
+  for (int c = 0; c <= Q->m && !done; ++c)
+    if (fabs(l[c] + r[c] - whole[c]) > 1e-14 * (lm[c] + rm[c]) + 1e-300) done = -1;
+  if (done != -1) {
+    for (int c = 0; c <= Q->m; ++c) acc[c] += l[c] + r[c];
+    return;
+  }
+  xadapt(Q, a, mid, l, depth + 1, acc);
+  xadapt(Q, mid, b, r, depth + 1, acc);
+}
+
+/* I = int_lo^hi f, dI[j] = int df/dp_j, over 16 starting panels */
+static int xnorm(const xprog* p, const double* th, int m, double lo, double hi, double* I,
+                 double* dI) {
+  xquad Q;
+  Q.p = p;
+  Q.th = th;
+  Q.m = m;
+  Q.budget = 200000;
+  Q.bad = 0;
+  gl_rule(Q.t, Q.w);
+  double acc[1 + ORC_MAXNP] = {0};
+  for (int k = 0; k < 16; ++k) {
+    double a = lo + (hi - lo) * k / 16.0, b = k == 15 ? hi : lo + (hi - lo) * (k + 1) / 16.0;
+    double whole[1 + ORC_MAXNP], mag[1 + ORC_MAXNP];
+    xrule(&Q, a, b, whole, mag);
+    xadapt(&Q, a, b, whole, 0, acc);
+  }
+  *I = acc[0];
+  for (int j = 0; j < m; ++j) dI[j] = acc[1 + j];
+  if (Q.bad || !isfinite(*I) || !(*I > 0.0)) return ORC_EDOMAIN;
+  return ORC_OK;
+}
+
+int orc_expr_check(const char* text, int npar) {
+  xprog* p = (xprog*)malloc(sizeof(xprog));
+  if (!p) return ORC_EINVAL;
+  int rc = xparse(text, npar, p);
+  free(p);
+  return rc;
+}
+
+int orc_expr_logf(const char* text, const double* theta, int ntheta, double x, double* logf,
+                  double* dlogf) {
+  xprog* p = (xprog*)malloc(sizeof(xprog));
+  if (!p) return ORC_EINVAL;
+  int rc = xparse(text, ntheta, p);
+  if (rc == ORC_OK) {
+    double v, dv[ORC_MAXNP];
+    xeval(p, p->root, x, theta, ntheta, &v, dv);
+    *logf = v > 0.0 ? log(v) : (v == 0.0 ? -INFINITY : NAN);
+    for (int j = 0; j < ntheta; ++j) dlogf[j] = v > 0.0 ? dv[j] / v : 0.0;
+  }
+  free(p);
+  return rc;
+}
+
+int orc_expr_norm(const char* text, const double* theta, int ntheta, double lo, double hi,
+                  double* I, double* dI) {
+  if (!(hi > lo)) return ORC_EINVAL;
+  xprog* p = (xprog*)malloc(sizeof(xprog));
+  if (!p) return ORC_EINVAL;
+  int rc = xparse(text, ntheta, p);
+  if (rc == ORC_OK) rc = xnorm(p, theta, ntheta, lo, hi, I, dI);
+  free(p);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* leaves: unnormalised value f and d log f / d theta_j                */
 /* ------------------------------------------------------------------ */
 
 /* Returns f(x) (may be 0, or negative for a Chebychev polynomial) and fills
  * dlogf[j] = d log f / d theta_j where f > 0. */
 static int leaf_value(int type, const double* th, int nth, double lo, double hi,
-                      double x, double* f_out, double* dlogf) {
+                      double x, const xprog* xp, double* f_out, double* dlogf) {
   for (int j = 0; j < nth; ++j) dlogf[j] = 0.0;
   switch (type) {
+    case ORC_EXPR: {
+      if (!xp) return ORC_EINVAL;
+      double dv[ORC_MAXNP];
+      xeval(xp, xp->root, x, th, nth, f_out, dv);
+      if (*f_out > 0.0)
+        for (int j = 0; j < nth; ++j) dlogf[j] = dv[j] / *f_out;
+      return ORC_OK;
+    }
     case ORC_GAUSS: {
       if (nth != 2) return ORC_EINVAL;
       double mu = th[0], sigma = th[1];
@@ -230,10 +709,13 @@ static double argus_G(double q, double tau, double c) {
 }
 
 static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
-                     double* I_out, double* dI) {
+                     const xprog* xp, double* I_out, double* dI) {
   for (int j = 0; j < nth; ++j) dI[j] = 0.0;
   if (!(hi > lo)) return ORC_EINVAL;
   switch (type) {
+    case ORC_EXPR:
+      if (!xp) return ORC_EINVAL;
+      return xnorm(xp, th, nth, lo, hi, I_out, dI);
     case ORC_GAUSS: {
       if (nth != 2) return ORC_EINVAL;
       double mu = th[0], sigma = th[1];
@@ -383,7 +865,7 @@ static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
 int orc_leaf_logf(int type, const double* theta, int ntheta, double lo,
                   double hi, double x, double* logf, double* dlogf) {
   double f;
-  int rc = leaf_value(type, theta, ntheta, lo, hi, x, &f, dlogf);
+  int rc = leaf_value(type, theta, ntheta, lo, hi, x, NULL, &f, dlogf);
   if (rc) return rc;
   *logf = f > 0.0 ? log(f) : (f == 0.0 ? -INFINITY : NAN);
   return ORC_OK;
@@ -391,18 +873,23 @@ int orc_leaf_logf(int type, const double* theta, int ntheta, double lo,
 
 int orc_leaf_norm(int type, const double* theta, int ntheta, double lo,
                   double hi, double* I, double* dI) {
-  return leaf_norm(type, theta, ntheta, lo, hi, I, dI);
+  return leaf_norm(type, theta, ntheta, lo, hi, NULL, I, dI);
 }
 
 /* ------------------------------------------------------------------ */
 /* graph walk                                                          */
 /* ------------------------------------------------------------------ */
 
-static int is_leaf(int t) { return (t >= ORC_GAUSS && t <= ORC_ARGUS) || t == ORC_JOHNSON; }
+static int is_leaf(int t) {
+  return (t >= ORC_GAUSS && t <= ORC_ARGUS) || t == ORC_JOHNSON || t == ORC_EXPR;
+}
 
+#define ORC_MAXXL 4 /* expression leaves per model */
 typedef struct {
   double I[ORC_MAXNODE];
   double dlogI[ORC_MAXNODE][ORC_MAXNP];
+  int xslot[ORC_MAXNODE]; /* parsed expression of node i, or -1 */
+  xprog xp[ORC_MAXXL];
 } leaf_cache;
 
 /* bit mask of the observables a subtree depends on; -1 on a malformed graph */
@@ -430,7 +917,8 @@ static int validate(const orc_model* m) {
   if (m->n_par < 0 || m->n_par > ORC_MAXPAR) return ORC_EINVAL;
   for (int i = 0; i < m->n_nodes; ++i) {
     int t = m->type[i];
-    if (t < ORC_GAUSS || t > ORC_JOHNSON) return ORC_EINVAL;
+    if (t < ORC_GAUSS || t > ORC_EXPR) return ORC_EINVAL;
+    if (t == ORC_EXPR && !(m->expr && m->expr[i])) return ORC_EINVAL;
     if (m->npar[i] < 0 || m->npar[i] > ORC_MAXNP) return ORC_EINVAL;
     for (int j = 0; j < m->npar[i]; ++j) {
       int p = m->par[i * ORC_MAXNP + j];
@@ -454,7 +942,14 @@ static int validate(const orc_model* m) {
 }
 
 static int fill_cache(const orc_model* m, const double* params, leaf_cache* lc) {
-  int rc_any = ORC_OK;
+  int rc_any = ORC_OK, nx = 0;
+  for (int i = 0; i < m->n_nodes; ++i) {
+    lc->xslot[i] = -1;
+    if (m->type[i] != ORC_EXPR) continue;
+    if (nx == ORC_MAXXL) return ORC_EUNSUPPORTED;
+    if (xparse(m->expr[i], m->npar[i], &lc->xp[nx])) return ORC_EINVAL;
+    lc->xslot[i] = nx++;
+  }
   for (int i = 0; i < m->n_nodes; ++i) {
     if (!is_leaf(m->type[i])) continue;
     double th[ORC_MAXNP], dI[ORC_MAXNP];
@@ -462,7 +957,8 @@ static int fill_cache(const orc_model* m, const double* params, leaf_cache* lc) 
     for (int j = 0; j < np; ++j) th[j] = params[m->par[i * ORC_MAXNP + j]];
     int o = m->obs[i];
     double I;
-    int rc = leaf_norm(m->type[i], th, np, m->obs_lo[o], m->obs_hi[o], &I, dI);
+    const xprog* xp = lc->xslot[i] >= 0 ? &lc->xp[lc->xslot[i]] : NULL;
+    int rc = leaf_norm(m->type[i], th, np, m->obs_lo[o], m->obs_hi[o], xp, &I, dI);
     if (rc == ORC_EINVAL || rc == ORC_EUNSUPPORTED) return rc;
     if (rc == ORC_EDOMAIN || !(I > 0.0) || !isfinite(I)) rc_any = ORC_EDOMAIN;
     lc->I[i] = I;
@@ -483,7 +979,8 @@ static void eval_node(const orc_model* m, int i, const double* params,
     double th[ORC_MAXNP] = {0}, dlogf[ORC_MAXNP], f;
     int np = m->npar[i], o = m->obs[i];
     for (int j = 0; j < np; ++j) th[j] = params[m->par[i * ORC_MAXNP + j]];
-    leaf_value(t, th, np, m->obs_lo[o], m->obs_hi[o], xrow[o], &f, dlogf);
+    leaf_value(t, th, np, m->obs_lo[o], m->obs_hi[o], xrow[o],
+               lc->xslot[i] >= 0 ? &lc->xp[lc->xslot[i]] : NULL, &f, dlogf);
     double val = f / lc->I[i];
     *v = val;
     if (dv && f != 0.0)
@@ -926,6 +1423,8 @@ int orc_generate(const orc_model* m, const double* params_matrix, int32_t toys,
   for (int c = 0; c < nc; ++c) {
     nlv[c] = comp_leaves(m, comps[c], lv[c]);
     if (nlv[c] < 0) return ORC_EUNSUPPORTED;
+    for (int k = 0; k < nlv[c]; ++k)
+      if (m->type[lv[c][k]] == ORC_EXPR) return ORC_EUNSUPPORTED; /* no sampler */
     int64_t cover = 0;
     for (int k = 0; k < nlv[c]; ++k) cover |= (int64_t)1 << m->obs[lv[c][k]];
     if (cover != ((int64_t)1 << m->n_obs) - 1) return ORC_EUNSUPPORTED;

@@ -39,7 +39,8 @@ enum {
   ORC_ADD_FRAC = 6, /* K children, K-1 fraction params         */
   ORC_ADD_EXT = 7,  /* K children, K yield params; root only   */
   ORC_PROD = 8,     /* K children on disjoint observables      */
-  ORC_JOHNSON = 9   /* params (mu, lambda, gamma, delta): Johnson's SU */
+  ORC_JOHNSON = 9,  /* params (mu, lambda, gamma, delta): Johnson's SU */
+  ORC_EXPR = 10     /* params p0 .. p(m-1) of a formula f(x; p) given as text */
 };
 
 #define ORC_MAXCH 8   /* children per node   */
@@ -67,6 +68,8 @@ typedef struct {
   const int32_t* par;
   const double* obs_lo;
   const double* obs_hi;
+  const char* const* expr; /* [n_nodes]: formula of each ORC_EXPR node (others
+                              ignored); may be NULL without ORC_EXPR nodes */
 } orc_model;
 
 /* Unnormalised log-density of one leaf and its derivatives with respect to the
@@ -77,6 +80,20 @@ int orc_leaf_logf(int type, const double* theta, int ntheta, double lo,
 
 /* Normalisation integral I = int_lo^hi f(x) dx of one leaf and dI/dtheta_j. */
 int orc_leaf_norm(int type, const double* theta, int ntheta, double lo,
+                  double hi, double* I, double* dI);
+
+/* Formula leaves (ORC_EXPR).  Grammar: sums, products, quotients, unary
+ * minus, '^' (right-associative), numbers, the observable x, parameters
+ * p0 .. p(ntheta-1), and exp log sqrt sin cos tanh sinh cosh asinh atan erf
+ * erfc abs pow(a, b).  An integer literal exponent is a repeated product; any
+ * other a^b is exp(b log a).  check: ORC_OK or ORC_EINVAL.  logf: log f(x) and
+ * d log f/dp_j.  norm: I = int_lo^hi f and dI/dp_j by adaptive Gauss-Legendre
+ * quadrature (20 points, bisection until both halves reproduce their parent to
+ * 1e-14 of the integral of |.|); ORC_EDOMAIN when f is not finite or I <= 0. */
+int orc_expr_check(const char* text, int npar);
+int orc_expr_logf(const char* text, const double* theta, int ntheta, double x,
+                  double* logf, double* dlogf);
+int orc_expr_norm(const char* text, const double* theta, int ntheta, double lo,
                   double hi, double* I, double* dI);
 
 /* NLL = -sum_i log P(x_i)  (+ sum_k nu_k for an extended root) and, if grad is

@@ -247,12 +247,12 @@ struct rf_graph {
   int last_launches = 0;
   // per-graph specialised kernels (NVRTC), by events per thread (index 0 or
   // 1 of the precision's two options) and, for the fused kernel, register
-  // budget (min_blocks 2 or 3); compiled on first need
+  // budget (min_blocks 2..4); compiled on first need
   bool jit = false;
-  cudaKernel_t jk_fused[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaKernel_t jk_fused[2][3] = {};
   cudaKernel_t jk_toys[2] = {nullptr, nullptr};
   cudaKernel_t jk_logp = nullptr;
-  int jk_regs[2][2] = {{0, 0}, {0, 0}};
+  int jk_regs[2][3] = {};
 };
 
 // index of an events-per-thread option within its precision's pair
@@ -262,7 +262,7 @@ static int ept_index(int eval, int coldt, int ept) {
   return 0;
 }
 
-static bool min_blocks_ok(int mb) { return mb == 2 || mb == 3; }
+static bool min_blocks_ok(int mb) { return mb >= 2 && mb <= 4; }
 
 static cudaKernel_t jit_fused(rf_graph* g, int ept, int min_blocks, std::string* err) {
   const int i = ept_index(g->eval, g->coldt, ept), m = min_blocks - 2;
@@ -284,6 +284,15 @@ static int toy_ept(const rf_graph* g) {
   }
   return 8;  // measured on C4: 8 beats 16 (registers, occupancy) in FP32 and 4 in FP64
 }
+// register budget of the segment kernel: 0 = the compiler's choice, else
+// launch bounds for 3 or 4 resident blocks of 256 threads (tuning)
+static int toy_min_blocks() {
+  if (const char* v = getenv("RF_TOY_MINBLOCKS")) {
+    const int m = atoi(v);
+    if (m == 3 || m == 4) return m;
+  }
+  return 0;
+}
 static RfLaunchCfg toy_cfg(const rf_graph* g) {
   RfLaunchCfg c = g->cfg;
   c.ept = toy_ept(g);
@@ -294,8 +303,8 @@ static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
   int i = ept_index(g->eval, toy_coldt(g), ept);
   if (!g->jk_toys[i]) {
     cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g),
-                                   g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept, 0, nullptr,
-                                   err);
+                                   g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept,
+                                   toy_min_blocks(), nullptr, err);
     if (k && g->toy_bulk) {  // its stage ring may use more than 48 KB of shared memory
       int optin = 0;
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
@@ -451,7 +460,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
     const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
     const int ke = toy ? 8 : ept;
-    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, 3, &err))
+    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, toy ? 0 : 3, &err))
       return fail(RF_ECUDA, err);
   }
   return RF_OK;
@@ -831,7 +840,7 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
     return fail(RF_EINVAL, "events per thread not available for this precision / dtype");
   if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
     return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
-  if (!min_blocks_ok(cfg->min_blocks)) return fail(RF_EINVAL, "min_blocks must be 2 or 3");
+  if (!min_blocks_ok(cfg->min_blocks)) return fail(RF_EINVAL, "min_blocks must be 2, 3 or 4");
   if (g->jit) {
     std::string err;
     if (!jit_fused(g, cfg->ept, cfg->min_blocks, &err))

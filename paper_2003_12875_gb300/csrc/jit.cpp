@@ -131,7 +131,10 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
       << R << ", " << C << ", " << ept << ">(P, ev, n, head, vec, params, W, nll, grad);\n}\n";
   } else if (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) {
     o << kRfJitToysPrelude << "\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(256) rf_toys_jit(const RfProgram P, const "
+    // min_blocks > 0: launch bounds for that many resident blocks of 256
+    const std::string tlb = min_blocks > 0 ? "__launch_bounds__(256, " + std::to_string(min_blocks) + ")"
+                                           : std::string("__launch_bounds__(256)");
+    o << "extern \"C\" __global__ void " << tlb << " rf_toys_jit(const RfProgram P, const "
       << C << "* __restrict__ ev, int64_t stride, int vec, const int64_t* __restrict__ offsets, "
               "int32_t toys, int stages, RfWork W) {\n  rf::"
       << (kind == RF_JIT_TOYS ? "toy_segment_body_reg" : "toy_segment_body") << "<RfModel, "

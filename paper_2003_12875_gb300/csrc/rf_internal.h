@@ -105,7 +105,7 @@ struct RfLaunchCfg {
   int block;
   int ept;
   int blocks_per_sm;
-  int min_blocks;  // register budget of the specialised fused kernel (2 or 3)
+  int min_blocks;  // register budget of the specialised fused kernel (2..4)
 };
 
 #ifndef __CUDACC_RTC__
@@ -170,8 +170,8 @@ void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int ele
 // rings (RF_JIT_TOYS_BULK)
 enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2, RF_JIT_TOYS_BULK = 3 };
 typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
-// min_blocks: the fused kernel's launch bounds (blocks of 256 threads per SM);
-// the other kinds ignore it
+// min_blocks: launch bounds of the fused and toy kernels (resident blocks of 256
+// threads per SM; 0 for the toy kernel: none); the log P kernel ignores it
 std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept,
                           int min_blocks);
 uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept, int min_blocks);

@@ -143,7 +143,7 @@ def test_every_launch_configuration(rf, jit):
         for block in (64, 128, 256):
             for ept in epts:
                 for bps in (1, 2, 3, 4, 6, 8):
-                    for mb in ((2, 3) if jit else (2,)):
+                    for mb in ((2, 3, 4) if jit else (2,)):
                         G.set_launch(block=block, ept=ept, blocks_per_sm=bps, min_blocks=mb)
                         nll, grad = G.nll(ev, pd)
                         cfg = (block, ept, bps, mb)
@@ -158,7 +158,7 @@ def test_launch_defaults_and_invalid_register_budget(rf):
     G = rf.Graph(w["spec"], "f64", "fp64")
     assert G.get_launch()["min_blocks"] == 2
     with pytest.raises(rf.RFError):
-        G.set_launch(min_blocks=4)
+        G.set_launch(min_blocks=5)
     assert G.get_launch()["min_blocks"] == 2
 
 
