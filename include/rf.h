@@ -23,6 +23,30 @@
  *   RF_JOHNSON (mu, lambda, gamma, delta)  Johnson's SU (Sec. 3): with
  *             z = (x-mu)/lambda, w = gamma + delta asinh z standard normal:
  *             delta / (lambda sqrt(2 pi (1+z^2))) exp(-w^2/2)
+ *   RF_FORMULA (p0 .. p(m-1)), m <= 4   a density written as text in the
+ *             observable x and the node's parameters p0..p3 -- the formula
+ *             PDFs of Sec. 4 (RooGenericPdf, compiled just in time).  Grammar:
+ *             + - * / and unary minus, '^' (right-associative, binds tighter
+ *             than unary minus), decimal literals, parentheses, and exp log
+ *             sqrt sin cos tanh sinh cosh asinh atan erf erfc abs pow(a, b).
+ *             An integer literal exponent is a repeated product (any base);
+ *             any other a^b is exp(b log a).  The text is compiled (NVRTC)
+ *             into the graph's kernels with forward-mode derivatives; its
+ *             integral over the range and the integral's derivatives are
+ *             computed numerically in FP64 on every call (16-point
+ *             Gauss-Legendre on 128 equal panels: exact to rounding for
+ *             formulas whose features are wider than about 1/100 of the
+ *             range).  Under RF_EVAL_FP32 the formula runs in FP32 on the
+ *             parameters rounded to FP32 (first-order corrected, as the
+ *             built-ins) and on its literals rounded to FP32 (not corrected:
+ *             give location-like constants as fixed parameters).  The
+ *             density must be positive on the range (else NLL = +inf and
+ *             RF_STATUS_NONFINITE; a non-positive integral gives
+ *             RF_STATUS_PARAM_DOMAIN).  Graphs with formula leaves need the
+ *             specialised kernels (rf_graph_set_jit(g, 0) returns
+ *             RF_EUNSUPPORTED, as does rf_graph_compile without NVRTC) and do
+ *             not take toy studies, toy generation, the plain baseline or
+ *             rf_nll_noalloc (RF_EUNSUPPORTED).
  * Composites:
  *   RF_ADD_FRAC (K children, K-1 fractions)  P = sum_{k<K-1} f_k P_k + (1-sum f) P_{K-1}
  *   RF_ADD_EXT  (K children, K yields; root) P = sum nu_k P_k, NLL += sum nu_k
@@ -79,7 +103,8 @@ enum {
   RF_ADD_FRAC = 6,
   RF_ADD_EXT = 7,
   RF_PROD = 8,
-  RF_JOHNSON = 9
+  RF_JOHNSON = 9,
+  RF_FORMULA = 10
 };
 
 enum { RF_F32 = 0, RF_F64 = 1 };           /* column dtype              */
@@ -103,12 +128,15 @@ enum {
 #define RF_MAX_PARAMS 64
 
 typedef struct {
-  int32_t type;     /* RF_GAUSS .. RF_JOHNSON                                */
+  int32_t type;     /* RF_GAUSS .. RF_FORMULA                                */
   int32_t obs;      /* leaves: observable (column) index; composites: -1     */
   int32_t n_children;
   int32_t children[RF_MAX_CHILDREN]; /* node indices                        */
   int32_t n_params;
   int32_t params[RF_MAX_NODE_PARAMS]; /* indices into the parameter vector  */
+  const char* formula; /* RF_FORMULA: the density's text (NUL-terminated, at
+                          most 4096 characters; read during validate/compile
+                          only); ignored for other types                     */
 } rf_node_desc;
 
 typedef struct {

@@ -15,7 +15,7 @@ A model is the plain-data ``spec`` dict used throughout the repository::
 
 Leaf parameter order: gauss (mu, sigma); exp (lambda); cheb (c_1..c_m);
 cb (m0, sigma, alpha, n); argus (m0, c, p); johnson (mu, lambda, gamma,
-delta); expr (p0 .. p(m-1) of the node's "expr" formula in x).
+delta); formula (p0 .. p(m-1) of the node's "formula" text in x).
 """
 from __future__ import annotations
 
@@ -32,7 +32,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5, "johnson": 9,
-         "expr": 10, "add_frac": 6, "add_ext": 7, "prod": 8}
+         "formula": 10, "add_frac": 6, "add_ext": 7, "prod": 8}
 MAXCH, MAXNP, MAXPAR = 8, 8, 64
 OK, EINVAL, EUNSUPPORTED, EDOMAIN = 0, 1, 2, 3
 
@@ -129,7 +129,7 @@ class Model:
             ps = nd.get("params", [])
             self.npar[i] = len(ps)
             self.par[i * MAXNP:i * MAXNP + len(ps)] = ps
-        self.texts = [nd.get("expr", "").encode() for nd in nodes]
+        self.texts = [nd.get("formula", "").encode() for nd in nodes]
         self.expr = (C.c_char_p * N)(*self.texts)
         rng = np.asarray(spec["obs"], np.float64).reshape(-1, 2)
         self.lo = np.ascontiguousarray(rng[:, 0])

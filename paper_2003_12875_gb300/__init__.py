@@ -30,7 +30,7 @@ from . import build as _build
 __all__ = ["Graph", "RFNll", "RFError", "load", "microbench", "TYPES"]
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5,
-         "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9}
+         "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9, "formula": 10}
 _STATUS = {0: "RF_OK", 1: "RF_EINVAL", 2: "RF_EUNSUPPORTED", 3: "RF_EALIGN",
            4: "RF_ECUDA", 5: "RF_ENOMEM"}
 MAX_CHILDREN, MAX_NODE_PARAMS = 8, 8
@@ -46,7 +46,7 @@ class RFError(RuntimeError):
 class _Node(C.Structure):
     _fields_ = [("type", C.c_int32), ("obs", C.c_int32), ("n_children", C.c_int32),
                 ("children", C.c_int32 * MAX_CHILDREN), ("n_params", C.c_int32),
-                ("params", C.c_int32 * MAX_NODE_PARAMS)]
+                ("params", C.c_int32 * MAX_NODE_PARAMS), ("formula", C.c_char_p)]
 
 
 class _Desc(C.Structure):
@@ -148,8 +148,10 @@ def make_desc(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64
     tuple)."""
     nodes = spec["nodes"]
     arr = (_Node * len(nodes))()
+    texts = [nd["formula"].encode() if "formula" in nd else None for nd in nodes]
     for i, nd in enumerate(nodes):
         arr[i].type = TYPES[nd["type"]]
+        arr[i].formula = texts[i]
         arr[i].obs = nd.get("obs", -1)
         ch = nd.get("children", [])
         arr[i].n_children = len(ch)
@@ -167,7 +169,7 @@ def make_desc(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64
     fx = (C.c_uint8 * max(npar, 1))(*[1 if (fixed and fixed[j]) else 0 for j in range(npar)])
     d = _Desc(len(nodes), arr, spec.get("root", len(nodes) - 1), len(rng), lo, hi, npar,
               fx, 0 if column_dtype == "f32" else 1, 0 if eval_precision == "fp32" else 1)
-    return d, (arr, lo, hi, fx)
+    return d, (arr, lo, hi, fx, texts)
 
 
 def validate(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64") -> int:

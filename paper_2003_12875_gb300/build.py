@@ -55,6 +55,7 @@ def _stale() -> bool:
 # first list; toy kernels also get the second
 PRELUDE_HEADERS = ["rf_internal.h", "rf_device.cuh", "rf_kernels.cuh"]
 TOY_PRELUDE_HEADERS = ["rf_toys.cuh"]
+FORMULA_PRELUDE_HEADERS = ["rf_expr.cuh"]
 
 
 def _raw(name: str, headers: list[str]) -> str:
@@ -74,7 +75,8 @@ def _raw(name: str, headers: list[str]) -> str:
 def write_prelude() -> str:
     """Embed the device headers as C++ raw strings (rf_jit_prelude.inc)."""
     out = os.path.join(BUILD, "rf_jit_prelude.inc")
-    text = _raw("kRfJitPrelude", PRELUDE_HEADERS) + _raw("kRfJitToysPrelude", TOY_PRELUDE_HEADERS)
+    text = (_raw("kRfJitPrelude", PRELUDE_HEADERS) + _raw("kRfJitToysPrelude", TOY_PRELUDE_HEADERS)
+            + _raw("kRfJitFormulaPrelude", FORMULA_PRELUDE_HEADERS))
     if not os.path.exists(out) or open(out).read() != text:
         with open(out, "w") as f:
             f.write(text)
@@ -113,7 +115,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = _cuda_lib_dir(nvcc)
     link = [nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs,
-            "-L", libdir, "-lnvrtc", "-Xlinker", f"-rpath,{libdir}"]
+            "-L", libdir, "-lnvrtc", "-lpthread", "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -36,7 +36,9 @@ rf_status cuda_fail(cudaError_t e, const char* where) {
   return RF_ECUDA;
 }
 
-bool is_leaf(int t) { return (t >= RF_GAUSS && t <= RF_ARGUS) || t == RF_JOHNSON; }
+bool is_leaf(int t) {
+  return (t >= RF_GAUSS && t <= RF_ARGUS) || t == RF_JOHNSON || t == RF_FORMULA;
+}
 
 int leaf_nparams_ok(int t, int np) {
   switch (t) {
@@ -46,6 +48,7 @@ int leaf_nparams_ok(int t, int np) {
     case RF_CB: return np == 4;
     case RF_ARGUS: return np == 3;
     case RF_JOHNSON: return np == 4;
+    case RF_FORMULA: return np >= 0 && np <= RF_LEAF_MAXP;
   }
   return 0;
 }
@@ -70,7 +73,7 @@ rf_status validate_desc(const rf_graph_desc* d) {
       return fail(RF_EINVAL, "observable " + std::to_string(o) + " has an empty or non-finite range");
   for (int i = 0; i < d->n_nodes; ++i) {
     const rf_node_desc& n = d->nodes[i];
-    if (n.type < RF_GAUSS || n.type > RF_JOHNSON)
+    if (n.type < RF_GAUSS || n.type > RF_FORMULA)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": unknown type");
     if (n.n_params < 0 || n.n_params > RF_MAX_NODE_PARAMS)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_params");
@@ -84,6 +87,11 @@ rf_status validate_desc(const rf_graph_desc* d) {
         return fail(RF_EUNSUPPORTED, "Chebychev order above 4 is not supported on the GPU");
       if (!leaf_nparams_ok(n.type, n.n_params))
         return fail(RF_EINVAL, "node " + std::to_string(i) + ": wrong parameter count for its type");
+      if (n.type == RF_FORMULA) {
+        std::string code, err;
+        if (!rf_expr_translate(n.formula, n.n_params, &code, &err))
+          return fail(RF_EINVAL, "node " + std::to_string(i) + ": " + err);
+      }
     } else {
       if (n.n_children < 1 || n.n_children > RF_MAX_CHILDREN)
         return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_children");
@@ -109,7 +117,7 @@ struct Canon {
 
 // Map the descriptor onto the sum-of-products program (fixed-size arrays
 // only: no heap allocation on the success path).
-rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
+rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nullptr) {
   std::memset(P, 0, sizeof(*P));
   P->ext_weight = 1.0;
   const rf_node_desc& root = d->nodes[d->root];
@@ -176,6 +184,7 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P) {
           return fail(RF_EUNSUPPORTED, "PROD children must use disjoint observables");
         comp_obs |= 1ull << n.obs;
       }
+      if (leaf_node) leaf_node[k] = comp_leaf[c][li];
       RfLeafProg& L = P->leaf[k++];
       L.type = n.type;  // RF_<leaf> == RFL_<leaf>
       L.comp = c;
@@ -252,6 +261,13 @@ struct rf_graph {
   cudaKernel_t jk_fused[2][3] = {};
   cudaKernel_t jk_toys[2] = {nullptr, nullptr};
   cudaKernel_t jk_logp = nullptr;
+  // formula leaves: translated code, the normalisation kernel and its
+  // workspace (log I and derivatives, block partials, tickets)
+  int n_formula = 0;
+  RfFormulaCode fcode;
+  cudaKernel_t jk_norm = nullptr;
+  double* formula_buf = nullptr;
+  unsigned int* formula_ticket = nullptr;
   int jk_regs[2][3] = {};
 };
 
@@ -264,11 +280,15 @@ static int ept_index(int eval, int coldt, int ept) {
 
 static bool min_blocks_ok(int mb) { return mb >= 2 && mb <= 4; }
 
+static const RfFormulaCode* fcode(const rf_graph* g) {
+  return g->n_formula ? &g->fcode : nullptr;
+}
+
 static cudaKernel_t jit_fused(rf_graph* g, int ept, int min_blocks, std::string* err) {
   const int i = ept_index(g->eval, g->coldt, ept), m = min_blocks - 2;
   if (!g->jk_fused[i][m])
-    g->jk_fused[i][m] = rf_jit_kernel(g->prog, g->eval, g->coldt, RF_JIT_FUSED, ept, min_blocks,
-                                      &g->jk_regs[i][m], err);
+    g->jk_fused[i][m] = rf_jit_kernel(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED, ept,
+                                      min_blocks, &g->jk_regs[i][m], err);
   return g->jk_fused[i][m];
 }
 
@@ -302,7 +322,7 @@ static RfLaunchCfg toy_cfg(const rf_graph* g) {
 static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
   int i = ept_index(g->eval, toy_coldt(g), ept);
   if (!g->jk_toys[i]) {
-    cudaKernel_t k = rf_jit_kernel(g->prog, g->eval, toy_coldt(g),
+    cudaKernel_t k = rf_jit_kernel(g->prog, fcode(g), g->eval, toy_coldt(g),
                                    g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, ept,
                                    toy_min_blocks(), nullptr, err);
     if (k && g->toy_bulk) {  // its stage ring may use more than 48 KB of shared memory
@@ -332,6 +352,8 @@ static void free_work(rf_graph* g) {
   cudaFree(g->plain_partials);
   if (g->fit_stream) cudaStreamDestroy(g->fit_stream);
   cudaFree(g->pro_buf);
+  cudaFree(g->formula_buf);
+  cudaFree(g->formula_ticket);
 }
 
 // For other translation units of the library (noalloc.cu): validation plus
@@ -339,7 +361,12 @@ static void free_work(rf_graph* g) {
 rf_status rf_canonical_program(const rf_graph_desc* desc, RfProgram* P) {
   rf_status s = validate_desc(desc);
   if (s) return s;
-  return canonicalise(desc, P);
+  s = canonicalise(desc, P);
+  if (s) return s;
+  for (int k = 0; k < P->n_leaves; ++k)
+    if (P->leaf[k].type == RFL_FORMULA)
+      return fail(RF_EUNSUPPORTED, "formula leaves need rf_graph_compile (specialised kernels)");
+  return RF_OK;
 }
 
 void rf_set_last_error(const char* msg) { g_err = msg; }
@@ -363,10 +390,18 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   rf_status s = validate_desc(desc);
   if (s) return s;
   rf_graph* g = new rf_graph();
-  s = canonicalise(desc, &g->prog);
+  int leaf_node[RF_MAXL] = {0, 0, 0, 0};
+  s = canonicalise(desc, &g->prog, leaf_node);
   if (s) {
     delete g;
     return s;
+  }
+  for (int k = 0; k < g->prog.n_leaves; ++k) {
+    if (g->prog.leaf[k].type != RFL_FORMULA) continue;
+    const rf_node_desc& n = desc->nodes[leaf_node[k]];
+    std::string err;
+    rf_expr_translate(n.formula, n.n_params, &g->fcode.leaf[k], &err);  // validated above
+    ++g->n_formula;
   }
   g->eval = desc->eval_precision;
   g->coldt = desc->column_dtype;
@@ -401,14 +436,41 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
     return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
   }
   g->work.consts = g->pro_buf;
+  if (g->n_formula) {
+    // [RF_MAXL * NV] log I and derivatives, then [RF_MAXL * blocks * NV]
+    // partials; tickets
+    const size_t nv = RF_FORMULA_NV;
+    e = cudaMalloc(&g->formula_buf, sizeof(double) * nv * RF_MAXL * (1 + RF_FORMULA_BLOCKS));
+    if (e == cudaSuccess) e = cudaMalloc(&g->formula_ticket, sizeof(unsigned int) * RF_MAXL);
+    if (e == cudaSuccess) e = cudaMemset(g->formula_ticket, 0, sizeof(unsigned int) * RF_MAXL);
+    if (e != cudaSuccess) {
+      free_work(g);
+      delete g;
+      return fail(RF_ENOMEM, std::string("rf_graph_compile: ") + cudaGetErrorString(e));
+    }
+    g->prog.formula_norm = g->formula_buf;
+  }
   // Specialise the fused kernel for this graph unless RF_JIT=0.  If that is
   // not possible the graph keeps the precompiled generic kernels (same device
   // code, run-time dispatch); rf_graph_uses_jit reports which one runs.
+  // Formula leaves exist only in specialised kernels: without them the
+  // compile fails.
   const char* env = getenv("RF_JIT");
-  if (!(env && env[0] == '0')) {
+  if (!(env && env[0] == '0') || g->n_formula) {
     g->jit = true;
     std::string err;
-    if (!jit_fused(g, g->cfg.ept, g->cfg.min_blocks, &err)) {
+    bool ok = jit_fused(g, g->cfg.ept, g->cfg.min_blocks, &err) != nullptr;
+    if (ok && g->n_formula) {
+      g->jk_norm = rf_jit_kernel(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_NORM, 0, 0, nullptr,
+                                 &err);
+      ok = g->jk_norm != nullptr;
+    }
+    if (!ok && g->n_formula) {
+      free_work(g);
+      delete g;
+      return fail(RF_ECUDA, "formula leaves need the specialised kernels: " + err);
+    }
+    if (!ok) {
       g->jit = false;
       g_err = "JIT unavailable, generic kernels in use: " + err;
     }
@@ -420,6 +482,8 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
 rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
   if (!g) return fail(RF_EINVAL, "graph is NULL");
   if (!enable) {
+    if (g->n_formula)
+      return fail(RF_EUNSUPPORTED, "formula leaves run only in the specialised kernels");
     g->jit = false;
     return RF_OK;
   }
@@ -437,7 +501,8 @@ int32_t rf_graph_uses_jit(const rf_graph* g) { return g && g->jit ? 1 : 0; }
 
 uint64_t rf_graph_kernel_hash(const rf_graph* g) {
   if (!g || !g->jit) return 0;
-  return rf_jit_hash(g->prog, g->eval, g->coldt, RF_JIT_FUSED, g->cfg.ept, g->cfg.min_blocks);
+  return rf_jit_hash(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED, g->cfg.ept,
+                     g->cfg.min_blocks);
 }
 
 int32_t rf_graph_kernel_regs(const rf_graph* g) {
@@ -450,17 +515,28 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
   rf_status s = validate_desc(desc);
   if (s) return s;
   RfProgram P;
-  s = canonicalise(desc, &P);
+  int leaf_node[RF_MAXL] = {0, 0, 0, 0};
+  s = canonicalise(desc, &P, leaf_node);
   if (s) return s;
+  RfFormulaCode fc;
+  int nf = 0;
   std::string err;
+  for (int k = 0; k < P.n_leaves; ++k)
+    if (P.leaf[k].type == RFL_FORMULA) {
+      const rf_node_desc& n = desc->nodes[leaf_node[k]];
+      rf_expr_translate(n.formula, n.n_params, &fc.leaf[k], &err);
+      ++nf;
+    }
+  const RfFormulaCode* fcp = nf ? &fc : nullptr;
   const int ept = desc->eval_precision == RF_EVAL_FP32 ? 4 : (desc->column_dtype == RF_F64 ? 2 : 4);
-  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_TOYS_BULK, RF_JIT_LOGP}) {
+  for (int kind : {RF_JIT_FUSED, RF_JIT_TOYS, RF_JIT_TOYS_BULK, RF_JIT_LOGP, RF_JIT_NORM}) {
+    if (nf ? (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) : kind == RF_JIT_NORM) continue;
     // FP32-evaluated toy kernels read FP32 columns (converted at bind time)
     const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
     const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
     const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
     const int ke = toy ? 8 : ept;
-    if (!rf_jit_compile_only(P, desc->eval_precision, cd, kind, ke, toy ? 0 : 3, &err))
+    if (!rf_jit_compile_only(P, fcp, desc->eval_precision, cd, kind, ke, toy ? 0 : 3, &err))
       return fail(RF_ECUDA, err);
   }
   return RF_OK;
@@ -487,7 +563,12 @@ static rf_status check_events(const rf_graph* g, const void* events, int64_t n) 
 static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, int64_t n,
                           const double* params, double* nll, double* grad, cudaStream_t st) {
   const RfProgram& P = g->prog;
-  int pe = rf_launch_prologue(P, g->eval, params, g->work, st);
+  if (g->n_formula) {  // their integrals first; the prologue then runs after them
+    int ne = rf_jit_launch_norm(g->jk_norm, P, g->n_formula, params,
+                                g->formula_buf + RF_FORMULA_NV * RF_MAXL, g->formula_ticket, st);
+    if (ne) return ne;
+  }
+  int pe = rf_launch_prologue(P, g->eval, params, g->work, g->n_formula == 0, st);
   if (pe) return pe;
   if (g->jit) {
     cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)][cfg.min_blocks - 2];
@@ -513,7 +594,7 @@ rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events, const double
   if (!nll) return fail(RF_EINVAL, "nll is NULL");
   int e = fused_dispatch(g, g->cfg, events, n_events, params, nll, grad,
                          reinterpret_cast<cudaStream_t>(stream));
-  g->last_launches = 2;
+  g->last_launches = g->n_formula ? 3 : 2;
   if (e) return cuda_fail((cudaError_t)e, "rf_nll launch");
   return RF_OK;
 }
@@ -564,7 +645,7 @@ rf_status rf_nll_host(rf_graph* g, const void* host_events, int64_t n_events,
     e = cudaMemcpyAsync(dp, host_params, sizeof(double) * np, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "rf_nll_host H2D");
   int le = fused_dispatch(g, g->cfg, ev_dev, n_events, dp, dout, host_grad ? dout + 1 : nullptr, st);
-  g->last_launches = 2;
+  g->last_launches = g->n_formula ? 3 : 2;
   if (le) return cuda_fail((cudaError_t)le, "rf_nll_host launch");
   e = cudaMemcpyAsync(host_nll, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && host_grad && np)
@@ -587,8 +668,15 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events, const doubl
   int e;
   if (g->jit && !g->jk_logp) {
     std::string err;  // first call compiles the kernel (host-synchronous)
-    g->jk_logp = rf_jit_kernel(P, g->eval, g->coldt, RF_JIT_LOGP, 0, 0, nullptr, &err);
+    g->jk_logp = rf_jit_kernel(P, fcode(g), g->eval, g->coldt, RF_JIT_LOGP, 0, 0, nullptr, &err);
     if (!g->jk_logp) return fail(RF_ECUDA, "JIT log P kernel: " + err);
+  }
+  int launches = 1;
+  if (g->n_formula) {
+    e = rf_jit_launch_norm(g->jk_norm, P, g->n_formula, params,
+                           g->formula_buf + RF_FORMULA_NV * RF_MAXL, g->formula_ticket, st);
+    if (e) return cuda_fail((cudaError_t)e, "rf_logp normalisation launch");
+    ++launches;
   }
   if (g->jit)
     e = rf_jit_launch_logp(g->jk_logp, P, events, n_events, params, logp, st);
@@ -598,7 +686,7 @@ rf_status rf_logp(rf_graph* g, const void* events, int64_t n_events, const doubl
   else
     e = g->coldt == RF_F32 ? rf_logp_f64_c32(P, events, n_events, params, logp, st)
                            : rf_logp_f64_c64(P, events, n_events, params, logp, st);
-  g->last_launches = 1;
+  g->last_launches = launches;
   if (e) return cuda_fail((cudaError_t)e, "rf_logp launch");
   return RF_OK;
 }
@@ -609,6 +697,8 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   rf_status s = check_events(g, events, n_events);
   if (s) return s;
   if (max_toys < 1) return fail(RF_EINVAL, "max_toys must be >= 1");
+  if (g->n_formula)
+    return fail(RF_EUNSUPPORTED, "toy studies do not take formula leaves (per-toy quadrature)");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "rf_graph_bind_events sync");
   cudaFree(g->work.toy_consts);
@@ -771,6 +861,7 @@ rf_status rf_generate_toys(rf_graph* g, const double* params_matrix, const int64
   if (toys < 1 || !params_matrix || !comp_counts || !offsets || n_events < 0 ||
       (n_events > 0 && !events))
     return fail(RF_EINVAL, "NULL or negative argument");
+  if (g->n_formula) return fail(RF_EUNSUPPORTED, "formula leaves have no sampler");
   const RfProgram& P = g->prog;
   // every component must draw every observable
   if (P.n_cols != g->n_obs) return fail(RF_EUNSUPPORTED, "an observable no leaf reads");
@@ -793,6 +884,7 @@ rf_status rf_generate_toys(rf_graph* g, const double* params_matrix, const int64
 rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events, const double* params,
                        double* nll, double* grad, rf_stream stream) {
   if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (g->n_formula) return fail(RF_EUNSUPPORTED, "the node-by-node baseline has no formula leaves");
   rf_status s = check_events(g, events, n_events);
   if (s) return s;
   if ((!params && g->prog.n_par > 0) || !nll) return fail(RF_EINVAL, "NULL argument");
@@ -879,11 +971,17 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   } else {
     epts[0] = epts[1] = 4;
   }
-  // register budgets: both for the specialised kernel, the generic kernels
-  // have one
-  const int n_mb = g->jit ? 2 : 1;
-  const int mbs[2] = {g->jit ? 2 : g->cfg.min_blocks, 3};
+  // register budgets: three for the specialised kernel (compiled in
+  // parallel first), the generic kernels have one
+  const int n_mb = g->jit ? 3 : 1;
+  const int mbs[3] = {g->jit ? 2 : g->cfg.min_blocks, 3, 4};
   if (g->jit) {
+    std::vector<std::string> srcs;
+    for (int ei = 0; ei < 2; ++ei)
+      for (int mi = 0; mi < n_mb; ++mi)
+        srcs.push_back(rf_jit_source(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED, epts[ei],
+                                     mbs[mi]));
+    rf_jit_precompile(srcs);
     std::string err;
     for (int ei = 0; ei < 2; ++ei)
       for (int mi = 0; mi < n_mb; ++mi)

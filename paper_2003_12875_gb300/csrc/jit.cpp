@@ -22,11 +22,14 @@
 #include <memory>
 #include <mutex>
 #include <sstream>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rf_internal.h"
-#include "rf_jit_prelude.inc"  // kRfJitPrelude, kRfJitToysPrelude: device headers as text
+#include "rf_jit_prelude.inc"  // kRfJitPrelude, kRfJitToysPrelude, kRfJitFormulaPrelude:
+                               // device headers as text
 
 namespace {
 
@@ -64,8 +67,37 @@ std::string cache_dir() {
 
 }  // namespace
 
-std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                          int min_blocks) {
+namespace {
+
+bool has_formula(const RfProgram& P) {
+  for (int k = 0; k < P.n_leaves; ++k)
+    if (P.leaf[k].type == RFL_FORMULA) return true;
+  return false;
+}
+
+// One struct per formula leaf k: NP and eval<Real>(x, p) -> Dual<Real, NP'>
+// (the translated text over the leaf's parameters as duals).
+void emit_formulas(std::ostringstream& o, const RfProgram& P, const RfFormulaCode* fc) {
+  o << kRfJitFormulaPrelude << "\n";
+  for (int k = 0; k < P.n_leaves; ++k) {
+    const RfLeafProg& L = P.leaf[k];
+    if (L.type != RFL_FORMULA) continue;
+    const int np = L.npar, nd = np > 0 ? np : 1;
+    o << "struct RfFormula" << k << " {\n  static constexpr int NP = " << np << ";\n"
+      << "  template <typename Real>\n  static __device__ __forceinline__ rf::Dual<Real, " << nd
+      << "> eval(Real x, const Real* __restrict__ pc) {\n"
+      << "    using D = rf::Dual<Real, " << nd << ">;\n";
+    for (int j = 0; j < np; ++j)
+      o << "    const D p" << j << " = D::var(pc[" << j << "], " << j << ");\n";
+    o << "    (void)x;\n    (void)pc;\n"
+      << "    return rf::as_dual<D>(" << (fc ? fc->leaf[k] : std::string("Real(1)")) << ");\n  }\n};\n";
+  }
+}
+
+}  // namespace
+
+std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                          int kind, int ept, int min_blocks) {
   const int NL = P.n_leaves, NC = P.n_comp;
   unsigned long long amask = 1ull;  // ell
   for (int c = 0; c < NC; ++c) amask |= 1ull << (1 + c);
@@ -74,7 +106,35 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
       if ((P.leaf[k].gmask >> j) & 1) amask |= 1ull << (1 + NL + k * RF_LEAF_MAXP + j);
   std::ostringstream o;
   if (getenv("RF_EVENTS_KEEP_L2")) o << "#define RF_EVENTS_KEEP_L2 1\n";  // experiment switch
-  o << kRfJitPrelude << "\n// ---- model emitted for this graph\n";
+  o << kRfJitPrelude << "\n";
+  if (has_formula(P)) emit_formulas(o, P, fc);
+  if (kind == RF_JIT_NORM) {
+    // FP64 normalisation of the formula leaves: blockIdx.y = formula number
+    double t[16], w[16];
+    rf_gauss_legendre16(t, w);
+    char buf[64];
+    o << "__device__ const double kRfGlT[16] = {";
+    for (int i = 0; i < 16; ++i) {
+      snprintf(buf, sizeof(buf), "%a%s", t[i], i < 15 ? ", " : "};\n");
+      o << buf;
+    }
+    o << "__device__ const double kRfGlW[16] = {";
+    for (int i = 0; i < 16; ++i) {
+      snprintf(buf, sizeof(buf), "%a%s", w[i], i < 15 ? ", " : "};\n");
+      o << buf;
+    }
+    o << "extern \"C\" __global__ void __launch_bounds__(128) rf_norm_jit(const RfProgram P, "
+         "const double* __restrict__ params, double* part, unsigned int* ticket) {\n"
+         "  switch (blockIdx.y) {\n";
+    int f = 0;
+    for (int k = 0; k < NL; ++k)
+      if (P.leaf[k].type == RFL_FORMULA)
+        o << "    case " << f++ << ": rf::formula_norm_body<RfFormula" << k << ">(P, " << k
+          << ", params, kRfGlT, kRfGlW, part, ticket, P.formula_norm); break;\n";
+    o << "  }\n}\n";
+    return o.str();
+  }
+  o << "// ---- model emitted for this graph\n";
   o << "struct RfModel {\n  static constexpr int NL_ = " << NL << ";\n"
     << "  static constexpr int NCOL = " << P.n_cols << ";\n"
     << "  static constexpr unsigned long long AMASK = " << amask << "ull;\n"
@@ -82,8 +142,12 @@ std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int
        "const rf::EvalConsts<Real, NL_>& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
   for (int k = 0; k < NL; ++k) {
     const RfLeafProg& L = P.leaf[k];
-    o << "    Real u" << k << ", g" << k << "[4];\n    rf::" << leaf_fn(L.type) << "<Real, "
-      << L.gmask << ">(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k << ");\n";
+    o << "    Real u" << k << ", g" << k << "[4];\n    ";
+    if (L.type == RFL_FORMULA)
+      o << "rf::formula_leaf<RfFormula" << k << ", Real, " << L.gmask << ">";
+    else
+      o << "rf::" << leaf_fn(L.type) << "<Real, " << L.gmask << ">";
+    o << "(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k << ");\n";
   }
   o << "    Real v[" << NC << "], w[" << NC << "];\n";
   std::vector<std::string> usum(NC);
@@ -182,27 +246,65 @@ static bool compile_cubin(const std::string& src, std::vector<char>* cubin, std:
   return true;
 }
 
-uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept, int min_blocks) {
-  return fnv1a(rf_jit_source(P, eval, coldt, kind, ept, min_blocks));
+namespace {
+
+std::string cubin_path(const std::string& src) {
+  char name[64];
+  snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v11"));
+  return cache_dir() + name;
 }
 
-bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                         int min_blocks, std::string* err) {
+// written under a temporary name and renamed, so readers never see a partial file
+void store_cubin(const std::string& path, const std::vector<char>& cubin) {
+  mkdir(cache_dir().c_str(), 0700);
+  static std::atomic<unsigned> seq{0};
+  const std::string tmp = path + "." + std::to_string(getpid()) + "." + std::to_string(seq++);
+  if (FILE* f = fopen(tmp.c_str(), "wb")) {
+    const bool ok = fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+    fclose(f);
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+  }
+}
+
+}  // namespace
+
+void rf_jit_precompile(const std::vector<std::string>& sources) {
+  std::vector<std::thread> th;
+  for (const std::string& src : sources) {
+    const std::string path = cubin_path(src);
+    if (access(path.c_str(), R_OK) == 0) continue;
+    th.emplace_back([src, path] {
+      std::vector<char> cubin;
+      std::string err;  // a failure here is reported by the compile that follows
+      if (compile_cubin(src, &cubin, &err)) store_cubin(path, cubin);
+    });
+  }
+  for (std::thread& t : th) t.join();
+}
+
+uint64_t rf_jit_hash(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt, int kind,
+                     int ept, int min_blocks) {
+  return fnv1a(rf_jit_source(P, fc, eval, coldt, kind, ept, min_blocks));
+}
+
+bool rf_jit_compile_only(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                         int kind, int ept, int min_blocks, std::string* err) {
   std::vector<char> cubin;
-  return compile_cubin(rf_jit_source(P, eval, coldt, kind, ept, min_blocks), &cubin, err);
+  return compile_cubin(rf_jit_source(P, fc, eval, coldt, kind, ept, min_blocks), &cubin, err);
 }
 
 // The kernel of the given kind specialised for P: from the process cache, else
 // from the on-disk cache, else compiled with NVRTC (and written to disk).
 // Host-synchronous; returns nullptr and fills *err on failure.
-cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                           int min_blocks, int* regs, std::string* err) {
+cudaKernel_t rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                           int kind, int ept, int min_blocks, int* regs, std::string* err) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     *err = "no current device";
     return nullptr;
   }
-  std::string src = rf_jit_source(P, eval, coldt, kind, ept, min_blocks);
+  std::string src = rf_jit_source(P, fc, eval, coldt, kind, ept, min_blocks);
   std::string key = std::to_string(dev) + "|" + src;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(key);
@@ -210,9 +312,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
   if (it != g_cache.end()) {
     k = it->second;
   } else {
-    char name[64];
-    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(src + "|sm_103a|v11"));
-    const std::string dir = cache_dir(), path = dir + name;
+    const std::string path = cubin_path(src);
     std::vector<char> cubin;
     if (FILE* f = fopen(path.c_str(), "rb")) {
       fseek(f, 0, SEEK_END);
@@ -226,14 +326,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
     }
     if (cubin.empty()) {
       if (!compile_cubin(src, &cubin, err)) return nullptr;
-      mkdir(dir.c_str(), 0700);
-      std::string tmp = path + "." + std::to_string(getpid());
-      if (FILE* f = fopen(tmp.c_str(), "wb")) {
-        bool ok = fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
-        fclose(f);
-        if (ok) rename(tmp.c_str(), path.c_str());
-        else remove(tmp.c_str());
-      }
+      store_cubin(path, cubin);
     }
     cudaLibrary_t lib = nullptr;
     cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
@@ -242,7 +335,8 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, in
       return nullptr;
     }
     const char* kname = kind == RF_JIT_FUSED ? "rf_fused_jit"
-                        : (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) ? "rf_toys_jit" : "rf_logp_jit";
+                        : (kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK) ? "rf_toys_jit"
+                        : kind == RF_JIT_NORM ? "rf_norm_jit" : "rf_logp_jit";
     e = cudaLibraryGetKernel(&k, lib, kname);
     if (e != cudaSuccess) {
       *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
@@ -304,6 +398,14 @@ int rf_jit_launch_toys(cudaKernel_t k, const RfProgram& P, int grid, int block, 
   lc.attrs = at;
   lc.numAttrs = 1;
   return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void*>(k), args);
+}
+
+int rf_jit_launch_norm(cudaKernel_t k, const RfProgram& P, int n_formula, const double* params,
+                       double* part, unsigned int* ticket, cudaStream_t st) {
+  RfProgram Pc = P;
+  void* args[] = {&Pc, &params, &part, &ticket};
+  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(RF_FORMULA_BLOCKS, n_formula),
+                               dim3(128), args, 0, st);
 }
 
 int rf_jit_launch_logp(cudaKernel_t k, const RfProgram& P, const void* events, int64_t n,

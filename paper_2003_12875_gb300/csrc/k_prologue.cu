@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(32 * RF_MAXL) prologue_kernel(const RfProgram 
 }  // namespace rf
 
 int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
-                       cudaStream_t st) {
+                       bool chain, cudaStream_t st) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(1);
   lc.blockDim = dim3(32 * (P.n_leaves > 0 ? P.n_leaves : 1));
@@ -43,8 +43,8 @@ int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWor
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
-  lc.attrs = at;
-  lc.numAttrs = 1;
+  lc.attrs = chain ? at : nullptr;
+  lc.numAttrs = chain ? 1 : 0;
   if (eval) return (int)cudaLaunchKernelEx(&lc, rf::prologue_kernel<double>, P, params, W);
   return (int)cudaLaunchKernelEx(&lc, rf::prologue_kernel<float>, P, params, W);
 }

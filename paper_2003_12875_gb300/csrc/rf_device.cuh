@@ -270,8 +270,17 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   const RfLeafProg& L = P.leaf[k];
   double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
   for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
-  double dln[RF_LEAF_MAXP];
-  bool ok = leaf_lognorm(L.type, th, L.lo, L.hi, lnI_out, dln);
+  double dln[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+  bool ok;
+  if (L.type == RFL_FORMULA) {
+    // log I and (dI/dp_j)/I from the normalisation kernel (NaN: I <= 0)
+    const double* nrm = P.formula_norm + k * RF_FORMULA_NV;
+    *lnI_out = nrm[0];
+    for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
+    ok = isfinite(*lnI_out);
+  } else {
+    ok = leaf_lognorm(L.type, th, L.lo, L.hi, lnI_out, dln);
+  }
   K.lnI[k] = *lnI_out;
   Real* pc = K.pc[k];
   for (int j = 0; j < RF_PC; ++j) pc[j] = Real(0);
@@ -329,6 +338,15 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       K.dtheta[k][3] = (double)pc[4] - th[3];
       K.gmul[k][0] = K.gmul[k][1] = -1.0 / th[1];  // d u/d mu = -du/dz / lambda, etc.
       K.gmul[k][2] = K.gmul[k][3] = -1.0;         // d u/d gamma = -w, d u/d delta = -w asinh z
+      break;
+    }
+    case RFL_FORMULA: {
+      // the formula runs on the parameters rounded to Real (first-order
+      // correction through dtheta, as for the built-in leaves)
+      for (int j = 0; j < L.npar; ++j) {
+        pc[j] = (Real)th[j];
+        K.dtheta[k][j] = (double)pc[j] - th[j];
+      }
       break;
     }
     case RFL_ARGUS: {

@@ -32,6 +32,12 @@ typedef unsigned long long uintptr_t;
 #define RF_NACC_MAX RF_NACC(RF_MAXL)
 // blocks whose partial sums fit the static scratch of rf_nll_noalloc
 #define RF_NOALLOC_MAX_BLOCKS 1024
+// formula-leaf normalisation: 16-point Gauss-Legendre on RF_FORMULA_PANELS
+// panels, one node per thread, RF_FORMULA_BLOCKS blocks of 128 threads; per
+// leaf 1 + RF_LEAF_MAXP values (log I, then (dI/dp_j)/I)
+#define RF_FORMULA_PANELS 128
+#define RF_FORMULA_BLOCKS 16
+#define RF_FORMULA_NV (1 + RF_LEAF_MAXP)
 
 enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 // device status bits (same values as RF_STATUS_* in include/rf.h)
@@ -39,7 +45,15 @@ enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 #define RF_STATUS_NONFINITE_BIT 2u
 #define RF_STATUS_TIMEOUT_BIT 4u
 #define RF_STATUS_GEN_EXHAUSTED_BIT 8u
-enum { RFL_GAUSS = 1, RFL_EXP = 2, RFL_CHEB = 3, RFL_CB = 4, RFL_ARGUS = 5, RFL_JOHNSON = 9 };
+enum {
+  RFL_GAUSS = 1,
+  RFL_EXP = 2,
+  RFL_CHEB = 3,
+  RFL_CB = 4,
+  RFL_ARGUS = 5,
+  RFL_JOHNSON = 9,
+  RFL_FORMULA = 10  // a formula given as text; specialised kernels only
+};
 
 struct RfLeafProg {
   int32_t type;      // RFL_*
@@ -64,6 +78,9 @@ struct RfProgram {
   uint64_t fixed_lo, fixed_hi;  // bit p: parameter p is fixed (grad = 0)
   double ext_weight;         // weight of the extended term sum(nu) and its
                              // gradient (1; 0 on all shards but one)
+  double* formula_norm;      // device [RF_MAXL * (1 + RF_LEAF_MAXP)]: log I and
+                             // (dI/dp_j)/I of each formula leaf, written by the
+                             // normalisation kernel before the prologue reads them
   RfLeafProg leaf[RF_MAXL];
 };
 
@@ -124,11 +141,13 @@ RF_DECL_FUSED(f64, c32)
 RF_DECL_FUSED(f64, c64)
 
 // FP64 prologue kernel for the single-dataset path: one block, one warp per
-// leaf; writes W.consts.  Launched as a programmatic dependent of the previous
-// kernel in the stream and lets its own dependent (the fused kernel) launch at
-// once.
+// leaf; writes W.consts.  With chain, launched as a programmatic dependent of
+// the previous kernel in the stream (its FP64 work overlaps that kernel's
+// end; without chain it starts after it, as it must after the normalisation
+// kernel of formula leaves whose results it reads); either way it lets its
+// own dependent (the fused kernel) launch at once.
 int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWork W,
-                       rf_cuda_stream st);
+                       bool chain, rf_cuda_stream st);
 
 // Toy studies: prep kernel (per-toy FP64 constants), segment kernel (events
 // split evenly over the launch's warps), finalize kernel (one warp per toy:
@@ -166,19 +185,35 @@ void rf_vec_plan(const RfProgram& P, const void* events, int64_t stride, int ele
 
 // per-graph specialised kernels (jit.cpp)
 #include <string>
+#include <vector>
 // toy segment kernel: register streaming (RF_JIT_TOYS) or bulk-copy stage
 // rings (RF_JIT_TOYS_BULK)
-enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2, RF_JIT_TOYS_BULK = 3 };
+// RF_JIT_NORM: the FP64 normalisation kernel of a graph's formula leaves
+enum { RF_JIT_FUSED = 0, RF_JIT_TOYS = 1, RF_JIT_LOGP = 2, RF_JIT_TOYS_BULK = 3, RF_JIT_NORM = 4 };
+// CUDA text of each formula leaf (rf_expr_translate), empty for the others
+struct RfFormulaCode {
+  std::string leaf[RF_MAXL];
+};
+bool rf_expr_translate(const char* text, int npar, std::string* code, std::string* err);
+void rf_gauss_legendre16(double* t, double* w);
 typedef struct CUkern_st* rf_cuda_kernel;  // == cudaKernel_t
 // min_blocks: launch bounds of the fused and toy kernels (resident blocks of 256
 // threads per SM; 0 for the toy kernel: none); the log P kernel ignores it
-std::string rf_jit_source(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                          int min_blocks);
-uint64_t rf_jit_hash(const RfProgram& P, int eval, int coldt, int kind, int ept, int min_blocks);
-bool rf_jit_compile_only(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                         int min_blocks, std::string* err);
-rf_cuda_kernel rf_jit_kernel(const RfProgram& P, int eval, int coldt, int kind, int ept,
-                             int min_blocks, int* regs, std::string* err);
+// fc: the graph's formula-leaf code (NULL without formula leaves)
+std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                          int kind, int ept, int min_blocks);
+uint64_t rf_jit_hash(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt, int kind,
+                     int ept, int min_blocks);
+bool rf_jit_compile_only(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                         int kind, int ept, int min_blocks, std::string* err);
+rf_cuda_kernel rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
+                             int kind, int ept, int min_blocks, int* regs, std::string* err);
+// compiles the sources not yet in the on-disk cache, in parallel threads
+void rf_jit_precompile(const std::vector<std::string>& sources);
+// normalisation kernel of the formula leaves (grid RF_FORMULA_BLOCKS x leaves)
+int rf_jit_launch_norm(rf_cuda_kernel k, const RfProgram& P, int n_formula,
+                       const double* params, double* part, unsigned int* ticket,
+                       rf_cuda_stream st);
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
                         RfWork W, double* nll, double* grad, rf_cuda_stream st);

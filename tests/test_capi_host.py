@@ -120,3 +120,53 @@ def test_specialised_kernels_compile_without_gpu(rf, make, dt, prec):
     w = make()
     rc = rf.jit_check(w["spec"], dt, prec)
     assert rc == 0, rf.load().rf_last_error().decode()[:2000]
+
+
+# ------------------------------------------------------------ formula leaves
+
+def _formula(text, npar=2, lo=-1.0, hi=2.0):
+    return {"obs": [(lo, hi)], "params": [0.3, 0.7, 0.2, 0.1][:max(npar, 1)],
+            "nodes": [{"type": "formula", "formula": text, "obs": 0, "params": list(range(npar))}],
+            "root": 0}
+
+
+def test_formula_texts_accepted_and_rejected_like_the_oracle(rf):
+    """The library's translator and the oracle's parser are separate code for
+    the same grammar: they accept and reject the same texts."""
+    import oracle
+    texts = ["exp(-0.5*((x-p0)/p1)^2)", "2^3^2", "-2^2+5", "(-2)^2", "10/2/5", "2^-1",
+             "pow(-2, 3) + 9", "1e-3*1000", ".5*4", "2.5E+1/25", "+3", "--2", "p01 + x",
+             "exp(0)+log(1)+sqrt(4)+abs(-1)", "erf(x)+erfc(x)+tanh(x)+atan(x)+asinh(x)",
+             "", "1+", "x)", "(x", "p2", "foo(x)", "exp x", "1e", "x x", "pow(x)", "exp(x,1)",
+             "p", "y", "1..2", "x^", "*x", "p0001", "exp()", "1 2"]
+    for t in texts:
+        want = oracle.expr_check(t, 2)
+        got = rf.validate(_formula(t))
+        assert (got == 0) == (want == 0), (t, got, want)
+        if want:
+            assert got == EINVAL
+
+
+def test_formula_parameter_counts(rf):
+    assert rf.validate(_formula("1 + x", 0)) == 0
+    assert rf.validate(_formula("1 + p3*x", 4)) == 0
+    s = _formula("1 + p0*x", 2)
+    s["nodes"][0]["params"] = [0, 0, 0, 0, 0]
+    assert rf.validate(s) == EINVAL                     # more than 4 parameters
+    s = _formula("1 + p0*x", 1)
+    del s["nodes"][0]["formula"]
+    assert rf.validate(s) == EINVAL                     # no text
+
+
+@pytest.mark.parametrize("prec,dt", [("fp32", "f32"), ("fp64", "f64"), ("fp32", "f64")])
+def test_formula_kernels_compile_without_gpu(rf, prec, dt):
+    """Formula leaves with every function and power form compile into the
+    fused, log P and normalisation kernels (toy kernels are not built)."""
+    spec = datagen.gauss_exp_ext_spec()
+    spec["nodes"][0] = dict(spec["nodes"][0], type="formula",
+                            formula="exp(-0.5*((x-p0)/p1)^2) * (1 + 0*(sin(x)+cos(x)+tanh(x)"
+                                    "+sinh(x)+cosh(x)+asinh(x)+atan(x)+erf(x)+erfc(x)+abs(x)"
+                                    "+sqrt(2+x)+log(2+x)+pow(2+x, p0)+pow(2, p1)+x^-3+p0^2.5))")
+    spec["nodes"][1] = dict(spec["nodes"][1], type="formula", formula="exp(p0*x)")
+    assert rf.jit_check(spec, dt, prec) == 0, rf.load().rf_last_error().decode()[:2000]
+    assert rf.jit_check(_formula("1 + 0.5*x", 0), dt, prec) == 0

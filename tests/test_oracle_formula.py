@@ -1,4 +1,4 @@
-"""Pins of the oracle's formula leaves (expr): a PDF given as text, as the
+"""Pins of the oracle's formula leaves (type "formula"): a PDF given as text, as the
 formula PDFs of Sec. 4 are, evaluated by walking its parse tree with forward
 derivatives and normalised by adaptive Gauss-Legendre quadrature.
 
@@ -166,8 +166,8 @@ def test_rejected_syntax(text, npar):
 def test_model_with_formula_leaf_equals_builtin_model():
     spec = datagen.gauss_exp_ext_spec(nu_s=300.0, nu_b=700.0)
     cols = datagen.c4(toys=1)["cols"][:, :1000]
-    alt = {**spec, "nodes": [dict(spec["nodes"][0], type="expr", expr=GAUSS),
-                             dict(spec["nodes"][1], type="expr", expr="exp(p0*x)"),
+    alt = {**spec, "nodes": [dict(spec["nodes"][0], type="formula", formula=GAUSS),
+                             dict(spec["nodes"][1], type="formula", formula="exp(p0*x)"),
                              spec["nodes"][2]]}
     p = [5.05, 0.52, -0.28, 310.0, 690.0]
     v, g, rc = oracle.nll(spec, p, cols)
@@ -182,10 +182,10 @@ def test_model_with_formula_leaf_equals_builtin_model():
 
 def test_formula_domain_and_generation():
     spec = {"obs": [(-1.0, 1.0)], "params": [0.5],
-            "nodes": [{"type": "expr", "expr": "x - p0", "obs": 0, "params": [0]}], "root": 0}
+            "nodes": [{"type": "formula", "formula": "x - p0", "obs": 0, "params": [0]}], "root": 0}
     v, g, rc = oracle.nll(spec, [0.5], np.array([[0.7, 0.9]]))
     assert rc == oracle.EDOMAIN and v == math.inf          # integral <= 0
-    bad = {**spec, "nodes": [dict(spec["nodes"][0], expr="x +")]}
+    bad = {**spec, "nodes": [dict(spec["nodes"][0], formula="x +")]}
     assert oracle.nll(bad, [0.5], np.array([[0.7]]))[2] == oracle.EINVAL
-    ok = {**spec, "nodes": [dict(spec["nodes"][0], expr="1 + p0*x")]}
+    ok = {**spec, "nodes": [dict(spec["nodes"][0], formula="1 + p0*x")]}
     assert oracle.generate(ok, [[0.5]], [[3]], [0, 3], seed=1, col_f32=False)[2] == oracle.EUNSUPPORTED
