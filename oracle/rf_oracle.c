@@ -468,36 +468,39 @@ static void gl_rule(double* t, double* w) {
   }
 }
 
+/* integrand: v[0] = f(x), v[1..m] = its parameter derivatives */
+typedef void (*qfn)(double x, const void* ctx, int m, double* v);
 typedef struct {
-  const xprog* p;
-  const double* th;
+  qfn fn;
+  const void* ctx;
   int m;
   double t[ORC_GLN], w[ORC_GLN];
+  double floor[1 + ORC_MAXNP]; /* absolute error allowed per unit length */
   long budget;
   int bad;
 } xquad;
 
-/* rule on [a, b]: out[0] = int f, out[1+j] = int df/dp_j; mag[] = int |.| */
+/* rule on [a, b]: out[c] = int v[c]; mag[] = int |v[c]| */
 static void xrule(xquad* Q, double a, double b, double* out, double* mag) {
   double mid = 0.5 * (a + b), half = 0.5 * (b - a);
   for (int c = 0; c <= Q->m; ++c) out[c] = mag[c] = 0.0;
   for (int i = 0; i < ORC_GLN; ++i) {
-    double v, dv[ORC_MAXNP];
-    xeval(Q->p, Q->p->root, mid + half * Q->t[i], Q->th, Q->m, &v, dv);
-    if (!isfinite(v)) Q->bad = 1;
+    double v[1 + ORC_MAXNP];
+    Q->fn(mid + half * Q->t[i], Q->ctx, Q->m, v);
     double wh = Q->w[i] * half;
-    out[0] += wh * v;
-    mag[0] += wh * fabs(v);
-    for (int j = 0; j < Q->m; ++j) {
-      out[1 + j] += wh * dv[j];
-      mag[1 + j] += wh * fabs(dv[j]);
+    for (int c = 0; c <= Q->m; ++c) {
+      if (!isfinite(v[c])) Q->bad = 1;
+      out[c] += wh * v[c];
+      mag[c] += wh * fabs(v[c]);
     }
   }
   Q->budget--;
 }
 
 /* adaptive bisection: accept the halves once they reproduce the whole to
- * 1e-14 of the absolute integrand in every component */
+ * 1e-14 of the absolute integrand in every component, or to the panel's share
+ * of 1e-15 of the whole range's absolute integral (rounding noise of the
+ * integrand near a singular end point must not force endless refinement) */
 static void xadapt(xquad* Q, double a, double b, const double* whole, int depth, double* acc) {
   double l[1 + ORC_MAXNP], lm[1 + ORC_MAXNP], r[1 + ORC_MAXNP], rm[1 + ORC_MAXNP];
   double mid = 0.5 * (a + b);
@@ -505,7 +508,8 @@ static void xadapt(xquad* Q, double a, double b, const double* whole, int depth,
   xrule(Q, mid, b, r, rm);
   int done = depth >= 50 || Q->budget <= 0 || Q->bad;
   for (int c = 0; c <= Q->m && !done; ++c)
-    if (fabs(l[c] + r[c] - whole[c]) > 1e-14 * (lm[c] + rm[c]) + 1e-300) done = -1;
+    if (fabs(l[c] + r[c] - whole[c]) > 1e-14 * (lm[c] + rm[c]) + Q->floor[c] * (b - a) + 1e-300)
+      done = -1;
   if (done != -1) {
     for (int c = 0; c <= Q->m; ++c) acc[c] += l[c] + r[c];
     return;
@@ -514,27 +518,73 @@ static void xadapt(xquad* Q, double a, double b, const double* whole, int depth,
   xadapt(Q, mid, b, r, depth + 1, acc);
 }
 
-/* I = int_lo^hi f, dI[j] = int df/dp_j, over 16 starting panels */
-static int xnorm(const xprog* p, const double* th, int m, double lo, double hi, double* I,
-                 double* dI) {
+/* out[c] = int_lo^hi v[c] over 16 starting panels, adaptively refined;
+ * returns 1 when the integrand was not finite somewhere */
+static int quad(qfn fn, const void* ctx, int m, double lo, double hi, double* out) {
   xquad Q;
-  Q.p = p;
-  Q.th = th;
+  Q.fn = fn;
+  Q.ctx = ctx;
   Q.m = m;
   Q.budget = 200000;
   Q.bad = 0;
   gl_rule(Q.t, Q.w);
-  double acc[1 + ORC_MAXNP] = {0};
+  double whole[16][1 + ORC_MAXNP], mag[1 + ORC_MAXNP], tot[1 + ORC_MAXNP] = {0};
   for (int k = 0; k < 16; ++k) {
     double a = lo + (hi - lo) * k / 16.0, b = k == 15 ? hi : lo + (hi - lo) * (k + 1) / 16.0;
-    double whole[1 + ORC_MAXNP], mag[1 + ORC_MAXNP];
-    xrule(&Q, a, b, whole, mag);
-    xadapt(&Q, a, b, whole, 0, acc);
+    xrule(&Q, a, b, whole[k], mag);
+    for (int c = 0; c <= m; ++c) tot[c] += mag[c];
   }
+  for (int c = 0; c <= m; ++c) {
+    Q.floor[c] = 1e-15 * tot[c] / (hi - lo);
+    out[c] = 0.0;
+  }
+  for (int k = 0; k < 16; ++k) {
+    double a = lo + (hi - lo) * k / 16.0, b = k == 15 ? hi : lo + (hi - lo) * (k + 1) / 16.0;
+    xadapt(&Q, a, b, whole[k], 0, out);
+  }
+  return Q.bad;
+}
+
+typedef struct {
+  const xprog* p;
+  const double* th;
+} xctx;
+
+static void formula_fn(double x, const void* ctx, int m, double* v) {
+  const xctx* c = (const xctx*)ctx;
+  xeval(c->p, c->p->root, x, c->th, m, &v[0], &v[1]);
+}
+
+/* I = int_lo^hi f, dI[j] = int df/dp_j */
+static int xnorm(const xprog* p, const double* th, int m, double lo, double hi, double* I,
+                 double* dI) {
+  xctx c = {p, th};
+  double acc[1 + ORC_MAXNP];
+  int bad = quad(formula_fn, &c, m, lo, hi, acc);
   *I = acc[0];
   for (int j = 0; j < m; ++j) dI[j] = acc[1 + j];
-  if (Q.bad || !isfinite(*I) || !(*I > 0.0)) return ORC_EDOMAIN;
+  if (bad || !isfinite(*I) || !(*I > 0.0)) return ORC_EDOMAIN;
   return ORC_OK;
+}
+
+/* ARGUS density x tau^p e^{c tau} and its c and p derivatives (tau and
+ * log tau times it), zero from m0 up */
+typedef struct {
+  double m0, c, p;
+} argus_ctx;
+
+static void argus_fn(double x, const void* ctx, int m, double* v) {
+  const argus_ctx* a = (const argus_ctx*)ctx;
+  (void)m;
+  if (x >= a->m0) {
+    v[0] = v[1] = v[2] = 0.0;
+    return;
+  }
+  double tau = (a->m0 - x) * (a->m0 + x) / (a->m0 * a->m0); /* no cancellation near m0 */
+  double f = x * pow(tau, a->p) * exp(a->c * tau);
+  v[0] = f;
+  v[1] = f * tau;
+  v[2] = f * log(tau);
 }
 
 int orc_expr_check(const char* text, int npar) {
@@ -821,9 +871,26 @@ static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
     case ORC_ARGUS: {
       if (nth != 3) return ORC_EINVAL;
       double m0 = th[0], c = th[1], p = th[2];
-      if (p != 0.5) return ORC_EUNSUPPORTED;
-      if (!(m0 > lo) || lo < 0.0) return ORC_EDOMAIN;
+      if (!(m0 > lo) || lo < 0.0 || !(p > 0.0)) return ORC_EDOMAIN;
       double bp = hi < m0 ? hi : m0;
+      /* the integral and its c and p derivatives by quadrature of the
+       * density (the p derivative always: it has no closed form) */
+      argus_ctx ac = {m0, c, p};
+      double q[3];
+      if (quad(argus_fn, &ac, 2, lo, bp, q)) return ORC_EDOMAIN;
+      dI[2] = q[2];
+      if (p != 0.5) {
+        /* d/dm0 by differentiating under the integral sign with the limit
+         * b' = min(hi, m0): in tau = 1 - (x/m0)^2 the integral is
+         * (m0^2/2) int_{tau(b')}^{tau(lo)} tau^p e^{c tau}, whose m0
+         * derivative is 2I/m0 + (lo^2/m0) f_tau(tau(lo)) - (b'^2/m0) f_tau(tau(b')) */
+        double ta = 1.0 - (lo / m0) * (lo / m0), tb = 1.0 - (bp / m0) * (bp / m0);
+        double ea = pow(ta, p) * exp(c * ta), eb = tb > 0.0 ? pow(tb, p) * exp(c * tb) : 0.0;
+        *I_out = q[0];
+        dI[1] = q[1];
+        dI[0] = 2.0 * q[0] / m0 + (lo * lo / m0) * ea - (bp * bp / m0) * eb;
+        return ORC_OK;
+      }
       double ra = lo / m0, rb = bp / m0;
       double ta = 1.0 - ra * ra, tb = 1.0 - rb * rb;
       /* m dm = -(m0^2/2) d tau */
@@ -834,7 +901,6 @@ static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
       double ea = (1.0 - ta) * pow(ta, p) * exp(c * ta);
       double eb = tb > 0.0 ? (1.0 - tb) * pow(tb, p) * exp(c * tb) : 0.0;
       dI[0] = m0 * (ea - eb) + 2.0 * I / m0;
-      dI[2] = NAN; /* d/dp of the incomplete gamma: not provided */
       return ORC_OK;
     }
     case ORC_JOHNSON: {
@@ -1440,6 +1506,7 @@ int orc_generate(const orc_model* m, const double* params_matrix, int32_t toys,
           int node = lv[c][k], o = m->obs[node];
           double th[ORC_MAXNP];
           for (int j = 0; j < m->npar[node]; ++j) th[j] = p[m->par[node * ORC_MAXNP + j]];
+          if (m->type[node] == ORC_ARGUS && th[2] != 0.5) return ORC_EUNSUPPORTED;
           double lo = m->obs_lo[o], hi = m->obs_hi[o], x = NAN;
           int ok = 0;
           for (uint64_t r = 0; r < 4096 && !ok; ++r) {

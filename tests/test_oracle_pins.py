@@ -113,6 +113,10 @@ LEAF_CASES = [
     ("argus", [5.29, -1.0, 0.5], 5.0, 5.29),    # series branch
     ("argus", [1.0, -40.0, 0.5], 0.2, 0.9),     # range ends below m0
     ("argus", [1.0, -3.0, 0.5], 0.0, 1.5),      # range extends past m0
+    ("argus", [5.29, -20.0, 0.8], 5.20, 5.29),  # p other than 1/2
+    ("argus", [1.0, -3.0, 1.0], 0.0, 1.5),
+    ("argus", [1.0, 4.0, 2.5], 0.2, 0.9),       # c > 0, range below m0
+    ("argus", [1.0, -30.0, 0.3], 0.5, 1.0),
     ("johnson", [0.5, 1.3, -0.4, 1.7], -2.0, 3.0),
     ("johnson", [5.28, 0.004, 0.8, 1.1], 5.20, 5.29),   # heavy tails, skewed
     ("johnson", [0.0, 1.0, 0.0, 3.0], -1.0, 8.0),       # near-Gaussian core
@@ -125,6 +129,9 @@ def test_normalised_leaf_matches_library_density(kind, th, lo, hi):
     if kind == "cb" and th[3] <= 1.0 + 1e-3:
         pytest.skip("scipy's full-line Crystal Ball is improper for n <= 1; "
                     "this case is pinned by quadrature")
+    if kind == "argus" and th[2] != 0.5:
+        pytest.skip("scipy's ARGUS has p = 1/2; other p are pinned by quadrature and, "
+                    "for p = 1, by the closed form")
     top = min(hi, th[0]) if kind == "argus" else hi
     xs = np.linspace(lo, top, 23)[1:-1]
     want = lib_logpdf(kind, th, lo, hi, xs)
@@ -169,9 +176,6 @@ def test_norm_derivatives_match_differences(kind, th, lo, hi):
     I, dI, rc = oracle.leaf_norm(kind, th, lo, hi)
     assert rc == 0
     for j in range(len(th)):
-        if kind == "argus" and j == 2:
-            assert math.isnan(dI[j])   # d/dp is not provided
-            continue
         h = fd_step(kind, th, j, lo, hi, 2e-4)
 
         def I_of(v):
@@ -195,8 +199,6 @@ def test_logf_derivatives_match_differences(kind, th, lo, hi):
     for x in np.linspace(lo, top, 9)[1:-1]:
         _, d, rc = oracle.leaf_logf(kind, th, lo, hi, float(x))
         for j in range(len(th)):
-            if kind == "argus" and j == 2:
-                continue
             h = fd_step(kind, th, j, lo, hi, 1e-4)
 
             def lf(v):
@@ -215,9 +217,37 @@ def test_argus_p_derivative_is_log_tau():
     assert abs(d[2] - richardson(lf, 0.5, 1e-4)) < 1e-9
 
 
-def test_unsupported_argus_p():
-    _, _, rc = oracle.leaf_norm("argus", [5.29, -20.0, 0.7], 5.2, 5.29)
-    assert rc == oracle.EUNSUPPORTED
+def test_argus_p_domain():
+    for p in (0.0, -0.3):
+        _, _, rc = oracle.leaf_norm("argus", [5.29, -20.0, p], 5.2, 5.29)
+        assert rc == oracle.EDOMAIN
+
+
+@pytest.mark.parametrize("m0,c,lo,hi", [(1.0, -3.0, 0.0, 1.5), (5.29, -20.0, 5.2, 5.29),
+                                        (1.0, 4.0, 0.2, 0.9), (2.0, -0.7, 0.5, 1.9)])
+def test_argus_p1_closed_form(m0, c, lo, hi):
+    """p = 1: int tau e^{c tau} d tau = e^{c tau} (c tau - 1) / c^2, so
+    I = (m0^2/2) [g(tau(lo)) - g(tau(b'))], b' = min(hi, m0)."""
+    b = min(hi, m0)
+    ta, tb = 1 - (lo / m0) ** 2, 1 - (b / m0) ** 2
+    g = lambda t: math.exp(c * t) * (c * t - 1) / c**2
+    want = 0.5 * m0 * m0 * (g(ta) - g(tb))
+    I, dI, rc = oracle.leaf_norm("argus", [m0, c, 1.0], lo, hi)
+    assert rc == 0 and abs(I - want) <= 1e-13 * want
+    # d/dc of the closed form
+    dg = lambda t: (math.exp(c * t) * (t * (c * t - 1) + t) * c**2 - 2 * c * math.exp(c * t) * (c * t - 1)) / c**4
+    assert abs(dI[1] - 0.5 * m0 * m0 * (dg(ta) - dg(tb))) <= 1e-12 * abs(dI[1])
+
+
+def test_argus_general_p_continuous_at_one_half():
+    """The closed form at p = 1/2 and the quadrature just beside it agree."""
+    th = [5.29, -20.0, 0.5]
+    I, dI, _ = oracle.leaf_norm("argus", th, 5.2, 5.29)
+    for e in (1e-9, -1e-9):
+        Ie, dIe, rc = oracle.leaf_norm("argus", [5.29, -20.0, 0.5 + e], 5.2, 5.29)
+        assert rc == 0
+        assert abs(Ie - (I + e * dI[2])) <= 3e-13 * I + 1e-6 * abs(e * dI[2])
+        np.testing.assert_allclose(dIe[:2], dI[:2], rtol=1e-7)
 
 
 # ---------------------------------------------------------------- whole NLLs
