@@ -133,7 +133,7 @@ LEAF_INSTR = {
     "exp": (3, {0: 0}, 0),
     "cheb": (13, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
     "cb": (12, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
-    "argus": (14, {0: 5, 1: 1}, 0),
+    "argus": (14, {0: 5, 1: 1, 2: 3}, 0),   # a free p: one more log and its product
     "johnson": (14, {0: 0, 1: 1, 2: 0, 3: 1}, 4),
 }
 LOG_INSTR = 2          # hardware log2 and a multiply by ln 2
@@ -434,6 +434,8 @@ def main():
                     help="events per thread of the fused kernel (0: default / tuned)")
     ap.add_argument("--generic", action="store_true",
                     help="run the precompiled generic kernels instead of the per-graph ones")
+    ap.add_argument("--min-blocks", type=int, default=0,
+                    help="register budget of the specialised kernel (2, 3 or 4; with --no-tune)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="events for the CPU oracle baseline (0: the whole workload)")
@@ -476,6 +478,8 @@ def main():
     tuned_ms = None
     if args.ept:
         G.set_launch(ept=args.ept)
+    if args.min_blocks:
+        G.set_launch(min_blocks=args.min_blocks)
     if not args.no_tune:
         tuned_ms = G.tune(ev, params)
     for _ in range(args.warmup):

@@ -19,7 +19,11 @@
  *   RF_EXP    (lambda)               exp(lambda x)
  *   RF_CHEB   (c_1..c_m), m <= 4     1 + sum_j c_j T_j(x'), x' = (2x-lo-hi)/(hi-lo)
  *   RF_CB     (m0, sigma, alpha, n)  Crystal Ball; alpha > 0: tail below m0
- *   RF_ARGUS  (m0, c, p), p = 1/2    x sqrt(1-(x/m0)^2) exp(c (1-(x/m0)^2)), x < m0
+ *   RF_ARGUS  (m0, c, p)             x tau^p exp(c tau), tau = 1-(x/m0)^2, x < m0;
+ *             a fixed p must be 1/2 (its one-log form and closed-form
+ *             integral); a free p takes any p > 0, its integral and d/dp from
+ *             positive-term series of the incomplete gamma function (toy
+ *             generation draws p = 1/2 only)
  *   RF_JOHNSON (mu, lambda, gamma, delta)  Johnson's SU (Sec. 3): with
  *             z = (x-mu)/lambda, w = gamma + delta asinh z standard normal:
  *             delta / (lambda sqrt(2 pi (1+z^2))) exp(-w^2/2)

@@ -35,7 +35,7 @@ enum {
   ORC_EXP = 2,      /* params (lambda)                         */
   ORC_CHEB = 3,     /* params (c_1 .. c_m), m <= ORC_MAXNP     */
   ORC_CB = 4,       /* params (m0, sigma, alpha, n)            */
-  ORC_ARGUS = 5,    /* params (m0, c, p); p must equal 0.5     */
+  ORC_ARGUS = 5,    /* params (m0, c, p), p > 0                */
   ORC_ADD_FRAC = 6, /* K children, K-1 fraction params         */
   ORC_ADD_EXT = 7,  /* K children, K yield params; root only   */
   ORC_PROD = 8,     /* K children on disjoint observables      */

@@ -203,11 +203,8 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
       int gm = 0;
       for (int j = 0; j < n.n_params; ++j)
         if (!fixed(n.params[j])) gm |= 1 << j;
-      if (n.type == RF_ARGUS) {
-        if (!fixed(n.params[2]))
-          return fail(RF_EUNSUPPORTED, "ARGUS p must be a fixed parameter (its integral's d/dp is not provided)");
-        gm &= 3;
-      }
+      // ARGUS: a free p selects the general-p form (d/dp included); a fixed
+      // p must be 1/2 at run time (checked in the prologue)
       L.gmask = gm;
     }
   }

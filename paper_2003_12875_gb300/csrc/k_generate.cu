@@ -212,6 +212,11 @@ __global__ void __launch_bounds__(256)
       const int obs = P.col_obs[L.col];
       double th[RF_LEAF_MAXP];
       for (int j = 0; j < L.npar; ++j) th[j] = row[L.par[j]];
+      if (L.type == RFL_ARGUS && th[2] != 0.5) {  // the sampler draws p = 1/2 only
+        atomicOr(status, RF_STATUS_PARAM_DOMAIN_BIT);
+        ev[(int64_t)obs * n_events + i] = Col(nan(""));
+        continue;
+      }
       double x = nan("");
       bool ok = false;
       Col v = Col(0);

@@ -120,7 +120,51 @@ __device__ inline void argus_int2(double tau, double c, double* J12, double* J32
 // the constant the per-event code leaves out of u = log f - off (Exponential:
 // lambda * lo, so that u = lambda (x - lo) stays small).  Returns false when
 // the parameters are outside the leaf's definition range.
-static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, double lo,
+// ARGUS with a general power p, s = p + 1 > 1: J(t) = int_0^t tau^p e^{c tau}
+// d tau and dJ/dp, for 0 <= t <= 1.  Both series have positive terms only:
+//   c <= 0 (k = -c): J = t^s e^{ct} sum_n T_n, T_n = (kt)^n / (s (s+1) ... (s+n))
+//     (the lower incomplete gamma's Kummer series, J = gamma(s, kt) / k^s);
+//     dJ/ds = log(t) J - t^s e^{ct} sum_n T_n H_n, H_n = sum_{j<=n} 1/(s+j)
+//   c > 0: J = t^s sum_n U_n, U_n = (ct)^n / (n! (s+n));
+//     dJ/ds = log(t) J - t^s sum_n U_n / (s+n)
+// The terms grow while n < |c| t, then fall; the sums stop once a term is
+// below 1e-18 of its sum past that point.
+__device__ inline void argus_jp(double t, double c, double s, double* J, double* dJ) {
+  if (t <= 0.0) {
+    *J = 0.0;
+    *dJ = 0.0;
+    return;
+  }
+  const double y = fabs(c) * t, lt = d_log(t), ts = d_exp(s * lt);
+  double sum = 0.0, dsum = 0.0;
+  if (c <= 0.0) {
+    double T = 1.0 / s, H = 1.0 / s;
+    for (int n = 0; n < 4000; ++n) {
+      sum += T;
+      dsum += T * H;
+      if (n > y && T < 1e-18 * sum) break;
+      T *= y / (s + n + 1.0);
+      H += 1.0 / (s + n + 1.0);
+    }
+    const double e = d_exp(c * t);
+    *J = ts * e * sum;
+    *dJ = lt * *J - ts * e * dsum;
+  } else {
+    double a = 1.0;  // (ct)^n / n!
+    for (int n = 0; n < 4000; ++n) {
+      const double U = a / (s + n);
+      sum += U;
+      dsum += U / (s + n);
+      if (n > y && U < 1e-18 * sum) break;
+      a *= y / (n + 1.0);
+    }
+    *J = ts * sum;
+    *dJ = lt * *J - ts * dsum;
+  }
+}
+
+// gm: the leaf's gradient mask (ARGUS: bit 2 selects the general-p form)
+static __device__ __noinline__ bool leaf_lognorm(int type, int gm, const double* th, double lo,
                                     double hi, double* lnI, double* dln) {
   for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = 0.0;
   switch (type) {
@@ -235,10 +279,30 @@ static __device__ __noinline__ bool leaf_lognorm(int type, const double* th, dou
     }
     case RFL_ARGUS: {
       double m0 = th[0], c = th[1], p = th[2];
-      if (p != 0.5 || !(m0 > lo) || lo < 0.0) return false;
+      if (!(m0 > lo) || lo < 0.0) return false;
       double b = fmin(hi, m0);
       double ta = 1.0 - (lo / m0) * (lo / m0), tb = 1.0 - (b / m0) * (b / m0);
       double h = 0.5 * m0 * m0;
+      if (gm & 4) {  // p free: any p > 0, with d/dp
+        if (!(p > 0.0)) return false;
+        // I = (m0^2/2) [J(tau_a) - J(tau_b)]; d/dc takes J at p + 1; d/dm0
+        // adds the limits' motion: 2I/m0 + (lo^2/m0) tau_a^p e^{c tau_a}
+        // - (b'^2/m0) tau_b^p e^{c tau_b}
+        double Ja, Pa, Jb, Pb, Ka, Kb, dummy;
+        argus_jp(ta, c, p + 1.0, &Ja, &Pa);
+        argus_jp(tb, c, p + 1.0, &Jb, &Pb);
+        argus_jp(ta, c, p + 2.0, &Ka, &dummy);
+        argus_jp(tb, c, p + 2.0, &Kb, &dummy);
+        const double I = h * (Ja - Jb);
+        const double ea = ta > 0.0 ? d_exp(p * d_log(ta) + c * ta) : 0.0;
+        const double eb = tb > 0.0 ? d_exp(p * d_log(tb) + c * tb) : 0.0;
+        *lnI = d_log(I);
+        dln[0] = (2.0 * I / m0 + (lo * lo / m0) * ea - (b * b / m0) * eb) / I;
+        dln[1] = h * (Ka - Kb) / I;
+        dln[2] = h * (Pa - Pb) / I;
+        return I > 0.0 && isfinite(I);
+      }
+      if (p != 0.5) return false;  // a fixed p must be 1/2 (the kernels' p = 1/2 form)
       double Ja, Ka, Ea, Jb, Kb, Eb;
       argus_int2(ta, c, &Ja, &Ka, &Ea);
       argus_int2(tb, c, &Jb, &Kb, &Eb);
@@ -279,7 +343,7 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
     ok = isfinite(*lnI_out);
   } else {
-    ok = leaf_lognorm(L.type, th, L.lo, L.hi, lnI_out, dln);
+    ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
   }
   K.lnI[k] = *lnI_out;
   Real* pc = K.pc[k];
@@ -354,8 +418,10 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       pc[2] = (Real)(1.0 / (th[0] * th[0]));
       pc[3] = (Real)th[1];
       pc[4] = (Real)(2.0 / th[0]);
+      pc[5] = (Real)th[2];  // p (general-p form)
       K.dtheta[k][1] = (double)pc[3] - th[1];
-      K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (1/(2 tau) + c)(1 - tau)
+      if (L.gmask & 4) K.dtheta[k][2] = (double)pc[5] - th[2];
+      K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
     }
   }
@@ -588,7 +654,9 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   }
 }
 
-// ARGUS, p = 1/2: u = (1/2) log(x^2 tau) + c tau; -inf at and above m0.
+// ARGUS: u = log x + p log tau + c tau, -inf at and above m0.  Without the
+// p derivative (GM bit 2 clear) p is 1/2 and u = (1/2) log(x^2 tau) + c tau
+// (one log); with it, p = pc[5] and d u/d p = log tau.
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, Real& u,
                                            Real (&g)[RF_LEAF_MAXP]) {
@@ -597,15 +665,23 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
   Real sm = (pc[0] + x) + pc[1];
   Real tau = dm * sm * pc[2];
   bool ok = tau > Real(0);
-  u = ok ? Real(0.5) * F::log(x * x * tau) + pc[3] * tau : F::ninf();
+  const Real p = (GM & 4) ? pc[5] : Real(0.5);
+  if (GM & 4) {
+    const Real lt = F::log(tau);
+    u = ok ? F::log(x) + p * lt + pc[3] * tau : F::ninf();
+    g[2] = ok ? lt : Real(0);
+  } else {
+    u = ok ? Real(0.5) * F::log(x * x * tau) + pc[3] * tau : F::ninf();
+    g[2] = Real(0);
+  }
   g[1] = (GM & 2) ? (ok ? tau : Real(0)) : Real(0);
   if (GM & 1) {
     Real r = F::rcp(tau);
-    g[0] = ok ? (Real(0.5) * r + pc[3]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
+    g[0] = ok ? (p * r + pc[3]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
   } else {
     g[0] = Real(0);
   }
-  g[2] = g[3] = Real(0);
+  g[3] = Real(0);
 }
 
 // Johnson's SU: t = 1 + z^2, u = -(log t + w^2)/2 with w = gamma + delta asinh z
@@ -644,7 +720,8 @@ __device__ __forceinline__ void eval_leaf(int type, int gm, Real x,
     case RFL_CHEB: leaf_cheb<Real, 15>(x, pc, u, g); break;
     case RFL_CB: leaf_cb<Real, 15>(x, pc, u, g); break;
     case RFL_ARGUS:
-      if (gm & 1) leaf_argus<Real, 3>(x, pc, u, g);
+      if (gm & 4) leaf_argus<Real, 7>(x, pc, u, g);
+      else if (gm & 1) leaf_argus<Real, 3>(x, pc, u, g);
       else leaf_argus<Real, 2>(x, pc, u, g);
       break;
     case RFL_JOHNSON: leaf_johnson<Real, 15>(x, pc, u, g); break;

@@ -100,10 +100,10 @@ def test_unsupported_shapes(rf):
     s = {"obs": [(-1.0, 1.0)], "params": [0.1] * 5,
          "nodes": [{"type": "cheb", "obs": 0, "params": [0, 1, 2, 3, 4]}], "root": 0}
     assert rf.validate(s) == EUNSUPPORTED
-    # ARGUS with a free p
+    # ARGUS with a free p: the general-p form
     s = copy.deepcopy(datagen.cb_argus_spec())
     s["fixed"][6] = False
-    assert rf.validate(s, "f32", "fp32") == EUNSUPPORTED
+    assert rf.validate(s, "f32", "fp32") == 0
     # Add of an Add
     s = copy.deepcopy(datagen.gauss_exp_spec())
     s["nodes"].append({"type": "add_frac", "children": [2, 0], "params": [3]})

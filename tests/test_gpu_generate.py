@@ -112,6 +112,18 @@ def test_extended_model_many_toys(rf):
     compare(got.cpu().numpy()[:, :off[-1]], want, False)
 
 
+def test_argus_p_other_than_one_half_is_not_sampled(rf):
+    spec = single("argus", [5.29, -20.0, 0.8], 5.20, 5.29, [True, False, False])
+    G = rf.Graph(spec, "f64", "fp64")
+    pm = torch.tensor([[5.29, -20.0, 0.8]], dtype=torch.float64, device=DEV)
+    ev = G.generate_toys(pm, torch.tensor([[10]], dtype=torch.int64, device=DEV),
+                         torch.tensor([0, 10], dtype=torch.int64, device=DEV), seed=3)
+    assert G.status() & rf.STATUS_PARAM_DOMAIN
+    assert torch.isnan(ev).all()
+    assert oracle.generate(spec, [[5.29, -20.0, 0.8]], [[10]], [0, 10], seed=3,
+                           col_f32=False)[2] == oracle.EUNSUPPORTED
+
+
 def test_counts_that_do_not_fill_a_toy(rf):
     spec = datagen.gauss_exp_ext_spec()
     G = rf.Graph(spec, "f64", "fp64")

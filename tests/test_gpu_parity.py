@@ -41,6 +41,7 @@ SMALL = {
     "c3_noext": lambda: datagen.c3(n=50_001, extended=False),
     "c5": lambda: datagen.c5(3_000, 300_000),
     "johnson": lambda: datagen.johnson_exp(20_011, 80_000),
+    "c5_free_p": lambda: _free_p(datagen.c5(3_000, 300_000)),
 }
 OFF_MIN = {  # gradient checks away from the minimum
     "c1": [0.25, 1.1],
@@ -49,7 +50,16 @@ OFF_MIN = {  # gradient checks away from the minimum
     "c3_noext": [0.05, 1.55, -0.48, 0.21, -0.09, 0.055, 0.025],
     "c5": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.5, 3_050.0, 299_000.0],
     "johnson": [4.05, 0.78, -0.45, 1.62, -0.21, 19_800.0, 80_300.0],
+    "c5_free_p": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.58, 3_050.0, 299_000.0],
 }
+
+
+def _free_p(w):
+    """The C5 model with the ARGUS power p free (general-p form, d/dp)."""
+    spec = dict(w["spec"])
+    spec["fixed"] = list(spec["fixed"])
+    spec["fixed"][6] = False
+    return {**w, "spec": spec}
 _cache = {}
 
 
@@ -87,7 +97,7 @@ def test_nll_and_gradient_match_oracle(rf, name, prec, jit):
 
 @pytest.mark.parametrize("jit", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson", "c5_free_p"])
 def test_per_event_log_probability(rf, name, prec, jit):
     w, p, *_ = workload(name)
     sub = {**w, "cols": w["cols"][:, :20_011]}
@@ -568,3 +578,36 @@ def test_microbench_reports_positive_rates(rf):
     r = rf.microbench()
     assert all(v > 0 for v in r.values())
     assert r["fp32_fma"] > r["fp64_fma"]
+
+
+def test_argus_fixed_p_other_than_one_half_is_a_domain_error(rf):
+    """A fixed p runs the p = 1/2 form; another value sets the parameter-
+    domain bit (a free p takes any p > 0)."""
+    w, p, *_ = workload("c5")
+    G = rf.Graph(w["spec"], "f32", "fp32")
+    q = list(p)
+    q[6] = 0.7
+    nll, grad = G.nll(to_dev(w), params_dev(q))
+    assert nll.item() == float("inf") and G.status() & rf.STATUS_PARAM_DOMAIN
+    w2, p2, v2, *_ = workload("c5_free_p")
+    G2 = rf.Graph(w2["spec"], "f32", "fp64")
+    q2 = list(p2)
+    for bad in (0.0, -0.2):
+        q2[6] = bad
+        nll, _ = G2.nll(to_dev(w2), params_dev(q2))
+        assert nll.item() == float("inf") and G2.status() & rf.STATUS_PARAM_DOMAIN
+
+
+@pytest.mark.parametrize("pval", [0.5, 1.3])
+def test_argus_free_p_values(rf, pval):
+    """Free p away from 1/2, FP64 evaluation: NLL and gradient (d/dp
+    included) against the oracle."""
+    w, p, *_ = workload("c5_free_p")
+    q = list(p)
+    q[6] = pval
+    v, g, sc, rc = oracle.nll_scaled(w["spec"], q, w["cols"].astype(np.float64))
+    assert rc == 0
+    G = rf.Graph(w["spec"], "f32", "fp64")
+    nll, grad = G.nll(to_dev(w), params_dev(q))
+    assert rel_nll(float(nll.item()), v) <= TOL["fp64"]["nll"]
+    assert grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"])).max() <= TOL["fp64"]["grad"]
