@@ -308,7 +308,44 @@ def small_configs(rf, torch):
                 r["cold_us_median"] = statistics.median(ts)
             r["events_per_s_graph"] = n / (r["graph_us"] * 1e-6) if r.get("graph_us") else None
             res[f"{name}_{prec}"] = r
+    res["formula_leaves"] = formula_vs_builtin(rf, torch)
     return res
+
+
+def formula_vs_builtin(rf, torch):
+    """The C3 model (1e7 x 3 FP32 columns) with its Gaussian and Exponential
+    written as formula leaves, against the same model with the built-in
+    leaves: per-call time of each (the formula graph adds its normalisation
+    kernel)."""
+    import numpy as np
+
+    w = make_workload("c3")
+    spec = w["spec"]
+    alt = {**spec, "nodes": [dict(n) for n in spec["nodes"]]}
+    for n in alt["nodes"]:
+        if n["type"] == "gauss":
+            n.update(type="formula", formula="exp(-0.5*((x-p0)/p1)^2)")
+        elif n["type"] == "exp":
+            n.update(type="formula", formula="exp(p0*x)")
+    ev = torch.from_numpy(np.ascontiguousarray(w["cols"])).cuda()
+    params = torch.tensor(spec["params"], dtype=torch.float64, device="cuda")
+    out = {}
+    for tag, sp in (("builtin", spec), ("formula", alt)):
+        G = rf.Graph(sp, w["dtype"], "fp32")
+        G.tune(ev, params)
+        o = torch.empty(1 + len(sp["params"]), dtype=torch.float64, device="cuda")
+        for _ in range(10):
+            G.nll(ev, params, out=o)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(100):
+            G.nll(ev, params, out=o)
+        b.record()
+        torch.cuda.synchronize()
+        out[tag] = {"us_per_call": a.elapsed_time(b) * 10.0, "launches": G.last_launches(),
+                    "nll": float(o[0].item())}
+    return out
 
 
 def toy_bench(args, rf, torch, rank, world, pk):

@@ -325,8 +325,12 @@ static cudaKernel_t jit_toys(rf_graph* g, int ept, std::string* err) {
     if (k && g->toy_bulk) {  // its stage ring may use more than 48 KB of shared memory
       int optin = 0;
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
-      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      cudaFuncAttributes fa;  // the kernel's static shared memory comes off the opt-in total
+      cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
       if (e != cudaSuccess) {
         *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return nullptr;
