@@ -388,7 +388,7 @@ def toy_bench(args, rf, torch, rank, world, pk):
         dist.barrier()
     clk = clocks.stop()
     ms = max_over_ranks(a.elapsed_time(b), dist, "cuda") / args.steps
-    # roofline of the step (prep and segment kernels): FP32 issue for
+    # roofline of the step (prep + segment + finalize kernels): FP32 issue for
     # FP32 evaluation (columns read as FP32, rounded once at bind), with the
     # HBM figure beside it
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -404,7 +404,7 @@ def toy_bench(args, rf, torch, rank, world, pk):
         achieved = instr * n / (ms * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                     "unit": "G FP32-lane instr/s", "frac": achieved / peak, "traffic": None,
-                    "kernel": "rf_toys_jit (+ prep)",
+                    "kernel": "rf_toys_jit (+ prep, finalize)",
                     "algorithmic_instr_per_event": instr,
                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                     "launch_ms": ms, "hbm": hbm}
@@ -473,8 +473,6 @@ def main():
                     help="run the precompiled generic kernels instead of the per-graph ones")
     ap.add_argument("--min-blocks", type=int, default=0,
                     help="register budget of the specialised kernel (2, 3 or 4; with --no-tune)")
-    ap.add_argument("--blocks-per-sm", type=int, default=0,
-                    help="grid of the fused kernel in blocks per SM (1..8; with --no-tune)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="events for the CPU oracle baseline (0: the whole workload)")
@@ -519,8 +517,6 @@ def main():
         G.set_launch(ept=args.ept)
     if args.min_blocks:
         G.set_launch(min_blocks=args.min_blocks)
-    if args.blocks_per_sm:
-        G.set_launch(blocks_per_sm=args.blocks_per_sm)
     if not args.no_tune:
         tuned_ms = G.tune(ev, params)
     for _ in range(args.warmup):

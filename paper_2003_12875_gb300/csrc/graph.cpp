@@ -347,7 +347,6 @@ static void free_work(rf_graph* g) {
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
-  cudaFree(g->work.toy_ticket);
   cudaFree(g->bound32);
   cudaFree(g->stage);
   cudaFree(g->plain_buf);
@@ -706,10 +705,8 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   cudaFree(g->work.toy_consts);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
-  cudaFree(g->work.toy_ticket);
   g->work.toy_consts = nullptr;
   g->work.adam_m1 = g->work.adam_m2 = nullptr;
-  g->work.toy_ticket = nullptr;
   g->bound = false;
   g->max_toys = 0;
   // one row per (warp, toy) segment: at most (launch warps) + toys, and a
@@ -729,8 +726,6 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m1, sizeof(double) * np * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
-  if (e == cudaSuccess)
-    e = cudaMalloc(&g->work.toy_ticket, sizeof(unsigned int) * (size_t)max_toys);
   if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
   const void* toy_events = events;
   if (g->eval == RF_EVAL_FP32 && g->coldt == RF_F64) {

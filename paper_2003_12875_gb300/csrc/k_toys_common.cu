@@ -1,5 +1,4 @@
-// Toy-study orchestration: the prep kernel, then the segment kernel (which
-// also finishes every toy).
+// Toy-study orchestration: prep kernel, segment kernel, finalize kernel.
 #include <algorithm>
 #include <cstdlib>
 
@@ -34,6 +33,24 @@ size_t rf_consts_size(int eval) {
   return eval ? sizeof(RfConsts<double>) : sizeof(RfConsts<float>);
 }
 
+namespace {
+
+template <typename Real>
+int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, int64_t stride,
+                    int64_t warps, double* pm, double* out, RfWork W,
+                    const double* adam_scale, double adam_lr, cudaStream_t st) {
+  const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, 32 toys per block
+  switch (P.n_leaves) {
+    case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 3: rf::toy_finalize_kernel<Real, 3><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 4: rf::toy_finalize_kernel<Real, 4><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
 
 int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg& cfg,
                       int num_sms, const void* events, int64_t n_events,
@@ -69,11 +86,7 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   const int64_t room = max_rows - toys;
   if (wpb < 1 || room < wpb) return (int)cudaErrorInvalidValue;
   if (grid * wpb > room) grid = room / wpb;
-  // the segment kernel finishes the toys: their outputs and the fit step
-  W.toy_out = out;
-  W.toy_pm = pm;
-  W.adam_scale = adam_scale;
-  W.adam_lr = adam_lr;
+  const int64_t warps = grid * wpb;
 
   // prep: blocks of one warp per leaf and 32 toys
   const int pb = 32 * std::max(P.n_leaves, 1);
@@ -82,11 +95,11 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   if (eval)
     rf::toy_prep_kernel<double><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
                                                    static_cast<RfConsts<double>*>(W.toy_consts),
-                                                   W.status, at, W.toy_ticket);
+                                                   W.status, at);
   else
     rf::toy_prep_kernel<float><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
                                                   static_cast<RfConsts<float>*>(W.toy_consts),
-                                                  W.status, at, W.toy_ticket);
+                                                  W.status, at);
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
   const int g = (int)grid;
@@ -101,6 +114,11 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
     rc = rf_toys_f64_c32(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
   else
     rc = rf_toys_f64_c64(P, cfg.ept, g, cfg.block, vec, stages, smem, events, n_events, offsets, toys, W, st);
-  if (launches) *launches = 2;
+  if (rc) return rc;
+  rc = eval ? launch_finalize<double>(P, offsets, toys, n_events, warps, pm, out, W, adam_scale,
+                                      adam_lr, st)
+            : launch_finalize<float>(P, offsets, toys, n_events, warps, pm, out, W, adam_scale,
+                                     adam_lr, st);
+  if (launches) *launches = 3;
   return rc;
 }

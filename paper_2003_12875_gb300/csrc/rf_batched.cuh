@@ -5,10 +5,9 @@
 //                   the toy's offsets.
 //  segment kernel   the toys' events split evenly over the launch's warps;
 //                   each warp writes one FP64 row per toy its range meets
-//                   (launched as a programmatic dependent of the prep kernel);
-//                   the warp that writes a toy's last row sums its rows in
-//                   order and runs the FP64 epilogue (NLL, gradient),
-//                   optionally one Adam step.
+//                   (launched as a programmatic dependent of the prep kernel).
+//  finalize kernel  one warp per toy: its rows summed in order, the FP64
+//                   epilogue (NLL, gradient), optionally one Adam step.
 // Results depend only on the inputs and the launch shape, not on timing.
 #pragma once
 #include "rf_toys.cuh"
@@ -25,7 +24,7 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
                                               const int64_t* __restrict__ offsets,
                                               int32_t toys, int64_t n_events,
                                               RfConsts<Real>* consts, unsigned int* status,
-                                              int32_t* adam_t, unsigned int* ticket) {
+                                              int32_t* adam_t) {
   asm volatile("griddepcontrol.launch_dependents;");
   __shared__ double lnI_s[RF_MAXL][32];
   __shared__ int ok_s[RF_MAXL][32];
@@ -39,7 +38,6 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
   }
   __syncthreads();
   if (k == 0 && t < toys) {
-    ticket[t] = 0u;  // rows of this call's segment kernel counted from zero
     const int64_t b = offsets[t], e = offsets[t + 1];
     if (b < 0 || e < b || e > n_events) atomicOr(status, RF_STATUS_NONFINITE_BIT);
     double l[RF_MAXL];
@@ -52,12 +50,86 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
   }
 }
 
+// Finalize kernel: one thread per toy (the FP64 unit takes one warp
+// instruction at a time whatever the number of active lanes, so 32 toys per
+// warp cost what one does).  The thread sums the toy's segment rows in row
+// order, runs the FP64 epilogue into out row t and, for a fit, applies one
+// Adam step (Kingma & Ba 2015) to the toy's free parameters in units of its
+// scale row.
+template <typename Real, int NL>
+__device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
+                                                  const int64_t* __restrict__ offsets,
+                                                  int32_t toys, int64_t stride, int64_t warps,
+                                                  double* pm, double* out, RfWork& W,
+                                                  const double* __restrict__ adam_scale,
+                                                  double adam_lr) {
+  constexpr int NA = RF_NACC(NL);
+  // the block's (up to 32) toys' constants: one bulk copy into shared memory
+  // (RfConsts is a multiple of 16 bytes, the array 256-byte aligned)
+  __shared__ RfConsts<Real> Ks[32];
+  __shared__ __align__(8) uint64_t bar;
+  {
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t nt = toys - t0 < 32 ? toys - t0 : 32;
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = (uint32_t)(nt * (int64_t)sizeof(RfConsts<Real>));
+      bulk::bar_init(&bar, 1);
+      bulk::fence_bar_init();
+      bulk::arrive_expect_tx(&bar, bytes);
+      bulk::copy(Ks, static_cast<const RfConsts<Real>*>(W.toy_consts) + t0, bytes, &bar);
+    }
+    __syncwarp();
+    if (!bulk::wait(&bar, 0u)) {
+      if (threadIdx.x == 0) atomicOr(W.status, RF_STATUS_TIMEOUT_BIT);
+      return;
+    }
+  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= toys) return;
+  const ToySplit S = toy_split(offsets, toys, stride, warps);
+  int64_t ob = toy_off(offsets, t, stride), oe = toy_off(offsets, t + 1, stride);
+  ob = ob < S.B ? S.B : ob;
+  oe = oe > S.E ? S.E : oe;
+  if (oe < ob) oe = ob;
+  double tot[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) tot[i] = 0.0;
+  if (oe > ob) {  // a toy meets a few warp ranges: plain FP64 sums of a few rows
+    const int64_t r1 = S.warp_of(oe - 1) + t;
+    for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
+      const double* row = W.partials + r * RF_NACC_MAX;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) tot[i] += __ldcg(row + i);
+    }
+  }
+  double* row = out + t * (int64_t)(1 + P.n_par);
+  epilogue<Real, NL>(P, Ks[threadIdx.x], tot, oe - ob, row, row + 1, W.status);
+  if (adam_scale && isfinite(row[0])) {
+    const int step = *W.adam_t;
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    double* th = pm + t * (int64_t)P.n_par;
+    double* m1 = W.adam_m1 + t * (int64_t)P.n_par;
+    double* m2 = W.adam_m2 + t * (int64_t)P.n_par;
+    for (int p = 0; p < P.n_par; ++p) {
+      const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
+      if (fx) continue;
+      const double sc = adam_scale[t * (int64_t)P.n_par + p];
+      const double gsc = row[1 + p] * sc;
+      m1[p] = b1 * m1[p] + (1.0 - b1) * gsc;
+      m2[p] = b2 * m2[p] + (1.0 - b2) * gsc * gsc;
+      const double mh = m1[p] / c1, vh = m2[p] / c2;
+      th[p] -= sc * adam_lr * mh / (sqrt(vh) + eps);
+    }
+  }
+}
+
 template <typename Real>
 __global__ void toy_prep_kernel(const RfProgram P, const double* __restrict__ pm,
                                 const int64_t* __restrict__ offsets, int32_t toys,
                                 int64_t n_events, RfConsts<Real>* consts,
-                                unsigned int* status, int32_t* adam_t, unsigned int* ticket) {
-  toy_prep_body<Real>(P, pm, offsets, toys, n_events, consts, status, adam_t, ticket);
+                                unsigned int* status, int32_t* adam_t) {
+  toy_prep_body<Real>(P, pm, offsets, toys, n_events, consts, status, adam_t);
 }
 
 template <typename Real, typename Col, int NL, int EPT>
@@ -66,6 +138,14 @@ __global__ void __launch_bounds__(256)
                        const int64_t* __restrict__ offsets, int32_t toys, int stages, RfWork W) {
   toy_segment_body_reg<GenericModel<NL>, Real, Col, EPT>(P, ev, stride, vec, offsets, toys, stages,
                                                          W);
+}
+
+template <typename Real, int NL>
+__global__ void __launch_bounds__(256)
+    toy_finalize_kernel(const RfProgram P, const int64_t* __restrict__ offsets, int32_t toys,
+                        int64_t stride, int64_t warps, double* pm, double* out, RfWork W,
+                        const double* __restrict__ adam_scale, double adam_lr) {
+  toy_finalize_body<Real, NL>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr);
 }
 
 template <typename Real, typename Col, int NL, int EPT>

@@ -116,13 +116,6 @@ struct RfWork {
   // single dataset: constants from the separate prologue kernel (NULL: each
   // block computes them itself)
   void* consts;            // [1] RfConsts<Real>
-  // toy studies, set for each call: the segment kernel's warp that writes the
-  // last of a toy's rows finishes the toy (epilogue, optional Adam step)
-  unsigned int* toy_ticket;  // [max_toys] rows written so far (zeroed by prep)
-  double* toy_out;           // [toys * (1 + n_par)] NLL and gradient per toy
-  double* toy_pm;            // [toys * n_par] parameter rows (the fit updates them)
-  const double* adam_scale;  // [toys * n_par] units of the fit step; NULL: no step
-  double adam_lr;
 };
 
 struct RfLaunchCfg {

@@ -16,8 +16,8 @@ namespace rf {
 // partials, which no other segment uses (w + t counts the warp starts and toy
 // starts before the segment).  Toy t's segments are therefore the rows w + t
 // for w = warp_of(offsets[t]) .. warp_of(offsets[t+1] - 1), summed in that
-// order by the warp that writes the last of them.  Every warp reads one
-// contiguous stretch of the columns, and no warp waits on another.
+// order by the finalize kernel.  Every warp reads one contiguous stretch of
+// the columns, and no warp waits on another.
 struct ToySplit {
   int64_t B, E, N;
   __device__ __forceinline__ int64_t start(int64_t w) const {
@@ -215,96 +215,6 @@ __device__ __forceinline__ void eval_chunk(const RfProgram& P, const EvalConsts<
 // seek() moves to the toy holding event p, writing the finished toy's row
 // (when it had events) and skipping empty toys; false only when p lies past
 // the last toy (a non-monotone offset table).
-// Finishing a toy inside the segment kernel.  Each toy's rows are written by
-// the warps whose event ranges meet it; the one that writes the last row (a
-// per-toy ticket, zeroed by the prep kernel, counts them) adds the rows in row
-// order, runs the FP64 epilogue with one lane per term and per gradient
-// component, and, in a fit, takes the toy's Adam step (Kingma & Ba 2015,
-// Algorithm 1) on its free parameters in units of its scale row.  Toys with no
-// events are finished by a strided pass over all warps after streaming.
-template <typename Real, int NL>
-struct ToyEnd {
-  static constexpr int NA = RF_NACC(NL);
-  const RfProgram* P;
-  const RfConsts<Real>* consts;
-  const int64_t* offsets;
-  int64_t stride;
-  int32_t toys;
-  ToySplit S;
-  RfWork* W;
-  double* red;  // [RF_NACC_MAX] of this warp, shared memory
-
-  // the toy's events, clamped to the split's [B, E)
-  __device__ __forceinline__ void range(int32_t t, int64_t& ob, int64_t& oe) const {
-    ob = toy_off(offsets, t, stride);
-    oe = toy_off(offsets, (int64_t)t + 1, stride);
-    ob = ob < S.B ? S.B : ob;
-    oe = oe > S.E ? S.E : oe;
-    if (oe < ob) oe = ob;
-  }
-
-  __device__ void finish(int32_t t, int64_t ob, int64_t oe) const {
-    const int lane = threadIdx.x & 31;
-    if (lane < NA) {
-      double s = 0.0;
-      if (oe > ob) {
-        const int64_t r1 = S.warp_of(oe - 1) + t;
-        for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r)
-          s += __ldcg(W->partials + r * RF_NACC_MAX + lane);
-      }
-      red[lane] = s;
-    }
-    __syncwarp();
-    double* row = W->toy_out + (int64_t)t * (1 + P->n_par);
-    epilogue_warp<Real, NL>(*P, consts[t], red, oe - ob, row, row + 1, W->status);
-    __syncwarp();
-    if (W->adam_scale && isfinite(row[0])) {
-      const int step = *W->adam_t;
-      const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
-      const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
-      const int64_t base = (int64_t)t * P->n_par;
-      for (int p = lane; p < P->n_par; p += 32) {
-        const bool fx = p < 64 ? ((P->fixed_lo >> p) & 1) : ((P->fixed_hi >> (p - 64)) & 1);
-        if (fx) continue;
-        const double sc = W->adam_scale[base + p];
-        const double gsc = row[1 + p] * sc;
-        const double m1 = b1 * W->adam_m1[base + p] + (1.0 - b1) * gsc;
-        const double m2 = b2 * W->adam_m2[base + p] + (1.0 - b2) * gsc * gsc;
-        W->adam_m1[base + p] = m1;
-        W->adam_m2[base + p] = m2;
-        const double mh = m1 / c1, vh = m2 / c2;
-        W->toy_pm[base + p] -= sc * W->adam_lr * mh / (sqrt(vh) + eps);
-      }
-    }
-    __syncwarp();
-  }
-
-  // called by the whole warp after it wrote its row of toy t
-  __device__ __noinline__ void row_written(int32_t t) const {
-    int64_t ob, oe;
-    range(t, ob, oe);
-    const unsigned need = (unsigned)(S.warp_of(oe - 1) - S.warp_of(ob) + 1);
-    __syncwarp();
-    __threadfence();
-    unsigned last = 0;
-    if ((threadIdx.x & 31) == 0) last = atomicAdd(W->toy_ticket + t, 1u) + 1u == need ? 1u : 0u;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      finish(t, ob, oe);
-    }
-  }
-
-  // toys without events: warp gw of gn (all warps of the grid)
-  __device__ __noinline__ void finish_empty(int64_t gw, int64_t gn) const {
-    for (int64_t t = gw; t < toys; t += gn) {
-      int64_t ob, oe;
-      range((int32_t)t, ob, oe);
-      if (oe == ob) finish((int32_t)t, ob, ob);
-    }
-  }
-};
-
 template <class M, typename Real>
 struct ToyState {
   static constexpr int NL = M::NL_;
@@ -314,7 +224,6 @@ struct ToyState {
   bool bad, any;
   EvalConsts<Real, NL> E;
   Acc<Real, NA, M::AMASK> acc;
-  const ToyEnd<Real, NL>* fin;
   __device__ __forceinline__ void open(const RfConsts<Real>* consts, const int64_t* offsets,
                                        int64_t stride, int32_t tt) {
     t = tt;
@@ -326,10 +235,7 @@ struct ToyState {
     any = false;
   }
   __device__ __forceinline__ void close(double* rows) {
-    if (any) {
-      WarpRow<Real, NA, M::AMASK>::write(acc, rows + (int64_t)t * RF_NACC_MAX);
-      fin->row_written(t);
-    }
+    if (any) WarpRow<Real, NA, M::AMASK>::write(acc, rows + (int64_t)t * RF_NACC_MAX);
   }
   __device__ __forceinline__ bool seek(const RfConsts<Real>* consts, const int64_t* offsets,
                                        int64_t stride, int32_t toys, int64_t p, double* rows) {
@@ -344,8 +250,7 @@ struct ToyState {
 // Segment kernel: warp w streams [start(w), start(w+1)) through its stage
 // ring (chunks of 32*EPT events from the first 16-byte-aligned event; the
 // ragged ends are read directly), switching toy constants at toy boundaries
-// and writing one FP64 row per toy it meets; the warp that writes a toy's last
-// row finishes the toy (ToyEnd).  The bulk copies of the first
+// and writing one FP64 row per toy it meets.  The bulk copies of the first
 // stages and the search for the first toy need only the offsets and the
 // events, so they are issued before the wait for the prep kernel.
 // Dynamic shared memory: warps * (kMaxStages barriers + S stages of
@@ -397,12 +302,10 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
   }
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!active) return;
+
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  __shared__ double fin_red[8][RF_NACC_MAX];
-  const ToyEnd<Real, NL> fin{&P, consts, offsets, stride, toys, Sp, &W, fin_red[wib]};
-  if (active) {
   ToyState<M, Real> T;
-  T.fin = &fin;
   T.open(consts, offsets, stride, t);
   double* rows = W.partials + w * RF_NACC_MAX;  // row of (w, t) = rows + t * RF_NACC_MAX
   // ragged head, straight from the columns
@@ -464,8 +367,6 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
     p = q;
   }
   T.close(rows);
-  }
-  fin.finish_empty(w, (int64_t)gridDim.x * wpb);
 }
 
 // Segment kernel, register-streaming form: the same warp ranges, toy walk
@@ -492,12 +393,9 @@ __device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
     t = find_toy(offsets, toys, stride, wb);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!active) return;
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
-  __shared__ double fin_red[8][RF_NACC_MAX];
-  const ToyEnd<Real, M::NL_> fin{&P, consts, offsets, stride, toys, Sp, &W, fin_red[wib]};
-  if (active) {
   ToyState<M, Real> T;
-  T.fin = &fin;
   T.open(consts, offsets, stride, t);
   double* rows = W.partials + w * RF_NACC_MAX;
   for (int64_t p = wb; p < we;) {
@@ -520,8 +418,6 @@ __device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
     p = q;
   }
   T.close(rows);
-  }
-  fin.finish_empty(w, (int64_t)gridDim.x * wpb);
 }
 
 }  // namespace rf

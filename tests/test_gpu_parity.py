@@ -374,7 +374,7 @@ def test_batched_toys_match_oracle_and_single(rf, prec, shape, jit):
     off = torch.from_numpy(w["offsets"]).to(DEV)
     pmd = torch.from_numpy(pm).to(DEV)
     got = G.nll_batched(off, pmd).cpu().numpy()
-    assert G.last_launches() == 2   # prep, segment (which finishes the toys)
+    assert G.last_launches() == 3
     for t in range(64):
         b, e = w["offsets"][t], w["offsets"][t + 1]
         _, gref, sc, _ = oracle.nll_scaled(w["spec"], pm[t], w["cols"][:, b:e])
@@ -508,7 +508,7 @@ def test_fit_toys_follows_oracle_adam(rf):
     pmd = torch.from_numpy(pm0.copy()).to(DEV)
     G.fit_toys(torch.from_numpy(w["offsets"]).to(DEV), pmd,
                torch.from_numpy(scale).to(DEV), iters, lr)
-    assert G.last_launches() == 2 * iters
+    assert G.last_launches() == 3 * iters
     got = pmd.cpu().numpy()
     for t in range(16):
         b, e = w["offsets"][t], w["offsets"][t + 1]
