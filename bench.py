@@ -473,6 +473,8 @@ def main():
                     help="run the precompiled generic kernels instead of the per-graph ones")
     ap.add_argument("--min-blocks", type=int, default=0,
                     help="register budget of the specialised kernel (2, 3 or 4; with --no-tune)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="grid of the fused kernel in blocks per SM (1..8; with --no-tune)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="events for the CPU oracle baseline (0: the whole workload)")
@@ -517,6 +519,8 @@ def main():
         G.set_launch(ept=args.ept)
     if args.min_blocks:
         G.set_launch(min_blocks=args.min_blocks)
+    if args.blocks_per_sm:
+        G.set_launch(blocks_per_sm=args.blocks_per_sm)
     if not args.no_tune:
         tuned_ms = G.tune(ev, params)
     for _ in range(args.warmup):

@@ -176,8 +176,9 @@ rf_status rf_graph_destroy(rf_graph* g);
  *   nll     dev [1] FP64
  *   grad    dev [n_params] FP64 or NULL; entries of fixed params are 0
  * Two launches on `stream`, no allocation, no host sync: an FP64 prologue
- * (normalisations, coefficients) and the fused event kernel.  The prologue
- * is a programmatic dependent of the kernel before it in the stream, so that
+ * (normalisations, coefficients) and the fused event kernel (with formula
+ * leaves a third before them: their normalisation).  The first kernel of a
+ * call is a programmatic dependent of the kernel before it in the stream, so that
  * back-to-back calls overlap a call's FP64 prologue with the previous call's
  * event pass; it reads `params` while that kernel may still run, so params
  * must not be written by the kernels of the call immediately before on the

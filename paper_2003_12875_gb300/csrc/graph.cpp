@@ -569,7 +569,7 @@ static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, i
                                 g->formula_buf + RF_FORMULA_NV * RF_MAXL, g->formula_ticket, st);
     if (ne) return ne;
   }
-  int pe = rf_launch_prologue(P, g->eval, params, g->work, g->n_formula == 0, st);
+  int pe = rf_launch_prologue(P, g->eval, params, g->work, true, st);
   if (pe) return pe;
   if (g->jit) {
     cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)][cfg.min_blocks - 2];

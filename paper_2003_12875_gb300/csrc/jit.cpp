@@ -404,8 +404,18 @@ int rf_jit_launch_norm(cudaKernel_t k, const RfProgram& P, int n_formula, const 
                        double* part, unsigned int* ticket, cudaStream_t st) {
   RfProgram Pc = P;
   void* args[] = {&Pc, &params, &part, &ticket};
-  return (int)cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(RF_FORMULA_BLOCKS, n_formula),
-                               dim3(128), args, 0, st);
+  // a programmatic dependent of the kernel before it (as the prologue is);
+  // the prologue after it waits for it before reading the integrals
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(RF_FORMULA_BLOCKS, n_formula);
+  lc.blockDim = dim3(128);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void*>(k), args);
 }
 
 int rf_jit_launch_logp(cudaKernel_t k, const RfProgram& P, const void* events, int64_t n,

@@ -18,6 +18,9 @@ __device__ __forceinline__ void prologue_body(const RfProgram& P, const double* 
   __shared__ RfConsts<Real> K;
   __shared__ double lnI[RF_MAXL];
   __shared__ int ok[RF_MAXL];
+  // formula leaves: their integrals come from the normalisation kernel just
+  // before, so wait for it first
+  if (P.formula_norm) asm volatile("griddepcontrol.wait;" ::: "memory");
   block_prologue(P, params, K, lnI, ok);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));

@@ -99,7 +99,7 @@ __device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
     for (int64_t r = S.warp_of(ob) + t; r <= r1; ++r) {
       const double* row = W.partials + r * RF_NACC_MAX;
 #pragma unroll
-      for (int i = 0; i < NA; ++i) tot[i] += __ldcg(row + i);
+      for (int i = 0; i < NA; ++i) tot[i] += WarpRow<Real, NA, 0>::value(__ldcg(row + i));
     }
   }
   double* row = out + t * (int64_t)(1 + P.n_par);

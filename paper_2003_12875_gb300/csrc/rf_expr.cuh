@@ -274,8 +274,10 @@ template <class F, typename Real, int GM>
 __device__ __forceinline__ void formula_leaf(Real x, const Real* __restrict__ pc, Real& u,
                                              Real (&g)[RF_LEAF_MAXP]) {
   const auto f = F::template eval<Real>(x, pc);
-  u = fx::log(f.v);
-  const Real r = Real(1) / f.v;
+  // the log and reciprocal of the built-in leaves (hardware approximations
+  // in FP32); the formula's own functions keep CUDA's accurate versions
+  u = Fn<Real>::log(f.v);
+  const Real r = Fn<Real>::rcp(f.v);
 #pragma unroll
   for (int j = 0; j < RF_LEAF_MAXP; ++j)
     g[j] = (j < F::NP && ((GM >> j) & 1)) ? f.d[j < F::NP ? j : 0] * r : Real(0);
@@ -297,6 +299,7 @@ __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
   constexpr int NP = F::NP, NV = 1 + NP;
   __shared__ double red[4][NV];
   __shared__ int s_last;
+  asm volatile("griddepcontrol.launch_dependents;");
   const RfLeafProg& L = P.leaf[k];
   double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
   for (int j = 0; j < NP; ++j) th[j] = params[L.par[j]];

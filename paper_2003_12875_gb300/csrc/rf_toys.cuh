@@ -80,25 +80,36 @@ __device__ inline int32_t find_toy(const int64_t* __restrict__ off, int32_t toys
 // FP32 evaluation, FP64 otherwise); lane 0 writes the FP64 row.
 template <typename Real, int NA, unsigned long long MASK>
 struct WarpRow;
+// FP32 rows hold each sum as its FP32 pair (h, l) packed into the 64-bit slot:
+// the segment kernel then issues no FP64 instruction (one takes its
+// sub-partition's FP64 unit for ~64 cycles, stalling the FP32 event loop of
+// the warps beside it), and the finalize kernel widens h + l.
 template <int NA, unsigned long long MASK>
 struct WarpRow<float, NA, MASK> {
   static __device__ __forceinline__ void write(const Acc<float, NA, MASK>& acc, double* row) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      double r = 0.0;
+      float h = 0.0f, l = 0.0f;
       if ((MASK >> i) & 1ull) {
-        float h = acc.s[i], l = -acc.c[i];
+        h = acc.s[i];
+        l = -acc.c[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
           const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
           ds_add(h, l, h2, l2);
         }
-        r = (double)h + (double)l;
       }
-      if (lane == 0) row[i] = r;
+      if (lane == 0)
+        reinterpret_cast<unsigned long long*>(row)[i] =
+            ((unsigned long long)__float_as_uint(l) << 32) | __float_as_uint(h);
     }
+  }
+  static __device__ __forceinline__ double value(double stored) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(stored);
+    return (double)__uint_as_float((unsigned)(b & 0xffffffffull)) +
+           (double)__uint_as_float((unsigned)(b >> 32));
   }
 };
 template <int NA, unsigned long long MASK>
@@ -111,6 +122,7 @@ struct WarpRow<double, NA, MASK> {
       if (lane == 0) row[i] = r;
     }
   }
+  static __device__ __forceinline__ double value(double stored) { return stored; }
 };
 
 // ------------------------------------------------ bulk-copy event streaming
