@@ -574,16 +574,8 @@ static int fused_dispatch(rf_graph* g, const RfLaunchCfg& cfg, const void* ev, i
   if (g->jit) {
     cudaKernel_t k = g->jk_fused[ept_index(g->eval, g->coldt, cfg.ept)][cfg.min_blocks - 2];
     if (!k) return (int)cudaErrorInvalidValue;  // compiled by compile/set_launch/tune
-    if (void* kc = rf_jit_kconst_ptr(k)) {
-      // constants into the kernel's constant bank, then the kernel in stream order
-      cudaError_t ce = cudaMemcpyAsync(kc, g->work.consts, rf_consts_size(g->eval),
-                                       cudaMemcpyDeviceToDevice, st);
-      if (ce != cudaSuccess) return (int)ce;
-      return rf_jit_launch_fused(k, P, g->coldt, cfg, g->num_sms, ev, n, params, g->work, nll,
-                                 grad, false, st);
-    }
     return rf_jit_launch_fused(k, P, g->coldt, cfg, g->num_sms, ev, n, params, g->work, nll,
-                               grad, true, st);
+                               grad, st);
   }
   if (g->eval == RF_EVAL_FP32)
     return g->coldt == RF_F32

@@ -35,7 +35,6 @@ namespace {
 
 std::mutex g_mu;
 std::map<std::string, cudaKernel_t> g_cache;      // (device | source) -> kernel
-std::map<cudaKernel_t, void*> g_kconst;           // kernel -> its module's rf_kc
 std::vector<cudaLibrary_t> g_libs;                // kept loaded for the process
 
 const char* leaf_fn(int type) {
@@ -67,17 +66,6 @@ std::string cache_dir() {
 }
 
 }  // namespace
-
-bool rf_jit_kconst() {
-  const char* v = getenv("RF_KCONST");
-  return v && v[0] == '1';
-}
-
-void* rf_jit_kconst_ptr(cudaKernel_t k) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_kconst.find(k);
-  return it == g_kconst.end() ? nullptr : it->second;
-}
 
 namespace {
 
@@ -147,22 +135,11 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
     return o.str();
   }
   o << "// ---- model emitted for this graph\n";
-  // The fused kernel may read the per-call constants from this module's
-  // constant bank (rf_kc, filled by a copy after the prologue): FP32
-  // instructions then take them as operands instead of holding them in
-  // registers.
-  const bool kconst = kind == RF_JIT_FUSED && rf_jit_kconst();
-  const char* R = eval ? "double" : "float";
-  if (kconst) o << "__constant__ RfConsts<" << R << "> rf_kc;\n";
   o << "struct RfModel {\n  static constexpr int NL_ = " << NL << ";\n"
     << "  static constexpr int NCOL = " << P.n_cols << ";\n"
     << "  static constexpr unsigned long long AMASK = " << amask << "ull;\n"
-    << "  static constexpr bool KCONST = " << (kconst ? "true" : "false") << ";\n";
-  if (kconst)
-    o << "  template <typename Real>\n  static __device__ __forceinline__ const RfConsts<" << R
-      << ">& kconst() { return rf_kc; }\n";
-  o << "  template <typename Real, class KT>\n  static __device__ __forceinline__ void event(const "
-       "RfProgram& P, const KT& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
+    << "  template <typename Real>\n  static __device__ __forceinline__ void event(const RfProgram& P, "
+       "const rf::EvalConsts<Real, NL_>& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
   for (int k = 0; k < NL; ++k) {
     const RfLeafProg& L = P.leaf[k];
     o << "    Real u" << k << ", g" << k << "[4];\n    ";
@@ -200,6 +177,7 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
         o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += w[" << P.leaf[k].comp << "] * g" << k
           << "[" << j << "];\n";
   o << "  }\n};\n";
+  const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
   // The fused kernel is declared for min_blocks resident blocks of 256
   // threads per SM: a register budget of 80 (3 blocks) or 128 (2 blocks).
@@ -367,12 +345,6 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval
     }
     g_libs.push_back(lib);
     g_cache[key] = k;
-    if (kind == RF_JIT_FUSED) {  // the constant bank of the per-call constants, if any
-      void* kc = nullptr;
-      size_t kcb = 0;
-      if (cudaLibraryGetGlobal(&kc, &kcb, lib, "rf_kc") == cudaSuccess) g_kconst[k] = kc;
-      else cudaGetLastError();
-    }
   }
   if (regs) {
     cudaFuncAttributes a;
@@ -383,7 +355,7 @@ cudaKernel_t rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval
 
 int rf_jit_launch_fused(cudaKernel_t k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
-                        RfWork W, double* nll, double* grad, bool chained, cudaStream_t st) {
+                        RfWork W, double* nll, double* grad, cudaStream_t st) {
   int vec = 0;
   int64_t head = 0;
   rf_vec_plan(P, events, n, coldt ? 8 : 4, &vec, &head);
@@ -399,7 +371,7 @@ int rf_jit_launch_fused(cudaKernel_t k, const RfProgram& P, int coldt, const RfL
   lc.blockDim = dim3(cfg.block);
   lc.stream = st;
   cudaLaunchAttribute at[1];
-  if (chained) {  // dependent of the prologue kernel launched just before
+  if (W.consts) {  // dependent of the prologue kernel launched just before
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;

@@ -208,21 +208,15 @@ bool rf_jit_compile_only(const RfProgram& P, const RfFormulaCode* fc, int eval, 
                          int kind, int ept, int min_blocks, std::string* err);
 rf_cuda_kernel rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
                              int kind, int ept, int min_blocks, int* regs, std::string* err);
-// fused kernels read their per-call constants from the module's constant bank
-// (RF_KCONST=1); rf_jit_kconst_ptr: that bank's device address for a kernel
-// (NULL when it has none)
-bool rf_jit_kconst();
-void* rf_jit_kconst_ptr(rf_cuda_kernel k);
 // compiles the sources not yet in the on-disk cache, in parallel threads
 void rf_jit_precompile(const std::vector<std::string>& sources);
 // normalisation kernel of the formula leaves (grid RF_FORMULA_BLOCKS x leaves)
 int rf_jit_launch_norm(rf_cuda_kernel k, const RfProgram& P, int n_formula,
                        const double* params, double* part, unsigned int* ticket,
                        rf_cuda_stream st);
-// chained: launched as a programmatic dependent of the prologue just before
 int rf_jit_launch_fused(rf_cuda_kernel k, const RfProgram& P, int coldt, const RfLaunchCfg& cfg,
                         int num_sms, const void* events, int64_t n, const double* params,
-                        RfWork W, double* nll, double* grad, bool chained, rf_cuda_stream st);
+                        RfWork W, double* nll, double* grad, rf_cuda_stream st);
 // segment kernel of a toy study, as a programmatic dependent of the prep
 // kernel launched just before it
 int rf_jit_launch_toys(rf_cuda_kernel k, const RfProgram& P, int grid, int block, int vec,

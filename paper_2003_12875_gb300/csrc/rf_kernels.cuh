@@ -23,13 +23,11 @@ struct GenericModel {
   static constexpr int NL_ = NL;
   static constexpr int NCOL = NL;
   static constexpr unsigned long long AMASK = ~0ull;
-  static constexpr bool KCONST = false;  // constants in registers (EvalConsts)
 
-  // leaves -> components -> log-sum-exp -> adjoint weights, into q.  KT:
-  // EvalConsts (registers) or RfConsts (the constant bank of a specialised
-  // kernel); both name the per-event fields alike.
-  template <typename Real, class KT>
-  static __device__ __forceinline__ void event(const RfProgram& P, const KT& K,
+  // leaves -> components -> log-sum-exp -> adjoint weights, into q
+  template <typename Real>
+  static __device__ __forceinline__ void event(const RfProgram& P,
+                                               const EvalConsts<Real, NL>& K,
                                                const Real (&xc)[NL],
                                                Real (&q)[RF_NACC(NL)]) {
     typedef Fn<Real> F;
@@ -226,8 +224,9 @@ struct BlockRow<double, NA, MASK> {
 };
 
 // EPT events already in registers -> the iteration's partial sums -> acc.
-template <class M, typename Real, int EPT, class KT>
-__device__ __forceinline__ void compute_full(const RfProgram& P, const KT& K,
+template <class M, typename Real, int EPT>
+__device__ __forceinline__ void compute_full(const RfProgram& P,
+                                             const EvalConsts<Real, M::NL_>& K,
                                              const Real (&x)[M::NL_][EPT],
                                              Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
   constexpr int NL = M::NL_;
@@ -239,7 +238,7 @@ __device__ __forceinline__ void compute_full(const RfProgram& P, const KT& K,
     Real xc[NL];
 #pragma unroll
     for (int c = 0; c < NL; ++c) xc[c] = x[c][e];
-    M::template event<Real, KT>(P, K, xc, q);
+    M::template event<Real>(P, K, xc, q);
   }
   acc.add(q);
 }
@@ -248,8 +247,9 @@ __device__ __forceinline__ void compute_full(const RfProgram& P, const KT& K,
 // event base + c*EPT).  The next chunk's 128-bit loads are issued before the
 // current chunk is computed (register double buffering), so the memory
 // latency overlaps the arithmetic.
-template <class M, typename Real, typename Col, int EPT, class KT>
-__device__ __forceinline__ void stream_chunks(const RfProgram& P, const KT& K,
+template <class M, typename Real, typename Col, int EPT>
+__device__ __forceinline__ void stream_chunks(const RfProgram& P,
+                                              const EvalConsts<Real, M::NL_>& K,
                                               const Col* __restrict__ ev, int64_t stride,
                                               int64_t base, int64_t first, int64_t step,
                                               int64_t nfull, bool vec,
@@ -263,7 +263,7 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P, const KT& K,
     const bool more = nx < nfull;
     Real xb[NL][EPT];
     if (more) load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nx * EPT, vec, xb);
-    compute_full<M, Real, EPT, KT>(P, K, xa, acc);
+    compute_full<M, Real, EPT>(P, K, xa, acc);
     if (!more) break;
 #pragma unroll
     for (int c = 0; c < NL; ++c)
@@ -273,8 +273,8 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P, const KT& K,
   }
 }
 
-template <class M, typename Real, typename Col, class KT>
-__device__ inline void iterate_scalar(const RfProgram& P, const KT& K,
+template <class M, typename Real, typename Col>
+__device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real, M::NL_>& K,
                                       const Col* __restrict__ ev, int64_t stride, int64_t i0,
                                       int64_t i1, Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc,
                                       int step = 1) {
@@ -288,7 +288,7 @@ __device__ inline void iterate_scalar(const RfProgram& P, const KT& K,
     Real q[RF_NACC(NL)];
 #pragma unroll
     for (int j = 0; j < RF_NACC(NL); ++j) q[j] = Real(0);
-    M::template event<Real, KT>(P, K, xc, q);
+    M::template event<Real>(P, K, xc, q);
     acc.add(q);
   }
 }
@@ -326,12 +326,7 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   __shared__ double tot[NA];
   __shared__ int s_last;
 
-  if constexpr (M::KCONST) {
-    // constants in this module's constant bank, copied there after the
-    // prologue and before this launch (stream order); the next call's
-    // prologue writes only the global copy, so it may start at once
-    asm volatile("griddepcontrol.launch_dependents;");
-  } else if (W.consts) {
+  if (W.consts) {
     // constants from the prologue kernel, which this launch may overlap:
     // wait for it (a no-op when this grid was not launched as its dependent)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -349,25 +344,15 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
 
   Acc<Real, NA, M::AMASK> acc;
   acc.zero();
-  const int64_t h = head < n ? head : n;
-  const int64_t nfull = (n - h) / EPT;
-  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool tail = blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1;
-  if constexpr (M::KCONST) {
-    const RfConsts<Real>& KC = M::template kconst<Real>();
-    if (!KC.bad) {
-      stream_chunks<M, Real, Col, EPT>(P, KC, ev, n, h, first, gsz, nfull, vec != 0, acc);
-      if (tail) {
-        iterate_scalar<M, Real, Col>(P, KC, ev, n, 0, h, acc);
-        iterate_scalar<M, Real, Col>(P, KC, ev, n, h + nfull * EPT, n, acc);
-      }
-    }
-  } else if (!K.bad) {
+  if (!K.bad) {
     EvalConsts<Real, NL> E;
     E.load(K);
-    stream_chunks<M, Real, Col, EPT>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
-    if (tail) {
+    const int64_t h = head < n ? head : n;
+    const int64_t nfull = (n - h) / EPT;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    stream_chunks<M, Real, Col, EPT>(P, E, ev, n, h, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                     gsz, nfull, vec != 0, acc);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
       iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
       iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
     }
@@ -381,12 +366,7 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   if (s_last) {
     __threadfence();
     BlockRow<Real, NA, M::AMASK>::sum(W.partials, gridDim.x, red, tot);
-    if (threadIdx.x < 32) {
-      if constexpr (M::KCONST)
-        epilogue_warp<Real, NL>(P, M::template kconst<Real>(), tot, n, nll, grad, W.status);
-      else
-        epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
-    }
+    if (threadIdx.x < 32) epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
     if (threadIdx.x == 0) *W.counter = 0u;
   }
 }
