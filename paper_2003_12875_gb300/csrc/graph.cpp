@@ -212,8 +212,10 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
   return RF_OK;
 }
 
-bool ept_ok(int eval, int coldt, int ept) {
-  if (eval == RF_EVAL_FP32) return ept == 4 || ept == 8;
+// events per thread: FP32 evaluation 4 or 8, and 16 in the specialised
+// kernels (the generic ones are not instantiated for it); FP64 2 or 4
+bool ept_ok(int eval, int coldt, int ept, bool jit) {
+  if (eval == RF_EVAL_FP32) return ept == 4 || ept == 8 || (jit && ept == 16);
   if (coldt == RF_F64) return ept == 2 || ept == 4;
   return ept == 4;
 }
@@ -255,8 +257,8 @@ struct rf_graph {
   // 1 of the precision's two options) and, for the fused kernel, register
   // budget (min_blocks 2..4); compiled on first need
   bool jit = false;
-  cudaKernel_t jk_fused[2][3] = {};
-  cudaKernel_t jk_toys[2] = {nullptr, nullptr};
+  cudaKernel_t jk_fused[3][3] = {};
+  cudaKernel_t jk_toys[3] = {nullptr, nullptr, nullptr};
   cudaKernel_t jk_logp = nullptr;
   // formula leaves: translated code, the normalisation kernel and its
   // workspace (log I and derivatives, block partials, tickets)
@@ -265,12 +267,12 @@ struct rf_graph {
   cudaKernel_t jk_norm = nullptr;
   double* formula_buf = nullptr;
   unsigned int* formula_ticket = nullptr;
-  int jk_regs[2][3] = {};
+  int jk_regs[3][3] = {};
 };
 
-// index of an events-per-thread option within its precision's pair
+// index of an events-per-thread option within its precision's set
 static int ept_index(int eval, int coldt, int ept) {
-  if (eval == RF_EVAL_FP32) return ept == 8 ? 1 : 0;
+  if (eval == RF_EVAL_FP32) return ept == 16 ? 2 : (ept == 8 ? 1 : 0);
   if (coldt == RF_F64) return ept == 4 ? 1 : 0;
   return 0;
 }
@@ -486,6 +488,7 @@ rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
     if (g->n_formula)
       return fail(RF_EUNSUPPORTED, "formula leaves run only in the specialised kernels");
     g->jit = false;
+    if (g->cfg.ept == 16) g->cfg.ept = 8;  // not instantiated in the generic kernels
     return RF_OK;
   }
   bool was = g->jit;
@@ -929,7 +932,7 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
   if (!g || !cfg) return fail(RF_EINVAL, "NULL argument");
   if (cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
     return fail(RF_EINVAL, "block must be 64, 128 or 256");
-  if (!ept_ok(g->eval, g->coldt, cfg->ept))
+  if (!ept_ok(g->eval, g->coldt, cfg->ept, g->jit))
     return fail(RF_EINVAL, "events per thread not available for this precision / dtype");
   if (cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8)
     return fail(RF_EINVAL, "blocks_per_sm must be in 1..8");
@@ -962,15 +965,19 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   cudaEventCreate(&b);
   const int blocks[3] = {64, 128, 256};
   const int bpss[6] = {1, 2, 3, 4, 6, 8};
-  int epts[2];
+  int epts[3], n_ept;
   if (g->eval == RF_EVAL_FP32) {
     epts[0] = 4;
     epts[1] = 8;
+    epts[2] = 16;
+    n_ept = g->jit ? 3 : 2;
   } else if (g->coldt == RF_F64) {
     epts[0] = 2;
     epts[1] = 4;
+    n_ept = 2;
   } else {
-    epts[0] = epts[1] = 4;
+    epts[0] = 4;
+    n_ept = 1;
   }
   // register budgets: three for the specialised kernel (compiled in
   // parallel first), the generic kernels have one
@@ -978,13 +985,13 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   const int mbs[3] = {g->jit ? 2 : g->cfg.min_blocks, 3, 4};
   if (g->jit) {
     std::vector<std::string> srcs;
-    for (int ei = 0; ei < 2; ++ei)
+    for (int ei = 0; ei < n_ept; ++ei)
       for (int mi = 0; mi < n_mb; ++mi)
         srcs.push_back(rf_jit_source(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED, epts[ei],
                                      mbs[mi]));
     rf_jit_precompile(srcs);
     std::string err;
-    for (int ei = 0; ei < 2; ++ei)
+    for (int ei = 0; ei < n_ept; ++ei)
       for (int mi = 0; mi < n_mb; ++mi)
         if (!jit_fused(g, epts[ei], mbs[mi], &err)) {
           cudaFree(dout);
@@ -994,8 +1001,7 @@ rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const
   RfLaunchCfg best = g->cfg;
   float best_t = 1e30f;
   for (int bi = 0; bi < 3; ++bi)
-    for (int ei = 0; ei < 2; ++ei) {
-      if (ei == 1 && epts[1] == epts[0]) continue;
+    for (int ei = 0; ei < n_ept; ++ei) {
       for (int pi = 0; pi < 6 * n_mb; ++pi) {
         RfLaunchCfg c = g->cfg;
         c.block = blocks[bi];

@@ -147,7 +147,7 @@ def test_every_launch_configuration(rf, jit):
     w, p, v, g, sc = workload("c5")
     ev = to_dev(w)
     pd = params_dev(p)
-    for prec, epts in (("fp32", (4, 8)), ("fp64", (4,))):
+    for prec, epts in (("fp32", (4, 8, 16) if jit else (4, 8)), ("fp64", (4,))):
         G = rf.Graph(w["spec"], "f32", prec)
         G.set_jit(jit)
         for block in (64, 128, 256):
@@ -178,7 +178,7 @@ def test_tuner_picks_a_valid_configuration(rf):
     ms = G.tune(to_dev(w), params_dev(p))
     assert ms > 0
     cfg = G.get_launch()
-    assert cfg["block"] in (64, 128, 256) and cfg["ept"] in (4, 8)
+    assert cfg["block"] in (64, 128, 256) and cfg["ept"] in (4, 8, 16)
     assert cfg["min_blocks"] in (2, 3)
     nll, _ = G.nll(to_dev(w), params_dev(p))
     assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
