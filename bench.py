@@ -448,7 +448,7 @@ def reference_arm(args, rank, world):
         rates.append(r)
     value = statistics.median(rates)
     line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "events/s",
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "gpus_used": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sample / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "events": n, "sample_events": sample},
