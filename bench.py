@@ -14,7 +14,8 @@ normalisation, reduction and gradient accumulation.  The event column (404 MB)
 is larger than L2 (129 MB), so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-(the reference this build is checked against) on the host cores instead.
+(the reference implementation the GPU results are checked against) on the
+host cores instead.
 """
 from __future__ import annotations
 
@@ -125,7 +126,8 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
 
 
 # FP32-pipe instructions per event of the fused kernel's formulation, by piece
-# (derived op by op from the formulas; the table is in DESIGN.md, "Roofline").
+# (derived op by op from the formulas of each leaf, the log-sum-exp and the
+# adjoint sums).
 # leaf type -> (base, extra per wanted derivative by leaf-parameter index,
 #               shared extra when any derivative is wanted)
 LEAF_INSTR = {
