@@ -92,15 +92,25 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   const int pb = 32 * std::max(P.n_leaves, 1);
   const int pg = (toys + 31) / 32 > 0 ? (toys + 31) / 32 : 1;
   int32_t* at = adam_scale ? W.adam_t : nullptr;
-  if (eval)
-    rf::toy_prep_kernel<double><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
-                                                   static_cast<RfConsts<double>*>(W.toy_consts),
-                                                   W.status, at);
-  else
-    rf::toy_prep_kernel<float><<<pg, pb, 0, st>>>(P, pm, offsets, toys, n_events,
-                                                  static_cast<RfConsts<float>*>(W.toy_consts),
-                                                  W.status, at);
-  int rc = (int)cudaGetLastError();
+  // a programmatic dependent of the kernel before it (back to back: the
+  // previous call's finalize kernel), publishing its constants after it
+  cudaLaunchConfig_t plc = {};
+  plc.gridDim = dim3(pg);
+  plc.blockDim = dim3(pb);
+  plc.stream = st;
+  cudaLaunchAttribute pat[1];
+  pat[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pat[0].val.programmaticStreamSerializationAllowed = 1;
+  plc.attrs = pat;
+  plc.numAttrs = 1;
+  const double* pmc = pm;
+  int rc = eval ? (int)cudaLaunchKernelEx(&plc, rf::toy_prep_kernel<double>, P, pmc, offsets,
+                                          toys, n_events,
+                                          static_cast<RfConsts<double>*>(W.toy_consts), W.status,
+                                          at)
+                : (int)cudaLaunchKernelEx(&plc, rf::toy_prep_kernel<float>, P, pmc, offsets, toys,
+                                          n_events, static_cast<RfConsts<float>*>(W.toy_consts),
+                                          W.status, at);
   if (rc) return rc;
   const int g = (int)grid;
   if (jit_toys)

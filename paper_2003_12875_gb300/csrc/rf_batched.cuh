@@ -17,8 +17,12 @@ namespace rf {
 // Prep kernel: blocks of n_leaves warps and 32 toys; warp k computes leaf k
 // of every toy of the block (lane l: toy 32 b + l), so the leaves' FP64
 // chains run side by side on different SM sub-partitions, then warp 0 checks
-// the toys' offsets and combines.  Constants are written straight to the
-// toy's global slot.  Lets the segment kernel launch at once.
+// the toys' offsets and combines.  Lets the segment kernel launch at once.
+// The constants are built in shared memory and published only after the wait
+// for the kernel before (the previous call's finalize kernel, which reads
+// them), so back to back the FP64 chains of this call's prep run beside the
+// previous call's finalize.  A fit step (adam_t set) reads parameter rows that
+// the previous finalize kernel has just updated, so it waits first.
 template <typename Real>
 __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* __restrict__ pm,
                                               const int64_t* __restrict__ offsets,
@@ -26,14 +30,18 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
                                               RfConsts<Real>* consts, unsigned int* status,
                                               int32_t* adam_t) {
   asm volatile("griddepcontrol.launch_dependents;");
+  __shared__ RfConsts<Real> Ks[32];
   __shared__ double lnI_s[RF_MAXL][32];
   __shared__ int ok_s[RF_MAXL][32];
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
-  const int64_t t = (int64_t)blockIdx.x * 32 + lane;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && adam_t) *adam_t += 1;
+  const int64_t t0 = (int64_t)blockIdx.x * 32, t = t0 + lane;
+  if (adam_t) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (blockIdx.x == 0 && threadIdx.x == 0) *adam_t += 1;
+  }
   if (t < toys && k < P.n_leaves) {
     double l = 0.0;
-    ok_s[k][lane] = leaf_consts(P, pm + t * P.n_par, consts[t], k, &l) ? 1 : 0;
+    ok_s[k][lane] = leaf_consts(P, pm + t * P.n_par, Ks[lane], k, &l) ? 1 : 0;
     lnI_s[k][lane] = l;
   }
   __syncthreads();
@@ -46,8 +54,16 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
       l[j] = lnI_s[j][lane];
       all &= ok_s[j][lane] != 0;
     }
-    comb_consts(P, pm + t * P.n_par, consts[t], l, all);
+    comb_consts(P, pm + t * P.n_par, Ks[lane], l, all);
   }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __syncthreads();
+  // publish: the block's toys' constants, a contiguous stretch of words
+  const int64_t nt = toys - t0 < 32 ? toys - t0 : 32;
+  constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
+  const double* src = reinterpret_cast<const double*>(Ks);
+  double* dst = reinterpret_cast<double*>(consts + t0);
+  for (int64_t w = threadIdx.x; w < nt * kWords; w += blockDim.x) dst[w] = src[w];
 }
 
 // Finalize kernel: one thread per toy (the FP64 unit takes one warp
@@ -84,6 +100,10 @@ __device__ __forceinline__ void toy_finalize_body(const RfProgram& P,
       return;
     }
   }
+  // the next call's prep kernel may start (it publishes new constants only
+  // after this grid has finished); the segment rows: after the segment kernel
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= toys) return;
   const ToySplit S = toy_split(offsets, toys, stride, warps);
