@@ -40,24 +40,14 @@ int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, in
                     int64_t warps, double* pm, double* out, RfWork W,
                     const double* adam_scale, double adam_lr, cudaStream_t st) {
   const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, 32 toys per block
-  // a programmatic dependent of the segment kernel: its blocks become
-  // resident as that grid runs and proceed the moment it completes
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(fg);
-  lc.blockDim = dim3(fb);
-  lc.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  lc.attrs = at;
-  lc.numAttrs = 1;
   switch (P.n_leaves) {
-    case 1: return (int)cudaLaunchKernelEx(&lc, rf::toy_finalize_kernel<Real, 1>, P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr);
-    case 2: return (int)cudaLaunchKernelEx(&lc, rf::toy_finalize_kernel<Real, 2>, P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr);
-    case 3: return (int)cudaLaunchKernelEx(&lc, rf::toy_finalize_kernel<Real, 3>, P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr);
-    case 4: return (int)cudaLaunchKernelEx(&lc, rf::toy_finalize_kernel<Real, 4>, P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr);
+    case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 3: rf::toy_finalize_kernel<Real, 3><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 4: rf::toy_finalize_kernel<Real, 4><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    default: return (int)cudaErrorInvalidValue;
   }
-  return (int)cudaErrorInvalidValue;
+  return (int)cudaGetLastError();
 }
 
 }  // namespace

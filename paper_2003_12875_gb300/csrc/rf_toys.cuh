@@ -314,9 +314,6 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
   }
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  // the finalize kernel may be scheduled now: it copies the (complete) toy
-  // constants, then waits for this grid's rows
-  asm volatile("griddepcontrol.launch_dependents;");
   if (!active) return;
 
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
@@ -408,9 +405,6 @@ __device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
     t = find_toy(offsets, toys, stride, wb);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  // the finalize kernel may be scheduled now: it copies the (complete) toy
-  // constants, then waits for this grid's rows
-  asm volatile("griddepcontrol.launch_dependents;");
   if (!active) return;
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
   ToyState<M, Real> T;
