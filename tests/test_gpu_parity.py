@@ -179,7 +179,7 @@ def test_tuner_picks_a_valid_configuration(rf):
     assert ms > 0
     cfg = G.get_launch()
     assert cfg["block"] in (64, 128, 256) and cfg["ept"] in (4, 8, 16)
-    assert cfg["min_blocks"] in (2, 3)
+    assert cfg["min_blocks"] in (2, 3, 4)
     nll, _ = G.nll(to_dev(w), params_dev(p))
     assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
 
