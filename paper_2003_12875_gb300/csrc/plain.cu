@@ -31,7 +31,7 @@ __global__ void plain_leaf_kernel(const RfProgram P, int k,
        i += (int64_t)gridDim.x * blockDim.x) {
     double u, g[RF_LEAF_MAXP];
     eval_leaf<double>(L.type, L.gmask & 4, (double)col[i], pc, u, g);  // ARGUS form
-    out[i] = exp(u - lnI);
+    out[i] = exp(kLn2 * u - lnI);  // u is in base-2 units
   }
 }
 

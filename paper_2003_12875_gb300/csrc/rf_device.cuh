@@ -32,6 +32,13 @@ __device__ __forceinline__ double kNaN() { return __longlong_as_double(0x7ff8000
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kSqrtHalfPi = 1.25331413731550025121;
 constexpr double kSqrtPi = 1.77245385090551602730;
+// The per-event code works in base-2 log units (u / ln 2): the hardware's
+// lg2 and ex2 then need no conversion factor, and the FP64 epilogue turns the
+// summed log-likelihood back into natural units once.
+constexpr double kLn2 = 0.693147180559945309417;
+constexpr double kLog2e = 1.44269504088896340736;
+// sqrt(log2(e) / 2): the Gaussian's -d^2/2 in base-2 units is -(kG d)^2
+constexpr double kG = 0.84932180028801904272;
 
 // ------------------------------------------------------------------ FP64 math
 // One out-of-line copy of each FP64 function the prologue calls: the prologue
@@ -355,16 +362,18 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   }
   switch (L.type) {
     case RFL_GAUSS: {
+      // d = kG (x - mu) / sigma, so that u (base 2) = -d^2
       split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(1.0 / th[1]);
-      K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
-      K.gmul[k][0] = K.gmul[k][1] = 1.0 / th[1];  // d u/d mu = d/sigma, d u/d sigma = d^2/sigma
+      pc[2] = (Real)(kG / th[1]);
+      K.dtheta[k][1] = kG / (double)pc[2] - th[1];
+      K.gmul[k][0] = 1.0 / (kG * th[1]);         // d u/d mu = (x - mu)/sigma^2 = d / (kG sigma)
+      K.gmul[k][1] = 1.0 / (kG * kG * th[1]);    // d u/d sigma = d^2 / (kG^2 sigma)
       break;
     }
     case RFL_EXP: {
-      pc[0] = (Real)th[0];
+      pc[0] = (Real)(th[0] * kLog2e);  // lambda in base-2 units
       split_hi_lo(L.lo, pc[1], pc[2]);
-      K.dtheta[k][0] = (double)pc[0] - th[0];
+      K.dtheta[k][0] = kLn2 * (double)pc[0] - th[0];
       break;
     }
     case RFL_CHEB: {
@@ -385,7 +394,7 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       pc[4] = (Real)A;
       pc[5] = (Real)(A / n);
       pc[6] = (Real)n;
-      pc[7] = (Real)(-0.5 * A * A);
+      pc[7] = (Real)(-0.5 * A * A * kLog2e);
       K.dtheta[k][1] = 1.0 / fabs((double)pc[2]) - th[1];
       K.gmul[k][0] = -s / th[1];   // d u/d m0 = -(s/sigma) du/dt
       K.gmul[k][1] = -1.0 / th[1]; // d u/d sigma = -(t/sigma) du/dt
@@ -416,10 +425,11 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     case RFL_ARGUS: {
       split_hi_lo(th[0], pc[0], pc[1]);
       pc[2] = (Real)(1.0 / (th[0] * th[0]));
-      pc[3] = (Real)th[1];
+      pc[3] = (Real)(th[1] * kLog2e);  // c in base-2 units (for u)
       pc[4] = (Real)(2.0 / th[0]);
       pc[5] = (Real)th[2];  // p (general-p form)
-      K.dtheta[k][1] = (double)pc[3] - th[1];
+      pc[6] = (Real)th[1];  // c (for the m0 derivative)
+      K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
       if (L.gmask & 4) K.dtheta[k][2] = (double)pc[5] - th[2];
       K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
@@ -487,14 +497,15 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
   for (int c = 0; c < RF_MAXC; ++c) {
     K.coef[c] = coef[c];
     if (c < C && !((zero >> c) & 1)) {
+      // in base-2 units per event; the remainder in natural units
       double d = beta[c] - ref;
-      K.delta[c] = (Real)d;
-      K.delta_lo[c] = d - (double)K.delta[c];
+      K.delta[c] = (Real)(d * kLog2e);
+      K.delta_lo[c] = d - kLn2 * (double)K.delta[c];
     } else {
       K.delta[c] = (Real)(-kInf());
       K.delta_lo[c] = 0.0;
     }
-    K.delta_nc[c] = (Real)(c < C ? base[c] - ref : 0.0);
+    K.delta_nc[c] = (Real)(c < C ? (base[c] - ref) * kLog2e : 0.0);
   }
   K.bad = bad ? 1 : 0;
 }
@@ -532,12 +543,24 @@ __device__ __forceinline__ float log_fast(float x) {
   return r * 0.693147182f;
 }
 // exp(x) for x <= 0 through the hardware base-2 exponential (max relative
-// error 2^-22 by the PTX specification) of x * log2(e); used for the mixture
-// weight exp(-|v1 - v0|) in (0, 1], whose absolute error then stays below
-// 4e-8 for every argument.
+// error 2^-22 by the PTX specification) of x * log2(e).
 __device__ __forceinline__ float exp_neg_approx(float x) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.44269504f));
+  return r;
+}
+// The same hardware functions in base 2, as the per-event code uses them:
+// lg2.approx (error as above, in log2 units) and ex2.approx (2^-22 relative;
+// the mixture weights 2^-|dv| in (0, 1] thus carry an absolute error below
+// 4e-8).
+__device__ __forceinline__ float lg2_fast(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
@@ -573,6 +596,8 @@ struct Fn<float> {
   // x known positive and finite wherever its result is used
   static __device__ __forceinline__ float logp(float x) { return log_fast(x); }
   static __device__ __forceinline__ float exp_neg(float x) { return exp_neg_approx(x); }
+  static __device__ __forceinline__ float lg2(float x) { return lg2_fast(x); }
+  static __device__ __forceinline__ float ex2(float x) { return ex2_fast(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
   static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
@@ -583,21 +608,25 @@ struct Fn<double> {
   static __device__ __forceinline__ double log(double x) { return ::log(x); }
   static __device__ __forceinline__ double logp(double x) { return ::log(x); }
   static __device__ __forceinline__ double exp_neg(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
+  static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   static __device__ __forceinline__ double ninf() { return -kInf(); }
 };
 
-// Typed leaves: u = log f(x) - off and g_j = d u / d theta_j.  GM is the
+// Typed leaves: u = (log f(x) - off) / ln 2, in base-2 units, and
+// g_j = d (log f)/d theta_j in natural units (up to the constant factor gmul
+// applied in the epilogue).  GM is the
 // compile-time mask of the derivatives that are needed; the others are 0.
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_gauss(Real x, const Real* __restrict__ pc, Real& u,
                                            Real (&g)[RF_LEAF_MAXP]) {
-  Real d = ((x - pc[0]) - pc[1]) * pc[2];
-  u = Real(-0.5) * d * d;
-  g[0] = (GM & 1) ? d : Real(0);       // times 1/sigma (gmul)
-  g[1] = (GM & 2) ? d * d : Real(0);   // times 1/sigma (gmul)
+  Real d = ((x - pc[0]) - pc[1]) * pc[2];  // kG (x - mu) / sigma
+  u = -(d * d);                              // -(x - mu)^2 / (2 sigma^2) in base 2
+  g[0] = (GM & 1) ? d : Real(0);       // times 1/(kG sigma) (gmul)
+  g[1] = (GM & 2) ? d * d : Real(0);   // times 1/(kG^2 sigma) (gmul)
   g[2] = g[3] = Real(0);
 }
 
@@ -618,7 +647,7 @@ __device__ __forceinline__ void leaf_cheb(Real x, const Real* __restrict__ pc, R
   Real t1 = xp, t2 = Real(2) * xp * t1 - Real(1);
   Real t3 = Real(2) * xp * t2 - t1, t4 = Real(2) * xp * t3 - t2;
   Real f = Real(1) + pc[2] * t1 + pc[3] * t2 + pc[4] * t3 + pc[5] * t4;
-  u = F::log(f);
+  u = F::lg2(f);
   if (GM) {
     Real r = F::rcp(f);
     g[0] = (GM & 1) ? t1 * r : Real(0);
@@ -639,8 +668,8 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   Real t = ((x - pc[0]) - pc[1]) * pc[2];  // s (x - m0) / sigma
   bool tail = t <= -A;
   Real D = Real(1) - pc[5] * (A + t);
-  Real Lg = F::logp(D);  // used only in the tail, where D >= 1
-  u = tail ? pc[7] - pc[6] * Lg : Real(-0.5) * t * t;
+  Real Lg = F::lg2(D);  // log2 D, used only in the tail, where D >= 1
+  u = tail ? pc[7] - pc[6] * Lg : Real(-0.5 * kLog2e) * t * t;
   if (GM) {
     Real rD = F::rcp(D);
     Real dudt = tail ? A * rD : -t;
@@ -648,7 +677,7 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
     g[0] = (GM & 1) ? dudt : Real(0);
     g[1] = (GM & 2) ? dudt * t : Real(0);
     g[2] = (GM & 4) ? (tail ? (Real(2) * A + t) * rD - A : Real(0)) : Real(0);
-    g[3] = (GM & 8) ? (tail ? (Real(1) - rD) - Lg : Real(0)) : Real(0);
+    g[3] = (GM & 8) ? (tail ? (Real(1) - rD) - Real(kLn2) * Lg : Real(0)) : Real(0);
   } else {
     g[0] = g[1] = g[2] = g[3] = Real(0);
   }
@@ -666,18 +695,19 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
   Real tau = dm * sm * pc[2];
   bool ok = tau > Real(0);
   const Real p = (GM & 4) ? pc[5] : Real(0.5);
+  // pc[3] = c log2(e) for u (base 2), pc[6] = c for the derivatives
   if (GM & 4) {
-    const Real lt = F::log(tau);
-    u = ok ? F::log(x) + p * lt + pc[3] * tau : F::ninf();
-    g[2] = ok ? lt : Real(0);
+    const Real lt = F::lg2(tau);
+    u = ok ? F::lg2(x) + p * lt + pc[3] * tau : F::ninf();
+    g[2] = ok ? Real(kLn2) * lt : Real(0);
   } else {
-    u = ok ? Real(0.5) * F::log(x * x * tau) + pc[3] * tau : F::ninf();
+    u = ok ? Real(0.5) * F::lg2(x * x * tau) + pc[3] * tau : F::ninf();
     g[2] = Real(0);
   }
   g[1] = (GM & 2) ? (ok ? tau : Real(0)) : Real(0);
   if (GM & 1) {
     Real r = F::rcp(tau);
-    g[0] = ok ? (p * r + pc[3]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
+    g[0] = ok ? (p * r + pc[6]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
   } else {
     g[0] = Real(0);
   }
@@ -696,7 +726,7 @@ __device__ __forceinline__ void leaf_johnson(Real x, const Real* __restrict__ pc
   const Real r = F::sqrt(t);
   const Real as = copysign(F::logp(fabs(z) + r), z);
   const Real w = pc[3] + pc[4] * as;
-  u = Real(-0.5) * (F::logp(t) + w * w);
+  u = Real(-0.5) * F::lg2(t) + Real(-0.5 * kLog2e) * (w * w);
   if (GM & 3) {
     const Real dudz = -(z + w * pc[4] * r) * F::rcp(t);
     g[0] = (GM & 1) ? dudz : Real(0);
@@ -740,13 +770,13 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
     return v[0];
   } else if constexpr (NC == 2) {
     Real dv = v[1] - v[0];
-    Real e = F::exp_neg(-fabs(dv));
+    Real e = F::ex2(-fabs(dv));
     Real s = Real(1) + e;
     Real rs = F::rcp(s);
     Real wb = rs, ws = e * rs;
     w[0] = dv > Real(0) ? ws : wb;
     w[1] = dv > Real(0) ? wb : ws;
-    return fmax(v[0], v[1]) + F::log(s);  // s in [1, 2], or NaN from NaN inputs
+    return fmax(v[0], v[1]) + F::lg2(s);  // s in [1, 2], or NaN from NaN inputs
   } else {
     Real m = v[0];
 #pragma unroll
@@ -754,13 +784,13 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
     Real s = Real(0);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      w[c] = F::exp(v[c] - m);
+      w[c] = F::ex2(v[c] - m);
       s += w[c];
     }
     Real rs = F::rcp(s);
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] *= rs;
-    return m + F::log(s);
+    return m + F::lg2(s);
   }
 }
 
@@ -768,7 +798,7 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
 // coefficient is exactly 0 (vnc = delta_nc_c + sum of the component's u).
 template <typename Real>
 __device__ __forceinline__ Real comp_weight(int zero_mask, int c, Real vnc, Real ell, Real wc) {
-  if ((zero_mask >> c) & 1) return Fn<Real>::exp(vnc - ell);
+  if ((zero_mask >> c) & 1) return Fn<Real>::ex2(vnc - ell);
   return wc;
 }
 
@@ -948,7 +978,7 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
                                 const double* T, int64_t n, double* nll,
                                 double* grad, unsigned int* status) {
   const int C = P.n_comp;
-  double L = T[0];
+  double L = kLn2 * T[0];  // the per-event sums are in base-2 units
   for (int c = 0; c < C; ++c)
     if (!((K.zero_mask >> c) & 1)) L += T[1 + c] * K.delta_lo[c];
   for (int k = 0; k < P.n_leaves; ++k)
@@ -1004,7 +1034,7 @@ __device__ __forceinline__ void epilogue_warp(const RfProgram& P, const RfConsts
   const int C = P.n_comp;
   double term = 0.0;
   if (lane == 0) {
-    term = T[0];
+    term = kLn2 * T[0];  // the per-event sums are in base-2 units
   } else if (lane <= C) {
     const int c = lane - 1;
     if (!((K.zero_mask >> c) & 1)) term = T[1 + c] * K.delta_lo[c];

@@ -5,7 +5,7 @@
 // A formula's value carries its derivatives with respect to the leaf's
 // parameters (Dual<Real, N>: value v and d[j] = dv/dp_j); the observable and
 // the literals are plain Real, so parameter-free subexpressions cost what they
-// cost without derivatives.  The per-event leaf is u = log f, g_j = f_j / f;
+// cost without derivatives.  The per-event leaf is u = log2 f, g_j = f_j / f;
 // its normalisation I = int f over the range and dI/dp_j are taken in FP64 by
 // composite Gauss-Legendre quadrature, 16 nodes on each of 128 equal panels.
 #pragma once
@@ -269,14 +269,14 @@ __device__ __forceinline__ D as_dual(const D& a) {
   return a;
 }
 
-// Per-event formula leaf: u = log f, g_j = (df/dp_j) / f for wanted j.
+// Per-event formula leaf: u = log2 f, g_j = (df/dp_j) / f for wanted j.
 template <class F, typename Real, int GM>
 __device__ __forceinline__ void formula_leaf(Real x, const Real* __restrict__ pc, Real& u,
                                              Real (&g)[RF_LEAF_MAXP]) {
   const auto f = F::template eval<Real>(x, pc);
   // the log and reciprocal of the built-in leaves (hardware approximations
   // in FP32); the formula's own functions keep CUDA's accurate versions
-  u = Fn<Real>::log(f.v);
+  u = Fn<Real>::lg2(f.v);  // base-2 units, as the built-in leaves
   const Real r = Fn<Real>::rcp(f.v);
 #pragma unroll
   for (int j = 0; j < RF_LEAF_MAXP; ++j)

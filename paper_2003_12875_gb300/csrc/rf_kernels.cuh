@@ -395,7 +395,7 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
 #pragma unroll
     for (int j = 0; j < NA; ++j) q[j] = Real(0);
     M::template event<Real>(P, E, xc, q);
-    logp[i] = K.bad ? kNaN() : K.beta_ref + (double)q[0];
+    logp[i] = K.bad ? kNaN() : K.beta_ref + kLn2 * (double)q[0];
   }
 }
 
