@@ -56,11 +56,11 @@ struct GenericModel {
       ell = v[0];
       w[0] = Real(1);
     } else if (NL >= 2 && C == 2) {
-      Real dv = v[1] - v[0];
-      Real e = F::exp(-fabs(dv));
+      Real dv = v[1] - v[0];  // base-2 units, as everything per event
+      Real e = F::ex2(-fabs(dv));
       Real s = Real(1) + e;
       Real rs = F::rcp(s);
-      ell = fmax(v[0], v[1]) + F::log(s);
+      ell = fmax(v[0], v[1]) + F::lg2(s);
       Real wb = rs, ws = e * rs;
       w[0] = dv > Real(0) ? ws : wb;
       w[1] = dv > Real(0) ? wb : ws;
@@ -72,10 +72,10 @@ struct GenericModel {
       Real s = Real(0);
 #pragma unroll
       for (int c = 0; c < NL; ++c) {
-        w[c] = (c < C) ? F::exp(v[c] - m) : Real(0);
+        w[c] = (c < C) ? F::ex2(v[c] - m) : Real(0);
         s += w[c];
       }
-      ell = m + F::log(s);
+      ell = m + F::lg2(s);
       Real rs = F::rcp(s);
 #pragma unroll
       for (int c = 0; c < NL; ++c) w[c] *= rs;
