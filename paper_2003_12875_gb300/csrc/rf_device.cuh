@@ -598,6 +598,7 @@ struct Fn<float> {
   static __device__ __forceinline__ float exp_neg(float x) { return exp_neg_approx(x); }
   static __device__ __forceinline__ float lg2(float x) { return lg2_fast(x); }
   static __device__ __forceinline__ float ex2(float x) { return ex2_fast(x); }
+  static __device__ __forceinline__ float ex2_exact(float x) { return exp2f(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
   static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
@@ -610,6 +611,7 @@ struct Fn<double> {
   static __device__ __forceinline__ double exp_neg(double x) { return ::exp(x); }
   static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
   static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
+  static __device__ __forceinline__ double ex2_exact(double x) { return ::exp2(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
@@ -798,7 +800,9 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
 // coefficient is exactly 0 (vnc = delta_nc_c + sum of the component's u).
 template <typename Real>
 __device__ __forceinline__ Real comp_weight(int zero_mask, int c, Real vnc, Real ell, Real wc) {
-  if ((zero_mask >> c) & 1) return Fn<Real>::ex2(vnc - ell);
+  // CUDA's accurate exp2: this weight is not bounded by 1, so the
+  // approximation's relative error would not stay small in absolute terms
+  if ((zero_mask >> c) & 1) return Fn<Real>::ex2_exact(vnc - ell);
   return wc;
 }
 
