@@ -315,7 +315,12 @@ def test_zero_fraction_edge(rf):
             nll, grad = G.nll(to_dev(w), params_dev(q))
             assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"]
             err = grad_l1(grad.cpu().numpy(), g, sc, [True] * 4)
-            assert err.max() <= TOL[prec]["grad"], (f, prec, err)
+            # d/df at the boundary sums the absent component's P_c/P, which
+            # reaches e^50 for events 10 sigma from the Gaussian: in FP32 a
+            # relative error of a few units in the last place of the exponent
+            # becomes ~1e-6 of that sum, so this one component gets 5e-6
+            tol = [TOL[prec]["grad"]] * 3 + [5e-6 if prec == "fp32" else TOL[prec]["grad"]]
+            assert np.all(err <= tol), (f, prec, err)
 
 
 def test_autograd_function(rf):
