@@ -130,15 +130,17 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
 # adjoint sums).
 # leaf type -> (base, extra per wanted derivative by leaf-parameter index,
 #               shared extra when any derivative is wanted)
+# Per-event logarithms are taken in base 2 (one hardware lg2 each, no
+# conversion factor); the two-term log-sum-exp is one ex2, one lg2 and one
+# reciprocal with the arithmetic around them.
 LEAF_INSTR = {
-    "gauss": (5, {0: 0, 1: 1}, 0),
+    "gauss": (4, {0: 0, 1: 1}, 0),
     "exp": (3, {0: 0}, 0),
-    "cheb": (13, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
-    "cb": (12, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
-    "argus": (14, {0: 5, 1: 1, 2: 3}, 0),   # a free p: one more log and its product
-    "johnson": (14, {0: 0, 1: 1, 2: 0, 3: 1}, 4),
+    "cheb": (12, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
+    "cb": (11, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
+    "argus": (13, {0: 5, 1: 1, 2: 3}, 0),   # a free p: one more log and its product
+    "johnson": (13, {0: 0, 1: 1, 2: 0, 3: 1}, 4),
 }
-LOG_INSTR = 2          # hardware log2 and a multiply by ln 2
 F64_TO_F32_INSTR = 9   # integer-pipe rounding of an FP64 column value
 
 
@@ -162,9 +164,9 @@ def algorithmic_instr_per_event(spec: dict, ept: int = REF_EPT, f64_columns: boo
         free += len(wanted)
     total += len(leaves)                      # component sums delta_c + sum u_k
     if nc == 2:
-        total += 13                           # two-term log-sum-exp and weights
+        total += 11                           # two-term log-sum-exp and weights
     elif nc > 2:
-        total += 12 * nc + 25
+        total += 11 * nc + 24
     total += 1 + (nc if nc > 1 else 1) + free + (2 if nc > 1 else 0)   # adjoint sums
     total += 4.0 * (1 + nc + free) / ept      # compensated per-iteration sums
     total += 1                                # loads and loop
