@@ -138,7 +138,8 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
   o << "struct RfModel {\n  static constexpr int NL_ = " << NL << ";\n"
     << "  static constexpr int NCOL = " << P.n_cols << ";\n"
     << "  static constexpr unsigned long long AMASK = " << amask << "ull;\n"
-    << "  template <typename Real>\n  static __device__ __forceinline__ void event(const RfProgram& P, "
+    << "  template <typename Real, bool ANYZERO = true>\n  static __device__ __forceinline__ void "
+       "event(const RfProgram& P, "
        "const rf::EvalConsts<Real, NL_>& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
   for (int k = 0; k < NL; ++k) {
     const RfLeafProg& L = P.leaf[k];
@@ -163,7 +164,7 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
     o << "    q[1] += Real(1);\n";
   } else {
     // common case first: no coefficient is exactly zero (one uniform branch)
-    o << "    if (K.zero_mask == 0) {\n";
+    o << "    if (!ANYZERO || K.zero_mask == 0) {\n";
     for (int c = 0; c < NC; ++c) o << "      q[" << 1 + c << "] += w[" << c << "];\n";
     o << "    } else {\n";
     for (int c = 0; c < NC; ++c)

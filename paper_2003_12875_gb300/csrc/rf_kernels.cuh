@@ -24,8 +24,9 @@ struct GenericModel {
   static constexpr int NCOL = NL;
   static constexpr unsigned long long AMASK = ~0ull;
 
-  // leaves -> components -> log-sum-exp -> adjoint weights, into q
-  template <typename Real>
+  // leaves -> components -> log-sum-exp -> adjoint weights, into q.
+  // ANYZERO false: the caller knows no coefficient is zero (no per-event test)
+  template <typename Real, bool ANYZERO = true>
   static __device__ __forceinline__ void event(const RfProgram& P,
                                                const EvalConsts<Real, NL>& K,
                                                const Real (&xc)[NL],
@@ -81,7 +82,7 @@ struct GenericModel {
       for (int c = 0; c < NL; ++c) w[c] *= rs;
     }
     q[0] += ell;
-    if (K.zero_mask == 0) {
+    if (!ANYZERO || K.zero_mask == 0) {
 #pragma unroll
       for (int c = 0; c < NL; ++c) q[1 + c] += w[c];
     } else {
@@ -224,7 +225,7 @@ struct BlockRow<double, NA, MASK> {
 };
 
 // EPT events already in registers -> the iteration's partial sums -> acc.
-template <class M, typename Real, int EPT>
+template <class M, typename Real, int EPT, bool ANYZERO>
 __device__ __forceinline__ void compute_full(const RfProgram& P,
                                              const EvalConsts<Real, M::NL_>& K,
                                              const Real (&x)[M::NL_][EPT],
@@ -238,7 +239,7 @@ __device__ __forceinline__ void compute_full(const RfProgram& P,
     Real xc[NL];
 #pragma unroll
     for (int c = 0; c < NL; ++c) xc[c] = x[c][e];
-    M::template event<Real>(P, K, xc, q);
+    M::template event<Real, ANYZERO>(P, K, xc, q);
   }
   acc.add(q);
 }
@@ -246,8 +247,10 @@ __device__ __forceinline__ void compute_full(const RfProgram& P,
 // Chunks first, first+step, ... < nfull of EPT events each (chunk c starts at
 // event base + c*EPT).  The next chunk's 128-bit loads are issued before the
 // current chunk is computed (register double buffering), so the memory
-// latency overlaps the arithmetic.
-template <class M, typename Real, typename Col, int EPT>
+// latency overlaps the arithmetic.  ANYZERO: some coefficient may be exactly
+// zero (the per-event code then tests for it); the callers pick the variant
+// once from the call's constants.
+template <class M, typename Real, typename Col, int EPT, bool ANYZERO = true>
 __device__ __forceinline__ void stream_chunks(const RfProgram& P,
                                               const EvalConsts<Real, M::NL_>& K,
                                               const Col* __restrict__ ev, int64_t stride,
@@ -263,7 +266,7 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
     const bool more = nx < nfull;
     Real xb[NL][EPT];
     if (more) load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nx * EPT, vec, xb);
-    compute_full<M, Real, EPT>(P, K, xa, acc);
+    compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
     if (!more) break;
 #pragma unroll
     for (int c = 0; c < NL; ++c)
@@ -350,8 +353,11 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     const int64_t h = head < n ? head : n;
     const int64_t nfull = (n - h) / EPT;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    stream_chunks<M, Real, Col, EPT>(P, E, ev, n, h, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                     gsz, nfull, vec != 0, acc);
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (E.zero_mask == 0)
+      stream_chunks<M, Real, Col, EPT, false>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
+    else
+      stream_chunks<M, Real, Col, EPT, true>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
       iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
       iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
