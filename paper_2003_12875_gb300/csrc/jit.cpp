@@ -105,7 +105,6 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
     for (int j = 0; j < RF_LEAF_MAXP; ++j)
       if ((P.leaf[k].gmask >> j) & 1) amask |= 1ull << (1 + NL + k * RF_LEAF_MAXP + j);
   std::ostringstream o;
-  if (getenv("RF_EVENTS_KEEP_L2")) o << "#define RF_EVENTS_KEEP_L2 1\n";  // experiment switch
   o << kRfJitPrelude << "\n";
   if (has_formula(P)) emit_formulas(o, P, fc);
   if (kind == RF_JIT_NORM) {

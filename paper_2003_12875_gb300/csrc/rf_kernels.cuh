@@ -138,13 +138,9 @@ __device__ __forceinline__ void load_full(const RfProgram& P, const Col* __restr
         const typename Vec<Col>::T* vp = reinterpret_cast<const typename Vec<Col>::T*>(col);
 #pragma unroll
         for (int v = 0; v < EPT / W; ++v) {
-#ifdef RF_EVENTS_KEEP_L2
-          typename Vec<Col>::T t = __ldg(vp + v);
-#else
           // events are read once per call: streaming (evict-first) loads, so
           // they do not push the prologue's code and constants out of L2
           typename Vec<Col>::T t = __ldcs(vp + v);
-#endif
           const Col* tc = reinterpret_cast<const Col*>(&t);
 #pragma unroll
           for (int e = 0; e < W; ++e) x[c][v * W + e] = cvt<Real, Col>(tc[e]);
