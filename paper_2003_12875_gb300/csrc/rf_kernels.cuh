@@ -260,15 +260,6 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
   for (int64_t ch = first;;) {
     const int64_t nx = ch + step;
     const bool more = nx < nfull;
-    // the chunk after the next one into L2 (no registers held): its loads
-    // then wait on L2 instead of DRAM latency
-    if (nx + step < nfull) {
-#pragma unroll
-      for (int c = 0; c < NL; ++c)
-        if (c < M::NCOL && c < P.n_cols)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(ev + (int64_t)P.col_obs[c] * stride + base +
-                                                       (nx + step) * EPT));
-    }
     Real xb[NL][EPT];
     if (more) load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nx * EPT, vec, xb);
     compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
