@@ -298,7 +298,7 @@ rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events,
  * graph-specialised fused kernel is compiled for: room for that many blocks
  * of 256 threads on one SM (at most 128, 80 or 64 registers per thread); the
  * generic kernels ignore it.  Defaults: 3 for FP32 evaluation, 2 for FP64;
- * rf_graph_tune tries 2 and 3. */
+ * rf_graph_tune tries 2, 3 and 4. */
 typedef struct {
   int32_t block;
   int32_t ept;
@@ -309,11 +309,30 @@ typedef struct {
 rf_status rf_graph_get_launch(const rf_graph* g, rf_launch* cfg);
 rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg);
 
-/* Autotune: times every launch configuration on the given data with CUDA
- * events and keeps the fastest (host-synchronous).  best_ms may be NULL. */
+/* Autotune: times every launch configuration (block x events per thread x
+ * blocks per SM x, for the graph-specialised kernel, register budget) on the
+ * given data with CUDA events and keeps the fastest (host-synchronous).
+ * The choice is cached on disk, in the folder RF_JIT_CACHE_DIR (default
+ * $TMPDIR/rfgpu-jit, else /tmp/rfgpu-jit), keyed by the kernel (the
+ * specialised source, else the graph structure and library build), the
+ * column and evaluation precisions, floor(log2 n_events) and the device's
+ * compute capability and SM count; a later rf_graph_tune with the same key
+ * applies the cached configuration and times only that one.  best_ms (may be
+ * NULL) receives the mean time of one call with the chosen configuration.
+ * Same errors as rf_nll; the configuration is unchanged on error. */
 rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events,
                         const double* params, rf_stream stream,
                         double* best_ms);
+
+#define RF_TUNE_NO_CACHE 1 /* neither read nor write the on-disk cache */
+#define RF_TUNE_REFRESH 2  /* time every configuration and overwrite the entry */
+
+/* rf_graph_tune with flags (RF_TUNE_*; other bits: RF_EINVAL).  *from_cache
+ * (may be NULL) is set to 1 when the configuration came from the cache, else
+ * 0.  An entry that no longer validates is ignored and overwritten. */
+rf_status rf_graph_tune_ex(rf_graph* g, const void* events, int64_t n_events,
+                           const double* params, rf_stream stream, int32_t flags,
+                           double* best_ms, int32_t* from_cache);
 
 /* NLL and gradient for callers that cannot allocate device memory (no
  * counterpart in the paper).  Some callers cannot call cudaMalloc at all --

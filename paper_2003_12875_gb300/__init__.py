@@ -35,6 +35,7 @@ _STATUS = {0: "RF_OK", 1: "RF_EINVAL", 2: "RF_EUNSUPPORTED", 3: "RF_EALIGN",
            4: "RF_ECUDA", 5: "RF_ENOMEM"}
 MAX_CHILDREN, MAX_NODE_PARAMS = 8, 8
 STATUS_PARAM_DOMAIN, STATUS_NONFINITE = 1, 2
+TUNE_NO_CACHE, TUNE_REFRESH = 1, 2
 
 
 class RFError(RuntimeError):
@@ -70,7 +71,8 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_graph_tune", "rf_graph_status", "rf_graph_last_launches", "rf_last_error",
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
            "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
-           "rf_check_d2f", "rf_generate_toys", "rf_graph_set_shard_weight"]
+           "rf_check_d2f", "rf_generate_toys", "rf_graph_set_shard_weight",
+           "rf_graph_tune_ex"]
 
 
 def lib_path() -> str:
@@ -106,6 +108,7 @@ def load(build_if_missing: bool = True):
         L.rf_graph_get_launch.argtypes = [vp, C.POINTER(_Launch)]
         L.rf_graph_set_launch.argtypes = [vp, C.POINTER(_Launch)]
         L.rf_graph_tune.argtypes = [vp, vp, i64, vp, vp, dp]
+        L.rf_graph_tune_ex.argtypes = [vp, vp, i64, vp, vp, i32, dp, C.POINTER(i32)]
         L.rf_graph_status.argtypes = [vp, C.POINTER(C.c_uint32)]
         L.rf_graph_last_launches.argtypes = [vp]
         L.rf_graph_last_launches.restype = i32
@@ -231,6 +234,7 @@ class Graph:
         _check(L.rf_graph_compile(C.byref(d), C.byref(h)))
         self._h = h
         self._bound = None
+        self.tune_from_cache = False
 
     def close(self):
         if getattr(self, "_h", None):
@@ -373,12 +377,18 @@ class Graph:
                     blocks_per_sm or cur["blocks_per_sm"], min_blocks or cur["min_blocks"])
         _check(load().rf_graph_set_launch(self._h, C.byref(c)))
 
-    def tune(self, events: torch.Tensor, params: torch.Tensor) -> float:
+    def tune(self, events: torch.Tensor, params: torch.Tensor, cache: bool = True,
+             refresh: bool = False) -> float:
+        """Picks the fastest launch configuration (mean ms of one call with it
+        returned); the choice is cached on disk unless cache=False, and
+        refresh=True times every configuration even on a cache hit."""
         n = self._events(events)
         self._params(params)
-        ms = C.c_double()
-        _check(load().rf_graph_tune(self._h, _ptr(events), n, _ptr(params), _stream(),
-                                    C.byref(ms)))
+        ms, hit = C.c_double(), C.c_int32()
+        flags = (0 if cache else TUNE_NO_CACHE) | (TUNE_REFRESH if refresh else 0)
+        _check(load().rf_graph_tune_ex(self._h, _ptr(events), n, _ptr(params), _stream(),
+                                       flags, C.byref(ms), C.byref(hit)))
+        self.tune_from_cache = bool(hit.value)
         return ms.value
 
     def status(self) -> int:

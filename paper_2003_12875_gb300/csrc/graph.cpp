@@ -10,6 +10,8 @@
 // batch interface of Sec. 5.2 as the baseline; the range checks follow
 // Sec. 3 ("Checking parameters").
 #include <cuda_runtime.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -951,85 +953,191 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg) {
   return RF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Key of a tuning result in the on-disk cache: the kernel it was timed with
+// (the graph-specialised source, else the structure the generic kernels
+// branch on and the library build), the precisions, the size bucket
+// floor(log2 n) and the device (compute capability and SM count).
+uint64_t tune_key(const rf_graph* g, int64_t n_events) {
+  std::string k;
+  char buf[96];
+  if (g->jit) {
+    snprintf(buf, sizeof(buf), "jit %016llx",
+             (unsigned long long)rf_jit_hash(g->prog, fcode(g), g->eval, g->coldt,
+                                             RF_JIT_FUSED, 4, 2));
+    k = buf;
+  } else {
+    k = std::string("generic ") + __DATE__ + " " + __TIME__;
+    const RfProgram& P = g->prog;
+    snprintf(buf, sizeof(buf), " %d %d %d %d %d", P.kind, P.n_leaves, P.n_comp, P.n_cols,
+             P.coef_free);
+    k += buf;
+    for (int i = 0; i < P.n_leaves; ++i) {
+      snprintf(buf, sizeof(buf), " %d/%d", P.leaf[i].type, P.leaf[i].gmask);
+      k += buf;
+    }
+  }
+  int dev = 0, sms = 0, maj = 0, mnr = 0, bucket = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
+  for (int64_t n = n_events; n > 1; n >>= 1) ++bucket;
+  snprintf(buf, sizeof(buf), "|%d|%d|%d|sm%d%d|%d", g->eval, g->coldt, bucket, maj, mnr, sms);
+  return rf_text_hash(k + buf);
+}
+
+std::string tune_path(uint64_t key) {
+  char name[64];
+  snprintf(name, sizeof(name), "/tune-%016llx.txt", (unsigned long long)key);
+  return rf_cache_dir() + name;
+}
+
+bool tune_load(uint64_t key, rf_launch* c) {
+  FILE* f = fopen(tune_path(key).c_str(), "r");
+  if (!f) return false;
+  const bool ok = fscanf(f, "rf-tune 1 %d %d %d %d", &c->block, &c->ept, &c->blocks_per_sm,
+                         &c->min_blocks) == 4;
+  fclose(f);
+  return ok;
+}
+
+// written under a temporary name and renamed, so readers never see a partial file
+void tune_store(uint64_t key, const RfLaunchCfg& c) {
+  const std::string dir = rf_cache_dir(), path = tune_path(key);
+  mkdir(dir.c_str(), 0700);
+  const std::string tmp = path + "." + std::to_string(getpid());
+  if (FILE* f = fopen(tmp.c_str(), "w")) {
+    const bool ok = fprintf(f, "rf-tune 1 %d %d %d %d\n", c.block, c.ept, c.blocks_per_sm,
+                            c.min_blocks) > 0;
+    fclose(f);
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+  }
+}
+
+// Mean time of one fused call with configuration c: 7 calls, the first two
+// are warm-up.  Adds the five timed calls to *tsum.
+cudaError_t time_config(rf_graph* g, const RfLaunchCfg& c, const void* events, int64_t n_events,
+                        const double* params, double* dout, cudaEvent_t a, cudaEvent_t b,
+                        cudaStream_t st, float* tsum) {
+  cudaError_t e = cudaSuccess;
+  *tsum = 0.f;
+  for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(a, st);
+    int le = fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
+    cudaEventRecord(b, st);
+    if (le) e = (cudaError_t)le;
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (rep >= 2) *tsum += ms;
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events, const double* params,
                         rf_stream stream, double* best_ms) {
+  return rf_graph_tune_ex(g, events, n_events, params, stream, 0, best_ms, nullptr);
+}
+
+rf_status rf_graph_tune_ex(rf_graph* g, const void* events, int64_t n_events,
+                           const double* params, rf_stream stream, int32_t flags,
+                           double* best_ms, int32_t* from_cache) {
   if (!g) return fail(RF_EINVAL, "graph is NULL");
+  if (flags & ~(RF_TUNE_NO_CACHE | RF_TUNE_REFRESH)) return fail(RF_EINVAL, "unknown tune flags");
   rf_status s = check_events(g, events, n_events);
   if (s) return s;
+  if (from_cache) *from_cache = 0;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool use_cache = !(flags & RF_TUNE_NO_CACHE);
+  const uint64_t key = use_cache ? tune_key(g, n_events) : 0;
   double* dout = nullptr;
   cudaError_t e = cudaMalloc(&dout, sizeof(double) * (1 + RF_MAXPAR));
   if (e != cudaSuccess) return fail(RF_ENOMEM, "tune scratch");
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int blocks[3] = {64, 128, 256};
-  const int bpss[6] = {1, 2, 3, 4, 6, 8};
-  int epts[3], n_ept;
-  if (g->eval == RF_EVAL_FP32) {
-    epts[0] = 4;
-    epts[1] = 8;
-    epts[2] = 16;
-    n_ept = g->jit ? 3 : 2;
-  } else if (g->coldt == RF_F64) {
-    epts[0] = 2;
-    epts[1] = 4;
-    n_ept = 2;
-  } else {
-    epts[0] = 4;
-    n_ept = 1;
-  }
-  // register budgets: three for the specialised kernel (compiled in
-  // parallel first), the generic kernels have one
-  const int n_mb = g->jit ? 3 : 1;
-  const int mbs[3] = {g->jit ? 2 : g->cfg.min_blocks, 3, 4};
-  if (g->jit) {
-    std::vector<std::string> srcs;
-    for (int ei = 0; ei < n_ept; ++ei)
-      for (int mi = 0; mi < n_mb; ++mi)
-        srcs.push_back(rf_jit_source(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED, epts[ei],
-                                     mbs[mi]));
-    rf_jit_precompile(srcs);
-    std::string err;
-    for (int ei = 0; ei < n_ept; ++ei)
-      for (int mi = 0; mi < n_mb; ++mi)
-        if (!jit_fused(g, epts[ei], mbs[mi], &err)) {
-          cudaFree(dout);
-          return fail(RF_ECUDA, "JIT fused kernel: " + err);
-        }
-  }
+  const RfLaunchCfg old = g->cfg;
   RfLaunchCfg best = g->cfg;
   float best_t = 1e30f;
-  for (int bi = 0; bi < 3; ++bi)
-    for (int ei = 0; ei < n_ept; ++ei) {
-      for (int pi = 0; pi < 6 * n_mb; ++pi) {
-        RfLaunchCfg c = g->cfg;
-        c.block = blocks[bi];
-        c.ept = epts[ei];
-        c.blocks_per_sm = bpss[pi % 6];
-        c.min_blocks = mbs[pi / 6];
-        float tsum = 0.f;
-        for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
-          cudaEventRecord(a, st);
-          int le = fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
-          cudaEventRecord(b, st);
-          if (le) e = (cudaError_t)le;
-          if (e == cudaSuccess) e = cudaEventSynchronize(b);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, a, b);
-          if (rep >= 2) tsum += ms;  // first two are warm-up
-        }
-        if (e != cudaSuccess) break;
-        if (tsum < best_t) {
-          best_t = tsum;
-          best = c;
-        }
-      }
+  rf_launch hit;
+  // a cached entry that no longer validates (another library version, a
+  // damaged file) is ignored and overwritten
+  if (use_cache && !(flags & RF_TUNE_REFRESH) && tune_load(key, &hit) &&
+      rf_graph_set_launch(g, &hit) == RF_OK) {
+    e = time_config(g, g->cfg, events, n_events, params, dout, a, b, st, &best_t);
+    best = g->cfg;
+    if (from_cache) *from_cache = 1;
+  } else {
+    const int blocks[3] = {64, 128, 256};
+    const int bpss[6] = {1, 2, 3, 4, 6, 8};
+    int epts[3], n_ept;
+    if (g->eval == RF_EVAL_FP32) {
+      epts[0] = 4;
+      epts[1] = 8;
+      epts[2] = 16;
+      n_ept = g->jit ? 3 : 2;
+    } else if (g->coldt == RF_F64) {
+      epts[0] = 2;
+      epts[1] = 4;
+      n_ept = 2;
+    } else {
+      epts[0] = 4;
+      n_ept = 1;
     }
+    // register budgets: three for the specialised kernel (compiled in
+    // parallel first), the generic kernels have one
+    const int n_mb = g->jit ? 3 : 1;
+    const int mbs[3] = {g->jit ? 2 : g->cfg.min_blocks, 3, 4};
+    if (g->jit) {
+      std::vector<std::string> srcs;
+      for (int ei = 0; ei < n_ept; ++ei)
+        for (int mi = 0; mi < n_mb; ++mi)
+          srcs.push_back(rf_jit_source(g->prog, fcode(g), g->eval, g->coldt, RF_JIT_FUSED,
+                                       epts[ei], mbs[mi]));
+      rf_jit_precompile(srcs);
+      std::string err;
+      for (int ei = 0; ei < n_ept; ++ei)
+        for (int mi = 0; mi < n_mb; ++mi)
+          if (!jit_fused(g, epts[ei], mbs[mi], &err)) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaFree(dout);
+            return fail(RF_ECUDA, "JIT fused kernel: " + err);
+          }
+    }
+    for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi)
+      for (int ei = 0; ei < n_ept && e == cudaSuccess; ++ei)
+        for (int pi = 0; pi < 6 * n_mb && e == cudaSuccess; ++pi) {
+          RfLaunchCfg c = g->cfg;
+          c.block = blocks[bi];
+          c.ept = epts[ei];
+          c.blocks_per_sm = bpss[pi % 6];
+          c.min_blocks = mbs[pi / 6];
+          float tsum = 0.f;
+          e = time_config(g, c, events, n_events, params, dout, a, b, st, &tsum);
+          if (e == cudaSuccess && tsum < best_t) {
+            best_t = tsum;
+            best = c;
+          }
+        }
+    if (e == cudaSuccess && use_cache) tune_store(key, best);
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(dout);
-  if (e != cudaSuccess) return cuda_fail(e, "rf_graph_tune");
+  if (e != cudaSuccess) {
+    g->cfg = old;
+    return cuda_fail(e, "rf_graph_tune");
+  }
   g->cfg.block = best.block;
   g->cfg.ept = best.ept;
   g->cfg.blocks_per_sm = best.blocks_per_sm;

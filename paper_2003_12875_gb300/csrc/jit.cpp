@@ -283,6 +283,10 @@ void rf_jit_precompile(const std::vector<std::string>& sources) {
   for (std::thread& t : th) t.join();
 }
 
+std::string rf_cache_dir() { return cache_dir(); }
+
+uint64_t rf_text_hash(const std::string& s) { return fnv1a(s); }
+
 uint64_t rf_jit_hash(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt, int kind,
                      int ept, int min_blocks) {
   return fnv1a(rf_jit_source(P, fc, eval, coldt, kind, ept, min_blocks));

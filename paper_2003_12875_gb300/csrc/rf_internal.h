@@ -208,6 +208,10 @@ bool rf_jit_compile_only(const RfProgram& P, const RfFormulaCode* fc, int eval, 
                          int kind, int ept, int min_blocks, std::string* err);
 rf_cuda_kernel rf_jit_kernel(const RfProgram& P, const RfFormulaCode* fc, int eval, int coldt,
                              int kind, int ept, int min_blocks, int* regs, std::string* err);
+// on-disk cache folder (RF_JIT_CACHE_DIR, else $TMPDIR/rfgpu-jit) and the
+// FNV-1a hash its file names use
+std::string rf_cache_dir();
+uint64_t rf_text_hash(const std::string& s);
 // compiles the sources not yet in the on-disk cache, in parallel threads
 void rf_jit_precompile(const std::vector<std::string>& sources);
 // normalisation kernel of the formula leaves (grid RF_FORMULA_BLOCKS x leaves)

@@ -79,6 +79,12 @@ def test_validation_errors(rf):
     assert rf.validate(s) == 0
 
 
+def test_tune_rejects_null_graph(rf):
+    lib = rf.load()
+    assert lib.rf_graph_tune(None, None, 0, None, None, None) == EINVAL
+    assert lib.rf_graph_tune_ex(None, None, 0, None, None, 0, None, None) == EINVAL
+
+
 def test_unsupported_shapes(rf):
     # Prod of two leaves on the same observable
     s = {"obs": [(0.0, 1.0)], "params": [0.5, 1.0, -1.0],

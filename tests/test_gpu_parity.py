@@ -189,6 +189,25 @@ def test_tuner_picks_a_valid_configuration(rf):
     assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
 
 
+def test_tuner_cache_round_trip(rf):
+    """A tuned configuration is stored on disk under the graph's kernel,
+    precisions, size bucket and device: a second graph of the same model finds
+    it and times only that configuration; cache=False times every one."""
+    w, p, v, *_ = workload("c2")
+    ev, pd = to_dev(w), params_dev(p)
+    G = rf.Graph(w["spec"], "f64", "fp32")
+    G.tune(ev, pd, refresh=True)
+    assert not G.tune_from_cache
+    first = G.get_launch()
+    H = rf.Graph(w["spec"], "f64", "fp32")
+    assert H.tune(ev, pd) > 0
+    assert H.tune_from_cache and H.get_launch() == first
+    H.tune(ev, pd, cache=False)
+    assert not H.tune_from_cache
+    nll, _ = H.nll(ev, pd)
+    assert rel_nll(float(nll.item()), v) <= TOL["fp32"]["nll"]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_run_to_run_bitwise_determinism(rf, prec):
     w, p, *_ = workload("c5")
