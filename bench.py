@@ -408,18 +408,19 @@ def toy_bench(args, rf, torch, rank, world, pk):
     hbm = {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
            "bytes_per_launch": n * col_bytes}
+    traffic = profiled_traffic(G.toy_kernel_hash()) if G.uses_jit() else None
     if args.precision == "fp32":
         instr = algorithmic_instr_per_event(w["spec"], REF_EPT, False)
         peak = sms * 128 * sm_mhz * 1e6
         achieved = instr * n / (ms * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                    "unit": "G FP32-lane instr/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "G FP32-lane instr/s", "frac": achieved / peak, "traffic": traffic,
                     "kernel": "rf_toys_jit (+ prep, finalize)",
                     "algorithmic_instr_per_event": instr,
                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                     "launch_ms": ms, "hbm": hbm}
     else:
-        roofline = {"bound": "hbm", **hbm, "traffic": None, "kernel": "rf_toys_jit",
+        roofline = {"bound": "hbm", **hbm, "traffic": traffic, "kernel": "rf_toys_jit",
                     "launch_ms": ms}
     line = {"metric": METRIC, "value": job_throughput(n, world, ms), "unit": "events/s",
             "toy_nll_per_s": world * toys / (ms * 1e-3), "n_gpus": world, "steps": args.steps,
@@ -428,6 +429,7 @@ def toy_bench(args, rf, torch, rank, world, pk):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": w["name"], "toys": toys, "events": n,
                        "launch": G.get_launch(), "kernel": G.uses_jit(),
+                       "kernel_hash": G.toy_kernel_hash(),
                        "l2": f"inputs larger than L2 ({n * col_bytes / 1e6:.0f} MB > 2 x 129 MB), "
                              "no flush"},
             "clocks": clk,

@@ -377,6 +377,9 @@ int32_t rf_graph_uses_jit(const rf_graph* g);
  * launch configuration (0 for the generic kernels): identifies the exact
  * kernel a profile was taken on. */
 uint64_t rf_graph_kernel_hash(const rf_graph* g);
+/* The same for the toy segment kernel of the bound toy sample (0 before
+ * rf_graph_bind_events or with the generic kernels). */
+uint64_t rf_graph_toy_kernel_hash(const rf_graph* g);
 int32_t rf_graph_kernel_regs(const rf_graph* g);
 
 /* Synchronises the device, returns the OR of RF_STATUS_* bits raised since

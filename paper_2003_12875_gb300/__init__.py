@@ -72,7 +72,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
            "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
            "rf_check_d2f", "rf_generate_toys", "rf_graph_set_shard_weight",
-           "rf_graph_tune_ex"]
+           "rf_graph_tune_ex", "rf_graph_toy_kernel_hash"]
 
 
 def lib_path() -> str:
@@ -125,9 +125,12 @@ def load(build_if_missing: bool = True):
         L.rf_check_d2f.argtypes = [vp, vp, vp, i64, vp]
         L.rf_graph_kernel_hash.argtypes = [vp]
         L.rf_graph_kernel_hash.restype = C.c_uint64
+        L.rf_graph_toy_kernel_hash.argtypes = [vp]
+        L.rf_graph_toy_kernel_hash.restype = C.c_uint64
         for name in SYMBOLS:
             if name not in ("rf_last_error", "rf_graph_last_launches", "rf_graph_uses_jit",
-                            "rf_graph_kernel_regs", "rf_graph_kernel_hash"):
+                            "rf_graph_kernel_regs", "rf_graph_kernel_hash",
+                            "rf_graph_toy_kernel_hash"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -410,6 +413,9 @@ class Graph:
 
     def kernel_hash(self) -> str:
         return f"{int(load().rf_graph_kernel_hash(self._h)):016x}"
+
+    def toy_kernel_hash(self) -> str:
+        return f"{int(load().rf_graph_toy_kernel_hash(self._h)):016x}"
 
 
 class RFNll(torch.autograd.Function):

@@ -511,6 +511,12 @@ uint64_t rf_graph_kernel_hash(const rf_graph* g) {
                      g->cfg.min_blocks);
 }
 
+uint64_t rf_graph_toy_kernel_hash(const rf_graph* g) {
+  if (!g || !g->jit || !g->bound) return 0;
+  return rf_jit_hash(g->prog, fcode(g), g->eval, g->coldt,
+                     g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, toy_ept(g), toy_min_blocks());
+}
+
 int32_t rf_graph_kernel_regs(const rf_graph* g) {
   if (!g || !g->jit) return 0;
   return g->jk_regs[ept_index(g->eval, g->coldt, g->cfg.ept)][g->cfg.min_blocks - 2];
