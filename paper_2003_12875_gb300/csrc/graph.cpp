@@ -303,7 +303,9 @@ static int toy_ept(const rf_graph* g) {
     const int e = atoi(v);
     if (g->eval == RF_EVAL_FP32 ? (e == 8 || e == 16) : (e == 4 || e == 8)) return e;
   }
-  return 8;  // measured on C4: 8 beats 16 (registers, occupancy) in FP32 and 4 in FP64
+  // measured on the 4096 Gauss + Exponential toys (1.3e8 events): FP32, 16
+  // (0.182 ms a step) beats 8 (0.205 ms); FP64, 8 beats 4
+  return g->eval == RF_EVAL_FP32 ? 16 : 8;
 }
 // register budget of the segment kernel: 0 = the compiler's choice, else
 // launch bounds for 3 or 4 resident blocks of 256 threads (tuning)
