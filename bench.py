@@ -180,15 +180,16 @@ def profiled_traffic(kernel_hash: str):
     kernel (matched by its source hash), else None."""
     import glob
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
-        kv = {}
+        # one (kernel_hash, dram_bytes_per_launch) pair per kernel section
+        cur = None
         with open(path) as f:
             for line in f:
-                if "=" in line and line.strip().split("=")[0].strip() in (
-                        "kernel_hash", "dram_bytes_per_launch"):
-                    k, v = line.split("=", 1)
-                    kv[k.strip()] = v.strip().strip("`")
-        if kv.get("kernel_hash") == kernel_hash and "dram_bytes_per_launch" in kv:
-            return float(kv["dram_bytes_per_launch"])
+                key, _, val = line.partition("=")
+                key, val = key.strip(), val.strip().strip("`")
+                if key == "kernel_hash":
+                    cur = val
+                elif key == "dram_bytes_per_launch" and cur == kernel_hash and cur != "n/a":
+                    return float(val)
     return None
 
 
