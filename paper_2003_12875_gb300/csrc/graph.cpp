@@ -14,6 +14,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -1017,7 +1018,8 @@ bool tune_load(uint64_t key, rf_launch* c) {
 void tune_store(uint64_t key, const RfLaunchCfg& c) {
   const std::string dir = rf_cache_dir(), path = tune_path(key);
   mkdir(dir.c_str(), 0700);
-  const std::string tmp = path + "." + std::to_string(getpid());
+  static std::atomic<unsigned> seq{0};  // graphs tuned from several threads
+  const std::string tmp = path + "." + std::to_string(getpid()) + "." + std::to_string(seq++);
   if (FILE* f = fopen(tmp.c_str(), "w")) {
     const bool ok = fprintf(f, "rf-tune 1 %d %d %d %d\n", c.block, c.ept, c.blocks_per_sm,
                             c.min_blocks) > 0;
