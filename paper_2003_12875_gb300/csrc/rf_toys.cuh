@@ -178,8 +178,9 @@ constexpr int kMaxStages = 8;
 // CE = 32*EPT events, column c at buf[c * CE + j].  Lanes read 128-bit
 // vectors (conflict-free: a warp's loads cover contiguous 512 bytes): lane l
 // takes vectors l + 32 m, i.e. events V (l + 32 m) + r.  FULL: the chunk lies
-// inside [p0, p1) (no per-event test).
-template <class M, typename Real, typename Col, int EPT, bool FULL>
+// inside [p0, p1) (no per-event test).  ANYZERO: some coefficient of the
+// toy may be exactly zero (the per-event test; see the register form).
+template <class M, typename Real, typename Col, int EPT, bool FULL, bool ANYZERO>
 __device__ __forceinline__ void eval_chunk(const RfProgram& P, const EvalConsts<Real, M::NL_>& E,
                                            Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc,
                                            const Col* buf, int64_t c0, int64_t p0, int64_t p1) {
@@ -216,7 +217,7 @@ __device__ __forceinline__ void eval_chunk(const RfProgram& P, const EvalConsts<
         Real xc[NL];
 #pragma unroll
         for (int c = 0; c < NL; ++c) xc[c] = cvt<Real, Col>(xv[c][r]);
-        M::template event<Real>(P, E, xc, q);
+        M::template event<Real, ANYZERO>(P, E, xc, q);
       }
     }
   }
@@ -345,13 +346,16 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
     }
     const Col* buf = ring + s * stage_elems;
     if (c0 + CE <= T.te && c0 >= T.tb) {  // the whole chunk in the current toy
-      if (!T.bad) eval_chunk<M, Real, Col, EPT, true>(P, T.E, T.acc, buf, c0, c0, c0 + CE);
+      if (!T.bad && T.E.zero_mask == 0)
+        eval_chunk<M, Real, Col, EPT, true, false>(P, T.E, T.acc, buf, c0, c0, c0 + CE);
+      else if (!T.bad)
+        eval_chunk<M, Real, Col, EPT, true, true>(P, T.E, T.acc, buf, c0, c0, c0 + CE);
       T.any = true;
     } else {
       for (int64_t p = c0; p < c0 + CE;) {
         if (!T.seek(consts, offsets, stride, toys, p, rows)) break;
         const int64_t q = c0 + CE < T.te ? c0 + CE : T.te;
-        if (!T.bad) eval_chunk<M, Real, Col, EPT, false>(P, T.E, T.acc, buf, c0, p, q);
+        if (!T.bad) eval_chunk<M, Real, Col, EPT, false, true>(P, T.E, T.acc, buf, c0, p, q);
         T.any = true;
         p = q;
       }
