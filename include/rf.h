@@ -153,9 +153,14 @@ typedef struct {
   int32_t n_params;
   const uint8_t* param_fixed; /* [n_params] or NULL: 1 = no gradient wanted   */
   int32_t column_dtype;       /* RF_F32 / RF_F64                              */
-  int32_t eval_precision;     /* RF_EVAL_FP32: per-event math in FP32, with
-                                 normalisation, reduction and gradient sums in
-                                 FP64; RF_EVAL_FP64: all FP64                 */
+  int32_t eval_precision;     /* RF_EVAL_FP32: per-event math in FP32; the
+                                 normalisations in FP64; each thread's sums
+                                 Kahan-compensated in FP32, a block's (or a
+                                 toy segment's) sums added in FP32 pairs and
+                                 converted once to FP64, every sum above that
+                                 (blocks, groups, a toy's segments) and the
+                                 gradient epilogue in FP64.
+                                 RF_EVAL_FP64: all FP64                       */
 } rf_graph_desc;
 
 typedef struct rf_graph rf_graph;
@@ -219,12 +224,14 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events,
 /*   offsets        dev int64 [toys+1], non-decreasing, offsets[toys] <= n_events
  *   params_matrix  dev FP64 [toys * n_params], row t = toy t's parameters
  *   out            dev FP64 [toys * (1 + n_params)], row t = (NLL_t, grad_t)
- * Three kernels: a per-toy FP64 prologue (one thread per toy); a segment
- * kernel that splits all toys' events [offsets[0], offsets[toys]) evenly over
- * its warps (one grid of SMs x blocks_per_sm blocks) and writes one FP64 row
- * of partial sums per (warp, toy) pair that share events; and a finalize
- * kernel, one warp per toy, that sums the toy's rows in a fixed order and
- * writes (NLL, grad).  Results depend on the inputs and the launch shape
+ * Three kernels: a per-toy FP64 prologue (blocks of one warp per leaf and
+ * 32 toys: warp k computes leaf k of each of the block's toys, lane l toy
+ * 32b + l); a segment kernel that splits all toys' events
+ * [offsets[0], offsets[toys]) evenly over its warps (one grid of SMs x
+ * blocks_per_sm blocks) and writes one row of partial sums per (warp, toy)
+ * pair that share events (FP32 evaluation: each sum as an FP32 pair, FP64
+ * evaluation: FP64); and a finalize kernel, one thread per toy, that widens
+ * the toy's rows to FP64, sums them in a fixed order and writes (NLL, grad).  Results depend on the inputs and the launch shape
  * only.  Offsets outside [0, n_events] are clamped and a decreasing pair
  * raises RF_STATUS_NONFINITE (the affected toys' results are then
  * meaningless, but nothing outside the bound columns is read).  No
@@ -343,13 +350,16 @@ rf_status rf_graph_tune_ex(rf_graph* g, const void* events, int64_t n_events,
  * allocates its workspace.  This entry point takes the descriptor directly
  * and runs the precompiled generic fused kernel with its scratch (per-block
  * partial sums, block ticket, status word) in a file-scope static device
- * array of the library: about 172 KB, enough for the partial sums of
- * blocks <= 1024 (0 = twice the SM count, capped at 1024; larger values
- * return RF_EINVAL).  Every GPU that loads the library holds that array until
+ * array of the library: about 178 KB, enough for the partial sums of
+ * blocks <= 1024 and of the grid tree's 32 groups (0 = twice the SM count,
+ * capped at 1024; larger values return RF_EINVAL).  Every GPU that loads the library holds that array until
  * the process exits.  It allocates nothing: no cudaMalloc/cudaFree and no
  * allocating library routine.  Its first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the
+ * make that first call before any stream capture.  The address is kept for
+ * the process: a cudaDeviceReset unloads the library's device image and
+ * makes it stale, so do not call this entry point on a device after
+ * resetting it.  Every call shares the
  * array and it keeps the last call's contents: the ticket and status words
  * are cleared on `stream` at the start of each call, and calls that overlap
  * on the GPU race on the array.  Arguments, layout and results as rf_nll

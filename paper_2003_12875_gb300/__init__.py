@@ -27,7 +27,8 @@ import torch
 
 from . import build as _build
 
-__all__ = ["Graph", "RFNll", "RFError", "load", "microbench", "TYPES"]
+__all__ = ["Graph", "RFNll", "RFError", "load", "microbench", "TYPES", "shard_range",
+           "sharded_nll", "rank_order_sum"]
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5,
          "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9, "formula": 10}
@@ -452,16 +453,36 @@ def shard_range(n_events: int, rank: int, world: int) -> tuple[int, int]:
     return rank * n_events // world, (rank + 1) * n_events // world
 
 
+def rank_order_sum(parts: torch.Tensor) -> torch.Tensor:
+    """Sum of the rows of parts [world, m] in row (rank) order with
+    Neumaier's compensation (Neumaier 1974): the result depends only on the
+    rows' values and order, never on a collective's internal reduction order,
+    so every rank that holds the same rows gets the same bits."""
+    s = parts[0].clone()
+    c = torch.zeros_like(s)
+    for r in range(1, parts.shape[0]):
+        x = parts[r]
+        t = s + x
+        c += torch.where(s.abs() >= x.abs(), (s - t) + x, (x - t) + s)
+        s = t
+    return s + c
+
+
 def sharded_nll(graph: "Graph", shard_events: torch.Tensor, params: torch.Tensor,
                 rank: int, group=None) -> torch.Tensor:
     """NLL and gradient of a dataset split over the processes of a
-    torch.distributed group: this rank evaluates its contiguous shard
-    (rf_nll; the extended term on rank 0 only) and one sum all-reduce adds the
-    ranks' (1 + n_params) values.  Returns [1 + n_params] (NLL, gradient) of
-    the whole dataset on every rank."""
+    torch.distributed group (the multi-process mode of the paper's Sec. 5.2:
+    contiguous batches of the dataset divided among processes).  This rank
+    evaluates its contiguous shard with rf_nll (the extended term on rank 0
+    only), the ranks' (1 + n_params) values are all-gathered, and every rank
+    adds them in rank order with Neumaier compensation (rank_order_sum), so
+    all ranks return the same bits, run after run.  Returns [1 + n_params]
+    (NLL, gradient) of the whole dataset."""
     import torch.distributed as dist
     graph.set_shard_weight(1.0 if rank == 0 else 0.0)
     out = torch.empty(1 + graph.n_par, dtype=torch.float64, device=shard_events.device)
     graph.nll(shard_events, params, out=out)
-    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
-    return out
+    world = dist.get_world_size(group)
+    parts = [torch.empty_like(out) for _ in range(world)]
+    dist.all_gather(parts, out, group=group)
+    return rank_order_sum(torch.stack(parts))

@@ -425,10 +425,12 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
     delete g;
     return cuda_fail(e, "rf_graph_compile: device query");
   }
-  g->max_rows_single = (int64_t)g->num_sms * 8;
+  // block rows of the largest grid (8 blocks per SM) and the group rows of the
+  // grid's FP64 tree
+  g->max_rows_single = (int64_t)g->num_sms * 8 + RF_TREE_GROUPS;
   e = cudaMalloc(&g->work.partials, sizeof(double) * RF_NACC_MAX * g->max_rows_single);
-  if (e == cudaSuccess) e = cudaMalloc(&g->work.counter, 4 * sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMemset(g->work.counter, 0, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.counter, RF_COUNTER_WORDS * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(g->work.counter, 0, RF_COUNTER_WORDS * sizeof(unsigned int));
   if (e != cudaSuccess) {
     free_work(g);
     delete g;
@@ -725,7 +727,7 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   g->max_toys = 0;
   // one row per (warp, toy) segment: at most (launch warps) + toys, and a
   // launch has at most 8 blocks of 8 warps per SM
-  const int64_t rows = (int64_t)max_toys + (int64_t)g->num_sms * 64;
+  const int64_t rows = (int64_t)max_toys + (int64_t)g->num_sms * 64 + RF_TREE_GROUPS;
   if (rows > g->max_rows_single) {
     cudaFree(g->work.partials);
     g->work.partials = nullptr;

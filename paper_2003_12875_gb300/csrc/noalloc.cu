@@ -7,10 +7,10 @@
 // build an rf_graph either, because rf_graph_compile allocates the graph's
 // workspace.  This entry point takes the descriptor directly, evaluates it with
 // the precompiled generic fused kernel, and gives that kernel its scratch --
-// the per-block partial sums, the block ticket and the status word -- from a
+// the per-block and per-group partial sums, the tickets and the status word -- from a
 // file-scope static device array instead of an allocation.
 //
-// The array (RF_NOALLOC_BYTES, about 172 KB) is part of this library's device
+// The array (kBytes, about 178 KB) is part of this library's device
 // image: every GPU that loads the library holds it until the process exits.
 // Every call shares it and it keeps the last call's contents, so calls that
 // overlap on the GPU (two streams, or two threads on one stream without
@@ -29,8 +29,12 @@ void rf_set_last_error(const char* msg);
 namespace {
 
 constexpr int kMaxBlocks = RF_NOALLOC_MAX_BLOCKS;
-constexpr size_t kHeader = 256;  // ticket, status, padding
-constexpr size_t kBytes = kHeader + sizeof(double) * RF_NACC_MAX * (size_t)kMaxBlocks;
+// ticket and status words (RF_COUNTER_WORDS), then the rows of the grid's
+// FP64 tree: one per block and one per group
+constexpr size_t kHeader = 256;
+static_assert(kHeader >= RF_COUNTER_WORDS * sizeof(unsigned int), "ticket words");
+constexpr size_t kBytes =
+    kHeader + sizeof(double) * RF_NACC_MAX * (size_t)(kMaxBlocks + RF_TREE_GROUPS);
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol; its device address comes from cudaGetSymbolAddress below.
@@ -97,7 +101,8 @@ extern "C" rf_status rf_nll_noalloc(const rf_graph_desc* desc, const void* event
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned int* words = static_cast<unsigned int*>(base);
-  e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned int), st);  // ticket and status start at 0
+  // tickets and status start at 0
+  e = cudaMemsetAsync(words, 0, RF_COUNTER_WORDS * sizeof(unsigned int), st);
   if (e != cudaSuccess) {
     rf_set_last_error("rf_nll_noalloc: clearing the ticket failed");
     return RF_ECUDA;

@@ -867,41 +867,10 @@ __device__ __forceinline__ void ds_add(float& h, float& l, float h2, float l2) {
 }
 
 // Block sum of N per-thread FP32 pairs (h_i + l_i) in a fixed order, entirely
-// in FP32 pair arithmetic (the FP64 pipe of this GPU is narrow); one FP64
-// conversion per accumulator at the end.  Accumulators not in MASK give 0.
-// red: [32*N] float2 shared; result in out[0..N) (shared), valid after the
-// trailing barrier.
-template <int N, unsigned long long MASK>
-__device__ inline void block_sum_ds(const float (&hs)[N], const float (&ls)[N], float2* red,
-                                    double* out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    if (!((MASK >> i) & 1ull)) continue;
-    float h = hs[i], l = ls[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
-      const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
-      ds_add(h, l, h2, l2);
-    }
-    if (lane == 0) red[wid * N + i] = make_float2(h, l);
-  }
-  __syncthreads();
-  if (threadIdx.x < N) {
-    double r = 0.0;
-    if ((MASK >> threadIdx.x) & 1ull) {
-      float h = 0.f, l = 0.f;
-      for (int w = 0; w < nw; ++w) ds_add(h, l, red[w * N + threadIdx.x].x, red[w * N + threadIdx.x].y);
-      r = (double)h + (double)l;
-    }
-    out[threadIdx.x] = r;
-  }
-  __syncthreads();
-}
-
-// As block_sum_ds, but the block totals stay FP32 pairs: out[i] (shared).
+// in FP32 pair arithmetic (the FP64 pipe of this GPU is narrow: one warp
+// instruction per ~64 cycles per sub-partition); the block totals stay FP32
+// pairs, out[i] (shared).  Accumulators not in MASK give 0.  red: [32*N]
+// float2 shared; valid after the trailing barrier.
 template <int N, unsigned long long MASK>
 __device__ inline void block_sum_ds2(const float (&hs)[N], const float (&ls)[N], float2* red,
                                      float2* out) {
@@ -929,25 +898,56 @@ __device__ inline void block_sum_ds2(const float (&hs)[N], const float (&ls)[N],
   __syncthreads();
 }
 
-// Rows [r0, r1) of FP32-pair partials (pair i of row r in the 8-byte slot
-// partials[r * RF_NACC_MAX + i]) summed in FP32-pair arithmetic in a fixed
-// order for a given block size; FP64 totals in out[0..N) (shared).
+// FP64 block sum of the accumulators in MASK (the others give 0), in a
+// fixed order: a shuffle tree per warp, then warp totals in warp order.
+// red: [32*N] shared; result in out[0..N) (shared), valid after the trailing
+// barrier.
 template <int N, unsigned long long MASK>
-__device__ inline void rows_sum_ds(const double* partials, int64_t r0, int64_t r1, float2* red,
-                                   double* out) {
-  float h[N], l[N];
+__device__ inline void block_sum_m(const double (&val)[N], double* red, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-  for (int i = 0; i < N; ++i) h[i] = l[i] = 0.f;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const float2* row = reinterpret_cast<const float2*>(partials + r * RF_NACC_MAX);
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      if ((MASK >> i) & 1ull) {
-        const float2 v = __ldcg(row + i);
-        ds_add(h[i], l[i], v.x, v.y);
-      }
+  for (int i = 0; i < N; ++i) {
+    if (!((MASK >> i) & 1ull)) continue;
+    const double v = warp_sum(val[i]);
+    if (lane == 0) red[wid * N + i] = v;
   }
-  block_sum_ds<N, MASK>(h, l, red, out);
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    if ((MASK >> threadIdx.x) & 1ull)
+      for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// One level of the grid's FP64 tree: rows [r0, r1) of
+// partials[row * RF_NACC_MAX + i] summed for the accumulators i in MASK, in a
+// fixed order (warp w takes rows r0 + w, r0 + w + warps, ... with lane i on
+// accumulator i; the warps' sums are then added in warp order).  One warp
+// instruction covers every accumulator, so a level of up to ~40 rows costs
+// a few FP64 instructions per warp.  red: [32*N] shared; result in out[0..N)
+// (shared), valid after the trailing barrier.
+template <int N, unsigned long long MASK>
+__device__ inline void rows_tree(const double* partials, int64_t r0, int64_t r1, double* red,
+                                 double* out) {
+  static_assert(N <= 32, "one lane per accumulator");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (lane < N) {
+    double s = 0.0;
+    if ((MASK >> lane) & 1ull)
+      for (int64_t r = r0 + wid; r < r1; r += nw) s += __ldcg(partials + r * RF_NACC_MAX + lane);
+    red[wid * N + lane] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
 }
 
 // Sum rows [r0, r1) of partials[row * RF_NACC_MAX + i] for i < N, in a fixed

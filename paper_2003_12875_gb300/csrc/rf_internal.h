@@ -32,6 +32,15 @@ typedef unsigned long long uintptr_t;
 #define RF_NACC_MAX RF_NACC(RF_MAXL)
 // blocks whose partial sums fit the static scratch of rf_nll_noalloc
 #define RF_NOALLOC_MAX_BLOCKS 1024
+// Grid reduction of the single-dataset kernels: a two-level fixed-order FP64
+// tree.  The block rows are split into at most RF_TREE_GROUPS contiguous
+// groups; the last block of a group to finish sums the group's rows into a
+// group row (rows gridDim.x + g of the partials), and the last group sums the
+// group rows.  Ticket words (RfWork::counter, RF_COUNTER_WORDS of them):
+// [0] the group ticket, [1] status, [2] Adam step, [RF_TREE_GROUPS ..
+// 2*RF_TREE_GROUPS) one ticket per group.
+#define RF_TREE_GROUPS 32
+#define RF_COUNTER_WORDS (2 * RF_TREE_GROUPS)
 // formula-leaf normalisation: 16-point Gauss-Legendre on RF_FORMULA_PANELS
 // panels, one node per thread, RF_FORMULA_BLOCKS blocks of 128 threads; per
 // leaf 1 + RF_LEAF_MAXP values (log I, then (dI/dp_j)/I)
@@ -104,9 +113,9 @@ struct alignas(16) RfConsts {  // 16-byte multiple: arrays of it are bulk-copied
 
 // Device workspace owned by an rf_graph.
 struct RfWork {
-  double* partials;        // [rows * RF_NACC_MAX]: block partials (single
-                           // dataset) or segment partials (toys)
-  unsigned int* counter;   // [1] block ticket (single dataset)
+  double* partials;        // [rows * RF_NACC_MAX]: block rows and group rows
+                           // (single dataset) or segment partials (toys)
+  unsigned int* counter;   // [RF_COUNTER_WORDS] tickets (single dataset)
   unsigned int* status;    // [1] RF_STATUS_* bits
   // batched mode
   void* toy_consts;        // [max_toys] RfConsts<Real>

@@ -180,11 +180,12 @@ struct Acc {
   }
 };
 
-// A block's row of partial sums and the last block's sum over all rows, in a
-// fixed order.  FP32 evaluation: FP32 pairs (TwoSum) from the thread sums to
-// the final total, one FP64 conversion per accumulator at the very end (the
-// FP64 pipe of this GPU is narrow); a pair sits in the row's 8-byte slot.
-// FP64 evaluation: FP64 throughout.  red: shared, 32 * NA doubles.
+// A block's row of partial sums, in FP64.  FP32 evaluation: the per-thread
+// Kahan sums are added over the block in FP32 pairs (TwoSum; about 48
+// significant bits, the FP64 pipe of this GPU is narrow), and each of the
+// block's pair totals is converted to FP64 once, when the row is written (a
+// few FP64 instructions per block).  FP64 evaluation: FP64 throughout.  red:
+// shared, 32 * NA doubles.
 template <typename Real, int NA, unsigned long long MASK>
 struct BlockRow;
 template <int NA, unsigned long long MASK>
@@ -196,11 +197,10 @@ struct BlockRow<float, NA, MASK> {
 #pragma unroll
     for (int i = 0; i < NA; ++i) ls[i] = -acc.c[i];  // Kahan keeps -(lost low part)
     block_sum_ds2<NA, MASK>(acc.s, ls, reinterpret_cast<float2*>(red), pr);
-    if (threadIdx.x < NA) reinterpret_cast<float2*>(row)[threadIdx.x] = pr[threadIdx.x];
-  }
-  static __device__ __forceinline__ void sum(const double* partials, int64_t rows, double* red,
-                                             double* tot) {
-    rows_sum_ds<NA, MASK>(partials, 0, rows, reinterpret_cast<float2*>(red), tot);
+    if (threadIdx.x < NA)
+      row[threadIdx.x] = ((MASK >> threadIdx.x) & 1ull)
+                             ? (double)pr[threadIdx.x].x + (double)pr[threadIdx.x].y
+                             : 0.0;
   }
 };
 template <int NA, unsigned long long MASK>
@@ -211,14 +211,52 @@ struct BlockRow<double, NA, MASK> {
     double val[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) val[i] = acc.value(i);
-    block_sum<NA>(val, red, bt);
+    block_sum_m<NA, MASK>(val, red, bt);
     if (threadIdx.x < NA) row[threadIdx.x] = bt[threadIdx.x];
   }
-  static __device__ __forceinline__ void sum(const double* partials, int64_t rows, double* red,
-                                             double* tot) {
-    rows_sum<NA>(partials, 0, rows, red, tot);
-  }
 };
+
+// The grid's FP64 tree over the block rows (see RF_TREE_GROUPS): called by
+// every block after its row is written; returns true in the one block that
+// holds the grid totals in tot[0..NA) (shared) afterwards.  The groups are
+// contiguous runs of gsz rows; each level sums its rows in a fixed order, so
+// the totals depend only on the grid size.  Each ticket is reset by the block
+// that takes its last number.
+template <int NA, unsigned long long MASK>
+__device__ __forceinline__ bool grid_tree(double* partials, unsigned int* counter, double* red,
+                                          double* tot) {
+  __shared__ int s_last;
+  const int64_t G = gridDim.x;
+  const int64_t gsz = (G + RF_TREE_GROUPS - 1) / RF_TREE_GROUPS;
+  const int64_t ng = (G + gsz - 1) / gsz;
+  const int64_t g = blockIdx.x / gsz;
+  const int64_t r0 = g * gsz, r1 = (r0 + gsz < G) ? r0 + gsz : G;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int* tk = counter + RF_TREE_GROUPS + g;
+    const bool last = atomicAdd(tk, 1u) == (unsigned)(r1 - r0 - 1);
+    if (last) *tk = 0u;
+    s_last = last ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  rows_tree<NA, MASK>(partials, r0, r1, red, tot);
+  if (threadIdx.x < NA) partials[(G + g) * RF_NACC_MAX + threadIdx.x] = tot[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool last = atomicAdd(counter, 1u) == (unsigned)(ng - 1);
+    if (last) *counter = 0u;
+    s_last = last ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  rows_tree<NA, MASK>(partials, G, G + ng, red, tot);
+  return true;
+}
 
 // EPT events already in registers -> the iteration's partial sums -> acc.
 template <class M, typename Real, int EPT, bool ANYZERO>
@@ -323,7 +361,6 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   __shared__ int ok[RF_MAXL];
   __shared__ double red[32 * NA];
   __shared__ double tot[NA];
-  __shared__ int s_last;
 
   if (W.consts) {
     // constants from the prologue kernel, which this launch may overlap:
@@ -361,16 +398,8 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   }
 
   BlockRow<Real, NA, M::AMASK>::write(acc, red, W.partials + (int64_t)blockIdx.x * RF_NACC_MAX);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(W.counter, 1u) == gridDim.x - 1) ? 1 : 0;
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    BlockRow<Real, NA, M::AMASK>::sum(W.partials, gridDim.x, red, tot);
-    if (threadIdx.x < 32) epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
-    if (threadIdx.x == 0) *W.counter = 0u;
-  }
+  if (grid_tree<NA, M::AMASK>(W.partials, W.counter, red, tot) && threadIdx.x < 32)
+    epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
 }
 
 // Per-event log P(x_i) = beta_ref + ell_i (FP64 output), one event per thread.

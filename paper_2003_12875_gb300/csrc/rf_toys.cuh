@@ -336,7 +336,11 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
   for (int64_t c = 0; c < nch; ++c, c0 += CE) {
     if (!bulk::wait(&bars[s], ph)) {
       if (lane == 0) atomicOr(W.status, RF_STATUS_TIMEOUT_BIT);
-      int ds = s;  // let the copies already issued land before the warp leaves
+      // let the copies already issued land before the warp leaves: first one
+      // more bounded wait on the stage whose copy did not arrive, then on the
+      // stages after it (the status bit stays set whatever these waits give)
+      bulk::wait(&bars[s], ph);
+      int ds = s;
       uint32_t dph = ph;
       for (int64_t d = c + 1; d < nch && d < c + stages; ++d) {
         if (++ds == stages) { ds = 0; dph ^= 1u; }

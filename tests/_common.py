@@ -5,10 +5,12 @@ Tolerances (relative NLL error; gradient error in the L1 metric
 to zero at the minimum):
   FP64 evaluation   NLL <= 1e-12, gradient <= 1e-10
   FP32 evaluation   NLL <= 1e-7,  gradient <= 1e-6
-FP32 evaluation rounds each event's log-density at ~6e-8 relative; the sum is
-compensated and FP64 from the thread level up, so the NLL error stays near the
-per-event rounding (1e-7 allows one unit of the last place in the worst event
-to be systematic); the gradient bound is the target the method is held to.
+FP32 evaluation rounds each event's log-density at ~6e-8 relative; each
+thread's sums are Kahan-compensated in FP32, a block adds them in FP32 pairs
+(about 48 significant bits) and converts its totals to FP64 once, and every
+sum above the block is FP64, so the NLL error stays near the per-event
+rounding (1e-7 allows one unit of the last place in the worst event to be
+systematic); the gradient bound is the target the method is held to.
 Per-event log P: FP64 within 1e-13 * max(1, |log P|), FP32 within
 2e-6 * max(1, |log P|).
 """

@@ -258,24 +258,30 @@ def test_back_to_back_calls_with_changing_parameters(rf):
 @pytest.mark.parametrize("shards", [2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sharded_evaluation_adds_up(rf, shards, prec):
-    """A dataset split into contiguous shards (the multi-process mode): with
-    the extended term weighted 1 on one shard and 0 on the others, the
-    shards' NLLs and gradients add up to the whole dataset's."""
+    """A dataset split into contiguous shards (the multi-process mode of
+    Sec. 5.2): each shard evaluated by its own graph on the GPU, the extended
+    term weighted 1 on one shard and 0 on the others, the shards' (NLL,
+    gradient) added in rank order with compensation (the reduction every rank
+    of sharded_nll runs) -- against the oracle's whole-dataset NLL and
+    gradient."""
     w = datagen.c4(toys=1, nu_s_range=(30_000, 30_001), nu_b_range=(90_000, 90_001))
     spec = w["spec"]
     p = [5.03, 0.51, -0.29, 29_500.0, 91_000.0]
     ev = to_dev(w)
     n = ev.shape[1]
-    whole = torch.cat(rf.Graph(spec, "f64", prec).nll(ev, params_dev(p))).cpu().numpy()
-    total = np.zeros_like(whole)
+    parts = []
     for r in range(shards):
         lo, hi = rf.shard_range(n, r, shards)
         G = rf.Graph(spec, "f64", prec)
         G.set_shard_weight(1.0 if r == 0 else 0.0)
-        total += torch.cat(G.nll(ev[:, lo:hi].contiguous(), params_dev(p))).cpu().numpy()
-    assert rel_nll(total[0], whole[0]) <= TOL[prec]["nll"]
-    _, gref, sc, _ = oracle.nll_scaled(spec, p, w["cols"])
-    assert grad_l1(total[1:], whole[1:], sc, [True] * 5).max() <= TOL[prec]["grad"]
+        parts.append(torch.cat(G.nll(ev[:, lo:hi].contiguous(), params_dev(p))))
+    total = rf.rank_order_sum(torch.stack(parts)).cpu().numpy()
+    v, gref, sc, rc = oracle.nll_scaled(spec, p, w["cols"])
+    assert rc == 0
+    assert rel_nll(total[0], v) <= TOL[prec]["nll"]
+    assert grad_l1(total[1:], gref, sc, [True] * 5).max() <= TOL[prec]["grad"]
+    again = rf.rank_order_sum(torch.stack(parts)).cpu().numpy()
+    assert np.array_equal(again.view(np.int64), total.view(np.int64))
 
 
 def test_gradient_against_finite_differences(rf):

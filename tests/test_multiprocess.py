@@ -112,31 +112,65 @@ def _shard_worker(rank, world, port, q):
         lo, hi = rf.shard_range(n, rank, world)
         p = [5.02, 0.51, -0.29, 790.0, 2010.0]
         G = _FakeGraph(w["spec"], w["cols"][:, lo:hi], p)
-        out = rf.sharded_nll(G, torch.empty(1, hi - lo), torch.tensor(p), rank)
-        q.put((rank, G.w, out.numpy().tolist()))
+        runs = [rf.sharded_nll(G, torch.empty(1, hi - lo), torch.tensor(p), rank).numpy()
+                for _ in range(2)]
+        q.put((rank, G.w, [r.tolist() for r in runs],
+               [r.view(np.int64).tolist() for r in runs]))
     finally:
         dist.destroy_process_group()
 
 
-def test_sharded_nll_helper_reduces_over_ranks():
-    """paper_2003_12875_gb300.sharded_nll on three gloo ranks: the extended
-    term is weighted on rank 0 only and the all-reduced result is the whole
-    dataset's NLL and gradient (oracle shards stand in for the GPU)."""
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_nll_helper_reduces_over_ranks(world):
+    """paper_2003_12875_gb300.sharded_nll on gloo ranks: the extended term is
+    weighted on rank 0 only, the all-gathered shard values are added in rank
+    order, and the result is the whole dataset's NLL and gradient, bit for bit
+    the same on every rank and in two runs (oracle shards stand in for the
+    GPU)."""
     import datagen
     import oracle
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_shard_worker, args=(r, 3, port, q)) for r in range(3)]
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
     for pr in procs:
         pr.start()
-    res = sorted(q.get(timeout=180) for _ in range(3))
+    res = sorted(q.get(timeout=180) for _ in range(world))
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    assert [r[1] for r in res] == [1.0, 0.0, 0.0]
+    assert [r[1] for r in res] == [1.0] + [0.0] * (world - 1)
+    bits = res[0][3][0]
+    for _, _, _, b in res:
+        assert b[0] == bits and b[1] == bits        # every rank, both runs
     w = datagen.c4(toys=1, nu_s_range=(800, 800.001), nu_b_range=(2000, 2000.001))
     v, g, rc = oracle.nll(w["spec"], [5.02, 0.51, -0.29, 790.0, 2010.0], w["cols"])
-    for _, _, out in res:
-        assert abs(out[0] - v) <= 1e-11 * abs(v)
-        np.testing.assert_allclose(out[1:], g, rtol=1e-9, atol=1e-9)
+    out = res[0][2][0]
+    assert abs(out[0] - v) <= 1e-11 * abs(v)
+    np.testing.assert_allclose(out[1:], g, rtol=1e-9, atol=1e-9)
+
+
+def test_rank_order_sum_is_compensated_and_ordered():
+    """rank_order_sum against the exactly rounded sum (math.fsum) on values
+    whose plain sum loses everything, and its fixed order: permuting the rows
+    may change the bits, repeating the call never does."""
+    import math
+
+    import torch
+
+    import paper_2003_12875_gb300 as rf
+    rows = torch.tensor([[1e16, 3.0], [1.0, -1e-3], [-1e16, 2.5], [1.0, 7e-4]],
+                        dtype=torch.float64)
+    got = rf.rank_order_sum(rows).numpy()
+    for j in range(2):
+        assert got[j] == math.fsum(rows[:, j].tolist())
+    plain = 0.0
+    for v in rows[:, 0].tolist():
+        plain += v
+    assert plain == 1.0 and got[0] == 2.0               # the plain sum loses a 1
+    r = np.random.default_rng(3).standard_normal((8, 5)) * 10.0 ** np.arange(5)
+    t = torch.from_numpy(r)
+    a, b = rf.rank_order_sum(t), rf.rank_order_sum(t.clone())
+    assert torch.equal(a, b)
+    for j in range(5):
+        assert abs(float(a[j]) - math.fsum(r[:, j])) <= 4e-16 * np.abs(r[:, j]).sum()
