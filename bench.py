@@ -175,6 +175,49 @@ def algorithmic_instr_per_event(spec: dict, ept: int = REF_EPT, f64_columns: boo
     return total
 
 
+# The roofline of a step: t_roof = max(n B / BW, n sum_op N_op / R_op).  N_op
+# are the minimal operation counts per event of each workload's formulas (the
+# leaf densities, the log of the mixture, the adjoint sums), B the bytes a step
+# must read per event, BW the measured HBM copy bandwidth, and R_op the
+# throughput of each operation measured alone on this GPU by rf_microbench --
+# for FP32 evaluation the hardware approximations the kernels issue (base-2
+# exp and log, reciprocal, square root: the fastest form of each, so the
+# roofline is the strict one), for FP64 evaluation the FP64 functions the
+# kernels call (exp2, log2, division, sqrt) and the FP64 FMA.
+OPS_PER_EVENT = {
+    "c1": {"fma": 6},                                          # 3 FMA + 3 sums
+    "c2": {"exp": 2, "log": 1, "rcp": 1, "fma": 6},
+    "c3": {"log": 1, "rcp": 1, "fma": 16},                     # Clenshaw(4) 8 + 8 sums
+    "c4": {"exp": 2, "log": 1, "rcp": 1, "fma": 6},
+    "c5": {"exp": 2, "log": 2, "sqrt": 1, "rcp": 1, "fma": 8},
+}
+RATE_KEYS = {
+    "fp32": {"exp": "ex2_approx_f32", "log": "lg2_approx_f32", "rcp": "rcp_approx_f32",
+             "sqrt": "sqrt_approx_f32", "fma": "fp32_fma"},
+    "fp64": {"exp": "exp2_f64", "log": "log2_f64", "rcp": "div_f64", "sqrt": "sqrt_f64",
+             "fma": "fp64_fma"},
+}
+
+
+def roofline_8d(cfg: str, prec: str, n: int, bytes_per_event: float, step_ms: float,
+                rates: dict, hbm_gbs: float) -> dict:
+    """The fraction of the roofline reached by a step of `n` events that took
+    step_ms: t_roof / t_step, with t_roof from the op list above."""
+    ops = OPS_PER_EVENT[cfg]
+    t_ops = {k: n * v / rates[RATE_KEYS[prec][k]] for k, v in ops.items()}
+    t_compute = sum(t_ops.values())
+    t_hbm = n * bytes_per_event / (hbm_gbs * 1e9)
+    t_roof = max(t_compute, t_hbm)
+    t = step_ms * 1e-3
+    return {"bound": "alu" if t_compute >= t_hbm else "hbm", "unit": "events/s",
+            "achieved": n / t, "peak": n / t_roof, "frac": t_roof / t,
+            "t_roof_us": t_roof * 1e6, "t_compute_us": t_compute * 1e6, "t_hbm_us": t_hbm * 1e6,
+            "step_us": t * 1e6, "ops_per_event": ops,
+            "op_us": {k: v * 1e6 for k, v in t_ops.items()},
+            "bytes_per_event": bytes_per_event,
+            "rates": {RATE_KEYS[prec][k]: rates[RATE_KEYS[prec][k]] for k in ops}}
+
+
 def profiled_traffic(kernel_hash: str):
     """DRAM bytes per launch from a committed ncu summary taken on exactly this
     kernel (matched by its source hash), else None."""
@@ -209,7 +252,7 @@ def job_throughput(events_per_rank: int, world: int, ms_per_step: float) -> floa
     return world * events_per_rank / (ms_per_step * 1e-3)
 
 
-def toy_study(rf, torch, toys=4096, iters=50):
+def toy_study(rf, torch, toys=4096, iters=50, rates=None, hbm_gbs=None):
     """Toy NLLs/s: 4096 extended Gauss+Exp toys (about 1.3e8 FP64 events), one
     batched evaluation and a 50-iteration Adam fit replayed from a CUDA graph,
     FP32 and FP64 per-event arithmetic."""
@@ -241,6 +284,11 @@ def toy_study(rf, torch, toys=4096, iters=50):
                      "events_per_s": res["events"] / (t_eval * 1e-3),
                      "fit_ms": t_fit, "fit_toy_iters_per_s": toys * iters / (t_fit * 1e-3),
                      "launches_per_fit": G.last_launches(), "kernel": G.uses_jit()}
+        if rates:
+            # FP32 evaluation reads the FP32 copy of the columns made once at bind
+            res[prec]["roofline"] = roofline_8d("c4", prec, res["events"],
+                                                4 if prec == "fp32" else 8, t_eval, rates,
+                                                hbm_gbs)
     # toy generation on the device: the same 4096 toys (per-component counts
     # = the workload's signal / background split), FP64 columns
     G = rf.Graph(w["spec"], "f64", "fp64")
@@ -263,7 +311,7 @@ def toy_study(rf, torch, toys=4096, iters=50):
     return res
 
 
-def small_configs(rf, torch):
+def small_configs(rf, torch, rates=None, hbm_gbs=None):
     """Per-call latency of the small workloads (C1 1e4, C2 1e6, C3 1e7 events):
     a host loop of calls on one stream, and the same calls replayed from a
     CUDA graph (GPU time only); C2 (8 MB, L2-resident) also with L2 flushed
@@ -318,6 +366,13 @@ def small_configs(rf, torch):
                     ts.append(a.elapsed_time(b) * 1e3)
                 r["cold_us_median"] = statistics.median(ts)
             r["events_per_s_graph"] = n / (r["graph_us"] * 1e-6) if r.get("graph_us") else None
+            if rates and r.get("graph_us"):
+                bpe = w["cols"].shape[0] * (4 if w["dtype"] == "f32" else 8)
+                r["roofline"] = roofline_8d(name, prec, n, bpe, r["graph_us"] * 1e-3, rates,
+                                            hbm_gbs)
+                if "cold_us_median" in r:
+                    r["roofline_cold"] = roofline_8d(name, prec, n, bpe,
+                                                     r["cold_us_median"] * 1e-3, rates, hbm_gbs)
             res[f"{name}_{prec}"] = r
     res["formula_leaves"] = formula_vs_builtin(rf, torch)
     return res
@@ -399,9 +454,9 @@ def toy_bench(args, rf, torch, rank, world, pk):
         dist.barrier()
     clk = clocks.stop()
     ms = max_over_ranks(a.elapsed_time(b), dist, "cuda") / args.steps
-    # roofline of the step (prep + segment + finalize kernels): FP32 issue for
-    # FP32 evaluation (columns read as FP32, rounded once at bind), with the
-    # HBM figure beside it
+    # roofline of the step (prep + segment + finalize kernels): the op-list
+    # roofline (FP32 evaluation reads the FP32 copy of the columns made once at
+    # bind: 4 bytes per event), with the FP32 issue fraction and HBM beside it
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sm_mhz = float(pk.get("sm_max_mhz") or 2070.0)
     col_bytes = 4 if args.precision == "fp32" else 8
@@ -410,19 +465,22 @@ def toy_bench(args, rf, torch, rank, world, pk):
            "frac": hbm_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
            "bytes_per_launch": n * col_bytes}
     traffic = profiled_traffic(G.toy_kernel_hash()) if G.uses_jit() else None
+    rates = rf.microbench()
+    roofline = {**roofline_8d("c4", args.precision, n, col_bytes, ms, rates, pk["hbm_gbs"]),
+                "traffic": traffic, "kernel": "rf_toys_jit (+ prep, finalize)",
+                "peak_source": "derived: per-event operation counts x operation rates measured "
+                               "alone on this GPU (rf_microbench), HBM bandwidth of "
+                               + pk["source"],
+                "launch_ms": ms, "hbm": hbm}
     if args.precision == "fp32":
         instr = algorithmic_instr_per_event(w["spec"], REF_EPT, False)
         peak = sms * 128 * sm_mhz * 1e6
         achieved = instr * n / (ms * 1e-3)
-        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                    "unit": "G FP32-lane instr/s", "frac": achieved / peak, "traffic": traffic,
-                    "kernel": "rf_toys_jit (+ prep, finalize)",
-                    "algorithmic_instr_per_event": instr,
-                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
-                    "launch_ms": ms, "hbm": hbm}
-    else:
-        roofline = {"bound": "hbm", **hbm, "traffic": traffic, "kernel": "rf_toys_jit",
-                    "launch_ms": ms}
+        roofline["issue"] = {"achieved": achieved / 1e9, "peak": peak / 1e9,
+                             "unit": "G FP32-lane instr/s", "frac": achieved / peak,
+                             "instr_per_event": instr,
+                             "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x "
+                                            f"{sm_mhz:.0f} MHz"}
     line = {"metric": METRIC, "value": job_throughput(n, world, ms), "unit": "events/s",
             "toy_nll_per_s": world * toys / (ms * 1e-3), "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -613,33 +671,36 @@ def main():
                       else "read in place by the kernel over the host link") + ")"}
 
     # ----------------------------------------------------------- roofline
-    # The fused FP32-eval kernel is bound by instruction issue (transcendentals
-    # and selects per event), not by HBM: report it against the FP32 issue
-    # peak of the chip (SMs x 128 lanes x max SM clock), with the HBM figure
-    # beside it.  per_launch is the time per call; back to back, a call's FP64
-    # prologue overlaps the previous call's event pass.
+    # The roofline of the step (t_roof above: the slower of the event bytes at
+    # the measured HBM bandwidth and the per-event operations at their
+    # measured rates); per_launch is the time per call (back to back, a call's
+    # FP64 prologue overlaps the previous call's event pass).  Beside it: the
+    # FP32 issue fraction by this kernel's own instruction count, and HBM.
     bytes_per_launch = n * w["cols"].shape[0] * col_bytes
     hbm_achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = float(pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
-    launch_cfg = G.get_launch()
     traffic = profiled_traffic(G.kernel_hash()) if G.uses_jit() else None
     hbm = {"achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_achieved / pk["hbm_gbs"], "peak_source": pk["source"],
            "bytes_per_launch": bytes_per_launch}
+    rates = rf.microbench()
+    r8 = roofline_8d(args.workload, args.precision, n, w["cols"].shape[0] * col_bytes,
+                     per_launch, rates, pk["hbm_gbs"])
+    roofline = {**r8, "traffic": traffic, "kernel": "rf_fused_jit (+ prologue)",
+                "peak_source": "derived: per-event operation counts x operation rates measured "
+                               "alone on this GPU (rf_microbench), HBM bandwidth of "
+                               + pk["source"],
+                "launch_ms": per_launch, "hbm": hbm}
     if args.precision == "fp32":
         instr = algorithmic_instr_per_event(spec, REF_EPT, w["dtype"] == "f64")
         peak = sms * 128 * sm_mhz * 1e6
         achieved = instr * n / (per_launch * 1e-3)
-        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                    "unit": "G FP32-lane instr/s", "frac": achieved / peak,
-                    "traffic": traffic, "kernel": "rf_fused_jit (+ prologue)",
-                    "algorithmic_instr_per_event": instr,
-                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
-                    "launch_ms": per_launch, "hbm": hbm}
-    else:
-        roofline = {"bound": "hbm", **hbm, "traffic": traffic, "kernel": "rf_fused_jit",
-                    "launch_ms": per_launch}
+        roofline["issue"] = {"achieved": achieved / 1e9, "peak": peak / 1e9,
+                             "unit": "G FP32-lane instr/s", "frac": achieved / peak,
+                             "instr_per_event": instr,
+                             "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x "
+                                            f"{sm_mhz:.0f} MHz"}
 
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -677,7 +738,10 @@ def main():
         torch.cuda.synchronize()
         t64 = a.elapsed_time(b) / 3
         ex["fused_fp64_eval"] = {"events_per_s": n / (t64 * 1e-3), "ms": t64,
-                                 "nll": float(o64[0].item())}
+                                 "nll": float(o64[0].item()),
+                                 "roofline": roofline_8d(args.workload, "fp64", n,
+                                                         w["cols"].shape[0] * col_bytes, t64,
+                                                         rates, pk["hbm_gbs"])}
         # plain FP64 node-by-node baseline, gradient by central differences
         v, g = G.nll_plain(ev, params)
         torch.cuda.synchronize()
@@ -694,9 +758,9 @@ def main():
         b.record()
         torch.cuda.synchronize()
         ex["plain_fp64_nll_only_ms"] = a.elapsed_time(b)
-        ex["microbench_ops_per_s"] = rf.microbench()
-        ex["small_configs"] = small_configs(rf, torch)
-        ex["toys"] = toy_study(rf, torch)
+        ex["microbench_ops_per_s"] = rates
+        ex["small_configs"] = small_configs(rf, torch, rates, pk["hbm_gbs"])
+        ex["toys"] = toy_study(rf, torch, rates=rates, hbm_gbs=pk["hbm_gbs"])
         line["extras"] = ex
 
     if rank == 0 and world == 1 and not args.no_cpu:

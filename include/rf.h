@@ -20,10 +20,13 @@
  *   RF_CHEB   (c_1..c_m), m <= 4     1 + sum_j c_j T_j(x'), x' = (2x-lo-hi)/(hi-lo)
  *   RF_CB     (m0, sigma, alpha, n)  Crystal Ball; alpha > 0: tail below m0
  *   RF_ARGUS  (m0, c, p)             x tau^p exp(c tau), tau = 1-(x/m0)^2, x < m0;
- *             a fixed p must be 1/2 (its one-log form and closed-form
- *             integral); a free p takes any p > 0, its integral and d/dp from
- *             positive-term series of the incomplete gamma function (toy
- *             generation draws p = 1/2 only)
+ *             p = 1/2 has a one-log form and a closed-form integral; any other
+ *             p > 0 takes the general form (two logs per event; the integral
+ *             and d/dp from positive-term series of the incomplete gamma
+ *             function).  A free p always takes the general form; a fixed p
+ *             takes it when rf_graph_desc.param_values gives it a value other
+ *             than 1/2 (without values, a fixed p must be 1/2).  Toy
+ *             generation draws p = 1/2 only
  *   RF_JOHNSON (mu, lambda, gamma, delta)  Johnson's SU (Sec. 3): with
  *             z = (x-mu)/lambda, w = gamma + delta asinh z standard normal:
  *             delta / (lambda sqrt(2 pi (1+z^2))) exp(-w^2/2)
@@ -161,6 +164,12 @@ typedef struct {
                                  (blocks, groups, a toy's segments) and the
                                  gradient epilogue in FP64.
                                  RF_EVAL_FP64: all FP64                       */
+  const double* param_values; /* [n_params] or NULL, host, read at validate /
+                                 compile only: values known when the graph is
+                                 compiled.  They select forms, not results:
+                                 an ARGUS p that is fixed at a value other
+                                 than 1/2 here gets the general-p form (calls
+                                 still take their parameters from `params`) */
 } rf_graph_desc;
 
 typedef struct rf_graph rf_graph;
@@ -422,7 +431,11 @@ rf_status rf_check_d2f(const double* x, float* y_fast, float* y_ref, int64_t n,
  * packed FP32x2 FMA instructions; then latencies in ns per dependent
  * operation within one warp: out[12] FP64 FMA with 1 active lane, out[13]
  * FP64 FMA with 32 active lanes, out[14] exp (FP64) with 1 lane, out[15]
- * exp (FP64) with 32 lanes.  out has 16 entries.
+ * exp (FP64) with 32 lanes; then throughputs again: out[16] sqrtf (IEEE),
+ * out[17] the hardware FP32 square root (sqrt.approx), out[18] log2 (FP64),
+ * out[19] exp2 (FP64), out[20] FP64 division, out[21] the hardware base-2
+ * log (lg2.approx), out[22] the hardware base-2 exp (ex2.approx), out[23]
+ * sqrt (FP64).  out has 24 entries.
  * Host-synchronous; allocates a small scratch buffer. */
 rf_status rf_microbench(double* out);
 

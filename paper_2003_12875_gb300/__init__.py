@@ -56,7 +56,7 @@ class _Desc(C.Structure):
                 ("n_obs", C.c_int32), ("obs_lo", C.POINTER(C.c_double)),
                 ("obs_hi", C.POINTER(C.c_double)), ("n_params", C.c_int32),
                 ("param_fixed", C.POINTER(C.c_uint8)), ("column_dtype", C.c_int32),
-                ("eval_precision", C.c_int32)]
+                ("eval_precision", C.c_int32), ("param_values", C.POINTER(C.c_double))]
 
 
 class _Launch(C.Structure):
@@ -174,9 +174,13 @@ def make_desc(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64
     npar = len(spec["params"])
     fixed = spec.get("fixed")
     fx = (C.c_uint8 * max(npar, 1))(*[1 if (fixed and fixed[j]) else 0 for j in range(npar)])
+    # the spec's parameter values at compile time (they select forms only,
+    # e.g. the general ARGUS form for a p fixed away from 1/2)
+    vals = (C.c_double * max(npar, 1))(*[float(v) for v in spec["params"]])
     d = _Desc(len(nodes), arr, spec.get("root", len(nodes) - 1), len(rng), lo, hi, npar,
-              fx, 0 if column_dtype == "f32" else 1, 0 if eval_precision == "fp32" else 1)
-    return d, (arr, lo, hi, fx, texts)
+              fx, 0 if column_dtype == "f32" else 1, 0 if eval_precision == "fp32" else 1,
+              vals)
+    return d, (arr, lo, hi, fx, texts, vals)
 
 
 def validate(spec: dict, column_dtype: str = "f64", eval_precision: str = "fp64") -> int:
@@ -439,12 +443,14 @@ class RFNll(torch.autograd.Function):
 def microbench() -> dict:
     """Measured per-operation throughput (operations/s) on the current GPU,
     and single-warp FP64 latencies (ns per dependent operation)."""
-    out = (C.c_double * 16)()
+    out = (C.c_double * 24)()
     _check(load().rf_microbench(out))
     keys = ["fp32_fma", "expf", "logf", "rcp_f32", "fp64_fma", "exp_f64", "log_f64", "erf_f64",
             "log_fast_f32", "exp_neg_f32", "rcp_approx_f32", "fp32_fma_packed_x2",
             "fp64_fma_latency_ns_1lane", "fp64_fma_latency_ns_32lanes",
-            "exp_f64_latency_ns_1lane", "exp_f64_latency_ns_32lanes"]
+            "exp_f64_latency_ns_1lane", "exp_f64_latency_ns_32lanes",
+            "sqrtf", "sqrt_approx_f32", "log2_f64", "exp2_f64", "div_f64", "lg2_approx_f32",
+            "ex2_approx_f32", "sqrt_f64"]
     return dict(zip(keys, list(out)))
 
 

@@ -206,8 +206,12 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
       int gm = 0;
       for (int j = 0; j < n.n_params; ++j)
         if (!fixed(n.params[j])) gm |= 1 << j;
-      // ARGUS: a free p selects the general-p form (d/dp included); a fixed
-      // p must be 1/2 at run time (checked in the prologue)
+      // ARGUS: a free p selects the general-p form (d/dp included); so does
+      // a fixed p whose compile-time value is not 1/2 (without d/dp);
+      // otherwise a fixed p must be 1/2 at run time (checked in the prologue)
+      if (n.type == RF_ARGUS && !(gm & 4) && d->param_values &&
+          d->param_values[n.params[2]] != 0.5)
+        gm |= RF_ARGUS_GENERAL;
       L.gmask = gm;
     }
   }

@@ -30,6 +30,26 @@ template <> struct Op<11> {
   }
 };
 
+// more single operations for the roofline's op list: IEEE sqrtf, the
+// hardware square root, FP64 log2 / exp2 / division / square root (the FP64
+// kernels' per-event functions), and the hardware base-2 log / exp as the
+// per-event code issues them (one instruction each)
+template <> struct Op<12> { typedef float T; static __device__ __forceinline__ float f(float a) { return sqrtf(a + 1.0f); } };
+template <> struct Op<13> {
+  typedef float T;
+  static __device__ __forceinline__ float f(float a) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a + 1.0f));
+    return r;
+  }
+};
+template <> struct Op<14> { typedef double T; static __device__ __forceinline__ double f(double a) { return log2(a + 2.0); } };
+template <> struct Op<15> { typedef double T; static __device__ __forceinline__ double f(double a) { return exp2(-a); } };
+template <> struct Op<16> { typedef double T; static __device__ __forceinline__ double f(double a) { return 1.0 / (a + 1.0); } };
+template <> struct Op<17> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::lg2_fast(a + 2.0f); } };
+template <> struct Op<18> { typedef float T; static __device__ __forceinline__ float f(float a) { return rf::ex2_fast(-a); } };
+template <> struct Op<19> { typedef double T; static __device__ __forceinline__ double f(double a) { return sqrt(a + 1.0); } };
+
 template <int OP>
 __global__ void __launch_bounds__(256) mb_kernel(typename Op<OP>::T* sink, int iters) {
   typedef typename Op<OP>::T T;
@@ -133,6 +153,14 @@ int rf_run_microbench(double* out) {
   out[13] = lat_ns<4>(sink, 200000, 32);
   out[14] = lat_ns<5>(sink, 20000, 1);
   out[15] = lat_ns<5>(sink, 20000, 32);
+  out[16] = run<12>(sms, sink, 1024);
+  out[17] = run<13>(sms, sink, 1024);
+  out[18] = run<14>(sms, sink, 32);
+  out[19] = run<15>(sms, sink, 32);
+  out[20] = run<16>(sms, sink, 64);
+  out[21] = run<17>(sms, sink, 1024);
+  out[22] = run<18>(sms, sink, 1024);
+  out[23] = run<19>(sms, sink, 64);
   e = cudaGetLastError();
   cudaFree(sink);
   return (int)e;

@@ -30,7 +30,7 @@ __global__ void plain_leaf_kernel(const RfProgram P, int k,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double u, g[RF_LEAF_MAXP];
-    eval_leaf<double>(L.type, L.gmask & 4, (double)col[i], pc, u, g);  // ARGUS form
+    eval_leaf<double>(L.type, L.gmask & (4 | RF_ARGUS_GENERAL), (double)col[i], pc, u, g);  // ARGUS form
     out[i] = exp(kLn2 * u - lnI);  // u is in base-2 units
   }
 }

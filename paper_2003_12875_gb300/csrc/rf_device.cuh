@@ -290,7 +290,7 @@ static __device__ __noinline__ bool leaf_lognorm(int type, int gm, const double*
       double b = fmin(hi, m0);
       double ta = 1.0 - (lo / m0) * (lo / m0), tb = 1.0 - (b / m0) * (b / m0);
       double h = 0.5 * m0 * m0;
-      if (gm & 4) {  // p free: any p > 0, with d/dp
+      if (gm & (4 | RF_ARGUS_GENERAL)) {  // general p (free, or fixed away from 1/2)
         if (!(p > 0.0)) return false;
         // I = (m0^2/2) [J(tau_a) - J(tau_b)]; d/dc takes J at p + 1; d/dm0
         // adds the limits' motion: 2I/m0 + (lo^2/m0) tau_a^p e^{c tau_a}
@@ -309,7 +309,7 @@ static __device__ __noinline__ bool leaf_lognorm(int type, int gm, const double*
         dln[2] = h * (Pa - Pb) / I;
         return I > 0.0 && isfinite(I);
       }
-      if (p != 0.5) return false;  // a fixed p must be 1/2 (the kernels' p = 1/2 form)
+      if (p != 0.5) return false;  // the p = 1/2 form was compiled for this leaf
       double Ja, Ka, Ea, Jb, Kb, Eb;
       argus_int2(ta, c, &Ja, &Ka, &Ea);
       argus_int2(tb, c, &Jb, &Kb, &Eb);
@@ -427,10 +427,10 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       pc[2] = (Real)(1.0 / (th[0] * th[0]));
       pc[3] = (Real)(th[1] * kLog2e);  // c in base-2 units (for u)
       pc[4] = (Real)(2.0 / th[0]);
-      pc[5] = (Real)th[2];  // p (general-p form)
+      split_hi_lo(th[2], pc[5], pc[7]);  // p (general-p form), hi + lo
       pc[6] = (Real)th[1];  // c (for the m0 derivative)
       K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
-      if (L.gmask & 4) K.dtheta[k][2] = (double)pc[5] - th[2];
+      if (L.gmask & 4) K.dtheta[k][2] = ((double)pc[5] + (double)pc[7]) - th[2];
       K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
     }
@@ -685,9 +685,10 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   }
 }
 
-// ARGUS: u = log x + p log tau + c tau, -inf at and above m0.  Without the
-// p derivative (GM bit 2 clear) p is 1/2 and u = (1/2) log(x^2 tau) + c tau
-// (one log); with it, p = pc[5] and d u/d p = log tau.
+// ARGUS: u = log x + p log tau + c tau, -inf at and above m0.  In the
+// general form (GM bit 2: p free, or RF_ARGUS_GENERAL: p fixed away from 1/2)
+// p = pc[5], and with bit 2 d u/d p = log tau; otherwise p is 1/2 and
+// u = (1/2) log(x^2 tau) + c tau (one log).
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, Real& u,
                                            Real (&g)[RF_LEAF_MAXP]) {
@@ -696,12 +697,15 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
   Real sm = (pc[0] + x) + pc[1];
   Real tau = dm * sm * pc[2];
   bool ok = tau > Real(0);
-  const Real p = (GM & 4) ? pc[5] : Real(0.5);
+  constexpr bool general = (GM & (4 | RF_ARGUS_GENERAL)) != 0;
+  const Real p = general ? pc[5] : Real(0.5);
   // pc[3] = c log2(e) for u (base 2), pc[6] = c for the derivatives
-  if (GM & 4) {
+  if (general) {
+    // p = pc[5] + pc[7] (hi + lo: a fixed p has no d/dp sum to correct its
+    // rounding with)
     const Real lt = F::lg2(tau);
-    u = ok ? F::lg2(x) + p * lt + pc[3] * tau : F::ninf();
-    g[2] = ok ? Real(kLn2) * lt : Real(0);
+    u = ok ? (F::lg2(x) + p * lt + pc[3] * tau) + pc[7] * lt : F::ninf();
+    g[2] = ((GM & 4) && ok) ? Real(kLn2) * lt : Real(0);
   } else {
     u = ok ? Real(0.5) * F::lg2(x * x * tau) + pc[3] * tau : F::ninf();
     g[2] = Real(0);
@@ -752,7 +756,7 @@ __device__ __forceinline__ void eval_leaf(int type, int gm, Real x,
     case RFL_CHEB: leaf_cheb<Real, 15>(x, pc, u, g); break;
     case RFL_CB: leaf_cb<Real, 15>(x, pc, u, g); break;
     case RFL_ARGUS:
-      if (gm & 4) leaf_argus<Real, 7>(x, pc, u, g);
+      if (gm & (4 | RF_ARGUS_GENERAL)) leaf_argus<Real, 7>(x, pc, u, g);
       else if (gm & 1) leaf_argus<Real, 3>(x, pc, u, g);
       else leaf_argus<Real, 2>(x, pc, u, g);
       break;

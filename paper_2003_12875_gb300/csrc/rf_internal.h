@@ -49,6 +49,9 @@ typedef unsigned long long uintptr_t;
 #define RF_FORMULA_NV (1 + RF_LEAF_MAXP)
 
 enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
+// gmask bit of an ARGUS leaf whose fixed p is not 1/2 (general-p form, no
+// d/dp accumulator; bits 0..3 are the per-parameter gradient bits)
+#define RF_ARGUS_GENERAL 16
 // device status bits (same values as RF_STATUS_* in include/rf.h)
 #define RF_STATUS_PARAM_DOMAIN_BIT 1u
 #define RF_STATUS_NONFINITE_BIT 2u
@@ -70,7 +73,9 @@ struct RfLeafProg {
   int32_t comp;      // component index
   int32_t npar;      // parameters of this leaf
   int32_t par[RF_LEAF_MAXP];  // global parameter slots
-  int32_t gmask;     // bit j: gradient of leaf param j is wanted
+  int32_t gmask;     // bit j: gradient of leaf param j is wanted; ARGUS:
+                     // RF_ARGUS_GENERAL selects the general-p form for a
+                     // fixed p (a free p, bit 2, always takes it)
   int32_t pad_;
   double lo, hi;     // observable range
 };

@@ -42,6 +42,7 @@ SMALL = {
     "c5": lambda: datagen.c5(3_000, 300_000),
     "johnson": lambda: datagen.johnson_exp(20_011, 80_000),
     "c5_free_p": lambda: _free_p(datagen.c5(3_000, 300_000)),
+    "c5_fixed_p": lambda: _fixed_p(datagen.c5(3_000, 300_000), 0.8),
 }
 OFF_MIN = {  # gradient checks away from the minimum
     "c1": [0.25, 1.1],
@@ -51,6 +52,7 @@ OFF_MIN = {  # gradient checks away from the minimum
     "c5": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.5, 3_050.0, 299_000.0],
     "johnson": [4.05, 0.78, -0.45, 1.62, -0.21, 19_800.0, 80_300.0],
     "c5_free_p": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.58, 3_050.0, 299_000.0],
+    "c5_fixed_p": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.8, 3_050.0, 299_000.0],
 }
 
 
@@ -60,6 +62,18 @@ def _free_p(w):
     spec["fixed"] = list(spec["fixed"])
     spec["fixed"][6] = False
     return {**w, "spec": spec}
+
+
+def _fixed_p(w, pval):
+    """The C5 model with the ARGUS power fixed at pval != 1/2: the graph is
+    compiled with that value, which selects the general-p form without a
+    d/dp sum."""
+    spec = dict(w["spec"])
+    spec["params"] = list(spec["params"])
+    spec["params"][6] = pval
+    return {**w, "spec": spec}
+
+
 _cache = {}
 
 
@@ -97,7 +111,7 @@ def test_nll_and_gradient_match_oracle(rf, name, prec, jit):
 
 @pytest.mark.parametrize("jit", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson", "c5_free_p"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson", "c5_free_p", "c5_fixed_p"])
 def test_per_event_log_probability(rf, name, prec, jit):
     w, p, *_ = workload(name)
     sub = {**w, "cols": w["cols"][:, :20_011]}
@@ -619,8 +633,9 @@ def test_microbench_reports_positive_rates(rf):
 
 
 def test_argus_fixed_p_other_than_one_half_is_a_domain_error(rf):
-    """A fixed p runs the p = 1/2 form; another value sets the parameter-
-    domain bit (a free p takes any p > 0)."""
+    """A p fixed at 1/2 when the graph is compiled runs the p = 1/2 form;
+    calling it with another value sets the parameter-domain bit (a free p
+    takes any p > 0, and so does a p fixed away from 1/2 at compile time)."""
     w, p, *_ = workload("c5")
     G = rf.Graph(w["spec"], "f32", "fp32")
     q = list(p)
