@@ -176,7 +176,38 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
       if ((P.leaf[k].gmask >> j) & 1)
         o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += w[" << P.leaf[k].comp << "] * g" << k
           << "[" << j << "];\n";
-  o << "  }\n};\n";
+  o << "  }\n";
+  // The same event in FP64 on the FP64 constants, for FP32 evaluation of a
+  // call or toy with a coefficient exactly 0 (x: the column values in their
+  // own precision); returns log2 P - beta_ref / ln 2.
+  o << "  static __device__ __noinline__ double event_exact(const RfConsts<float>* __restrict__ Kp, "
+       "const double* __restrict__ x, float* __restrict__ q) {\n"
+       "    const RfConsts<float>& K = *Kp;\n";
+  for (int k = 0; k < NL; ++k) {
+    const RfLeafProg& L = P.leaf[k];
+    o << "    double u" << k << ", g" << k << "[4];\n    ";
+    if (L.type == RFL_FORMULA)
+      o << "rf::formula_leaf<RfFormula" << k << ", double, " << L.gmask << ">";
+    else
+      o << "rf::" << leaf_fn(L.type) << "<double, " << L.gmask << ">";
+    o << "(x[" << L.col << "], K.pcd[" << k << "], u" << k << ", g" << k << ");\n";
+  }
+  o << "    double v[" << NC << "], w[" << NC << "];\n";
+  for (int c = 0; c < NC; ++c) o << "    v[" << c << "] = K.delta_d[" << c << "]" << usum[c] << ";\n";
+  o << "    const double ell = rf::lse<double, " << NC << ">(v, w);\n    q[0] += (float)ell;\n";
+  if (NC == 1) {
+    o << "    q[1] += 1.0f;\n";
+  } else {
+    for (int c = 0; c < NC; ++c)
+      o << "    q[" << 1 + c << "] += (float)(((K.zero_mask >> " << c << ") & 1) ? exp2(K.delta_nc_d["
+        << c << "]" << usum[c] << " - ell) : w[" << c << "]);\n";
+  }
+  for (int k = 0; k < NL; ++k)
+    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+      if ((P.leaf[k].gmask >> j) & 1)
+        o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += (float)(w[" << P.leaf[k].comp
+          << "] * g" << k << "[" << j << "]);\n";
+  o << "    return ell;\n  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";
   // The fused kernel is declared for min_blocks resident blocks of 256

@@ -334,7 +334,58 @@ __device__ inline void split_hi_lo(double v, Real& hi, Real& lo) {
   lo = (Real)(v - (double)hi);
 }
 
-// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k] and lnI_out.
+// Leaf L's per-event constants in type T from its parameters th (FP64):
+// location-like values split into T pairs (hi, lo), the rest rounded to T.
+template <typename T>
+__device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
+  for (int j = 0; j < RF_PC; ++j) pc[j] = T(0);
+  switch (L.type) {
+    case RFL_GAUSS:  // d = kG (x - mu) / sigma, so that u (base 2) = -d^2
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (T)(kG / th[1]);
+      break;
+    case RFL_EXP:
+      pc[0] = (T)(th[0] * kLog2e);  // lambda in base-2 units
+      split_hi_lo(L.lo, pc[1], pc[2]);
+      break;
+    case RFL_CHEB:  // x' = (x - mid) * (2/(hi-lo))
+      pc[0] = (T)(2.0 / (L.hi - L.lo));
+      pc[1] = (T)(-(L.hi + L.lo) / (L.hi - L.lo));
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) pc[2 + j] = (T)th[j];
+      break;
+    case RFL_CB: {
+      const double s = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (T)(s / th[1]);  // t = (x - m0) * s/sigma
+      pc[3] = (T)s;
+      pc[4] = (T)A;
+      pc[5] = (T)(A / n);
+      pc[6] = (T)n;
+      pc[7] = (T)(-0.5 * A * A * kLog2e);
+      break;
+    }
+    case RFL_JOHNSON:
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (T)(1.0 / th[1]);
+      pc[3] = (T)th[2];
+      pc[4] = (T)th[3];
+      break;
+    case RFL_FORMULA:  // the formula runs on the parameters rounded to T
+      for (int j = 0; j < L.npar; ++j) pc[j] = (T)th[j];
+      break;
+    case RFL_ARGUS:
+      split_hi_lo(th[0], pc[0], pc[1]);
+      pc[2] = (T)(1.0 / (th[0] * th[0]));
+      pc[3] = (T)(th[1] * kLog2e);  // c in base-2 units (for u)
+      pc[4] = (T)(2.0 / th[0]);
+      split_hi_lo(th[2], pc[5], pc[7]);  // p (general-p form), hi + lo
+      pc[6] = (T)th[1];  // c (for the m0 derivative)
+      break;
+  }
+}
+
+// Leaf k's constants.  Writes K.pc[k], K.pcd[k], K.dlogI[k], K.dtheta[k],
+// K.gmul[k], K.lmeta[k] and lnI_out.
 template <typename Real>
 __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, int k, double* lnI_out) {
@@ -353,87 +404,54 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
   }
   K.lnI[k] = *lnI_out;
+  K.lmeta[k] = (L.type & 0xff) | ((L.gmask & 0xff) << 8) | ((L.comp & 0xff) << 16) |
+               ((L.col & 0xff) << 24);
   Real* pc = K.pc[k];
-  for (int j = 0; j < RF_PC; ++j) pc[j] = Real(0);
+  leaf_pc<Real>(L, th, pc);
+  leaf_pc<double>(L, th, K.pcd[k]);
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
     K.dlogI[k][j] = dln[j];
     K.dtheta[k][j] = 0.0;
     K.gmul[k][j] = 1.0;
   }
+  // dtheta: the parameter value the per-event code uses (through its rounded
+  // constants) minus the parameter; gmul: the constant factor of d u/d theta
+  // that the per-event sums leave out
   switch (L.type) {
-    case RFL_GAUSS: {
-      // d = kG (x - mu) / sigma, so that u (base 2) = -d^2
-      split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(kG / th[1]);
+    case RFL_GAUSS:
       K.dtheta[k][1] = kG / (double)pc[2] - th[1];
       K.gmul[k][0] = 1.0 / (kG * th[1]);         // d u/d mu = (x - mu)/sigma^2 = d / (kG sigma)
       K.gmul[k][1] = 1.0 / (kG * kG * th[1]);    // d u/d sigma = d^2 / (kG^2 sigma)
       break;
-    }
-    case RFL_EXP: {
-      pc[0] = (Real)(th[0] * kLog2e);  // lambda in base-2 units
-      split_hi_lo(L.lo, pc[1], pc[2]);
+    case RFL_EXP:
       K.dtheta[k][0] = kLn2 * (double)pc[0] - th[0];
       break;
-    }
-    case RFL_CHEB: {
-      // x' = (x - mid) * (2/(hi-lo))
-      pc[0] = (Real)(2.0 / (L.hi - L.lo));
-      pc[1] = (Real)(-(L.hi + L.lo) / (L.hi - L.lo));
-      for (int j = 0; j < RF_LEAF_MAXP; ++j) {
-        pc[2 + j] = (Real)th[j];
-        K.dtheta[k][j] = (double)pc[2 + j] - th[j];
-      }
+    case RFL_CHEB:
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = (double)pc[2 + j] - th[j];
       break;
-    }
     case RFL_CB: {
-      double s = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
-      split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(s / th[1]);  // t = (x - m0) * s/sigma
-      pc[3] = (Real)s;
-      pc[4] = (Real)A;
-      pc[5] = (Real)(A / n);
-      pc[6] = (Real)n;
-      pc[7] = (Real)(-0.5 * A * A * kLog2e);
+      const double s = th[2] > 0.0 ? 1.0 : -1.0;
       K.dtheta[k][1] = 1.0 / fabs((double)pc[2]) - th[1];
       K.gmul[k][0] = -s / th[1];   // d u/d m0 = -(s/sigma) du/dt
       K.gmul[k][1] = -1.0 / th[1]; // d u/d sigma = -(t/sigma) du/dt
       K.gmul[k][2] = s;            // d u/d alpha = s d u/d|alpha|
       break;
     }
-    case RFL_JOHNSON: {
-      split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(1.0 / th[1]);
-      pc[3] = (Real)th[2];
-      pc[4] = (Real)th[3];
+    case RFL_JOHNSON:
       K.dtheta[k][1] = 1.0 / (double)pc[2] - th[1];
       K.dtheta[k][2] = (double)pc[3] - th[2];
       K.dtheta[k][3] = (double)pc[4] - th[3];
       K.gmul[k][0] = K.gmul[k][1] = -1.0 / th[1];  // d u/d mu = -du/dz / lambda, etc.
       K.gmul[k][2] = K.gmul[k][3] = -1.0;         // d u/d gamma = -w, d u/d delta = -w asinh z
       break;
-    }
-    case RFL_FORMULA: {
-      // the formula runs on the parameters rounded to Real (first-order
-      // correction through dtheta, as for the built-in leaves)
-      for (int j = 0; j < L.npar; ++j) {
-        pc[j] = (Real)th[j];
-        K.dtheta[k][j] = (double)pc[j] - th[j];
-      }
+    case RFL_FORMULA:  // first-order correction through dtheta, as for the built-ins
+      for (int j = 0; j < L.npar; ++j) K.dtheta[k][j] = (double)pc[j] - th[j];
       break;
-    }
-    case RFL_ARGUS: {
-      split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (Real)(1.0 / (th[0] * th[0]));
-      pc[3] = (Real)(th[1] * kLog2e);  // c in base-2 units (for u)
-      pc[4] = (Real)(2.0 / th[0]);
-      split_hi_lo(th[2], pc[5], pc[7]);  // p (general-p form), hi + lo
-      pc[6] = (Real)th[1];  // c (for the m0 derivative)
+    case RFL_ARGUS:
       K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
       if (L.gmask & 4) K.dtheta[k][2] = ((double)pc[5] + (double)pc[7]) - th[2];
       K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
-    }
   }
   return ok;
 }
@@ -494,6 +512,7 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
   }
   K.beta_ref = ref;
   K.zero_mask = zero;
+  K.n_comp = C;
   for (int c = 0; c < RF_MAXC; ++c) {
     K.coef[c] = coef[c];
     if (c < C && !((zero >> c) & 1)) {
@@ -501,11 +520,21 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
       double d = beta[c] - ref;
       K.delta[c] = (Real)(d * kLog2e);
       K.delta_lo[c] = d - kLn2 * (double)K.delta[c];
+      K.delta_d[c] = d * kLog2e;
     } else {
       K.delta[c] = (Real)(-kInf());
       K.delta_lo[c] = 0.0;
+      K.delta_d[c] = -kInf();
     }
     K.delta_nc[c] = (Real)(c < C ? (base[c] - ref) * kLog2e : 0.0);
+    K.delta_nc_d[c] = c < C ? (base[c] - ref) * kLog2e : 0.0;
+  }
+  if (sizeof(Real) == 4 && zero != 0) {
+    // FP32 evaluation with a zero coefficient runs every event in FP64 on the
+    // exact constants (pcd, delta_d): nothing to correct for rounding
+    for (int c = 0; c < RF_MAXC; ++c) K.delta_lo[c] = 0.0;
+    for (int k = 0; k < RF_MAXL; ++k)
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = 0.0;
   }
   K.bad = bad ? 1 : 0;
 }
@@ -817,7 +846,9 @@ struct EvalConsts {
   Real delta[NL];
   Real delta_nc[NL];
   int zero_mask;
+  const RfConsts<Real>* full;  // the constants these came from (FP64 path)
   __device__ __forceinline__ void load(const RfConsts<Real>& K) {
+    full = &K;
 #pragma unroll
     for (int k = 0; k < NL; ++k)
 #pragma unroll

@@ -114,6 +114,15 @@ struct alignas(16) RfConsts {  // 16-byte multiple: arrays of it are bulk-copied
   double ext_sum;              // sum of yields (extended) else 0
   int32_t zero_mask;           // bit c: coef_c == 0
   int32_t bad;                 // parameter outside its definition range
+  // FP32 evaluation of a call (or toy) with a coefficient exactly 0 evaluates
+  // every event in FP64 (the absent component's P_c/P grows without bound
+  // in the tails of the others, beyond what FP32 log-densities resolve): the
+  // per-event constants and the deltas in FP64, and each leaf's form
+  double pcd[RF_MAXL][RF_PC];  // pc in FP64 (hi + lo pairs as (value, 0))
+  double delta_d[RF_MAXC];     // delta_c in base-2 units (-inf: coef_c == 0)
+  double delta_nc_d[RF_MAXC];  // (delta_c - log coef_c) in base-2 units
+  int32_t lmeta[RF_MAXL];      // type | gmask << 8 | comp << 16 | col << 24
+  int32_t n_comp;
 };
 
 // Device workspace owned by an rf_graph.

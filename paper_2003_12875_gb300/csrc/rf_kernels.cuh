@@ -18,11 +18,74 @@
 
 namespace rf {
 
+template <typename T>
+struct IsF32 {
+  static constexpr bool v = false;
+};
+template <>
+struct IsF32<float> {
+  static constexpr bool v = true;
+};
+
 template <int NL>
 struct GenericModel {
   static constexpr int NL_ = NL;
   static constexpr int NCOL = NL;
   static constexpr unsigned long long AMASK = ~0ull;
+
+  // One event entirely in FP64 (FP32 evaluation of a call with a coefficient
+  // exactly 0; x: the event's column values in their own precision): the same
+  // formulas on the FP64 constants, the absent components' P_c/P from FP64
+  // log-densities.  Adds the event's terms to q (FP32 sums) and returns
+  // log2 P - beta_ref / ln 2.  Not inlined: it stays out of the event loops.
+  static __device__ __noinline__ double event_exact(const RfConsts<float>* __restrict__ Kp,
+                                                    const double* __restrict__ x,
+                                                    float* __restrict__ q) {
+    const RfConsts<float>& K = *Kp;
+    double u[NL], g[NL][RF_LEAF_MAXP];
+    int comp[NL], gms[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int m = K.lmeta[k];
+      gms[k] = (m >> 8) & 0xff;
+      comp[k] = (m >> 16) & 0xff;
+      eval_leaf<double>(m & 0xff, gms[k], x[(m >> 24) & 0xff], K.pcd[k], u[k], g[k]);
+    }
+    const int C = K.n_comp;
+    double v[NL], w[NL], vm = -kInf();
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      v[c] = c < C ? K.delta_d[c] : -kInf();
+#pragma unroll
+      for (int k = 0; k < NL; ++k)
+        if (comp[k] == c) v[c] += u[k];
+      vm = fmax(vm, v[c]);
+    }
+    double sw = 0.0;
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      w[c] = c < C ? exp2(v[c] - vm) : 0.0;
+      sw += w[c];
+    }
+    const double ell = vm + log2(sw);
+    q[0] += (float)ell;
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+      if (c >= C) continue;
+      w[c] /= sw;
+      double vnc = K.delta_nc_d[c];
+#pragma unroll
+      for (int k = 0; k < NL; ++k)
+        if (comp[k] == c) vnc += u[k];
+      q[1 + c] += (float)(((K.zero_mask >> c) & 1) ? exp2(vnc - ell) : w[c]);
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+#pragma unroll
+      for (int j = 0; j < RF_LEAF_MAXP; ++j)
+        if ((gms[k] >> j) & 1) q[1 + NL + k * RF_LEAF_MAXP + j] += (float)(w[comp[k]] * g[k][j]);
+    return ell;
+  }
 
   // leaves -> components -> log-sum-exp -> adjoint weights, into q.
   // ANYZERO false: the caller knows no coefficient is zero (no per-event test)
@@ -310,12 +373,40 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
   }
 }
 
+// Events i0, i0 + step, ... < i1 through the model's FP64 event (FP32
+// evaluation of a call or toy with a coefficient exactly 0), the column
+// values read in their own precision.
+template <class M, typename Col>
+__device__ inline void iterate_exact(const RfProgram& P, const EvalConsts<float, M::NL_>& K,
+                                     const Col* __restrict__ ev, int64_t stride, int64_t i0,
+                                     int64_t i1, int64_t step,
+                                     Acc<float, RF_NACC(M::NL_), M::AMASK>& acc) {
+  constexpr int NL = M::NL_;
+  for (int64_t i = i0; i < i1; i += step) {
+    double x[NL];
+#pragma unroll
+    for (int c = 0; c < NL; ++c)
+      x[c] = (c < M::NCOL && c < P.n_cols) ? (double)ev[(int64_t)P.col_obs[c] * stride + i] : 0.0;
+    float q[RF_NACC(NL)];
+#pragma unroll
+    for (int j = 0; j < RF_NACC(NL); ++j) q[j] = 0.f;
+    M::event_exact(K.full, x, q);
+    acc.add(q);
+  }
+}
+
 template <class M, typename Real, typename Col>
 __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real, M::NL_>& K,
                                       const Col* __restrict__ ev, int64_t stride, int64_t i0,
                                       int64_t i1, Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc,
                                       int step = 1) {
   constexpr int NL = M::NL_;
+  if constexpr (IsF32<Real>::v) {
+    if (K.zero_mask != 0) {
+      iterate_exact<M, Col>(P, K, ev, stride, i0, i1, step, acc);
+      return;
+    }
+  }
   for (int64_t i = i0; i < i1; i += step) {
     Real xc[NL];
 #pragma unroll
@@ -387,13 +478,23 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     const int64_t nfull = (n - h) / EPT;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (E.zero_mask == 0)
-      stream_chunks<M, Real, Col, EPT, false>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
-    else
-      stream_chunks<M, Real, Col, EPT, true>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
-      iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
-      iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
+    bool exact = false;
+    if constexpr (IsF32<Real>::v) {
+      // a coefficient exactly 0: every event in FP64 (rare; speed is no aim)
+      if (E.zero_mask != 0) {
+        iterate_exact<M, Col>(P, E, ev, n, first, n, gsz, acc);
+        exact = true;
+      }
+    }
+    if (!exact) {
+      if (E.zero_mask == 0)
+        stream_chunks<M, Real, Col, EPT, false>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
+      else
+        stream_chunks<M, Real, Col, EPT, true>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
+      if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+        iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
+        iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
+      }
     }
   }
 
@@ -425,6 +526,17 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
     Real q[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) q[j] = Real(0);
+    if constexpr (IsF32<Real>::v) {
+      if (E.zero_mask != 0) {  // FP64 event, as in the NLL kernels
+        double xd[NL];
+#pragma unroll
+        for (int c = 0; c < NL; ++c)
+          xd[c] = (c < M::NCOL && c < P.n_cols) ? (double)ev[(int64_t)P.col_obs[c] * n + i] : 0.0;
+        const double ell = M::event_exact(E.full, xd, q);
+        logp[i] = K.bad ? kNaN() : K.beta_ref + kLn2 * ell;
+        continue;
+      }
+    }
     M::template event<Real>(P, E, xc, q);
     logp[i] = K.bad ? kNaN() : K.beta_ref + kLn2 * (double)q[0];
   }

@@ -214,6 +214,20 @@ __device__ __forceinline__ void eval_chunk(const RfProgram& P, const EvalConsts<
     for (int r = 0; r < V; ++r) {
       const int j = V * vi + r;
       if (FULL || (c0 + j >= p0 && c0 + j < p1)) {
+        if constexpr (ANYZERO && IsF32<Real>::v) {
+          if (E.zero_mask != 0) {  // a coefficient exactly 0: the FP64 event
+            double xd[NL];
+            float qe[NA];
+#pragma unroll
+            for (int c = 0; c < NL; ++c) xd[c] = (double)xv[c][r];
+#pragma unroll
+            for (int i = 0; i < NA; ++i) qe[i] = 0.f;
+            M::event_exact(E.full, xd, qe);
+#pragma unroll
+            for (int i = 0; i < NA; ++i) q[i] += qe[i];
+            continue;
+          }
+        }
         Real xc[NL];
 #pragma unroll
         for (int c = 0; c < NL; ++c) xc[c] = cvt<Real, Col>(xv[c][r]);
