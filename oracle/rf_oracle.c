@@ -698,8 +698,9 @@ static int leaf_value(int type, const double* th, int nth, double lo, double hi,
         *f_out = 0.0;
         return ORC_OK;
       }
-      double r = x / m0;
-      double tau = 1.0 - r * r;
+      /* tau = 1 - (x/m0)^2 as (m0 - x)(m0 + x) / m0^2: the same value
+       * without the cancellation of 1 - r^2 as x approaches m0 */
+      double tau = (m0 - x) * (m0 + x) / (m0 * m0);
       *f_out = x * pow(tau, p) * exp(c * tau);
       dlogf[0] = (p / tau + c) * 2.0 * x * x / (m0 * m0 * m0);
       dlogf[1] = tau;
