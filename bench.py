@@ -126,20 +126,22 @@ def cpu_oracle_rate(w, sample_events, nthreads=0):
 
 
 # FP32-pipe instructions per event of the fused kernel's formulation, by piece
-# (derived op by op from the formulas of each leaf, the log-sum-exp and the
-# adjoint sums).
+# (derived op by op from the formulas of each leaf, the log of the mixture and
+# the adjoint sums; the secondary "issue" figure of the bench line).
 # leaf type -> (base, extra per wanted derivative by leaf-parameter index,
 #               shared extra when any derivative is wanted)
 # Per-event logarithms are taken in base 2 (one hardware lg2 each, no
-# conversion factor); the two-term log-sum-exp is one ex2, one lg2 and one
-# reciprocal with the arithmetic around them.
+# conversion factor); a location shift is one subtraction and one FMA; each
+# component's log-coefficient is folded into its first leaf (no addition);
+# the two-term log-sum-exp is one ex2, one lg2 and one reciprocal with the
+# arithmetic around them.
 LEAF_INSTR = {
-    "gauss": (4, {0: 0, 1: 1}, 0),
-    "exp": (3, {0: 0}, 0),
-    "cheb": (12, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
-    "cb": (11, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
-    "argus": (13, {0: 5, 1: 1, 2: 3}, 0),   # a free p: one more log and its product
-    "johnson": (13, {0: 0, 1: 1, 2: 0, 3: 1}, 4),
+    "gauss": (4, {0: 0, 1: 0}, 0),
+    "exp": (3, {0: 0}, 0),                  # 1 when the range starts at 0 (no shift)
+    "cheb": (11, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
+    "cb": (8, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
+    "argus": (10, {0: 6, 1: 0, 2: 4}, 0),   # a free p: the general form (+2) and d/dp (+2)
+    "johnson": (12, {0: 0, 1: 1, 2: 0, 3: 1}, 5),
 }
 F64_TO_F32_INSTR = 9   # integer-pipe rounding of an FP64 column value
 
@@ -159,15 +161,17 @@ def algorithmic_instr_per_event(spec: dict, ept: int = REF_EPT, f64_columns: boo
     total, free = 0.0, 0
     for lf in leaves:
         base, per, shared = LEAF_INSTR[lf["type"]]
+        if lf["type"] == "exp" and spec["obs"][lf["obs"]][0] == 0.0:
+            base = 1
         wanted = [j for j, p in enumerate(lf["params"]) if not fixed[p] and j in per]
         total += base + (shared if wanted else 0) + sum(per[j] for j in wanted)
         free += len(wanted)
-    total += len(leaves)                      # component sums delta_c + sum u_k
+    total += len(leaves) - nc                 # sums of a component's leaves
     if nc == 2:
         total += 11                           # two-term log-sum-exp and weights
     elif nc > 2:
         total += 11 * nc + 24
-    total += 1 + (nc if nc > 1 else 1) + free + (2 if nc > 1 else 0)   # adjoint sums
+    total += 1 + (nc if nc > 1 else 1) + free  # adjoint sums
     total += 4.0 * (1 + nc + free) / ept      # compensated per-iteration sums
     total += 1                                # loads and loop
     if f64_columns:

@@ -556,7 +556,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
     const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
     const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
-    const int ke = toy ? 8 : ept;
+    const int ke = toy ? (fp32 ? 16 : 8) : ept;  // the segment kernel's events per lane
     if (!rf_jit_compile_only(P, fcp, desc->eval_precision, cd, kind, ke, toy ? 0 : 3, &err))
       return fail(RF_ECUDA, err);
   }

@@ -49,6 +49,12 @@ const char* leaf_fn(int type) {
   return nullptr;
 }
 
+// The leaf function's compile-time mask: the gradient bits, and for an
+// Exponential whose range starts at 0 the form without the shift
+int leaf_gm(const RfLeafProg& L) {
+  return L.gmask | ((L.type == RFL_EXP && L.lo == 0.0) ? RF_GM_AT0 : 0);
+}
+
 // FNV-1a, for the on-disk cache file name
 uint64_t fnv1a(const std::string& s) {
   uint64_t h = 1469598103934665603ull;
@@ -140,23 +146,33 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
     << "  template <typename Real, bool ANYZERO = true>\n  static __device__ __forceinline__ void "
        "event(const RfProgram& P, "
        "const rf::EvalConsts<Real, NL_>& K, const Real (&x)[NL_], Real (&q)[RF_NACC(NL_)]) {\n";
+  // Without a zero coefficient (ANYZERO false) each component's delta is
+  // added inside its first leaf (folded into a constant or an FMA there);
+  // otherwise the leaves return the bare log-densities and delta / delta_nc
+  // are added here.
+  std::vector<int> first(NC, -1);
+  for (int k = 0; k < NL; ++k)
+    if (first[P.leaf[k].comp] < 0) first[P.leaf[k].comp] = k;
   for (int k = 0; k < NL; ++k) {
     const RfLeafProg& L = P.leaf[k];
     o << "    Real u" << k << ", g" << k << "[4];\n    ";
     if (L.type == RFL_FORMULA)
       o << "rf::formula_leaf<RfFormula" << k << ", Real, " << L.gmask << ">";
     else
-      o << "rf::" << leaf_fn(L.type) << "<Real, " << L.gmask << ">";
-    o << "(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k << ");\n";
+      o << "rf::" << leaf_fn(L.type) << "<Real, " << leaf_gm(L) << ">";
+    o << "(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k;
+    if (first[L.comp] == k) o << ", ANYZERO ? Real(-0.0) : K.delta[" << L.comp << "]";
+    o << ");\n";
   }
   o << "    Real v[" << NC << "], w[" << NC << "];\n";
   std::vector<std::string> usum(NC);
   for (int c = 0; c < NC; ++c) {
     std::string s;
     for (int k = 0; k < NL; ++k)
-      if (P.leaf[k].comp == c) s += " + u" + std::to_string(k);
-    usum[c] = s;
-    o << "    v[" << c << "] = K.delta[" << c << "]" << s << ";\n";
+      if (P.leaf[k].comp == c) s += (s.empty() ? "u" : " + u") + std::to_string(k);
+    usum[c] = " + " + s;
+    o << "    if constexpr (ANYZERO) v[" << c << "] = K.delta[" << c << "] + " << s << ";\n"
+      << "    else v[" << c << "] = " << s << ";\n";
   }
   o << "    const Real ell = rf::lse<Real, " << NC << ">(v, w);\n    q[0] += ell;\n";
   if (NC == 1) {
@@ -189,7 +205,7 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
     if (L.type == RFL_FORMULA)
       o << "rf::formula_leaf<RfFormula" << k << ", double, " << L.gmask << ">";
     else
-      o << "rf::" << leaf_fn(L.type) << "<double, " << L.gmask << ">";
+      o << "rf::" << leaf_fn(L.type) << "<double, " << leaf_gm(L) << ">";
     o << "(x[" << L.col << "], K.pcd[" << k << "], u" << k << ", g" << k << ");\n";
   }
   o << "    double v[" << NC << "], w[" << NC << "];\n";

@@ -340,10 +340,13 @@ template <typename T>
 __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
   for (int j = 0; j < RF_PC; ++j) pc[j] = T(0);
   switch (L.type) {
-    case RFL_GAUSS:  // d = kG (x - mu) / sigma, so that u (base 2) = -d^2
-      split_hi_lo(th[0], pc[0], pc[1]);
+    case RFL_GAUSS: {  // d = kG (x - mu) / sigma, so that u (base 2) = -d^2
+      T lo;
+      split_hi_lo(th[0], pc[0], lo);
       pc[2] = (T)(kG / th[1]);
+      pc[1] = (T)(-(double)lo * (double)pc[2]);
       break;
+    }
     case RFL_EXP:
       pc[0] = (T)(th[0] * kLog2e);  // lambda in base-2 units
       split_hi_lo(L.lo, pc[1], pc[2]);
@@ -354,27 +357,33 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
       for (int j = 0; j < RF_LEAF_MAXP; ++j) pc[2 + j] = (T)th[j];
       break;
     case RFL_CB: {
-      const double s = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
-      split_hi_lo(th[0], pc[0], pc[1]);
-      pc[2] = (T)(s / th[1]);  // t = (x - m0) * s/sigma
-      pc[3] = (T)s;
-      pc[4] = (T)A;
-      pc[5] = (T)(A / n);
-      pc[6] = (T)n;
+      // s = kG t, t = s_alpha (x - m0)/sigma
+      const double sg = th[2] > 0.0 ? 1.0 : -1.0, A = fabs(th[2]), n = th[3];
+      T lo;
+      split_hi_lo(th[0], pc[0], lo);
+      pc[2] = (T)(kG * sg / th[1]);
+      pc[1] = (T)(-(double)lo * (double)pc[2]);
+      pc[3] = (T)(1.0 - A * A / n);        // D = pc[3] + pc[5] s
+      pc[4] = (T)(-kG * A);                // the tail: s <= pc[4]
+      pc[5] = (T)(-A / (n * kG));
+      pc[6] = (T)(-n);
       pc[7] = (T)(-0.5 * A * A * kLog2e);
       break;
     }
-    case RFL_JOHNSON:
-      split_hi_lo(th[0], pc[0], pc[1]);
+    case RFL_JOHNSON: {
+      T lo;
+      split_hi_lo(th[0], pc[0], lo);
       pc[2] = (T)(1.0 / th[1]);
+      pc[1] = (T)(-(double)lo * (double)pc[2]);
       pc[3] = (T)th[2];
       pc[4] = (T)th[3];
       break;
+    }
     case RFL_FORMULA:  // the formula runs on the parameters rounded to T
       for (int j = 0; j < L.npar; ++j) pc[j] = (T)th[j];
       break;
     case RFL_ARGUS:
-      split_hi_lo(th[0], pc[0], pc[1]);
+      split_hi_lo(th[0] * th[0], pc[0], pc[1]);  // m0^2, hi + lo
       pc[2] = (T)(1.0 / (th[0] * th[0]));
       pc[3] = (T)(th[1] * kLog2e);  // c in base-2 units (for u)
       pc[4] = (T)(2.0 / th[0]);
@@ -384,8 +393,8 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
   }
 }
 
-// Leaf k's constants.  Writes K.pc[k], K.pcd[k], K.dlogI[k], K.dtheta[k],
-// K.gmul[k], K.lmeta[k] and lnI_out.
+// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k], K.gmul[k],
+// K.lmeta[k] and lnI_out (K.pcd: comb_consts, when FP32 evaluation needs it).
 template <typename Real>
 __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, int k, double* lnI_out) {
@@ -408,7 +417,6 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
                ((L.col & 0xff) << 24);
   Real* pc = K.pc[k];
   leaf_pc<Real>(L, th, pc);
-  leaf_pc<double>(L, th, K.pcd[k]);
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
     K.dlogI[k][j] = dln[j];
     K.dtheta[k][j] = 0.0;
@@ -430,11 +438,12 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = (double)pc[2 + j] - th[j];
       break;
     case RFL_CB: {
-      const double s = th[2] > 0.0 ? 1.0 : -1.0;
-      K.dtheta[k][1] = 1.0 / fabs((double)pc[2]) - th[1];
-      K.gmul[k][0] = -s / th[1];   // d u/d m0 = -(s/sigma) du/dt
-      K.gmul[k][1] = -1.0 / th[1]; // d u/d sigma = -(t/sigma) du/dt
-      K.gmul[k][2] = s;            // d u/d alpha = s d u/d|alpha|
+      // per event h = -kG du/dt (t = s_alpha (x - m0)/sigma), h s = -kG^2 t du/dt
+      const double sg = th[2] > 0.0 ? 1.0 : -1.0;
+      K.dtheta[k][1] = kG / fabs((double)pc[2]) - th[1];
+      K.gmul[k][0] = sg / (kG * th[1]);        // d u/d m0 = -(s_alpha/sigma) du/dt
+      K.gmul[k][1] = 1.0 / (kG * kG * th[1]);  // d u/d sigma = -(t/sigma) du/dt
+      K.gmul[k][2] = sg / kG;                  // d u/d alpha = s_alpha d u/d|alpha|
       break;
     }
     case RFL_JOHNSON:
@@ -520,19 +529,27 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
       double d = beta[c] - ref;
       K.delta[c] = (Real)(d * kLog2e);
       K.delta_lo[c] = d - kLn2 * (double)K.delta[c];
-      K.delta_d[c] = d * kLog2e;
     } else {
       K.delta[c] = (Real)(-kInf());
       K.delta_lo[c] = 0.0;
-      K.delta_d[c] = -kInf();
     }
     K.delta_nc[c] = (Real)(c < C ? (base[c] - ref) * kLog2e : 0.0);
-    K.delta_nc_d[c] = c < C ? (base[c] - ref) * kLog2e : 0.0;
   }
   if (sizeof(Real) == 4 && zero != 0) {
     // FP32 evaluation with a zero coefficient runs every event in FP64 on the
-    // exact constants (pcd, delta_d): nothing to correct for rounding
-    for (int c = 0; c < RF_MAXC; ++c) K.delta_lo[c] = 0.0;
+    // exact constants (pcd, delta_d, delta_nc_d; built only here, the rare
+    // case): nothing to correct for rounding
+    for (int c = 0; c < RF_MAXC; ++c) {
+      K.delta_d[c] = (c < C && !((zero >> c) & 1)) ? (beta[c] - ref) * kLog2e : -kInf();
+      K.delta_nc_d[c] = c < C ? (base[c] - ref) * kLog2e : 0.0;
+      K.delta_lo[c] = 0.0;
+    }
+    for (int k = 0; k < P.n_leaves; ++k) {
+      const RfLeafProg& L = P.leaf[k];
+      double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
+      leaf_pc<double>(L, th, K.pcd[k]);
+    }
     for (int k = 0; k < RF_MAXL; ++k)
       for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = 0.0;
   }
@@ -647,40 +664,49 @@ struct Fn<double> {
   static __device__ __forceinline__ double ninf() { return -kInf(); }
 };
 
-// Typed leaves: u = (log f(x) - off) / ln 2, in base-2 units, and
+// Typed leaves: u = add + (log f(x) - off) / ln 2, in base-2 units, and
 // g_j = d (log f)/d theta_j in natural units (up to the constant factor gmul
-// applied in the epilogue).  GM is the
-// compile-time mask of the derivatives that are needed; the others are 0.
+// applied in the epilogue).  GM is the compile-time mask of the derivatives
+// that are needed; the others are 0.  `add` is a per-call constant the caller
+// wants added to u (the graph compiler folds a component's log-coefficient
+// into its first leaf this way); its default -0 adds nothing (x + -0 == x
+// for every x, so the addition folds away).
+// Location-like parameters enter as (x - hi) * scale + lo', lo' = -lo *
+// scale: the difference is exact for x near hi, and one FMA applies the
+// scale and the low part.
+
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_gauss(Real x, const Real* __restrict__ pc, Real& u,
-                                           Real (&g)[RF_LEAF_MAXP]) {
-  Real d = ((x - pc[0]) - pc[1]) * pc[2];  // kG (x - mu) / sigma
-  u = -(d * d);                              // -(x - mu)^2 / (2 sigma^2) in base 2
+                                           Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
+  const Real d = fma(x - pc[0], pc[2], pc[1]);  // kG (x - mu) / sigma
+  const Real dd = d * d;
+  u = add - dd;                                  // -(x - mu)^2 / (2 sigma^2) in base 2
   g[0] = (GM & 1) ? d : Real(0);       // times 1/(kG sigma) (gmul)
-  g[1] = (GM & 2) ? d * d : Real(0);   // times 1/(kG^2 sigma) (gmul)
+  g[1] = (GM & 2) ? dd : Real(0);      // times 1/(kG^2 sigma) (gmul)
   g[2] = g[3] = Real(0);
 }
 
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_exp(Real x, const Real* __restrict__ pc, Real& u,
-                                         Real (&g)[RF_LEAF_MAXP]) {
-  Real d = (x - pc[1]) - pc[2];
-  u = pc[0] * d;
+                                         Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
+  const Real d = (GM & RF_GM_AT0) ? x : (x - pc[1]) - pc[2];  // x - lo
+  u = fma(pc[0], d, add);
   g[0] = (GM & 1) ? d : Real(0);
   g[1] = g[2] = g[3] = Real(0);
 }
 
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_cheb(Real x, const Real* __restrict__ pc, Real& u,
-                                          Real (&g)[RF_LEAF_MAXP]) {
+                                          Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   typedef Fn<Real> F;
-  Real xp = x * pc[0] + pc[1];
-  Real t1 = xp, t2 = Real(2) * xp * t1 - Real(1);
-  Real t3 = Real(2) * xp * t2 - t1, t4 = Real(2) * xp * t3 - t2;
-  Real f = Real(1) + pc[2] * t1 + pc[3] * t2 + pc[4] * t3 + pc[5] * t4;
-  u = F::lg2(f);
-  if (GM) {
-    Real r = F::rcp(f);
+  const Real xp = fma(x, pc[0], pc[1]);
+  const Real x2 = xp + xp;
+  const Real t1 = xp, t2 = fma(x2, t1, Real(-1));
+  const Real t3 = fma(x2, t2, -t1), t4 = fma(x2, t3, -t2);
+  const Real f = fma(pc[5], t4, fma(pc[4], t3, fma(pc[3], t2, fma(pc[2], t1, Real(1)))));
+  u = F::lg2(f) + add;
+  if (GM & 15) {
+    const Real r = F::rcp(f);
     g[0] = (GM & 1) ? t1 * r : Real(0);
     g[1] = (GM & 2) ? t2 * r : Real(0);
     g[2] = (GM & 4) ? t3 * r : Real(0);
@@ -690,59 +716,63 @@ __device__ __forceinline__ void leaf_cheb(Real x, const Real* __restrict__ pc, R
   }
 }
 
-// Crystal Ball: both pieces are evaluated and one is selected (no divergence).
+// Crystal Ball, in s = kG s_alpha (x - m0)/sigma (the core is then -s^2 in
+// base 2): tail for s <= pc[4] = -kG A, D = 1 - (A/n)(A + t) = pc[3] + pc[5] s,
+// u = add + pc[7] - n log2 D there; both pieces are evaluated and one is
+// selected (no divergence).  Derivatives (times gmul): h = pc[4] / D in the
+// tail, s in the core (-kG du/dt); h s; the tail's d/dA and d/dn.
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Real& u,
-                                        Real (&g)[RF_LEAF_MAXP]) {
+                                        Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   typedef Fn<Real> F;
-  const Real A = pc[4];
-  Real t = ((x - pc[0]) - pc[1]) * pc[2];  // s (x - m0) / sigma
-  bool tail = t <= -A;
-  Real D = Real(1) - pc[5] * (A + t);
-  Real Lg = F::lg2(D);  // log2 D, used only in the tail, where D >= 1
-  u = tail ? pc[7] - pc[6] * Lg : Real(-0.5 * kLog2e) * t * t;
-  if (GM) {
-    Real rD = F::rcp(D);
-    Real dudt = tail ? A * rD : -t;
-    // constant factors (-s/sigma, -1/sigma, s) are applied to the sums (gmul)
-    g[0] = (GM & 1) ? dudt : Real(0);
-    g[1] = (GM & 2) ? dudt * t : Real(0);
-    g[2] = (GM & 4) ? (tail ? (Real(2) * A + t) * rD - A : Real(0)) : Real(0);
-    g[3] = (GM & 8) ? (tail ? (Real(1) - rD) - Real(kLn2) * Lg : Real(0)) : Real(0);
+  const Real s = fma(x - pc[0], pc[2], pc[1]);
+  const bool tail = s <= pc[4];
+  const Real D = fma(pc[5], s, pc[3]);
+  const Real Lg = F::lg2(D);  // log2 D, used only in the tail, where D >= 1
+  u = tail ? fma(pc[6], Lg, pc[7] + add) : fma(-s, s, add);
+  if (GM & 15) {
+    const Real rD = F::rcp(D);
+    const Real h = tail ? pc[4] * rD : s;
+    g[0] = (GM & 1) ? h : Real(0);
+    g[1] = (GM & 2) ? h * s : Real(0);
+    g[2] = (GM & 4) ? (tail ? fma(s - Real(2) * pc[4], rD, pc[4]) : Real(0)) : Real(0);
+    g[3] = (GM & 8) ? (tail ? fma(Real(-kLn2), Lg, Real(1) - rD) : Real(0)) : Real(0);
   } else {
     g[0] = g[1] = g[2] = g[3] = Real(0);
   }
 }
 
-// ARGUS: u = log x + p log tau + c tau, -inf at and above m0.  In the
-// general form (GM bit 2: p free, or RF_ARGUS_GENERAL: p fixed away from 1/2)
-// p = pc[5], and with bit 2 d u/d p = log tau; otherwise p is 1/2 and
-// u = (1/2) log(x^2 tau) + c tau (one log).
+// ARGUS: u = log x + p log tau + c tau, -inf at and above m0, with
+// tau = (m0^2 - x^2) / m0^2 (m0^2 = pc[0] + pc[1]; one FMA forms m0^2 - x^2
+// from the exact square, so tau keeps its relative precision near m0).  In the general form (GM bit 2: p free, or
+// RF_ARGUS_GENERAL: p fixed away from 1/2) p = pc[5] + pc[7], and with bit 2
+// d u/d p = log tau; otherwise p is 1/2 and u = (1/2) log2(x^2 tau) + c tau
+// (one log; x^2 tau clamped at 0 gives -inf at and above m0, where the
+// component's weight, and so every derivative term, is 0).
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, Real& u,
-                                           Real (&g)[RF_LEAF_MAXP]) {
+                                           Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   typedef Fn<Real> F;
-  Real dm = (pc[0] - x) + pc[1];
-  Real sm = (pc[0] + x) + pc[1];
-  Real tau = dm * sm * pc[2];
-  bool ok = tau > Real(0);
+  const Real tau = (fma(-x, x, pc[0]) + pc[1]) * pc[2];
   constexpr bool general = (GM & (4 | RF_ARGUS_GENERAL)) != 0;
-  const Real p = general ? pc[5] : Real(0.5);
   // pc[3] = c log2(e) for u (base 2), pc[6] = c for the derivatives
+  const Real ct = fma(pc[3], tau, add);
   if (general) {
+    const bool ok = tau > Real(0);
     // p = pc[5] + pc[7] (hi + lo: a fixed p has no d/dp sum to correct its
     // rounding with)
     const Real lt = F::lg2(tau);
-    u = ok ? (F::lg2(x) + p * lt + pc[3] * tau) + pc[7] * lt : F::ninf();
+    u = ok ? fma(pc[7], lt, fma(pc[5], lt, ct) + F::lg2(x)) : F::ninf();
     g[2] = ((GM & 4) && ok) ? Real(kLn2) * lt : Real(0);
   } else {
-    u = ok ? Real(0.5) * F::lg2(x * x * tau) + pc[3] * tau : F::ninf();
+    u = fma(Real(0.5), F::lg2(fmax(x * x * tau, Real(0))), ct);
     g[2] = Real(0);
   }
-  g[1] = (GM & 2) ? (ok ? tau : Real(0)) : Real(0);
+  g[1] = (GM & 2) ? tau : Real(0);
   if (GM & 1) {
-    Real r = F::rcp(tau);
-    g[0] = ok ? (p * r + pc[6]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
+    const Real p = general ? pc[5] : Real(0.5);
+    const Real r = F::rcp(tau);
+    g[0] = tau > Real(0) ? (p * r + pc[6]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
   } else {
     g[0] = Real(0);
   }
@@ -754,14 +784,14 @@ __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, 
 // Constant factors (-1/lambda, -1) are applied to the sums (gmul).
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_johnson(Real x, const Real* __restrict__ pc, Real& u,
-                                             Real (&g)[RF_LEAF_MAXP]) {
+                                             Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   typedef Fn<Real> F;
-  const Real z = ((x - pc[0]) - pc[1]) * pc[2];
-  const Real t = Real(1) + z * z;
+  const Real z = fma(x - pc[0], pc[2], pc[1]);
+  const Real t = fma(z, z, Real(1));
   const Real r = F::sqrt(t);
   const Real as = copysign(F::logp(fabs(z) + r), z);
-  const Real w = pc[3] + pc[4] * as;
-  u = Real(-0.5) * F::lg2(t) + Real(-0.5 * kLog2e) * (w * w);
+  const Real w = fma(pc[4], as, pc[3]);
+  u = fma(Real(-0.5), F::lg2(t), fma(Real(-0.5 * kLog2e) * w, w, add));
   if (GM & 3) {
     const Real dudz = -(z + w * pc[4] * r) * F::rcp(t);
     g[0] = (GM & 1) ? dudz : Real(0);

@@ -269,14 +269,14 @@ __device__ __forceinline__ D as_dual(const D& a) {
   return a;
 }
 
-// Per-event formula leaf: u = log2 f, g_j = (df/dp_j) / f for wanted j.
+// Per-event formula leaf: u = add + log2 f, g_j = (df/dp_j) / f for wanted j.
 template <class F, typename Real, int GM>
 __device__ __forceinline__ void formula_leaf(Real x, const Real* __restrict__ pc, Real& u,
-                                             Real (&g)[RF_LEAF_MAXP]) {
+                                             Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   const auto f = F::template eval<Real>(x, pc);
   // the log and reciprocal of the built-in leaves (hardware approximations
   // in FP32); the formula's own functions keep CUDA's accurate versions
-  u = Fn<Real>::lg2(f.v);  // base-2 units, as the built-in leaves
+  u = Fn<Real>::lg2(f.v) + add;  // base-2 units, as the built-in leaves
   const Real r = Fn<Real>::rcp(f.v);
 #pragma unroll
   for (int j = 0; j < RF_LEAF_MAXP; ++j)

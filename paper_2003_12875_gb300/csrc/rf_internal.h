@@ -52,6 +52,9 @@ enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 // gmask bit of an ARGUS leaf whose fixed p is not 1/2 (general-p form, no
 // d/dp accumulator; bits 0..3 are the per-parameter gradient bits)
 #define RF_ARGUS_GENERAL 16
+// compile-time leaf form bit (never in a gmask): an Exponential whose range
+// starts at 0 needs no shift of x
+#define RF_GM_AT0 32
 // device status bits (same values as RF_STATUS_* in include/rf.h)
 #define RF_STATUS_PARAM_DOMAIN_BIT 1u
 #define RF_STATUS_NONFINITE_BIT 2u

@@ -328,9 +328,10 @@ __device__ __forceinline__ void compute_full(const RfProgram& P,
                                              const Real (&x)[M::NL_][EPT],
                                              Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
   constexpr int NL = M::NL_;
+  // -0: the first event's additions fold into moves (x + -0 == x)
   Real q[RF_NACC(NL)];
 #pragma unroll
-  for (int i = 0; i < RF_NACC(NL); ++i) q[i] = Real(0);
+  for (int i = 0; i < RF_NACC(NL); ++i) q[i] = Real(-0.0);
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     Real xc[NL];
@@ -356,20 +357,26 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
                                               Acc<Real, RF_NACC(M::NL_), M::AMASK>& acc) {
   constexpr int NL = M::NL_;
   if (first >= nfull) return;
-  Real xa[NL][EPT];
+  // two register buffers used in turn (unrolled by two, so no buffer is
+  // copied into the other)
+  Real xa[NL][EPT], xb[NL][EPT];
   load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + first * EPT, vec, xa);
   for (int64_t ch = first;;) {
-    const int64_t nx = ch + step;
-    const bool more = nx < nfull;
-    Real xb[NL][EPT];
-    if (more) load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nx * EPT, vec, xb);
+    const int64_t nb = ch + step;
+    if (nb >= nfull) {
+      compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
+      break;
+    }
+    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nb * EPT, vec, xb);
     compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
-    if (!more) break;
-#pragma unroll
-    for (int c = 0; c < NL; ++c)
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) xa[c][e] = xb[c][e];
-    ch = nx;
+    const int64_t na = nb + step;
+    if (na >= nfull) {
+      compute_full<M, Real, EPT, ANYZERO>(P, K, xb, acc);
+      break;
+    }
+    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + na * EPT, vec, xa);
+    compute_full<M, Real, EPT, ANYZERO>(P, K, xb, acc);
+    ch = na;
   }
 }
 

@@ -373,8 +373,8 @@ def test_zero_yield_toys_and_ragged_ends(rf):
     spec = datagen.gauss_exp_ext_spec()
     w = datagen.c4(toys=24, nu_s_range=(300, 3000), nu_b_range=(500, 5000))
     pm = np.array(w["params_matrix"], np.float64)
-    pm[3::4, 3] = 0.0          # signal yield 0 in every fourth toy
-    pm[5::7, 4] = 0.0          # background yield 0 in some others
+    pm[3::4, 3] = 0.0          # signal yield 0 in toys 3, 7, 11, ...
+    pm[2::6, 4] = 0.0          # background yield 0 in toys 2, 8, 14, 20
     want, rc = oracle.nll_batched(spec, w["cols"], w["offsets"], pm)
     assert rc == 0
     for prec in ("fp32", "fp64"):
