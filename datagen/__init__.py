@@ -31,7 +31,7 @@ import numpy as np
 
 CHUNK = 1 << 20
 SEEDS = {"c1": 12875001, "c2": 12875002, "c3": 12875003, "c4": 12875004,
-         "c5": 12875005, "johnson": 12875006}
+         "c5": 12875005, "johnson": 12875006, "prod6": 12875007}
 
 
 def rng(seed: int, chunk: int = 0) -> np.random.Generator:
@@ -286,6 +286,46 @@ def johnson_exp(n_sig=20_000, n_bkg=80_000, seed=SEEDS["johnson"]):
     r.shuffle(ev)
     return {"name": "johnson_exp_ext_f32", "spec": johnson_exp_spec(n_sig, n_bkg),
             "cols": ev.reshape(1, -1), "dtype": "f32"}
+
+
+def prod6_spec(f1=0.3, f2=0.3):
+    """Six leaves in three two-observable components (x on [0, 10], y on
+    [-1, 1]): Gauss(x) Exp(y) + CB(x) Cheb2(y) + Exp(x) Gauss(y), fractions
+    f1, f2 on the first two."""
+    # params: 0 mu1, 1 sigma1, 2 lambda1 (y), 3 m0, 4 sigma2, 5 alpha, 6 n,
+    #         7 c1, 8 c2 (y), 9 lambda3 (x), 10 mu3 (y), 11 sigma3, 12 f1, 13 f2
+    return {"obs": [(0.0, 10.0), (-1.0, 1.0)],
+            "params": [5.0, 0.6, -1.2, 3.0, 0.4, 1.2, 2.5, 0.3, -0.2, -0.25, 0.2, 0.3,
+                       float(f1), float(f2)],
+            "fixed": [False] * 14,
+            "nodes": [{"type": "gauss", "obs": 0, "params": [0, 1]},
+                      {"type": "exp", "obs": 1, "params": [2]},
+                      {"type": "prod", "children": [0, 1]},
+                      {"type": "cb", "obs": 0, "params": [3, 4, 5, 6]},
+                      {"type": "cheb", "obs": 1, "params": [7, 8]},
+                      {"type": "prod", "children": [3, 4]},
+                      {"type": "exp", "obs": 0, "params": [9]},
+                      {"type": "gauss", "obs": 1, "params": [10, 11]},
+                      {"type": "prod", "children": [6, 7]},
+                      {"type": "add_frac", "children": [2, 5, 8], "params": [12, 13]}],
+            "root": 9}
+
+
+def prod6(n=60_000, seed=SEEDS["prod6"], dtype=np.float32):
+    """Events of prod6_spec(): per component its (x, y) pairs drawn from its
+    two leaves, 30% / 30% / 40%, shuffled; two columns."""
+    r = rng(seed, 0)
+    k = r.multinomial(n, [0.3, 0.3, 0.4])
+    x = np.concatenate([gauss(r, int(k[0]), 5.0, 0.6, 0.0, 10.0, dtype),
+                        crystal_ball(r, int(k[1]), 3.0, 0.4, 1.2, 2.5, 0.0, 10.0, dtype),
+                        expo(r, int(k[2]), -0.25, 0.0, 10.0, dtype)])
+    y = np.concatenate([expo(r, int(k[0]), -1.2, -1.0, 1.0, dtype),
+                        cheb(r, int(k[1]), [0.3, -0.2], -1.0, 1.0, dtype),
+                        gauss(r, int(k[2]), 0.2, 0.3, -1.0, 1.0, dtype)])
+    perm = r.permutation(n)
+    cols = np.stack([x[perm], y[perm]])
+    return {"name": "prod6_frac_f32", "spec": prod6_spec(), "cols": np.ascontiguousarray(cols),
+            "dtype": "f32" if dtype == np.float32 else "f64"}
 
 
 def _chunked(n, seed, draw, ncols=1, dtype=np.float64):

@@ -60,7 +60,9 @@
  *   RF_PROD     (children on disjoint observables) P = prod P_k
  * The GPU compiler accepts graphs whose root is a leaf, a PROD of leaves, or
  * an ADD (fractions or extended) whose children are leaves or PRODs of leaves;
- * at most 4 leaves and 4 components.  Other shapes return RF_EUNSUPPORTED.
+ * at most 6 leaves and 6 components (the precompiled generic kernels, and so
+ * rf_graph_set_jit(g, 0) and rf_nll_noalloc, take at most 4 leaves).  Other
+ * shapes return RF_EUNSUPPORTED.
  *
  * Memory: every pointer argument marked "dev" is caller-owned device memory
  * (e.g. a torch tensor).  Event columns are structure-of-arrays: observable j
@@ -328,14 +330,16 @@ rf_status rf_graph_set_launch(rf_graph* g, const rf_launch* cfg);
 
 /* Autotune: times every launch configuration (block x events per thread x
  * blocks per SM x, for the graph-specialised kernel, register budget) on the
- * given data with CUDA events and keeps the fastest (host-synchronous).
+ * given data with CUDA events -- five calls issued back to back, after two
+ * warm-up calls -- and keeps the fastest (host-synchronous).
  * The choice is cached on disk, in the folder RF_JIT_CACHE_DIR (default
  * $TMPDIR/rfgpu-jit, else /tmp/rfgpu-jit), keyed by the kernel (the
  * specialised source, else the graph structure and library build), the
  * column and evaluation precisions, floor(log2 n_events) and the device's
  * compute capability and SM count; a later rf_graph_tune with the same key
  * applies the cached configuration and times only that one.  best_ms (may be
- * NULL) receives the mean time of one call with the chosen configuration.
+ * NULL) receives the mean time of one call (back to back) with the chosen
+ * configuration.
  * Same errors as rf_nll; the configuration is unchanged on error. */
 rf_status rf_graph_tune(rf_graph* g, const void* events, int64_t n_events,
                         const double* params, rf_stream stream,
@@ -359,7 +363,7 @@ rf_status rf_graph_tune_ex(rf_graph* g, const void* events, int64_t n_events,
  * allocates its workspace.  This entry point takes the descriptor directly
  * and runs the precompiled generic fused kernel with its scratch (per-block
  * partial sums, block ticket, status word) in a file-scope static device
- * array of the library: about 178 KB, enough for the partial sums of
+ * array of the library: 256 KiB, enough for the partial sums of
  * blocks <= 1024 and of the grid tree's 32 groups (0 = twice the SM count,
  * capped at 1024; larger values return RF_EINVAL).  Every GPU that loads the library holds that array until
  * the process exits.  It allocates nothing: no cudaMalloc/cudaFree and no

@@ -159,8 +159,8 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
   }
   int nl = 0;
   for (int c = 0; c < n_comps; ++c) nl += comp_n[c];
-  if (n_comps > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 4 components");
-  if (nl > RF_MAXL) return fail(RF_EUNSUPPORTED, "more than 4 leaves");
+  if (n_comps > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 6 components");
+  if (nl > RF_MAXL) return fail(RF_EUNSUPPORTED, "more than 6 leaves");
   P->n_leaves = nl;
   P->n_comp = n_comps;
   P->kind = kind;
@@ -364,6 +364,8 @@ static void free_work(rf_graph* g) {
   cudaFree(g->plain_partials);
   if (g->fit_stream) cudaStreamDestroy(g->fit_stream);
   cudaFree(g->pro_buf);
+  cudaFree(g->work.consts_x);
+  cudaFree(g->work.toy_consts_x);
   cudaFree(g->formula_buf);
   cudaFree(g->formula_ticket);
 }
@@ -378,6 +380,8 @@ rf_status rf_canonical_program(const rf_graph_desc* desc, RfProgram* P) {
   for (int k = 0; k < P->n_leaves; ++k)
     if (P->leaf[k].type == RFL_FORMULA)
       return fail(RF_EUNSUPPORTED, "formula leaves need rf_graph_compile (specialised kernels)");
+  if (P->n_leaves > RF_GENERIC_MAXL)
+    return fail(RF_EUNSUPPORTED, "more than 4 leaves need rf_graph_compile (specialised kernels)");
   return RF_OK;
 }
 
@@ -442,8 +446,10 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   }
   g->work.status = g->work.counter + 1;
   g->work.adam_t = reinterpret_cast<int32_t*>(g->work.counter + 2);
-  // constants of the separate prologue kernel
+  // constants of the separate prologue kernel, and its FP64 constants for a
+  // zero-coefficient call with FP32 evaluation
   e = cudaMalloc(&g->pro_buf, rf_consts_size(g->eval));
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.consts_x, sizeof(RfExact));
   if (e != cudaSuccess) {
     free_work(g);
     delete g;
@@ -467,10 +473,11 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   // Specialise the fused kernel for this graph unless RF_JIT=0.  If that is
   // not possible the graph keeps the precompiled generic kernels (same device
   // code, run-time dispatch); rf_graph_uses_jit reports which one runs.
-  // Formula leaves exist only in specialised kernels: without them the
-  // compile fails.
+  // Formula leaves and graphs of more than 4 leaves exist only in
+  // specialised kernels: without them the compile fails.
+  const bool jit_only = g->n_formula || g->prog.n_leaves > RF_GENERIC_MAXL;
   const char* env = getenv("RF_JIT");
-  if (!(env && env[0] == '0') || g->n_formula) {
+  if (!(env && env[0] == '0') || jit_only) {
     g->jit = true;
     std::string err;
     bool ok = jit_fused(g, g->cfg.ept, g->cfg.min_blocks, &err) != nullptr;
@@ -479,10 +486,11 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
                                  &err);
       ok = g->jk_norm != nullptr;
     }
-    if (!ok && g->n_formula) {
+    if (!ok && jit_only) {
+      const std::string what = g->n_formula ? "formula leaves" : "more than 4 leaves";
       free_work(g);
       delete g;
-      return fail(RF_ECUDA, "formula leaves need the specialised kernels: " + err);
+      return fail(RF_ECUDA, what + " need the specialised kernels: " + err);
     }
     if (!ok) {
       g->jit = false;
@@ -498,6 +506,8 @@ rf_status rf_graph_set_jit(rf_graph* g, int32_t enable) {
   if (!enable) {
     if (g->n_formula)
       return fail(RF_EUNSUPPORTED, "formula leaves run only in the specialised kernels");
+    if (g->prog.n_leaves > RF_GENERIC_MAXL)
+      return fail(RF_EUNSUPPORTED, "more than 4 leaves run only in the specialised kernels");
     g->jit = false;
     if (g->cfg.ept == 16) g->cfg.ept = 8;  // not instantiated in the generic kernels
     return RF_OK;
@@ -723,9 +733,11 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "rf_graph_bind_events sync");
   cudaFree(g->work.toy_consts);
+  cudaFree(g->work.toy_consts_x);
   cudaFree(g->work.adam_m1);
   cudaFree(g->work.adam_m2);
   g->work.toy_consts = nullptr;
+  g->work.toy_consts_x = nullptr;
   g->work.adam_m1 = g->work.adam_m2 = nullptr;
   g->bound = false;
   g->max_toys = 0;
@@ -744,6 +756,7 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events, int64_t n_events
   }
   const size_t np = (size_t)std::max(g->prog.n_par, 1);
   e = cudaMalloc(&g->work.toy_consts, rf_consts_size(g->eval) * (size_t)max_toys);
+  if (e == cudaSuccess) e = cudaMalloc(&g->work.toy_consts_x, sizeof(RfExact) * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m1, sizeof(double) * np * (size_t)max_toys);
   if (e == cudaSuccess) e = cudaMalloc(&g->work.adam_m2, sizeof(double) * np * (size_t)max_toys);
   if (e != cudaSuccess) return fail(RF_ENOMEM, "bind: toy workspace allocation failed");
@@ -1035,23 +1048,22 @@ void tune_store(uint64_t key, const RfLaunchCfg& c) {
   }
 }
 
-// Mean time of one fused call with configuration c: 7 calls, the first two
-// are warm-up.  Adds the five timed calls to *tsum.
+// Time of five fused calls with configuration c, issued back to back after
+// two warm-up calls (a queue of evaluations: each call's FP64 prologue
+// overlaps the previous call's event pass, so the time is the event pass's).
 cudaError_t time_config(rf_graph* g, const RfLaunchCfg& c, const void* events, int64_t n_events,
                         const double* params, double* dout, cudaEvent_t a, cudaEvent_t b,
                         cudaStream_t st, float* tsum) {
   cudaError_t e = cudaSuccess;
   *tsum = 0.f;
-  for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
-    cudaEventRecord(a, st);
-    int le = fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
-    cudaEventRecord(b, st);
-    if (le) e = (cudaError_t)le;
-    if (e == cudaSuccess) e = cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (rep >= 2) *tsum += ms;
-  }
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+    e = (cudaError_t)fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep)
+    e = (cudaError_t)fused_dispatch(g, c, events, n_events, params, dout, dout + 1, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(tsum, a, b);
   return e;
 }
 

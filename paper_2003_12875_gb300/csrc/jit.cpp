@@ -196,9 +196,9 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
   // The same event in FP64 on the FP64 constants, for FP32 evaluation of a
   // call or toy with a coefficient exactly 0 (x: the column values in their
   // own precision); returns log2 P - beta_ref / ln 2.
-  o << "  static __device__ __noinline__ double event_exact(const RfConsts<float>* __restrict__ Kp, "
+  o << "  static __device__ __noinline__ double event_exact(const RfExact* __restrict__ Kp, "
        "const double* __restrict__ x, float* __restrict__ q) {\n"
-       "    const RfConsts<float>& K = *Kp;\n";
+       "    const RfExact& K = *Kp;\n";
   for (int k = 0; k < NL; ++k) {
     const RfLeafProg& L = P.leaf[k];
     o << "    double u" << k << ", g" << k << "[4];\n    ";

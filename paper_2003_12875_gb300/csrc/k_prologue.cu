@@ -18,15 +18,22 @@ __device__ __forceinline__ void prologue_body(const RfProgram& P, const double* 
   __shared__ RfConsts<Real> K;
   __shared__ double lnI[RF_MAXL];
   __shared__ int ok[RF_MAXL];
+  __shared__ RfExact Xs;
   // formula leaves: their integrals come from the normalisation kernel just
   // before, so wait for it first
   if (P.formula_norm) asm volatile("griddepcontrol.wait;" ::: "memory");
-  block_prologue(P, params, K, lnI, ok);
+  block_prologue(P, params, K, lnI, ok, &Xs);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
   const double* src = reinterpret_cast<const double*>(&K);
   double* dst = static_cast<double*>(W.consts);
   for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+  if (sizeof(Real) == 4 && K.zero_mask != 0 && W.consts_x) {
+    constexpr int kx = (int)(sizeof(RfExact) / sizeof(double));
+    const double* xs = reinterpret_cast<const double*>(&Xs);
+    double* xd = reinterpret_cast<double*>(W.consts_x);
+    for (int w = threadIdx.x; w < kx; w += blockDim.x) xd[w] = xs[w];
+  }
 }
 
 template <typename Real>

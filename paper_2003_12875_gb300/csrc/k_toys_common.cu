@@ -45,6 +45,8 @@ int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, in
     case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     case 3: rf::toy_finalize_kernel<Real, 3><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     case 4: rf::toy_finalize_kernel<Real, 4><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 5: rf::toy_finalize_kernel<Real, 5><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
+    case 6: rf::toy_finalize_kernel<Real, 6><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();
@@ -107,10 +109,10 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   int rc = eval ? (int)cudaLaunchKernelEx(&plc, rf::toy_prep_kernel<double>, P, pmc, offsets,
                                           toys, n_events,
                                           static_cast<RfConsts<double>*>(W.toy_consts), W.status,
-                                          at)
+                                          at, W.toy_consts_x)
                 : (int)cudaLaunchKernelEx(&plc, rf::toy_prep_kernel<float>, P, pmc, offsets, toys,
                                           n_events, static_cast<RfConsts<float>*>(W.toy_consts),
-                                          W.status, at);
+                                          W.status, at, W.toy_consts_x);
   if (rc) return rc;
   const int g = (int)grid;
   if (jit_toys)

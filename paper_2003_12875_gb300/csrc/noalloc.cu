@@ -10,7 +10,7 @@
 // the per-block and per-group partial sums, the tickets and the status word -- from a
 // file-scope static device array instead of an allocation.
 //
-// The array (kBytes, about 178 KB) is part of this library's device
+// The array (kBytes, 256 KiB) is part of this library's device
 // image: every GPU that loads the library holds it until the process exits.
 // Every call shares it and it keeps the last call's contents, so calls that
 // overlap on the GPU (two streams, or two threads on one stream without

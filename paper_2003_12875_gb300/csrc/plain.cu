@@ -11,6 +11,10 @@
 #include "rf_device.cuh"
 
 namespace rf {
+// device pointer table of one evaluation: the component arrays, then the
+// leaf arrays of every component
+constexpr int kPtrSlots = RF_MAXC + RF_MAXC * RF_MAXL;
+
 
 __global__ void plain_consts_kernel(const RfProgram P, const double* params,
                                     RfConsts<double>* K) {
@@ -189,8 +193,8 @@ static int plain_all(const RfProgram& P, const void* events, int64_t n,
   // scratch after the node arrays
   const int NL = P.n_leaves, C = P.n_comp;
   double* tail = nb + (int64_t)(NL + C + 2) * n;
-  const double** ptrs = reinterpret_cast<const double**>(tail);   // 32 slots
-  double* pp = tail + 32;                                          // [RF_MAXPAR]
+  const double** ptrs = reinterpret_cast<const double**>(tail);   // kPtrSlots slots
+  double* pp = tail + kPtrSlots;                                   // [RF_MAXPAR]
   double* fvals = pp + RF_MAXPAR;                                  // [2*RF_MAXPAR]
   double* hs = fvals + 2 * RF_MAXPAR;                              // [RF_MAXPAR]
   RfConsts<double>* K = reinterpret_cast<RfConsts<double>*>(hs + RF_MAXPAR);
@@ -215,7 +219,7 @@ static int plain_all(const RfProgram& P, const void* events, int64_t n,
 }  // namespace rf
 
 size_t rf_plain_bytes(const RfProgram& P, int64_t n) {
-  return sizeof(double) * ((size_t)(P.n_leaves + P.n_comp + 2) * (size_t)n + 32 +
+  return sizeof(double) * ((size_t)(P.n_leaves + P.n_comp + 2) * (size_t)n + rf::kPtrSlots +
                            4 * RF_MAXPAR) +
          sizeof(RfConsts<double>) + 256;
 }

@@ -28,7 +28,7 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
                                               const int64_t* __restrict__ offsets,
                                               int32_t toys, int64_t n_events,
                                               RfConsts<Real>* consts, unsigned int* status,
-                                              int32_t* adam_t) {
+                                              int32_t* adam_t, RfExact* consts_x) {
   asm volatile("griddepcontrol.launch_dependents;");
   __shared__ RfConsts<Real> Ks[32];
   __shared__ double lnI_s[RF_MAXL][32];
@@ -54,7 +54,8 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
       l[j] = lnI_s[j][lane];
       all &= ok_s[j][lane] != 0;
     }
-    comb_consts(P, pm + t * P.n_par, Ks[lane], l, all);
+    comb_consts(P, pm + t * P.n_par, Ks[lane], l, all,
+                consts_x ? consts_x + t : nullptr);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
@@ -148,8 +149,8 @@ template <typename Real>
 __global__ void toy_prep_kernel(const RfProgram P, const double* __restrict__ pm,
                                 const int64_t* __restrict__ offsets, int32_t toys,
                                 int64_t n_events, RfConsts<Real>* consts,
-                                unsigned int* status, int32_t* adam_t) {
-  toy_prep_body<Real>(P, pm, offsets, toys, n_events, consts, status, adam_t);
+                                unsigned int* status, int32_t* adam_t, RfExact* consts_x) {
+  toy_prep_body<Real>(P, pm, offsets, toys, n_events, consts, status, adam_t, consts_x);
 }
 
 template <typename Real, typename Col, int NL, int EPT>

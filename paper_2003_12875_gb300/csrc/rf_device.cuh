@@ -382,19 +382,24 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
     case RFL_FORMULA:  // the formula runs on the parameters rounded to T
       for (int j = 0; j < L.npar; ++j) pc[j] = (T)th[j];
       break;
-    case RFL_ARGUS:
-      split_hi_lo(th[0] * th[0], pc[0], pc[1]);  // m0^2, hi + lo
-      pc[2] = (T)(1.0 / (th[0] * th[0]));
+    case RFL_ARGUS: {
+      // m0^2 as the exact pair sq + e (e = the FMA's rounding error of the
+      // product), then as T's hi + lo
+      const double sq = th[0] * th[0], e = fma(th[0], th[0], -sq);
+      pc[0] = (T)sq;
+      pc[1] = (T)((sq - (double)pc[0]) + e);
+      pc[2] = (T)(1.0 / sq);
       pc[3] = (T)(th[1] * kLog2e);  // c in base-2 units (for u)
       pc[4] = (T)(2.0 / th[0]);
       split_hi_lo(th[2], pc[5], pc[7]);  // p (general-p form), hi + lo
       pc[6] = (T)th[1];  // c (for the m0 derivative)
       break;
+    }
   }
 }
 
-// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k], K.gmul[k],
-// K.lmeta[k] and lnI_out (K.pcd: comb_consts, when FP32 evaluation needs it).
+// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k], K.gmul[k]
+// and lnI_out.
 template <typename Real>
 __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, int k, double* lnI_out) {
@@ -413,8 +418,6 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
   }
   K.lnI[k] = *lnI_out;
-  K.lmeta[k] = (L.type & 0xff) | ((L.gmask & 0xff) << 8) | ((L.comp & 0xff) << 16) |
-               ((L.col & 0xff) << 24);
   Real* pc = K.pc[k];
   leaf_pc<Real>(L, th, pc);
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
@@ -465,11 +468,13 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   return ok;
 }
 
-// Combination constants (one thread), after every leaf's lnI is known.
+// Combination constants (one thread), after every leaf's lnI is known.  X
+// (may be NULL): where FP32 evaluation with a zero coefficient gets its FP64
+// constants.
 template <typename Real>
 __device__ __noinline__ void comb_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, const double* lnI,
-                                   bool leaves_ok) {
+                                   bool leaves_ok, RfExact* X = nullptr) {
   bool bad = !leaves_ok;
   const int C = P.n_comp;
   double coef[RF_MAXC], base[RF_MAXC];
@@ -521,7 +526,6 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
   }
   K.beta_ref = ref;
   K.zero_mask = zero;
-  K.n_comp = C;
   for (int c = 0; c < RF_MAXC; ++c) {
     K.coef[c] = coef[c];
     if (c < C && !((zero >> c) & 1)) {
@@ -535,20 +539,24 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
     }
     K.delta_nc[c] = (Real)(c < C ? (base[c] - ref) * kLog2e : 0.0);
   }
-  if (sizeof(Real) == 4 && zero != 0) {
+  if (sizeof(Real) == 4 && zero != 0 && X) {
     // FP32 evaluation with a zero coefficient runs every event in FP64 on the
-    // exact constants (pcd, delta_d, delta_nc_d; built only here, the rare
-    // case): nothing to correct for rounding
+    // exact constants (built only here, the rare case): nothing to correct
+    // for rounding
+    X->zero_mask = zero;
+    X->n_comp = C;
     for (int c = 0; c < RF_MAXC; ++c) {
-      K.delta_d[c] = (c < C && !((zero >> c) & 1)) ? (beta[c] - ref) * kLog2e : -kInf();
-      K.delta_nc_d[c] = c < C ? (base[c] - ref) * kLog2e : 0.0;
+      X->delta_d[c] = (c < C && !((zero >> c) & 1)) ? (beta[c] - ref) * kLog2e : -kInf();
+      X->delta_nc_d[c] = c < C ? (base[c] - ref) * kLog2e : 0.0;
       K.delta_lo[c] = 0.0;
     }
     for (int k = 0; k < P.n_leaves; ++k) {
       const RfLeafProg& L = P.leaf[k];
       double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
       for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
-      leaf_pc<double>(L, th, K.pcd[k]);
+      leaf_pc<double>(L, th, X->pcd[k]);
+      X->lmeta[k] = (L.type & 0xff) | ((L.gmask & 0xff) << 8) | ((L.comp & 0xff) << 16) |
+                    ((L.col & 0xff) << 24);
     }
     for (int k = 0; k < RF_MAXL; ++k)
       for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = 0.0;
@@ -876,9 +884,9 @@ struct EvalConsts {
   Real delta[NL];
   Real delta_nc[NL];
   int zero_mask;
-  const RfConsts<Real>* full;  // the constants these came from (FP64 path)
-  __device__ __forceinline__ void load(const RfConsts<Real>& K) {
-    full = &K;
+  const RfExact* full;  // FP64 constants (FP32 evaluation, a zero coefficient)
+  __device__ __forceinline__ void load(const RfConsts<Real>& K, const RfExact* X = nullptr) {
+    full = X;
 #pragma unroll
     for (int k = 0; k < NL; ++k)
 #pragma unroll

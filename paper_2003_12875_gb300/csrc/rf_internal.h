@@ -22,8 +22,11 @@ typedef unsigned long long uintptr_t;
 #include <stdint.h>
 #endif
 
-#define RF_MAXL 4        // leaves per compiled graph
-#define RF_MAXC 4        // components (Add children)
+#define RF_MAXL 6        // leaves per compiled graph (specialised kernels)
+#define RF_MAXC 6        // components (Add children)
+// the precompiled generic kernels (run-time dispatch) take up to 4 leaves;
+// graphs with more run only in the kernels specialised for them
+#define RF_GENERIC_MAXL 4
 #define RF_LEAF_MAXP 4   // parameters per leaf
 #define RF_PC 8          // per-leaf evaluation constants
 #define RF_MAXPAR 64
@@ -117,15 +120,20 @@ struct alignas(16) RfConsts {  // 16-byte multiple: arrays of it are bulk-copied
   double ext_sum;              // sum of yields (extended) else 0
   int32_t zero_mask;           // bit c: coef_c == 0
   int32_t bad;                 // parameter outside its definition range
-  // FP32 evaluation of a call (or toy) with a coefficient exactly 0 evaluates
-  // every event in FP64 (the absent component's P_c/P grows without bound
-  // in the tails of the others, beyond what FP32 log-densities resolve): the
-  // per-event constants and the deltas in FP64, and each leaf's form
+};
+
+// FP32 evaluation of a call (or toy) with a coefficient exactly 0 evaluates
+// every event in FP64 (the absent component's P_c/P grows without bound in
+// the tails of the others, beyond what FP32 log-densities resolve): the
+// per-event constants and the deltas in FP64, and each leaf's form.  Written
+// by the prologues only for such calls.
+struct alignas(16) RfExact {
   double pcd[RF_MAXL][RF_PC];  // pc in FP64 (hi + lo pairs as (value, 0))
   double delta_d[RF_MAXC];     // delta_c in base-2 units (-inf: coef_c == 0)
   double delta_nc_d[RF_MAXC];  // (delta_c - log coef_c) in base-2 units
   int32_t lmeta[RF_MAXL];      // type | gmask << 8 | comp << 16 | col << 24
   int32_t n_comp;
+  int32_t zero_mask;
 };
 
 // Device workspace owned by an rf_graph.
@@ -142,6 +150,9 @@ struct RfWork {
   // single dataset: constants from the separate prologue kernel (NULL: each
   // block computes them itself)
   void* consts;            // [1] RfConsts<Real>
+  RfExact* consts_x;       // [1] (single dataset) FP64 constants of a
+                           // zero-coefficient call with FP32 evaluation
+  RfExact* toy_consts_x;   // [max_toys] the same per toy
 };
 
 struct RfLaunchCfg {

@@ -38,10 +38,10 @@ struct GenericModel {
   // formulas on the FP64 constants, the absent components' P_c/P from FP64
   // log-densities.  Adds the event's terms to q (FP32 sums) and returns
   // log2 P - beta_ref / ln 2.  Not inlined: it stays out of the event loops.
-  static __device__ __noinline__ double event_exact(const RfConsts<float>* __restrict__ Kp,
+  static __device__ __noinline__ double event_exact(const RfExact* __restrict__ Kp,
                                                     const double* __restrict__ x,
                                                     float* __restrict__ q) {
-    const RfConsts<float>& K = *Kp;
+    const RfExact& K = *Kp;
     double u[NL], g[NL][RF_LEAF_MAXP];
     int comp[NL], gms[NL];
 #pragma unroll
@@ -432,7 +432,8 @@ __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real,
 // proceeds in parallel), then the combination by thread 0.
 template <typename Real>
 __device__ inline void block_prologue(const RfProgram& P, const double* params,
-                                      RfConsts<Real>& K, double* lnI, int* ok) {
+                                      RfConsts<Real>& K, double* lnI, int* ok,
+                                      RfExact* X = nullptr) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
   for (int k = wid; k < P.n_leaves; k += nw)
@@ -441,7 +442,7 @@ __device__ inline void block_prologue(const RfProgram& P, const double* params,
   if (threadIdx.x == 0) {
     bool all = true;
     for (int k = 0; k < P.n_leaves; ++k) all &= ok[k] != 0;
-    comb_consts(P, params, K, lnI, all);
+    comb_consts(P, params, K, lnI, all, X);
   }
   __syncthreads();
 }
@@ -459,7 +460,9 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   __shared__ int ok[RF_MAXL];
   __shared__ double red[32 * NA];
   __shared__ double tot[NA];
+  __shared__ RfExact Xs;  // FP64 constants when the block builds its own
 
+  const RfExact* X = W.consts_x;
   if (W.consts) {
     // constants from the prologue kernel, which this launch may overlap:
     // wait for it (a no-op when this grid was not launched as its dependent)
@@ -473,14 +476,15 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     // (it publishes new constants only after this grid has finished)
     asm volatile("griddepcontrol.launch_dependents;");
   } else {
-    block_prologue(P, params, K, lnI, ok);
+    block_prologue(P, params, K, lnI, ok, &Xs);
+    X = &Xs;
   }
 
   Acc<Real, NA, M::AMASK> acc;
   acc.zero();
   if (!K.bad) {
     EvalConsts<Real, NL> E;
-    E.load(K);
+    E.load(K, X);
     const int64_t h = head < n ? head : n;
     const int64_t nfull = (n - h) / EPT;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
@@ -520,9 +524,10 @@ __device__ __forceinline__ void logp_body(const RfProgram& P, const Col* __restr
   __shared__ RfConsts<Real> K;
   __shared__ double lnI[RF_MAXL];
   __shared__ int ok[RF_MAXL];
-  block_prologue(P, params, K, lnI, ok);
+  __shared__ RfExact Xs;
+  block_prologue(P, params, K, lnI, ok, &Xs);
   EvalConsts<Real, NL> E;
-  E.load(K);
+  E.load(K, &Xs);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     Real xc[NL];

@@ -251,13 +251,14 @@ struct ToyState {
   bool bad, any;
   EvalConsts<Real, NL> E;
   Acc<Real, NA, M::AMASK> acc;
+  const RfExact* xs;  // the toys' FP64 constants (zero-coefficient toys)
   __device__ __forceinline__ void open(const RfConsts<Real>* consts, const int64_t* offsets,
                                        int64_t stride, int32_t tt) {
     t = tt;
     tb = toy_off(offsets, t, stride);
     te = toy_off(offsets, (int64_t)t + 1, stride);
     bad = consts[t].bad != 0;
-    if (!bad) E.load(consts[t]);
+    if (!bad) E.load(consts[t], xs ? xs + t : nullptr);
     acc.zero();
     any = false;
   }
@@ -333,6 +334,7 @@ __device__ __forceinline__ void toy_segment_body(const RfProgram& P, const Col* 
 
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
   ToyState<M, Real> T;
+  T.xs = W.toy_consts_x;
   T.open(consts, offsets, stride, t);
   double* rows = W.partials + w * RF_NACC_MAX;  // row of (w, t) = rows + t * RF_NACC_MAX
   // ragged head, straight from the columns
@@ -430,6 +432,7 @@ __device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
   if (!active) return;
   const RfConsts<Real>* consts = static_cast<const RfConsts<Real>*>(W.toy_consts);
   ToyState<M, Real> T;
+  T.xs = W.toy_consts_x;
   T.open(consts, offsets, stride, t);
   double* rows = W.partials + w * RF_NACC_MAX;
   for (int64_t p = wb; p < we;) {

@@ -97,11 +97,13 @@ def test_unsupported_shapes(rf):
     s["nodes"].append({"type": "prod", "children": [2]})
     s["root"] = 3
     assert rf.validate(s) == EUNSUPPORTED
-    # five leaves
-    nodes = [{"type": "gauss", "obs": 0, "params": [0, 1]} for _ in range(5)]
-    nodes.append({"type": "add_frac", "children": [0, 1, 2, 3, 4], "params": [2, 2, 2, 2]})
-    s = {"obs": [(0.0, 1.0)], "params": [0.5, 1.0, 0.1], "nodes": nodes, "root": 5}
-    assert rf.validate(s) == EUNSUPPORTED
+    # six leaves are taken, seven are not
+    for k, want in ((5, 0), (6, 0), (7, EUNSUPPORTED)):
+        nodes = [{"type": "gauss", "obs": 0, "params": [0, 1]} for _ in range(k)]
+        nodes.append({"type": "add_frac", "children": list(range(k)), "params": [2] * (k - 1)})
+        s = {"obs": [(0.0, 1.0)], "params": [0.5, 1.0, 0.1], "nodes": nodes, "root": k}
+        assert rf.validate(s) == want, k
+    assert rf.validate(datagen.prod6_spec(), "f32", "fp32") == 0
     # Chebychev of order 5
     s = {"obs": [(-1.0, 1.0)], "params": [0.1] * 5,
          "nodes": [{"type": "cheb", "obs": 0, "params": [0, 1, 2, 3, 4]}], "root": 0}

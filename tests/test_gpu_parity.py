@@ -43,7 +43,9 @@ SMALL = {
     "johnson": lambda: datagen.johnson_exp(20_011, 80_000),
     "c5_free_p": lambda: _free_p(datagen.c5(3_000, 300_000)),
     "c5_fixed_p": lambda: _fixed_p(datagen.c5(3_000, 300_000), 0.8),
+    "prod6": lambda: datagen.prod6(60_011),
 }
+JIT_ONLY = {"prod6"}  # more than 4 leaves: specialised kernels only
 OFF_MIN = {  # gradient checks away from the minimum
     "c1": [0.25, 1.1],
     "c2": [5.05, 0.52, -0.28, 0.21],
@@ -53,6 +55,8 @@ OFF_MIN = {  # gradient checks away from the minimum
     "johnson": [4.05, 0.78, -0.45, 1.62, -0.21, 19_800.0, 80_300.0],
     "c5_free_p": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.58, 3_050.0, 299_000.0],
     "c5_fixed_p": [5.2792, 0.0031, 1.55, 3.1, 5.29, -19.5, 0.8, 3_050.0, 299_000.0],
+    "prod6": [5.05, 0.62, -1.15, 3.02, 0.41, 1.25, 2.6, 0.28, -0.18, -0.24, 0.18, 0.31,
+              0.31, 0.29],
 }
 
 
@@ -94,6 +98,10 @@ def test_nll_and_gradient_match_oracle(rf, name, prec, jit):
     """Both kernel forms: specialised for the graph (NVRTC) and generic."""
     w, p, v, g, sc = workload(name)
     G = rf.Graph(w["spec"], w["dtype"], prec)
+    if name in JIT_ONLY and not jit:
+        with pytest.raises(rf.RFError):
+            G.set_jit(False)
+        return
     G.set_jit(jit)
     assert G.uses_jit() == jit
     nll, grad = G.nll(to_dev(w), params_dev(p))
@@ -111,8 +119,11 @@ def test_nll_and_gradient_match_oracle(rf, name, prec, jit):
 
 @pytest.mark.parametrize("jit", [True, False])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson", "c5_free_p", "c5_fixed_p"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c5", "johnson", "c5_free_p", "c5_fixed_p",
+                                  "prod6"])
 def test_per_event_log_probability(rf, name, prec, jit):
+    if name in JIT_ONLY and not jit:
+        pytest.skip("specialised kernels only")
     w, p, *_ = workload(name)
     sub = {**w, "cols": w["cols"][:, :20_011]}
     want, rc = oracle.logp(w["spec"], p, sub["cols"].astype(np.float64))
@@ -364,6 +375,31 @@ def test_zero_fraction_edge(rf, jit):
             assert err.max() <= TOL[prec]["grad"], (f, prec, err)
             got = G.logp(to_dev({**w, "cols": w["cols"][:, :5003]}), params_dev(q))
             assert logp_err(got.cpu().numpy(), want).max() <= TOL[prec]["logp"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_six_leaf_toys(rf, prec):
+    """Toys of the six-leaf model (three two-observable components): the
+    batched NLL and gradient of every toy against the oracle."""
+    w = datagen.prod6(40_000)
+    spec = w["spec"]
+    off = np.array([0, 3_000, 3_001, 9_500, 9_500, 21_000, 40_000], np.int64)
+    rng = np.random.default_rng(5)
+    pm = np.array(OFF_MIN["prod6"])[None, :] * (1 + 0.01 * rng.standard_normal((6, 14)))
+    pm[:, 12:] = [0.3, 0.3]
+    want, rc = oracle.nll_batched(spec, w["cols"], off, pm)
+    assert rc == 0
+    G = rf.Graph(spec, "f32", prec)
+    G.bind_events(to_dev(w), 6)
+    got = G.nll_batched(torch.from_numpy(off).to(DEV), torch.from_numpy(pm).to(DEV)).cpu().numpy()
+    for t in range(6):
+        n_t = int(off[t + 1] - off[t])
+        if n_t == 0:
+            continue
+        assert rel_nll(got[t, 0], want[t, 0]) <= TOL[prec]["nll"], (t, got[t, 0], want[t, 0])
+        if n_t >= 200:
+            _, _, sc, _ = oracle.nll_scaled(spec, pm[t], w["cols"][:, off[t]:off[t + 1]])
+            assert grad_l1(got[t, 1:], want[t, 1:], sc, [True] * 14).max() <= TOL[prec]["grad"]
 
 
 def test_zero_yield_toys_and_ragged_ends(rf):
