@@ -378,8 +378,38 @@ def small_configs(rf, torch, rates=None, hbm_gbs=None):
                     r["roofline_cold"] = roofline_8d(name, prec, n, bpe,
                                                      r["cold_us_median"] * 1e-3, rates, hbm_gbs)
             res[f"{name}_{prec}"] = r
+    res["c3_fp32_n_odd"] = odd_length_c3(rf, torch, rates, hbm_gbs)
     res["formula_leaves"] = formula_vs_builtin(rf, torch)
     return res
+
+
+def odd_length_c3(rf, torch, rates=None, hbm_gbs=None):
+    """C3 with 10,000,001 events: the three FP32 columns start at different
+    16-byte phases (column j at j * n * 4 bytes), so the fused kernel reads
+    them with 32-bit loads; per-event time against the 10,000,000-event run."""
+    import numpy as np
+
+    import datagen
+    w = datagen.c3(n=10_000_001)
+    ev = torch.from_numpy(np.ascontiguousarray(w["cols"])).cuda()
+    n = w["cols"].shape[1]
+    params = torch.tensor(w["spec"]["params"], dtype=torch.float64, device="cuda")
+    G = rf.Graph(w["spec"], w["dtype"], "fp32")
+    G.tune(ev, params)
+    out = torch.empty(1 + len(w["spec"]["params"]), dtype=torch.float64, device="cuda")
+    for _ in range(20):
+        G.nll(ev, params, out=out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(200):
+        G.nll(ev, params, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    r = {"events": n, "stream_us": a.elapsed_time(b) * 1e3 / 200, "launch": G.get_launch()}
+    if rates:
+        r["roofline"] = roofline_8d("c3", "fp32", n, 12, r["stream_us"] * 1e-3, rates, hbm_gbs)
+    return r
 
 
 def formula_vs_builtin(rf, torch):

@@ -312,9 +312,9 @@ rf_status rf_nll_plain(rf_graph* g, const void* events, int64_t n_events,
  * blocks per SM used to size the grid (1..8) of the fused and segment
  * kernels, and events per thread per iteration of the fused kernel (FP32
  * eval: 4, 8, or 16 with the graph-specialised kernels; FP64 eval: 2 or 4;
- * the toy segment kernel takes its own: 16 events per lane with FP32
- * evaluation, 8 with FP64).  min_blocks (2, 3 or 4) is the register budget the
- * graph-specialised fused kernel is compiled for: room for that many blocks
+ * the toy segment kernel takes its own: 8 events per lane).  min_blocks
+ * (2, 3 or 4) is the register budget the graph-specialised fused kernel is
+ * compiled for: room for that many blocks
  * of 256 threads on one SM (at most 128, 80 or 64 registers per thread); the
  * generic kernels ignore it.  Defaults: 3 for FP32 evaluation, 2 for FP64;
  * rf_graph_tune tries 2, 3 and 4. */

@@ -308,9 +308,10 @@ static int toy_ept(const rf_graph* g) {
     const int e = atoi(v);
     if (g->eval == RF_EVAL_FP32 ? (e == 8 || e == 16) : (e == 4 || e == 8)) return e;
   }
-  // measured on the 4096 Gauss + Exponential toys (1.3e8 events): FP32, 16
-  // (0.182 ms a step) beats 8 (0.205 ms); FP64, 8 beats 4
-  return g->eval == RF_EVAL_FP32 ? 16 : 8;
+  // measured on the 4096 Gauss + Exponential toys (1.3e8 events): FP32, 8
+  // (0.174 ms a step) beats 16 (0.194 ms) since the per-event code shrank;
+  // FP64, 8 beats 4
+  return 8;
 }
 // register budget of the segment kernel: 0 = the compiler's choice, else
 // launch bounds for 3 or 4 resident blocks of 256 threads (tuning)
@@ -566,7 +567,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     const bool fp32 = desc->eval_precision == RF_EVAL_FP32;
     const bool toy = kind == RF_JIT_TOYS || kind == RF_JIT_TOYS_BULK;
     const int cd = (toy && fp32) ? (int)RF_F32 : (int)desc->column_dtype;
-    const int ke = toy ? (fp32 ? 16 : 8) : ept;  // the segment kernel's events per lane
+    const int ke = toy ? 8 : ept;  // the segment kernel's events per lane
     if (!rf_jit_compile_only(P, fcp, desc->eval_precision, cd, kind, ke, toy ? 0 : 3, &err))
       return fail(RF_ECUDA, err);
   }

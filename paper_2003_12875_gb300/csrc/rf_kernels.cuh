@@ -219,8 +219,11 @@ __device__ __forceinline__ void load_full(const RfProgram& P, const Col* __restr
   }
 }
 
-// Kahan-compensated running sums (value = s - c) over the accumulators in
-// MASK; the others stay zero and generate no instructions.
+// A thread's running sums over the accumulators in MASK (the others stay
+// zero and generate no instructions).  The log-likelihood sum (accumulator 0,
+// held to the tighter NLL bound) is Kahan-compensated (value = s - c); the
+// weight and gradient sums, whose bound is relative to the sum of the terms'
+// magnitudes, are plain sums of the per-chunk partials (c stays 0).
 template <typename Real, int N, unsigned long long MASK>
 struct Acc {
   Real s[N], c[N];
@@ -232,10 +235,14 @@ struct Acc {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!((MASK >> i) & 1ull)) continue;
-      Real y = q[i] - c[i];
-      Real t = s[i] + y;
-      c[i] = (t - s[i]) - y;
-      s[i] = t;
+      if (i == 0) {
+        Real y = q[i] - c[i];
+        Real t = s[i] + y;
+        c[i] = (t - s[i]) - y;
+        s[i] = t;
+      } else {
+        s[i] += q[i];
+      }
     }
   }
   __device__ __forceinline__ double value(int i) const {

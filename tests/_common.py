@@ -11,14 +11,15 @@ thread's sums are Kahan-compensated in FP32, a block adds them in FP32 pairs
 sum above the block is FP64, so the NLL error stays near the per-event
 rounding (1e-7 allows one unit of the last place in the worst event to be
 systematic); the gradient bound is the target the method is held to.
-Per-event log P: FP64 within 1e-13 * max(1, |log P|), FP32 within
+Per-event log P: FP64 within 2e-14 * max(1, |log P|) (the batch-vs-classic
+accuracy of the paper's Sec. 5.3 on log-likelihoods), FP32 within
 2e-6 * max(1, |log P|).
 """
 import math
 
 import numpy as np
 
-TOL = {"fp64": {"nll": 1e-12, "grad": 1e-10, "logp": 1e-13},
+TOL = {"fp64": {"nll": 1e-12, "grad": 1e-10, "logp": 2e-14},
        "fp32": {"nll": 1e-7, "grad": 1e-6, "logp": 2e-6}}
 
 
