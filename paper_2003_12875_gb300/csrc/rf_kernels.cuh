@@ -187,6 +187,22 @@ struct Vec<double> {
   typedef double2 T;
 };
 
+// Chunk ch of EPT events per thread from event `base`: with 128-bit loads
+// (vec) the EPT consecutive events base + ch*EPT ...; without (the columns do
+// not share a 16-byte phase) the lanes of a warp interleave, so that each
+// 32-bit load of the warp reads 32 consecutive events: lane l (= ch mod 32)
+// of warp chunk ch/32 takes base + (ch/32)*32*EPT + l + 32 e.  Either way the
+// chunks 0 .. nfull-1 cover [base, base + nfull*EPT) once (without vec, nfull
+// is a multiple of 32).
+template <int EPT>
+__device__ __forceinline__ int64_t chunk_start(int64_t base, int64_t ch, bool vec) {
+  return vec ? base + ch * EPT : base + (ch >> 5) * (32 * EPT) + (ch & 31);
+}
+template <int EPT>
+__device__ __forceinline__ int64_t full_chunks(int64_t len, bool vec) {
+  return vec ? len / EPT : (len / (32 * EPT)) * 32;
+}
+
 template <typename Real, typename Col, int NL, int NCOL, int EPT>
 __device__ __forceinline__ void load_full(const RfProgram& P, const Col* __restrict__ ev,
                                           int64_t stride, int64_t i0, bool vec,
@@ -210,7 +226,7 @@ __device__ __forceinline__ void load_full(const RfProgram& P, const Col* __restr
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) x[c][e] = cvt<Real, Col>(__ldcs(col + e));
+        for (int e = 0; e < EPT; ++e) x[c][e] = cvt<Real, Col>(__ldcs(col + 32 * e));
       }
     } else {
 #pragma unroll
@@ -367,21 +383,24 @@ __device__ __forceinline__ void stream_chunks(const RfProgram& P,
   // two register buffers used in turn (unrolled by two, so no buffer is
   // copied into the other)
   Real xa[NL][EPT], xb[NL][EPT];
-  load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + first * EPT, vec, xa);
+  load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, chunk_start<EPT>(base, first, vec), vec,
+                                         xa);
   for (int64_t ch = first;;) {
     const int64_t nb = ch + step;
     if (nb >= nfull) {
       compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
       break;
     }
-    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + nb * EPT, vec, xb);
+    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, chunk_start<EPT>(base, nb, vec), vec,
+                                           xb);
     compute_full<M, Real, EPT, ANYZERO>(P, K, xa, acc);
     const int64_t na = nb + step;
     if (na >= nfull) {
       compute_full<M, Real, EPT, ANYZERO>(P, K, xb, acc);
       break;
     }
-    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, base + na * EPT, vec, xa);
+    load_full<Real, Col, NL, M::NCOL, EPT>(P, ev, stride, chunk_start<EPT>(base, na, vec), vec,
+                                           xa);
     compute_full<M, Real, EPT, ANYZERO>(P, K, xb, acc);
     ch = na;
   }
@@ -493,7 +512,7 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     EvalConsts<Real, NL> E;
     E.load(K, X);
     const int64_t h = head < n ? head : n;
-    const int64_t nfull = (n - h) / EPT;
+    const int64_t nfull = full_chunks<EPT>(n - h, vec != 0);
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool exact = false;
@@ -509,10 +528,10 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
         stream_chunks<M, Real, Col, EPT, false>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
       else
         stream_chunks<M, Real, Col, EPT, true>(P, E, ev, n, h, first, gsz, nfull, vec != 0, acc);
-      if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
-        iterate_scalar<M, Real, Col>(P, E, ev, n, 0, h, acc);
-        iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT, n, acc);
-      }
+      // the events before the first aligned one and after the last full
+      // chunk: at most one each per thread, coalesced
+      iterate_scalar<M, Real, Col>(P, E, ev, n, first, h, acc, (int)gsz);
+      iterate_scalar<M, Real, Col>(P, E, ev, n, h + nfull * EPT + first, n, acc, (int)gsz);
     }
   }
 

@@ -445,7 +445,7 @@ __device__ __forceinline__ void toy_segment_body_reg(const RfProgram& P,
         h = (int64_t)(((16u - (a & 15u)) & 15u) / sizeof(Col));
         if (h > q - p) h = q - p;
       }
-      const int64_t nfull = (q - p - h) / EPT;
+      const int64_t nfull = full_chunks<EPT>(q - p - h, vec != 0);
       // the chunk loop without the per-event zero-coefficient test (with it,
       // the 4096 Gauss + Exponential toys ran 43.8 instructions per event,
       // without it 37.7, at 8 events per lane)

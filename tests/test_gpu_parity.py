@@ -156,10 +156,12 @@ def test_shape_sweep(rf, n, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n,shift", [(4001, 0), (4000, 1), (4003, 3), (4004, 2), (2, 1)])
+@pytest.mark.parametrize("n,shift", [(4001, 0), (4000, 1), (4003, 3), (4004, 2), (2, 1),
+                                     (200_003, 1)])
 def test_unaligned_columns(rf, n, shift, prec):
     """Column bases off the 16-byte grid (a sliced buffer) and column phases
-    that differ between observables (n not a multiple of 4)."""
+    that differ between observables (n not a multiple of 4): the lane-
+    interleaved 32-bit loads, their tail, and (200,003 events) many blocks."""
     w = datagen.c3(n=n)
     p = OFF_MIN["c3"][:7] + [float(n)]
     v, g, sc, rc = oracle.nll_scaled(w["spec"], p, w["cols"].astype(np.float64))
