@@ -15,7 +15,8 @@ A model is the plain-data ``spec`` dict used throughout the repository::
 
 Leaf parameter order: gauss (mu, sigma); exp (lambda); cheb (c_1..c_m);
 cb (m0, sigma, alpha, n); argus (m0, c, p); johnson (mu, lambda, gamma,
-delta); formula (p0 .. p(m-1) of the node's "formula" text in x).
+delta); formula (p0 .. p(m-1) of the node's "formula" text in x); hypatia2
+(lambda, zeta, beta, sigma, mu, a, n, a2, n2).
 """
 from __future__ import annotations
 
@@ -32,8 +33,8 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "rf_oracle.c")
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5, "johnson": 9,
-         "formula": 10, "add_frac": 6, "add_ext": 7, "prod": 8}
-MAXCH, MAXNP, MAXPAR = 8, 8, 64
+         "formula": 10, "hypatia2": 11, "add_frac": 6, "add_ext": 7, "prod": 8}
+MAXCH, MAXNP, MAXPAR = 8, 12, 64
 OK, EINVAL, EUNSUPPORTED, EDOMAIN = 0, 1, 2, 3
 
 _lock = threading.Lock()
@@ -95,6 +96,7 @@ def lib():
             i64p = C.POINTER(C.c_int64)
             L.orc_generate.argtypes = [C.POINTER(_Model), dp, C.c_int32, i64p, i64p, C.c_uint64,
                                        C.c_int, dp, C.c_int64, i64p]
+            L.orc_besselk.argtypes = [C.c_double, C.c_double, dp]
             L.orc_expr_check.argtypes = [C.c_char_p, C.c_int]
             L.orc_expr_logf.argtypes = [C.c_char_p, dp, C.c_int, C.c_double, dp, dp]
             L.orc_expr_norm.argtypes = [C.c_char_p, dp, C.c_int, C.c_double, C.c_double, dp,
@@ -257,6 +259,14 @@ def philox4x64(counter, key):
     o = (C.c_uint64 * 4)()
     lib().orc_philox4x64(c, k, o)
     return [int(x) for x in o]
+
+
+def besselk(nu: float, z: float):
+    """(K_nu(z), dK/dz, dK/dnu, return code) from the oracle's quadrature of
+    the integral representation."""
+    out = np.zeros(3)
+    rc = lib().orc_besselk(float(nu), float(z), _dp(out))
+    return float(out[0]), float(out[1]), float(out[2]), rc
 
 
 def erfcinv(q: float) -> float:

@@ -587,6 +587,225 @@ static void argus_fn(double x, const void* ctx, int m, double* v) {
   v[2] = f * log(tau);
 }
 
+/* ------------------------------------------------------------------ */
+/* Bessel K of real order and the Hypatia2 leaf (ORC_HYPATIA2)         */
+/* ------------------------------------------------------------------ */
+/* K_nu(z) = int_0^inf e^{-z cosh t} cosh(nu t) dt (z > 0), in the scaled form
+ * e^z K_nu(z) = int_0^inf phi(t) cosh(nu t) dt, phi = e^{-z (cosh t - 1)}.
+ * bk_sums integrates, over [0, T], with the adaptive Gauss-Legendre rule:
+ *   S0 = int phi cosh(nu t)            = e^z K
+ *   S1 = -int cosh t phi cosh(nu t)    = e^z dK/dz
+ *   S2 = int t phi sinh(nu t)          = e^z dK/dnu
+ *   S3 = int cosh^2 t phi cosh(nu t)   = e^z d2K/dz2
+ *   S4 = -int t cosh t phi sinh(nu t)  = e^z d2K/dz dnu
+ * T lies past the integrand's peak t* = asinh(|nu|/z) where the largest
+ * moment has fallen by e^-46 from its value at t*. */
+typedef struct {
+  double nu, z;
+} bk_ctx;
+
+static void bk_fn(double t, const void* ctx, int m, double* v) {
+  const bk_ctx* b = (const bk_ctx*)ctx;
+  (void)m;
+  double ch = cosh(t), ph = exp(-b->z * (ch - 1.0));
+  double cn = cosh(b->nu * t), sn = sinh(b->nu * t);
+  v[0] = ph * cn;
+  v[1] = -ch * ph * cn;
+  v[2] = t * ph * sn;
+  v[3] = ch * ch * ph * cn;
+  v[4] = -t * ch * ph * sn;
+}
+
+static int bk_sums(double nu, double z, double* S) {
+  if (!(z > 0.0) || !isfinite(z) || !isfinite(nu)) return ORC_EDOMAIN;
+  double an = fabs(nu), tp = asinh(an / z);
+  /* log of the largest moment's integrand, up to constants */
+  double gpk = -z * (cosh(tp) - 1.0) + an * tp + 2.0 * tp + log(tp + 1.0);
+  double T = tp + 0.5, step = 0.5;
+  for (int it = 0; it < 400; ++it) {
+    double g = -z * (cosh(T) - 1.0) + an * T + 2.0 * T + log(T + 1.0);
+    if (g < gpk - 46.0) break;
+    T += step;
+  }
+  bk_ctx c = {nu, z};
+  int bad = quad(bk_fn, &c, 4, 0.0, T, S);
+  return bad || !(S[0] > 0.0) ? ORC_EDOMAIN : ORC_OK;
+}
+
+int orc_besselk(double nu, double z, double* out) {
+  double S[5];
+  int rc = bk_sums(nu, z, S);
+  if (rc) return rc;
+  double ez = exp(-z);
+  out[0] = S[0] * ez;
+  out[1] = S[1] * ez;
+  out[2] = S[2] * ez;
+  return ORC_OK;
+}
+
+/* forward-mode dual numbers over the nine Hypatia2 parameters */
+#define ORC_HNP 9
+typedef struct {
+  double v, d[ORC_HNP];
+} hd;
+
+static hd hd_c(double v) {
+  hd r;
+  r.v = v;
+  for (int j = 0; j < ORC_HNP; ++j) r.d[j] = 0.0;
+  return r;
+}
+static hd hd_var(double v, int k) {
+  hd r = hd_c(v);
+  r.d[k] = 1.0;
+  return r;
+}
+static hd hd_add(hd a, hd b) {
+  for (int j = 0; j < ORC_HNP; ++j) a.d[j] += b.d[j];
+  a.v += b.v;
+  return a;
+}
+static hd hd_sub(hd a, hd b) {
+  for (int j = 0; j < ORC_HNP; ++j) a.d[j] -= b.d[j];
+  a.v -= b.v;
+  return a;
+}
+static hd hd_mul(hd a, hd b) {
+  hd r;
+  r.v = a.v * b.v;
+  for (int j = 0; j < ORC_HNP; ++j) r.d[j] = a.d[j] * b.v + a.v * b.d[j];
+  return r;
+}
+static hd hd_div(hd a, hd b) {
+  hd r;
+  r.v = a.v / b.v;
+  for (int j = 0; j < ORC_HNP; ++j) r.d[j] = (a.d[j] - r.v * b.d[j]) / b.v;
+  return r;
+}
+static hd hd_scale(hd a, double s) {
+  a.v *= s;
+  for (int j = 0; j < ORC_HNP; ++j) a.d[j] *= s;
+  return a;
+}
+static hd hd_shift(hd a, double s) {
+  a.v += s;
+  return a;
+}
+/* f(a) from its value fv and slope fs at a.v */
+static hd hd_chain(hd a, double fv, double fs) {
+  hd r;
+  r.v = fv;
+  for (int j = 0; j < ORC_HNP; ++j) r.d[j] = fs * a.d[j];
+  return r;
+}
+static hd hd_log(hd a) { return hd_chain(a, log(a.v), 1.0 / a.v); }
+static hd hd_exp(hd a) {
+  double e = exp(a.v);
+  return hd_chain(a, e, e);
+}
+static hd hd_sqrt(hd a) {
+  double s = sqrt(a.v);
+  return hd_chain(a, s, 0.5 / s);
+}
+/* log K_nu(z) and d log K_nu(z)/dz, each with its derivatives through nu, z */
+static hd hd_logK(hd nu, hd z, int* rc) {
+  double S[5];
+  if (bk_sums(nu.v, z.v, S)) {
+    *rc = ORC_EDOMAIN;
+    return hd_c(NAN);
+  }
+  hd r;
+  r.v = log(S[0]) - z.v;
+  for (int j = 0; j < ORC_HNP; ++j) r.d[j] = S[2] / S[0] * nu.d[j] + S[1] / S[0] * z.d[j];
+  return r;
+}
+static hd hd_dlogK(hd nu, hd z, int* rc) {
+  double S[5];
+  if (bk_sums(nu.v, z.v, S)) {
+    *rc = ORC_EDOMAIN;
+    return hd_c(NAN);
+  }
+  const double q1 = S[1] / S[0], q2 = S[2] / S[0];
+  hd r;
+  r.v = q1;
+  for (int j = 0; j < ORC_HNP; ++j)
+    r.d[j] = (S[4] / S[0] - q1 * q2) * nu.d[j] + (S[3] / S[0] - q1 * q1) * z.d[j];
+  return r;
+}
+
+/* Hypatia2 (a reading: the paper names the PDF only).  With d = x - mu,
+ * phi = K_{lambda+1}(zeta) / K_lambda(zeta), delta = sigma sqrt(zeta / phi),
+ * alpha = sqrt(zeta phi) / sigma (alpha delta = zeta; beta enters through
+ * e^{beta d} only) and nu = lambda - 1/2, the core is the generalised
+ * hyperbolic density up to a constant factor:
+ *   L(d) = (nu/2) log(d^2 + delta^2) + beta d + log K_nu(alpha sqrt(d^2 + delta^2)) + zeta
+ * (the constant zeta keeps e^L of order one near the peak).  Below
+ * d_L = -a sigma and above d_R = a2 sigma, power-law tails continue it with
+ * the same value and slope k = dL/dd at the junction:
+ *   L = L(d_J) - m log(1 - (d - d_J) k(d_J) / m),  (d_J, m) = (d_L, n) or (d_R, n2).
+ * k(d) = nu d / (d^2 + delta^2) + beta + alpha (d / r) (d log K_nu / dz)(alpha r).
+ * Returns log f and its derivatives with respect to the nine parameters;
+ * log f = -inf where a tail's base is not positive. */
+static hd hyp2_core(hd d, hd nu, hd beta, hd alpha, hd delta2, hd zeta, hd* slope, int* rc) {
+  hd q = hd_add(hd_mul(d, d), delta2), r = hd_sqrt(q), z = hd_mul(alpha, r);
+  hd L = hd_add(hd_add(hd_scale(hd_mul(nu, hd_log(q)), 0.5), hd_mul(beta, d)),
+                hd_add(hd_logK(nu, z, rc), zeta));
+  if (slope)
+    *slope = hd_add(hd_add(hd_div(hd_mul(nu, d), q), beta),
+                    hd_mul(hd_div(hd_mul(alpha, d), r), hd_dlogK(nu, z, rc)));
+  return L;
+}
+
+static int hyp2_logf(const double* th, double x, double* logf, double* dlogf) {
+  hd lam = hd_var(th[0], 0), zeta = hd_var(th[1], 1), beta = hd_var(th[2], 2);
+  hd sigma = hd_var(th[3], 3), mu = hd_var(th[4], 4), a = hd_var(th[5], 5);
+  hd n = hd_var(th[6], 6), a2 = hd_var(th[7], 7), n2 = hd_var(th[8], 8);
+  if (!(th[1] > 0.0) || !(th[3] > 0.0) || !(th[5] > 0.0) || !(th[6] > 0.0) ||
+      !(th[7] > 0.0) || !(th[8] > 0.0))
+    return ORC_EDOMAIN;
+  int rc = ORC_OK;
+  hd logphi = hd_sub(hd_logK(hd_shift(lam, 1.0), zeta, &rc), hd_logK(lam, zeta, &rc));
+  hd logz = hd_log(zeta), logs = hd_log(sigma);
+  hd delta2 = hd_exp(hd_add(hd_scale(logs, 2.0), hd_sub(logz, logphi)));
+  hd alpha = hd_exp(hd_sub(hd_scale(hd_add(logz, logphi), 0.5), logs));
+  hd nu = hd_shift(lam, -0.5);
+  hd d = hd_sub(hd_c(x), mu);
+  hd dL = hd_scale(hd_mul(a, sigma), -1.0), dR = hd_mul(a2, sigma);
+  hd L;
+  if (d.v < dL.v || d.v > dR.v) {
+    const int left = d.v < dL.v;
+    hd dJ = left ? dL : dR, m = left ? n : n2, k;
+    hd LJ = hyp2_core(dJ, nu, beta, alpha, delta2, zeta, &k, &rc);
+    hd base = hd_sub(hd_c(1.0), hd_div(hd_mul(hd_sub(d, dJ), k), m));
+    if (!(base.v > 0.0)) {
+      *logf = -INFINITY;
+      for (int j = 0; j < ORC_HNP; ++j) dlogf[j] = 0.0;
+      return rc;
+    }
+    L = hd_sub(LJ, hd_mul(m, hd_log(base)));
+  } else {
+    L = hyp2_core(d, nu, beta, alpha, delta2, zeta, NULL, &rc);
+  }
+  *logf = L.v;
+  for (int j = 0; j < ORC_HNP; ++j) dlogf[j] = L.d[j];
+  return rc;
+}
+
+/* integrand of the normalisation: v[0] = f, v[1 + j] = df/dtheta_j */
+typedef struct {
+  const double* th;
+  int bad;
+} hyp2_ctx;
+
+static void hyp2_fn(double x, const void* ctx, int m, double* v) {
+  hyp2_ctx* c = (hyp2_ctx*)ctx;
+  double lf, dl[ORC_HNP];
+  if (hyp2_logf(c->th, x, &lf, dl)) c->bad = 1;
+  double f = exp(lf);
+  v[0] = f;
+  for (int j = 0; j < m; ++j) v[1 + j] = f == 0.0 ? 0.0 : f * dl[j];
+}
+
 int orc_expr_check(const char* text, int npar) {
   xprog* p = (xprog*)malloc(sizeof(xprog));
   if (!p) return ORC_EINVAL;
@@ -631,6 +850,14 @@ static int leaf_value(int type, const double* th, int nth, double lo, double hi,
                       double x, const xprog* xp, double* f_out, double* dlogf) {
   for (int j = 0; j < nth; ++j) dlogf[j] = 0.0;
   switch (type) {
+    case ORC_HYPATIA2: {
+      if (nth != 9) return ORC_EINVAL;
+      double lf;
+      int rc = hyp2_logf(th, x, &lf, dlogf);
+      if (rc) return rc;
+      *f_out = exp(lf);
+      return ORC_OK;
+    }
     case ORC_EXPR: {
       if (!xp) return ORC_EINVAL;
       double dv[ORC_MAXNP];
@@ -767,6 +994,27 @@ static int leaf_norm(int type, const double* th, int nth, double lo, double hi,
     case ORC_EXPR:
       if (!xp) return ORC_EINVAL;
       return xnorm(xp, th, nth, lo, hi, I_out, dI);
+    case ORC_HYPATIA2: {
+      /* no closed form: adaptive quadrature of f and its derivatives, on
+       * the pieces between the tail junctions mu - a sigma, mu + a2 sigma
+       * (the second derivative jumps there) */
+      if (nth != 9) return ORC_EINVAL;
+      hyp2_ctx c = {th, 0};
+      double cut[4] = {lo, th[4] - th[5] * th[3], th[4] + th[7] * th[3], hi};
+      int bad = 0;
+      *I_out = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double a = cut[k] < lo ? lo : (cut[k] > hi ? hi : cut[k]);
+        double b = cut[k + 1] < lo ? lo : (cut[k + 1] > hi ? hi : cut[k + 1]);
+        if (!(b > a)) continue;
+        double acc[1 + ORC_MAXNP];
+        bad |= quad(hyp2_fn, &c, 9, a, b, acc);
+        *I_out += acc[0];
+        for (int j = 0; j < 9; ++j) dI[j] += acc[1 + j];
+      }
+      if (bad || c.bad || !isfinite(*I_out) || !(*I_out > 0.0)) return ORC_EDOMAIN;
+      return ORC_OK;
+    }
     case ORC_GAUSS: {
       if (nth != 2) return ORC_EINVAL;
       double mu = th[0], sigma = th[1];
@@ -948,7 +1196,8 @@ int orc_leaf_norm(int type, const double* theta, int ntheta, double lo,
 /* ------------------------------------------------------------------ */
 
 static int is_leaf(int t) {
-  return (t >= ORC_GAUSS && t <= ORC_ARGUS) || t == ORC_JOHNSON || t == ORC_EXPR;
+  return (t >= ORC_GAUSS && t <= ORC_ARGUS) || t == ORC_JOHNSON || t == ORC_EXPR ||
+         t == ORC_HYPATIA2;
 }
 
 #define ORC_MAXXL 4 /* expression leaves per model */
@@ -984,7 +1233,7 @@ static int validate(const orc_model* m) {
   if (m->n_par < 0 || m->n_par > ORC_MAXPAR) return ORC_EINVAL;
   for (int i = 0; i < m->n_nodes; ++i) {
     int t = m->type[i];
-    if (t < ORC_GAUSS || t > ORC_EXPR) return ORC_EINVAL;
+    if (t < ORC_GAUSS || t > ORC_HYPATIA2) return ORC_EINVAL;
     if (t == ORC_EXPR && !(m->expr && m->expr[i])) return ORC_EINVAL;
     if (m->npar[i] < 0 || m->npar[i] > ORC_MAXNP) return ORC_EINVAL;
     for (int j = 0; j < m->npar[i]; ++j) {
@@ -1491,7 +1740,8 @@ int orc_generate(const orc_model* m, const double* params_matrix, int32_t toys,
     nlv[c] = comp_leaves(m, comps[c], lv[c]);
     if (nlv[c] < 0) return ORC_EUNSUPPORTED;
     for (int k = 0; k < nlv[c]; ++k)
-      if (m->type[lv[c][k]] == ORC_EXPR) return ORC_EUNSUPPORTED; /* no sampler */
+      if (m->type[lv[c][k]] == ORC_EXPR || m->type[lv[c][k]] == ORC_HYPATIA2)
+        return ORC_EUNSUPPORTED; /* no sampler */
     int64_t cover = 0;
     for (int k = 0; k < nlv[c]; ++k) cover |= (int64_t)1 << m->obs[lv[c][k]];
     if (cover != ((int64_t)1 << m->n_obs) - 1) return ORC_EUNSUPPORTED;

@@ -40,11 +40,13 @@ enum {
   ORC_ADD_EXT = 7,  /* K children, K yield params; root only   */
   ORC_PROD = 8,     /* K children on disjoint observables      */
   ORC_JOHNSON = 9,  /* params (mu, lambda, gamma, delta): Johnson's SU */
-  ORC_EXPR = 10     /* params p0 .. p(m-1) of a formula f(x; p) given as text */
+  ORC_EXPR = 10,    /* params p0 .. p(m-1) of a formula f(x; p) given as text */
+  ORC_HYPATIA2 = 11 /* params (lambda, zeta, beta, sigma, mu, a, n, a2, n2):
+                       a generalised hyperbolic core with power-law tails */
 };
 
 #define ORC_MAXCH 8   /* children per node   */
-#define ORC_MAXNP 8   /* params per node     */
+#define ORC_MAXNP 12  /* params per node     */
 #define ORC_MAXPAR 64 /* params per model    */
 #define ORC_MAXNODE 32
 
@@ -95,6 +97,12 @@ int orc_expr_logf(const char* text, const double* theta, int ntheta, double x,
                   double* logf, double* dlogf);
 int orc_expr_norm(const char* text, const double* theta, int ntheta, double lo,
                   double hi, double* I, double* dI);
+
+/* Modified Bessel function of the second kind of real order nu, z > 0, from
+ * its integral representation K_nu(z) = int_0^inf e^{-z cosh t} cosh(nu t) dt
+ * (adaptive Gauss-Legendre quadrature): out[0] = K_nu(z), out[1] = dK/dz,
+ * out[2] = dK/dnu. */
+int orc_besselk(double nu, double z, double* out);
 
 /* NLL = -sum_i log P(x_i)  (+ sum_k nu_k for an extended root) and, if grad is
  * not NULL, dNLL/dtheta for every parameter.  cols: observable j of event i at
