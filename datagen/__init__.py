@@ -31,7 +31,7 @@ import numpy as np
 
 CHUNK = 1 << 20
 SEEDS = {"c1": 12875001, "c2": 12875002, "c3": 12875003, "c4": 12875004,
-         "c5": 12875005, "johnson": 12875006, "prod6": 12875007}
+         "c5": 12875005, "johnson": 12875006, "prod6": 12875007, "hypatia2": 12875008}
 
 
 def rng(seed: int, chunk: int = 0) -> np.random.Generator:
@@ -326,6 +326,36 @@ def prod6(n=60_000, seed=SEEDS["prod6"], dtype=np.float32):
     cols = np.stack([x[perm], y[perm]])
     return {"name": "prod6_frac_f32", "spec": prod6_spec(), "cols": np.ascontiguousarray(cols),
             "dtype": "f32" if dtype == np.float32 else "f64"}
+
+
+def hypatia2_exp_spec(nu_s=2e4, nu_b=3e4):
+    """Extended Hypatia2 (lambda, zeta, beta, sigma, mu, a, n, a2, n2) +
+    Exponential on [0, 10]."""
+    return {"obs": [(0.0, 10.0)],
+            "params": [-1.5, 1.2, 0.1, 0.5, 5.0, 2.0, 3.0, 2.5, 4.0, -0.2,
+                       float(nu_s), float(nu_b)],
+            "fixed": [False] * 12,
+            "nodes": [{"type": "hypatia2", "obs": 0, "params": list(range(9))},
+                      {"type": "exp", "obs": 0, "params": [9]},
+                      {"type": "add_ext", "children": [0, 1], "params": [10, 11]}],
+            "root": 2}
+
+
+def hypatia2_exp(n_sig=20_000, n_bkg=30_000, seed=SEEDS["hypatia2"], dtype=np.float32):
+    """Signal from the generalised hyperbolic density that is Hypatia2's core
+    (scipy's sampler; the tails are not imposed), kept inside [0, 10], plus
+    Exp(-0.2) background, shuffled."""
+    import scipy.special as sps
+    import scipy.stats as sst
+    lam, zeta, beta, sigma, mu = -1.5, 1.2, 0.1, 0.5, 5.0
+    delta = sigma * np.sqrt(zeta * sps.kv(lam, zeta) / sps.kv(lam + 1, zeta))
+    d = sst.genhyperbolic(lam, zeta, beta * delta, loc=mu, scale=delta)
+    r = rng(seed, 0)
+    sig = _fill(r, n_sig, lambda r, k: d.rvs(size=k, random_state=r), dtype, 0.0, 10.0)
+    ev = np.concatenate([sig, expo(r, n_bkg, -0.2, 0.0, 10.0, dtype)])
+    r.shuffle(ev)
+    return {"name": "hypatia2_exp_ext", "spec": hypatia2_exp_spec(n_sig, n_bkg),
+            "cols": ev.reshape(1, -1), "dtype": "f32" if dtype == np.float32 else "f64"}
 
 
 def _chunked(n, seed, draw, ncols=1, dtype=np.float64):

@@ -30,6 +30,22 @@
  *   RF_JOHNSON (mu, lambda, gamma, delta)  Johnson's SU (Sec. 3): with
  *             z = (x-mu)/lambda, w = gamma + delta asinh z standard normal:
  *             delta / (lambda sqrt(2 pi (1+z^2))) exp(-w^2/2)
+ *   RF_HYPATIA2 (lambda, zeta, beta, sigma, mu, a, n, a2, n2)  Hypatia2
+ *             (Sec. 3): with d = x - mu, phi = K_{lambda+1}(zeta)/K_lambda(zeta),
+ *             delta = sigma sqrt(zeta/phi), alpha = sqrt(zeta phi)/sigma, a
+ *             generalised hyperbolic core
+ *               (d^2 + delta^2)^((lambda - 1/2)/2) e^{beta d}
+ *               K_{lambda-1/2}(alpha sqrt(d^2 + delta^2))
+ *             for -a sigma <= d <= a2 sigma and power-law tails beyond,
+ *             f(d_J) (1 - (d - d_J) k_J / m)^-m with the core's value and
+ *             logarithmic slope k_J at the junction d_J (m = n below, n2
+ *             above).  K_nu of real order by the trapezoid rule on its
+ *             integral representation; the integral over the range and its
+ *             derivatives numerically in FP64 (as for formula leaves, the
+ *             panels split at the junctions); zeta, sigma, a, n, a2, n2 must
+ *             be positive.  Takes three of the graph's six leaf slots;
+ *             specialised kernels only, no toy studies, generation, plain
+ *             baseline or rf_nll_noalloc (RF_EUNSUPPORTED)
  *   RF_FORMULA (p0 .. p(m-1)), m <= 4   a density written as text in the
  *             observable x and the node's parameters p0..p3 -- the formula
  *             PDFs of Sec. 4 (RooGenericPdf, compiled just in time).  Grammar:
@@ -113,7 +129,8 @@ enum {
   RF_ADD_EXT = 7,
   RF_PROD = 8,
   RF_JOHNSON = 9,
-  RF_FORMULA = 10
+  RF_FORMULA = 10,
+  RF_HYPATIA2 = 11
 };
 
 enum { RF_F32 = 0, RF_F64 = 1 };           /* column dtype              */
@@ -132,12 +149,12 @@ enum {
 };
 
 #define RF_MAX_CHILDREN 8
-#define RF_MAX_NODE_PARAMS 8
+#define RF_MAX_NODE_PARAMS 12
 #define RF_MAX_NODES 32
 #define RF_MAX_PARAMS 64
 
 typedef struct {
-  int32_t type;     /* RF_GAUSS .. RF_FORMULA                                */
+  int32_t type;     /* RF_GAUSS .. RF_HYPATIA2                               */
   int32_t obs;      /* leaves: observable (column) index; composites: -1     */
   int32_t n_children;
   int32_t children[RF_MAX_CHILDREN]; /* node indices                        */

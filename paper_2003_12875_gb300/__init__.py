@@ -31,10 +31,10 @@ __all__ = ["Graph", "RFNll", "RFError", "load", "microbench", "TYPES", "shard_ra
            "sharded_nll", "rank_order_sum"]
 
 TYPES = {"gauss": 1, "exp": 2, "cheb": 3, "cb": 4, "argus": 5,
-         "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9, "formula": 10}
+         "add_frac": 6, "add_ext": 7, "prod": 8, "johnson": 9, "formula": 10, "hypatia2": 11}
 _STATUS = {0: "RF_OK", 1: "RF_EINVAL", 2: "RF_EUNSUPPORTED", 3: "RF_EALIGN",
            4: "RF_ECUDA", 5: "RF_ENOMEM"}
-MAX_CHILDREN, MAX_NODE_PARAMS = 8, 8
+MAX_CHILDREN, MAX_NODE_PARAMS = 8, 12
 STATUS_PARAM_DOMAIN, STATUS_NONFINITE = 1, 2
 TUNE_NO_CACHE, TUNE_REFRESH = 1, 2
 

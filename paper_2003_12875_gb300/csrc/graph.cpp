@@ -40,8 +40,12 @@ rf_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 bool is_leaf(int t) {
-  return (t >= RF_GAUSS && t <= RF_ARGUS) || t == RF_JOHNSON || t == RF_FORMULA;
+  return (t >= RF_GAUSS && t <= RF_ARGUS) || t == RF_JOHNSON || t == RF_FORMULA ||
+         t == RF_HYPATIA2;
 }
+
+// leaf slots a leaf takes in the compiled program (four parameters a slot)
+int leaf_slots(int t) { return t == RF_HYPATIA2 ? 3 : 1; }
 
 int leaf_nparams_ok(int t, int np) {
   switch (t) {
@@ -52,6 +56,7 @@ int leaf_nparams_ok(int t, int np) {
     case RF_ARGUS: return np == 3;
     case RF_JOHNSON: return np == 4;
     case RF_FORMULA: return np >= 0 && np <= RF_LEAF_MAXP;
+    case RF_HYPATIA2: return np == 9;
   }
   return 0;
 }
@@ -76,7 +81,7 @@ rf_status validate_desc(const rf_graph_desc* d) {
       return fail(RF_EINVAL, "observable " + std::to_string(o) + " has an empty or non-finite range");
   for (int i = 0; i < d->n_nodes; ++i) {
     const rf_node_desc& n = d->nodes[i];
-    if (n.type < RF_GAUSS || n.type > RF_FORMULA)
+    if (n.type < RF_GAUSS || n.type > RF_HYPATIA2)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": unknown type");
     if (n.n_params < 0 || n.n_params > RF_MAX_NODE_PARAMS)
       return fail(RF_EINVAL, "node " + std::to_string(i) + ": bad n_params");
@@ -158,7 +163,8 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
       for (int j = 0; j < root.n_params; ++j) P->coef_par[j] = root.params[j];
   }
   int nl = 0;
-  for (int c = 0; c < n_comps; ++c) nl += comp_n[c];
+  for (int c = 0; c < n_comps; ++c)
+    for (int li = 0; li < comp_n[c]; ++li) nl += leaf_slots(d->nodes[comp_leaf[c][li]].type);
   if (n_comps > RF_MAXC) return fail(RF_EUNSUPPORTED, "more than 6 components");
   if (nl > RF_MAXL) return fail(RF_EUNSUPPORTED, "more than 6 leaves");
   P->n_leaves = nl;
@@ -204,7 +210,7 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
       }
       L.col = slot;
       int gm = 0;
-      for (int j = 0; j < n.n_params; ++j)
+      for (int j = 0; j < n.n_params && j < RF_LEAF_MAXP; ++j)
         if (!fixed(n.params[j])) gm |= 1 << j;
       // ARGUS: a free p selects the general-p form (d/dp included); so does
       // a fixed p whose compile-time value is not 1/2 (without d/dp);
@@ -213,6 +219,28 @@ rf_status canonicalise(const rf_graph_desc* d, RfProgram* P, int* leaf_node = nu
           d->param_values[n.params[2]] != 0.5)
         gm |= RF_ARGUS_GENERAL;
       L.gmask = gm;
+      if (n.type == RF_HYPATIA2) {
+        L.npar = RF_LEAF_MAXP;
+        // its parameters 4.. in the next slots: same component and column,
+        // no per-event work of their own
+        for (int part = 1; part < leaf_slots(n.type); ++part) {
+          if (leaf_node) leaf_node[k] = comp_leaf[c][li];
+          RfLeafProg& X = P->leaf[k++];
+          X = L;
+          X.type = RFL_PARAMS;
+          X.part = part;
+          X.npar = 0;
+          X.gmask = 0;
+          for (int j = 0; j < RF_LEAF_MAXP; ++j) {
+            const int q = RF_LEAF_MAXP * part + j;
+            X.par[j] = q < n.n_params ? n.params[q] : 0;
+            if (q < n.n_params) {
+              X.npar = j + 1;
+              if (!fixed(n.params[q])) X.gmask |= 1 << j;
+            }
+          }
+        }
+      }
     }
   }
   P->n_cols = n_cols;
@@ -379,8 +407,9 @@ rf_status rf_canonical_program(const rf_graph_desc* desc, RfProgram* P) {
   s = canonicalise(desc, P);
   if (s) return s;
   for (int k = 0; k < P->n_leaves; ++k)
-    if (P->leaf[k].type == RFL_FORMULA)
-      return fail(RF_EUNSUPPORTED, "formula leaves need rf_graph_compile (specialised kernels)");
+    if (P->leaf[k].type == RFL_FORMULA || P->leaf[k].type == RFL_HYPATIA2)
+      return fail(RF_EUNSUPPORTED,
+                  "formula and Hypatia2 leaves need rf_graph_compile (specialised kernels)");
   if (P->n_leaves > RF_GENERIC_MAXL)
     return fail(RF_EUNSUPPORTED, "more than 4 leaves need rf_graph_compile (specialised kernels)");
   return RF_OK;
@@ -407,17 +436,20 @@ rf_status rf_graph_compile(const rf_graph_desc* desc, rf_graph** out) {
   rf_status s = validate_desc(desc);
   if (s) return s;
   rf_graph* g = new rf_graph();
-  int leaf_node[RF_MAXL] = {0, 0, 0, 0};
+  int leaf_node[RF_MAXL] = {0};
   s = canonicalise(desc, &g->prog, leaf_node);
   if (s) {
     delete g;
     return s;
   }
   for (int k = 0; k < g->prog.n_leaves; ++k) {
-    if (g->prog.leaf[k].type != RFL_FORMULA) continue;
-    const rf_node_desc& n = desc->nodes[leaf_node[k]];
-    std::string err;
-    rf_expr_translate(n.formula, n.n_params, &g->fcode.leaf[k], &err);  // validated above
+    const int t = g->prog.leaf[k].type;
+    if (t != RFL_FORMULA && t != RFL_HYPATIA2) continue;  // numerically normalised
+    if (t == RFL_FORMULA) {
+      const rf_node_desc& n = desc->nodes[leaf_node[k]];
+      std::string err;
+      rf_expr_translate(n.formula, n.n_params, &g->fcode.leaf[k], &err);  // validated above
+    }
     ++g->n_formula;
   }
   g->eval = desc->eval_precision;
@@ -547,7 +579,7 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
   rf_status s = validate_desc(desc);
   if (s) return s;
   RfProgram P;
-  int leaf_node[RF_MAXL] = {0, 0, 0, 0};
+  int leaf_node[RF_MAXL] = {0};
   s = canonicalise(desc, &P, leaf_node);
   if (s) return s;
   RfFormulaCode fc;
@@ -557,6 +589,8 @@ rf_status rf_jit_check(const rf_graph_desc* desc) {
     if (P.leaf[k].type == RFL_FORMULA) {
       const rf_node_desc& n = desc->nodes[leaf_node[k]];
       rf_expr_translate(n.formula, n.n_params, &fc.leaf[k], &err);
+      ++nf;
+    } else if (P.leaf[k].type == RFL_HYPATIA2) {
       ++nf;
     }
   const RfFormulaCode* fcp = nf ? &fc : nullptr;

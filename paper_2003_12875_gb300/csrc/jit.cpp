@@ -75,10 +75,45 @@ std::string cache_dir() {
 
 namespace {
 
+// leaves normalised numerically (formula and Hypatia2 leaves): they need the
+// device header of formula leaves and the normalisation kernel
 bool has_formula(const RfProgram& P) {
   for (int k = 0; k < P.n_leaves; ++k)
-    if (P.leaf[k].type == RFL_FORMULA) return true;
+    if (P.leaf[k].type == RFL_FORMULA || P.leaf[k].type == RFL_HYPATIA2) return true;
   return false;
+}
+
+// derivatives a leaf returns per event (Hypatia2: nine, over its slots)
+int leaf_nder(const RfLeafProg& L) { return L.type == RFL_HYPATIA2 ? 9 : RF_LEAF_MAXP; }
+
+// whether the derivative j of leaf k is wanted (j >= 4: the next slots')
+bool wants(const RfProgram& P, int k, int j) {
+  return (P.leaf[k + j / RF_LEAF_MAXP].gmask >> (j % RF_LEAF_MAXP)) & 1;
+}
+
+// the per-event call of leaf k in type R on constants `pc` (empty for a slot
+// that only holds parameters of the leaf before)
+std::string leaf_call(const RfProgram& P, int k, const char* R, const std::string& pc,
+                      const std::string& add) {
+  const RfLeafProg& L = P.leaf[k];
+  if (L.type == RFL_PARAMS) return std::string();
+  std::ostringstream o;
+  const std::string ks = std::to_string(k);
+  o << "    " << R << " u" << ks << ", g" << ks << "[" << leaf_nder(L) << "];\n    ";
+  if (L.type == RFL_FORMULA) {
+    o << "rf::formula_leaf<RfFormula" << ks << ", " << R << ", " << L.gmask << ">";
+  } else if (L.type == RFL_HYPATIA2) {
+    int gm9 = 0;
+    for (int j = 0; j < 9; ++j)
+      if (wants(P, k, j)) gm9 |= 1 << j;
+    o << "rf::hypatia2_leaf<" << R << ", " << gm9 << ">";
+  } else {
+    o << "rf::" << leaf_fn(L.type) << "<" << R << ", " << leaf_gm(L) << ">";
+  }
+  o << "(x[" << L.col << "], " << pc << ", u" << ks << ", g" << ks;
+  if (!add.empty()) o << ", " << add;
+  o << ");\n";
+  return o.str();
 }
 
 // One struct per formula leaf k: NP and eval<Real>(x, p) -> Dual<Real, NP'>
@@ -133,9 +168,11 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
          "  switch (blockIdx.y) {\n";
     int f = 0;
     for (int k = 0; k < NL; ++k)
-      if (P.leaf[k].type == RFL_FORMULA)
-        o << "    case " << f++ << ": rf::formula_norm_body<RfFormula" << k << ">(P, " << k
-          << ", params, kRfGlT, kRfGlW, part, ticket, P.formula_norm); break;\n";
+      if (P.leaf[k].type == RFL_FORMULA || P.leaf[k].type == RFL_HYPATIA2)
+        o << "    case " << f++ << ": rf::formula_norm_body<"
+          << (P.leaf[k].type == RFL_HYPATIA2 ? std::string("rf::Hypatia2Leaf")
+                                              : "RfFormula" + std::to_string(k))
+          << ">(P, " << k << ", params, kRfGlT, kRfGlW, part, ticket, P.formula_norm); break;\n";
     o << "  }\n}\n";
     return o.str();
   }
@@ -153,23 +190,18 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
   std::vector<int> first(NC, -1);
   for (int k = 0; k < NL; ++k)
     if (first[P.leaf[k].comp] < 0) first[P.leaf[k].comp] = k;
-  for (int k = 0; k < NL; ++k) {
-    const RfLeafProg& L = P.leaf[k];
-    o << "    Real u" << k << ", g" << k << "[4];\n    ";
-    if (L.type == RFL_FORMULA)
-      o << "rf::formula_leaf<RfFormula" << k << ", Real, " << L.gmask << ">";
-    else
-      o << "rf::" << leaf_fn(L.type) << "<Real, " << leaf_gm(L) << ">";
-    o << "(x[" << L.col << "], K.pc[" << k << "], u" << k << ", g" << k;
-    if (first[L.comp] == k) o << ", ANYZERO ? Real(-0.0) : K.delta[" << L.comp << "]";
-    o << ");\n";
-  }
+  for (int k = 0; k < NL; ++k)
+    o << leaf_call(P, k, "Real", "K.pc[" + std::to_string(k) + "]",
+                   first[P.leaf[k].comp] == k
+                       ? "ANYZERO ? Real(-0.0) : K.delta[" + std::to_string(P.leaf[k].comp) + "]"
+                       : std::string());
   o << "    Real v[" << NC << "], w[" << NC << "];\n";
   std::vector<std::string> usum(NC);
   for (int c = 0; c < NC; ++c) {
     std::string s;
     for (int k = 0; k < NL; ++k)
-      if (P.leaf[k].comp == c) s += (s.empty() ? "u" : " + u") + std::to_string(k);
+      if (P.leaf[k].comp == c && P.leaf[k].type != RFL_PARAMS)
+        s += (s.empty() ? "u" : " + u") + std::to_string(k);
     usum[c] = " + " + s;
     o << "    if constexpr (ANYZERO) v[" << c << "] = K.delta[" << c << "] + " << s << ";\n"
       << "    else v[" << c << "] = " << s << ";\n";
@@ -187,11 +219,13 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
         << ", K.delta_nc[" << c << "]" << usum[c] << ", ell, w[" << c << "]);\n";
     o << "    }\n";
   }
-  for (int k = 0; k < NL; ++k)
-    for (int j = 0; j < RF_LEAF_MAXP; ++j)
-      if ((P.leaf[k].gmask >> j) & 1)
+  for (int k = 0; k < NL; ++k) {
+    if (P.leaf[k].type == RFL_PARAMS) continue;
+    for (int j = 0; j < leaf_nder(P.leaf[k]); ++j)
+      if (wants(P, k, j))
         o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += w[" << P.leaf[k].comp << "] * g" << k
           << "[" << j << "];\n";
+  }
   o << "  }\n";
   // The same event in FP64 on the FP64 constants, for FP32 evaluation of a
   // call or toy with a coefficient exactly 0 (x: the column values in their
@@ -199,15 +233,8 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
   o << "  static __device__ __noinline__ double event_exact(const RfExact* __restrict__ Kp, "
        "const double* __restrict__ x, float* __restrict__ q) {\n"
        "    const RfExact& K = *Kp;\n";
-  for (int k = 0; k < NL; ++k) {
-    const RfLeafProg& L = P.leaf[k];
-    o << "    double u" << k << ", g" << k << "[4];\n    ";
-    if (L.type == RFL_FORMULA)
-      o << "rf::formula_leaf<RfFormula" << k << ", double, " << L.gmask << ">";
-    else
-      o << "rf::" << leaf_fn(L.type) << "<double, " << leaf_gm(L) << ">";
-    o << "(x[" << L.col << "], K.pcd[" << k << "], u" << k << ", g" << k << ");\n";
-  }
+  for (int k = 0; k < NL; ++k)
+    o << leaf_call(P, k, "double", "K.pcd[" + std::to_string(k) + "]", std::string());
   o << "    double v[" << NC << "], w[" << NC << "];\n";
   for (int c = 0; c < NC; ++c) o << "    v[" << c << "] = K.delta_d[" << c << "]" << usum[c] << ";\n";
   o << "    const double ell = rf::lse<double, " << NC << ">(v, w);\n    q[0] += (float)ell;\n";
@@ -218,11 +245,13 @@ std::string rf_jit_source(const RfProgram& P, const RfFormulaCode* fc, int eval,
       o << "    q[" << 1 + c << "] += (float)(((K.zero_mask >> " << c << ") & 1) ? exp2(K.delta_nc_d["
         << c << "]" << usum[c] << " - ell) : w[" << c << "]);\n";
   }
-  for (int k = 0; k < NL; ++k)
-    for (int j = 0; j < RF_LEAF_MAXP; ++j)
-      if ((P.leaf[k].gmask >> j) & 1)
+  for (int k = 0; k < NL; ++k) {
+    if (P.leaf[k].type == RFL_PARAMS) continue;
+    for (int j = 0; j < leaf_nder(P.leaf[k]); ++j)
+      if (wants(P, k, j))
         o << "    q[" << 1 + NL + k * RF_LEAF_MAXP + j << "] += (float)(w[" << P.leaf[k].comp
           << "] * g" << k << "[" << j << "]);\n";
+  }
   o << "    return ell;\n  }\n};\n";
   const char* R = eval ? "double" : "float";
   const char* C = coldt ? "double" : "float";

@@ -380,6 +380,8 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
       break;
     }
     case RFL_FORMULA:  // the formula runs on the parameters rounded to T
+    case RFL_HYPATIA2:
+    case RFL_PARAMS:
       for (int j = 0; j < L.npar; ++j) pc[j] = (T)th[j];
       break;
     case RFL_ARGUS: {
@@ -408,12 +410,22 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
   double dln[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
   bool ok;
-  if (L.type == RFL_FORMULA) {
+  if (L.type == RFL_FORMULA || L.type == RFL_HYPATIA2) {
     // log I and (dI/dp_j)/I from the normalisation kernel (NaN: I <= 0)
     const double* nrm = P.formula_norm + k * RF_FORMULA_NV;
     *lnI_out = nrm[0];
     for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
     ok = isfinite(*lnI_out);
+  } else if (L.type == RFL_PARAMS) {
+    // parameters 4 part .. of the leaf `part` slots before: their share of
+    // that leaf's (dI/dp_j)/I; the integral itself is counted there
+    const double* nrm = P.formula_norm + (k - L.part) * RF_FORMULA_NV;
+    *lnI_out = 0.0;
+    for (int j = 0; j < RF_LEAF_MAXP; ++j) {
+      const int q = RF_LEAF_MAXP * L.part + j;
+      dln[j] = q < RF_FORMULA_MAXP ? nrm[1 + q] : 0.0;
+    }
+    ok = true;
   } else {
     ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
   }
@@ -457,6 +469,8 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       K.gmul[k][2] = K.gmul[k][3] = -1.0;         // d u/d gamma = -w, d u/d delta = -w asinh z
       break;
     case RFL_FORMULA:  // first-order correction through dtheta, as for the built-ins
+    case RFL_HYPATIA2:
+    case RFL_PARAMS:
       for (int j = 0; j < L.npar; ++j) K.dtheta[k][j] = (double)pc[j] - th[j];
       break;
     case RFL_ARGUS:

@@ -283,6 +283,174 @@ __device__ __forceinline__ void formula_leaf(Real x, const Real* __restrict__ pc
     g[j] = (j < F::NP && ((GM >> j) & 1)) ? f.d[j < F::NP ? j : 0] * r : Real(0);
 }
 
+// ------------------------------------------------------------------ Hypatia2
+// Modified Bessel function of the second kind of real order from its integral
+// representation K_nu(z) = int_0^inf e^{-z cosh t} cosh(nu t) dt (z > 0), by
+// the trapezoid rule (exponentially convergent for this analytic, rapidly
+// decaying integrand; Trefethen & Weideman, SIAM Review 56 (2014) 385) on the
+// scaled integrand phi(t) = e^{-z (cosh t - 1)} with step h = 0.2/sqrt(max(1, z))
+// (the integrand's width shrinks as 1/sqrt(z)), summed until past the peak
+// t* = asinh(|nu|/z) the largest moment's term is below eps of the sum (FP64
+// 1e-17, FP32 1e-9).  cosh t - 1 = expm1(t)^2 / (2 e^t), without cancellation.
+// s0 = e^z K, s1 = e^z dK/dz, s2 = e^z dK/dnu, s3 = e^z d2K/dz2,
+// s4 = e^z d2K/dz dnu.
+template <typename R>
+struct BesselKSums {
+  R s0, s1, s2, s3, s4;
+};
+
+template <typename R>
+__device__ __noinline__ BesselKSums<R> besselk_sums(R nu, R z) {
+  const R h = R(0.2) / fx::sqrt(z > R(1) ? z : R(1));
+  const R an = fx::abs(nu), tp = fx::asinh(an / z);
+  const R eps = sizeof(R) == 4 ? R(1e-9) : R(1e-17);
+  // t = 0 carries half weight: phi = 1, cosh t = 1, cosh(nu t) = 1, sinh = 0
+  R s0 = R(0.5), s1 = R(-0.5), s2 = R(0), s3 = R(0.5), s4 = R(0);
+  for (int j = 1; j < 4000; ++j) {
+    const R t = R(j) * h;
+    const R em = expm1(t), et = em + R(1);
+    const R chm1 = em * em / (R(2) * et), ch = chm1 + R(1);
+    const R ph = fx::exp(-z * chm1);
+    const R en = fx::exp(an * t), ien = R(1) / en;
+    const R cn = R(0.5) * (en + ien), sn = copysign(R(0.5) * (en - ien), nu);
+    const R pcn = ph * cn, psn = ph * sn;
+    s0 += pcn;
+    s1 -= ch * pcn;
+    s2 += t * psn;
+    s3 += ch * ch * pcn;
+    s4 -= t * ch * psn;
+    if (t > tp && ch * ch * pcn <= eps * s0) break;
+  }
+  return BesselKSums<R>{h * s0, h * s1, h * s2, h * s3, h * s4};
+}
+
+// log K_nu(z) and d log K_nu / dz as duals, their derivatives through nu, z
+template <typename R, int N>
+__device__ __forceinline__ Dual<R, N> log_besselk(const Dual<R, N>& nu, const Dual<R, N>& z) {
+  const BesselKSums<R> S = besselk_sums(nu.v, z.v);
+  const R q1 = S.s1 / S.s0, q2 = S.s2 / S.s0;
+  Dual<R, N> r;
+  r.v = fx::log(S.s0) - z.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = q2 * nu.d[i] + q1 * z.d[i];
+  return r;
+}
+template <typename R, int N>
+__device__ __forceinline__ Dual<R, N> dlog_besselk(const Dual<R, N>& nu, const Dual<R, N>& z) {
+  const BesselKSums<R> S = besselk_sums(nu.v, z.v);
+  const R q1 = S.s1 / S.s0, q2 = S.s2 / S.s0;
+  Dual<R, N> r;
+  r.v = q1;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    r.d[i] = (S.s4 / S.s0 - q1 * q2) * nu.d[i] + (S.s3 / S.s0 - q1 * q1) * z.d[i];
+  return r;
+}
+
+// Hypatia2 (the paper names it among the improved PDFs; the form is a
+// reading): parameters p = (lambda, zeta, beta, sigma, mu, a, n, a2, n2).
+// With d = x - mu, phi = K_{lambda+1}(zeta)/K_lambda(zeta),
+// delta = sigma sqrt(zeta/phi), alpha = sqrt(zeta phi)/sigma, nu = lambda - 1/2:
+//   core  L(d) = (nu/2) log(d^2 + delta^2) + beta d + log K_nu(alpha r) + zeta,
+//         r = sqrt(d^2 + delta^2) (a generalised hyperbolic density up to a
+//         constant; + zeta keeps e^L of order one near the peak),
+//   tails below d_L = -a sigma and above d_R = a2 sigma:
+//         L(d_J) - m log(1 - (d - d_J) k(d_J)/m), (d_J, m) = (d_L, n) or (d_R, n2),
+//         k(d) = dL/dd = nu d/(d^2 + delta^2) + beta + alpha (d/r) dlogK/dz(alpha r),
+// so value and slope are continuous at both junctions.  log f = -inf where a
+// tail's base is not positive; NaN for parameters outside their domain.
+struct Hypatia2Leaf {
+  static constexpr int NP = 9;
+  template <typename R>
+  static __device__ __forceinline__ Dual<R, 9> core(const Dual<R, 9>& d, const Dual<R, 9>& nu,
+                                                    const Dual<R, 9>& beta,
+                                                    const Dual<R, 9>& alpha,
+                                                    const Dual<R, 9>& delta2, R zeta_v,
+                                                    const Dual<R, 9>& zeta, Dual<R, 9>* slope) {
+    (void)zeta_v;
+    const Dual<R, 9> q = d * d + delta2, r = fx::sqrt(q), z = alpha * r;
+    const Dual<R, 9> L = (R(0.5) * (nu * fx::log(q)) + beta * d) + (log_besselk(nu, z) + zeta);
+    if (slope) *slope = (nu * d / q + beta) + (alpha * d / r) * dlog_besselk(nu, z);
+    return L;
+  }
+  // log f and d log f / dp_j
+  template <typename R>
+  static __device__ __noinline__ Dual<R, 9> logf(R x, const R* __restrict__ p) {
+    using D = Dual<R, 9>;
+    const D lam = D::var(p[0], 0), zeta = D::var(p[1], 1), beta = D::var(p[2], 2);
+    const D sigma = D::var(p[3], 3), mu = D::var(p[4], 4), a = D::var(p[5], 5);
+    const D n = D::var(p[6], 6), a2 = D::var(p[7], 7), n2 = D::var(p[8], 8);
+    D out;
+    if (!(p[1] > R(0)) || !(p[3] > R(0)) || !(p[5] > R(0)) || !(p[6] > R(0)) ||
+        !(p[7] > R(0)) || !(p[8] > R(0))) {
+      out.v = R(0) / R(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) out.d[i] = R(0);
+      return out;
+    }
+    const D logphi = log_besselk(lam + R(1), zeta) - log_besselk(lam, zeta);
+    const D logz = fx::log(zeta), logs = fx::log(sigma);
+    const D delta2 = fx::exp(R(2) * logs + (logz - logphi));
+    const D alpha = fx::exp(R(0.5) * (logz + logphi) - logs);
+    const D nu = lam - R(0.5);
+    const D d = x - mu;
+    const D dL = -(a * sigma), dR = a2 * sigma;
+    if (d.v < dL.v || d.v > dR.v) {
+      const bool left = d.v < dL.v;
+      const D dJ = left ? dL : dR, m = left ? n : n2;
+      D k;
+      const D LJ = core<R>(dJ, nu, beta, alpha, delta2, p[1], zeta, &k);
+      const D base = R(1) - (d - dJ) * k / m;
+      if (!(base.v > R(0))) {
+        out.v = -R(1) / R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out.d[i] = R(0);
+        return out;
+      }
+      return LJ - m * fx::log(base);
+    }
+    return core<R>(d, nu, beta, alpha, delta2, p[1], zeta, nullptr);
+  }
+  // f and df/dp_j (for the normalisation kernel)
+  template <typename R>
+  static __device__ __forceinline__ Dual<R, 9> eval(R x, const R* __restrict__ p) {
+    const Dual<R, 9> L = logf<R>(x, p);
+    if (!(L.v > -R(1) / R(0))) {  // f = 0 (or NaN)
+      Dual<R, 9> z;
+      z.v = L.v == L.v ? R(0) : L.v;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) z.d[i] = R(0);
+      return z;
+    }
+    return fx::exp(L);
+  }
+  // the normalisation's pieces: [lo, mu - a sigma], [mu - a sigma,
+  // mu + a2 sigma], [mu + a2 sigma, hi], clipped to the range
+  static __device__ __forceinline__ int cuts(const double* p, double lo, double hi, double* c) {
+    c[0] = lo;
+    c[1] = fmin(fmax(p[4] - p[5] * p[3], lo), hi);
+    c[2] = fmin(fmax(p[4] + p[7] * p[3], lo), hi);
+    c[3] = hi;
+    return 3;
+  }
+};
+
+// The per-event Hypatia2 leaf: u = add + log2 f, g_j = d log f/dp_j for the
+// wanted j (GM9: bit j for parameter j).  Its nine parameters sit in three
+// consecutive leaf slots of the per-event constants (pc rows k, k+1, k+2:
+// p0..p3, p4..p7, p8).
+template <typename Real, int GM9>
+__device__ __forceinline__ void hypatia2_leaf(Real x, const Real* __restrict__ pc, Real& u,
+                                              Real (&g)[9], Real add = Real(-0.0)) {
+  Real p[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) p[j] = pc[(j >> 2) * RF_PC + (j & 3)];
+  const Dual<Real, 9> L = Hypatia2Leaf::logf<Real>(x, p);
+  u = L.v * Real(1.44269504088896340736) + add;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) g[j] = ((GM9 >> j) & 1) ? L.d[j] : Real(0);
+}
+
 // Normalisation of formula leaf k (FP64): composite 16-point Gauss-Legendre on
 // RF_FORMULA_PANELS equal panels, one node per thread, blocks of 128 threads,
 // gridDim.x = RF_FORMULA_BLOCKS.  Each block writes its partial sums (value
@@ -290,6 +458,16 @@ __device__ __forceinline__ void formula_leaf(Real x, const Real* __restrict__ pc
 // (ticket) adds the partials in block order and writes, for the prologue,
 // out[0] = log I (NaN when I is not positive and finite) and out[1+j] =
 // (dI/dp_j) / I.
+// F::cuts (where a leaf's normalisation must be split into pieces), if F has it
+template <class F, class = void>
+struct HasCuts {
+  static constexpr bool v = false;
+};
+template <class F>
+struct HasCuts<F, decltype((void)&F::cuts)> {
+  static constexpr bool v = true;
+};
+
 template <class F>
 __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
                                                   const double* __restrict__ params,
@@ -301,12 +479,34 @@ __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
   __shared__ int s_last;
   asm volatile("griddepcontrol.launch_dependents;");
   const RfLeafProg& L = P.leaf[k];
-  double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
-  for (int j = 0; j < NP; ++j) th[j] = params[L.par[j]];
+  // parameters j >= 4 sit in the slots after the leaf's (four per slot)
+  double th[NP > 0 ? NP : 1];
+  for (int j = 0; j < NP; ++j) th[j] = params[P.leaf[k + (j >> 2)].par[j & 3]];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // node
-  const int panel = i >> 4, node = i & 15;
-  const double h = (L.hi - L.lo) / RF_FORMULA_PANELS;
-  const double x = L.lo + h * (panel + 0.5 + 0.5 * gl_t[node]);
+  int panel = i >> 4;
+  const int node = i & 15;
+  double a = L.lo, h = (L.hi - L.lo) / RF_FORMULA_PANELS;
+  if constexpr (HasCuts<F>::v) {
+    // panels shared among the pieces in proportion to their lengths (at
+    // least one each), so that no panel straddles a piece's end
+    double c[4];
+    const int np = F::cuts(th, L.lo, L.hi, c);
+    int first = 0;
+    for (int q = 0; q < np; ++q) {
+      const double len = c[q + 1] - c[q];
+      int cnt = (int)(RF_FORMULA_PANELS * len / (L.hi - L.lo));
+      if (len > 0.0 && cnt < 1) cnt = 1;
+      if (q == np - 1 || first + cnt > RF_FORMULA_PANELS) cnt = RF_FORMULA_PANELS - first;
+      if (panel < first + cnt || q == np - 1) {
+        a = c[q];
+        h = cnt > 0 ? len / cnt : 0.0;
+        panel -= first;
+        break;
+      }
+      first += cnt;
+    }
+  }
+  const double x = a + h * (panel + 0.5 + 0.5 * gl_t[node]);
   const double wt = 0.5 * h * gl_w[node];
   const auto f = F::template eval<double>(x, th);
   double v[NV];
@@ -345,7 +545,7 @@ __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
     const double I = tot[0];
     const bool ok = I > 0.0 && isfinite(I);
     out[k * RF_FORMULA_NV] = ok ? ::log(I) : __longlong_as_double(0x7ff8000000000000ll);
-    for (int j = 0; j < RF_LEAF_MAXP; ++j)
+    for (int j = 0; j < RF_FORMULA_NV - 1; ++j)
       out[k * RF_FORMULA_NV + 1 + j] = (ok && j < NP) ? tot[1 + j] / I : 0.0;
     ticket[k] = 0u;
   }

@@ -49,7 +49,8 @@ typedef unsigned long long uintptr_t;
 // leaf 1 + RF_LEAF_MAXP values (log I, then (dI/dp_j)/I)
 #define RF_FORMULA_PANELS 128
 #define RF_FORMULA_BLOCKS 16
-#define RF_FORMULA_NV (1 + RF_LEAF_MAXP)
+#define RF_FORMULA_MAXP 9  // parameters of a numerically normalised leaf (Hypatia2: 9)
+#define RF_FORMULA_NV (1 + RF_FORMULA_MAXP)
 
 enum { RF_KIND_PROD = 0, RF_KIND_FRAC = 1, RF_KIND_EXT = 2 };
 // gmask bit of an ARGUS leaf whose fixed p is not 1/2 (general-p form, no
@@ -70,7 +71,11 @@ enum {
   RFL_CB = 4,
   RFL_ARGUS = 5,
   RFL_JOHNSON = 9,
-  RFL_FORMULA = 10  // a formula given as text; specialised kernels only
+  RFL_FORMULA = 10,  // a formula given as text; specialised kernels only
+  RFL_HYPATIA2 = 11, // Hypatia2 (9 parameters, numeric normalisation);
+                     // specialised kernels only
+  RFL_PARAMS = 12    // parameters 4.. of the Hypatia2 leaf in the slot before
+                     // (no per-event work of its own)
 };
 
 struct RfLeafProg {
@@ -82,7 +87,8 @@ struct RfLeafProg {
   int32_t gmask;     // bit j: gradient of leaf param j is wanted; ARGUS:
                      // RF_ARGUS_GENERAL selects the general-p form for a
                      // fixed p (a free p, bit 2, always takes it)
-  int32_t pad_;
+  int32_t part;      // RFL_PARAMS: which four parameters of the leaf `part`
+                     // slots before (parameters 4 part .. 4 part + 3)
   double lo, hi;     // observable range
 };
 

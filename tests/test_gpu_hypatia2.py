@@ -1,0 +1,92 @@
+"""Hypatia2 leaves on the GPU (specialised kernels) against the oracle: NLL,
+gradient in all twelve parameters of an extended Hypatia2 + Exponential
+model, and per-event log P, in FP64 and FP32 evaluation; a fixed tail
+parameter; the calls that refuse the leaf."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+from _common import TOL, free_mask, grad_l1, logp_err, rel_nll
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def rf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2003_12875_gb300 as rf
+    rf.load()
+    return rf
+
+
+@pytest.fixture(scope="module")
+def data():
+    w = datagen.hypatia2_exp(8_000, 12_003)
+    p = list(w["spec"]["params"])
+    p[0], p[1], p[3], p[4], p[9] = -1.4, 1.3, 0.52, 5.02, -0.21
+    v, g, sc, rc = oracle.nll_scaled(w["spec"], p, w["cols"].astype(np.float64))
+    assert rc == 0
+    return w, p, v, g, sc
+
+
+def dev(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dt)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nll_and_gradient_match_oracle(rf, data, prec):
+    w, p, v, g, sc = data
+    G = rf.Graph(w["spec"], "f32", prec)
+    assert G.uses_jit()
+    nll, grad = G.nll(dev(w["cols"], torch.float32), dev(p))
+    assert rel_nll(float(nll.item()), v) <= TOL[prec]["nll"], (float(nll.item()), v)
+    err = grad_l1(grad.cpu().numpy(), g, sc, free_mask(w["spec"]))
+    assert err.max() <= TOL[prec]["grad"], err
+    assert G.status() == 0
+    assert G.last_launches() == 3      # normalisation, prologue, fused kernel
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_per_event_log_probability(rf, data, prec):
+    w, p, *_ = data
+    sub = w["cols"][:, :4001]
+    want, rc = oracle.logp(w["spec"], p, sub.astype(np.float64))
+    G = rf.Graph(w["spec"], "f32", prec)
+    got = G.logp(dev(sub, torch.float32), dev(p)).cpu().numpy()
+    assert logp_err(got, want).max() <= TOL[prec]["logp"]
+
+
+def test_fixed_tail_parameters(rf, data):
+    """n and a2 fixed: their derivative slots drop out, the rest still match."""
+    w, p, *_ = data
+    spec = dict(w["spec"])
+    spec["fixed"] = list(spec["fixed"])
+    spec["fixed"][6] = spec["fixed"][7] = True
+    v, g, sc, rc = oracle.nll_scaled(spec, p, w["cols"].astype(np.float64))
+    assert rc == 0
+    G = rf.Graph(spec, "f32", "fp64")
+    nll, grad = G.nll(dev(w["cols"], torch.float32), dev(p))
+    grad = grad.cpu().numpy()
+    assert rel_nll(float(nll.item()), v) <= TOL["fp64"]["nll"]
+    assert grad_l1(grad, g, sc, free_mask(spec)).max() <= TOL["fp64"]["grad"]
+    assert grad[6] == 0.0 and grad[7] == 0.0
+
+
+def test_domain_error_and_refusals(rf, data):
+    w, p, *_ = data
+    G = rf.Graph(w["spec"], "f32", "fp64")
+    q = list(p)
+    q[1] = -0.5                       # zeta must be positive
+    nll, grad = G.nll(dev(w["cols"], torch.float32), dev(q))
+    assert float(nll.item()) == float("inf") and torch.isnan(grad).all()
+    assert G.status() & rf.STATUS_PARAM_DOMAIN
+    with pytest.raises(rf.RFError):
+        G.set_jit(False)
+    with pytest.raises(rf.RFError):
+        G.bind_events(dev(w["cols"], torch.float32), 4)
+    with pytest.raises(rf.RFError):
+        G.nll_plain(dev(w["cols"], torch.float32), dev(p))
