@@ -521,7 +521,7 @@ def toy_bench(args, rf, torch, rank, world, pk):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": w["name"], "toys": toys, "events": n,
-                       "launch": G.get_launch(), "kernel": G.uses_jit(),
+                       "launch": G.get_toy_launch(), "kernel": G.uses_jit(),
                        "kernel_hash": G.toy_kernel_hash(),
                        "l2": f"inputs larger than L2 ({n * col_bytes / 1e6:.0f} MB > 2 x 129 MB), "
                              "no flush"},

@@ -421,6 +421,14 @@ uint64_t rf_graph_kernel_hash(const rf_graph* g);
 /* The same for the toy segment kernel of the bound toy sample (0 before
  * rf_graph_bind_events or with the generic kernels). */
 uint64_t rf_graph_toy_kernel_hash(const rf_graph* g);
+/* The toy segment kernel's launch (Sec. 5.1's batches, one per toy, run as
+ * one grid): threads per block, events per lane per chunk, and registers per
+ * thread of the specialised kernel of the bound toy sample (0 before
+ * rf_graph_bind_events or with the generic kernels).  The grid is the SM
+ * count times the resident blocks of that size.  RF_EINVAL for a NULL
+ * argument; writes only the three outputs. */
+rf_status rf_graph_get_toy_launch(const rf_graph* g, int32_t* block, int32_t* events_per_lane,
+                                  int32_t* regs);
 int32_t rf_graph_kernel_regs(const rf_graph* g);
 
 /* Synchronises the device, returns the OR of RF_STATUS_* bits raised since

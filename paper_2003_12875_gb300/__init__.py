@@ -73,7 +73,7 @@ SYMBOLS = ["rf_graph_validate", "rf_graph_compile", "rf_graph_destroy", "rf_nll"
            "rf_microbench", "rf_graph_set_jit", "rf_graph_uses_jit", "rf_graph_kernel_regs",
            "rf_jit_check", "rf_check_log", "rf_nll_noalloc", "rf_graph_kernel_hash",
            "rf_check_d2f", "rf_generate_toys", "rf_graph_set_shard_weight",
-           "rf_graph_tune_ex", "rf_graph_toy_kernel_hash"]
+           "rf_graph_tune_ex", "rf_graph_toy_kernel_hash", "rf_graph_get_toy_launch"]
 
 
 def lib_path() -> str:
@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True):
         L.rf_graph_kernel_hash.restype = C.c_uint64
         L.rf_graph_toy_kernel_hash.argtypes = [vp]
         L.rf_graph_toy_kernel_hash.restype = C.c_uint64
+        i32p = C.POINTER(C.c_int32)
+        L.rf_graph_get_toy_launch.argtypes = [vp, i32p, i32p, i32p]
         for name in SYMBOLS:
             if name not in ("rf_last_error", "rf_graph_last_launches", "rf_graph_uses_jit",
                             "rf_graph_kernel_regs", "rf_graph_kernel_hash",
@@ -421,6 +423,13 @@ class Graph:
 
     def toy_kernel_hash(self) -> str:
         return f"{int(load().rf_graph_toy_kernel_hash(self._h)):016x}"
+
+    def get_toy_launch(self) -> dict:
+        """The toy segment kernel's block size, events per lane and registers
+        per thread (0 before bind_events or with the generic kernels)."""
+        b, e, r = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().rf_graph_get_toy_launch(self._h, C.byref(b), C.byref(e), C.byref(r)))
+        return {"block": b.value, "events_per_lane": e.value, "regs_per_thread": r.value}
 
 
 class RFNll(torch.autograd.Function):

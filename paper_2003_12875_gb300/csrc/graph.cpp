@@ -565,8 +565,26 @@ uint64_t rf_graph_kernel_hash(const rf_graph* g) {
 
 uint64_t rf_graph_toy_kernel_hash(const rf_graph* g) {
   if (!g || !g->jit || !g->bound) return 0;
-  return rf_jit_hash(g->prog, fcode(g), g->eval, g->coldt,
+  return rf_jit_hash(g->prog, fcode(g), g->eval, toy_coldt(g),
                      g->toy_bulk ? RF_JIT_TOYS_BULK : RF_JIT_TOYS, toy_ept(g), toy_min_blocks());
+}
+
+rf_status rf_graph_get_toy_launch(const rf_graph* g, int32_t* block, int32_t* events_per_lane,
+                                  int32_t* regs) {
+  g_err.clear();
+  if (!g || !block || !events_per_lane || !regs) return fail(RF_EINVAL, "NULL argument");
+  *block = g->cfg.block;
+  *events_per_lane = toy_ept(g);
+  *regs = 0;
+  if (g->jit && g->bound) {
+    const cudaKernel_t k = g->jk_toys[ept_index(g->eval, toy_coldt(g), toy_ept(g))];
+    cudaFuncAttributes fa;
+    if (k && cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k)) == cudaSuccess)
+      *regs = fa.numRegs;
+    else
+      cudaGetLastError();
+  }
+  return RF_OK;
 }
 
 int32_t rf_graph_kernel_regs(const rf_graph* g) {

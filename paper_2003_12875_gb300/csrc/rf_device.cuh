@@ -400,6 +400,39 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
   }
 }
 
+// Hypatia2's shape constants (per call, FP64) into columns 4..7 of its first
+// two slots: with phi = K_{lambda+1}(zeta)/K_lambda(zeta) and log phi's
+// derivatives in lambda and zeta (exported by the normalisation kernel),
+// delta^2 = sigma^2 zeta/phi into slot 0 and alpha = sqrt(zeta phi)/sigma into
+// slot 1, each as (value, d/d lambda, d/d zeta, d/d sigma).  k is the leaf's
+// first slot or its second (a parameter slot with part 1).
+template <typename T>
+__device__ __forceinline__ void hyp2_shape_pc(const RfProgram& P, int k, const double* params,
+                                              T* pc) {
+  const RfLeafProg& L = P.leaf[k];
+  const int k0 = L.type == RFL_PARAMS ? k - L.part : k;
+  const RfLeafProg& M = P.leaf[k0];
+  const double zeta = params[M.par[1]], sigma = params[M.par[3]];
+  const double* sh = P.formula_norm + (k0 + 1) * RF_FORMULA_NV;
+  const double lp = sh[0], dl = sh[1], dz = sh[2];
+  if (k == k0) {
+    const double d2 = sigma * sigma * zeta * exp(-lp);
+    pc[4] = (T)d2;
+    pc[5] = (T)(-d2 * dl);
+    pc[6] = (T)(d2 * (1.0 / zeta - dz));
+    pc[7] = (T)(2.0 * d2 / sigma);
+  } else {
+    const double al = sqrt(zeta * exp(lp)) / sigma;
+    pc[4] = (T)al;
+    pc[5] = (T)(0.5 * al * dl);
+    pc[6] = (T)(0.5 * al * (1.0 / zeta + dz));
+    pc[7] = (T)(-al / sigma);
+  }
+}
+__device__ __forceinline__ bool hyp2_shape_slot(const RfLeafProg& L) {
+  return L.type == RFL_HYPATIA2 || (L.type == RFL_PARAMS && L.part == 1);
+}
+
 // Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k], K.gmul[k]
 // and lnI_out.
 template <typename Real>
@@ -416,6 +449,12 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     *lnI_out = nrm[0];
     for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
     ok = isfinite(*lnI_out);
+    if (L.type == RFL_HYPATIA2) {
+      // the per-event code evaluates f e^{-zeta} (its core's + zeta left out),
+      // so its integral is I e^{-zeta}
+      *lnI_out -= th[1];
+      dln[1] -= 1.0;
+    }
   } else if (L.type == RFL_PARAMS) {
     // parameters 4 part .. of the leaf `part` slots before: their share of
     // that leaf's (dI/dp_j)/I; the integral itself is counted there
@@ -432,6 +471,7 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
   K.lnI[k] = *lnI_out;
   Real* pc = K.pc[k];
   leaf_pc<Real>(L, th, pc);
+  if (hyp2_shape_slot(L)) hyp2_shape_pc<Real>(P, k, params, pc);
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
     K.dlogI[k][j] = dln[j];
     K.dtheta[k][j] = 0.0;
@@ -472,6 +512,9 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
     case RFL_HYPATIA2:
     case RFL_PARAMS:
       for (int j = 0; j < L.npar; ++j) K.dtheta[k][j] = (double)pc[j] - th[j];
+      // Hypatia2's zeta reaches the per-event code only through the FP64
+      // shape constants
+      if (L.type == RFL_HYPATIA2) K.dtheta[k][1] = 0.0;
       break;
     case RFL_ARGUS:
       K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
@@ -569,6 +612,7 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
       double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
       for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
       leaf_pc<double>(L, th, X->pcd[k]);
+      if (hyp2_shape_slot(L)) hyp2_shape_pc<double>(P, k, params, X->pcd[k]);
       X->lmeta[k] = (L.type & 0xff) | ((L.gmask & 0xff) << 8) | ((L.comp & 0xff) << 16) |
                     ((L.col & 0xff) << 24);
     }

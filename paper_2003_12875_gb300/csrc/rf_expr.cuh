@@ -361,37 +361,52 @@ __device__ __forceinline__ Dual<R, N> dlog_besselk(const Dual<R, N>& nu, const D
 // tail's base is not positive; NaN for parameters outside their domain.
 struct Hypatia2Leaf {
   static constexpr int NP = 9;
+  // the normalisation kernel exports log phi and its derivatives in lambda
+  // and zeta (FP64) into the row of the leaf's second slot
+  static constexpr int kShapeRow = 1;
   template <typename R>
   static __device__ __forceinline__ Dual<R, 9> core(const Dual<R, 9>& d, const Dual<R, 9>& nu,
                                                     const Dual<R, 9>& beta,
                                                     const Dual<R, 9>& alpha,
-                                                    const Dual<R, 9>& delta2, R zeta_v,
-                                                    const Dual<R, 9>& zeta, Dual<R, 9>* slope) {
-    (void)zeta_v;
+                                                    const Dual<R, 9>& delta2, Dual<R, 9>* slope) {
     const Dual<R, 9> q = d * d + delta2, r = fx::sqrt(q), z = alpha * r;
-    const Dual<R, 9> L = (R(0.5) * (nu * fx::log(q)) + beta * d) + (log_besselk(nu, z) + zeta);
+    const Dual<R, 9> L = (R(0.5) * (nu * fx::log(q)) + beta * d) + log_besselk(nu, z);
     if (slope) *slope = (nu * d / q + beta) + (alpha * d / r) * dlog_besselk(nu, z);
     return L;
   }
-  // log f and d log f / dp_j
+  static __device__ __forceinline__ bool in_domain(const double* p) {
+    return p[1] > 0.0 && p[3] > 0.0 && p[5] > 0.0 && p[6] > 0.0 && p[7] > 0.0 && p[8] > 0.0;
+  }
   template <typename R>
-  static __device__ __noinline__ Dual<R, 9> logf(R x, const R* __restrict__ p) {
+  static __device__ __forceinline__ bool in_domain(const R* p) {
+    return p[1] > R(0) && p[3] > R(0) && p[5] > R(0) && p[6] > R(0) && p[7] > R(0) && p[8] > R(0);
+  }
+  // log f - zeta and its derivatives d/dp_j from the nine parameters p[0..8]
+  // and the shape constants p[9..16]: delta^2 and its derivatives in
+  // (lambda, zeta, sigma), then alpha and its derivatives in the same three
+  // (per-call constants, computed once in FP64).  zeta enters only through
+  // them: the per-event sums then carry no constant term (the prologue takes
+  // zeta off log I and 1 off d log I/d zeta instead).
+  template <typename R>
+  static __device__ __noinline__ Dual<R, 9> logf_shaped(R x, const R* __restrict__ p) {
     using D = Dual<R, 9>;
-    const D lam = D::var(p[0], 0), zeta = D::var(p[1], 1), beta = D::var(p[2], 2);
+    const D lam = D::var(p[0], 0), beta = D::var(p[2], 2);
     const D sigma = D::var(p[3], 3), mu = D::var(p[4], 4), a = D::var(p[5], 5);
     const D n = D::var(p[6], 6), a2 = D::var(p[7], 7), n2 = D::var(p[8], 8);
     D out;
-    if (!(p[1] > R(0)) || !(p[3] > R(0)) || !(p[5] > R(0)) || !(p[6] > R(0)) ||
-        !(p[7] > R(0)) || !(p[8] > R(0))) {
+    if (!in_domain<R>(p)) {
       out.v = R(0) / R(0);
 #pragma unroll
       for (int i = 0; i < 9; ++i) out.d[i] = R(0);
       return out;
     }
-    const D logphi = log_besselk(lam + R(1), zeta) - log_besselk(lam, zeta);
-    const D logz = fx::log(zeta), logs = fx::log(sigma);
-    const D delta2 = fx::exp(R(2) * logs + (logz - logphi));
-    const D alpha = fx::exp(R(0.5) * (logz + logphi) - logs);
+    D delta2, alpha;
+    delta2.v = p[9];
+    alpha.v = p[13];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) delta2.d[i] = alpha.d[i] = R(0);
+    delta2.d[0] = p[10], delta2.d[1] = p[11], delta2.d[3] = p[12];
+    alpha.d[0] = p[14], alpha.d[1] = p[15], alpha.d[3] = p[16];
     const D nu = lam - R(0.5);
     const D d = x - mu;
     const D dL = -(a * sigma), dR = a2 * sigma;
@@ -399,7 +414,7 @@ struct Hypatia2Leaf {
       const bool left = d.v < dL.v;
       const D dJ = left ? dL : dR, m = left ? n : n2;
       D k;
-      const D LJ = core<R>(dJ, nu, beta, alpha, delta2, p[1], zeta, &k);
+      const D LJ = core<R>(dJ, nu, beta, alpha, delta2, &k);
       const D base = R(1) - (d - dJ) * k / m;
       if (!(base.v > R(0))) {
         out.v = -R(1) / R(0);
@@ -409,12 +424,44 @@ struct Hypatia2Leaf {
       }
       return LJ - m * fx::log(base);
     }
-    return core<R>(d, nu, beta, alpha, delta2, p[1], zeta, nullptr);
+    return core<R>(d, nu, beta, alpha, delta2, nullptr);
+  }
+  // log f and d log f / dp_j from the nine parameters alone (FP64, for the
+  // normalisation kernel): log phi = log K_{lambda+1}(zeta) - log K_lambda(zeta)
+  // computed here, and written as (value, d/d lambda, d/d zeta) to lp_out when
+  // it is given (NaN outside the domain); log f includes the + zeta of the
+  // core
+  template <typename R>
+  static __device__ __forceinline__ Dual<R, 9> logf(R x, const R* __restrict__ p,
+                                                    R* lp_out = nullptr) {
+    using D = Dual<R, 9>;
+    R q[17];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) q[j] = p[j];
+    if (!in_domain<R>(p)) {
+      if (lp_out) lp_out[0] = lp_out[1] = lp_out[2] = R(0) / R(0);
+      return logf_shaped<R>(x, q);
+    }
+    const D lam = D::var(p[0], 0), zeta = D::var(p[1], 1), sigma = D::var(p[3], 3);
+    const D logphi = log_besselk(lam + R(1), zeta) - log_besselk(lam, zeta);
+    if (lp_out) lp_out[0] = logphi.v, lp_out[1] = logphi.d[0], lp_out[2] = logphi.d[1];
+    const D logz = fx::log(zeta), logs = fx::log(sigma);
+    const D delta2 = fx::exp(R(2) * logs + (logz - logphi));
+    const D alpha = fx::exp(R(0.5) * (logz + logphi) - logs);
+    q[9] = delta2.v, q[10] = delta2.d[0], q[11] = delta2.d[1], q[12] = delta2.d[3];
+    q[13] = alpha.v, q[14] = alpha.d[0], q[15] = alpha.d[1], q[16] = alpha.d[3];
+    D L = logf_shaped<R>(x, q);
+    if (L.v > -R(1) / R(0)) {  // + zeta keeps e^L of order one near the peak
+      L.v += p[1];
+      L.d[1] += R(1);
+    }
+    return L;
   }
   // f and df/dp_j (for the normalisation kernel)
   template <typename R>
-  static __device__ __forceinline__ Dual<R, 9> eval(R x, const R* __restrict__ p) {
-    const Dual<R, 9> L = logf<R>(x, p);
+  static __device__ __forceinline__ Dual<R, 9> eval(R x, const R* __restrict__ p,
+                                                    R* lp_out = nullptr) {
+    const Dual<R, 9> L = logf<R>(x, p, lp_out);
     if (!(L.v > -R(1) / R(0))) {  // f = 0 (or NaN)
       Dual<R, 9> z;
       z.v = L.v == L.v ? R(0) : L.v;
@@ -436,16 +483,23 @@ struct Hypatia2Leaf {
 };
 
 // The per-event Hypatia2 leaf: u = add + log2 f, g_j = d log f/dp_j for the
-// wanted j (GM9: bit j for parameter j).  Its nine parameters sit in three
-// consecutive leaf slots of the per-event constants (pc rows k, k+1, k+2:
-// p0..p3, p4..p7, p8).
+// wanted j (GM9: bit j for parameter j).  Its nine parameters and eight shape
+// constants sit in three consecutive leaf slots of the per-event constants:
+// row k p0..p3 then delta^2 (value, d/d lambda, d/d zeta, d/d sigma), row
+// k+1 p4..p7 then alpha (the same four), row k+2 p8.
 template <typename Real, int GM9>
 __device__ __forceinline__ void hypatia2_leaf(Real x, const Real* __restrict__ pc, Real& u,
                                               Real (&g)[9], Real add = Real(-0.0)) {
-  Real p[9];
+  Real p[17];
 #pragma unroll
-  for (int j = 0; j < 9; ++j) p[j] = pc[(j >> 2) * RF_PC + (j & 3)];
-  const Dual<Real, 9> L = Hypatia2Leaf::logf<Real>(x, p);
+  for (int j = 0; j < 4; ++j) {
+    p[j] = pc[j];
+    p[4 + j] = pc[RF_PC + j];
+    p[9 + j] = pc[4 + j];
+    p[13 + j] = pc[RF_PC + 4 + j];
+  }
+  p[8] = pc[2 * RF_PC];
+  const Dual<Real, 9> L = Hypatia2Leaf::logf_shaped<Real>(x, p);
   u = L.v * Real(1.44269504088896340736) + add;
 #pragma unroll
   for (int j = 0; j < 9; ++j) g[j] = ((GM9 >> j) & 1) ? L.d[j] : Real(0);
@@ -467,6 +521,23 @@ template <class F>
 struct HasCuts<F, decltype((void)&F::cuts)> {
   static constexpr bool v = true;
 };
+
+// F::kShapeRow (a leaf that exports per-call shape constants), if F has it
+template <class F, class = void>
+struct HasShape {
+  static constexpr bool v = false;
+};
+template <class F>
+struct HasShape<F, decltype((void)F::kShapeRow)> {
+  static constexpr bool v = true;
+};
+template <class F>
+__device__ __forceinline__ auto norm_eval(double x, const double* th, double* sh) {
+  if constexpr (HasShape<F>::v)
+    return F::template eval<double>(x, th, sh);
+  else
+    return F::template eval<double>(x, th);
+}
 
 template <class F>
 __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
@@ -508,7 +579,10 @@ __device__ __forceinline__ void formula_norm_body(const RfProgram& P, int k,
   }
   const double x = a + h * (panel + 0.5 + 0.5 * gl_t[node]);
   const double wt = 0.5 * h * gl_w[node];
-  const auto f = F::template eval<double>(x, th);
+  double* sh = nullptr;  // one node's thread writes the leaf's shape constants
+  if constexpr (HasShape<F>::v)
+    if (blockIdx.x == 0 && threadIdx.x == 0) sh = out + (k + F::kShapeRow) * RF_FORMULA_NV;
+  const auto f = norm_eval<F>(x, th, sh);
   double v[NV];
   v[0] = wt * f.v;
 #pragma unroll

@@ -104,9 +104,12 @@ struct RfProgram {
   uint64_t fixed_lo, fixed_hi;  // bit p: parameter p is fixed (grad = 0)
   double ext_weight;         // weight of the extended term sum(nu) and its
                              // gradient (1; 0 on all shards but one)
-  double* formula_norm;      // device [RF_MAXL * (1 + RF_LEAF_MAXP)]: log I and
-                             // (dI/dp_j)/I of each formula leaf, written by the
-                             // normalisation kernel before the prologue reads them
+  double* formula_norm;      // device [RF_MAXL * RF_FORMULA_NV]: row k holds log I
+                             // and (dI/dp_j)/I of the formula or Hypatia2 leaf in
+                             // slot k; a Hypatia2 leaf's second row holds log phi
+                             // and its derivatives in lambda and zeta.  Written
+                             // by the normalisation kernel before the prologue
+                             // reads them
   RfLeafProg leaf[RF_MAXL];
 };
 

@@ -178,3 +178,13 @@ def test_formula_kernels_compile_without_gpu(rf, prec, dt):
     spec["nodes"][1] = dict(spec["nodes"][1], type="formula", formula="exp(p0*x)")
     assert rf.jit_check(spec, dt, prec) == 0, rf.load().rf_last_error().decode()[:2000]
     assert rf.jit_check(_formula("1 + 0.5*x", 0), dt, prec) == 0
+
+
+# ------------------------------------------------------------ Hypatia2 leaves
+
+@pytest.mark.parametrize("dt,prec", [("f64", "fp64"), ("f32", "fp32")])
+def test_hypatia2_kernels_compile_without_gpu(rf, dt, prec):
+    """A Hypatia2 leaf compiles into the fused, log P and normalisation
+    kernels (with its shape constants exported by the normalisation kernel)."""
+    spec = datagen.hypatia2_exp_spec()
+    assert rf.jit_check(spec, dt, prec) == 0, rf.load().rf_last_error().decode()[:2000]

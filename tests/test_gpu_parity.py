@@ -499,9 +499,13 @@ def test_batched_toys_match_oracle_and_single(rf, prec, shape, jit):
     ev = to_dev(w)
     G.set_launch(block=shape[0], blocks_per_sm=shape[1])
     assert int(G.toy_kernel_hash(), 16) == 0  # no toy kernel before the bind
+    assert G.get_toy_launch()["regs_per_thread"] == 0
     G.bind_events(ev, 64)
     assert (int(G.toy_kernel_hash(), 16) != 0) == jit
     assert G.toy_kernel_hash() != G.kernel_hash() or not jit
+    tl = G.get_toy_launch()
+    assert tl["block"] == shape[0] and tl["events_per_lane"] in (4, 8, 16)
+    assert (tl["regs_per_thread"] > 0) == jit
     off = torch.from_numpy(w["offsets"]).to(DEV)
     pmd = torch.from_numpy(pm).to(DEV)
     got = G.nll_batched(off, pmd).cpu().numpy()
