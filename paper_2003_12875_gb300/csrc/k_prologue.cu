@@ -1,12 +1,14 @@
 // The single-dataset FP64 prologue kernel (normalisation integrals, their
 // derivatives and the coefficients), shared by the generic and the
-// per-graph fused kernels.  One block of one warp per leaf.
+// per-graph fused kernels.  One block of 2 n_leaves + 1 warps (block_prologue's
+// tasks, all at once).
 #include "rf_kernels.cuh"
 
 namespace rf {
-// Single-dataset prologue: one block, warp k computes leaf k's normalisation
-// and constants (the leaves' FP64 chains run on different SM sub-partitions),
-// thread 0 combines, all in shared memory.  It lets its dependent (the fused
+// Single-dataset prologue: one block; each leaf's integral, each leaf's
+// per-event constants and the coefficients' logs on warps of their own (the
+// FP64 chains run on different SM sub-partitions), thread 0 combines, all in
+// shared memory.  It lets its dependent (the fused
 // kernel) launch at once, and it is itself launched as a programmatic
 // dependent of the previous kernel in the stream: when that is the previous
 // call's fused kernel, this FP64 work overlaps it, and the wait before the
@@ -37,7 +39,7 @@ __device__ __forceinline__ void prologue_body(const RfProgram& P, const double* 
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(32 * RF_MAXL) prologue_kernel(const RfProgram P,
+__global__ void __launch_bounds__(32 * (2 * RF_MAXL + 1)) prologue_kernel(const RfProgram P,
                                                                 const double* __restrict__ params,
                                                                 RfWork W) {
   prologue_body<Real>(P, params, W);
@@ -48,7 +50,7 @@ int rf_launch_prologue(const RfProgram& P, int eval, const double* params, RfWor
                        bool chain, cudaStream_t st) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(1);
-  lc.blockDim = dim3(32 * (P.n_leaves > 0 ? P.n_leaves : 1));
+  lc.blockDim = dim3(32 * (2 * (P.n_leaves > 0 ? P.n_leaves : 1) + 1));
   lc.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -90,8 +90,8 @@ int rf_launch_batched(const RfProgram& P, int eval, int coldt, const RfLaunchCfg
   if (grid * wpb > room) grid = room / wpb;
   const int64_t warps = grid * wpb;
 
-  // prep: blocks of one warp per leaf and 32 toys
-  const int pb = 32 * std::max(P.n_leaves, 1);
+  // prep: blocks of 32 toys and 3 warps per leaf + 1
+  const int pb = 32 * (3 * std::max(P.n_leaves, 1) + 1);
   const int pg = (toys + 31) / 32 > 0 ? (toys + 31) / 32 : 1;
   int32_t* at = adam_scale ? W.adam_t : nullptr;
   // a programmatic dependent of the kernel before it (back to back: the

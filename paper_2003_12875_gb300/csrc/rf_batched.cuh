@@ -1,12 +1,12 @@
 // rf_batched.cuh -- many datasets (toys) of uneven size sharing one graph.
 //
-//  prep kernel      one thread per toy: the toy's FP64 normalisations and
-//                   coefficients (RfConsts) from its parameter row; checks
-//                   the toy's offsets.
+//  prep kernel      32 toys per block, their FP64 normalisations, per-event
+//                   constants and coefficients (RfConsts) from their
+//                   parameter rows on separate warps; checks the offsets.
 //  segment kernel   the toys' events split evenly over the launch's warps;
 //                   each warp writes one FP64 row per toy its range meets
 //                   (launched as a programmatic dependent of the prep kernel).
-//  finalize kernel  one warp per toy: its rows summed in order, the FP64
+//  finalize kernel  one thread per toy: its rows summed in order, the FP64
 //                   epilogue (NLL, gradient), optionally one Adam step.
 // Results depend only on the inputs and the launch shape, not on timing.
 #pragma once
@@ -14,15 +14,20 @@
 
 namespace rf {
 
-// Prep kernel: blocks of n_leaves warps and 32 toys; warp k computes leaf k
-// of every toy of the block (lane l: toy 32 b + l), so the leaves' FP64
-// chains run side by side on different SM sub-partitions, then warp 0 checks
-// the toys' offsets and combines.  Lets the segment kernel launch at once.
-// The constants are built in shared memory and published only after the wait
-// for the kernel before (the previous call's finalize kernel, which reads
-// them), so back to back the FP64 chains of this call's prep run beside the
-// previous call's finalize.  A fit step (adam_t set) reads parameter rows that
-// the previous finalize kernel has just updated, so it waits first.
+// Prep kernel: blocks of 32 toys and 3 n_leaves + 1 warps, the tasks of the
+// single-dataset prologue for 32 toys at once (the FP64 unit takes one warp
+// instruction at a time, so the toys share each instruction and the tasks run
+// on separate SM sub-partitions): warps 2k and 2k + 1 take leaf k's integral
+// of the block's toys 0-15 and 16-31, one lane pair per toy
+// (leaf_norm_pair); warp 2L + k leaf k's per-event constants, lane l for toy
+// l; warp 3L the coefficients' logs, lane l for toy l.  Then warp 0 checks
+// the toys' offsets and combines, lane l for toy l.  Lets the segment kernel
+// launch at once.  The constants are built in shared memory and published
+// only after the wait for the kernel before (the previous call's finalize
+// kernel, which reads them), so back to back the FP64 chains of this call's
+// prep run beside the previous call's finalize.  A fit step (adam_t set)
+// reads parameter rows that the previous finalize kernel has just updated, so
+// it waits first.
 template <typename Real>
 __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* __restrict__ pm,
                                               const int64_t* __restrict__ offsets,
@@ -33,29 +38,50 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
   __shared__ RfConsts<Real> Ks[32];
   __shared__ double lnI_s[RF_MAXL][32];
   __shared__ int ok_s[RF_MAXL][32];
-  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
-  const int64_t t0 = (int64_t)blockIdx.x * 32, t = t0 + lane;
+  __shared__ double logc_s[RF_MAXC][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NL = P.n_leaves;
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
   if (adam_t) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (blockIdx.x == 0 && threadIdx.x == 0) *adam_t += 1;
   }
-  if (t < toys && k < P.n_leaves) {
-    double l = 0.0;
-    ok_s[k][lane] = leaf_consts(P, pm + t * P.n_par, Ks[lane], k, &l) ? 1 : 0;
-    lnI_s[k][lane] = l;
+  if (w < 2 * NL) {
+    const int k = w >> 1, j = 16 * (w & 1) + (lane >> 1);
+    const int64_t t = t0 + j;
+    if (t < toys) {  // the same for both lanes of a pair
+      double l = 0.0;
+      const bool o = leaf_norm_pair(P, pm + t * P.n_par, Ks[j], k, &l);
+      if ((lane & 1) == 0) {
+        ok_s[k][j] = o ? 1 : 0;
+        lnI_s[k][j] = l;
+      }
+    }
+  } else if (w < 3 * NL) {
+    const int64_t t = t0 + lane;
+    if (t < toys) leaf_eval_consts(P, pm + t * P.n_par, Ks[lane], w - 2 * NL);
+  } else if (w == 3 * NL) {
+    const int64_t t = t0 + lane;
+    if (t < toys) {
+      double coef[RF_MAXC], es;
+      bool bad = false;
+      root_coefs(P, pm + t * P.n_par, coef, &es, &bad);
+      for (int c = 0; c < P.n_comp; ++c)
+        logc_s[c][lane] = coef[c] > 0.0 ? d_log(coef[c]) : -kInf();
+    }
   }
   __syncthreads();
-  if (k == 0 && t < toys) {
+  const int64_t t = t0 + lane;
+  if (w == 0 && t < toys) {
     const int64_t b = offsets[t], e = offsets[t + 1];
     if (b < 0 || e < b || e > n_events) atomicOr(status, RF_STATUS_NONFINITE_BIT);
     double l[RF_MAXL];
     bool all = true;
-    for (int j = 0; j < P.n_leaves; ++j) {
+    for (int j = 0; j < NL; ++j) {
       l[j] = lnI_s[j][lane];
       all &= ok_s[j][lane] != 0;
     }
-    comb_consts(P, pm + t * P.n_par, Ks[lane], l, all,
-                consts_x ? consts_x + t : nullptr);
+    comb_consts(P, pm + t * P.n_par, Ks[lane], l, all, consts_x ? consts_x + t : nullptr,
+                &logc_s[0][lane], 32);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
@@ -64,7 +90,7 @@ __device__ __forceinline__ void toy_prep_body(const RfProgram& P, const double* 
   constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
   const double* src = reinterpret_cast<const double*>(Ks);
   double* dst = reinterpret_cast<double*>(consts + t0);
-  for (int64_t w = threadIdx.x; w < nt * kWords; w += blockDim.x) dst[w] = src[w];
+  for (int64_t q = threadIdx.x; q < nt * kWords; q += blockDim.x) dst[q] = src[q];
 }
 
 // Finalize kernel: one thread per toy (the FP64 unit takes one warp

@@ -30,6 +30,7 @@ __device__ __forceinline__ double kInf() { return __longlong_as_double(0x7ff0000
 __device__ __forceinline__ double kNaN() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kInvSqrt2 = 0.70710678118654752440;
 constexpr double kSqrtHalfPi = 1.25331413731550025121;
 constexpr double kSqrtPi = 1.77245385090551602730;
 // The per-event code works in base-2 log units (u / ln 2): the hardware's
@@ -327,6 +328,54 @@ static __device__ __noinline__ bool leaf_lognorm(int type, int gm, const double*
   return false;
 }
 
+// The Gaussian's and the Exponential's log I and d log I/d theta on an
+// aligned lane pair: both lanes call it, lane e (0 or 1) takes range end e of
+// each pair of like transcendental functions (the two ends' erf and exp for
+// the Gaussian, e^s - 1 and e^-s - 1 for the Exponential), so the FP64 unit
+// evaluates both in one pass (it takes one warp instruction at a time however
+// many lanes are active), then both lanes finish with the same values.
+// Same formulas as leaf_lognorm; reciprocals are formed once and multiplied.
+static __device__ __noinline__ bool lognorm_pair(int type, const double* th, double lo,
+                                                 double hi, int e, double* lnI, double* dln) {
+  const unsigned pm = 3u << ((threadIdx.x & 31) & 30);
+  for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = 0.0;
+  if (type == RFL_GAUSS) {
+    const double mu = th[0], sg = th[1];
+    if (!(sg > 0.0)) return false;
+    const double rs = 1.0 / sg;
+    const double za = (lo - mu) * rs, zb = (hi - mu) * rs;
+    // erfc at both ends on one side of the mean (no cancellation), else erf
+    const int mode = za >= 0.0 ? 0 : (zb <= 0.0 ? 1 : 2);
+    const double z = e ? zb : za, w = z * kInvSqrt2;
+    const double F = mode == 2 ? d_erf(w) : d_erfc(mode == 0 ? w : -w);
+    const double g = d_exp(-0.5 * z * z);
+    const double Fo = __shfl_xor_sync(pm, F, 1), go = __shfl_xor_sync(pm, g, 1);
+    const double Fa = e ? Fo : F, Fb = e ? F : Fo, pa = e ? go : g, pb = e ? g : go;
+    const double I = sg * kSqrtHalfPi * (mode == 0 ? Fa - Fb : Fb - Fa);
+    *lnI = d_log(I);
+    const double rI = 1.0 / I;
+    dln[0] = (pa - pb) * rI;
+    dln[1] = rs + (za * pa - zb * pb) * rI;
+    return I > 0.0 && isfinite(I);
+  }
+  // Exponential: I = e^{lambda lo} L (e^s - 1)/s with s = lambda L (off =
+  // lambda lo); d log I/d lambda - lo = L (1/(1 - e^-s) - 1/s)
+  const double lam = th[0], L = hi - lo, s = lam * L;
+  const double q = d_expm1(e ? -s : s);
+  const double qo = __shfl_xor_sync(pm, q, 1);
+  const double q0 = e ? qo : q, q1 = e ? q : qo;
+  // one division pass: lane 0 (e^s - 1)/s, lane 1 1/(1 - e^-s) - 1/s
+  const double r = e ? (s + q1) / (-s * q1) : q0 / s;
+  const double ro = __shfl_xor_sync(pm, r, 1);
+  const double E = s == 0.0 ? 1.0 : (e ? ro : r), M = e ? r : ro;
+  *lnI = d_log(L * E);
+  const double m = (fabs(s) < 1e-3)
+                       ? 0.5 + s / 12.0 - s * s * s / 720.0 + s * s * s * s * s / 30240.0
+                       : M;
+  dln[0] = L * m;
+  return isfinite(*lnI);
+}
+
 // --------------------------------------------------------- prologue (FP64)
 template <typename Real>
 __device__ inline void split_hi_lo(double v, Real& hi, Real& lo) {
@@ -433,47 +482,18 @@ __device__ __forceinline__ bool hyp2_shape_slot(const RfLeafProg& L) {
   return L.type == RFL_HYPATIA2 || (L.type == RFL_PARAMS && L.part == 1);
 }
 
-// Leaf k's constants.  Writes K.pc[k], K.dlogI[k], K.dtheta[k], K.gmul[k]
-// and lnI_out.
+// Leaf k's per-event constants: K.pc[k], K.dtheta[k], K.gmul[k] (nothing
+// here needs the integral, so it runs beside leaf_norm).
 template <typename Real>
-__device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* params,
-                                   RfConsts<Real>& K, int k, double* lnI_out) {
+__device__ __noinline__ void leaf_eval_consts(const RfProgram& P, const double* params,
+                                              RfConsts<Real>& K, int k) {
   const RfLeafProg& L = P.leaf[k];
   double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
   for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
-  double dln[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
-  bool ok;
-  if (L.type == RFL_FORMULA || L.type == RFL_HYPATIA2) {
-    // log I and (dI/dp_j)/I from the normalisation kernel (NaN: I <= 0)
-    const double* nrm = P.formula_norm + k * RF_FORMULA_NV;
-    *lnI_out = nrm[0];
-    for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
-    ok = isfinite(*lnI_out);
-    if (L.type == RFL_HYPATIA2) {
-      // the per-event code evaluates f e^{-zeta} (its core's + zeta left out),
-      // so its integral is I e^{-zeta}
-      *lnI_out -= th[1];
-      dln[1] -= 1.0;
-    }
-  } else if (L.type == RFL_PARAMS) {
-    // parameters 4 part .. of the leaf `part` slots before: their share of
-    // that leaf's (dI/dp_j)/I; the integral itself is counted there
-    const double* nrm = P.formula_norm + (k - L.part) * RF_FORMULA_NV;
-    *lnI_out = 0.0;
-    for (int j = 0; j < RF_LEAF_MAXP; ++j) {
-      const int q = RF_LEAF_MAXP * L.part + j;
-      dln[j] = q < RF_FORMULA_MAXP ? nrm[1 + q] : 0.0;
-    }
-    ok = true;
-  } else {
-    ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
-  }
-  K.lnI[k] = *lnI_out;
   Real* pc = K.pc[k];
   leaf_pc<Real>(L, th, pc);
   if (hyp2_shape_slot(L)) hyp2_shape_pc<Real>(P, k, params, pc);
   for (int j = 0; j < RF_LEAF_MAXP; ++j) {
-    K.dlogI[k][j] = dln[j];
     K.dtheta[k][j] = 0.0;
     K.gmul[k][j] = 1.0;
   }
@@ -522,55 +542,150 @@ __device__ __noinline__ bool leaf_consts(const RfProgram& P, const double* param
       K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
   }
+}
+
+// Leaf k's log I and d log I/d theta (K.lnI[k], K.dlogI[k] and lnI_out);
+// false when its parameters are outside the leaf's definition range.
+template <typename Real>
+__device__ __noinline__ bool leaf_norm(const RfProgram& P, const double* params,
+                                       RfConsts<Real>& K, int k, double* lnI_out) {
+  const RfLeafProg& L = P.leaf[k];
+  double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
+  double dln[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+  bool ok;
+  if (L.type == RFL_FORMULA || L.type == RFL_HYPATIA2) {
+    // log I and (dI/dp_j)/I from the normalisation kernel (NaN: I <= 0)
+    const double* nrm = P.formula_norm + k * RF_FORMULA_NV;
+    *lnI_out = nrm[0];
+    for (int j = 0; j < RF_LEAF_MAXP; ++j) dln[j] = nrm[1 + j];
+    ok = isfinite(*lnI_out);
+    if (L.type == RFL_HYPATIA2) {
+      // the per-event code evaluates f e^{-zeta} (its core's + zeta left out),
+      // so its integral is I e^{-zeta}
+      *lnI_out -= th[1];
+      dln[1] -= 1.0;
+    }
+  } else if (L.type == RFL_PARAMS) {
+    // parameters 4 part .. of the leaf `part` slots before: their share of
+    // that leaf's (dI/dp_j)/I; the integral itself is counted there
+    const double* nrm = P.formula_norm + (k - L.part) * RF_FORMULA_NV;
+    *lnI_out = 0.0;
+    for (int j = 0; j < RF_LEAF_MAXP; ++j) {
+      const int q = RF_LEAF_MAXP * L.part + j;
+      dln[j] = q < RF_FORMULA_MAXP ? nrm[1 + q] : 0.0;
+    }
+    ok = true;
+  } else {
+    ok = leaf_lognorm(L.type, L.gmask, th, L.lo, L.hi, lnI_out, dln);
+  }
+  K.lnI[k] = *lnI_out;
+  for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dlogI[k][j] = dln[j];
   return ok;
 }
 
-// Combination constants (one thread), after every leaf's lnI is known.  X
-// (may be NULL): where FP32 evaluation with a zero coefficient gets its FP64
-// constants.
+// leaf_norm on an aligned lane pair (both lanes call it; lane e = threadIdx.x
+// & 1): the Gaussian and the Exponential split their range ends over the two
+// lanes (lognorm_pair), the other leaves run on the pair's first lane.  Only
+// the first lane writes K and lnI_out and its return value counts.
 template <typename Real>
-__device__ __noinline__ void comb_consts(const RfProgram& P, const double* params,
-                                   RfConsts<Real>& K, const double* lnI,
-                                   bool leaves_ok, RfExact* X = nullptr) {
-  bool bad = !leaves_ok;
-  const int C = P.n_comp;
-  double coef[RF_MAXC], base[RF_MAXC];
-  for (int c = 0; c < RF_MAXC; ++c) {
-    coef[c] = 0.0;
-    base[c] = 0.0;
+__device__ __noinline__ bool leaf_norm_pair(const RfProgram& P, const double* params,
+                                            RfConsts<Real>& K, int k, double* lnI_out) {
+  const RfLeafProg& L = P.leaf[k];
+  const int e = threadIdx.x & 1;
+  if (L.type == RFL_GAUSS || L.type == RFL_EXP) {
+    double th[RF_LEAF_MAXP] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < L.npar; ++j) th[j] = params[L.par[j]];
+    double l = 0.0, dln[RF_LEAF_MAXP];
+    const bool ok = lognorm_pair(L.type, th, L.lo, L.hi, e, &l, dln);
+    if (e == 0) {
+      *lnI_out = l;
+      K.lnI[k] = l;
+      for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dlogI[k][j] = dln[j];
+    }
+    return ok;
   }
-  K.ext_sum = 0.0;
+  if (e != 0) return true;
+  return leaf_norm<Real>(P, params, K, k, lnI_out);
+}
+
+// Leaf k's constants, all of them in one thread.
+template <typename Real>
+__device__ __forceinline__ bool leaf_consts(const RfProgram& P, const double* params,
+                                            RfConsts<Real>& K, int k, double* lnI_out) {
+  leaf_eval_consts<Real>(P, params, K, k);
+  return leaf_norm<Real>(P, params, K, k, lnI_out);
+}
+
+// The root's coefficients from the parameters (fractions, the last one 1 -
+// their sum; yields; 1 for a product), the extended term sum(nu) (weighted)
+// and whether a coefficient is outside its range.
+__device__ __forceinline__ void root_coefs(const RfProgram& P, const double* params,
+                                           double* coef, double* ext_sum, bool* bad) {
+  const int C = P.n_comp;
+  for (int c = 0; c < RF_MAXC; ++c) coef[c] = 0.0;
+  *ext_sum = 0.0;
   if (P.kind == RF_KIND_PROD) {
     coef[0] = 1.0;
   } else if (P.kind == RF_KIND_FRAC) {
     double rest = 1.0;
     for (int c = 0; c < C - 1; ++c) {
       double f = params[P.coef_par[c]];
-      if (!(f >= 0.0 && f <= 1.0)) bad = true;
+      if (!(f >= 0.0 && f <= 1.0)) *bad = true;
       coef[c] = f;
       rest -= f;
     }
     if (rest < 0.0) {
-      if (rest < -1e-15) bad = true;
+      if (rest < -1e-15) *bad = true;
       rest = 0.0;
     }
     coef[C - 1] = rest;
   } else {
     for (int c = 0; c < C; ++c) {
       double v = params[P.coef_par[c]];
-      if (!(v >= 0.0) || !isfinite(v)) bad = true;
+      if (!(v >= 0.0) || !isfinite(v)) *bad = true;
       coef[c] = v;
-      K.ext_sum += v;
+      *ext_sum += v;
     }
-    K.ext_sum *= P.ext_weight;
+    *ext_sum *= P.ext_weight;
   }
+}
+
+// log coef_c (-inf for a zero coefficient), for comb_consts to take ready
+// made: lane c of the calling warp computes component c's, so one FP64 pass
+// covers all of them; lanes >= n_comp write nothing.
+__device__ __forceinline__ void coef_logs_lanes(const RfProgram& P, const double* params,
+                                                int lane, double* logc) {
+  double coef[RF_MAXC], es;
+  bool bad = false;
+  root_coefs(P, params, coef, &es, &bad);
+  double c = 0.0;
+  for (int j = 0; j < RF_MAXC; ++j)
+    if (j == lane) c = coef[j];
+  if (lane < P.n_comp) logc[lane] = c > 0.0 ? d_log(c) : -kInf();
+}
+
+// Combination constants (one thread), after every leaf's lnI is known.  X
+// (may be NULL): where FP32 evaluation with a zero coefficient gets its FP64
+// constants.  logc (may be NULL): the coefficients' logs, component c at
+// logc[c * logc_stride], from coef_logs_lanes or the like.
+template <typename Real>
+__device__ __noinline__ void comb_consts(const RfProgram& P, const double* params,
+                                   RfConsts<Real>& K, const double* lnI,
+                                   bool leaves_ok, RfExact* X = nullptr,
+                                   const double* logc = nullptr, int logc_stride = 1) {
+  bool bad = !leaves_ok;
+  const int C = P.n_comp;
+  double coef[RF_MAXC], base[RF_MAXC];
+  for (int c = 0; c < RF_MAXC; ++c) base[c] = 0.0;
+  root_coefs(P, params, coef, &K.ext_sum, &bad);
   for (int k = 0; k < P.n_leaves; ++k) base[P.leaf[k].comp] -= lnI[k];
   double beta[RF_MAXC];
   double ref = -kInf();
   int zero = 0;
   for (int c = 0; c < C; ++c) {
     if (coef[c] > 0.0) {
-      beta[c] = d_log(coef[c]) + base[c];
+      beta[c] = (logc ? logc[c * logc_stride] : d_log(coef[c])) + base[c];
       ref = fmax(ref, beta[c]);
     } else {
       beta[c] = -kInf();
@@ -1108,10 +1223,15 @@ __device__ inline void rows_sum(const double* partials, int64_t r0, int64_t r1,
 
 // ---------------------------------------------------------------- epilogue
 // T: FP64 totals of the accumulators, n: events.  Writes NLL and gradient.
+// The gradient is summed in a thread-local array and stored once per
+// component: updating it in place in global memory would put a round trip to
+// L2 behind every term.
 template <typename Real, int NL>
 __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& K,
                                 const double* T, int64_t n, double* nll,
-                                double* grad, unsigned int* status) {
+                                double* grad_out, unsigned int* status) {
+  double g_local[RF_MAXPAR];
+  double* grad = grad_out ? g_local : nullptr;
   const int C = P.n_comp;
   double L = kLn2 * T[0];  // the per-event sums are in base-2 units
   for (int c = 0; c < C; ++c)
@@ -1145,6 +1265,7 @@ __device__ __noinline__ void epilogue(const RfProgram& P, const RfConsts<Real>& 
       bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
       if (fx) grad[p] = 0.0;
       if (bad) grad[p] = kNaN();
+      grad_out[p] = grad[p];
     }
   }
   if (bad) {

@@ -454,21 +454,45 @@ __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real,
   }
 }
 
-// Prologue run by every block: leaf k by lane 0 of warp k (their FP64 work
-// proceeds in parallel), then the combination by thread 0.
+// Prologue of one block.  The FP64 unit of an SM sub-partition takes one warp
+// instruction about every 64 cycles, whatever the number of active lanes, so
+// a chain's length is its instruction count: the work is cut into
+// independent tasks on separate warps (sub-partitions), and like functions go
+// on separate lanes of one instruction.  Task k < L: leaf k's integral on
+// lanes 0-1 (leaf_norm_pair); task L + k: leaf k's per-event constants on
+// lane 0; task 2L: the coefficients' logs, one per lane.  Warps take tasks
+// round robin (warp w: tasks w, w + warps, ...), so any block of 32 threads
+// or more works; 2L + 1 warps run them all at once.  Thread 0 then combines
+// (no transcendental function left there).
 template <typename Real>
 __device__ inline void block_prologue(const RfProgram& P, const double* params,
                                       RfConsts<Real>& K, double* lnI, int* ok,
                                       RfExact* X = nullptr) {
+  __shared__ double logc[RF_MAXC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
-  for (int k = wid; k < P.n_leaves; k += nw)
-    if (lane == 0) ok[k] = leaf_consts(P, params, K, k, &lnI[k]) ? 1 : 0;
+  const int NL = P.n_leaves, ntask = 2 * NL + 1;
+  for (int task = wid; task < ntask; task += nw) {
+    if (task < NL) {
+      if (lane < 2) {
+        double l = 0.0;
+        const bool o = leaf_norm_pair(P, params, K, task, &l);
+        if (lane == 0) {
+          ok[task] = o ? 1 : 0;
+          lnI[task] = l;
+        }
+      }
+    } else if (task < 2 * NL) {
+      if (lane == 0) leaf_eval_consts(P, params, K, task - NL);
+    } else {
+      coef_logs_lanes(P, params, lane, logc);
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     bool all = true;
-    for (int k = 0; k < P.n_leaves; ++k) all &= ok[k] != 0;
-    comb_consts(P, params, K, lnI, all, X);
+    for (int k = 0; k < NL; ++k) all &= ok[k] != 0;
+    comb_consts(P, params, K, lnI, all, X, logc);
   }
   __syncthreads();
 }
