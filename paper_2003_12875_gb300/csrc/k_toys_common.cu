@@ -39,7 +39,8 @@ template <typename Real>
 int launch_finalize(const RfProgram& P, const int64_t* offsets, int32_t toys, int64_t stride,
                     int64_t warps, double* pm, double* out, RfWork W,
                     const double* adam_scale, double adam_lr, cudaStream_t st) {
-  const int fb = 32, fg = (toys + fb - 1) / fb;  // one thread per toy, 32 toys per block
+  // 32 toys per block, RF_FIN_GROUP lanes per toy
+  const int fb = 32 * RF_FIN_GROUP, fg = (toys + 31) / 32;
   switch (P.n_leaves) {
     case 1: rf::toy_finalize_kernel<Real, 1><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;
     case 2: rf::toy_finalize_kernel<Real, 2><<<fg, fb, 0, st>>>(P, offsets, toys, stride, warps, pm, out, W, adam_scale, adam_lr); break;

@@ -449,37 +449,38 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
   }
 }
 
-// Hypatia2's shape constants (per call, FP64) into columns 4..7 of its first
-// two slots: with phi = K_{lambda+1}(zeta)/K_lambda(zeta) and log phi's
-// derivatives in lambda and zeta (exported by the normalisation kernel),
-// delta^2 = sigma^2 zeta/phi into slot 0 and alpha = sqrt(zeta phi)/sigma into
-// slot 1, each as (value, d/d lambda, d/d zeta, d/d sigma).  k is the leaf's
-// first slot or its second (a parameter slot with part 1).
+// Hypatia2's shape constants (per call, FP64): with phi = K_{lambda+1}(zeta)/
+// K_lambda(zeta) and log phi's derivatives in lambda and zeta (exported by
+// the normalisation kernel), delta^2 = sigma^2 zeta/phi and alpha =
+// sqrt(zeta phi)/sigma, each as (value, d/d lambda, d/d zeta, d/d sigma).
+// Slot 0 of the leaf (k0) takes delta^2's four in columns 4..7, slot 1
+// alpha's, slot 2 the low parts (v - (T)v) of the six derivatives in columns
+// 1..6.  k is one of the leaf's three slots.
 template <typename T>
 __device__ __forceinline__ void hyp2_shape_pc(const RfProgram& P, int k, const double* params,
                                               T* pc) {
   const RfLeafProg& L = P.leaf[k];
-  const int k0 = L.type == RFL_PARAMS ? k - L.part : k;
+  const int part = L.type == RFL_PARAMS ? L.part : 0;
+  const int k0 = k - part;
   const RfLeafProg& M = P.leaf[k0];
   const double zeta = params[M.par[1]], sigma = params[M.par[3]];
   const double* sh = P.formula_norm + (k0 + 1) * RF_FORMULA_NV;
   const double lp = sh[0], dl = sh[1], dz = sh[2];
-  if (k == k0) {
-    const double d2 = sigma * sigma * zeta * exp(-lp);
-    pc[4] = (T)d2;
-    pc[5] = (T)(-d2 * dl);
-    pc[6] = (T)(d2 * (1.0 / zeta - dz));
-    pc[7] = (T)(2.0 * d2 / sigma);
+  const double d2 = sigma * sigma * zeta * exp(-lp);
+  const double al = sqrt(zeta * exp(lp)) / sigma;
+  const double v[8] = {d2, -d2 * dl, d2 * (1.0 / zeta - dz), 2.0 * d2 / sigma,
+                       al, 0.5 * al * dl, 0.5 * al * (1.0 / zeta + dz), -al / sigma};
+  if (part < 2) {
+    for (int j = 0; j < 4; ++j) pc[4 + j] = (T)v[4 * part + j];
   } else {
-    const double al = sqrt(zeta * exp(lp)) / sigma;
-    pc[4] = (T)al;
-    pc[5] = (T)(0.5 * al * dl);
-    pc[6] = (T)(0.5 * al * (1.0 / zeta + dz));
-    pc[7] = (T)(-al / sigma);
+    for (int j = 0; j < 3; ++j) {
+      pc[1 + j] = (T)(v[1 + j] - (double)(T)v[1 + j]);
+      pc[4 + j] = (T)(v[5 + j] - (double)(T)v[5 + j]);
+    }
   }
 }
 __device__ __forceinline__ bool hyp2_shape_slot(const RfLeafProg& L) {
-  return L.type == RFL_HYPATIA2 || (L.type == RFL_PARAMS && L.part == 1);
+  return L.type == RFL_HYPATIA2 || L.type == RFL_PARAMS;
 }
 
 // Leaf k's per-event constants: K.pc[k], K.dtheta[k], K.gmul[k] (nothing
@@ -651,41 +652,75 @@ __device__ __forceinline__ void root_coefs(const RfProgram& P, const double* par
   }
 }
 
-// log coef_c (-inf for a zero coefficient), for comb_consts to take ready
-// made: lane c of the calling warp computes component c's, so one FP64 pass
-// covers all of them; lanes >= n_comp write nothing.
-__device__ __forceinline__ void coef_logs_lanes(const RfProgram& P, const double* params,
-                                                int lane, double* logc) {
+// The root's coefficients made ready for comb_consts (in shared memory, so
+// that the combination reads no parameter from global memory): the values,
+// their logs (-inf for a zero coefficient), sum(nu) and the range check.
+struct CoefPre {
+  double coef[RF_MAXC];
+  double logc[RF_MAXC];
+  double ext_sum;
+  int32_t bad;
+};
+
+// CoefPre by one warp: lane c computes log coef_c (one FP64 pass for all
+// components), lane 0 writes the rest.
+__device__ __forceinline__ void coef_pre_lanes(const RfProgram& P, const double* params,
+                                               int lane, CoefPre* cp) {
   double coef[RF_MAXC], es;
   bool bad = false;
   root_coefs(P, params, coef, &es, &bad);
   double c = 0.0;
   for (int j = 0; j < RF_MAXC; ++j)
     if (j == lane) c = coef[j];
-  if (lane < P.n_comp) logc[lane] = c > 0.0 ? d_log(c) : -kInf();
+  if (lane < P.n_comp) cp->logc[lane] = c > 0.0 ? d_log(c) : -kInf();
+  if (lane == 0) {
+    for (int j = 0; j < RF_MAXC; ++j) cp->coef[j] = coef[j];
+    cp->ext_sum = es;
+    cp->bad = bad ? 1 : 0;
+  }
+}
+
+// CoefPre by one thread (the toy prep: one lane per toy).
+__device__ __forceinline__ void coef_pre_serial(const RfProgram& P, const double* params,
+                                                CoefPre* cp) {
+  double coef[RF_MAXC], es;
+  bool bad = false;
+  root_coefs(P, params, coef, &es, &bad);
+  for (int j = 0; j < RF_MAXC; ++j) {
+    cp->coef[j] = coef[j];
+    cp->logc[j] = (j < P.n_comp && coef[j] > 0.0) ? d_log(coef[j]) : -kInf();
+  }
+  cp->ext_sum = es;
+  cp->bad = bad ? 1 : 0;
 }
 
 // Combination constants (one thread), after every leaf's lnI is known.  X
 // (may be NULL): where FP32 evaluation with a zero coefficient gets its FP64
-// constants.  logc (may be NULL): the coefficients' logs, component c at
-// logc[c * logc_stride], from coef_logs_lanes or the like.
+// constants.  cp (may be NULL): the coefficients made ready (CoefPre);
+// without it they are computed here.
 template <typename Real>
 __device__ __noinline__ void comb_consts(const RfProgram& P, const double* params,
                                    RfConsts<Real>& K, const double* lnI,
                                    bool leaves_ok, RfExact* X = nullptr,
-                                   const double* logc = nullptr, int logc_stride = 1) {
+                                   const CoefPre* cp = nullptr) {
   bool bad = !leaves_ok;
   const int C = P.n_comp;
   double coef[RF_MAXC], base[RF_MAXC];
   for (int c = 0; c < RF_MAXC; ++c) base[c] = 0.0;
-  root_coefs(P, params, coef, &K.ext_sum, &bad);
+  if (cp) {
+    for (int c = 0; c < RF_MAXC; ++c) coef[c] = cp->coef[c];
+    K.ext_sum = cp->ext_sum;
+    bad |= cp->bad != 0;
+  } else {
+    root_coefs(P, params, coef, &K.ext_sum, &bad);
+  }
   for (int k = 0; k < P.n_leaves; ++k) base[P.leaf[k].comp] -= lnI[k];
   double beta[RF_MAXC];
   double ref = -kInf();
   int zero = 0;
   for (int c = 0; c < C; ++c) {
     if (coef[c] > 0.0) {
-      beta[c] = (logc ? logc[c * logc_stride] : d_log(coef[c])) + base[c];
+      beta[c] = (cp ? cp->logc[c] : d_log(coef[c])) + base[c];
       ref = fmax(ref, beta[c]);
     } else {
       beta[c] = -kInf();
@@ -735,6 +770,85 @@ __device__ __noinline__ void comb_consts(const RfProgram& P, const double* param
       for (int j = 0; j < RF_LEAF_MAXP; ++j) K.dtheta[k][j] = 0.0;
   }
   K.bad = bad ? 1 : 0;
+}
+
+// comb_consts on an aligned group of G lanes (all 32 lanes of the warp call
+// it, each group for its own dataset): component c on group lane c mod G, so
+// the per-component FP64 steps (the deltas and their FP32 roundings) run in
+// one pass, the reference beta_ref and the zero mask by shuffles over the
+// group.  lnI of leaf k at lnI[k * lnI_stride]; cp: the coefficients made
+// ready (required).  valid: the group has a dataset (false: it only takes
+// part in the shuffles, writes nothing).  A call with a zero coefficient and
+// X set (FP32 evaluation's exact constants) goes to comb_consts on the
+// group's first lane: same values, the rare path.
+template <typename Real, int G>
+__device__ __forceinline__ void comb_consts_group(const RfProgram& P, const double* params,
+                                                  RfConsts<Real>& K, const double* lnI,
+                                                  int lnI_stride, bool leaves_ok, RfExact* X,
+                                                  const CoefPre* cp, bool valid) {
+  constexpr int NCL = (RF_MAXC + G - 1) / G;  // components per lane
+  const int q = threadIdx.x & (G - 1);
+  const int C = P.n_comp;
+  double base[NCL], beta[NCL];
+  double ref = -kInf();
+  int zero = 0;
+#pragma unroll
+  for (int m = 0; m < NCL; ++m) {
+    const int c = q + m * G;
+    base[m] = 0.0;
+    beta[m] = -kInf();
+    if (c < C) {
+      for (int k = 0; k < P.n_leaves; ++k)
+        if (P.leaf[k].comp == c) base[m] -= lnI[k * lnI_stride];
+      if (cp->coef[c] > 0.0) {
+        beta[m] = cp->logc[c] + base[m];
+        ref = fmax(ref, beta[m]);
+      } else {
+        zero |= 1 << c;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    ref = fmax(ref, __shfl_xor_sync(0xffffffffu, ref, o));
+    zero |= __shfl_xor_sync(0xffffffffu, zero, o);
+  }
+  bool bad = !leaves_ok || cp->bad != 0;
+  if (!(ref > -kInf()) || !isfinite(ref)) {
+    bad = true;
+    ref = 0.0;
+  }
+  if (!valid) return;
+  if (sizeof(Real) == 4 && zero != 0 && X) {
+    if (q == 0) {
+      double l[RF_MAXL];
+      for (int k = 0; k < P.n_leaves; ++k) l[k] = lnI[k * lnI_stride];
+      comb_consts<Real>(P, params, K, l, leaves_ok, X, cp);
+    }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < NCL; ++m) {
+    const int c = q + m * G;
+    if (c >= RF_MAXC) continue;
+    K.coef[c] = cp->coef[c];
+    if (c < C && !((zero >> c) & 1)) {
+      // in base-2 units per event; the remainder in natural units
+      const double d = beta[m] - ref;
+      K.delta[c] = (Real)(d * kLog2e);
+      K.delta_lo[c] = d - kLn2 * (double)K.delta[c];
+    } else {
+      K.delta[c] = (Real)(-kInf());
+      K.delta_lo[c] = 0.0;
+    }
+    K.delta_nc[c] = (Real)(c < C ? (base[m] - ref) * kLog2e : 0.0);
+  }
+  if (q == 0) {
+    K.beta_ref = ref;
+    K.zero_mask = zero;
+    K.ext_sum = cp->ext_sum;
+    K.bad = bad ? 1 : 0;
+  }
 }
 
 // All constants by one thread (batched prologue: one thread per toy).
@@ -1340,6 +1454,79 @@ __device__ __forceinline__ void epilogue_warp(const RfProgram& P, const RfConsts
     }
     *nll = v;
   }
+}
+
+// The epilogue on an aligned group of G lanes (G divides 32; all 32 lanes of
+// the warp call it, each group for its own totals T and constants K): the
+// NLL's terms split over the group's lanes and summed by a shuffle tree,
+// gradient component p on group lane p mod G.  Same formulas as epilogue();
+// the group's chains are about G times shorter (the FP64 unit takes one warp
+// instruction at a time however many lanes are active).  valid: the group
+// has a dataset (false: it only takes part in the shuffles, writes nothing).
+// Returns the NLL (+inf when bad) on every lane of the group.
+template <typename Real, int NL, int G>
+__device__ __forceinline__ double epilogue_group(const RfProgram& P, const RfConsts<Real>& K,
+                                                 const double* T, int64_t n, double* nll,
+                                                 double* grad, unsigned int* status, bool valid) {
+  const int q = threadIdx.x & (G - 1);
+  const int C = P.n_comp;
+  const int nterm = 1 + C + RF_LEAF_MAXP * P.n_leaves;
+  double L = 0.0;
+  for (int tau = q; tau < nterm; tau += G) {
+    double term = 0.0;
+    if (tau == 0) {
+      term = kLn2 * T[0];  // the per-event sums are in base-2 units
+    } else if (tau <= C) {
+      const int c = tau - 1;
+      if (!((K.zero_mask >> c) & 1)) term = T[1 + c] * K.delta_lo[c];
+    } else {
+      const int idx = tau - 1 - C, k = idx >> 2, j = idx & 3;
+      if ((P.leaf[k].gmask >> j) & 1)
+        term = -(T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] * K.dtheta[k][j]);
+    }
+    L += term;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+  double v = -((double)n * K.beta_ref + L) + K.ext_sum;
+  const bool bad = K.bad || !isfinite(v);
+  if (grad && valid) {
+    for (int p = q; p < P.n_par; p += G) {
+      double g = 0.0;
+      for (int k = 0; k < P.n_leaves; ++k) {
+        const RfLeafProg& lf = P.leaf[k];
+        for (int j = 0; j < RF_LEAF_MAXP; ++j)
+          if (((lf.gmask >> j) & 1) && lf.par[j] == p) {
+            const double S = ((K.zero_mask >> lf.comp) & 1) ? 0.0 : T[1 + lf.comp];
+            g -= T[1 + NL + k * RF_LEAF_MAXP + j] * K.gmul[k][j] - S * K.dlogI[k][j];
+          }
+      }
+      for (int c = 0; c < C; ++c) {
+        if (!((P.coef_free >> c) & 1)) continue;
+        if (P.kind == RF_KIND_FRAC && c < C - 1 && P.coef_par[c] == p) {
+          const double Rc = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
+          const int l = C - 1;
+          const double Rl = ((K.zero_mask >> l) & 1) ? T[1 + l] : T[1 + l] / K.coef[l];
+          g -= Rc - Rl;
+        } else if (P.kind == RF_KIND_EXT && P.coef_par[c] == p) {
+          const double Rc = ((K.zero_mask >> c) & 1) ? T[1 + c] : T[1 + c] / K.coef[c];
+          g += P.ext_weight - Rc;
+        }
+      }
+      const bool fx = p < 64 ? ((P.fixed_lo >> p) & 1) : ((P.fixed_hi >> (p - 64)) & 1);
+      if (fx) g = 0.0;
+      if (bad) g = kNaN();
+      grad[p] = g;
+    }
+  }
+  if (bad) v = kInf();
+  if (valid && q == 0) {
+    if (bad && status)
+      atomicOr(status, K.bad ? (unsigned)RF_STATUS_PARAM_DOMAIN_BIT
+                             : (unsigned)RF_STATUS_NONFINITE_BIT);
+    *nll = v;
+  }
+  return v;
 }
 
 }  // namespace rf

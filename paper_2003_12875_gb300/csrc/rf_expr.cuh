@@ -305,7 +305,11 @@ __device__ __noinline__ BesselKSums<R> besselk_sums(R nu, R z) {
   const R an = fx::abs(nu), tp = fx::asinh(an / z);
   const R eps = sizeof(R) == 4 ? R(1e-9) : R(1e-17);
   // t = 0 carries half weight: phi = 1, cosh t = 1, cosh(nu t) = 1, sinh = 0
-  R s0 = R(0.5), s1 = R(-0.5), s2 = R(0), s3 = R(0.5), s4 = R(0);
+  R s[5] = {R(0.5), R(-0.5), R(0), R(0.5), R(0)};
+  // FP32: Kahan compensation on every sum (some twenty terms of order one
+  // each; their rounding repeats for events of similar z, so it would not
+  // average out over a dataset)
+  R c[5] = {R(0), R(0), R(0), R(0), R(0)};
   for (int j = 1; j < 4000; ++j) {
     const R t = R(j) * h;
     const R em = expm1(t), et = em + R(1);
@@ -314,14 +318,21 @@ __device__ __noinline__ BesselKSums<R> besselk_sums(R nu, R z) {
     const R en = fx::exp(an * t), ien = R(1) / en;
     const R cn = R(0.5) * (en + ien), sn = copysign(R(0.5) * (en - ien), nu);
     const R pcn = ph * cn, psn = ph * sn;
-    s0 += pcn;
-    s1 -= ch * pcn;
-    s2 += t * psn;
-    s3 += ch * ch * pcn;
-    s4 -= t * ch * psn;
-    if (t > tp && ch * ch * pcn <= eps * s0) break;
+    const R v[5] = {pcn, -(ch * pcn), t * psn, ch * ch * pcn, -(t * ch * psn)};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if constexpr (sizeof(R) == 4) {
+        const R y = v[i] - c[i], tt = s[i] + y;
+        c[i] = (tt - s[i]) - y;
+        s[i] = tt;
+      } else {
+        s[i] += v[i];
+      }
+    }
+    if (t > tp && v[3] <= eps * s[0]) break;
   }
-  return BesselKSums<R>{h * s0, h * s1, h * s2, h * s3, h * s4};
+  return BesselKSums<R>{h * (s[0] - c[0]), h * (s[1] - c[1]), h * (s[2] - c[2]),
+                        h * (s[3] - c[3]), h * (s[4] - c[4])};
 }
 
 // log K_nu(z) and d log K_nu / dz as duals, their derivatives through nu, z
@@ -364,13 +375,13 @@ struct Hypatia2Leaf {
   // the normalisation kernel exports log phi and its derivatives in lambda
   // and zeta (FP64) into the row of the leaf's second slot
   static constexpr int kShapeRow = 1;
-  template <typename R>
-  static __device__ __forceinline__ Dual<R, 9> core(const Dual<R, 9>& d, const Dual<R, 9>& nu,
-                                                    const Dual<R, 9>& beta,
-                                                    const Dual<R, 9>& alpha,
-                                                    const Dual<R, 9>& delta2, Dual<R, 9>* slope) {
-    const Dual<R, 9> q = d * d + delta2, r = fx::sqrt(q), z = alpha * r;
-    const Dual<R, 9> L = (R(0.5) * (nu * fx::log(q)) + beta * d) + log_besselk(nu, z);
+  template <typename R, int N>
+  static __device__ __forceinline__ Dual<R, N> core(const Dual<R, N>& d, const Dual<R, N>& nu,
+                                                    const Dual<R, N>& beta,
+                                                    const Dual<R, N>& alpha,
+                                                    const Dual<R, N>& delta2, Dual<R, N>* slope) {
+    const Dual<R, N> q = d * d + delta2, r = fx::sqrt(q), z = alpha * r;
+    const Dual<R, N> L = (R(0.5) * (nu * fx::log(q)) + beta * d) + log_besselk(nu, z);
     if (slope) *slope = (nu * d / q + beta) + (alpha * d / r) * dlog_besselk(nu, z);
     return L;
   }
@@ -382,49 +393,60 @@ struct Hypatia2Leaf {
     return p[1] > R(0) && p[3] > R(0) && p[5] > R(0) && p[6] > R(0) && p[7] > R(0) && p[8] > R(0);
   }
   // log f - zeta and its derivatives d/dp_j from the nine parameters p[0..8]
-  // and the shape constants p[9..16]: delta^2 and its derivatives in
-  // (lambda, zeta, sigma), then alpha and its derivatives in the same three
-  // (per-call constants, computed once in FP64).  zeta enters only through
-  // them: the per-event sums then carry no constant term (the prologue takes
-  // zeta off log I and 1 off d log I/d zeta instead).
+  // and the per-call shape constants p[9..22] (computed once in FP64):
+  // delta^2 and its derivatives in (lambda, zeta, sigma) p[9..12], alpha and
+  // its derivatives in the same three p[13..16], then the low FP32 parts of
+  // those six derivatives p[17..22] (zero in FP64).  zeta enters only through
+  // delta^2 and alpha: the per-event sums then carry no constant term (the
+  // prologue takes zeta off log I and 1 off d log I/d zeta instead).  The
+  // duals carry d/d delta^2 (slot 1) and d/d alpha (slot 9) rather than the
+  // chain through them, which is applied at the end with the derivatives as
+  // hi + lo pairs: rounded once per call, those would otherwise shift every
+  // event's derivative alike.
   template <typename R>
   static __device__ __noinline__ Dual<R, 9> logf_shaped(R x, const R* __restrict__ p) {
-    using D = Dual<R, 9>;
+    using D = Dual<R, 10>;
     const D lam = D::var(p[0], 0), beta = D::var(p[2], 2);
     const D sigma = D::var(p[3], 3), mu = D::var(p[4], 4), a = D::var(p[5], 5);
     const D n = D::var(p[6], 6), a2 = D::var(p[7], 7), n2 = D::var(p[8], 8);
-    D out;
+    const D delta2 = D::var(p[9], 1), alpha = D::var(p[13], 9);
+    D L;
     if (!in_domain<R>(p)) {
-      out.v = R(0) / R(0);
+      L.v = R(0) / R(0);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) out.d[i] = R(0);
-      return out;
-    }
-    D delta2, alpha;
-    delta2.v = p[9];
-    alpha.v = p[13];
+      for (int i = 0; i < 10; ++i) L.d[i] = R(0);
+    } else {
+      const D nu = lam - R(0.5);
+      const D d = x - mu;
+      const D dL = -(a * sigma), dR = a2 * sigma;
+      if (d.v < dL.v || d.v > dR.v) {
+        const bool left = d.v < dL.v;
+        const D dJ = left ? dL : dR, m = left ? n : n2;
+        D k;
+        const D LJ = core<R, 10>(dJ, nu, beta, alpha, delta2, &k);
+        const D base = R(1) - (d - dJ) * k / m;
+        if (!(base.v > R(0))) {
+          L.v = -R(1) / R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) delta2.d[i] = alpha.d[i] = R(0);
-    delta2.d[0] = p[10], delta2.d[1] = p[11], delta2.d[3] = p[12];
-    alpha.d[0] = p[14], alpha.d[1] = p[15], alpha.d[3] = p[16];
-    const D nu = lam - R(0.5);
-    const D d = x - mu;
-    const D dL = -(a * sigma), dR = a2 * sigma;
-    if (d.v < dL.v || d.v > dR.v) {
-      const bool left = d.v < dL.v;
-      const D dJ = left ? dL : dR, m = left ? n : n2;
-      D k;
-      const D LJ = core<R>(dJ, nu, beta, alpha, delta2, &k);
-      const D base = R(1) - (d - dJ) * k / m;
-      if (!(base.v > R(0))) {
-        out.v = -R(1) / R(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) out.d[i] = R(0);
-        return out;
+          for (int i = 0; i < 10; ++i) L.d[i] = R(0);
+        } else {
+          L = LJ - m * fx::log(base);
+        }
+      } else {
+        L = core<R, 10>(d, nu, beta, alpha, delta2, nullptr);
       }
-      return LJ - m * fx::log(base);
     }
-    return core<R>(d, nu, beta, alpha, delta2, nullptr);
+    // chain rule through delta^2 and alpha, the products of the high parts
+    // first, then those of the low parts
+    const R A = L.d[1], B = L.d[9];
+    Dual<R, 9> out;
+    out.v = L.v;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out.d[i] = L.d[i];
+    out.d[0] = L.d[0] + fma(A, p[10], B * p[14]) + fma(A, p[17], B * p[20]);
+    out.d[1] = fma(A, p[11], B * p[15]) + fma(A, p[18], B * p[21]);
+    out.d[3] = L.d[3] + fma(A, p[12], B * p[16]) + fma(A, p[19], B * p[22]);
+    return out;
   }
   // log f and d log f / dp_j from the nine parameters alone (FP64, for the
   // normalisation kernel): log phi = log K_{lambda+1}(zeta) - log K_lambda(zeta)
@@ -435,9 +457,11 @@ struct Hypatia2Leaf {
   static __device__ __forceinline__ Dual<R, 9> logf(R x, const R* __restrict__ p,
                                                     R* lp_out = nullptr) {
     using D = Dual<R, 9>;
-    R q[17];
+    R q[23];
 #pragma unroll
     for (int j = 0; j < 9; ++j) q[j] = p[j];
+#pragma unroll
+    for (int j = 17; j < 23; ++j) q[j] = R(0);
     if (!in_domain<R>(p)) {
       if (lp_out) lp_out[0] = lp_out[1] = lp_out[2] = R(0) / R(0);
       return logf_shaped<R>(x, q);
@@ -483,14 +507,15 @@ struct Hypatia2Leaf {
 };
 
 // The per-event Hypatia2 leaf: u = add + log2 f, g_j = d log f/dp_j for the
-// wanted j (GM9: bit j for parameter j).  Its nine parameters and eight shape
-// constants sit in three consecutive leaf slots of the per-event constants:
-// row k p0..p3 then delta^2 (value, d/d lambda, d/d zeta, d/d sigma), row
-// k+1 p4..p7 then alpha (the same four), row k+2 p8.
+// wanted j (GM9: bit j for parameter j).  Its nine parameters and fourteen
+// shape constants sit in three consecutive leaf slots of the per-event
+// constants: row k p0..p3 then delta^2 (value, d/d lambda, d/d zeta,
+// d/d sigma), row k+1 p4..p7 then alpha (the same four), row k+2 p8 then the
+// low parts of delta^2's three derivatives and of alpha's.
 template <typename Real, int GM9>
 __device__ __forceinline__ void hypatia2_leaf(Real x, const Real* __restrict__ pc, Real& u,
                                               Real (&g)[9], Real add = Real(-0.0)) {
-  Real p[17];
+  Real p[23];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     p[j] = pc[j];
@@ -499,6 +524,8 @@ __device__ __forceinline__ void hypatia2_leaf(Real x, const Real* __restrict__ p
     p[13 + j] = pc[RF_PC + 4 + j];
   }
   p[8] = pc[2 * RF_PC];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) p[17 + j] = pc[2 * RF_PC + 1 + j];
   const Dual<Real, 9> L = Hypatia2Leaf::logf_shaped<Real>(x, p);
   u = L.v * Real(1.44269504088896340736) + add;
 #pragma unroll

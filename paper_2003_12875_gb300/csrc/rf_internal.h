@@ -39,11 +39,15 @@ typedef unsigned long long uintptr_t;
 // tree.  The block rows are split into at most RF_TREE_GROUPS contiguous
 // groups; the last block of a group to finish sums the group's rows into a
 // group row (rows gridDim.x + g of the partials), and the last group sums the
-// group rows.  Ticket words (RfWork::counter, RF_COUNTER_WORDS of them):
-// [0] the group ticket, [1] status, [2] Adam step, [RF_TREE_GROUPS ..
+// group rows (a grid of at most RF_TREE_GROUPS blocks: one level, the last
+// block sums the block rows).  Ticket words (RfWork::counter,
+// RF_COUNTER_WORDS of them): [0] the group ticket (the grid ticket of a
+// one-level tree), [1] status, [2] Adam step, [RF_TREE_GROUPS ..
 // 2*RF_TREE_GROUPS) one ticket per group.
 #define RF_TREE_GROUPS 32
 #define RF_COUNTER_WORDS (2 * RF_TREE_GROUPS)
+// lanes per toy of the toy finalize kernel (blocks of 32 toys)
+#define RF_FIN_GROUP 4
 // formula-leaf normalisation: 16-point Gauss-Legendre on RF_FORMULA_PANELS
 // panels, one node per thread, RF_FORMULA_BLOCKS blocks of 128 threads; per
 // leaf 1 + RF_LEAF_MAXP values (log I, then (dI/dp_j)/I)

@@ -306,13 +306,29 @@ struct BlockRow<double, NA, MASK> {
 // every block after its row is written; returns true in the one block that
 // holds the grid totals in tot[0..NA) (shared) afterwards.  The groups are
 // contiguous runs of gsz rows; each level sums its rows in a fixed order, so
-// the totals depend only on the grid size.  Each ticket is reset by the block
-// that takes its last number.
+// the totals depend only on the grid size.  A grid of at most RF_TREE_GROUPS
+// blocks has one level: its last block sums the block rows (a first level of
+// one-row groups would only add a ticket and its fences to a short call).
+// Each ticket is reset by the block that takes its last number.
 template <int NA, unsigned long long MASK>
 __device__ __forceinline__ bool grid_tree(double* partials, unsigned int* counter, double* red,
                                           double* tot) {
   __shared__ int s_last;
   const int64_t G = gridDim.x;
+  if (G <= RF_TREE_GROUPS) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool last = atomicAdd(counter, 1u) == (unsigned)(G - 1);
+      if (last) *counter = 0u;
+      s_last = last ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    rows_tree<NA, MASK>(partials, 0, G, red, tot);
+    return true;
+  }
   const int64_t gsz = (G + RF_TREE_GROUPS - 1) / RF_TREE_GROUPS;
   const int64_t ng = (G + gsz - 1) / gsz;
   const int64_t g = blockIdx.x / gsz;
@@ -460,15 +476,15 @@ __device__ inline void iterate_scalar(const RfProgram& P, const EvalConsts<Real,
 // independent tasks on separate warps (sub-partitions), and like functions go
 // on separate lanes of one instruction.  Task k < L: leaf k's integral on
 // lanes 0-1 (leaf_norm_pair); task L + k: leaf k's per-event constants on
-// lane 0; task 2L: the coefficients' logs, one per lane.  Warps take tasks
+// lane 0; task 2L: the coefficients, their logs one per lane (CoefPre).  Warps take tasks
 // round robin (warp w: tasks w, w + warps, ...), so any block of 32 threads
-// or more works; 2L + 1 warps run them all at once.  Thread 0 then combines
-// (no transcendental function left there).
+// or more works; 2L + 1 warps run them all at once.  Then lanes 0-7 of warp 0
+// combine, one component per lane (no transcendental function left there).
 template <typename Real>
 __device__ inline void block_prologue(const RfProgram& P, const double* params,
                                       RfConsts<Real>& K, double* lnI, int* ok,
                                       RfExact* X = nullptr) {
-  __shared__ double logc[RF_MAXC];
+  __shared__ CoefPre cpre;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
   const int NL = P.n_leaves, ntask = 2 * NL + 1;
@@ -485,14 +501,14 @@ __device__ inline void block_prologue(const RfProgram& P, const double* params,
     } else if (task < 2 * NL) {
       if (lane == 0) leaf_eval_consts(P, params, K, task - NL);
     } else {
-      coef_logs_lanes(P, params, lane, logc);
+      coef_pre_lanes(P, params, lane, &cpre);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
     bool all = true;
     for (int k = 0; k < NL; ++k) all &= ok[k] != 0;
-    comb_consts(P, params, K, lnI, all, X, logc);
+    comb_consts_group<Real, 8>(P, params, K, lnI, 1, all, X, &cpre, lane < 8);
   }
   __syncthreads();
 }
