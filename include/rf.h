@@ -252,15 +252,15 @@ rf_status rf_graph_bind_events(rf_graph* g, const void* events,
 /*   offsets        dev int64 [toys+1], non-decreasing, offsets[toys] <= n_events
  *   params_matrix  dev FP64 [toys * n_params], row t = toy t's parameters
  *   out            dev FP64 [toys * (1 + n_params)], row t = (NLL_t, grad_t)
- * Three kernels: a per-toy FP64 prologue (blocks of one warp per leaf and
- * 32 toys: warp k computes leaf k of each of the block's toys, lane l toy
- * 32b + l); a segment kernel that splits all toys' events
+ * Three kernels: a per-toy FP64 prologue (blocks of 32 toys, the leaves'
+ * integrals, per-event constants and coefficients on separate warps, then a
+ * 4-lane combine per toy); a segment kernel that splits all toys' events
  * [offsets[0], offsets[toys]) evenly over its warps (one grid of SMs x
  * blocks_per_sm blocks) and writes one row of partial sums per (warp, toy)
  * pair that share events (FP32 evaluation: each sum as an FP32 pair, FP64
- * evaluation: FP64); and a finalize kernel, one thread per toy, that widens
- * the toy's rows to FP64, sums them in a fixed order and writes (NLL, grad).  Results depend on the inputs and the launch shape
- * only.  Offsets outside [0, n_events] are clamped and a decreasing pair
+ * evaluation: FP64); and a finalize kernel, 4 lanes per toy, that widens the
+ * toy's rows to FP64, sums them in a fixed order and writes (NLL, grad).
+ * Results depend on the inputs and the launch shape only.  Offsets outside [0, n_events] are clamped and a decreasing pair
  * raises RF_STATUS_NONFINITE (the affected toys' results are then
  * meaningless, but nothing outside the bound columns is read).  No
  * allocation, no host sync: capturable. */
