@@ -216,7 +216,11 @@ rf_status rf_graph_destroy(rf_graph* g);
  * event pass; it reads `params` while that kernel may still run, so params
  * must not be written by the kernels of the call immediately before on the
  * same stream (e.g. passing one call's gradient output as the next call's
- * params).  Work of any other kind between the two calls orders as usual. */
+ * params).  When the root is a leaf or a product of leaves, the event kernel
+ * too starts beside the prologue (it builds the leaves' per-event constants
+ * itself and waits for the integrals only before its reduction), under the
+ * same condition.  Work of any other kind between the two calls orders as
+ * usual. */
 rf_status rf_nll(rf_graph* g, const void* events, int64_t n_events,
                  const double* params, double* nll, double* grad,
                  rf_stream stream);

@@ -529,7 +529,33 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
   __shared__ RfExact Xs;  // FP64 constants when the block builds its own
 
   const RfExact* X = W.consts_x;
-  if (W.consts) {
+  // A product root (one component, coefficient 1) whose leaves need nothing
+  // from the normalisation kernel: the event pass uses only the leaves'
+  // per-event constants (a few FP64 divisions), so every block builds those
+  // itself and streams at once, beside the prologue.  The integrals and the
+  // combination enter only the epilogue: each block waits for the prologue
+  // before it writes its row (the prologue has itself waited for the
+  // previous call's grid, which is then done with the rows and tickets), and
+  // the block that finishes the tree loads the prologue's constants.
+  const bool early = W.consts && P.kind == RF_KIND_PROD && !P.formula_norm;
+  if (early) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = wid; k < P.n_leaves; k += nw)
+      if (lane == 0) leaf_eval_consts(P, params, K, k);
+    if (threadIdx.x < RF_MAXC) {
+      K.delta[threadIdx.x] = Real(0);
+      K.delta_nc[threadIdx.x] = Real(0);
+    }
+    if (threadIdx.x == 0) {
+      K.zero_mask = 0;
+      K.bad = 0;
+    }
+    __syncthreads();
+    // the next call's prologue may start (it publishes new constants only
+    // after this grid has finished)
+    asm volatile("griddepcontrol.launch_dependents;");
+  } else if (W.consts) {
     // constants from the prologue kernel, which this launch may overlap:
     // wait for it (a no-op when this grid was not launched as its dependent)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -575,9 +601,18 @@ __device__ __forceinline__ void fused_body(const RfProgram& P, const Col* __rest
     }
   }
 
+  if (early) asm volatile("griddepcontrol.wait;" ::: "memory");
   BlockRow<Real, NA, M::AMASK>::write(acc, red, W.partials + (int64_t)blockIdx.x * RF_NACC_MAX);
-  if (grid_tree<NA, M::AMASK>(W.partials, W.counter, red, tot) && threadIdx.x < 32)
-    epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
+  if (grid_tree<NA, M::AMASK>(W.partials, W.counter, red, tot)) {
+    if (early) {  // the prologue's constants (integrals, combination)
+      constexpr int kWords = (int)(sizeof(RfConsts<Real>) / sizeof(double));
+      const double* src = static_cast<const double*>(W.consts);
+      double* dst = reinterpret_cast<double*>(&K);
+      for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = __ldcg(src + w);
+      __syncthreads();
+    }
+    if (threadIdx.x < 32) epilogue_warp<Real, NL>(P, K, tot, n, nll, grad, W.status);
+  }
 }
 
 // Per-event log P(x_i) = beta_ref + ell_i (FP64 output), one event per thread.
