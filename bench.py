@@ -597,6 +597,8 @@ def main():
                     help="run the precompiled generic kernels instead of the per-graph ones")
     ap.add_argument("--min-blocks", type=int, default=0,
                     help="register budget of the specialised kernel (2, 3 or 4; with --no-tune)")
+    ap.add_argument("--block", type=int, default=0,
+                    help="threads per block of the fused kernel (64, 128 or 256; with --no-tune)")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="grid of the fused kernel in blocks per SM (1..8; with --no-tune)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -639,6 +641,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     tuned_ms = None
+    if args.block:
+        G.set_launch(block=args.block)
     if args.ept:
         G.set_launch(ept=args.ept)
     if args.min_blocks:
