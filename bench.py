@@ -155,7 +155,9 @@ LEAF_INSTR = {
     "exp": (3, {0: 0}, 0),                  # 1 when the range starts at 0 (no shift)
     "cheb": (11, {0: 1, 1: 1, 2: 1, 3: 1}, 1),
     "cb": (8, {0: 0, 1: 1, 2: 3, 3: 3}, 3),
-    "argus": (10, {0: 6, 1: 0, 2: 4}, 0),   # a free p: the general form (+2) and d/dp (+2)
+    # p = 1/2 on m0^2 - x^2 (no normalising multiply); d/dm0 needs tau (+1 of
+    # its 7); a free p: the general form (+3) and d/dp (+2)
+    "argus": (9, {0: 7, 1: 0, 2: 5}, 0),
     "johnson": (12, {0: 0, 1: 1, 2: 0, 3: 1}, 5),
 }
 F64_TO_F32_INSTR = 9   # integer-pipe rounding of an FP64 column value

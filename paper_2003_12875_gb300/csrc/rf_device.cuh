@@ -319,7 +319,10 @@ static __device__ __noinline__ bool leaf_lognorm(int type, int gm, const double*
       double ea = (1.0 - ta) * sqrt(ta) * Ea;
       double eb = tb > 0.0 ? (1.0 - tb) * sqrt(tb) * Eb : 0.0;
       double dIm = m0 * (ea - eb) + 2.0 * I / m0;
-      *lnI = d_log(I);
+      // log I + log m0: the per-event p = 1/2 form carries log m0 (leaf_argus);
+      // the derivatives stay those of log I, like the per-event ones, and
+      // the two constants cancel in the gradient
+      *lnI = d_log(I * m0);
       dln[0] = dIm / I;
       dln[1] = dIc / I;
       return I > 0.0 && isfinite(I);
@@ -441,7 +444,7 @@ __device__ inline void leaf_pc(const RfLeafProg& L, const double* th, T* pc) {
       pc[1] = (T)((sq - (double)pc[0]) + e);
       pc[2] = (T)(1.0 / sq);
       pc[3] = (T)(th[1] * kLog2e);  // c in base-2 units (for u)
-      pc[4] = (T)(2.0 / th[0]);
+      pc[4] = (T)(th[1] * kLog2e / sq);  // the same over m0^2 (the p = 1/2 form)
       split_hi_lo(th[2], pc[5], pc[7]);  // p (general-p form), hi + lo
       pc[6] = (T)th[1];  // c (for the m0 derivative)
       break;
@@ -538,7 +541,12 @@ __device__ __noinline__ void leaf_eval_consts(const RfProgram& P, const double* 
       if (L.type == RFL_HYPATIA2) K.dtheta[k][1] = 0.0;
       break;
     case RFL_ARGUS:
-      K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
+      if (L.gmask & (4 | RF_ARGUS_GENERAL)) {
+        K.dtheta[k][1] = kLn2 * (double)pc[3] - th[1];
+      } else {  // p = 1/2: c' = c log2(e)/m0^2 per event, d u/d c = tq/m0^2
+        K.dtheta[k][1] = kLn2 * (double)pc[4] * (th[0] * th[0]) - th[1];
+        K.gmul[k][1] = 1.0 / (th[0] * th[0]);
+      }
       if (L.gmask & 4) K.dtheta[k][2] = ((double)pc[5] + (double)pc[7]) - th[2];
       K.gmul[k][0] = 2.0 / th[0];  // d u/d m0 = (2/m0) (p/tau + c)(1 - tau)
       break;
@@ -1043,28 +1051,37 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
 // RF_ARGUS_GENERAL: p fixed away from 1/2) p = pc[5] + pc[7], and with bit 2
 // d u/d p = log tau; otherwise p is 1/2 and u = (1/2) log2(x^2 tau) + c tau
 // (one log; x^2 tau clamped at 0 gives -inf at and above m0, where the
-// component's weight, and so every derivative term, is 0).
+// component's weight, and so every derivative term, is 0), evaluated on
+// m0^2 - x^2 itself (see the p = 1/2 branch).
 template <typename Real, int GM>
 __device__ __forceinline__ void leaf_argus(Real x, const Real* __restrict__ pc, Real& u,
                                            Real (&g)[RF_LEAF_MAXP], Real add = Real(-0.0)) {
   typedef Fn<Real> F;
-  const Real tau = (fma(-x, x, pc[0]) + pc[1]) * pc[2];
+  const Real tq = fma(-x, x, pc[0]) + pc[1];  // m0^2 - x^2
   constexpr bool general = (GM & (4 | RF_ARGUS_GENERAL)) != 0;
-  // pc[3] = c log2(e) for u (base 2), pc[6] = c for the derivatives
-  const Real ct = fma(pc[3], tau, add);
+  Real tau;
   if (general) {
+    tau = tq * pc[2];
+    // pc[3] = c log2(e) for u (base 2)
+    const Real ct = fma(pc[3], tau, add);
     const bool ok = tau > Real(0);
     // p = pc[5] + pc[7] (hi + lo: a fixed p has no d/dp sum to correct its
     // rounding with)
     const Real lt = F::lg2(tau);
     u = ok ? fma(pc[7], lt, fma(pc[5], lt, ct) + F::lg2(x)) : F::ninf();
     g[2] = ((GM & 4) && ok) ? Real(kLn2) * lt : Real(0);
+    g[1] = (GM & 2) ? tau : Real(0);
   } else {
-    u = fma(Real(0.5), F::lg2(fmax(x * x * tau, Real(0))), ct);
+    // p = 1/2 on the unnormalised tq = m0^2 tau: u = (1/2) log2(x^2 tq) +
+    // c' tq with c' = c log2(e)/m0^2 (pc[4]), the form above plus log2 m0
+    // (the prologue adds ln m0 to log I), one multiply fewer per event
+    u = fma(Real(0.5), F::lg2(fmax(x * x * tq, Real(0))), fma(pc[4], tq, add));
     g[2] = Real(0);
+    g[1] = (GM & 2) ? tq : Real(0);  // times 1/m0^2 (gmul)
+    if (GM & 1) tau = tq * pc[2];
   }
-  g[1] = (GM & 2) ? tau : Real(0);
   if (GM & 1) {
+    // pc[6] = c
     const Real p = general ? pc[5] : Real(0.5);
     const Real r = F::rcp(tau);
     g[0] = tau > Real(0) ? (p * r + pc[6]) * (Real(1) - tau) : Real(0);  // times 2/m0 (gmul)
