@@ -337,7 +337,7 @@ def small_configs(rf, torch, rates=None, hbm_gbs=None):
     a host loop of calls on one stream, and the same calls replayed from a
     CUDA graph (GPU time only); C2 (8 MB) and C3 (120 MB) also with L2
     flushed before every call (L2Flush).  FP32 evaluation, plus FP64
-    evaluation for C1 and C2; C3 at the tuner's launch."""
+    evaluation for C1 and C2; C2 and C3 at the tuner's launch."""
     import numpy as np
 
     res = {}
@@ -349,7 +349,7 @@ def small_configs(rf, torch, rates=None, hbm_gbs=None):
         params = torch.tensor(w["spec"]["params"], dtype=torch.float64, device="cuda")
         for prec in precs:
             G = rf.Graph(w["spec"], w["dtype"], prec)
-            if name == "c3":  # the HBM-bound one: its launch shape matters
+            if name in ("c2", "c3"):  # events enough for the launch shape to matter
                 G.tune(ev, params)
             out = torch.empty(1 + len(w["spec"]["params"]), dtype=torch.float64, device="cuda")
             for _ in range(20):
