@@ -950,6 +950,12 @@ struct Fn<float> {
   static __device__ __forceinline__ float ex2_exact(float x) { return exp2f(x); }
   static __device__ __forceinline__ float exp(float x) { return expf(x); }
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  // 1/x from lg2x = lg2(x), already at hand: 2^(-lg2x), one ex2 (the special
+  // function unit issues ex2 at twice the rate of rcp)
+  static __device__ __forceinline__ float rcp_lg(float x, float lg2x) {
+    (void)x;
+    return ex2_fast(-lg2x);
+  }
   static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float ninf() { return -__int_as_float(0x7f800000); }
 };
@@ -963,6 +969,10 @@ struct Fn<double> {
   static __device__ __forceinline__ double ex2_exact(double x) { return ::exp2(x); }
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rcp_lg(double x, double lg2x) {
+    (void)lg2x;
+    return 1.0 / x;
+  }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   static __device__ __forceinline__ double ninf() { return -kInf(); }
 };
@@ -1034,7 +1044,7 @@ __device__ __forceinline__ void leaf_cb(Real x, const Real* __restrict__ pc, Rea
   const Real Lg = F::lg2(D);  // log2 D, used only in the tail, where D >= 1
   u = tail ? fma(pc[6], Lg, pc[7] + add) : fma(-s, s, add);
   if (GM & 15) {
-    const Real rD = F::rcp(D);
+    const Real rD = F::rcp_lg(D, Lg);  // used in the tail, where D >= 1
     const Real h = tail ? pc[4] * rD : s;
     g[0] = (GM & 1) ? h : Real(0);
     g[1] = (GM & 2) ? h * s : Real(0);
@@ -1149,11 +1159,12 @@ __device__ __forceinline__ Real lse(const Real (&v)[NC], Real (&w)[NC]) {
     Real dv = v[1] - v[0];
     Real e = F::ex2(-fabs(dv));
     Real s = Real(1) + e;
-    Real rs = F::rcp(s);
+    const Real ls = F::lg2(s);  // s in [1, 2], or NaN from NaN inputs
+    Real rs = F::rcp_lg(s, ls);
     Real wb = rs, ws = e * rs;
     w[0] = dv > Real(0) ? ws : wb;
     w[1] = dv > Real(0) ? wb : ws;
-    return fmax(v[0], v[1]) + F::lg2(s);  // s in [1, 2], or NaN from NaN inputs
+    return fmax(v[0], v[1]) + ls;
   } else {
     Real m = v[0];
 #pragma unroll
